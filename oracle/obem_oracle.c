@@ -1,0 +1,787 @@
+/*
+ * obem_oracle.c -- plain, slow, CPU reference ("oracle") for the OuroborosBEM
+ * field + tracking-step method (arXiv 2110.09214).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
+ * only the test-suite, the smoke check and the CPU-baseline leg of the bench
+ * load it.  It shares no source with the CUDA library.
+ *
+ * Floating point:
+ *   - geometry, panel integrals, the panel field, the N-body field, the BEM
+ *     matrix and its Gaussian elimination are FP64;
+ *   - the tracking step (flight, null-collision trials, ionisation, attachment,
+ *     recombination distances) is computed in IEEE binary32 with one rounding
+ *     per basic operation (build with -ffp-contract=off, no fast-math), because
+ *     every integer decision of the step (collision process, spawn count,
+ *     recombination partner) must be taken in the precision of the kernel.
+ *
+ * Every function cites the passage of the paper it restates.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018, SI */
+#define OR_E    1.602176634e-19
+#define OR_ME   9.1093837015e-31
+#define OR_EPS0 8.8541878128e-12
+#define OR_KB   1.380649e-23
+#define OR_AMU  1.66053906660e-27
+#define OR_PI   3.14159265358979323846
+#define OR_KC   (1.0 / (4.0 * OR_PI * OR_EPS0))
+
+/* ------------------------------------------------------------------------- */
+/* small FP64 vector helpers                                                  */
+/* ------------------------------------------------------------------------- */
+static double dot3(const double *a, const double *b) { return a[0]*b[0] + a[1]*b[1] + a[2]*b[2]; }
+static void cross3(const double *a, const double *b, double *c) {
+    c[0] = a[1]*b[2] - a[2]*b[1];
+    c[1] = a[2]*b[0] - a[0]*b[2];
+    c[2] = a[0]*b[1] - a[1]*b[0];
+}
+static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+
+/* Geometry of a flat triangular cell (Sec. 2.2: flat cells, centroid
+ * collocation, unit normal).  v = 9 doubles (v0, v1, v2).  The normal is
+ * (v1-v0)x(v2-v0) normalised: it points from medium 1 (eps_minus) to medium 2
+ * (eps_plus), the orientation used by Eq. (fldinterf1/2) and (NBC). */
+void or_tri_geometry(const double *v, double *centroid, double *normal, double *area)
+{
+    double e1[3], e2[3], nn[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = v[3 + k] - v[k];
+        e2[k] = v[6 + k] - v[k];
+        centroid[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0;
+    }
+    cross3(e1, e2, nn);
+    double a2 = norm3(nn);
+    for (int k = 0; k < 3; ++k) normal[k] = nn[k] / a2;
+    *area = 0.5 * a2;
+}
+
+/* Log of the line integral of 1/R along one edge, written so that no
+ * difference of nearly equal numbers is formed (products (R+l)(R-l) = R0^2 are
+ * the same at both ends of the edge). */
+static double edge_log(double lm, double lp, double Rm, double Rp, double R0sq)
+{
+    if (lm >= 0.0) return log((Rp + lp) / (Rm + lm));
+    if (lp <= 0.0) return log((Rm - lm) / (Rp - lp));
+    return log((Rp + lp) * (Rm - lm) / R0sq);
+}
+
+/*
+ * Closed-form surface integrals of a uniform unit density over a flat
+ * triangle, at observation point r (Sec. 2.2 states that the cell integrals of
+ * Eqs. (BEMpot), (BEMfld), (BEM2), (BEM3) are evaluated analytically but does
+ * not print them; this is the standard edge decomposition of the potential of
+ * a planar polygon (Wilton et al. 1984) with the solid angle of Van Oosterom &
+ * Strackee 1983):
+ *
+ *   phi(r) = int_T dA' / |r - r'|
+ *          = sum_edges p0_i L_i - h * Omega
+ *   F(r)   = int_T (r - r') / |r - r'|^3 dA'
+ *          = Omega n + sum_edges u_i L_i
+ *
+ * with h = (r - v0).n, u_i the outward in-plane unit normal of edge i, p0_i the
+ * signed in-plane distance from the projection of r to edge i (positive
+ * inside), L_i = ln((R+ + l+)/(R- + l-)) the edge line integral of 1/R, and
+ * Omega the solid angle of the triangle seen from r, signed like h.
+ * In the plane of the cell (h = 0) the normal part is the principal value,
+ * i.e. the mean of the two one-sided limits -+ 2pi of Eq. (fldinterf1/2), 0.
+ */
+void or_tri_integrals(const double *v, const double *r, double *phi, double *F)
+{
+    double e1[3], e2[3], nn[3], n[3], a[3][3], R[3];
+    for (int k = 0; k < 3; ++k) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
+    cross3(e1, e2, nn);
+    double a2 = norm3(nn);                 /* twice the area */
+    for (int k = 0; k < 3; ++k) n[k] = nn[k] / a2;
+    for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 3; ++k) a[i][k] = v[3 * i + k] - r[k];
+        R[i] = norm3(a[i]);
+    }
+    double h = -dot3(a[0], n);
+    double phis = 0.0, Fin[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3;
+        double ed[3], lhat[3], uhat[3];
+        for (int k = 0; k < 3; ++k) ed[k] = v[3 * j + k] - v[3 * i + k];
+        double len = norm3(ed);
+        for (int k = 0; k < 3; ++k) lhat[k] = ed[k] / len;
+        cross3(lhat, n, uhat);
+        double lm = dot3(a[i], lhat), lp = dot3(a[j], lhat);
+        double p0 = dot3(a[i], uhat);
+        double R0sq = p0 * p0 + h * h;
+        double L = edge_log(lm, lp, R[i], R[j], R0sq);
+        if (p0 != 0.0) phis += p0 * L;
+        for (int k = 0; k < 3; ++k) Fin[k] += uhat[k] * L;
+    }
+    double D = R[0] * R[1] * R[2] + dot3(a[0], a[1]) * R[2] + dot3(a[0], a[2]) * R[1]
+             + dot3(a[1], a[2]) * R[0];
+    double Om = (h == 0.0) ? 0.0 : 2.0 * atan2(a2 * h, D);
+    *phi = phis - h * Om;
+    for (int k = 0; k < 3; ++k) F[k] = Fin[k] + Om * n[k];
+}
+
+/* Potential and field of all panels at nt points, Eqs. (BEM2), (BEM3):
+ *   V(r) = k_C sum_j sigma_j phi_j(r),  E(r) = k_C sum_j sigma_j F_j(r). */
+void or_panel_field(int np, const double *tri, const double *sigma, int nt,
+                    const double *pts, double *E, double *V)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int t = 0; t < nt; ++t) {
+        double ex = 0, ey = 0, ez = 0, vv = 0;
+        for (int j = 0; j < np; ++j) {
+            double phi, F[3];
+            or_tri_integrals(tri + 9 * (size_t)j, pts + 3 * (size_t)t, &phi, F);
+            ex += sigma[j] * F[0]; ey += sigma[j] * F[1]; ez += sigma[j] * F[2];
+            vv += sigma[j] * phi;
+        }
+        E[3 * t] = OR_KC * ex; E[3 * t + 1] = OR_KC * ey; E[3 * t + 2] = OR_KC * ez;
+        if (V) V[t] = OR_KC * vv;
+    }
+}
+
+/* Coulomb field of point charges, Eq. (nbody):
+ *   E(r_t) = k_C sum_{p != t} q_p (r_t - r_p) / |r_t - r_p|^3
+ * src = [x,y,z,q] per source.  self_exclude: target t and source t are the same
+ * charge and that pair is skipped.  soft > 0 replaces |r|^2 by |r|^2 + soft^2
+ * (Plummer); soft == 0 is the paper's sum, in which pairs at zero distance are
+ * skipped (the sum is undefined there). */
+void or_nbody_field(int nt, const double *pts, int ns, const double *src,
+                    int self_exclude, double soft, double *E, double *V)
+{
+    double s2 = soft * soft;
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < nt; ++t) {
+        double ex = 0, ey = 0, ez = 0, vv = 0;
+        const double *r = pts + 3 * (size_t)t;
+        for (int p = 0; p < ns; ++p) {
+            if (self_exclude && p == t) continue;
+            const double *s = src + 4 * (size_t)p;
+            double dx = r[0] - s[0], dy = r[1] - s[1], dz = r[2] - s[2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 == 0.0 && s2 == 0.0) continue;
+            r2 += s2;
+            double ir = 1.0 / sqrt(r2);
+            double w = s[3] * ir * ir * ir;
+            ex += w * dx; ey += w * dy; ez += w * dz;
+            vv += s[3] * ir;
+        }
+        E[3 * t] = OR_KC * ex; E[3 * t + 1] = OR_KC * ey; E[3 * t + 2] = OR_KC * ez;
+        if (V) V[t] = OR_KC * vv;
+    }
+}
+
+/*
+ * Dense BEM matrix, Eqs. (BEMpot), (BEMfld), (matrixBEM), row-major n x n.
+ *   electrode (ed) rows:   A_ij = Q_ij = k_C phi_j(r_i)
+ *   dielectric (dd) rows:  A_ij = W_ij = (er+ + er-)/2 delta_ij
+ *                                 + (er+ - er-)/(4 pi) F_j(r_i).n_i   (j != i)
+ * r_i, n_i are the centroid and normal of cell i; er-/er+ are the relative
+ * permittivities on the negative / positive side of cell i.  For j == i the
+ * integral term vanishes for a flat cell (r_i - r' is in the cell's plane).
+ */
+void or_assemble(int np, const double *tri, const int *kind, const double *er_minus,
+                 const double *er_plus, double *A)
+{
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int i = 0; i < np; ++i) {
+        double c[3], n[3], area;
+        or_tri_geometry(tri + 9 * (size_t)i, c, n, &area);
+        for (int j = 0; j < np; ++j) {
+            double phi, F[3];
+            or_tri_integrals(tri + 9 * (size_t)j, c, &phi, F);
+            double aij;
+            if (kind[i] == 0) {
+                aij = OR_KC * phi;
+            } else if (i == j) {
+                aij = 0.5 * (er_plus[i] + er_minus[i]);
+            } else {
+                aij = (er_plus[i] - er_minus[i]) / (4.0 * OR_PI) * dot3(F, n);
+            }
+            A[(size_t)i * np + j] = aij;
+        }
+    }
+}
+
+/* Gaussian elimination with partial pivoting, in place; solves A x = b, x
+ * returned in b.  Returns 0, or -1 on an exactly singular pivot.  (Sec. 2.2:
+ * the dense system (matrixBEM) is solved directly.) */
+int or_solve_gepp(int n, double *A, double *b)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        double best = fabs(A[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; ++i) {
+            double v = fabs(A[(size_t)i * n + k]);
+            if (v > best) { best = v; p = i; }
+        }
+        if (best == 0.0) return -1;
+        if (p != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[(size_t)k * n + j]; A[(size_t)k * n + j] = A[(size_t)p * n + j]; A[(size_t)p * n + j] = t;
+            }
+            double t = b[k]; b[k] = b[p]; b[p] = t;
+        }
+        double piv = A[(size_t)k * n + k];
+        for (int i = k + 1; i < n; ++i) {
+            double f = A[(size_t)i * n + k] / piv;
+            if (f == 0.0) continue;
+            for (int j = k + 1; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+            b[i] -= f * b[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < n; ++j) s -= A[(size_t)i * n + j] * b[j];
+        b[i] = s / A[(size_t)i * n + i];
+    }
+    return 0;
+}
+
+/*
+ * Influence of point charges on the cells, Eqs. (potpart), (fldpart): the
+ * cell-averaged potential and field of the charges,
+ *   Vbar_i = k_C sum_p q_p phi_i(r_p) / A_i
+ *   Ebar_i = k_C sum_p q_p int_Ci (r - r_p)/|r - r_p|^3 dA / A_i
+ *          = -k_C sum_p q_p F_i(r_p) / A_i
+ * and the right-hand-side correction of Eqs. (BEMpotpart), (BEMfldpart):
+ *   ed rows: -Vbar_i;   dd rows: -(er+ - er-) eps0 Ebar_i . n_i
+ */
+void or_influence_rhs(int np, const double *tri, const int *kind, const double *er_minus,
+                      const double *er_plus, int nq, const double *src, double *drhs)
+{
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int i = 0; i < np; ++i) {
+        double c[3], n[3], area;
+        or_tri_geometry(tri + 9 * (size_t)i, c, n, &area);
+        double vs = 0.0, es[3] = {0, 0, 0};
+        for (int p = 0; p < nq; ++p) {
+            double phi, F[3];
+            or_tri_integrals(tri + 9 * (size_t)i, src + 4 * (size_t)p, &phi, F);
+            double q = src[4 * (size_t)p + 3];
+            vs += q * phi;
+            es[0] -= q * F[0]; es[1] -= q * F[1]; es[2] -= q * F[2];
+        }
+        if (kind[i] == 0) drhs[i] = -OR_KC * vs / area;
+        else drhs[i] = -(er_plus[i] - er_minus[i]) * OR_EPS0 * OR_KC * dot3(es, n) / area;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), counter-based RNG.      */
+/* ------------------------------------------------------------------------- */
+void or_philox4x32_10(const uint32_t *ctr_in, const uint32_t *key_in, uint32_t *out)
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The tracking step, IEEE binary32, one rounding per operation.              */
+/* ------------------------------------------------------------------------- */
+enum { K_ELASTIC = 0, K_EXCITATION = 1, K_IONISATION = 2, K_ATTACHMENT = 3 };
+enum { SP_ELECTRON = 0, SP_CATION = 1, SP_ANION = 2 };
+enum { ST_OK = 0, ST_CAPACITY = -6, ST_TRIALS = -8 };
+
+/* uniform in [0,1) from the top 24 bits of a 32-bit draw */
+static float u01(uint32_t u) { return (float)(u >> 8) * 5.9604645e-08f; }
+
+/* -ln(U) for U = ((u >> 8) + 1) 2^-24 in (0, 1]; written with basic binary32
+ * operations only: U = 2^(e-24) f, f in [1,2), ln f = 2 atanh((f-1)/(f+1)) by
+ * its odd series to t^13 (|t| < 1/3, truncation < 1e-8). */
+static float neg_log_u(uint32_t u)
+{
+    uint32_t m = (u >> 8) + 1u;          /* 1 .. 2^24 */
+    int e = 31 - __builtin_clz(m);       /* floor(log2 m) */
+    float mf = (float)m;
+    float f = mf / (float)(1u << e);     /* exact: power-of-two scaling */
+    float t = (f - 1.0f) / (f + 1.0f);
+    float t2 = t * t;
+    float s = 0.07692308f;               /* 1/13 */
+    s = s * t2 + 0.09090909f;            /* 1/11 */
+    s = s * t2 + 0.11111111f;            /* 1/9  */
+    s = s * t2 + 0.14285715f;            /* 1/7  */
+    s = s * t2 + 0.2f;                   /* 1/5  */
+    s = s * t2 + 0.33333334f;            /* 1/3  */
+    s = s * t2 + 1.0f;
+    float lnf = 2.0f * t * s;
+    float a = (float)(24 - e) * 0.6931472f;
+    return a - lnf;
+}
+
+/* sin and cos of a in [0, pi/2) by Taylor polynomials in a^2 (Horner),
+ * binary32 basic operations only. */
+static void sincos_q(float a, float *s, float *c)
+{
+    float a2 = a * a;
+    float ps = -1.6059044e-10f;          /* -1/13! */
+    ps = ps * a2 + 2.5052108e-08f;       /*  1/11! */
+    ps = ps * a2 - 2.7557319e-06f;       /* -1/9!  */
+    ps = ps * a2 + 0.0001984127f;        /*  1/7!  (sign applied below) */
+    ps = ps * a2 - 0.008333334f;
+    ps = ps * a2 + 0.16666667f;
+    ps = ps * a2 - 1.0f;
+    *s = -(a * ps);
+    float pc = 2.0876756e-09f;           /*  1/12! */
+    pc = pc * a2 - 2.755732e-07f;        /* -1/10! */
+    pc = pc * a2 + 2.4801588e-05f;       /*  1/8!  */
+    pc = pc * a2 - 0.0013888889f;        /* -1/6!  */
+    pc = pc * a2 + 0.041666668f;         /*  1/4!  */
+    pc = pc * a2 - 0.5f;
+    pc = pc * a2 + 1.0f;
+    *c = pc;
+}
+
+/* Isotropic unit direction from two 32-bit draws: cos(theta) = 1 - 2u,
+ * phi = 2 pi u' with the quadrant from the top two of u''s 24 bits. */
+static void iso_dir(uint32_t ua, uint32_t ub, float *d)
+{
+    float c = 1.0f - 2.0f * u01(ua);
+    float cc = c * c;
+    float om = 1.0f - cc;
+    if (om < 0.0f) om = 0.0f;
+    float s = sqrtf(om);
+    uint32_t b = ub >> 8;
+    uint32_t q = b >> 22;
+    float f = (float)(b & 0x3FFFFFu) * 5.9604645e-08f;   /* [0, 1/4) */
+    float a = f * 6.2831855f;
+    float sa, ca;
+    sincos_q(a, &sa, &ca);
+    float cp, sp;
+    if (q == 0) { cp = ca; sp = sa; }
+    else if (q == 1) { cp = -sa; sp = ca; }
+    else if (q == 2) { cp = -ca; sp = -sa; }
+    else { cp = sa; sp = -ca; }
+    d[0] = s * cp; d[1] = s * sp; d[2] = c;
+}
+
+/* one unit in the last place of x toward +inf (dir > 0) or -inf (dir < 0) */
+static float ulp_step(float x, float dir)
+{
+    return nextafterf(x, dir > 0.0f ? INFINITY : -INFINITY);
+}
+
+typedef struct {
+    /* primary parameters */
+    double dt, T, N, M_amu, nu_ion, z_lo, z_hi, beta;
+    uint32_t seed_lo, seed_hi;
+    int trial_cap;
+    /* gas table */
+    int n_proc, n_e;
+    const float *egrid, *xs, *thr, *nuc;
+    const int *pkind, *pmode;
+    /* derived binary32 constants */
+    float dt_f, nu_max_e, nu_ion_f, half_nu_ion, E_therm, v_th_ion, qm[3], K_e, K_ion,
+          two_m_over_M, KCE, N_f, z_lo_f, z_hi_f, rc2, ion_thr;
+    int recomb_on;
+} or_gas;
+
+/* Derived constants: each is computed in FP64 from the primary parameters and
+ * rounded once to binary32. */
+static void gas_derive(or_gas *g)
+{
+    double M = g->M_amu > 0 ? g->M_amu * OR_AMU : INFINITY;
+    g->dt_f = (float)g->dt;
+    g->nu_ion_f = (float)g->nu_ion;
+    g->half_nu_ion = (float)(0.5 * g->nu_ion);
+    g->E_therm = (float)(1.5 * OR_KB * g->T / OR_E);
+    g->v_th_ion = isinf(M) ? 0.0f : (float)sqrt(3.0 * OR_KB * g->T / M);
+    g->qm[SP_ELECTRON] = (float)(-OR_E / OR_ME);
+    g->qm[SP_CATION] = isinf(M) ? 0.0f : (float)(OR_E / M);
+    g->qm[SP_ANION] = isinf(M) ? 0.0f : (float)(-OR_E / M);
+    g->K_e = (float)(0.5 * OR_ME / OR_E);
+    g->K_ion = isinf(M) ? 0.0f : (float)(0.5 * M / OR_E);
+    g->two_m_over_M = isinf(M) ? 0.0f : (float)(2.0 * OR_ME / M);
+    g->KCE = (float)(OR_KC * OR_E);
+    g->N_f = (float)g->N;
+    g->z_lo_f = (float)g->z_lo;
+    g->z_hi_f = (float)g->z_hi;
+    /* majorant of the electron collision frequency (null-collision method,
+     * Skullerud 1968, cited in Sec. 3.3.1): constant-frequency processes add
+     * their frequency; tabulated ones are bounded on every grid segment by
+     * N max(sigma_tot(E_i), sigma_tot(E_i+1)) v(E_i+1). */
+    double nuc = 0.0, best = 0.0;
+    g->ion_thr = 0.0f;
+    for (int j = 0; j < g->n_proc; ++j) {
+        if (g->pmode[j] == 1) nuc += (double)g->nuc[j];
+        if (g->pkind[j] == K_IONISATION && g->ion_thr == 0.0f) g->ion_thr = g->thr[j];
+    }
+    for (int i = 0; i + 1 < g->n_e; ++i) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < g->n_proc; ++j) {
+            if (g->pmode[j] != 0) continue;
+            s0 += (double)g->xs[(size_t)j * g->n_e + i];
+            s1 += (double)g->xs[(size_t)j * g->n_e + i + 1];
+        }
+        double v1 = sqrt(2.0 * (double)g->egrid[i + 1] * OR_E / OR_ME);
+        double b = g->N * (s0 > s1 ? s0 : s1) * v1;
+        if (b > best) best = b;
+    }
+    g->nu_max_e = (float)(nuc + best);
+    /* recombination capture radius: with a rate coefficient beta the sphere
+     * swept in one step, R_c = (3 beta dt / 4 pi)^(1/3); with beta == 0 the
+     * Coulomb distance of Eq. (distRecomb), k_C e / (2 E_ioni); beta < 0: off. */
+    g->recomb_on = g->beta >= 0.0;
+    double rc = 0.0;
+    if (g->beta > 0.0) rc = cbrt(3.0 * g->beta * g->dt / (4.0 * OR_PI));
+    else if (g->beta == 0.0 && g->ion_thr > 0.0f) rc = OR_KC * OR_E / (2.0 * (double)g->ion_thr);
+    else if (g->beta == 0.0) g->recomb_on = 0;
+    g->rc2 = (float)(rc * rc);
+}
+
+void or_gas_constants(const double *prm, int n_proc, int n_e, const float *egrid,
+                      const float *xs, const int *pkind, const int *pmode, const float *thr,
+                      const float *nuc, float *out)
+{
+    or_gas g;
+    memset(&g, 0, sizeof g);
+    g.dt = prm[0]; g.T = prm[1]; g.N = prm[2]; g.M_amu = prm[3]; g.nu_ion = prm[4];
+    g.z_lo = prm[5]; g.z_hi = prm[6]; g.beta = prm[7];
+    g.n_proc = n_proc; g.n_e = n_e; g.egrid = egrid; g.xs = xs; g.pkind = pkind; g.pmode = pmode;
+    g.thr = thr; g.nuc = nuc;
+    gas_derive(&g);
+    out[0] = g.nu_max_e; out[1] = g.E_therm; out[2] = g.v_th_ion; out[3] = g.rc2;
+    out[4] = g.KCE; out[5] = g.K_e; out[6] = g.two_m_over_M; out[7] = (float)g.recomb_on;
+}
+
+typedef struct {
+    int n_out_sp;      /* spawn records written */
+    int dead;          /* absorbed */
+    int attached;
+    int collisions;
+    int trials;
+    int status;
+} flight_result;
+
+typedef struct { float p[3], v[3]; float pi[3], vi[3]; uint32_t parent; } spawn_rec;
+
+/*
+ * Flight and null-collision trials of one charge over one step dt under the
+ * step-start field E (Sec. 3.2.5 Euler stepper: one field evaluation per step;
+ * Sec. 3.3.1 collision sampling, replaced by the exact null-collision method
+ * of the cited Skullerud 1968).  The charge's state (p, v, species) is updated
+ * in place; ionisations append spawn records (Sec. 3.3.3, Eq. (distIoni)).
+ */
+static void fly_one(const or_gas *g, uint32_t id, uint32_t step, float *p, float *v,
+                    uint8_t *sp, const float *E, spawn_rec *recs, int rec_cap,
+                    flight_result *fr)
+{
+    uint32_t key[2] = {g->seed_lo, g->seed_hi};
+    int s = *sp;
+    float qm = g->qm[s];
+    float a[3] = {qm * E[0], qm * E[1], qm * E[2]};
+    float ha[3] = {0.5f * a[0], 0.5f * a[1], 0.5f * a[2]};
+    float numax = (s == SP_ELECTRON) ? g->nu_max_e : g->nu_ion_f;
+    float t = 0.0f;
+    uint32_t k = 0;
+    for (;;) {
+        float tau;
+        uint32_t r[4] = {0, 0, 0, 0};
+        if (numax > 0.0f) {
+            k += 1;
+            if ((int)k > g->trial_cap) { fr->status = ST_TRIALS; return; }
+            uint32_t ctr[4] = {id, step, k, 0u};
+            or_philox4x32_10(ctr, key, r);
+            tau = neg_log_u(r[0]) / numax;
+        } else {
+            tau = INFINITY;
+        }
+        float tn = t + tau;
+        float fl = (tn >= g->dt_f) ? (g->dt_f - t) : tau;
+        for (int c = 0; c < 3; ++c) {
+            float w = ha[c] * fl;
+            float x = v[c] + w;
+            float y = x * fl;
+            p[c] = p[c] + y;
+            float dv = a[c] * fl;
+            v[c] = v[c] + dv;
+        }
+        if (p[2] <= g->z_lo_f || p[2] >= g->z_hi_f) { fr->dead = 1; return; }
+        if (tn >= g->dt_f) return;
+        t = tn;
+        fr->trials += 1;
+        /* collision trial at time t */
+        float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        float speed = sqrtf(v2);
+        float x = u01(r[1]) * numax;
+        float d[3];
+        if (s == SP_ELECTRON) {
+            float eps = g->K_e * v2;
+            int lo = 0, hi = g->n_e - 1;
+            float w;
+            if (eps < g->egrid[0]) { lo = 0; w = 0.0f; }
+            else if (eps >= g->egrid[g->n_e - 1]) { lo = g->n_e - 2; w = 1.0f; }
+            else {
+                while (hi - lo > 1) { int mid = (lo + hi) / 2; if (g->egrid[mid] <= eps) lo = mid; else hi = mid; }
+                w = (eps - g->egrid[lo]) / (g->egrid[lo + 1] - g->egrid[lo]);
+            }
+            float Ns = g->N_f * speed;
+            float cum = 0.0f;
+            int proc = -1;
+            for (int j = 0; j < g->n_proc; ++j) {
+                float nu;
+                if (g->pmode[j] == 1) {
+                    nu = g->nuc[j];
+                } else {
+                    float s0 = g->xs[(size_t)j * g->n_e + lo];
+                    float s1 = g->xs[(size_t)j * g->n_e + lo + 1];
+                    float ds = s1 - s0;
+                    float sg = s0 + w * ds;
+                    if (eps < g->thr[j]) sg = 0.0f;
+                    nu = Ns * sg;
+                }
+                cum = cum + nu;
+                if (x < cum) { proc = j; break; }
+            }
+            if (proc < 0) continue;                     /* null collision */
+            int kind = g->pkind[proc];
+            if (kind == K_ELASTIC) {
+                iso_dir(r[2], r[3], d);
+                float cosx = 0.0f;
+                if (speed > 0.0f) cosx = (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) / speed;
+                float om = 1.0f - cosx;
+                float loss = g->two_m_over_M * om;
+                float f = 1.0f - loss;
+                float sn = speed * sqrtf(f);
+                v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
+                fr->collisions += 1;
+            } else if (kind == K_EXCITATION) {
+                float e2 = eps - g->thr[proc];
+                if (e2 < 0.0f) e2 = 0.0f;
+                float sn = sqrtf(e2 / g->K_e);
+                iso_dir(r[2], r[3], d);
+                v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
+                fr->collisions += 1;
+            } else if (kind == K_IONISATION) {
+                float er = eps - g->thr[proc];
+                er = er - g->E_therm;
+                if (!(er > 0.0f)) continue;             /* not enough energy: null */
+                if (fr->n_out_sp >= rec_cap) { fr->status = ST_CAPACITY; return; }
+                float half = 0.5f * er;
+                float sn = sqrtf(half / g->K_e);
+                iso_dir(r[2], r[3], d);
+                float rr = g->KCE / (2.0f * er);
+                float o[3] = {rr * d[0], rr * d[1], rr * d[2]};
+                spawn_rec *sr = &recs[fr->n_out_sp];
+                float pn[3], pp[3];
+                for (int c = 0; c < 3; ++c) { pn[c] = p[c] + o[c]; pp[c] = p[c] - o[c]; }
+                if (pn[0] == p[0] && pn[1] == p[1] && pn[2] == p[2]) {
+                    int ax = 0;
+                    float ad0 = fabsf(d[0]), ad1 = fabsf(d[1]), ad2 = fabsf(d[2]);
+                    if (ad1 > ad0) ax = 1;
+                    if (ad2 > (ax == 1 ? ad1 : ad0)) ax = 2;
+                    pn[ax] = ulp_step(p[ax], d[ax]);
+                    pp[ax] = ulp_step(p[ax], -d[ax]);
+                }
+                uint32_t ctr[4] = {id, step, k, 1u};
+                uint32_t r2[4];
+                or_philox4x32_10(ctr, key, r2);
+                float di[3];
+                iso_dir(r2[0], r2[1], di);
+                for (int c = 0; c < 3; ++c) {
+                    sr->pi[c] = p[c];
+                    sr->vi[c] = g->v_th_ion * di[c];
+                    sr->p[c] = pn[c];
+                    sr->v[c] = sn * d[c];
+                    p[c] = pp[c];
+                    v[c] = -sn * d[c];
+                }
+                fr->n_out_sp += 1;
+                fr->collisions += 1;
+            } else { /* K_ATTACHMENT: the electron becomes an anion in place */
+                iso_dir(r[2], r[3], d);
+                for (int c = 0; c < 3; ++c) v[c] = g->v_th_ion * d[c];
+                *sp = SP_ANION;
+                fr->attached = 1;
+                fr->collisions += 1;
+                return;
+            }
+        } else {
+            /* ions: constant frequency, half isotropic elastic (speed kept),
+             * half charge exchange (fresh thermal velocity) */
+            iso_dir(r[2], r[3], d);
+            float sn = (x < g->half_nu_ion) ? speed : g->v_th_ion;
+            v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
+            fr->collisions += 1;
+        }
+    }
+}
+
+/* Stats layout (doubles), shared by or_step's caller and the tests:
+ *  0 n_before 1 n_after 2 n_e 3 n_cation 4 n_anion 5 spawned_pairs 6 absorbed
+ *  7 attached 8 recombined_pairs 9 collisions 10 trials 11 required_capacity
+ * 12..14 sum x,y,z (electrons) 15..17 sum x^2,y^2,z^2 (electrons)
+ * 18..20 sum x,y,z (ions) 21..23 sum x^2,y^2,z^2 (ions) 24 sum kinetic energy of electrons (eV) */
+#define OR_NSTATS 25
+#define OR_MAX_TRIALS 256
+
+/*
+ * One tracking step of all charges (Sec. 3.2 - 3.3), in this order:
+ *  1. (field at the step-start positions: E, given)
+ *  2. recombination (Sec. 3.3.3, Eq. (distRecomb)): every electron proposes
+ *     its nearest cation within R_c (binary32 squared distance, ties to the
+ *     lower cation id; cations created in the previous step are exempt); every
+ *     cation accepts the proposing electron with the smallest (d^2, id); both
+ *     are removed;
+ *  3. flight and collisions of the remaining charges (fly_one);
+ *  4. compaction: survivors in their order, then the spawned charges ordered by
+ *     (parent, trial, electron before cation), with new ids next_id, next_id+1..
+ * Returns ST_OK, ST_CAPACITY (nothing written, stats[11] = required count) or
+ * ST_TRIALS.
+ */
+int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
+            const uint32_t *birth, const uint8_t *species, const float *E,
+            uint32_t step, uint32_t next_id, const double *prm,
+            int n_proc, int n_e, const float *egrid, const float *xs, const int *pkind,
+            const int *pmode, const float *thr, const float *nuc,
+            int cap, float *o_pos_q, float *o_vel, uint32_t *o_id, uint32_t *o_birth,
+            uint8_t *o_species, int *o_n, uint32_t *o_next_id, double *stats)
+{
+    or_gas g;
+    memset(&g, 0, sizeof g);
+    g.dt = prm[0]; g.T = prm[1]; g.N = prm[2]; g.M_amu = prm[3]; g.nu_ion = prm[4];
+    g.z_lo = prm[5]; g.z_hi = prm[6]; g.beta = prm[7];
+    g.seed_lo = (uint32_t)prm[8]; g.seed_hi = (uint32_t)prm[9]; g.trial_cap = (int)prm[10];
+    g.n_proc = n_proc; g.n_e = n_e; g.egrid = egrid; g.xs = xs; g.pkind = pkind; g.pmode = pmode;
+    g.thr = thr; g.nuc = nuc;
+    gas_derive(&g);
+    for (int i = 0; i < OR_NSTATS; ++i) stats[i] = 0.0;
+    stats[0] = n;
+
+    uint8_t *gone = calloc((size_t)n + 1, 1);
+    /* 2. recombination */
+    int recombined = 0;
+    if (g.recomb_on) {
+        int *prop = malloc(sizeof(int) * ((size_t)n + 1));
+        float *pd2 = malloc(sizeof(float) * ((size_t)n + 1));
+        for (int e = 0; e < n; ++e) {
+            prop[e] = -1; pd2[e] = 0.0f;
+            if (species[e] != SP_ELECTRON) continue;
+            for (int c = 0; c < n; ++c) {
+                if (species[c] != SP_CATION) continue;
+                if (birth[c] != 0u && birth[c] == step) continue;
+                float dx = pos_q[4 * e] - pos_q[4 * c];
+                float dy = pos_q[4 * e + 1] - pos_q[4 * c + 1];
+                float dz = pos_q[4 * e + 2] - pos_q[4 * c + 2];
+                float d2 = dx * dx + dy * dy + dz * dz;
+                if (!(d2 <= g.rc2)) continue;
+                if (prop[e] < 0 || d2 < pd2[e] || (d2 == pd2[e] && id[c] < id[prop[e]])) {
+                    prop[e] = c; pd2[e] = d2;
+                }
+            }
+        }
+        int *acc = malloc(sizeof(int) * ((size_t)n + 1));
+        for (int c = 0; c < n; ++c) acc[c] = -1;
+        for (int e = 0; e < n; ++e) {
+            int c = prop[e];
+            if (c < 0) continue;
+            int b = acc[c];
+            if (b < 0 || pd2[e] < pd2[b] || (pd2[e] == pd2[b] && id[e] < id[b])) acc[c] = e;
+        }
+        for (int c = 0; c < n; ++c)
+            if (acc[c] >= 0) { gone[c] = 1; gone[acc[c]] = 1; recombined += 1; }
+        free(prop); free(pd2); free(acc);
+    }
+
+    /* 3. flight */
+    float *np_ = malloc(sizeof(float) * 4 * ((size_t)n + 1));
+    float *nv_ = malloc(sizeof(float) * 4 * ((size_t)n + 1));
+    uint8_t *nsp = malloc((size_t)n + 1);
+    int rec_cap_total = 64;
+    spawn_rec *recs = malloc(sizeof(spawn_rec) * rec_cap_total);
+    int n_rec = 0;
+    int status = ST_OK, absorbed = 0, attached = 0, collisions = 0, trials = 0;
+    for (int i = 0; i < n; ++i) {
+        memcpy(np_ + 4 * (size_t)i, pos_q + 4 * (size_t)i, sizeof(float) * 4);
+        memcpy(nv_ + 4 * (size_t)i, vel + 4 * (size_t)i, sizeof(float) * 4);
+        nsp[i] = species[i];
+        if (gone[i]) continue;
+        spawn_rec local[OR_MAX_TRIALS];
+        flight_result fr;
+        memset(&fr, 0, sizeof fr);
+        fly_one(&g, id[i], step, np_ + 4 * (size_t)i, nv_ + 4 * (size_t)i, &nsp[i],
+                E + 3 * (size_t)i, local, OR_MAX_TRIALS, &fr);
+        if (fr.status != ST_OK) { status = fr.status; break; }
+        if (fr.dead) { gone[i] = 2; absorbed += 1; }
+        attached += fr.attached;
+        collisions += fr.collisions;
+        trials += fr.trials;
+        for (int r = 0; r < fr.n_out_sp; ++r) {
+            if (n_rec == rec_cap_total) {
+                rec_cap_total *= 2;
+                recs = realloc(recs, sizeof(spawn_rec) * rec_cap_total);
+            }
+            recs[n_rec] = local[r];
+            recs[n_rec].parent = (uint32_t)i;
+            n_rec += 1;
+        }
+    }
+    int n_keep = 0;
+    for (int i = 0; i < n; ++i) n_keep += gone[i] ? 0 : 1;
+    int n_new = n_keep + 2 * n_rec;
+    stats[5] = n_rec; stats[6] = absorbed; stats[7] = attached; stats[8] = recombined;
+    stats[9] = collisions; stats[10] = trials; stats[11] = n_new;
+    if (status == ST_OK && n_new > cap) status = ST_CAPACITY;
+    if (status != ST_OK) {
+        free(gone); free(np_); free(nv_); free(nsp); free(recs);
+        return status;
+    }
+    /* 4. compaction */
+    int o = 0;
+    for (int i = 0; i < n; ++i) {
+        if (gone[i]) continue;
+        memcpy(o_pos_q + 4 * (size_t)o, np_ + 4 * (size_t)i, sizeof(float) * 4);
+        memcpy(o_vel + 4 * (size_t)o, nv_ + 4 * (size_t)i, sizeof(float) * 4);
+        o_id[o] = id[i]; o_birth[o] = birth[i]; o_species[o] = nsp[i];
+        o += 1;
+    }
+    uint32_t nid = next_id;
+    for (int r = 0; r < n_rec; ++r) {
+        spawn_rec *sr = &recs[r];
+        for (int c = 0; c < 3; ++c) { o_pos_q[4 * (size_t)o + c] = sr->p[c]; o_vel[4 * (size_t)o + c] = sr->v[c]; }
+        o_pos_q[4 * (size_t)o + 3] = -(float)OR_E; o_vel[4 * (size_t)o + 3] = 0.0f;
+        o_id[o] = nid++; o_birth[o] = step + 1u; o_species[o] = SP_ELECTRON;
+        o += 1;
+        for (int c = 0; c < 3; ++c) { o_pos_q[4 * (size_t)o + c] = sr->pi[c]; o_vel[4 * (size_t)o + c] = sr->vi[c]; }
+        o_pos_q[4 * (size_t)o + 3] = (float)OR_E; o_vel[4 * (size_t)o + 3] = 0.0f;
+        o_id[o] = nid++; o_birth[o] = step + 1u; o_species[o] = SP_CATION;
+        o += 1;
+    }
+    *o_n = o;
+    *o_next_id = nid;
+    stats[1] = o;
+    for (int i = 0; i < o; ++i) {
+        int s = o_species[i];
+        const float *pp = o_pos_q + 4 * (size_t)i;
+        if (s == SP_ELECTRON) {
+            stats[2] += 1;
+            for (int c = 0; c < 3; ++c) { stats[12 + c] += pp[c]; stats[15 + c] += (double)pp[c] * pp[c]; }
+            const float *vv = o_vel + 4 * (size_t)i;
+            double v2 = (double)vv[0] * vv[0] + (double)vv[1] * vv[1] + (double)vv[2] * vv[2];
+            stats[24] += 0.5 * OR_ME * v2 / OR_E;
+        } else {
+            stats[s == SP_CATION ? 3 : 4] += 1;
+            for (int c = 0; c < 3; ++c) { stats[18 + c] += pp[c]; stats[21 + c] += (double)pp[c] * pp[c]; }
+        }
+    }
+    free(gone); free(np_); free(nv_); free(nsp); free(recs);
+    return ST_OK;
+}
+
+/* exported for the tests: the step's sampling helpers */
+float or_neg_log_u(uint32_t u) { return neg_log_u(u); }
+void or_iso_dir(uint32_t ua, uint32_t ub, float *d) { iso_dir(ua, ub, d); }
