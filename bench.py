@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the fused field + tracking step on the headline workload.
+
+Workload: single-GEM patch meshed into 60,000 triangles (electrode and
+dielectric cells), 1e6 charges (half electrons, half cations) in Gaussian
+clouds on the hole axes, synthetic argon-like gas, dt = 1 ps, space charge and
+recombination on.  One "step" = one obem_step: cell field + all-pairs Coulomb
+field at every charge, recombination, flight with null-collision trials,
+ionisation spawn, compaction, moments.
+
+Prints one JSON line.  value: electron-steps/s with the state resident in HBM;
+e2e: the same metric through the C ABI with the state copied from pinned host
+buffers and back every step.  --impl reference times the CPU oracle instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "electron-steps/s & field pair-evals/s (1e6 charges, 60k panels), % FP32 peak"
+UNIT = "electron-steps/s"
+FLOPS_PER_PAIR = 18          # 3 sub, 3 fma (r^2), 3 mul, 3 fma (E): FFMA counted as 2
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--charges", type=int, default=1_000_000)
+    p.add_argument("--cells", type=int, default=60000)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x9"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(", ") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (IndexError, ValueError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(seed, n, cells):
+    from paper_2110_09214_gb300 import inputs
+    return inputs.config_gem(seed=seed, n=n, target_panels=cells)
+
+
+def _synthetic_sigma(mesh):
+    """A smooth density on the cells, used only by the CPU baseline's timing
+    (its cost does not depend on the values)."""
+    cen = mesh.tri.mean(axis=1)
+    return 1e-6 * (1.0 + 0.3 * np.sin(cen[:, 0] / 1e-4)) * np.where(mesh.kind == 0, 1.0, 0.3)
+
+
+def cpu_baseline(mesh, ch, gas, trk, seconds, rng_seed=0):
+    """The oracle on the host cores, on a bounded sample of the workload:
+    the FP64 field (all cells + all charges) at S sampled electrons and the
+    binary32 step of those S electrons; electron-steps/s = S / time."""
+    import oracle
+    sig = _synthetic_sigma(mesh)
+    rng = np.random.default_rng(rng_seed)
+    el = np.flatnonzero(ch.species == 0)
+    src = ch.pos_q.astype(np.float64)
+
+    def run(S):
+        idx = np.sort(rng.choice(el, S, replace=False))
+        pts = ch.pos_q[idx, :3].astype(np.float64)
+        t0 = time.perf_counter()
+        E1, _ = oracle.panel_field(mesh.tri, sig, pts)
+        E2, _ = oracle.nbody_field(pts, src, False, trk.softening)
+        from types import SimpleNamespace
+        sub = SimpleNamespace(pos_q=ch.pos_q[idx], vel=ch.vel[idx], id=ch.id[idx], birth=ch.birth[idx],
+                              species=ch.species[idx])
+        oracle.step(sub, (E1 + E2).astype(np.float32), 0, int(ch.id.max()) + 1, gas, trk, 4 * S + 64)
+        return time.perf_counter() - t0
+
+    t = run(8)
+    S = int(max(8, min(len(el), 8 * seconds / max(t, 1e-3))))
+    t = run(S)
+    return {"value": S / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d sampled electrons: FP64 field from all %d cells and all %d charges, "
+                      "plus their binary32 step (%.1f s)" % (S, mesh.n, ch.n, t)}
+
+
+def run_reference(a, ws, rank):
+    """--impl reference: the CPU oracle as it stands, same workload and metric."""
+    if rank != 0:
+        return
+    from paper_2110_09214_gb300 import inputs  # noqa: F401
+    mesh, gas, ch, trk, geo = _workload(1, a.charges, a.cells)
+    trk.softening = 1e-9
+    per = max(2.0, min(a.cpu_seconds, 150.0 / max(1, a.steps + a.warmup)))
+    vals = []
+    for i in range(a.warmup + a.steps):
+        r = cpu_baseline(mesh, ch, gas, trk, per, rng_seed=i)
+        if i >= a.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 field / f32 step",
+            "data": "synthetic", "config": {"workload": "single-GEM patch, %d cells, %d charges" % (mesh.n, ch.n)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a, ws, rank, local):
+    import torch
+    from paper_2110_09214_gb300 import obem
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prec = {"fp32": obem.OBEM_LU_FP32, "tf32": obem.OBEM_LU_TF32, "bf16": obem.OBEM_LU_BF16,
+            "bf16x9": obem.OBEM_LU_BF16X9}[a.precision]
+    mesh, gas, ch, trk, geo = _workload(1 + rank, a.charges, a.cells)
+    trk.softening = 1e-9
+    cap = int(ch.n * 1.6) + 1024
+    ctx = obem.obem_create(capacity=cap, dt=trk.dt, seed=trk.seed, softening=trk.softening,
+                           z_lo=trk.z_lo, z_hi=trk.z_hi, beta=trk.beta, trial_cap=256,
+                           flags=obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD)
+    obem.obem_gas_load(ctx, gas)
+    obem.obem_mesh_load(ctx, mesh)
+    t0 = time.perf_counter()
+    obem.obem_bem_assemble(ctx, prec)
+    t_asm = time.perf_counter() - t0
+    sigma = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+    rep = obem.obem_bem_solve(ctx, mesh.group_voltage, sigma)
+    st = obem.DeviceState(cap)
+    st.upload(ch)
+    n_start = int((ch.species == 0).sum())
+    stats = [obem.new_stats() for _ in range(max(a.steps, a.warmup) + 1)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    step = 0
+    for _ in range(a.warmup):
+        obem.obem_step(ctx, st, step, stats[0])
+        step += 1
+    torch.cuda.synchronize()
+    if a.warmup:
+        w = obem.read_stats(stats[0])
+        assert w["status"] == 0, "warm-up step failed: %s" % w
+        n_start = w["n_electron"]
+    # ---- device-resident timed region
+    clocks = Clocks(local)
+    obem.obem_profile(ctx, True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for k in range(a.steps):
+        flush.zero_()
+        obem.obem_step(ctx, st, step, stats[k])
+        step += 1
+    ev1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = obem.obem_stage_times(ctx)
+    obem.obem_profile(ctx, False)
+    sts = [obem.read_stats(stats[k]) for k in range(a.steps)]
+    for s_ in sts:
+        assert s_["status"] == 0, "timed step failed: %s" % s_
+    e_counts = [n_start] + [s_["n_electron"] for s_ in sts[:-1]]
+    c_counts = [s_["n_before"] for s_ in sts]
+    electron_steps = float(sum(e_counts))
+    pairs = prof["charge_pairs"]
+    cell_evals = prof["cells_1pt"] + prof["cells_3pt"] + prof["cells_7pt"] + prof["cells_closed"]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([electron_steps, float(sum(c_counts)), float(pairs + cell_evals)],
+                           dtype=torch.float64, device=dev)
+        dist.all_reduce(tot)
+        electron_steps, charge_steps, pair_evals = [float(x) for x in tot.tolist()]
+    else:
+        charge_steps, pair_evals = float(sum(c_counts)), float(pairs + cell_evals)
+    sec = ms / 1e3
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12          # TFLOP/s at max clock
+    kern_s = prof["pairs_ms"] / 1e3
+    achieved = FLOPS_PER_PAIR * pairs / kern_s / 1e12 if kern_s > 0 else 0.0
+    peak_load = sms * FP32_LANES_PER_SM * 2 * (clk.get("sm_mhz") or sm_max) * 1e6 / 1e12
+    # ---- end to end: state from pinned host memory and back, every step
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(ctx, st, a.steps, step, dev)
+    obem.obem_destroy(ctx)
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, ch, gas, trk, a.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": electron_steps / sec, "unit": UNIT, "n_gpus": ws,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded GEM mesh, charge clouds, argon-like cross sections)",
+        "config": {"workload": "single-GEM patch: %d cells (electrode + dielectric), %d charges "
+                               "(e-/cation), argon-like gas, dt 1 ps, space charge + recombination"
+                               % (mesh.n, ch.n),
+                   "cells": mesh.n, "charges": ch.n, "l2": "flushed (256 MiB write) before every timed step",
+                   "bem_precision": a.precision, "bem_assemble_factor_s": round(t_asm, 3),
+                   "bem_factor_ms": rep["factor_ms"], "bem_solve_ms": rep["solve_ms"],
+                   "bem_ir_iterations": rep["iterations"], "bem_backward_error": rep["backward_error"]},
+        "charge_steps_per_s": charge_steps / sec,
+        "field_pair_evals_per_s": pair_evals / sec,
+        "fp32_peak_frac": achieved / peak if peak else None,
+        "fp32_peak_frac_at_load_clock": achieved / peak_load if peak_load else None,
+        "stage_ms_per_step": {"cells": prof["cell_ms"] / a.steps, "pairs": prof["pairs_ms"] / a.steps,
+                              "step": prof["step_ms"] / a.steps},
+        "cell_evals_per_step": {"centroid": prof["cells_1pt"] / a.steps, "3pt": prof["cells_3pt"] / a.steps,
+                                "7pt": prof["cells_7pt"] / a.steps, "closed_form": prof["cells_closed"] / a.steps},
+        "roofline": {"bound": "alu", "kernel": "nbody_kernel (all-pairs field)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                     "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (sms, sm_max),
+                     "traffic": None},
+        "clocks": clk,
+        "gpu_launches": prof["launches"],
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(ctx, st, steps, step0, dev):
+    """Same metric through obem_step with the state in pinned host buffers:
+    H2D of the whole state before, D2H of the new state and the stats after."""
+    import torch
+    from paper_2110_09214_gb300 import obem
+    cap = st.capacity
+    n = int(st.scalars[0].item())
+    host = {k: torch.empty_like(getattr(st, k), device="cpu").pin_memory()
+            for k in ("pos_q", "vel", "id", "birth", "species")}
+    hs = torch.empty(2, dtype=torch.int32).pin_memory()
+    hstat = torch.empty(obem.STATS_BYTES, dtype=torch.uint8).pin_memory()
+    for k in host:
+        host[k][:n].copy_(getattr(st, k)[:n])
+    hs.copy_(st.scalars)
+    stats = obem.new_stats()
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    e_steps = 0.0
+    n_e = int((host["species"][:n] == 0).sum())
+    t0 = time.perf_counter()
+    step = step0
+    for _ in range(steps):
+        n = int(hs[0].item())
+        for k in host:
+            getattr(st, k)[:n].copy_(host[k][:n], non_blocking=True)
+            h2d += host[k][:n].numel() * host[k].element_size()
+        st.scalars.copy_(hs, non_blocking=True)
+        h2d += 8
+        obem.obem_step(ctx, st, step, stats)
+        step += 1
+        hs.copy_(st.scalars, non_blocking=False)
+        m = int(hs[0].item())
+        for k in host:
+            host[k][:m].copy_(getattr(st, k)[:m], non_blocking=True)
+            d2h += host[k][:m].numel() * host[k].element_size()
+        hstat.copy_(stats, non_blocking=False)
+        d2h += 8 + obem.STATS_BYTES
+        torch.cuda.synchronize()
+        s_ = obem.obem_step_stats.from_buffer_copy(hstat.numpy().tobytes())
+        if s_.status != 0:
+            raise RuntimeError("e2e step failed with status %d" % s_.status)
+        e_steps += float(n_e)
+        n_e = s_.n_electron
+    sec = time.perf_counter() - t0
+    return {"value": e_steps / sec, "unit": UNIT, "h2d_bytes_per_step": h2d // steps,
+            "d2h_bytes_per_step": d2h // steps}
+
+
+def main():
+    a = _args()
+    ws, rank, local = _dist()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+    else:
+        run_ours(a, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

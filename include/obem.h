@@ -1,0 +1,232 @@
+/*
+ * obem.h -- C ABI of the GB300 field + tracking-step engine for the
+ * OuroborosBEM method (Quemener & Salvador, arXiv 2110.09214).
+ *
+ * The library evaluates the electric field at every free charge -- the
+ * boundary-element (BEM) cell field plus the all-pairs Coulomb field of the
+ * other charges -- and advances the charges by one tracking step
+ * (free flight, null-collision Monte Carlo on tabulated cross sections,
+ * ionisation with stream compaction, attachment, electron-ion recombination).
+ *
+ * Conventions for every call:
+ *   - SI units: metres, seconds, volts, coulombs; cross sections in m^2 on an
+ *     energy grid in eV.
+ *   - "device" pointers are CUDA global-memory pointers owned by the caller;
+ *     "host" pointers are read before the call returns.  The context owns
+ *     the BEM matrix, its factors, the gas tables and its scratch memory.
+ *   - Calls taking a stream enqueue work on it and return without waiting,
+ *     except obem_bem_assemble and obem_bem_solve, which synchronise that
+ *     stream (they are set-up calls).  obem_field_eval and obem_step allocate
+ *     nothing and never synchronise.
+ *   - The return value is an obem_status; on failure obem_last_error()
+ *     describes it.  Errors found on the GPU by obem_step are written to
+ *     obem_step_stats.status instead.
+ *   - Triangles only: a quadrilateral cell is passed as two triangles.
+ */
+#ifndef OBEM_H
+#define OBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *obem_stream;   /* same handle as cudaStream_t */
+typedef struct obem_ctx obem_ctx;          /* opaque */
+
+typedef enum {
+    OBEM_OK = 0,
+    OBEM_ERR_ARG = -1,            /* invalid argument (null pointer, size, range) */
+    OBEM_ERR_CUDA = -2,           /* a CUDA runtime or cuBLAS call failed */
+    OBEM_ERR_STATE = -3,          /* call out of order (e.g. solve before assemble) */
+    OBEM_ERR_SINGULAR = -4,       /* zero pivot in the LU factorisation */
+    OBEM_ERR_NOT_CONVERGED = -5,  /* iterative refinement did not converge */
+    OBEM_ERR_CAPACITY = -6,       /* step output exceeds capacity; nothing committed */
+    OBEM_ERR_TIMEOUT = -7,        /* a bounded device-side wait ran out */
+    OBEM_ERR_TRIALS = -8          /* a charge needed more null-collision trials than trial_cap */
+} obem_status;
+
+/* Cross-section process kinds (Sec. 3.3: elastic, inelastic, ionisation,
+ * attachment) and how the collision frequency of a process is given. */
+enum { OBEM_P_ELASTIC = 0, OBEM_P_EXCITATION = 1, OBEM_P_IONISATION = 2, OBEM_P_ATTACHMENT = 3 };
+enum { OBEM_MODE_TABLE = 0, OBEM_MODE_CONST = 1 };
+
+/* Cell kinds (Sec. 2.1): electrode-to-dielectric (Dirichlet rows, Eq. (DBC))
+ * and dielectric-to-dielectric (Neumann rows, Eq. (NBC)). */
+enum { OBEM_CELL_ELECTRODE = 0, OBEM_CELL_DIELECTRIC = 1 };
+
+/* Species of a charge; the charge value itself is in pos_q[4*i+3]. */
+enum { OBEM_ELECTRON = 0, OBEM_CATION = 1, OBEM_ANION = 2 };
+
+/* Arithmetic of the trailing updates of the BEM LU factorisation. */
+enum {
+    OBEM_LU_FP32 = 0,   /* FP32 on the CUDA cores */
+    OBEM_LU_TF32 = 1,   /* TF32 tensor cores, FP32 accumulation */
+    OBEM_LU_BF16 = 2,   /* BF16 tensor cores, FP32 accumulation */
+    OBEM_LU_BF16X9 = 3  /* FP32-accurate BF16x9 emulation on the tensor cores */
+};
+
+/* obem_step feature flags */
+enum {
+    OBEM_STEP_SPACE_CHARGE = 1,   /* add the all-pairs Coulomb field, Eq. (nbody) */
+    OBEM_STEP_CELL_FIELD = 2      /* add the BEM cell field, Eq. (BEM3), with the current sigma */
+};
+
+typedef struct obem_config {
+    int32_t capacity;       /* largest number of charges obem_step will hold */
+    int32_t trial_cap;      /* max null-collision trials per charge per step, 1..256 */
+    int32_t flags;          /* OBEM_STEP_* */
+    int32_t reserved;
+    double dt;              /* tracking step (s) */
+    uint64_t seed;          /* Philox4x32-10 key */
+    double softening;       /* Plummer length of the N-body field in obem_step (m); 0 = exact */
+    double z_lo, z_hi;      /* absorbing electrode planes z = z_lo, z = z_hi (m) */
+    double beta;            /* recombination rate coefficient (m^3/s): R_c = (3 beta dt / 4 pi)^(1/3);
+                               0: R_c from Eq. (distRecomb); < 0: no recombination */
+    double e_ext[3];        /* uniform field added at every charge in obem_step (V/m) */
+} obem_config;
+
+typedef struct obem_gas {
+    int32_t n_proc;             /* number of processes, 1..32 */
+    int32_t n_energy;           /* grid points, 2..4096 */
+    const float *energy_eV;     /* host [n_energy], strictly increasing */
+    const float *sigma_m2;      /* host [n_proc][n_energy], used for OBEM_MODE_TABLE rows */
+    const int32_t *kind;        /* host [n_proc], OBEM_P_* */
+    const int32_t *mode;        /* host [n_proc], OBEM_MODE_* */
+    const float *threshold_eV;  /* host [n_proc]; sigma = 0 below it; energy loss of excitations */
+    const float *nu_const;      /* host [n_proc], collision frequency (1/s) of OBEM_MODE_CONST rows */
+    double T;                   /* gas temperature (K) */
+    double N;                   /* gas number density (m^-3) */
+    double M_amu;               /* gas molecule / ion mass (amu); <= 0: infinite (no recoil, ions fixed) */
+    double nu_ion;              /* constant ion collision frequency (1/s) */
+} obem_gas;
+
+/* Charge state, structure of arrays in device memory, sorted by id. */
+typedef struct obem_state {
+    float *pos_q;          /* device [capacity][4]: x, y, z (m), q (C) */
+    float *vel;            /* device [capacity][4]: vx, vy, vz (m/s), unused */
+    uint32_t *id;          /* device [capacity]: unique, increasing */
+    uint32_t *birth;       /* device [capacity]: 0 for initial charges, s+1 if created in step s */
+    uint8_t *species;      /* device [capacity]: OBEM_ELECTRON / OBEM_CATION / OBEM_ANION */
+    int32_t *n;            /* device scalar: live charges; updated by obem_step */
+    uint32_t *next_id;     /* device scalar: next unused id; updated by obem_step */
+    int32_t capacity;      /* host: length of the arrays; must not exceed obem_config.capacity */
+} obem_state;
+
+/* Per-step observables and status, written to device memory by obem_step
+ * (Sec. 4.1: swarm parameters are extracted from the cloud moments). */
+typedef struct obem_step_stats {
+    int32_t status;             /* OBEM_OK, OBEM_ERR_CAPACITY or OBEM_ERR_TRIALS */
+    int32_t n_before, n_after;  /* charges before / after the step */
+    int32_t required_capacity;  /* charges the step produced (valid also on OBEM_ERR_CAPACITY) */
+    int32_t n_electron, n_cation, n_anion;
+    int32_t spawned_pairs, absorbed, attached, recombined_pairs, collisions;
+    int64_t trials;             /* collision trials (real + null) */
+    double sum_e[3], sum2_e[3]; /* electrons: sum of x,y,z and of x^2,y^2,z^2 (m, m^2) */
+    double sum_i[3], sum2_i[3]; /* ions (cations + anions) */
+    double sum_energy_e;        /* electrons: total kinetic energy (eV) */
+} obem_step_stats;
+
+typedef struct obem_solve_report {
+    int32_t iterations;         /* refinement iterations done */
+    int32_t status;             /* OBEM_OK or OBEM_ERR_NOT_CONVERGED */
+    double backward_error;      /* ||b - A s||_inf / (||A||_inf ||s||_inf + ||b||_inf), FP64 residual */
+    double factor_ms;           /* time of the last LU factorisation */
+    double solve_ms;            /* time of this solve */
+} obem_solve_report;
+
+/* Create a context.  cfg is copied; scratch for cfg->capacity charges is
+ * allocated here.  Returns OBEM_ERR_ARG for out-of-range fields. */
+int obem_create(obem_ctx **ctx, const obem_config *cfg);
+void obem_destroy(obem_ctx *ctx);
+/* Text of the last error of this context (static storage, never NULL). */
+const char *obem_last_error(const obem_ctx *ctx);
+
+/* Load the gas: cross-section tables and the constants of the collision
+ * model (Sec. 3.3, Eq. (leth) grid; ion model of Sec. 3.3).  Host arrays are
+ * copied to the device. */
+int obem_gas_load(obem_ctx *ctx, const obem_gas *gas);
+
+/* Load the cell mesh (Sec. 2.2).  tri_xyz: host [n_panels][3][3] vertices;
+ * the normal (v1-v0)x(v2-v0) points from the eps_minus to the eps_plus side.
+ * kind: OBEM_CELL_*; group: electrode group of electrode cells (0..n_groups-1),
+ * ignored for dielectric cells; eps_minus / eps_plus: relative permittivities
+ * (dielectric cells only).  Invalidates any previous factorisation. */
+int obem_mesh_load(obem_ctx *ctx, int32_t n_panels, const double *tri_xyz,
+                   const int32_t *kind, const int32_t *group, const double *eps_minus,
+                   const double *eps_plus, int32_t n_groups);
+
+/* Assemble the dense matrix of Eq. (matrixBEM) -- Q rows (Eq. (BEMpot)) for
+ * electrode cells, W rows (Eq. (BEMfld)) for dielectric cells, collocated at
+ * the cell centroids, rows equilibrated -- and factorise it (blocked LU with
+ * partial pivoting; trailing updates in the arithmetic `precision`,
+ * OBEM_LU_*).  Synchronises `stream`. */
+int obem_bem_assemble(obem_ctx *ctx, int32_t precision, obem_stream stream);
+
+/* Solve Eq. (matrixBEM) for sigma with the stored factors and iterative
+ * refinement (FP64 residuals) -- Sec. 2.2 keeps the factorisation to re-solve
+ * for new voltages or free charges.  group_voltage: host [n_groups];
+ * sigma_free: device [n_panels] free density of dielectric cells or NULL
+ * (Eq. (charge-up)); drhs: device [n_panels] right-hand-side correction or NULL
+ * (the influence terms of Eqs. (BEMpotpart), (BEMfldpart)); sigma_out: device
+ * [n_panels].  The solution also becomes the context's current sigma used by
+ * obem_step.  rep may be NULL.  Synchronises `stream`. */
+int obem_bem_solve(obem_ctx *ctx, const double *group_voltage, const float *sigma_free,
+                   const float *drhs, float *sigma_out, obem_solve_report *rep,
+                   obem_stream stream);
+
+/* Field and potential at nt points (Eqs. (BEM2), (BEM3), (nbody)):
+ *   E(r) = k_C sum_j sigma_j int_Cj (r - r')/|r - r'|^3 dA'
+ *        + k_C sum_p q_p (r - r_p)/|r - r_p|^3
+ * targets: device [nt][4] (x, y, z, unused); sources: device [ns][4]
+ * (x, y, z, q) or NULL (ns ignored); self_exclude: targets and sources are the
+ * same array and pair (t, t) is skipped (requires nt == ns); sigma: device
+ * [n_panels] cell densities of the loaded mesh, or NULL for no cell field;
+ * E_out: device [nt][4] (Ex, Ey, Ez, V).  The Coulomb sum is exact (no
+ * softening): a source at the exact position of a target other than its
+ * own self pair gives a non-finite result. */
+int obem_field_eval(obem_ctx *ctx, const float *targets, int32_t nt, const float *sources,
+                    int32_t ns, int32_t self_exclude, const float *sigma, float *E_out,
+                    obem_stream stream);
+
+/* One tracking step of all charges in st (Sec. 3.2 - 3.3):
+ *   1. field at the step-start positions: E_in (device [capacity][4]) if not
+ *      NULL, else evaluated here (cell field with the current sigma and/or
+ *      softened all-pairs field as cfg.flags say, plus cfg.e_ext);
+ *   2. recombination: every electron proposes its nearest cation within R_c
+ *      (binary32 squared distance, ties to the lower id; cations created in
+ *      the previous step exempt), every cation accepts the proposer with the
+ *      smallest (d^2, id), both are removed;
+ *   3. flight under the step-start field (Euler stepper, Sec. 3.2.5) with
+ *      exact null-collision trials (Philox4x32-10 keyed by seed, counter
+ *      (id, step, trial, tag)); ionisation spawns an electron and a cation
+ *      at the distance of Eq. (distIoni); attachment turns the electron into
+ *      an anion; crossing z_lo / z_hi absorbs the charge;
+ *   4. compaction: survivors in order, then spawned charges ordered by
+ *      (parent, trial, electron before cation) with ids next_id, next_id+1...
+ * The update is all-or-nothing: if the result exceeds st->capacity (or the
+ * context capacity), or a charge exceeds trial_cap, nothing is written and
+ * stats->status says why.  stats: device pointer. */
+int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t step,
+              obem_step_stats *stats, obem_stream stream);
+
+/* Stage timing of obem_step, for measurement (not part of the method).
+ * obem_profile(ctx, 1) starts recording CUDA events on the step's stream
+ * around its stages (up to 256 steps are kept; older ones are dropped);
+ * obem_stage_times() waits for the recorded events and returns, summed over
+ * the recorded steps:
+ *   ms[0] cell field kernel, ms[1] all-pairs field kernel, ms[2] step kernels
+ *   (recombination, flight, compaction, moments), ms[3] whole obem_step;
+ *   counts[0] steps recorded, counts[1] kernels launched by those steps,
+ *   counts[2] charge pairs of the all-pairs kernel,
+ *   counts[3..6] cell evaluations by tier (centroid, 3-point, 7-point, closed form).
+ * Recording is then reset.  obem_profile(ctx, 0) stops recording. */
+int obem_profile(obem_ctx *ctx, int32_t enable);
+int obem_stage_times(obem_ctx *ctx, double *ms /* [4] */, int64_t *counts /* [7] */);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OBEM_H */

@@ -1,0 +1,676 @@
+// BEM set-up: assembly of the dense system of Eq. (matrixBEM), its LU
+// factorisation, and solves with iterative refinement.  Sec. 2.2 fills the
+// matrix on the GPU and keeps an inverse so that new voltages or free charges
+// only need a new right-hand side; here the factors are kept instead of the
+// inverse (same reuse, half the flops, better conditioned).
+//
+//   assemble_kernel   one thread per matrix element (row-major, coalesced over
+//                     j): Q_ij = k_C phi_j(r_i) for electrode rows, W_ij for
+//                     dielectric rows; FP64 closed form for near cells,
+//                     FP32 quadrature (7/3/1 points by distance) for far ones
+//   equilibrate       scale every row by 1 / max |A_ij| (solution unchanged)
+//   LU                blocked right-looking, partial pivoting:
+//                       panel_kernel   cooperative: one row chunk per CTA held
+//                                      in shared memory, bounded grid barriers
+//                       laswp_kernel   row swaps outside the panel
+//                       trsm_kernel    U12 = L11^-1 A12
+//                       cuBLAS GEMM    A22 -= L21 U12 (FP32 / TF32 / BF16 /
+//                                      BF16x9 per the requested precision)
+//   solve             y = L^-1 P b, x = U^-1 y (blocked, FP32 factors) inside
+//                     iterative refinement with FP64 residuals r = b - A x
+#include <math.h>
+#include <vector>
+
+#include "obem_internal.cuh"
+
+#define LU_NB 64
+#define BARRIER_SPIN_LIMIT (1ll << 24)
+
+// ------------------------------------------------------------------ closed form (FP64)
+// Same expansion as the field kernels: unit-density potential phi and field F
+// of a flat triangle at r; principal value in the cell's plane.
+__device__ __noinline__ void bem_closed_form(const double *v, double rx, double ry, double rz,
+                                             double &phi, double &Fx, double &Fy, double &Fz)
+{
+    double e1x = v[3] - v[0], e1y = v[4] - v[1], e1z = v[5] - v[2];
+    double e2x = v[6] - v[0], e2y = v[7] - v[1], e2z = v[8] - v[2];
+    double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    double a2 = sqrt(nx * nx + ny * ny + nz * nz);
+    nx /= a2; ny /= a2; nz /= a2;
+    double ax[3], ay[3], az[3], R[3];
+    for (int i = 0; i < 3; ++i) {
+        ax[i] = v[3 * i] - rx; ay[i] = v[3 * i + 1] - ry; az[i] = v[3 * i + 2] - rz;
+        R[i] = sqrt(ax[i] * ax[i] + ay[i] * ay[i] + az[i] * az[i]);
+    }
+    double h = -(ax[0] * nx + ay[0] * ny + az[0] * nz);
+    double ps = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3;
+        double dx = v[3 * j] - v[3 * i], dy = v[3 * j + 1] - v[3 * i + 1], dz = v[3 * j + 2] - v[3 * i + 2];
+        double len = sqrt(dx * dx + dy * dy + dz * dz);
+        dx /= len; dy /= len; dz /= len;
+        double ux = dy * nz - dz * ny, uy = dz * nx - dx * nz, uz = dx * ny - dy * nx;
+        double lm = ax[i] * dx + ay[i] * dy + az[i] * dz;
+        double lp = ax[j] * dx + ay[j] * dy + az[j] * dz;
+        double p0 = ax[i] * ux + ay[i] * uy + az[i] * uz;
+        double L;
+        if (lm >= 0.0) L = log((R[j] + lp) / (R[i] + lm));
+        else if (lp <= 0.0) L = log((R[i] - lm) / (R[j] - lp));
+        else L = log((R[j] + lp) * (R[i] - lm) / (p0 * p0 + h * h));
+        if (p0 != 0.0) ps += p0 * L;
+        fx += ux * L; fy += uy * L; fz += uz * L;
+    }
+    double D = R[0] * R[1] * R[2] + (ax[0] * ax[1] + ay[0] * ay[1] + az[0] * az[1]) * R[2]
+             + (ax[0] * ax[2] + ay[0] * ay[2] + az[0] * az[2]) * R[1]
+             + (ax[1] * ax[2] + ay[1] * ay[2] + az[1] * az[2]) * R[0];
+    double Om = (h == 0.0) ? 0.0 : 2.0 * atan2(a2 * h, D);
+    phi = ps - h * Om;
+    Fx = fx + Om * nx; Fy = fy + Om * ny; Fz = fz + Om * nz;
+}
+
+// unit-density quadrature point (weight w = A w_k)
+__device__ __forceinline__ void bq(float tx, float ty, float tz, float px, float py, float pz, float w,
+                                   float &phi, float &fx, float &fy, float &fz)
+{
+    float dx = tx - px, dy = ty - py, dz = tz - pz;
+    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float inv = rsqrtf(r2);
+    float s = w * inv;
+    float s3 = s * inv * inv;
+    phi += s;
+    fx = fmaf(dx, s3, fx); fy = fmaf(dy, s3, fy); fz = fmaf(dz, s3, fz);
+}
+
+#define AS_CLOSED_H2 16.0f     // d < 4 h: FP64 closed form
+#define AS_7PT_H2 1024.0f      // d < 32 h: 7 points
+#define AS_3PT_H2 360000.0f    // d < 600 h: 3 points, else centroid
+
+__global__ void assemble_kernel(PanelsDev P, const int *kind, const double *em, const double *ep,
+                                float *A, int n)
+{
+    const int i = blockIdx.x;
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float4 ci = P.c_a[i];
+    const float4 cj = P.c_a[j];
+    const float4 g0 = P.g0_h[j];
+    float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+    float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float Aj = cj.w * (float)(1.0 / OBEM_KC);   // area
+    double phi, Fx, Fy, Fz;
+    if (i == j || d2 < AS_CLOSED_H2 * g0.w) {
+        const double *vi = P.v64 + 9 * (size_t)i;
+        double rx = (vi[0] + vi[3] + vi[6]) / 3.0, ry = (vi[1] + vi[4] + vi[7]) / 3.0,
+               rz = (vi[2] + vi[5] + vi[8]) / 3.0;
+        bem_closed_form(P.v64 + 9 * (size_t)j, rx, ry, rz, phi, Fx, Fy, Fz);
+        if (i == j) { Fx = Fy = Fz = 0.0; }
+    } else {
+        float ph = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+        const float4 g1 = P.g1[j], g2 = P.g2[j];
+        if (d2 < AS_7PT_H2 * g0.w) {
+            const float T1 = -0.410426192315345f, T2 = 0.696140478029631f;
+            const float w0 = Aj * 0.225f, w1 = Aj * 0.132394152788506f, w2 = Aj * 0.125939180544827f;
+            bq(ci.x, ci.y, ci.z, cj.x, cj.y, cj.z, w0, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(T1, g0.x, cj.x), fmaf(T1, g0.y, cj.y), fmaf(T1, g0.z, cj.z), w1, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(T1, g1.x, cj.x), fmaf(T1, g1.y, cj.y), fmaf(T1, g1.z, cj.z), w1, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(T1, g2.x, cj.x), fmaf(T1, g2.y, cj.y), fmaf(T1, g2.z, cj.z), w1, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(T2, g0.x, cj.x), fmaf(T2, g0.y, cj.y), fmaf(T2, g0.z, cj.z), w2, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(T2, g1.x, cj.x), fmaf(T2, g1.y, cj.y), fmaf(T2, g1.z, cj.z), w2, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(T2, g2.x, cj.x), fmaf(T2, g2.y, cj.y), fmaf(T2, g2.z, cj.z), w2, ph, fx, fy, fz);
+        } else if (d2 < AS_3PT_H2 * g0.w) {
+            const float w = Aj * (1.0f / 3.0f);
+            bq(ci.x, ci.y, ci.z, fmaf(0.5f, g0.x, cj.x), fmaf(0.5f, g0.y, cj.y), fmaf(0.5f, g0.z, cj.z), w, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(0.5f, g1.x, cj.x), fmaf(0.5f, g1.y, cj.y), fmaf(0.5f, g1.z, cj.z), w, ph, fx, fy, fz);
+            bq(ci.x, ci.y, ci.z, fmaf(0.5f, g2.x, cj.x), fmaf(0.5f, g2.y, cj.y), fmaf(0.5f, g2.z, cj.z), w, ph, fx, fy, fz);
+        } else {
+            bq(ci.x, ci.y, ci.z, cj.x, cj.y, cj.z, Aj, ph, fx, fy, fz);
+        }
+        phi = ph; Fx = fx; Fy = fy; Fz = fz;
+    }
+    double a;
+    if (kind[i] == OBEM_CELL_ELECTRODE) {
+        a = OBEM_KC * phi;
+    } else if (i == j) {
+        a = 0.5 * (ep[i] + em[i]);
+    } else {
+        const float4 ni = P.nrm[i];
+        a = (ep[i] - em[i]) / (4.0 * OBEM_PI) * (Fx * ni.x + Fy * ni.y + Fz * ni.z);
+    }
+    A[(size_t)i * n + j] = (float)a;
+}
+
+// one block per row: scale by 1 / max |a_ij|, record the scale and |row|_1
+__global__ void equilibrate_kernel(float *A, int n, double *rowscale, double *rownorm)
+{
+    __shared__ float smax[32];
+    __shared__ double ssum[32];
+    float *row = A + (size_t)blockIdx.x * n;
+    float m = 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) m = fmaxf(m, fabsf(row[j]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? smax[threadIdx.x] : 0.f;
+        for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) smax[0] = v;
+    }
+    __syncthreads();
+    const float mx = smax[0];
+    const float sc = mx > 0.f ? 1.0f / mx : 1.0f;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        float v = row[j] * sc;
+        row[j] = v;
+        s += fabs((double)v);
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) ssum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ssum[w];
+        rownorm[blockIdx.x] = t;
+        rowscale[blockIdx.x] = (double)sc;
+    }
+}
+
+// ------------------------------------------------------------------ grid barrier
+// Sense-free generation barrier among the CTAs of a cooperative launch.  The
+// wait is bounded: after BARRIER_SPIN_LIMIT polls the CTA records
+// OBEM_ERR_TIMEOUT in flag[0] and returns false.
+__device__ bool grid_barrier(int *flag, unsigned *count, volatile unsigned *gen, unsigned nblocks)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        unsigned g = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == nblocks - 1) {
+            *count = 0u;
+            __threadfence();
+            atomicAdd((unsigned *)gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > BARRIER_SPIN_LIMIT) {
+                    atomicExch(flag, OBEM_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)flag != 0) ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct PanelArgs {
+    float *A;
+    int n, k, kb, rows_per_cta;
+    int *piv;
+    int *flag;          // [0] status, [1] barrier count, [2] barrier generation
+    float *gval;        // [gridDim] candidate |pivot|
+    int *grow;          // [gridDim] candidate row
+    float *gpiv;        // [LU_NB] pivot row
+    float *gdiag;       // [LU_NB] row displaced by the pivot
+};
+
+// Panel factorisation of A[k:n, k:k+kb] with partial pivoting.  CTA b owns
+// rows k + b*R .. k + (b+1)*R - 1 of the panel in shared memory.
+__global__ void __launch_bounds__(256)
+panel_kernel(PanelArgs a)
+{
+    extern __shared__ float sp[];            // [R][kb + 1] (padded against bank conflicts)
+    __shared__ float sv[256];
+    __shared__ int si[256];
+    __shared__ float urow[LU_NB];
+    const int R = a.rows_per_cta, kb = a.kb, n = a.n, k = a.k;
+    const int ld = kb + 1;
+    const int r0 = k + blockIdx.x * R;
+    const int rows = max(0, min(R, n - r0));
+    unsigned *cnt = (unsigned *)&a.flag[1];
+    volatile unsigned *gen = (volatile unsigned *)&a.flag[2];
+    for (int t = threadIdx.x; t < rows * kb; t += blockDim.x) {
+        int r = t / kb, c = t % kb;
+        sp[r * ld + c] = a.A[(size_t)(r0 + r) * n + k + c];
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        const int pr = k + j;                     // row receiving the pivot
+        // local candidate: max |a| over own rows >= pr, ties to the lowest row
+        float bv = -1.f;
+        int bi = 0x7fffffff;
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            int gr = r0 + r;
+            if (gr < pr) continue;
+            float v = fabsf(sp[r * ld + j]);
+            if (v > bv || (v == bv && gr < bi)) { bv = v; bi = gr; }
+        }
+        sv[threadIdx.x] = bv;
+        si[threadIdx.x] = bi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                float v2 = sv[threadIdx.x + o];
+                int i2 = si[threadIdx.x + o];
+                if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+                    sv[threadIdx.x] = v2;
+                    si[threadIdx.x] = i2;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) { a.gval[blockIdx.x] = sv[0]; a.grow[blockIdx.x] = si[0]; }
+        if (!grid_barrier(a.flag, cnt, gen, gridDim.x)) return;
+        // global pivot (every CTA computes the same answer)
+        if (threadIdx.x == 0) {
+            float v = -1.f;
+            int p = 0x7fffffff;
+            for (int b = 0; b < (int)gridDim.x; ++b) {
+                float v2 = ((volatile float *)a.gval)[b];
+                int i2 = ((volatile int *)a.grow)[b];
+                if (v2 > v || (v2 == v && i2 < p)) { v = v2; p = i2; }
+            }
+            si[0] = p;
+            sv[0] = v;
+        }
+        __syncthreads();
+        const int p = si[0];
+        if (!(sv[0] > 0.f)) {
+            if (threadIdx.x == 0) atomicCAS(a.flag, 0, OBEM_ERR_SINGULAR);
+            return;
+        }
+        const bool own_p = p >= r0 && p < r0 + rows;
+        const bool own_d = pr >= r0 && pr < r0 + rows;
+        if (own_p)
+            for (int c = threadIdx.x; c < kb; c += blockDim.x) a.gpiv[c] = sp[(p - r0) * ld + c];
+        if (own_d)
+            for (int c = threadIdx.x; c < kb; c += blockDim.x) a.gdiag[c] = sp[(pr - r0) * ld + c];
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.piv[pr] = p;
+        if (!grid_barrier(a.flag, cnt, gen, gridDim.x)) return;
+        for (int c = threadIdx.x; c < kb; c += blockDim.x) urow[c] = ((volatile float *)a.gpiv)[c];
+        __syncthreads();
+        if (own_d)
+            for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[(pr - r0) * ld + c] = urow[c];
+        if (own_p && p != pr)
+            for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[(p - r0) * ld + c] = ((volatile float *)a.gdiag)[c];
+        __syncthreads();
+        const float inv = 1.0f / urow[j];
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            int gr = r0 + r;
+            if (gr <= pr) continue;
+            float l = sp[r * ld + j] * inv;
+            sp[r * ld + j] = l;
+            for (int c = j + 1; c < kb; ++c) sp[r * ld + c] = fmaf(-l, urow[c], sp[r * ld + c]);
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < rows * kb; t += blockDim.x) {
+        int r = t / kb, c = t % kb;
+        a.A[(size_t)(r0 + r) * n + k + c] = sp[r * ld + c];
+    }
+}
+
+// apply the panel's row swaps to the columns outside the panel
+__global__ void laswp_kernel(float *A, int n, int k, int kb, const int *piv)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || (c >= k && c < k + kb)) return;
+    for (int j = 0; j < kb; ++j) {
+        int p = piv[k + j];
+        if (p != k + j) {
+            float t = A[(size_t)(k + j) * n + c];
+            A[(size_t)(k + j) * n + c] = A[(size_t)p * n + c];
+            A[(size_t)p * n + c] = t;
+        }
+    }
+}
+
+// U12 = L11^-1 A12 with L11 unit lower triangular (kb x kb); a CTA of
+// TRSM_COLS threads owns TRSM_COLS columns, held in shared memory
+#define TRSM_COLS 64
+__global__ void trsm_kernel(float *A, int n, int k, int kb)
+{
+    __shared__ float L[LU_NB][LU_NB + 1];
+    __shared__ float X[LU_NB][TRSM_COLS];
+    for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
+        int r = t / kb, c = t % kb;
+        L[r][c] = A[(size_t)(k + r) * n + k + c];
+    }
+    const int c = k + kb + blockIdx.x * TRSM_COLS + threadIdx.x;
+    const bool act = c < n;
+    for (int r = 0; r < kb; ++r) X[r][threadIdx.x] = act ? A[(size_t)(k + r) * n + c] : 0.f;
+    __syncthreads();
+    for (int q = 0; q < kb; ++q) {
+        const float xq = X[q][threadIdx.x];
+        for (int r = q + 1; r < kb; ++r) X[r][threadIdx.x] = fmaf(-L[r][q], xq, X[r][threadIdx.x]);
+    }
+    if (act)
+        for (int r = 0; r < kb; ++r) A[(size_t)(k + r) * n + c] = X[r][threadIdx.x];
+}
+
+// ------------------------------------------------------------------ solve kernels
+// b_i = rowscale_i * (V_group or free density) + drhs_i  (drhs unscaled input)
+__global__ void rhs_kernel(const int *kind, const int *group, const double *gv, const float *sigma_free,
+                           const float *drhs, const double *rowscale, double *b, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = 0.0;
+    if (kind[i] == OBEM_CELL_ELECTRODE) v = gv[group[i]];
+    else if (sigma_free) v = (double)sigma_free[i];
+    if (drhs) v += (double)drhs[i];
+    b[i] = v * rowscale[i];
+}
+
+// r = b - A x (FP64 accumulation over the FP32 matrix), one warp per row
+__global__ void residual_kernel(const float *A, const double *x, const double *b, double *r, int n)
+{
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float *a = A + (size_t)row * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += (double)a[j] * x[j];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) r[row] = b[row] - s;
+}
+
+// out = [max|r|, max|x|, max|b|]
+__global__ void norms_kernel(const double *r, const double *x, const double *b, int n, double *out)
+{
+    __shared__ double s[3][256];
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a0 = fmax(a0, fabs(r[i])); a1 = fmax(a1, fabs(x[i])); a2 = fmax(a2, fabs(b[i]));
+    }
+    s[0][threadIdx.x] = a0; s[1][threadIdx.x] = a1; s[2][threadIdx.x] = a2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q = 0; q < 3; ++q) s[q][threadIdx.x] = fmax(s[q][threadIdx.x], s[q][threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = s[0][0]; out[1] = s[1][0]; out[2] = s[2][0]; }
+}
+
+// y = P r (in order of the factorisation's swaps), rounded to FP32 after scaling by 1/sc
+__global__ void permute_kernel(const double *r, float *y, const int *piv, int n, const double *norms)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double sc = norms[0] > 0 ? norms[0] : 1.0;
+    for (int i = 0; i < n; ++i) y[i] = (float)(r[i] / sc);
+    for (int i = 0; i < n; ++i) {
+        int p = piv[i];
+        if (p != i) { float t = y[i]; y[i] = y[p]; y[p] = t; }
+    }
+}
+
+// Forward (lower=1, unit diagonal) or backward (lower=0) substitution on the
+// diagonal block [k, k+kb) of the factors: one CTA of LU_NB threads, the block
+// in shared memory, one column eliminated per barrier.
+__global__ void trsv_block_kernel(const float *LU, float *y, int n, int k, int kb, int lower)
+{
+    __shared__ float T[LU_NB][LU_NB + 1];
+    __shared__ float yb[LU_NB];
+    for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
+        int r = t / kb, c = t % kb;
+        T[r][c] = LU[(size_t)(k + r) * n + k + c];
+    }
+    const int r = threadIdx.x;
+    if (r < kb) yb[r] = y[k + r];
+    __syncthreads();
+    if (lower) {
+        for (int q = 0; q < kb; ++q) {
+            if (r > q && r < kb) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
+            __syncthreads();
+        }
+    } else {
+        for (int q = kb - 1; q >= 0; --q) {
+            if (r == q) yb[q] = yb[q] / T[q][q];
+            __syncthreads();
+            if (r < q) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
+            __syncthreads();
+        }
+    }
+    if (r < kb) y[k + r] = yb[r];
+}
+
+// y[rows] -= LU[rows, k:k+kb] y[k:k+kb], one warp per row; rows = [r0, r1)
+__global__ void trsv_update_kernel(const float *LU, float *y, int n, int k, int kb, int r0, int r1)
+{
+    int row = r0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (row >= r1) return;
+    const float *a = LU + (size_t)row * n + k;
+    float s = 0.f;
+    for (int q = lane; q < kb; q += 32) s = fmaf(a[q], y[k + q], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] -= s;
+}
+
+__global__ void axpy_kernel(double *x, const float *d, const double *norms, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double sc = norms[0] > 0 ? norms[0] : 1.0;
+    x[i] += (double)d[i] * sc;
+}
+
+__global__ void to_float_kernel(const double *x, float *a, float *b, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = (float)x[i];
+    a[i] = v;
+    if (b) b[i] = v;
+}
+
+// ------------------------------------------------------------------ host drivers
+static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int kb, cudaStream_t s)
+{
+    const int M = n - k - kb;
+    if (M <= 0) return OBEM_OK;
+    const float alpha = -1.0f, beta = 1.0f;
+    float *A22 = A + (size_t)(k + kb) * n + (k + kb);
+    float *L21 = A + (size_t)(k + kb) * n + k;
+    float *U12 = A + (size_t)k * n + (k + kb);
+    cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
+    if (precision == OBEM_LU_TF32) ct = CUBLAS_COMPUTE_32F_FAST_TF32;
+    else if (precision == OBEM_LU_BF16) ct = CUBLAS_COMPUTE_32F_FAST_16BF;
+    else if (precision == OBEM_LU_BF16X9) ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+    cublasStatus_t st = cublasGemmEx(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, M, M, kb, &alpha, U12,
+                                     CUDA_R_32F, n, L21, CUDA_R_32F, n, &beta, A22, CUDA_R_32F, n, ct,
+                                     CUBLAS_GEMM_DEFAULT);
+    if (st != CUBLAS_STATUS_SUCCESS)
+        return obem_fail(c, OBEM_ERR_CUDA, "cublasGemmEx failed (status %d)", (int)st);
+    return OBEM_OK;
+}
+
+int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
+{
+    const int n = c->np;
+    const size_t nn = (size_t)n * n;
+    c->factored = 0;
+    if (!c->d_A) {
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_A, sizeof(float) * nn));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_LU, sizeof(float) * nn));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_piv, sizeof(int) * n));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_rowscale, sizeof(double) * n));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_work64, sizeof(double) * (4 * (size_t)n + 8)));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_work32, sizeof(float) * (2 * (size_t)n + 4096)));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_flag, sizeof(int) * 8));
+    }
+    if (!c->cublas) {
+        if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS)
+            return obem_fail(c, OBEM_ERR_CUDA, "cublasCreate failed");
+    }
+    cublasSetStream(c->cublas, s);
+    double *d_rownorm = c->d_work64;     // reused as scratch here
+    // --- assembly + equilibration
+    PanelsDev P;
+    P.c_a = c->d_c_a; P.g0_h = c->d_g0_h; P.g1 = c->d_g1; P.g2 = c->d_g2; P.nrm = c->d_nrm;
+    P.v64 = c->d_v64; P.np = n;
+    double *d_em = NULL, *d_ep = NULL;
+    OBEM_CUDA(c, cudaMalloc((void **)&d_em, sizeof(double) * n));
+    OBEM_CUDA(c, cudaMalloc((void **)&d_ep, sizeof(double) * n));
+    OBEM_CUDA(c, cudaMemcpyAsync(d_em, c->h_em, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    OBEM_CUDA(c, cudaMemcpyAsync(d_ep, c->h_ep, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    dim3 ag(n, (n + 127) / 128);
+    assemble_kernel<<<ag, 128, 0, s>>>(P, c->d_kind, d_em, d_ep, c->d_A, n);
+    OBEM_LAUNCH(c);
+    equilibrate_kernel<<<n, 256, 0, s>>>(c->d_A, n, c->d_rowscale, d_rownorm);
+    OBEM_LAUNCH(c);
+    std::vector<double> rn(n);
+    OBEM_CUDA(c, cudaMemcpyAsync(rn.data(), d_rownorm, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    OBEM_CUDA(c, cudaStreamSynchronize(s));
+    cudaFree(d_em);
+    cudaFree(d_ep);
+    c->a_norm_inf = 0.0;
+    for (int i = 0; i < n; ++i) c->a_norm_inf = rn[i] > c->a_norm_inf ? rn[i] : c->a_norm_inf;
+    // --- factorisation
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    OBEM_CUDA(c, cudaMemcpyAsync(c->d_LU, c->d_A, sizeof(float) * nn, cudaMemcpyDeviceToDevice, s));
+    OBEM_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int) * 8, s));
+    cudaEventRecord(e0, s);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    float *gval = c->d_work32;
+    int *grow = (int *)(c->d_work32 + 1024);
+    float *gpiv = c->d_work32 + 2048;
+    float *gdiag = c->d_work32 + 2048 + LU_NB;
+    for (int k = 0; k < n; k += LU_NB) {
+        const int kb = n - k < LU_NB ? n - k : LU_NB;
+        const int rows = n - k;
+        int G = (rows + 31) / 32;
+        if (G > nsm) G = nsm;
+        if (G > 1000) G = 1000;
+        int R = (rows + G - 1) / G;
+        G = (rows + R - 1) / R;
+        size_t smem = sizeof(float) * (size_t)R * (kb + 1);
+        if (smem > 200 * 1024)
+            return obem_fail(c, OBEM_ERR_ARG, "LU panel of %d rows does not fit shared memory", rows);
+        OBEM_CUDA(c, cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        OBEM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, 256, smem));
+        if (per_sm * nsm < G)
+            return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
+        PanelArgs pa;
+        pa.A = c->d_LU; pa.n = n; pa.k = k; pa.kb = kb; pa.rows_per_cta = R; pa.piv = c->d_piv;
+        pa.flag = c->d_flag; pa.gval = gval; pa.grow = grow; pa.gpiv = gpiv; pa.gdiag = gdiag;
+        void *args[] = {&pa};
+        OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
+        laswp_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_LU, n, k, kb, c->d_piv);
+        OBEM_LAUNCH(c);
+        if (k + kb < n) {
+            trsm_kernel<<<(n - k - kb + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, 0, s>>>(c->d_LU, n, k, kb);
+            OBEM_LAUNCH(c);
+            int rc = gemm_update(c, precision, c->d_LU, n, k, kb, s);
+            if (rc != OBEM_OK) return rc;
+        }
+    }
+    cudaEventRecord(e1, s);
+    int flag = 0;
+    OBEM_CUDA(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    OBEM_CUDA(c, cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->factor_ms = ms;
+    if (flag == OBEM_ERR_SINGULAR) return obem_fail(c, OBEM_ERR_SINGULAR, "LU: zero pivot");
+    if (flag == OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: panel grid barrier timed out");
+    c->factored = 1;
+    return OBEM_OK;
+}
+
+static int lu_solve(obem_ctx *c, float *y, cudaStream_t s)
+{
+    const int n = c->np;
+    for (int k = 0; k < n; k += LU_NB) {
+        const int kb = n - k < LU_NB ? n - k : LU_NB;
+        trsv_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 1);
+        if (k + kb < n)
+            trsv_update_kernel<<<(n - k - kb + 7) / 8, 256, 0, s>>>(c->d_LU, y, n, k, kb, k + kb, n);
+    }
+    for (int k = ((n - 1) / LU_NB) * LU_NB; k >= 0; k -= LU_NB) {
+        const int kb = n - k < LU_NB ? n - k : LU_NB;
+        trsv_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 0);
+        if (k > 0) trsv_update_kernel<<<(k + 7) / 8, 256, 0, s>>>(c->d_LU, y, n, k, kb, 0, k);
+    }
+    OBEM_LAUNCH(c);
+    return OBEM_OK;
+}
+
+int obem_solve_system(obem_ctx *c, const double *gv, const float *sigma_free, const float *drhs,
+                      float *sigma_out, obem_solve_report *rep, cudaStream_t s)
+{
+    const int n = c->np;
+    cublasSetStream(c->cublas, s);
+    double *b = c->d_work64, *x = b + n, *r = x + n, *nrm = r + n;
+    float *y = c->d_work32;
+    double *d_gv = NULL;
+    int ng = c->n_groups > 0 ? c->n_groups : 1;
+    OBEM_CUDA(c, cudaMalloc((void **)&d_gv, sizeof(double) * ng));
+    if (c->n_groups > 0)
+        OBEM_CUDA(c, cudaMemcpyAsync(d_gv, gv, sizeof(double) * c->n_groups, cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    rhs_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_kind, c->d_group, d_gv, sigma_free, drhs, c->d_rowscale, b, n);
+    OBEM_LAUNCH(c);
+    OBEM_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    double be = 1.0, be_prev = 2.0;
+    int it = 0, status = OBEM_ERR_NOT_CONVERGED;
+    const int max_it = 30;
+    for (; it <= max_it; ++it) {
+        residual_kernel<<<(n + 7) / 8, 256, 0, s>>>(c->d_A, x, b, r, n);
+        norms_kernel<<<1, 256, 0, s>>>(r, x, b, n, nrm);
+        OBEM_LAUNCH(c);
+        double h[3];
+        OBEM_CUDA(c, cudaMemcpyAsync(h, nrm, sizeof h, cudaMemcpyDeviceToHost, s));
+        OBEM_CUDA(c, cudaStreamSynchronize(s));
+        be = h[0] / (c->a_norm_inf * h[1] + h[2] + 1e-300);
+        // converged: at the FP64 rounding level, or no longer decreasing once
+        // below 1e-9 (the residual's own rounding floor for large n)
+        if (be < 1e-12 || (be < 1e-9 && be > 0.5 * be_prev)) { status = OBEM_OK; break; }
+        be_prev = be;
+        if (it == max_it) break;
+        permute_kernel<<<1, 32, 0, s>>>(r, y, c->d_piv, n, nrm);
+        OBEM_LAUNCH(c);
+        int rc = lu_solve(c, y, s);
+        if (rc != OBEM_OK) { cudaFree(d_gv); return rc; }
+        axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, nrm, n);
+        OBEM_LAUNCH(c);
+    }
+    to_float_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, sigma_out, c->d_sigma, n);
+    OBEM_LAUNCH(c);
+    cudaEventRecord(e1, s);
+    OBEM_CUDA(c, cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_gv);
+    c->sigma_valid = 1;
+    if (rep) {
+        rep->iterations = it;
+        rep->status = status;
+        rep->backward_error = be;
+        rep->factor_ms = c->factor_ms;
+        rep->solve_ms = ms;
+    }
+    if (status != OBEM_OK)
+        return obem_fail(c, OBEM_ERR_NOT_CONVERGED, "refinement stopped at backward error %.3e after %d iterations", be, it);
+    return OBEM_OK;
+}

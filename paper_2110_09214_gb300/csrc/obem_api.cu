@@ -1,0 +1,457 @@
+// Host side of the C ABI: context, gas and mesh loading, argument checks and
+// dispatch to the kernels of field.cu, step.cu and bem.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdlib.h>
+
+#include "obem_internal.cuh"
+
+int obem_fail(obem_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+static void free_dev(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+static void free_mesh(obem_ctx *c)
+{
+    free(c->h_kind); free(c->h_group); free(c->h_tri); free(c->h_em); free(c->h_ep);
+    c->h_kind = c->h_group = NULL;
+    c->h_tri = c->h_em = c->h_ep = NULL;
+    free_dev(c->d_c_a); free_dev(c->d_g0_h); free_dev(c->d_g1); free_dev(c->d_g2);
+    free_dev(c->d_nrm); free_dev(c->d_v64); free_dev(c->d_kind); free_dev(c->d_group);
+    free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
+    free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
+    c->d_c_a = c->d_g0_h = c->d_g1 = c->d_g2 = c->d_nrm = NULL;
+    c->d_v64 = NULL;
+    c->d_kind = c->d_group = NULL;
+    c->d_A = c->d_LU = NULL;
+    c->d_piv = NULL;
+    c->d_rowscale = NULL;
+    c->d_work64 = NULL;
+    c->d_work32 = NULL;
+    c->d_flag = NULL;
+    c->d_sigma = NULL;
+    c->np = 0;
+    c->factored = 0;
+    c->sigma_valid = 0;
+}
+
+extern "C" const char *obem_last_error(const obem_ctx *ctx)
+{
+    return ctx ? ctx->err : "null context";
+}
+
+extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
+{
+    if (!out || !cfg) return OBEM_ERR_ARG;
+    *out = NULL;
+    if (cfg->capacity < 1 || cfg->capacity > (1 << 30)) return OBEM_ERR_ARG;
+    if (cfg->trial_cap < 1 || cfg->trial_cap > OBEM_MAX_TRIALS) return OBEM_ERR_ARG;
+    if (!(cfg->dt > 0.0) || !(cfg->softening >= 0.0) || !(cfg->z_lo < cfg->z_hi)) return OBEM_ERR_ARG;
+    obem_ctx *c = (obem_ctx *)calloc(1, sizeof(obem_ctx));
+    if (!c) return OBEM_ERR_ARG;
+    c->cfg = *cfg;
+    strcpy(c->err, "no error");
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        free(c);
+        return OBEM_ERR_CUDA;
+    }
+    int cap = cfg->capacity;
+    c->cap = cap;
+    int max_blocks = (cap + 255) / 256 + 1;
+    size_t bytes = 0;
+#define ALLOC(p, n)                                                                     \
+    do {                                                                                \
+        if (cudaMalloc((void **)&(p), (size_t)(n)) != cudaSuccess) {                    \
+            obem_destroy(c);                                                            \
+            return OBEM_ERR_CUDA;                                                       \
+        }                                                                               \
+        bytes += (size_t)(n);                                                           \
+    } while (0)
+    ALLOC(c->s_E, sizeof(float4) * cap);
+    ALLOC(c->s_prop, sizeof(unsigned long long) * cap);
+    ALLOC(c->s_ionkey, sizeof(unsigned long long) * cap);
+    ALLOC(c->s_keep, sizeof(int32_t) * cap);
+    ALLOC(c->s_nsp, sizeof(int32_t) * cap);
+    ALLOC(c->s_blk, sizeof(int32_t) * 4 * max_blocks);
+    ALLOC(c->s_ctl, sizeof(StepCtl));
+    ALLOC(c->o_pos, sizeof(float4) * cap);
+    ALLOC(c->o_vel, sizeof(float4) * cap);
+    ALLOC(c->o_id, sizeof(uint32_t) * cap);
+    ALLOC(c->o_birth, sizeof(uint32_t) * cap);
+    ALLOC(c->o_sp, cap);
+#undef ALLOC
+    (void)bytes;
+    *out = c;
+    return OBEM_OK;
+}
+
+extern "C" void obem_destroy(obem_ctx *c)
+{
+    if (!c) return;
+    free_mesh(c);
+    free_dev(c->d_egrid); free_dev(c->d_xs);
+    free_dev(c->s_E); free_dev(c->s_prop); free_dev(c->s_ionkey); free_dev(c->s_keep);
+    free_dev(c->s_nsp); free_dev(c->s_blk); free_dev(c->s_ctl); free_dev(c->o_pos);
+    free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
+    if (c->cublas) cublasDestroy(c->cublas);
+    if (c->prof_ev) {
+        for (int i = 0; i < 4 * OBEM_PROF_MAX; ++i) cudaEventDestroy(c->prof_ev[i]);
+        free(c->prof_ev);
+    }
+    free_dev(c->d_counters);
+    free(c);
+}
+
+extern "C" int obem_profile(obem_ctx *c, int32_t enable)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (enable && !c->prof_ev) {
+        c->prof_ev = (cudaEvent_t *)calloc(4 * OBEM_PROF_MAX, sizeof(cudaEvent_t));
+        for (int i = 0; i < 4 * OBEM_PROF_MAX; ++i) OBEM_CUDA(c, cudaEventCreate(&c->prof_ev[i]));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_counters, sizeof(unsigned long long) * 5));
+    }
+    if (enable) {
+        OBEM_CUDA(c, cudaMemset(c->d_counters, 0, sizeof(unsigned long long) * 5));
+        c->prof_n = 0;
+        c->launches = 0;
+        c->steps_recorded = 0;
+    }
+    c->prof_on = enable ? 1 : 0;
+    return OBEM_OK;
+}
+
+extern "C" int obem_stage_times(obem_ctx *c, double *ms, int64_t *counts)
+{
+    if (!c || !ms || !counts) return OBEM_ERR_ARG;
+    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+    for (int k = 0; k < 7; ++k) counts[k] = 0;
+    if (!c->prof_ev) return OBEM_OK;
+    int n = c->prof_n < OBEM_PROF_MAX ? c->prof_n : OBEM_PROF_MAX;
+    for (int r = 0; r < n; ++r) {
+        cudaEvent_t *e = c->prof_ev + 4 * r;
+        OBEM_CUDA(c, cudaEventSynchronize(e[3]));
+        float t;
+        OBEM_CUDA(c, cudaEventElapsedTime(&t, e[0], e[1])); ms[0] += t;
+        OBEM_CUDA(c, cudaEventElapsedTime(&t, e[1], e[2])); ms[1] += t;
+        OBEM_CUDA(c, cudaEventElapsedTime(&t, e[2], e[3])); ms[2] += t;
+        OBEM_CUDA(c, cudaEventElapsedTime(&t, e[0], e[3])); ms[3] += t;
+    }
+    unsigned long long h[5];
+    OBEM_CUDA(c, cudaMemcpy(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost));
+    counts[0] = n;
+    counts[1] = c->launches;
+    for (int k = 0; k < 5; ++k) counts[2 + k] = (int64_t)h[k];
+    OBEM_CUDA(c, cudaMemset(c->d_counters, 0, sizeof h));
+    c->prof_n = 0;
+    c->launches = 0;
+    return OBEM_OK;
+}
+
+// Constants of the collision model, each computed in FP64 and rounded once.
+static void derive_gas(obem_ctx *c)
+{
+    GasDev &g = c->gas;
+    const obem_config &cf = c->cfg;
+    double M = c->gas_M_amu > 0 ? c->gas_M_amu * OBEM_AMU : INFINITY;
+    int Minf = isinf(M);
+    g.dt = (float)cf.dt;
+    g.nu_ion = (float)c->gas_nu_ion;
+    g.half_nu_ion = (float)(0.5 * c->gas_nu_ion);
+    g.E_therm = (float)(1.5 * OBEM_KB * c->gas_T / OBEM_QE);
+    g.v_th_ion = Minf ? 0.0f : (float)sqrt(3.0 * OBEM_KB * c->gas_T / M);
+    g.qm[OBEM_ELECTRON] = (float)(-OBEM_QE / OBEM_ME);
+    g.qm[OBEM_CATION] = Minf ? 0.0f : (float)(OBEM_QE / M);
+    g.qm[OBEM_ANION] = Minf ? 0.0f : (float)(-OBEM_QE / M);
+    g.K_e = (float)(0.5 * OBEM_ME / OBEM_QE);
+    g.two_m_over_M = Minf ? 0.0f : (float)(2.0 * OBEM_ME / M);
+    g.KCE = (float)(OBEM_KC * OBEM_QE);
+    g.N = (float)c->gas_N;
+    g.z_lo = (float)cf.z_lo;
+    g.z_hi = (float)cf.z_hi;
+    g.seed_lo = (uint32_t)(cf.seed & 0xFFFFFFFFu);
+    g.seed_hi = (uint32_t)(cf.seed >> 32);
+    g.trial_cap = cf.trial_cap;
+    g.recomb_on = cf.beta >= 0.0;
+    double rc = 0.0;
+    if (cf.beta > 0.0) rc = cbrt(3.0 * cf.beta * cf.dt / (4.0 * OBEM_PI));
+    else if (cf.beta == 0.0 && c->gas_thr_ioni > 0.0f) rc = OBEM_KC * OBEM_QE / (2.0 * (double)c->gas_thr_ioni);
+    else if (cf.beta == 0.0) g.recomb_on = 0;
+    g.rc2 = (float)(rc * rc);
+}
+
+extern "C" int obem_gas_load(obem_ctx *c, const obem_gas *gs)
+{
+    if (!c || !gs) return OBEM_ERR_ARG;
+    if (gs->n_proc < 1 || gs->n_proc > OBEM_MAX_PROC || gs->n_energy < 2 || gs->n_energy > 4096)
+        return obem_fail(c, OBEM_ERR_ARG, "gas: n_proc must be 1..%d, n_energy 2..4096", OBEM_MAX_PROC);
+    if (!gs->energy_eV || !gs->sigma_m2 || !gs->kind || !gs->mode || !gs->threshold_eV || !gs->nu_const)
+        return obem_fail(c, OBEM_ERR_ARG, "gas: null table pointer");
+    for (int i = 0; i + 1 < gs->n_energy; ++i)
+        if (!(gs->energy_eV[i] < gs->energy_eV[i + 1]))
+            return obem_fail(c, OBEM_ERR_ARG, "gas: energy grid not increasing at %d", i);
+    for (int j = 0; j < gs->n_proc; ++j) {
+        if (gs->kind[j] < 0 || gs->kind[j] > 3 || gs->mode[j] < 0 || gs->mode[j] > 1)
+            return obem_fail(c, OBEM_ERR_ARG, "gas: bad kind/mode of process %d", j);
+    }
+    if (!(gs->N >= 0.0) || !(gs->T >= 0.0) || !(gs->nu_ion >= 0.0))
+        return obem_fail(c, OBEM_ERR_ARG, "gas: negative N, T or nu_ion");
+    int ne = gs->n_energy, npr = gs->n_proc;
+    free_dev(c->d_egrid); free_dev(c->d_xs);
+    c->d_egrid = NULL; c->d_xs = NULL;
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_egrid, sizeof(float) * ne));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_xs, sizeof(float) * ne * npr));
+    OBEM_CUDA(c, cudaMemcpy(c->d_egrid, gs->energy_eV, sizeof(float) * ne, cudaMemcpyHostToDevice));
+    OBEM_CUDA(c, cudaMemcpy(c->d_xs, gs->sigma_m2, sizeof(float) * ne * npr, cudaMemcpyHostToDevice));
+    GasDev &g = c->gas;
+    memset(&g, 0, sizeof g);
+    g.egrid = c->d_egrid;
+    g.xs = c->d_xs;
+    g.n_proc = npr;
+    g.n_e = ne;
+    c->gas_T = gs->T; c->gas_N = gs->N; c->gas_M_amu = gs->M_amu; c->gas_nu_ion = gs->nu_ion;
+    c->gas_thr_ioni = 0.0f;
+    for (int j = 0; j < npr; ++j) {
+        g.kind[j] = gs->kind[j];
+        g.mode[j] = gs->mode[j];
+        g.thr[j] = gs->threshold_eV[j];
+        g.nuc[j] = gs->nu_const[j];
+        if (gs->kind[j] == OBEM_P_IONISATION && c->gas_thr_ioni == 0.0f) c->gas_thr_ioni = gs->threshold_eV[j];
+    }
+    // Majorant of the electron collision frequency for the null-collision
+    // method: constant-frequency processes add their frequency; tabulated ones
+    // are bounded on each grid segment by N max(sigma_tot) v(E_upper).
+    double nuc = 0.0, best = 0.0;
+    for (int j = 0; j < npr; ++j)
+        if (gs->mode[j] == OBEM_MODE_CONST) nuc += (double)gs->nu_const[j];
+    for (int i = 0; i + 1 < ne; ++i) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < npr; ++j) {
+            if (gs->mode[j] != OBEM_MODE_TABLE) continue;
+            s0 += (double)gs->sigma_m2[(size_t)j * ne + i];
+            s1 += (double)gs->sigma_m2[(size_t)j * ne + i + 1];
+        }
+        double v1 = sqrt(2.0 * (double)gs->energy_eV[i + 1] * OBEM_QE / OBEM_ME);
+        double b = gs->N * (s0 > s1 ? s0 : s1) * v1;
+        if (b > best) best = b;
+    }
+    g.nu_max_e = (float)(nuc + best);
+    derive_gas(c);
+    c->gas_loaded = 1;
+    return OBEM_OK;
+}
+
+extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const int32_t *kind,
+                              const int32_t *group, const double *em, const double *ep,
+                              int32_t n_groups)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (np < 1 || np > 200000) return obem_fail(c, OBEM_ERR_ARG, "mesh: n_panels must be 1..200000");
+    if (!tri || !kind || !group || !em || !ep) return obem_fail(c, OBEM_ERR_ARG, "mesh: null array");
+    if (n_groups < 0) return obem_fail(c, OBEM_ERR_ARG, "mesh: n_groups < 0");
+    for (int i = 0; i < np; ++i) {
+        if (kind[i] != OBEM_CELL_ELECTRODE && kind[i] != OBEM_CELL_DIELECTRIC)
+            return obem_fail(c, OBEM_ERR_ARG, "mesh: bad kind of cell %d", i);
+        if (kind[i] == OBEM_CELL_ELECTRODE && (group[i] < 0 || group[i] >= n_groups))
+            return obem_fail(c, OBEM_ERR_ARG, "mesh: cell %d has group %d outside 0..%d", i, group[i], n_groups - 1);
+    }
+    free_mesh(c);
+    c->np = np;
+    c->n_groups = n_groups;
+    c->h_kind = (int *)malloc(sizeof(int) * np);
+    c->h_group = (int *)malloc(sizeof(int) * np);
+    c->h_tri = (double *)malloc(sizeof(double) * 9 * np);
+    c->h_em = (double *)malloc(sizeof(double) * np);
+    c->h_ep = (double *)malloc(sizeof(double) * np);
+    memcpy(c->h_kind, kind, sizeof(int) * np);
+    memcpy(c->h_group, group, sizeof(int) * np);
+    memcpy(c->h_tri, tri, sizeof(double) * 9 * np);
+    memcpy(c->h_em, em, sizeof(double) * np);
+    memcpy(c->h_ep, ep, sizeof(double) * np);
+    float4 *ca = (float4 *)malloc(sizeof(float4) * np);
+    float4 *g0 = (float4 *)malloc(sizeof(float4) * np);
+    float4 *g1 = (float4 *)malloc(sizeof(float4) * np);
+    float4 *g2 = (float4 *)malloc(sizeof(float4) * np);
+    float4 *nr = (float4 *)malloc(sizeof(float4) * np);
+    for (int i = 0; i < np; ++i) {
+        const double *v = tri + 9 * (size_t)i;
+        double cc[3], e1[3], e2[3], nn[3];
+        for (int k = 0; k < 3; ++k) {
+            cc[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0;
+            e1[k] = v[3 + k] - v[k];
+            e2[k] = v[6 + k] - v[k];
+        }
+        nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double a2 = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+        if (!(a2 > 0.0)) {
+            free(ca); free(g0); free(g1); free(g2); free(nr);
+            free_mesh(c);
+            return obem_fail(c, OBEM_ERR_ARG, "mesh: cell %d is degenerate", i);
+        }
+        double h2 = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            const double *a = v + 3 * e, *b = v + 3 * ((e + 1) % 3);
+            double d = (a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]);
+            if (d > h2) h2 = d;
+        }
+        ca[i] = make_float4((float)cc[0], (float)cc[1], (float)cc[2], (float)(OBEM_KC * 0.5 * a2));
+        g0[i] = make_float4((float)(v[0] - cc[0]), (float)(v[1] - cc[1]), (float)(v[2] - cc[2]), (float)h2);
+        g1[i] = make_float4((float)(v[3] - cc[0]), (float)(v[4] - cc[1]), (float)(v[5] - cc[2]), 0.f);
+        g2[i] = make_float4((float)(v[6] - cc[0]), (float)(v[7] - cc[1]), (float)(v[8] - cc[2]), 0.f);
+        nr[i] = make_float4((float)(nn[0] / a2), (float)(nn[1] / a2), (float)(nn[2] / a2), (float)kind[i]);
+    }
+    int rc = OBEM_OK;
+    size_t f4 = sizeof(float4) * np;
+#define UP(dst, src, bytes)                                                              \
+    do {                                                                                 \
+        if (rc == OBEM_OK && (cudaMalloc((void **)&(dst), (bytes)) != cudaSuccess ||     \
+                              cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice)  \
+                                  != cudaSuccess))                                       \
+            rc = obem_fail(c, OBEM_ERR_CUDA, "mesh upload failed");                      \
+    } while (0)
+    UP(c->d_c_a, ca, f4);
+    UP(c->d_g0_h, g0, f4);
+    UP(c->d_g1, g1, f4);
+    UP(c->d_g2, g2, f4);
+    UP(c->d_nrm, nr, f4);
+    UP(c->d_v64, tri, sizeof(double) * 9 * np);
+    UP(c->d_kind, kind, sizeof(int) * np);
+    UP(c->d_group, group, sizeof(int) * np);
+#undef UP
+    free(ca); free(g0); free(g1); free(g2); free(nr);
+    if (rc == OBEM_OK && cudaMalloc((void **)&c->d_sigma, sizeof(float) * np) != cudaSuccess)
+        rc = obem_fail(c, OBEM_ERR_CUDA, "mesh: sigma allocation failed");
+    if (rc != OBEM_OK) free_mesh(c);
+    return rc;
+}
+
+static PanelsDev panels_of(const obem_ctx *c)
+{
+    PanelsDev p;
+    p.c_a = c->d_c_a; p.g0_h = c->d_g0_h; p.g1 = c->d_g1; p.g2 = c->d_g2; p.nrm = c->d_nrm;
+    p.v64 = c->d_v64;
+    p.np = c->np;
+    return p;
+}
+
+extern "C" int obem_bem_assemble(obem_ctx *c, int32_t precision, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (c->np < 1) return obem_fail(c, OBEM_ERR_STATE, "assemble: no mesh loaded");
+    if (precision < OBEM_LU_FP32 || precision > OBEM_LU_BF16X9)
+        return obem_fail(c, OBEM_ERR_ARG, "assemble: unknown precision %d", precision);
+    return obem_assemble_and_factor(c, precision, (cudaStream_t)stream);
+}
+
+extern "C" int obem_bem_solve(obem_ctx *c, const double *gv, const float *sigma_free,
+                              const float *drhs, float *sigma_out, obem_solve_report *rep,
+                              obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (!c->factored) return obem_fail(c, OBEM_ERR_STATE, "solve: call obem_bem_assemble first");
+    if (c->n_groups > 0 && !gv) return obem_fail(c, OBEM_ERR_ARG, "solve: group_voltage is NULL");
+    if (!sigma_out) return obem_fail(c, OBEM_ERR_ARG, "solve: sigma_out is NULL");
+    return obem_solve_system(c, gv, sigma_free, drhs, sigma_out, rep, (cudaStream_t)stream);
+}
+
+extern "C" int obem_field_eval(obem_ctx *c, const float *targets, int32_t nt, const float *sources,
+                               int32_t ns, int32_t self_exclude, const float *sigma, float *E_out,
+                               obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (nt < 0 || (sources && ns < 0)) return obem_fail(c, OBEM_ERR_ARG, "field: negative count");
+    if (nt == 0) return OBEM_OK;
+    if (!targets || !E_out) return obem_fail(c, OBEM_ERR_ARG, "field: null targets or E_out");
+    if (self_exclude && (!sources || ns != nt))
+        return obem_fail(c, OBEM_ERR_ARG, "field: self_exclude needs sources with ns == nt");
+    if (sigma && c->np < 1) return obem_fail(c, OBEM_ERR_STATE, "field: sigma given but no mesh loaded");
+    if (((uintptr_t)targets | (uintptr_t)E_out | (uintptr_t)sources) & 15)
+        return obem_fail(c, OBEM_ERR_ARG, "field: arrays must be 16-byte aligned");
+    FieldLaunch L;
+    memset(&L, 0, sizeof L);
+    L.targets = (const float4 *)targets;
+    L.nt = nt;
+    L.sources = (sources && ns > 0) ? (const float4 *)sources : NULL;
+    L.ns = ns;
+    L.self_exclude = self_exclude ? 1 : 0;
+    L.eps2 = 0.0f;
+    L.sigma = sigma;
+    L.panels = panels_of(c);
+    L.E_out = (float4 *)E_out;
+    L.e_ext = make_float3(0.f, 0.f, 0.f);
+    L.want_v = 1;
+    return obem_launch_field(c, L, nt, (cudaStream_t)stream);
+}
+
+extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, uint32_t step,
+                         obem_step_stats *stats, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (!c->gas_loaded) return obem_fail(c, OBEM_ERR_STATE, "step: call obem_gas_load first");
+    if (!st || !stats) return obem_fail(c, OBEM_ERR_ARG, "step: null state or stats");
+    if (!st->pos_q || !st->vel || !st->id || !st->birth || !st->species || !st->n || !st->next_id)
+        return obem_fail(c, OBEM_ERR_ARG, "step: null state array");
+    if (st->capacity < 1 || st->capacity > c->cap)
+        return obem_fail(c, OBEM_ERR_ARG, "step: state capacity %d outside 1..%d", st->capacity, c->cap);
+    if (((uintptr_t)st->pos_q | (uintptr_t)st->vel | (uintptr_t)E_in) & 15)
+        return obem_fail(c, OBEM_ERR_ARG, "step: pos_q / vel / E_in must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float4 *E = (const float4 *)E_in;
+    int partners_done = 0;
+    cudaEvent_t *ev = NULL;
+    if (c->prof_on) {
+        ev = c->prof_ev + 4 * (c->prof_n % OBEM_PROF_MAX);
+        if (c->prof_n < OBEM_PROF_MAX) c->prof_n++;
+        cudaEventRecord(ev[0], s);
+    }
+    int want_cells = (c->cfg.flags & OBEM_STEP_CELL_FIELD) && c->sigma_valid;
+    int want_nbody = (c->cfg.flags & OBEM_STEP_SPACE_CHARGE) != 0;
+    if (!E) {
+        FieldLaunch L;
+        memset(&L, 0, sizeof L);
+        L.targets = (const float4 *)st->pos_q;
+        L.nt_dev = st->n;
+        L.nt = st->capacity;
+        L.sources = want_nbody ? (const float4 *)st->pos_q : NULL;
+        L.ns_dev = st->n;
+        L.ns = st->capacity;
+        L.self_exclude = 1;
+        L.eps2 = (float)(c->cfg.softening * c->cfg.softening);
+        L.sigma = want_cells ? c->d_sigma : NULL;
+        L.panels = panels_of(c);
+        L.E_out = c->s_E;
+        L.e_ext = make_float3((float)c->cfg.e_ext[0], (float)c->cfg.e_ext[1], (float)c->cfg.e_ext[2]);
+        L.want_v = 0;
+        if (ev) L.counters = c->d_counters;
+        L.events = ev;
+        if (c->gas.recomb_on) {
+            L.species = st->species;
+            L.birth = st->birth;
+            L.step = step;
+            L.rc2 = c->gas.rc2;
+            L.prop = c->s_prop;
+        }
+        int rc = obem_launch_field(c, L, st->capacity, s);
+        if (rc != OBEM_OK) return rc;
+        E = c->s_E;
+        partners_done = want_nbody && c->gas.recomb_on;
+    } else if (ev) {
+        cudaEventRecord(ev[1], s);
+        cudaEventRecord(ev[2], s);
+    }
+    int rc = obem_launch_step(c, st, E, step, stats, s, partners_done);
+    if (ev) cudaEventRecord(ev[3], s);
+    return rc;
+}

@@ -1,0 +1,172 @@
+// Internal declarations shared by the translation units of libobem.
+// Not part of the public ABI (include/obem.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/obem.h"
+
+// ---------------------------------------------------------------- constants
+// CODATA 2018 (SI)
+#define OBEM_QE 1.602176634e-19
+#define OBEM_ME 9.1093837015e-31
+#define OBEM_EPS0 8.8541878128e-12
+#define OBEM_KB 1.380649e-23
+#define OBEM_AMU 1.66053906660e-27
+#define OBEM_PI 3.14159265358979323846
+#define OBEM_KC (1.0 / (4.0 * OBEM_PI * OBEM_EPS0))
+
+#define OBEM_MAX_PROC 32
+#define OBEM_MAX_TRIALS 256
+
+// ---------------------------------------------------------------- gas constants
+// Everything the step kernels need, passed by value.  The float members are
+// derived in FP64 on the host and rounded once.
+struct GasDev {
+    const float *egrid;   // [n_e]
+    const float *xs;      // [n_proc][n_e]
+    int n_proc, n_e;
+    int kind[OBEM_MAX_PROC];
+    int mode[OBEM_MAX_PROC];
+    float thr[OBEM_MAX_PROC];
+    float nuc[OBEM_MAX_PROC];
+    float dt, nu_max_e, nu_ion, half_nu_ion, E_therm, v_th_ion;
+    float qm[3];
+    float K_e, two_m_over_M, KCE, N, z_lo, z_hi, rc2;
+    float ion_thr;
+    int recomb_on;
+    uint32_t seed_lo, seed_hi;
+    int trial_cap;
+};
+
+// Cell geometry in the layout of the field kernels (structure of arrays).
+//   c_a  = (cx, cy, cz, k_C * area)
+//   g0_h = (v0 - c, h^2)      h = longest edge
+//   g1   = (v1 - c, 0)
+//   g2   = (v2 - c, 0)
+//   v64  = FP64 vertices [np][9] for the near-field closed form
+//   nrm  = (nx, ny, nz, kind)
+struct PanelsDev {
+    const float4 *c_a, *g0_h, *g1, *g2, *nrm;
+    const double *v64;
+    int np;
+};
+
+// Device-resident control block of one obem_step call.
+struct StepCtl {
+    int32_t abort;        // non-zero: do not commit
+    int32_t n_keep;       // survivors
+    int32_t n_spawn;      // spawned pairs
+    int32_t trial_overflow;
+};
+
+struct obem_ctx {
+    obem_config cfg;
+    char err[512];
+    int device;
+    // gas
+    int gas_loaded;
+    GasDev gas;
+    float *d_egrid, *d_xs;
+    float gas_thr_ioni;
+    double gas_T, gas_N, gas_M_amu, gas_nu_ion;
+    // mesh
+    int np, n_groups;
+    int *h_kind, *h_group;
+    double *h_tri, *h_em, *h_ep;
+    float4 *d_c_a, *d_g0_h, *d_g1, *d_g2, *d_nrm;
+    double *d_v64;
+    int *d_kind, *d_group;
+    // BEM
+    float *d_A;          // equilibrated matrix, row-major [np][np]
+    float *d_LU;         // LU factors (row-major, unit lower L below the diagonal)
+    int *d_piv;          // row swaps of the factorisation
+    double *d_rowscale;  // 1 / max |A_ij| per row
+    double *d_work64;    // 4 * np doubles
+    float *d_work32;     // 2 * np floats
+    int *d_flag;         // device status of the LU (singular / timeout)
+    int factored;
+    double factor_ms;
+    double a_norm_inf;
+    float *d_sigma;      // current sigma [np]
+    int sigma_valid;
+    cublasHandle_t cublas;
+    // step scratch (capacity-sized)
+    float4 *s_E;
+    unsigned long long *s_prop, *s_ionkey;
+    int32_t *s_keep, *s_nsp;
+    int32_t *s_blk;       // per-block sums / offsets (2 * max_blocks)
+    StepCtl *s_ctl;
+    float4 *o_pos, *o_vel;
+    uint32_t *o_id, *o_birth;
+    uint8_t *o_sp;
+    int cap;
+    // stage timing (obem_profile)
+    int prof_on;
+    int prof_n;                      // recorded steps (ring of OBEM_PROF_MAX)
+    cudaEvent_t *prof_ev;            // [OBEM_PROF_MAX][4]
+    unsigned long long *d_counters;  // [5] pairs, 1pt, 3pt, 7pt, closed form
+    long long launches;              // kernels launched by recorded steps
+    long long steps_recorded;
+};
+#define OBEM_PROF_MAX 256
+
+// ---------------------------------------------------------------- error helpers
+int obem_fail(obem_ctx *ctx, int code, const char *fmt, ...);
+#define OBEM_CUDA(ctx, call)                                                              \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return obem_fail((ctx), OBEM_ERR_CUDA, "%s failed: %s (%s:%d)", #call,        \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+    } while (0)
+#define OBEM_LAUNCH(ctx)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess)                                                            \
+            return obem_fail((ctx), OBEM_ERR_CUDA, "kernel launch failed: %s (%s:%d)",    \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+    } while (0)
+
+// ---------------------------------------------------------------- entry points between TUs
+// field.cu
+struct FieldLaunch {
+    const float4 *targets;
+    const int32_t *nt_dev;   // device count (step) or NULL
+    int nt;
+    const float4 *sources;   // NULL: no Coulomb part
+    const int32_t *ns_dev;
+    int ns;
+    int self_exclude;
+    float eps2;              // Plummer softening squared (m^2)
+    const float *sigma;      // NULL: no cell part
+    PanelsDev panels;
+    float4 *E_out;
+    float3 e_ext;
+    int want_v;
+    // recombination partner search
+    const uint8_t *species;
+    const uint32_t *birth;
+    uint32_t step;
+    float rc2;
+    unsigned long long *prop;
+    // optional tier counters [5]: charge pairs, 1-point, 3-point, 7-point, closed-form
+    unsigned long long *counters;
+    // optional events: [1] recorded after the cell kernel, [2] after the all-pairs kernel
+    cudaEvent_t *events;
+};
+int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets, cudaStream_t s);
+
+// step.cu
+// partners_done: the field pass already proposed recombination partners
+int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,
+                     obem_step_stats *stats, cudaStream_t s, int partners_done);
+
+// bem.cu
+int obem_assemble_and_factor(obem_ctx *ctx, int precision, cudaStream_t s);
+int obem_solve_system(obem_ctx *ctx, const double *gv, const float *sigma_free, const float *drhs,
+                      float *sigma_out, obem_solve_report *rep, cudaStream_t s);

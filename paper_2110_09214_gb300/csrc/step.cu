@@ -1,0 +1,604 @@
+// The tracking step (Sec. 3.2 - 3.3): recombination resolve, free flight with
+// exact null-collision trials, ionisation spawn, attachment, absorption on the
+// electrode planes, and a deterministic two-pass stream compaction.
+//
+// Built with --fmad=false: every binary32 operation of the step is one IEEE
+// rounding, so that, given the same field, the collision processes, spawns,
+// and the compacted order are reproducible bit for bit by any IEEE binary32
+// implementation of the same operation sequence.
+//
+// Passes (all stream-ordered, nothing synchronises):
+//   init      zero the stats and the control block
+//   partners  (only when the field kernel did not search them) nearest cation
+//   resolve   each proposing electron atomicMin's (d^2, e) into its cation
+//   count     simulate every charge without writing: survivors, spawn counts,
+//             per-block totals for the scan
+//   scan      one block: block offsets, totals, capacity check (all-or-nothing)
+//   write     simulate again (same counters, same draws) and write survivors
+//             and spawned charges to their final slots in scratch
+//   commit    copy scratch to the caller's arrays, update n and next_id
+//   moments   species counts and cloud moments of the new state
+#include "obem_internal.cuh"
+
+#define ST_THREADS 256
+
+typedef unsigned long long u64;
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror & Shaw, SC'11: ten rounds of two 32x32->64 multiplies
+// with a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform in [0, 1) from the top 24 bits
+__device__ __forceinline__ float unif01(uint32_t u)
+{
+    return (float)(u >> 8) * 5.9604645e-08f;
+}
+
+// -ln(U), U = ((u >> 8) + 1) 2^-24 in (0, 1]: U = 2^(e-24) f with f in [1, 2),
+// ln f = 2 atanh((f-1)/(f+1)) summed to the 13th power (basic operations only)
+__device__ float neg_log_unif(uint32_t u)
+{
+    uint32_t m = (u >> 8) + 1u;
+    int e = 31 - __clz(m);
+    float mf = (float)m;
+    float f = mf / (float)(1u << e);
+    float t = (f - 1.0f) / (f + 1.0f);
+    float t2 = t * t;
+    float s = 0.07692308f;
+    s = s * t2 + 0.09090909f;
+    s = s * t2 + 0.11111111f;
+    s = s * t2 + 0.14285715f;
+    s = s * t2 + 0.2f;
+    s = s * t2 + 0.33333334f;
+    s = s * t2 + 1.0f;
+    float lnf = 2.0f * t * s;
+    float a = (float)(24 - e) * 0.6931472f;
+    return a - lnf;
+}
+
+// sin, cos of a in [0, pi/2) by their Taylor series in a^2 (Horner)
+__device__ __forceinline__ void sincos_quadrant(float a, float &sn, float &cs)
+{
+    float a2 = a * a;
+    float ps = -1.6059044e-10f;
+    ps = ps * a2 + 2.5052108e-08f;
+    ps = ps * a2 - 2.7557319e-06f;
+    ps = ps * a2 + 0.0001984127f;
+    ps = ps * a2 - 0.008333334f;
+    ps = ps * a2 + 0.16666667f;
+    ps = ps * a2 - 1.0f;
+    sn = -(a * ps);
+    float pc = 2.0876756e-09f;
+    pc = pc * a2 - 2.755732e-07f;
+    pc = pc * a2 + 2.4801588e-05f;
+    pc = pc * a2 - 0.0013888889f;
+    pc = pc * a2 + 0.041666668f;
+    pc = pc * a2 - 0.5f;
+    pc = pc * a2 + 1.0f;
+    cs = pc;
+}
+
+// isotropic unit vector: cos(theta) = 1 - 2u, azimuth 2 pi u' with the
+// quadrant taken from the two top bits of u''s 24-bit fraction
+__device__ __forceinline__ float3 isotropic(uint32_t ua, uint32_t ub)
+{
+    float c = 1.0f - 2.0f * unif01(ua);
+    float cc = c * c;
+    float om = 1.0f - cc;
+    if (om < 0.0f) om = 0.0f;
+    float s = sqrtf(om);
+    uint32_t b = ub >> 8;
+    uint32_t q = b >> 22;
+    float f = (float)(b & 0x3FFFFFu) * 5.9604645e-08f;
+    float a = f * 6.2831855f;
+    float sa, ca;
+    sincos_quadrant(a, sa, ca);
+    float cp, sp;
+    if (q == 0u) { cp = ca; sp = sa; }
+    else if (q == 1u) { cp = -sa; sp = ca; }
+    else if (q == 2u) { cp = -ca; sp = -sa; }
+    else { cp = sa; sp = -ca; }
+    return make_float3(s * cp, s * sp, c);
+}
+
+// next representable float from x toward +inf (dir > 0) or -inf
+__device__ __forceinline__ float next_toward(float x, float dir)
+{
+    if (x == 0.0f) return dir > 0.0f ? __int_as_float(1) : __int_as_float((int)0x80000001u);
+    int b = __float_as_int(x);
+    bool up = dir > 0.0f;
+    bool pos = x > 0.0f;
+    return __int_as_float(up == pos ? b + 1 : b - 1);
+}
+
+// ------------------------------------------------------------------ one charge
+struct FlightOut {
+    int dead, attached, nsp, collisions, trials, overflow;
+};
+
+// Flight of charge i over one step under the field E (Euler in the field,
+// exact ballistic motion between trials), null-collision trials at
+// exponential waiting times -ln(U)/nu_max, process chosen with probability
+// nu_j(eps)/nu_max, ionisation products at the distance of Eq. (distIoni).
+// When emit is set, spawned pairs are written to o_* at slots sbase, sbase+1...
+template <bool EMIT>
+__device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, float3 &v, uint8_t &sp,
+                    float3 E, FlightOut &fo, float4 *o_pos, float4 *o_vel, uint32_t *o_id,
+                    uint32_t *o_birth, uint8_t *o_sp, int sbase, uint32_t id_base)
+{
+    const int s = sp;
+    const float qm = g.qm[s];
+    const float ax = qm * E.x, ay = qm * E.y, az = qm * E.z;
+    const float hx = 0.5f * ax, hy = 0.5f * ay, hz = 0.5f * az;
+    const float numax = (s == OBEM_ELECTRON) ? g.nu_max_e : g.nu_ion;
+    float t = 0.0f;
+    uint32_t k = 0;
+    for (;;) {
+        float tau;
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        if (numax > 0.0f) {
+            k += 1u;
+            if ((int)k > g.trial_cap) { fo.overflow = 1; return; }
+            r = philox4x32_10(make_uint4(id, step, k, 0u), g.seed_lo, g.seed_hi);
+            tau = neg_log_unif(r.x) / numax;
+        } else {
+            tau = __int_as_float(0x7f800000);
+        }
+        float tn = t + tau;
+        float fl = (tn >= g.dt) ? (g.dt - t) : tau;
+        {
+            float w = hx * fl; float xx = v.x + w; float y = xx * fl; p.x = p.x + y; float dv = ax * fl; v.x = v.x + dv;
+        }
+        {
+            float w = hy * fl; float xx = v.y + w; float y = xx * fl; p.y = p.y + y; float dv = ay * fl; v.y = v.y + dv;
+        }
+        {
+            float w = hz * fl; float xx = v.z + w; float y = xx * fl; p.z = p.z + y; float dv = az * fl; v.z = v.z + dv;
+        }
+        if (p.z <= g.z_lo || p.z >= g.z_hi) { fo.dead = 1; return; }
+        if (tn >= g.dt) return;
+        t = tn;
+        fo.trials += 1;
+        float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
+        float speed = sqrtf(v2);
+        float x = unif01(r.y) * numax;
+        if (s == OBEM_ELECTRON) {
+            float eps = g.K_e * v2;
+            int lo = 0, hi = g.n_e - 1;
+            float w;
+            if (eps < __ldg(&g.egrid[0])) { lo = 0; w = 0.0f; }
+            else if (eps >= __ldg(&g.egrid[g.n_e - 1])) { lo = g.n_e - 2; w = 1.0f; }
+            else {
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) / 2;
+                    if (__ldg(&g.egrid[mid]) <= eps) lo = mid; else hi = mid;
+                }
+                float e0 = __ldg(&g.egrid[lo]), e1 = __ldg(&g.egrid[lo + 1]);
+                w = (eps - e0) / (e1 - e0);
+            }
+            float Ns = g.N * speed;
+            float cum = 0.0f;
+            int proc = -1;
+            for (int j = 0; j < g.n_proc; ++j) {
+                float nu;
+                if (g.mode[j] == OBEM_MODE_CONST) {
+                    nu = g.nuc[j];
+                } else {
+                    const float *row = g.xs + (size_t)j * g.n_e;
+                    float s0 = __ldg(&row[lo]);
+                    float s1 = __ldg(&row[lo + 1]);
+                    float ds = s1 - s0;
+                    float sg = s0 + w * ds;
+                    if (eps < g.thr[j]) sg = 0.0f;
+                    nu = Ns * sg;
+                }
+                cum = cum + nu;
+                if (x < cum) { proc = j; break; }
+            }
+            if (proc < 0) continue;
+            const int kind = g.kind[proc];
+            if (kind == OBEM_P_ELASTIC) {
+                float3 d = isotropic(r.z, r.w);
+                float cosx = 0.0f;
+                if (speed > 0.0f) cosx = (v.x * d.x + v.y * d.y + v.z * d.z) / speed;
+                float om = 1.0f - cosx;
+                float loss = g.two_m_over_M * om;
+                float f = 1.0f - loss;
+                float sn = speed * sqrtf(f);
+                v = make_float3(sn * d.x, sn * d.y, sn * d.z);
+                fo.collisions += 1;
+            } else if (kind == OBEM_P_EXCITATION) {
+                float e2 = eps - g.thr[proc];
+                if (e2 < 0.0f) e2 = 0.0f;
+                float sn = sqrtf(e2 / g.K_e);
+                float3 d = isotropic(r.z, r.w);
+                v = make_float3(sn * d.x, sn * d.y, sn * d.z);
+                fo.collisions += 1;
+            } else if (kind == OBEM_P_IONISATION) {
+                float er = eps - g.thr[proc];
+                er = er - g.E_therm;
+                if (!(er > 0.0f)) continue;
+                float half = 0.5f * er;
+                float sn = sqrtf(half / g.K_e);
+                float3 d = isotropic(r.z, r.w);
+                float rr = g.KCE / (2.0f * er);
+                float ox = rr * d.x, oy = rr * d.y, oz = rr * d.z;
+                float3 pn = make_float3(p.x + ox, p.y + oy, p.z + oz);
+                float3 pp = make_float3(p.x - ox, p.y - oy, p.z - oz);
+                if (pn.x == p.x && pn.y == p.y && pn.z == p.z) {
+                    int axi = 0;
+                    float a0 = fabsf(d.x), a1 = fabsf(d.y), a2 = fabsf(d.z);
+                    if (a1 > a0) axi = 1;
+                    if (a2 > (axi == 1 ? a1 : a0)) axi = 2;
+                    if (axi == 0) { pn.x = next_toward(p.x, d.x); pp.x = next_toward(p.x, -d.x); }
+                    else if (axi == 1) { pn.y = next_toward(p.y, d.y); pp.y = next_toward(p.y, -d.y); }
+                    else { pn.z = next_toward(p.z, d.z); pp.z = next_toward(p.z, -d.z); }
+                }
+                if (EMIT) {
+                    uint4 r2 = philox4x32_10(make_uint4(id, step, k, 1u), g.seed_lo, g.seed_hi);
+                    float3 di = isotropic(r2.x, r2.y);
+                    int slot = sbase + 2 * fo.nsp;
+                    o_pos[slot] = make_float4(pn.x, pn.y, pn.z, -(float)OBEM_QE);
+                    o_vel[slot] = make_float4(sn * d.x, sn * d.y, sn * d.z, 0.0f);
+                    o_id[slot] = id_base + (uint32_t)(2 * fo.nsp);
+                    o_birth[slot] = step + 1u;
+                    o_sp[slot] = OBEM_ELECTRON;
+                    o_pos[slot + 1] = make_float4(p.x, p.y, p.z, (float)OBEM_QE);
+                    o_vel[slot + 1] = make_float4(g.v_th_ion * di.x, g.v_th_ion * di.y, g.v_th_ion * di.z, 0.0f);
+                    o_id[slot + 1] = id_base + (uint32_t)(2 * fo.nsp + 1);
+                    o_birth[slot + 1] = step + 1u;
+                    o_sp[slot + 1] = OBEM_CATION;
+                }
+                p = pp;
+                v = make_float3(-sn * d.x, -sn * d.y, -sn * d.z);
+                fo.nsp += 1;
+                fo.collisions += 1;
+            } else {
+                float3 d = isotropic(r.z, r.w);
+                v = make_float3(g.v_th_ion * d.x, g.v_th_ion * d.y, g.v_th_ion * d.z);
+                sp = OBEM_ANION;
+                fo.attached = 1;
+                fo.collisions += 1;
+                return;
+            }
+        } else {
+            float3 d = isotropic(r.z, r.w);
+            float sn = (x < g.half_nu_ion) ? speed : g.v_th_ion;
+            v = make_float3(sn * d.x, sn * d.y, sn * d.z);
+            fo.collisions += 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ int cur_n(const obem_state &st) { return *st.n; }
+
+__global__ void init_kernel(obem_step_stats *stats, StepCtl *ctl, const obem_state st)
+{
+    if (threadIdx.x == 0) {
+        memset(stats, 0, sizeof(obem_step_stats));
+        memset(ctl, 0, sizeof(StepCtl));
+        stats->n_before = *st.n;
+    }
+}
+
+// nearest-cation search without a field pass (used when the field is given)
+__global__ void partner_kernel(const obem_state st, GasDev g, uint32_t step, u64 *prop)
+{
+    const int n = cur_n(st);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u64 best = ~0ull;
+    if (st.species[i] == OBEM_ELECTRON) {
+        float4 pe = reinterpret_cast<const float4 *>(st.pos_q)[i];
+        for (int c = 0; c < n; ++c) {
+            if (st.species[c] != OBEM_CATION) continue;
+            uint32_t b = st.birth[c];
+            if (b != 0u && b == step) continue;
+            float4 pc = reinterpret_cast<const float4 *>(st.pos_q)[c];
+            float dx = pe.x - pc.x, dy = pe.y - pc.y, dz = pe.z - pc.z;
+            float d2 = dx * dx + dy * dy + dz * dz;
+            if (!(d2 <= g.rc2)) continue;
+            u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)c;
+            if (key < best) best = key;
+        }
+    }
+    prop[i] = best;
+}
+
+__global__ void resolve_kernel(const obem_state st, const u64 *prop, u64 *ionkey)
+{
+    const int n = cur_n(st);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u64 pr = prop[i];
+    if (pr == ~0ull || st.species[i] != OBEM_ELECTRON) return;
+    uint32_t ion = (uint32_t)(pr & 0xFFFFFFFFu);
+    u64 key = (pr & 0xFFFFFFFF00000000ull) | (u64)(uint32_t)i;
+    atomicMin(&ionkey[ion], key);
+}
+
+__device__ __forceinline__ bool recombined(int i, uint8_t s, const u64 *prop, const u64 *ionkey, int recomb_on)
+{
+    if (!recomb_on) return false;
+    if (s == OBEM_CATION) return ionkey[i] != ~0ull;
+    if (s == OBEM_ELECTRON) {
+        u64 pr = prop[i];
+        if (pr == ~0ull) return false;
+        uint32_t ion = (uint32_t)(pr & 0xFFFFFFFFu);
+        return ionkey[ion] == ((pr & 0xFFFFFFFF00000000ull) | (u64)(uint32_t)i);
+    }
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(ST_THREADS)
+count_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, const u64 *prop,
+             const u64 *ionkey, int32_t *keep, int32_t *nsp, int32_t *blk, obem_step_stats *stats,
+             StepCtl *ctl)
+{
+    __shared__ long long sh[ST_THREADS / 32];
+    const int n = cur_n(st);
+    int i = blockIdx.x * ST_THREADS + threadIdx.x;
+    int kp = 0, ns = 0, absorbed = 0, attached = 0, coll = 0, rec = 0, ovf = 0;
+    long long trials = 0;
+    if (i < n) {
+        uint8_t s = st.species[i];
+        if (recombined(i, s, prop, ionkey, g.recomb_on)) {
+            rec = (s == OBEM_CATION);
+        } else {
+            float4 pq = reinterpret_cast<const float4 *>(st.pos_q)[i];
+            float4 vv = reinterpret_cast<const float4 *>(st.vel)[i];
+            float4 e = E[i];
+            float3 p = make_float3(pq.x, pq.y, pq.z), v = make_float3(vv.x, vv.y, vv.z);
+            FlightOut fo = {0, 0, 0, 0, 0, 0};
+            fly<false>(g, st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, NULL, NULL, NULL,
+                       NULL, NULL, 0, 0u);
+            kp = !fo.dead;
+            ns = fo.nsp;
+            absorbed = fo.dead;
+            attached = fo.attached;
+            coll = fo.collisions;
+            trials = fo.trials;
+            ovf = fo.overflow;
+        }
+        keep[i] = kp;
+        nsp[i] = ns;
+    }
+    long long t;
+    t = block_sum<long long>(kp, sh);
+    if (threadIdx.x == 0) blk[2 * blockIdx.x] = (int32_t)t;
+    t = block_sum<long long>(ns, sh);
+    if (threadIdx.x == 0) blk[2 * blockIdx.x + 1] = (int32_t)t;
+    t = block_sum<long long>(absorbed, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stats->absorbed, (int)t);
+    t = block_sum<long long>(attached, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stats->attached, (int)t);
+    t = block_sum<long long>(coll, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stats->collisions, (int)t);
+    t = block_sum<long long>(rec, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stats->recombined_pairs, (int)t);
+    t = block_sum<long long>(trials, sh);
+    if (threadIdx.x == 0 && t) atomicAdd((unsigned long long *)&stats->trials, (unsigned long long)t);
+    t = block_sum<long long>(ovf, sh);
+    if (threadIdx.x == 0 && t) atomicOr(&ctl->trial_overflow, 1);
+}
+
+// single block: exclusive scan of the per-block (keep, spawn) totals
+__global__ void scan_kernel(const obem_state st, int32_t *blk, obem_step_stats *stats, StepCtl *ctl,
+                            int cap)
+{
+    __shared__ int32_t sk[1024], ss[1024];
+    __shared__ int32_t carry_k, carry_s;
+    const int n = cur_n(st);
+    const int nb = (n + ST_THREADS - 1) / ST_THREADS;
+    if (threadIdx.x == 0) { carry_k = 0; carry_s = 0; }
+    __syncthreads();
+    for (int c0 = 0; c0 < nb; c0 += 1024) {
+        int b = c0 + threadIdx.x;
+        int vk = b < nb ? blk[2 * b] : 0;
+        int vs = b < nb ? blk[2 * b + 1] : 0;
+        sk[threadIdx.x] = vk;
+        ss[threadIdx.x] = vs;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int ak = threadIdx.x >= off ? sk[threadIdx.x - off] : 0;
+            int as = threadIdx.x >= off ? ss[threadIdx.x - off] : 0;
+            __syncthreads();
+            sk[threadIdx.x] += ak;
+            ss[threadIdx.x] += as;
+            __syncthreads();
+        }
+        if (b < nb) {
+            blk[2 * b] = carry_k + sk[threadIdx.x] - vk;      // exclusive
+            blk[2 * b + 1] = carry_s + ss[threadIdx.x] - vs;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) { carry_k += sk[1023]; carry_s += ss[1023]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int nk = carry_k, nsp = carry_s;
+        long long total = (long long)nk + 2ll * nsp;
+        ctl->n_keep = nk;
+        ctl->n_spawn = nsp;
+        stats->spawned_pairs = nsp;
+        stats->required_capacity = total > 0x7fffffff ? 0x7fffffff : (int)total;
+        if (ctl->trial_overflow) {
+            ctl->abort = 1;
+            stats->status = OBEM_ERR_TRIALS;
+        } else if (total > cap) {
+            ctl->abort = 1;
+            stats->status = OBEM_ERR_CAPACITY;
+        }
+        stats->n_after = ctl->abort ? n : (int)total;
+    }
+}
+
+__global__ void __launch_bounds__(ST_THREADS)
+write_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, const u64 *prop,
+             const u64 *ionkey, const int32_t *keep, const int32_t *nsp, const int32_t *blk,
+             const StepCtl *ctl, float4 *o_pos, float4 *o_vel, uint32_t *o_id, uint32_t *o_birth,
+             uint8_t *o_sp)
+{
+    __shared__ int32_t wk[ST_THREADS / 32], ws[ST_THREADS / 32];
+    if (ctl->abort) return;
+    const int n = cur_n(st);
+    int i = blockIdx.x * ST_THREADS + threadIdx.x;
+    int kp = 0, ns = 0;
+    if (i < n) { kp = keep[i]; ns = nsp[i]; }
+    // block-local exclusive scan
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int ik = kp, is = ns;
+    for (int o = 1; o < 32; o <<= 1) {
+        int a = __shfl_up_sync(0xffffffffu, ik, o);
+        int b = __shfl_up_sync(0xffffffffu, is, o);
+        if (lane >= o) { ik += a; is += b; }
+    }
+    if (lane == 31) { wk[warp] = ik; ws[warp] = is; }
+    __syncthreads();
+    int pk_ = 0, ps_ = 0;
+    for (int w = 0; w < warp; ++w) { pk_ += wk[w]; ps_ += ws[w]; }
+    const int out_keep = blk[2 * blockIdx.x] + pk_ + ik - kp;
+    const int out_spawn = blk[2 * blockIdx.x + 1] + ps_ + is - ns;
+    if (i >= n || (!kp && !ns)) return;
+    uint8_t s = st.species[i];
+    float4 pq = reinterpret_cast<const float4 *>(st.pos_q)[i];
+    float4 vv = reinterpret_cast<const float4 *>(st.vel)[i];
+    float4 e = E[i];
+    float3 p = make_float3(pq.x, pq.y, pq.z), v = make_float3(vv.x, vv.y, vv.z);
+    FlightOut fo = {0, 0, 0, 0, 0, 0};
+    const int sbase = ctl->n_keep + 2 * out_spawn;
+    const uint32_t id_base = *st.next_id + (uint32_t)(2 * out_spawn);
+    fly<true>(g, st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, o_pos, o_vel, o_id, o_birth,
+              o_sp, sbase, id_base);
+    if (kp) {
+        o_pos[out_keep] = make_float4(p.x, p.y, p.z, pq.w);
+        o_vel[out_keep] = make_float4(v.x, v.y, v.z, vv.w);
+        o_id[out_keep] = st.id[i];
+        o_birth[out_keep] = st.birth[i];
+        o_sp[out_keep] = s;
+    }
+}
+
+__global__ void commit_kernel(const obem_state st, const StepCtl *ctl, const float4 *o_pos,
+                              const float4 *o_vel, const uint32_t *o_id, const uint32_t *o_birth,
+                              const uint8_t *o_sp)
+{
+    if (ctl->abort) return;
+    const int m = ctl->n_keep + 2 * ctl->n_spawn;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        reinterpret_cast<float4 *>(st.pos_q)[i] = o_pos[i];
+        reinterpret_cast<float4 *>(st.vel)[i] = o_vel[i];
+        st.id[i] = o_id[i];
+        st.birth[i] = o_birth[i];
+        st.species[i] = o_sp[i];
+    }
+}
+
+__global__ void finish_kernel(const obem_state st, const StepCtl *ctl)
+{
+    if (threadIdx.x != 0 || ctl->abort) return;
+    *st.n = ctl->n_keep + 2 * ctl->n_spawn;
+    *st.next_id = *st.next_id + (uint32_t)(2 * ctl->n_spawn);
+}
+
+__global__ void __launch_bounds__(ST_THREADS)
+moments_kernel(const obem_state st, obem_step_stats *stats)
+{
+    __shared__ double shd[ST_THREADS / 32];
+    __shared__ long long shl[ST_THREADS / 32];
+    const int n = cur_n(st);
+    int i = blockIdx.x * ST_THREADS + threadIdx.x;
+    int ne = 0, nc = 0, na = 0;
+    double se[3] = {0, 0, 0}, s2e[3] = {0, 0, 0}, si[3] = {0, 0, 0}, s2i[3] = {0, 0, 0}, en = 0.0;
+    if (i < n) {
+        uint8_t s = st.species[i];
+        float4 p = reinterpret_cast<const float4 *>(st.pos_q)[i];
+        double x[3] = {p.x, p.y, p.z};
+        if (s == OBEM_ELECTRON) {
+            ne = 1;
+            for (int c = 0; c < 3; ++c) { se[c] = x[c]; s2e[c] = x[c] * x[c]; }
+            float4 v = reinterpret_cast<const float4 *>(st.vel)[i];
+            double v2 = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
+            en = 0.5 * OBEM_ME * v2 / OBEM_QE;
+        } else {
+            if (s == OBEM_CATION) nc = 1; else na = 1;
+            for (int c = 0; c < 3; ++c) { si[c] = x[c]; s2i[c] = x[c] * x[c]; }
+        }
+    }
+    long long t;
+    t = block_sum<long long>(ne, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_electron, (int)t);
+    t = block_sum<long long>(nc, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_cation, (int)t);
+    t = block_sum<long long>(na, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_anion, (int)t);
+    double d;
+    for (int c = 0; c < 3; ++c) {
+        d = block_sum<double>(se[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum_e[c], d);
+        d = block_sum<double>(s2e[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum2_e[c], d);
+        d = block_sum<double>(si[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum_i[c], d);
+        d = block_sum<double>(s2i[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum2_i[c], d);
+    }
+    d = block_sum<double>(en, shd); if (threadIdx.x == 0) atomicAdd(&stats->sum_energy_e, d);
+}
+
+int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32_t step,
+                     obem_step_stats *stats, cudaStream_t s, int partners_done)
+{
+    const obem_state st = *stp;
+    const int cap = st.capacity;
+    const int nblk = (cap + ST_THREADS - 1) / ST_THREADS;
+    GasDev g = c->gas;
+    init_kernel<<<1, 32, 0, s>>>(stats, c->s_ctl, st);
+    OBEM_LAUNCH(c);
+    if (g.recomb_on) {
+        if (!partners_done) {
+            partner_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, step, c->s_prop);
+            OBEM_LAUNCH(c);
+        }
+        OBEM_CUDA(c, cudaMemsetAsync(c->s_ionkey, 0xFF, sizeof(u64) * (size_t)cap, s));
+        resolve_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_prop, c->s_ionkey);
+        OBEM_LAUNCH(c);
+    }
+    count_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, E, step, c->s_prop, c->s_ionkey, c->s_keep,
+                                             c->s_nsp, c->s_blk, stats, c->s_ctl);
+    OBEM_LAUNCH(c);
+    scan_kernel<<<1, 1024, 0, s>>>(st, c->s_blk, stats, c->s_ctl, cap < c->cap ? cap : c->cap);
+    OBEM_LAUNCH(c);
+    write_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, E, step, c->s_prop, c->s_ionkey, c->s_keep,
+                                             c->s_nsp, c->s_blk, c->s_ctl, c->o_pos, c->o_vel,
+                                             c->o_id, c->o_birth, c->o_sp);
+    OBEM_LAUNCH(c);
+    commit_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_ctl, c->o_pos, c->o_vel, c->o_id, c->o_birth,
+                                              c->o_sp);
+    OBEM_LAUNCH(c);
+    finish_kernel<<<1, 32, 0, s>>>(st, c->s_ctl);
+    OBEM_LAUNCH(c);
+    moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats);
+    OBEM_LAUNCH(c);
+    if (c->prof_on) c->launches += 8 + (g.recomb_on ? (partners_done ? 1 : 2) : 0);
+    return OBEM_OK;
+}

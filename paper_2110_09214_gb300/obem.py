@@ -1,0 +1,274 @@
+"""Python binding of the libobem C ABI (include/obem.h).
+
+Argument marshalling only: every function below calls the entry point of the
+same name in libobem.so with raw pointers taken from torch CUDA tensors (PyTorch
+is used for device memory and streams).  There is no fallback: if the CUDA
+library cannot be built or loaded, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OBEM_OK = 0
+OBEM_ERR_ARG, OBEM_ERR_CUDA, OBEM_ERR_STATE, OBEM_ERR_SINGULAR = -1, -2, -3, -4
+OBEM_ERR_NOT_CONVERGED, OBEM_ERR_CAPACITY, OBEM_ERR_TIMEOUT, OBEM_ERR_TRIALS = -5, -6, -7, -8
+OBEM_LU_FP32, OBEM_LU_TF32, OBEM_LU_BF16, OBEM_LU_BF16X9 = 0, 1, 2, 3
+OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD = 1, 2
+
+
+class ObemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("obem error %d: %s" % (code, msg))
+        self.code = code
+
+
+class obem_config(C.Structure):
+    _fields_ = [("capacity", C.c_int32), ("trial_cap", C.c_int32), ("flags", C.c_int32),
+                ("reserved", C.c_int32), ("dt", C.c_double), ("seed", C.c_uint64),
+                ("softening", C.c_double), ("z_lo", C.c_double), ("z_hi", C.c_double),
+                ("beta", C.c_double), ("e_ext", C.c_double * 3)]
+
+
+class obem_gas(C.Structure):
+    _fields_ = [("n_proc", C.c_int32), ("n_energy", C.c_int32), ("energy_eV", C.c_void_p),
+                ("sigma_m2", C.c_void_p), ("kind", C.c_void_p), ("mode", C.c_void_p),
+                ("threshold_eV", C.c_void_p), ("nu_const", C.c_void_p), ("T", C.c_double),
+                ("N", C.c_double), ("M_amu", C.c_double), ("nu_ion", C.c_double)]
+
+
+class obem_state(C.Structure):
+    _fields_ = [("pos_q", C.c_void_p), ("vel", C.c_void_p), ("id", C.c_void_p),
+                ("birth", C.c_void_p), ("species", C.c_void_p), ("n", C.c_void_p),
+                ("next_id", C.c_void_p), ("capacity", C.c_int32)]
+
+
+class obem_step_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_before", C.c_int32), ("n_after", C.c_int32),
+                ("required_capacity", C.c_int32), ("n_electron", C.c_int32),
+                ("n_cation", C.c_int32), ("n_anion", C.c_int32), ("spawned_pairs", C.c_int32),
+                ("absorbed", C.c_int32), ("attached", C.c_int32), ("recombined_pairs", C.c_int32),
+                ("collisions", C.c_int32), ("trials", C.c_int64), ("sum_e", C.c_double * 3),
+                ("sum2_e", C.c_double * 3), ("sum_i", C.c_double * 3), ("sum2_i", C.c_double * 3),
+                ("sum_energy_e", C.c_double)]
+
+
+class obem_solve_report(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("backward_error", C.c_double),
+                ("factor_ms", C.c_double), ("solve_ms", C.c_double)]
+
+
+STATS_BYTES = C.sizeof(obem_step_stats)
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load libobem.so, building it with nvcc first if the sources changed."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = C.CDLL(path)
+    P, I, U = C.c_void_p, C.c_int32, C.c_uint32
+    lib.obem_create.argtypes = [C.POINTER(P), C.POINTER(obem_config)]
+    lib.obem_destroy.argtypes = [P]
+    lib.obem_destroy.restype = None
+    lib.obem_last_error.argtypes = [P]
+    lib.obem_last_error.restype = C.c_char_p
+    lib.obem_gas_load.argtypes = [P, C.POINTER(obem_gas)]
+    lib.obem_mesh_load.argtypes = [P, I, P, P, P, P, P, I]
+    lib.obem_bem_assemble.argtypes = [P, I, P]
+    lib.obem_bem_solve.argtypes = [P, P, P, P, P, C.POINTER(obem_solve_report), P]
+    lib.obem_field_eval.argtypes = [P, P, I, P, I, I, P, P, P]
+    lib.obem_step.argtypes = [P, C.POINTER(obem_state), P, U, P, P]
+    lib.obem_profile.argtypes = [P, I]
+    lib.obem_stage_times.argtypes = [P, P, P]
+    for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
+              "obem_bem_solve", "obem_field_eval", "obem_step", "obem_profile",
+              "obem_stage_times"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(ctx, rc):
+    if rc != OBEM_OK:
+        msg = load().obem_last_error(ctx).decode() if ctx else "invalid argument"
+        raise ObemError(rc, msg)
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ---------------------------------------------------------------- entry points
+def obem_create(capacity, dt, seed=1, softening=0.0, z_lo=-1.0, z_hi=1.0, beta=-1.0,
+                trial_cap=256, flags=OBEM_STEP_SPACE_CHARGE | OBEM_STEP_CELL_FIELD,
+                e_ext=(0.0, 0.0, 0.0)):
+    cfg = obem_config(capacity=int(capacity), trial_cap=int(trial_cap), flags=int(flags),
+                      reserved=0, dt=float(dt), seed=int(seed), softening=float(softening),
+                      z_lo=float(z_lo), z_hi=float(z_hi), beta=float(beta),
+                      e_ext=(C.c_double * 3)(*[float(x) for x in e_ext]))
+    ctx = C.c_void_p()
+    rc = load().obem_create(C.byref(ctx), C.byref(cfg))
+    if rc != OBEM_OK:
+        raise ObemError(rc, "obem_create rejected the configuration")
+    return ctx
+
+
+def obem_destroy(ctx):
+    if ctx:
+        load().obem_destroy(ctx)
+
+
+def obem_last_error(ctx):
+    return load().obem_last_error(ctx).decode()
+
+
+def obem_gas_load(ctx, gas):
+    eg = _host(gas.egrid, np.float32)
+    xs = _host(gas.xs, np.float32)
+    kind = _host(gas.kind, np.int32)
+    mode = _host(gas.mode, np.int32)
+    thr = _host(gas.thr, np.float32)
+    nuc = _host(gas.nuc, np.float32)
+    g = obem_gas(n_proc=len(kind), n_energy=len(eg), energy_eV=eg.ctypes.data,
+                 sigma_m2=xs.ctypes.data, kind=kind.ctypes.data, mode=mode.ctypes.data,
+                 threshold_eV=thr.ctypes.data, nu_const=nuc.ctypes.data, T=float(gas.T),
+                 N=float(gas.N), M_amu=float(gas.M_amu), nu_ion=float(gas.nu_ion))
+    _check(ctx, load().obem_gas_load(ctx, C.byref(g)))
+
+
+def obem_mesh_load(ctx, mesh):
+    tri = _host(mesh.tri, np.float64)
+    kind = _host(mesh.kind, np.int32)
+    group = _host(mesh.group, np.int32)
+    em = _host(mesh.eps_minus, np.float64)
+    ep = _host(mesh.eps_plus, np.float64)
+    _check(ctx, load().obem_mesh_load(ctx, mesh.n, tri.ctypes.data, kind.ctypes.data,
+                                      group.ctypes.data, em.ctypes.data, ep.ctypes.data,
+                                      mesh.n_groups))
+
+
+def obem_bem_assemble(ctx, precision=OBEM_LU_FP32, stream=None):
+    _check(ctx, load().obem_bem_assemble(ctx, int(precision), _stream(stream)))
+
+
+def obem_bem_solve(ctx, group_voltage, sigma_out, sigma_free=None, drhs=None, stream=None,
+                   check=True):
+    gv = _host(group_voltage, np.float64)
+    rep = obem_solve_report()
+    rc = load().obem_bem_solve(ctx, gv.ctypes.data if len(gv) else None, _ptr(sigma_free),
+                               _ptr(drhs), _ptr(sigma_out), C.byref(rep), _stream(stream))
+    if check:
+        _check(ctx, rc)
+    return {"iterations": rep.iterations, "status": rep.status,
+            "backward_error": rep.backward_error, "factor_ms": rep.factor_ms,
+            "solve_ms": rep.solve_ms, "rc": rc}
+
+
+def obem_field_eval(ctx, targets, E_out, sources=None, self_exclude=False, sigma=None,
+                    stream=None):
+    nt = targets.shape[0]
+    ns = sources.shape[0] if sources is not None else 0
+    _check(ctx, load().obem_field_eval(ctx, _ptr(targets), nt, _ptr(sources), ns,
+                                       int(bool(self_exclude)), _ptr(sigma), _ptr(E_out),
+                                       _stream(stream)))
+
+
+def obem_step(ctx, state, step, stats, E_in=None, stream=None):
+    _check(ctx, load().obem_step(ctx, C.byref(state.c_struct()), _ptr(E_in), int(step),
+                                 _ptr(stats), _stream(stream)))
+
+
+def obem_profile(ctx, enable=True):
+    _check(ctx, load().obem_profile(ctx, int(bool(enable))))
+
+
+def obem_stage_times(ctx):
+    """Stage times (ms, summed over the recorded steps) and counters."""
+    ms = np.zeros(4, np.float64)
+    cnt = np.zeros(7, np.int64)
+    _check(ctx, load().obem_stage_times(ctx, ms.ctypes.data, cnt.ctypes.data))
+    return {"cell_ms": ms[0], "pairs_ms": ms[1], "step_ms": ms[2], "total_ms": ms[3],
+            "steps": int(cnt[0]), "launches": int(cnt[1]), "charge_pairs": int(cnt[2]),
+            "cells_1pt": int(cnt[3]), "cells_3pt": int(cnt[4]), "cells_7pt": int(cnt[5]),
+            "cells_closed": int(cnt[6])}
+
+
+# ---------------------------------------------------------------- device state
+class DeviceState:
+    """Charge arrays in device memory (torch tensors) in the layout of
+    obem_state, plus the device scalars n and next_id."""
+
+    def __init__(self, capacity, device="cuda"):
+        import torch
+        self.capacity = int(capacity)
+        self.pos_q = torch.zeros((capacity, 4), dtype=torch.float32, device=device)
+        self.vel = torch.zeros((capacity, 4), dtype=torch.float32, device=device)
+        self.id = torch.zeros(capacity, dtype=torch.int32, device=device)
+        self.birth = torch.zeros(capacity, dtype=torch.int32, device=device)
+        self.species = torch.zeros(capacity, dtype=torch.uint8, device=device)
+        self.scalars = torch.zeros(2, dtype=torch.int32, device=device)   # n, next_id
+
+    def c_struct(self):
+        return obem_state(pos_q=self.pos_q.data_ptr(), vel=self.vel.data_ptr(),
+                          id=self.id.data_ptr(), birth=self.birth.data_ptr(),
+                          species=self.species.data_ptr(), n=self.scalars.data_ptr(),
+                          next_id=self.scalars.data_ptr() + 4, capacity=self.capacity)
+
+    def upload(self, ch, next_id=None):
+        import torch
+        n = ch.pos_q.shape[0]
+        if n > self.capacity:
+            raise ValueError("state of %d charges exceeds capacity %d" % (n, self.capacity))
+        self.pos_q[:n].copy_(torch.from_numpy(np.ascontiguousarray(ch.pos_q, np.float32)))
+        self.vel[:n].copy_(torch.from_numpy(np.ascontiguousarray(ch.vel, np.float32)))
+        self.id[:n].copy_(torch.from_numpy(np.ascontiguousarray(ch.id).view(np.int32)))
+        self.birth[:n].copy_(torch.from_numpy(np.ascontiguousarray(ch.birth).view(np.int32)))
+        self.species[:n].copy_(torch.from_numpy(np.ascontiguousarray(ch.species, np.uint8)))
+        nid = n if next_id is None else int(next_id)
+        self.scalars.copy_(torch.tensor([n, np.uint32(nid).view(np.int32)], dtype=torch.int32))
+
+    def download(self):
+        from types import SimpleNamespace
+        sc = self.scalars.cpu().numpy()
+        n = int(sc[0])
+        return SimpleNamespace(
+            pos_q=self.pos_q[:n].cpu().numpy(), vel=self.vel[:n].cpu().numpy(),
+            id=self.id[:n].cpu().numpy().view(np.uint32), birth=self.birth[:n].cpu().numpy().view(np.uint32),
+            species=self.species[:n].cpu().numpy(), n=n), int(sc[1].view(np.uint32))
+
+
+def new_stats(device="cuda"):
+    import torch
+    return torch.zeros(STATS_BYTES, dtype=torch.uint8, device=device)
+
+
+def read_stats(stats):
+    raw = stats.cpu().numpy().tobytes()
+    s = obem_step_stats.from_buffer_copy(raw)
+    out = {f: getattr(s, f) for f, _ in obem_step_stats._fields_}
+    for k in ("sum_e", "sum2_e", "sum_i", "sum2_i"):
+        out[k] = list(out[k])
+    return out

@@ -1,0 +1,182 @@
+"""obem_field_eval (CUDA, through the C ABI) against the FP64 oracle:
+Eq. (nbody) for charges, Eqs. (BEM2)/(BEM3) for cells.  Tolerance: 1e-5 of
+max(|E_ref|, 1e-2 rms|E_ref|) per point."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_09214_gb300 import inputs, obem
+from gpu_util import FIELD_TOL, guarded_rel_err, pts4, to_dev
+
+pytestmark = pytest.mark.gpu
+E = 1.602176634e-19
+
+
+def _ctx(cap=16):
+    return obem.obem_create(capacity=cap, dt=1e-12)
+
+
+def _charges(rng, n, box=1e-3, pairs=0):
+    p = rng.uniform(0, box, (n, 3))
+    if pairs:
+        k = min(pairs, n // 2)
+        p[n - k:] = p[:k] + rng.normal(0, 1e-8, (k, 3))
+    q = rng.choice([-E, E], n)
+    return np.column_stack([p, q]).astype(np.float32)
+
+
+def _gpu_field(ctx, tgt, src=None, self_exclude=False, sigma=None):
+    t = to_dev(pts4(tgt))
+    s = to_dev(src) if src is not None else None
+    sg = to_dev(np.asarray(sigma, np.float32)) if sigma is not None else None
+    out = torch.empty((len(tgt), 4), dtype=torch.float32, device="cuda")
+    obem.obem_field_eval(ctx, t, out, sources=s, self_exclude=self_exclude, sigma=sg)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 511, 512, 513, 1000, 3001])
+def test_nbody_self_exclude(n):
+    rng = np.random.default_rng(n)
+    src = _charges(rng, n, pairs=n // 10)
+    ctx = _ctx()
+    try:
+        got = _gpu_field(ctx, src, src, self_exclude=True)
+    finally:
+        obem.obem_destroy(ctx)
+    Eref, Vref = oracle.nbody_field(src[:, :3].astype(np.float64), src.astype(np.float64), True)
+    if n == 1:
+        assert np.all(got == 0.0)
+        return
+    assert guarded_rel_err(got[:, :3], Eref) <= FIELD_TOL
+    assert guarded_rel_err(got[:, 3], Vref) <= FIELD_TOL
+
+
+@pytest.mark.parametrize("nt,ns", [(700, 1500), (1, 300), (1025, 257)])
+def test_nbody_separate_targets(nt, ns):
+    rng = np.random.default_rng(nt + ns)
+    src = _charges(rng, ns)
+    tgt = rng.uniform(-2e-4, 1.2e-3, (nt, 3)).astype(np.float32)
+    ctx = _ctx()
+    try:
+        got = _gpu_field(ctx, tgt, src)
+    finally:
+        obem.obem_destroy(ctx)
+    Eref, Vref = oracle.nbody_field(tgt.astype(np.float64), src.astype(np.float64))
+    assert guarded_rel_err(got[:, :3], Eref) <= FIELD_TOL
+    assert guarded_rel_err(got[:, 3], Vref) <= FIELD_TOL
+
+
+def _plate_targets(rng):
+    inner = rng.uniform([0, 0, 0], [1e-2, 1e-2, 1e-3], (600, 3))
+    near = np.column_stack([rng.uniform(0, 1e-2, (200, 2)), rng.choice([1e-6, 3e-5, 9.99e-4], 200)])
+    far = np.array([[5e-3, 5e-3, 5e-2], [0.3, -0.2, 0.4], [5e-3, 5e-3, -1.5e-3], [2e-2, 5e-3, 5e-4]])
+    return np.concatenate([inner, near, far]).astype(np.float32)
+
+
+def test_cells_parallel_plates_all_tiers():
+    rng = np.random.default_rng(7)
+    mesh = inputs.parallel_plates(1e-2, 1e-3, 16, 0.0, 100.0)
+    sigma = oracle.bem_solve(mesh).astype(np.float32)
+    tgt = _plate_targets(rng)
+    ctx = _ctx()
+    try:
+        obem.obem_mesh_load(ctx, mesh)
+        cnt = None
+        got = _gpu_field(ctx, tgt, sigma=sigma)
+    finally:
+        obem.obem_destroy(ctx)
+    Eref, Vref = oracle.panel_field(mesh.tri, sigma.astype(np.float64), tgt.astype(np.float64))
+    assert guarded_rel_err(got[:, :3], Eref) <= FIELD_TOL
+    assert guarded_rel_err(got[:, 3], Vref) <= FIELD_TOL
+
+
+def test_cells_gem_patch_smooth_density():
+    """Small GEM patch (7 holes), dielectric and electrode cells with a smooth
+    non-physical density, targets in Gaussian clouds on the hole axes."""
+    g = inputs.GemGeometry(rings=1)
+    mesh = inputs.gem_mesh(g, n_theta=24, n_r=3, n_zc=1, n_zk=6, n_plane=10)
+    cen = mesh.tri.mean(axis=1)
+    sigma = (1e-6 * (1.0 + 0.5 * np.sin(cen[:, 0] / 1e-4) * np.cos(cen[:, 2] / 3e-5))
+             * np.where(mesh.group % 2 == 0, 1.0, -1.0)).astype(np.float32)
+    rng = np.random.default_rng(3)
+    hc = g.hole_centres()
+    h = rng.integers(0, len(hc), 3000)
+    p = np.column_stack([hc[h], np.zeros(3000)]) + rng.normal(0, 20e-6, (3000, 3))
+    p = p[~inputs.gem_inside_solid(g, p)][:1500].astype(np.float32)
+    ctx = _ctx()
+    try:
+        obem.obem_mesh_load(ctx, mesh)
+        got = _gpu_field(ctx, p, sigma=sigma)
+    finally:
+        obem.obem_destroy(ctx)
+    Eref, Vref = oracle.panel_field(mesh.tri, sigma.astype(np.float64), p.astype(np.float64))
+    assert guarded_rel_err(got[:, :3], Eref) <= FIELD_TOL
+    assert guarded_rel_err(got[:, 3], Vref) <= FIELD_TOL
+
+
+def test_cells_plus_charges_combined():
+    rng = np.random.default_rng(11)
+    mesh = inputs.parallel_plates(1e-2, 1e-3, 16, 0.0, 100.0)
+    sigma = oracle.bem_solve(mesh).astype(np.float32)
+    src = _charges(rng, 2000, box=1e-3)
+    src[:, 2] *= 0.99
+    ctx = _ctx()
+    try:
+        obem.obem_mesh_load(ctx, mesh)
+        got = _gpu_field(ctx, src, src, self_exclude=True, sigma=sigma)
+    finally:
+        obem.obem_destroy(ctx)
+    pts = src[:, :3].astype(np.float64)
+    E1, V1 = oracle.panel_field(mesh.tri, sigma.astype(np.float64), pts)
+    E2, V2 = oracle.nbody_field(pts, src.astype(np.float64), True)
+    assert guarded_rel_err(got[:, :3], E1 + E2) <= FIELD_TOL
+    assert guarded_rel_err(got[:, 3], V1 + V2) <= FIELD_TOL
+
+
+def test_empty_and_bad_arguments():
+    ctx = _ctx()
+    try:
+        out = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+        obem.obem_field_eval(ctx, torch.empty((0, 4), device="cuda"), out)
+        t = torch.zeros((4, 4), device="cuda")
+        with pytest.raises(obem.ObemError) as e:
+            obem.obem_field_eval(ctx, t, torch.empty((4, 4), device="cuda"),
+                                 sources=torch.zeros((3, 4), device="cuda"), self_exclude=True)
+        assert e.value.code == obem.OBEM_ERR_ARG
+        with pytest.raises(obem.ObemError) as e:
+            obem.obem_field_eval(ctx, t, torch.empty((4, 4), device="cuda"),
+                                 sigma=torch.zeros(10, device="cuda"))
+        assert e.value.code == obem.OBEM_ERR_STATE
+    finally:
+        obem.obem_destroy(ctx)
+
+
+def test_full_size_gem_sampled():
+    """The headline workload at full size -- 60k cells, 1e6 charges -- in the
+    launch configuration of the bench; the oracle computes 64 sampled
+    targets one by one."""
+    mesh, gas, ch, trk, g = inputs.config_gem(seed=1, n=1_000_000)
+    cen = mesh.tri.mean(axis=1)
+    sigma = (1e-6 * (1.0 + 0.3 * np.sin(cen[:, 0] / 1e-4)) *
+             np.where(mesh.kind == 0, np.where(mesh.group % 2 == 0, 1.0, -1.0), 0.3)).astype(np.float32)
+    ctx = _ctx()
+    try:
+        obem.obem_mesh_load(ctx, mesh)
+        got = _gpu_field(ctx, ch.pos_q, ch.pos_q, self_exclude=True, sigma=sigma)
+    finally:
+        obem.obem_destroy(ctx)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(ch.n, 64, replace=False))
+    pts = ch.pos_q[idx, :3].astype(np.float64)
+    E1, V1 = oracle.panel_field(mesh.tri, sigma.astype(np.float64), pts)
+    src = ch.pos_q.astype(np.float64)
+    E2 = np.zeros_like(E1)
+    V2 = np.zeros(len(idx))
+    for k, i in enumerate(idx):
+        s = np.delete(src, i, axis=0)
+        e, v = oracle.nbody_field(pts[k:k + 1], s)
+        E2[k], V2[k] = e[0], v[0]
+    assert np.all(np.isfinite(got))
+    assert guarded_rel_err(got[idx, :3], E1 + E2) <= FIELD_TOL
