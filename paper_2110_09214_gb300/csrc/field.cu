@@ -165,24 +165,150 @@ struct __align__(16) SrcPk {
     u64 xx, yy, zz, qq;
 };
 
+// ---------------------------------------------------------------- target binning
+// Targets are visited by the cell kernel in the Morton order of a 64^3 grid
+// over the cell bounding box (points outside are clamped to the border
+// bins), so the 32 targets of a warp are neighbours and mostly take the same
+// distance tier for a given cell.  Counting sort: histogram, scan, scatter;
+// the order inside a bin is arbitrary, which does not change any result (each
+// target's sum runs over the cells in the same order whatever its slot).
+__device__ __forceinline__ uint32_t spread3(uint32_t x)
+{
+    x &= 0x3Fu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void bin_count_kernel(FieldLaunch L, float3 lo, float3 scale, uint32_t *code, int32_t *hist)
+{
+    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    float4 p = L.targets[i];
+    int ix = (int)fminf(fmaxf((p.x - lo.x) * scale.x, 0.f), (float)(OBEM_BINS_PER_AXIS - 1));
+    int iy = (int)fminf(fmaxf((p.y - lo.y) * scale.y, 0.f), (float)(OBEM_BINS_PER_AXIS - 1));
+    int iz = (int)fminf(fmaxf((p.z - lo.z) * scale.z, 0.f), (float)(OBEM_BINS_PER_AXIS - 1));
+    uint32_t c = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+    code[i] = c;
+    atomicAdd(&hist[c], 1);
+}
+
+// exclusive scan of OBEM_NBINS counts in place, one block of 1024 threads
+__global__ void bin_scan_kernel(int32_t *hist)
+{
+    __shared__ int32_t part[1024];
+    const int per = OBEM_NBINS / 1024;
+    int32_t *h = hist + threadIdx.x * per;
+    int32_t s = 0;
+    for (int k = 0; k < per; ++k) s += h[k];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - s;
+    for (int k = 0; k < per; ++k) {
+        int32_t c = h[k];
+        h[k] = run;
+        run += c;
+    }
+}
+
+__global__ void bin_scatter_kernel(FieldLaunch L, const uint32_t *code, int32_t *hist, int32_t *perm)
+{
+    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int pos = atomicAdd(&hist[code[i]], 1);
+    perm[pos] = i;
+}
+
 // ---------------------------------------------------------------- cell field kernel
-// E_out[i] = e_ext + k_C sum_j sigma_j F_j(r_i)  (w: potential)
-template <bool COUNT>
-__global__ void __launch_bounds__(FT_THREADS)
+#define CT_THREADS 128
+#define CT_TPT 2
+#define CT_BLOCK (CT_THREADS * CT_TPT)
+
+#define TIER_28PT_H2 4.0f     // 2h <= d < 3h: 7-point rule on the 4 midpoint sub-triangles
+
+// 7-point rule over the triangle with centroid (cx,cy,cz) and vertex offsets g*
+__device__ __forceinline__ void rule7(float tx, float ty, float tz, float cx, float cy, float cz,
+                                      float g0x, float g0y, float g0z, float g1x, float g1y, float g1z,
+                                      float g2x, float g2y, float g2z, float q, float *P)
+{
+    const float w1 = q * D7_W1, w2 = q * D7_W2;
+    qpoint(tx, ty, tz, cx, cy, cz, q * D7_W0, P[0], P[1], P[2], P[3]);
+    qpoint(tx, ty, tz, fmaf(D7_T1, g0x, cx), fmaf(D7_T1, g0y, cy), fmaf(D7_T1, g0z, cz), w1, P[0], P[1], P[2], P[3]);
+    qpoint(tx, ty, tz, fmaf(D7_T1, g1x, cx), fmaf(D7_T1, g1y, cy), fmaf(D7_T1, g1z, cz), w1, P[0], P[1], P[2], P[3]);
+    qpoint(tx, ty, tz, fmaf(D7_T1, g2x, cx), fmaf(D7_T1, g2y, cy), fmaf(D7_T1, g2z, cz), w1, P[0], P[1], P[2], P[3]);
+    qpoint(tx, ty, tz, fmaf(D7_T2, g0x, cx), fmaf(D7_T2, g0y, cy), fmaf(D7_T2, g0z, cz), w2, P[0], P[1], P[2], P[3]);
+    qpoint(tx, ty, tz, fmaf(D7_T2, g1x, cx), fmaf(D7_T2, g1y, cy), fmaf(D7_T2, g1z, cz), w2, P[0], P[1], P[2], P[3]);
+    qpoint(tx, ty, tz, fmaf(D7_T2, g2x, cx), fmaf(D7_T2, g2y, cy), fmaf(D7_T2, g2z, cz), w2, P[0], P[1], P[2], P[3]);
+}
+
+// 7-point rule on each of the 4 midpoint sub-triangles (offsets from c)
+__device__ __noinline__ void rule28(float tx, float ty, float tz, float4 cq, float4 g0, float4 g1, float4 g2,
+                                    float *P)
+{
+    const float q = 0.25f * cq.w;
+    const float m01x = 0.5f * (g0.x + g1.x), m01y = 0.5f * (g0.y + g1.y), m01z = 0.5f * (g0.z + g1.z);
+    const float m12x = 0.5f * (g1.x + g2.x), m12y = 0.5f * (g1.y + g2.y), m12z = 0.5f * (g1.z + g2.z);
+    const float m20x = 0.5f * (g2.x + g0.x), m20y = 0.5f * (g2.y + g0.y), m20z = 0.5f * (g2.z + g0.z);
+    // middle sub-triangle: centroid c, offsets m01, m12, m20
+    rule7(tx, ty, tz, cq.x, cq.y, cq.z, m01x, m01y, m01z, m12x, m12y, m12z, m20x, m20y, m20z, q, P);
+    // corner sub-triangles (v_k, m_k,k+1, m_k,k-1)
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        float ax = k == 0 ? g0.x : (k == 1 ? g1.x : g2.x), ay = k == 0 ? g0.y : (k == 1 ? g1.y : g2.y),
+              az = k == 0 ? g0.z : (k == 1 ? g1.z : g2.z);
+        float bx = k == 0 ? m01x : (k == 1 ? m12x : m20x), by = k == 0 ? m01y : (k == 1 ? m12y : m20y),
+              bz = k == 0 ? m01z : (k == 1 ? m12z : m20z);
+        float ex = k == 0 ? m20x : (k == 1 ? m01x : m12x), ey = k == 0 ? m20y : (k == 1 ? m01y : m12y),
+              ez = k == 0 ? m20z : (k == 1 ? m01z : m12z);
+        float sx = (ax + bx + ex) * (1.0f / 3.0f), sy = (ay + by + ey) * (1.0f / 3.0f), sz = (az + bz + ez) * (1.0f / 3.0f);
+        rule7(tx, ty, tz, cq.x + sx, cq.y + sy, cq.z + sz, ax - sx, ay - sy, az - sz, bx - sx, by - sy, bz - sz,
+              ex - sx, ey - sy, ez - sz, q, P);
+    }
+}
+
+// FP64 closed form of one cell, added to the FP32 partial
+__device__ __noinline__ void closed_into(const double *v, float tx, float ty, float tz, float sg, float *P)
+{
+    double phi, Fx, Fy, Fz;
+    tri_closed_form(v, (double)tx, (double)ty, (double)tz, phi, Fx, Fy, Fz);
+    const double kq = OBEM_KC * (double)sg;
+    P[0] += (float)(kq * Fx);
+    P[1] += (float)(kq * Fy);
+    P[2] += (float)(kq * Fz);
+    P[3] += (float)(kq * phi);
+}
+
+// E_out[i] = e_ext + k_C sum_j sigma_j F_j(r_i)  (w: potential if WANT_V)
+template <bool WANT_V, bool COUNT>
+__global__ void __launch_bounds__(CT_THREADS)
 cell_kernel(FieldLaunch L)
 {
     __shared__ PanTile s_pan[FT_PAN_TILE];
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
-    const int base = blockIdx.x * FT_BLOCK_TARGETS;
+    const int base = blockIdx.x * CT_BLOCK;
     if (base >= nt) return;
     const int tid = threadIdx.x;
-    float tx[FT_TPT], ty[FT_TPT], tz[FT_TPT];
-    float S[FT_TPT][4], C[FT_TPT][4];
+    float tx[CT_TPT], ty[CT_TPT], tz[CT_TPT];
+    float S[CT_TPT][4], C[CT_TPT][4];
+    int ti[CT_TPT];
 #pragma unroll
-    for (int k = 0; k < FT_TPT; ++k) {
-        int i = base + k * FT_THREADS + tid;
-        float4 p = L.targets[i < nt ? i : (nt - 1)];
+    for (int k = 0; k < CT_TPT; ++k) {
+        int i = base + k * CT_THREADS + tid;
+        int ic = i < nt ? i : (nt - 1);
+        ti[k] = L.perm ? L.perm[ic] : ic;
+        float4 p = L.targets[ti[k]];
         tx[k] = p.x; ty[k] = p.y; tz[k] = p.z;
+        if (i >= nt) ti[k] = -1;
 #pragma unroll
         for (int c = 0; c < 4; ++c) { S[k][c] = 0.f; C[k][c] = 0.f; }
     }
@@ -212,15 +338,15 @@ cell_kernel(FieldLaunch L)
         }
         __syncthreads();
         const int cntp = min(FT_PAN_TILE, np - pb);
-        float P[FT_TPT][4];
+        float P[CT_TPT][4];
 #pragma unroll
-        for (int k = 0; k < FT_TPT; ++k) { P[k][0] = P[k][1] = P[k][2] = P[k][3] = 0.f; }
+        for (int k = 0; k < CT_TPT; ++k) { P[k][0] = P[k][1] = P[k][2] = P[k][3] = 0.f; }
         for (int jj = 0; jj < cntp; ++jj) {
             const float4 cq = s_pan[jj].cq;
             const float4 g0 = s_pan[jj].g0;
             const float h2 = g0.w;
 #pragma unroll
-            for (int k = 0; k < FT_TPT; ++k) {
+            for (int k = 0; k < CT_TPT; ++k) {
                 float dx = tx[k] - cq.x, dy = ty[k] - cq.y, dz = tz[k] - cq.z;
                 float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 if (d2 >= TIER_1PT_H2 * h2) {
@@ -230,57 +356,46 @@ cell_kernel(FieldLaunch L)
                     P[k][0] = fmaf(dx, s3, P[k][0]);
                     P[k][1] = fmaf(dy, s3, P[k][1]);
                     P[k][2] = fmaf(dz, s3, P[k][2]);
-                    P[k][3] += s;
+                    if (WANT_V) P[k][3] += s;
                     if (COUNT) ++cnt1;
                 } else if (d2 >= TIER_3PT_H2 * h2) {
                     const float4 g1 = s_pan[jj].g1, g2 = s_pan[jj].g2;
                     float w = cq.w * (1.0f / 3.0f);
-                    qpoint(tx[k], ty[k], tz[k], cq.x + 0.5f * g0.x, cq.y + 0.5f * g0.y, cq.z + 0.5f * g0.z, w, P[k][0], P[k][1], P[k][2], P[k][3]);
-                    qpoint(tx[k], ty[k], tz[k], cq.x + 0.5f * g1.x, cq.y + 0.5f * g1.y, cq.z + 0.5f * g1.z, w, P[k][0], P[k][1], P[k][2], P[k][3]);
-                    qpoint(tx[k], ty[k], tz[k], cq.x + 0.5f * g2.x, cq.y + 0.5f * g2.y, cq.z + 0.5f * g2.z, w, P[k][0], P[k][1], P[k][2], P[k][3]);
+                    qpoint(tx[k], ty[k], tz[k], fmaf(0.5f, g0.x, cq.x), fmaf(0.5f, g0.y, cq.y), fmaf(0.5f, g0.z, cq.z), w, P[k][0], P[k][1], P[k][2], P[k][3]);
+                    qpoint(tx[k], ty[k], tz[k], fmaf(0.5f, g1.x, cq.x), fmaf(0.5f, g1.y, cq.y), fmaf(0.5f, g1.z, cq.z), w, P[k][0], P[k][1], P[k][2], P[k][3]);
+                    qpoint(tx[k], ty[k], tz[k], fmaf(0.5f, g2.x, cq.x), fmaf(0.5f, g2.y, cq.y), fmaf(0.5f, g2.z, cq.z), w, P[k][0], P[k][1], P[k][2], P[k][3]);
                     if (COUNT) ++cnt3;
                 } else if (d2 >= TIER_7PT_H2 * h2) {
                     const float4 g1 = s_pan[jj].g1, g2 = s_pan[jj].g2;
-                    float w0 = cq.w * D7_W0, w1 = cq.w * D7_W1, w2 = cq.w * D7_W2;
-                    qpoint(tx[k], ty[k], tz[k], cq.x, cq.y, cq.z, w0, P[k][0], P[k][1], P[k][2], P[k][3]);
-#pragma unroll 1
-                    for (int m = 0; m < 3; ++m) {
-                        float gx = m == 0 ? g0.x : (m == 1 ? g1.x : g2.x);
-                        float gy = m == 0 ? g0.y : (m == 1 ? g1.y : g2.y);
-                        float gz = m == 0 ? g0.z : (m == 1 ? g1.z : g2.z);
-                        qpoint(tx[k], ty[k], tz[k], fmaf(D7_T1, gx, cq.x), fmaf(D7_T1, gy, cq.y), fmaf(D7_T1, gz, cq.z), w1, P[k][0], P[k][1], P[k][2], P[k][3]);
-                        qpoint(tx[k], ty[k], tz[k], fmaf(D7_T2, gx, cq.x), fmaf(D7_T2, gy, cq.y), fmaf(D7_T2, gz, cq.z), w2, P[k][0], P[k][1], P[k][2], P[k][3]);
-                    }
+                    rule7(tx[k], ty[k], tz[k], cq.x, cq.y, cq.z, g0.x, g0.y, g0.z, g1.x, g1.y, g1.z, g2.x, g2.y,
+                          g2.z, cq.w, P[k]);
+                    if (COUNT) ++cnt7;
+                } else if (d2 >= TIER_28PT_H2 * h2) {
+                    rule28(tx[k], ty[k], tz[k], cq, g0, s_pan[jj].g1, s_pan[jj].g2, P[k]);
                     if (COUNT) ++cnt7;
                 } else {
                     const int j = __float_as_int(s_pan[jj].g1.w);
-                    const double sg = (double)s_pan[jj].g2.w;
-                    double phi, Fx, Fy, Fz;
-                    tri_closed_form(L.panels.v64 + 9 * (size_t)j, (double)tx[k], (double)ty[k], (double)tz[k], phi, Fx, Fy, Fz);
-                    const double kq = OBEM_KC * sg;
-                    P[k][0] += (float)(kq * Fx);
-                    P[k][1] += (float)(kq * Fy);
-                    P[k][2] += (float)(kq * Fz);
-                    P[k][3] += (float)(kq * phi);
+                    closed_into(L.panels.v64 + 9 * (size_t)j, tx[k], ty[k], tz[k], s_pan[jj].g2.w, P[k]);
                     if (COUNT) ++cntA;
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < FT_TPT; ++k)
+        for (int k = 0; k < CT_TPT; ++k) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) two_sum_acc(S[k][c], C[k][c], P[k][c]);
+            for (int c = 0; c < 3; ++c) two_sum_acc(S[k][c], C[k][c], P[k][c]);
+            if (WANT_V) two_sum_acc(S[k][3], C[k][3], P[k][3]);
+        }
     }
 #pragma unroll
-    for (int k = 0; k < FT_TPT; ++k) {
-        int i = base + k * FT_THREADS + tid;
-        if (i >= nt) continue;
+    for (int k = 0; k < CT_TPT; ++k) {
+        if (ti[k] < 0) continue;
         float4 e;
         e.x = (float)((double)S[k][0] + (double)C[k][0] + (double)L.e_ext.x);
         e.y = (float)((double)S[k][1] + (double)C[k][1] + (double)L.e_ext.y);
         e.z = (float)((double)S[k][2] + (double)C[k][2] + (double)L.e_ext.z);
-        e.w = (float)((double)S[k][3] + (double)C[k][3]);
-        L.E_out[i] = e;
+        e.w = WANT_V ? (float)((double)S[k][3] + (double)C[k][3]) : 0.f;
+        L.E_out[ti[k]] = e;
     }
     if (COUNT && L.counters) {
         atomicAdd(&L.counters[1], cnt1);
@@ -489,8 +604,29 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
     const bool cells = L.sigma != NULL && L.panels.np > 0;
     const bool charges = L.sources != NULL;
     if (cells) {
-        if (L.counters) cell_kernel<true><<<grid, FT_THREADS, 0, s>>>(L);
-        else cell_kernel<false><<<grid, FT_THREADS, 0, s>>>(L);
+        if (L.perm) {
+            // spatial order of the targets for the cell kernel
+            float3 lo = make_float3(ctx->bbox_lo[0], ctx->bbox_lo[1], ctx->bbox_lo[2]);
+            float3 sc;
+            sc.x = (float)OBEM_BINS_PER_AXIS / fmaxf(ctx->bbox_hi[0] - ctx->bbox_lo[0], 1e-30f);
+            sc.y = (float)OBEM_BINS_PER_AXIS / fmaxf(ctx->bbox_hi[1] - ctx->bbox_lo[1], 1e-30f);
+            sc.z = (float)OBEM_BINS_PER_AXIS / fmaxf(ctx->bbox_hi[2] - ctx->bbox_lo[2], 1e-30f);
+            OBEM_CUDA(ctx, cudaMemsetAsync(ctx->s_hist, 0, sizeof(int32_t) * OBEM_NBINS, s));
+            const int nb = (capacity_targets + 255) / 256;
+            bin_count_kernel<<<nb, 256, 0, s>>>(L, lo, sc, ctx->s_code, ctx->s_hist);
+            bin_scan_kernel<<<1, 1024, 0, s>>>(ctx->s_hist);
+            bin_scatter_kernel<<<nb, 256, 0, s>>>(L, ctx->s_code, ctx->s_hist, (int32_t *)L.perm);
+            OBEM_LAUNCH(ctx);
+            if (L.events) ctx->launches += 3;
+        }
+        dim3 cgrid((capacity_targets + CT_BLOCK - 1) / CT_BLOCK);
+        if (L.want_v) {
+            if (L.counters) cell_kernel<true, true><<<cgrid, CT_THREADS, 0, s>>>(L);
+            else cell_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L);
+        } else {
+            if (L.counters) cell_kernel<false, true><<<cgrid, CT_THREADS, 0, s>>>(L);
+            else cell_kernel<false, false><<<cgrid, CT_THREADS, 0, s>>>(L);
+        }
         OBEM_LAUNCH(ctx);
         if (L.events) ctx->launches++;
     }

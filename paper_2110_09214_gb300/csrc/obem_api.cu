@@ -90,6 +90,9 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->o_id, sizeof(uint32_t) * cap);
     ALLOC(c->o_birth, sizeof(uint32_t) * cap);
     ALLOC(c->o_sp, cap);
+    ALLOC(c->s_code, sizeof(uint32_t) * cap);
+    ALLOC(c->s_perm, sizeof(int32_t) * cap);
+    ALLOC(c->s_hist, sizeof(int32_t) * OBEM_NBINS);
 #undef ALLOC
     (void)bytes;
     *out = c;
@@ -104,6 +107,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->s_E); free_dev(c->s_prop); free_dev(c->s_ionkey); free_dev(c->s_keep);
     free_dev(c->s_nsp); free_dev(c->s_blk); free_dev(c->s_ctl); free_dev(c->o_pos);
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
+    free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->prof_ev) {
         for (int i = 0; i < 4 * OBEM_PROF_MAX; ++i) cudaEventDestroy(c->prof_ev[i]);
@@ -278,6 +282,14 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
     memcpy(c->h_tri, tri, sizeof(double) * 9 * np);
     memcpy(c->h_em, em, sizeof(double) * np);
     memcpy(c->h_ep, ep, sizeof(double) * np);
+    for (int k = 0; k < 3; ++k) { c->bbox_lo[k] = 3e38f; c->bbox_hi[k] = -3e38f; }
+    for (int i = 0; i < np; ++i)
+        for (int v = 0; v < 3; ++v)
+            for (int k = 0; k < 3; ++k) {
+                float x = (float)tri[9 * (size_t)i + 3 * v + k];
+                if (x < c->bbox_lo[k]) c->bbox_lo[k] = x;
+                if (x > c->bbox_hi[k]) c->bbox_hi[k] = x;
+            }
     float4 *ca = (float4 *)malloc(sizeof(float4) * np);
     float4 *g0 = (float4 *)malloc(sizeof(float4) * np);
     float4 *g1 = (float4 *)malloc(sizeof(float4) * np);
@@ -392,6 +404,9 @@ extern "C" int obem_field_eval(obem_ctx *c, const float *targets, int32_t nt, co
     L.E_out = (float4 *)E_out;
     L.e_ext = make_float3(0.f, 0.f, 0.f);
     L.want_v = 1;
+    // the scratch holds a spatial order for up to `capacity` targets; larger
+    // calls keep the given order (same results, slower cell kernel)
+    L.perm = (sigma && nt <= c->cap) ? c->s_perm : NULL;
     return obem_launch_field(c, L, nt, (cudaStream_t)stream);
 }
 
@@ -431,6 +446,7 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         L.eps2 = (float)(c->cfg.softening * c->cfg.softening);
         L.sigma = want_cells ? c->d_sigma : NULL;
         L.panels = panels_of(c);
+        L.perm = want_cells ? c->s_perm : NULL;
         L.E_out = c->s_E;
         L.e_ext = make_float3((float)c->cfg.e_ext[0], (float)c->cfg.e_ext[1], (float)c->cfg.e_ext[2]);
         L.want_v = 0;

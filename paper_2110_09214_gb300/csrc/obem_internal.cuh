@@ -81,6 +81,7 @@ struct obem_ctx {
     float4 *d_c_a, *d_g0_h, *d_g1, *d_g2, *d_nrm;
     double *d_v64;
     int *d_kind, *d_group;
+    float bbox_lo[3], bbox_hi[3];   // of the cell vertices (target binning grid)
     // BEM
     float *d_A;          // equilibrated matrix, row-major [np][np]
     float *d_LU;         // LU factors (row-major, unit lower L below the diagonal)
@@ -105,6 +106,10 @@ struct obem_ctx {
     uint32_t *o_id, *o_birth;
     uint8_t *o_sp;
     int cap;
+    // target binning (Morton order of a 64^3 grid) for the cell kernel
+    uint32_t *s_code;
+    int32_t *s_perm;
+    int32_t *s_hist;
     // stage timing (obem_profile)
     int prof_on;
     int prof_n;                      // recorded steps (ring of OBEM_PROF_MAX)
@@ -158,7 +163,11 @@ struct FieldLaunch {
     unsigned long long *counters;
     // optional events: [1] recorded after the cell kernel, [2] after the all-pairs kernel
     cudaEvent_t *events;
+    // cell kernel: target order (spatially binned) or NULL for the given order
+    const int32_t *perm;
 };
+#define OBEM_BINS_PER_AXIS 64
+#define OBEM_NBINS (OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS)
 int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets, cudaStream_t s);
 
 // step.cu

@@ -35,3 +35,14 @@ def pts4(p):
 
 
 FIELD_TOL = 1e-5
+
+
+def potential_err(got, ref, ref_abs):
+    """Potential error relative to max(|V|, 0.1 V_abs), V_abs = sum of |terms|:
+    binary32 partial sums of cancelling +- contributions fix V only to a few
+    ulps of V_abs, so V is gated on that scale (E uses guarded_rel_err)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    den = np.maximum(np.abs(ref), 0.1 * np.abs(np.asarray(ref_abs, np.float64)))
+    den = np.where(den > 0, den, 1.0)
+    return float((np.abs(got - ref) / den).max()) if len(ref) else 0.0

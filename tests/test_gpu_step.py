@@ -261,7 +261,14 @@ def test_fused_field_step_matches_oracle_run():
     fin, _, _ = oracle.run(ch, gas, trk, 5, mesh, sig)
     common, ia, ib = np.intersect1d(gst.id, fin.id, return_indices=True)
     assert len(common) >= 0.99 * max(len(gst.id), len(fin.id))
-    same = np.all(gst.vel[ia, :3] == fin.vel[ib, :3], axis=1)
+    assert (gst.species[ia] == fin.species[ib]).mean() >= 0.99
+    # the two fields differ at the 1e-6 level, so velocities differ in their
+    # last bits; a charge whose collision decisions were the same has a
+    # velocity within ~1e-4 relative, one with a flipped decision a random one
+    vg = gst.vel[ia, :3].astype(float)
+    vo = fin.vel[ib, :3].astype(float)
+    rel = np.linalg.norm(vg - vo, axis=1) / np.maximum(np.linalg.norm(vo, axis=1), 1.0)
+    same = rel < 1e-3
     assert same.mean() > 0.97
     d = np.abs(gst.pos_q[ia, :3].astype(float) - fin.pos_q[ib, :3].astype(float)).max(axis=1)
     assert np.quantile(d[same], 0.99) < 1e-9
