@@ -289,7 +289,8 @@ def run_ours(a, ws, rank, local):
         "field_pair_evals_per_s": pair_evals / sec,
         "fp32_peak_frac": achieved / peak if peak else None,
         "fp32_peak_frac_at_load_clock": achieved / peak_load if peak_load else None,
-        "stage_ms_per_step": {"cells": prof["cell_ms"] / a.steps, "pairs": prof["pairs_ms"] / a.steps,
+        "stage_ms_per_step": {"cells": prof["cell_ms"] / a.steps, "cells_near": prof["near_ms"] / a.steps,
+                              "pairs": prof["pairs_ms"] / a.steps,
                               "step": prof["step_ms"] / a.steps},
         "cell_evals_per_step": {"centroid": prof["cells_1pt"] / a.steps, "3pt": prof["cells_3pt"] / a.steps,
                                 "7pt": prof["cells_7pt"] / a.steps, "closed_form": prof["cells_closed"] / a.steps},

@@ -216,14 +216,15 @@ int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t s
  * around its stages (up to 256 steps are kept; older ones are dropped);
  * obem_stage_times() waits for the recorded events and returns, summed over
  * the recorded steps:
- *   ms[0] cell field kernel, ms[1] all-pairs field kernel, ms[2] step kernels
- *   (recombination, flight, compaction, moments), ms[3] whole obem_step;
+ *   ms[0] cell field (binning + near + far kernels), ms[1] all-pairs field
+ *   kernel, ms[2] step kernels (recombination, flight, compaction, moments),
+ *   ms[3] whole obem_step, ms[4] the near-cell kernel alone (part of ms[0]);
  *   counts[0] steps recorded, counts[1] kernels launched by those steps,
  *   counts[2] charge pairs of the all-pairs kernel,
  *   counts[3..6] cell evaluations by tier (centroid, 3-point, 7-point, closed form).
  * Recording is then reset.  obem_profile(ctx, 0) stops recording. */
 int obem_profile(obem_ctx *ctx, int32_t enable);
-int obem_stage_times(obem_ctx *ctx, double *ms /* [4] */, int64_t *counts /* [7] */);
+int obem_stage_times(obem_ctx *ctx, double *ms /* [5] */, int64_t *counts /* [7] */);
 
 #ifdef __cplusplus
 }

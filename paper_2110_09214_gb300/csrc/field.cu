@@ -11,10 +11,12 @@
 //
 // Cell field tiers, chosen per (target, cell) from the distance d to the
 // centroid and the longest edge h:
-//   d >= 200 h   centroid rule            (<= 3.4e-6 relative per cell)
-//   d >=  16 h   3-point degree-2 rule    (<= 2.7e-6)
-//   d >=   3 h   7-point degree-5 rule    (<= 1.4e-6)
-//   d <    3 h   closed form in FP64 (edge logarithms + solid angle)
+//   d >= 200 h   centroid rule                          (<= 3.4e-6 relative per cell)
+//   d >=  16 h   3-point degree-2 rule                  (<= 2.7e-6)
+//   d >=   3 h   7-point degree-5 rule                  (<= 1.8e-6)
+//   d >= 1.5 h   7-point rule on 4 midpoint sub-triangles  (<= 2.2e-6)
+//   d >=   h     7-point rule on 16 sub-triangles       (<= 1.3e-6)
+//   d <    h     closed form in FP64 (edge logarithms + solid angle)
 #include "obem_internal.cuh"
 
 #define FT_THREADS 128
@@ -220,6 +222,43 @@ __global__ void bin_scan_kernel(int32_t *hist)
     }
 }
 
+// Blocks of the cell kernels: the targets of one super-bin (2 x 2 x 2 bins,
+// contiguous in the sorted order) are cut into blocks of at most CT_BLOCK_N,
+// so a block never spans distant bins.  One block of 1024 threads; reads the
+// scanned histogram (bin start offsets) before the scatter advances it.
+#define CT_BLOCK_N 512
+__global__ void block_list_kernel(const int32_t *start, int nt_host, const int32_t *nt_dev, int2 *blocks,
+                                  int32_t *nblocks)
+{
+    __shared__ int32_t part[1024];
+    const int nt = nt_dev ? *nt_dev : nt_host;
+    const int per = OBEM_NSUPER / 1024;
+    int cnt[OBEM_NSUPER / 1024];
+    int32_t s = 0;
+    for (int q = 0; q < per; ++q) {
+        const int sb = threadIdx.x * per + q;
+        const int a = start[sb << OBEM_SUPER_SHIFT];
+        const int b = (sb + 1 < OBEM_NSUPER) ? start[(sb + 1) << OBEM_SUPER_SHIFT] : nt;
+        cnt[q] = b - a;
+        s += (b - a + CT_BLOCK_N - 1) / CT_BLOCK_N;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t o = part[threadIdx.x] - s;
+    for (int q = 0; q < per; ++q) {
+        const int sb = threadIdx.x * per + q;
+        const int a = start[sb << OBEM_SUPER_SHIFT];
+        for (int k = 0; k < cnt[q]; k += CT_BLOCK_N) blocks[o++] = make_int2(a + k, min(CT_BLOCK_N, cnt[q] - k));
+    }
+    if (threadIdx.x == 1023) nblocks[0] = part[1023];
+}
+
 __global__ void bin_scatter_kernel(FieldLaunch L, const uint32_t *code, int32_t *hist, int32_t *perm)
 {
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
@@ -229,54 +268,159 @@ __global__ void bin_scatter_kernel(FieldLaunch L, const uint32_t *code, int32_t 
     perm[pos] = i;
 }
 
-// ---------------------------------------------------------------- cell field kernel
+// ---------------------------------------------------------------- cell field kernels
+// The cell field is computed by three kernels over the same partition of the
+// (binned) targets into blocks of CT_BLOCK targets.  A cell is "near" a block
+// if its centroid is closer than 1.5 h to the bounding box of the block's
+// targets (or if the block is so spread out that its frame cannot resolve the
+// cell); the test is the same function in all three kernels.
+//   near_closed_kernel  near cells, targets with d < h: FP64 closed form;
+//                       writes E_out = e_ext + these terms
+//   near_quad_kernel    near cells, all other targets: 7-point rule on 16
+//                       sub-triangles (<= 1.3e-6 for d >= h), uniform for the
+//                       block, target-centroid differences exact
+//   cell_kernel         far cells: 1 / 3 / 7 / 28 quadrature points chosen by
+//                       the distance to the box, emitted as point sources in a
+//                       frame centred on the block and consumed by the packed
+//                       f32x2 loop
 #define CT_THREADS 128
-#define CT_TPT 2
+#define CT_TPT 4
 #define CT_BLOCK (CT_THREADS * CT_TPT)
+#define CT_CHUNK 32                 // far cells emitted per round
+#define CT_MAXPTS (CT_CHUNK * 28 + 4)
+#define NEAR_CHUNK 128              // cells tested per round
+#define NQ_CELLS 8                  // near cells per quadrature round
+#define NQ_PTS 112
 
-#define TIER_28PT_H2 4.0f     // 2h <= d < 3h: 7-point rule on the 4 midpoint sub-triangles
+#define TIER_28PT_H2 2.25f          // d >= 1.5 h
+#define FRAME_H 0.05f               // a cell needs h >= FRAME_H * frame scale to be far
 
-// 7-point rule over the triangle with centroid (cx,cy,cz) and vertex offsets g*
-__device__ __forceinline__ void rule7(float tx, float ty, float tz, float cx, float cy, float cz,
-                                      float g0x, float g0y, float g0z, float g1x, float g1y, float g1z,
-                                      float g2x, float g2y, float g2z, float q, float *P)
+// sub-triangle s of the midpoint subdivision of (A, B, C): 0 the middle one,
+// 1..3 the corner ones at A, B, C
+__device__ __forceinline__ void subtri(int s, float3 &A, float3 &B, float3 &C)
 {
-    const float w1 = q * D7_W1, w2 = q * D7_W2;
-    qpoint(tx, ty, tz, cx, cy, cz, q * D7_W0, P[0], P[1], P[2], P[3]);
-    qpoint(tx, ty, tz, fmaf(D7_T1, g0x, cx), fmaf(D7_T1, g0y, cy), fmaf(D7_T1, g0z, cz), w1, P[0], P[1], P[2], P[3]);
-    qpoint(tx, ty, tz, fmaf(D7_T1, g1x, cx), fmaf(D7_T1, g1y, cy), fmaf(D7_T1, g1z, cz), w1, P[0], P[1], P[2], P[3]);
-    qpoint(tx, ty, tz, fmaf(D7_T1, g2x, cx), fmaf(D7_T1, g2y, cy), fmaf(D7_T1, g2z, cz), w1, P[0], P[1], P[2], P[3]);
-    qpoint(tx, ty, tz, fmaf(D7_T2, g0x, cx), fmaf(D7_T2, g0y, cy), fmaf(D7_T2, g0z, cz), w2, P[0], P[1], P[2], P[3]);
-    qpoint(tx, ty, tz, fmaf(D7_T2, g1x, cx), fmaf(D7_T2, g1y, cy), fmaf(D7_T2, g1z, cz), w2, P[0], P[1], P[2], P[3]);
-    qpoint(tx, ty, tz, fmaf(D7_T2, g2x, cx), fmaf(D7_T2, g2y, cy), fmaf(D7_T2, g2z, cz), w2, P[0], P[1], P[2], P[3]);
+    const float3 ab = make_float3(0.5f * (A.x + B.x), 0.5f * (A.y + B.y), 0.5f * (A.z + B.z));
+    const float3 bc = make_float3(0.5f * (B.x + C.x), 0.5f * (B.y + C.y), 0.5f * (B.z + C.z));
+    const float3 ca = make_float3(0.5f * (C.x + A.x), 0.5f * (C.y + A.y), 0.5f * (C.z + A.z));
+    if (s == 0) { A = ab; B = bc; C = ca; }
+    else if (s == 1) { B = ab; C = ca; }
+    else if (s == 2) { A = B; B = bc; C = ab; }
+    else { A = C; B = ca; C = bc; }
 }
 
-// 7-point rule on each of the 4 midpoint sub-triangles (offsets from c)
-__device__ __noinline__ void rule28(float tx, float ty, float tz, float4 cq, float4 g0, float4 g1, float4 g2,
-                                    float *P)
+// Point k of the 7-point rule applied to the 4^level sub-triangles of the
+// cell with vertex offsets g0, g1, g2 (from its centroid): offset and weight
+// fraction of the point.
+__device__ __forceinline__ void rule_point(int level, int k, float3 g0, float3 g1, float3 g2, float3 &off,
+                                           float &wf)
 {
-    const float q = 0.25f * cq.w;
-    const float m01x = 0.5f * (g0.x + g1.x), m01y = 0.5f * (g0.y + g1.y), m01z = 0.5f * (g0.z + g1.z);
-    const float m12x = 0.5f * (g1.x + g2.x), m12y = 0.5f * (g1.y + g2.y), m12z = 0.5f * (g1.z + g2.z);
-    const float m20x = 0.5f * (g2.x + g0.x), m20y = 0.5f * (g2.y + g0.y), m20z = 0.5f * (g2.z + g0.z);
-    // middle sub-triangle: centroid c, offsets m01, m12, m20
-    rule7(tx, ty, tz, cq.x, cq.y, cq.z, m01x, m01y, m01z, m12x, m12y, m12z, m20x, m20y, m20z, q, P);
-    // corner sub-triangles (v_k, m_k,k+1, m_k,k-1)
-#pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
-        float ax = k == 0 ? g0.x : (k == 1 ? g1.x : g2.x), ay = k == 0 ? g0.y : (k == 1 ? g1.y : g2.y),
-              az = k == 0 ? g0.z : (k == 1 ? g1.z : g2.z);
-        float bx = k == 0 ? m01x : (k == 1 ? m12x : m20x), by = k == 0 ? m01y : (k == 1 ? m12y : m20y),
-              bz = k == 0 ? m01z : (k == 1 ? m12z : m20z);
-        float ex = k == 0 ? m20x : (k == 1 ? m01x : m12x), ey = k == 0 ? m20y : (k == 1 ? m01y : m12y),
-              ez = k == 0 ? m20z : (k == 1 ? m01z : m12z);
-        float sx = (ax + bx + ex) * (1.0f / 3.0f), sy = (ay + by + ey) * (1.0f / 3.0f), sz = (az + bz + ez) * (1.0f / 3.0f);
-        rule7(tx, ty, tz, cq.x + sx, cq.y + sy, cq.z + sz, ax - sx, ay - sy, az - sz, bx - sx, by - sy, bz - sz,
-              ex - sx, ey - sy, ez - sz, q, P);
+    int sub = k / 7;
+    const int m = k % 7;
+    float3 A = g0, B = g1, C = g2;
+    float scale = 1.0f;
+    for (int l = level - 1; l >= 0; --l) {
+        int s = (sub >> (2 * l)) & 3;
+        subtri(s, A, B, C);
+        scale *= 0.25f;
+    }
+    const float3 sc = make_float3((A.x + B.x + C.x) * (1.0f / 3.0f), (A.y + B.y + C.y) * (1.0f / 3.0f),
+                                  (A.z + B.z + C.z) * (1.0f / 3.0f));
+    if (m == 0) { off = sc; wf = scale * D7_W0; return; }
+    const int v = (m - 1) % 3;
+    const float t = m <= 3 ? D7_T1 : D7_T2;
+    const float3 V = v == 0 ? A : (v == 1 ? B : C);
+    off = make_float3(fmaf(t, V.x - sc.x, sc.x), fmaf(t, V.y - sc.y, sc.y), fmaf(t, V.z - sc.z, sc.z));
+    wf = scale * (m <= 3 ? D7_W1 : D7_W2);
+}
+
+// squared distance from point c to the box [lo, hi]
+__device__ __forceinline__ float box_d2(float cx, float cy, float cz, float3 lo, float3 hi)
+{
+    float dx = fmaxf(fmaxf(lo.x - cx, cx - hi.x), 0.f);
+    float dy = fmaxf(fmaxf(lo.y - cy, cy - hi.y), 0.f);
+    float dz = fmaxf(fmaxf(lo.z - cz, cz - hi.z), 0.f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+struct BlockFrame {
+    float3 lo, hi;      // box of the block's targets (absolute)
+    float3 o;           // frame origin: box centre if the block is compact, else 0
+    float scale2;       // squared largest |target - o| bound (box corners)
+};
+
+// This block's range of the (binned) target order: [base, end).  Returns
+// false for grid blocks beyond the block list.
+__device__ __forceinline__ bool block_range(const FieldLaunch &L, int nt, int &base, int &end)
+{
+    if (L.blocks) {
+        if ((int)blockIdx.x >= *L.nblocks) return false;
+        const int2 b = L.blocks[blockIdx.x];
+        base = b.x;
+        end = b.x + b.y;
+    } else {
+        base = blockIdx.x * CT_BLOCK;
+        end = min(nt, base + CT_BLOCK);
+    }
+    return base < nt;
+}
+
+// Targets of this block (binned order, absolute coordinates) and its frame.
+// Target slot k of thread t is base + k * CT_THREADS + t.
+__device__ __forceinline__ void block_targets(const FieldLaunch &L, int end, int base, float *tx, float *ty,
+                                              float *tz, int *ti, BlockFrame &F)
+{
+    __shared__ float red[6][CT_THREADS / 32];
+    float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
+#pragma unroll
+    for (int k = 0; k < CT_TPT; ++k) {
+        int i = base + k * CT_THREADS + threadIdx.x;
+        int ic = i < end ? i : (end - 1);
+        ti[k] = L.perm ? L.perm[ic] : ic;
+        float4 p = L.targets[ti[k]];
+        tx[k] = p.x; ty[k] = p.y; tz[k] = p.z;
+        if (i >= end) { ti[k] = -1; continue; }
+        mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+        mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int q = 16; q; q >>= 1) {
+            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], q));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], q));
+        }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 3; ++c) { red[c][w] = mn[c]; red[3 + c][w] = mx[c]; }
+    __syncthreads();
+    float r[6];
+    for (int c = 0; c < 6; ++c) {
+        float v = red[c][0];
+        for (int q = 1; q < CT_THREADS / 32; ++q) v = c < 3 ? fminf(v, red[c][q]) : fmaxf(v, red[c][q]);
+        r[c] = v;
+    }
+    F.lo = make_float3(r[0], r[1], r[2]);
+    F.hi = make_float3(r[3], r[4], r[5]);
+    const float hx = 0.5f * (r[3] - r[0]), hy = 0.5f * (r[4] - r[1]), hz = 0.5f * (r[5] - r[2]);
+    const float half2 = hx * hx + hy * hy + hz * hz;
+    const float ax = fmaxf(fabsf(r[0]), fabsf(r[3])), ay = fmaxf(fabsf(r[1]), fabsf(r[4])),
+                az = fmaxf(fabsf(r[2]), fabsf(r[5]));
+    const float abs2 = ax * ax + ay * ay + az * az;
+    if (half2 <= abs2) {
+        F.o = make_float3(0.5f * (r[0] + r[3]), 0.5f * (r[1] + r[4]), 0.5f * (r[2] + r[5]));
+        F.scale2 = half2;
+    } else {
+        F.o = make_float3(0.f, 0.f, 0.f);
+        F.scale2 = abs2;
     }
 }
 
-// FP64 closed form of one cell, added to the FP32 partial
+// the near test shared by the three cell kernels
+__device__ __forceinline__ bool cell_is_near(float4 ca, float h2, const BlockFrame &F)
+{
+    return box_d2(ca.x, ca.y, ca.z, F.lo, F.hi) < TIER_28PT_H2 * h2 || h2 < (FRAME_H * FRAME_H) * F.scale2;
+}
+
+// FP64 closed form of one cell, added into P
 __device__ __noinline__ void closed_into(const double *v, float tx, float ty, float tz, float sg, float *P)
 {
     double phi, Fx, Fy, Fz;
@@ -288,104 +432,78 @@ __device__ __noinline__ void closed_into(const double *v, float tx, float ty, fl
     P[3] += (float)(kq * phi);
 }
 
-// E_out[i] = e_ext + k_C sum_j sigma_j F_j(r_i)  (w: potential if WANT_V)
+// deterministic compaction of the near cells of [pb, pb + NEAR_CHUNK) into list
+__device__ __forceinline__ int near_list(const FieldLaunch &L, int pb, const BlockFrame &F, int *list, int *cnt)
+{
+    const int np = L.panels.np;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = pb + threadIdx.x;
+    bool near = false;
+    if (j < np) near = cell_is_near(L.panels.c_a[j], L.panels.g0_h[j].w, F);
+    const unsigned bal = __ballot_sync(0xffffffffu, near);
+    __syncthreads();
+    if (lane == 0) cnt[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < CT_THREADS / 32; ++w) { if (w < warp) off += cnt[w]; tot += cnt[w]; }
+    if (near) list[off + __popc(bal & ((1u << lane) - 1u))] = j;
+    __syncthreads();
+    return tot;
+}
+
+// exact target - centroid difference: (t - c_hi) - c_lo
+__device__ __forceinline__ void diff_exact(float t, float chi, float clo, float &d)
+{
+    d = (t - chi) - clo;
+}
+
+// near cells, targets within h of them: FP64 closed form; E_out = e_ext + that
 template <bool WANT_V, bool COUNT>
 __global__ void __launch_bounds__(CT_THREADS)
-cell_kernel(FieldLaunch L)
+near_closed_kernel(FieldLaunch L)
 {
-    __shared__ PanTile s_pan[FT_PAN_TILE];
+    __shared__ int s_list[NEAR_CHUNK];
+    __shared__ int s_cnt[CT_THREADS / 32];
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
-    const int base = blockIdx.x * CT_BLOCK;
-    if (base >= nt) return;
-    const int tid = threadIdx.x;
+    int base, end;
+    if (!block_range(L, nt, base, end)) return;
     float tx[CT_TPT], ty[CT_TPT], tz[CT_TPT];
-    float S[CT_TPT][4], C[CT_TPT][4];
     int ti[CT_TPT];
+    BlockFrame F;
+    block_targets(L, end, base, tx, ty, tz, ti, F);
+    // warps whose target slots are all padding skip the arithmetic
+    const bool warp_live = base + (int)(threadIdx.x & ~31u) < end;
+    float S[CT_TPT][4], C[CT_TPT][4];
 #pragma unroll
-    for (int k = 0; k < CT_TPT; ++k) {
-        int i = base + k * CT_THREADS + tid;
-        int ic = i < nt ? i : (nt - 1);
-        ti[k] = L.perm ? L.perm[ic] : ic;
-        float4 p = L.targets[ti[k]];
-        tx[k] = p.x; ty[k] = p.y; tz[k] = p.z;
-        if (i >= nt) ti[k] = -1;
+    for (int k = 0; k < CT_TPT; ++k)
 #pragma unroll
         for (int c = 0; c < 4; ++c) { S[k][c] = 0.f; C[k][c] = 0.f; }
-    }
-    unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0, cntA = 0;
-    const int np = L.panels.np;
-    for (int pb = 0; pb < np; pb += FT_PAN_TILE) {
-        __syncthreads();
-        if (tid < FT_PAN_TILE) {
-            int j = pb + tid;
-            PanTile t;
-            if (j < np) {
-                float4 ca = L.panels.c_a[j];
-                float sg = L.sigma[j];
-                t.cq = make_float4(ca.x, ca.y, ca.z, ca.w * sg);
-                t.g0 = L.panels.g0_h[j];
-                float4 g1 = L.panels.g1[j];
-                float4 g2 = L.panels.g2[j];
-                t.g1 = make_float4(g1.x, g1.y, g1.z, __int_as_float(j));
-                t.g2 = make_float4(g2.x, g2.y, g2.z, sg);
-            } else {
-                t.cq = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-                t.g0 = make_float4(0.f, 0.f, 0.f, 0.f);
-                t.g1 = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-                t.g2 = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            s_pan[tid] = t;
-        }
-        __syncthreads();
-        const int cntp = min(FT_PAN_TILE, np - pb);
+    unsigned long long cntA = 0;
+    for (int pb = 0; pb < L.panels.np; pb += NEAR_CHUNK) {
+        const int tot = near_list(L, pb, F, s_list, s_cnt);
+        if (tot == 0) continue;
         float P[CT_TPT][4];
 #pragma unroll
         for (int k = 0; k < CT_TPT; ++k) { P[k][0] = P[k][1] = P[k][2] = P[k][3] = 0.f; }
-        for (int jj = 0; jj < cntp; ++jj) {
-            const float4 cq = s_pan[jj].cq;
-            const float4 g0 = s_pan[jj].g0;
-            const float h2 = g0.w;
+        for (int q = 0; q < (warp_live ? tot : 0); ++q) {
+            const int j = s_list[q];
+            const float4 ca = L.panels.c_a[j], cl = L.panels.c_lo[j];
+            const float h2 = L.panels.g0_h[j].w;
 #pragma unroll
             for (int k = 0; k < CT_TPT; ++k) {
-                float dx = tx[k] - cq.x, dy = ty[k] - cq.y, dz = tz[k] - cq.z;
-                float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (d2 >= TIER_1PT_H2 * h2) {
-                    float inv = rsq(d2);
-                    float s = cq.w * inv;
-                    float s3 = s * (inv * inv);
-                    P[k][0] = fmaf(dx, s3, P[k][0]);
-                    P[k][1] = fmaf(dy, s3, P[k][1]);
-                    P[k][2] = fmaf(dz, s3, P[k][2]);
-                    if (WANT_V) P[k][3] += s;
-                    if (COUNT) ++cnt1;
-                } else if (d2 >= TIER_3PT_H2 * h2) {
-                    const float4 g1 = s_pan[jj].g1, g2 = s_pan[jj].g2;
-                    float w = cq.w * (1.0f / 3.0f);
-                    qpoint(tx[k], ty[k], tz[k], fmaf(0.5f, g0.x, cq.x), fmaf(0.5f, g0.y, cq.y), fmaf(0.5f, g0.z, cq.z), w, P[k][0], P[k][1], P[k][2], P[k][3]);
-                    qpoint(tx[k], ty[k], tz[k], fmaf(0.5f, g1.x, cq.x), fmaf(0.5f, g1.y, cq.y), fmaf(0.5f, g1.z, cq.z), w, P[k][0], P[k][1], P[k][2], P[k][3]);
-                    qpoint(tx[k], ty[k], tz[k], fmaf(0.5f, g2.x, cq.x), fmaf(0.5f, g2.y, cq.y), fmaf(0.5f, g2.z, cq.z), w, P[k][0], P[k][1], P[k][2], P[k][3]);
-                    if (COUNT) ++cnt3;
-                } else if (d2 >= TIER_7PT_H2 * h2) {
-                    const float4 g1 = s_pan[jj].g1, g2 = s_pan[jj].g2;
-                    rule7(tx[k], ty[k], tz[k], cq.x, cq.y, cq.z, g0.x, g0.y, g0.z, g1.x, g1.y, g1.z, g2.x, g2.y,
-                          g2.z, cq.w, P[k]);
-                    if (COUNT) ++cnt7;
-                } else if (d2 >= TIER_28PT_H2 * h2) {
-                    rule28(tx[k], ty[k], tz[k], cq, g0, s_pan[jj].g1, s_pan[jj].g2, P[k]);
-                    if (COUNT) ++cnt7;
-                } else {
-                    const int j = __float_as_int(s_pan[jj].g1.w);
-                    closed_into(L.panels.v64 + 9 * (size_t)j, tx[k], ty[k], tz[k], s_pan[jj].g2.w, P[k]);
+                if (ti[k] < 0) continue;
+                float dx, dy, dz;
+                diff_exact(tx[k], ca.x, cl.x, dx); diff_exact(ty[k], ca.y, cl.y, dy); diff_exact(tz[k], ca.z, cl.z, dz);
+                if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < h2) {
+                    closed_into(L.panels.v64 + 9 * (size_t)j, tx[k], ty[k], tz[k], L.sigma[j], P[k]);
                     if (COUNT) ++cntA;
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < CT_TPT; ++k) {
+        for (int k = 0; k < CT_TPT; ++k)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) two_sum_acc(S[k][c], C[k][c], P[k][c]);
-            if (WANT_V) two_sum_acc(S[k][3], C[k][3], P[k][3]);
-        }
+            for (int c = 0; c < 4; ++c) two_sum_acc(S[k][c], C[k][c], P[k][c]);
     }
 #pragma unroll
     for (int k = 0; k < CT_TPT; ++k) {
@@ -397,55 +515,36 @@ cell_kernel(FieldLaunch L)
         e.w = WANT_V ? (float)((double)S[k][3] + (double)C[k][3]) : 0.f;
         L.E_out[ti[k]] = e;
     }
-    if (COUNT && L.counters) {
-        atomicAdd(&L.counters[1], cnt1);
-        atomicAdd(&L.counters[2], cnt3);
-        atomicAdd(&L.counters[3], cnt7);
-        atomicAdd(&L.counters[4], cntA);
-    }
+    if (COUNT && L.counters) atomicAdd(&L.counters[4], cntA);
 }
 
-// ---------------------------------------------------------------- all-pairs kernel
-// E_out[i] = init + k_C sum_{p != i} q_p (r_i - r_p) / (|r_i - r_p|^2 + eps^2)^(3/2)
-// init = E_out[i] when the cell kernel ran first (ADD), else e_ext.
-template <bool WANT_V, bool RECOMB, bool ADD>
-__global__ void __launch_bounds__(FT_THREADS)
-nbody_kernel(FieldLaunch L)
+// near cells, targets at d >= h: 112-point rule, exact relative coordinates
+template <bool WANT_V, bool COUNT>
+__global__ void __launch_bounds__(CT_THREADS)
+near_quad_kernel(FieldLaunch L)
 {
-    __shared__ SrcPk s_src[FT_SRC_TILE];
-
+    __shared__ int s_list[NEAR_CHUNK];
+    __shared__ int s_cnt[CT_THREADS / 32];
+    __shared__ SrcPk s_off[NQ_CELLS][NQ_PTS];                // offsets from the centroid, weight
+    __shared__ float4 s_cell[NQ_CELLS][2];                    // (c_hi, h^2), (c_lo, 0)
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
-    const int ns = L.ns_dev ? *L.ns_dev : L.ns;
-    const int base = blockIdx.x * FT_BLOCK_TARGETS;
-    if (base >= nt) return;
+    int base, end;
+    if (!block_range(L, nt, base, end)) return;
     const int tid = threadIdx.x;
-
-    float tx[FT_TPT], ty[FT_TPT], tz[FT_TPT];
-    float S[FT_TPT][4], C[FT_TPT][4];
-    float rc2f[FT_TPT];
-    u64 best[FT_TPT];
+    float tx[CT_TPT], ty[CT_TPT], tz[CT_TPT];
+    int ti[CT_TPT];
+    BlockFrame F;
+    block_targets(L, end, base, tx, ty, tz, ti, F);
+    const bool warp_live = base + (int)(threadIdx.x & ~31u) < end;
+    float S[CT_TPT][4], C[CT_TPT][4];
 #pragma unroll
-    for (int k = 0; k < FT_TPT; ++k) {
-        int i = base + k * FT_THREADS + tid;
-        int ic = i < nt ? i : (nt - 1);
-        float4 p = L.targets[ic];
-        tx[k] = p.x; ty[k] = p.y; tz[k] = p.z;
-        if (ADD) {
-            float4 e = L.E_out[ic];
-            S[k][0] = e.x; S[k][1] = e.y; S[k][2] = e.z; S[k][3] = e.w;
-        } else {
-            S[k][0] = L.e_ext.x; S[k][1] = L.e_ext.y; S[k][2] = L.e_ext.z; S[k][3] = 0.f;
-        }
+    for (int k = 0; k < CT_TPT; ++k) {
+        int ic = ti[k] >= 0 ? ti[k] : 0;
+        float4 e = L.E_out[ic];
+        S[k][0] = e.x; S[k][1] = e.y; S[k][2] = e.z; S[k][3] = WANT_V ? e.w : 0.f;
 #pragma unroll
         for (int c = 0; c < 4; ++c) C[k][c] = 0.f;
-        best[k] = ~0ull;
-        rc2f[k] = -1.0f;
-        if (RECOMB && i < nt && L.species[i] == OBEM_ELECTRON)
-            rc2f[k] = (L.rc2 + L.eps2) * (1.0f + 3.814697265625e-06f) + 1e-30f;
     }
-
-    const float kC = (float)OBEM_KC;
-    const u64 EPS2 = pk(L.eps2, L.eps2);
     u64 TX[2], TY[2], TZ[2];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -453,6 +552,320 @@ nbody_kernel(FieldLaunch L)
         TY[p] = pk(ty[2 * p], ty[2 * p + 1]);
         TZ[p] = pk(tz[2 * p], tz[2 * p + 1]);
     }
+    unsigned long long cntQ = 0;
+    for (int pb = 0; pb < L.panels.np; pb += NEAR_CHUNK) {
+        const int tot = near_list(L, pb, F, s_list, s_cnt);
+        for (int g = 0; g < tot; g += NQ_CELLS) {
+            const int ng = min(NQ_CELLS, tot - g);
+            __syncthreads();
+            // quadrature offsets of the group's cells, 112 points each
+            for (int t = tid; t < ng * NQ_PTS; t += CT_THREADS) {
+                const int c = t / NQ_PTS, k = t % NQ_PTS;
+                const int j = s_list[g + c];
+                const float4 g0 = L.panels.g0_h[j], g1 = L.panels.g1[j], g2 = L.panels.g2[j];
+                float3 off;
+                float wf;
+                rule_point(2, k, make_float3(g0.x, g0.y, g0.z), make_float3(g1.x, g1.y, g1.z),
+                           make_float3(g2.x, g2.y, g2.z), off, wf);
+                const float w = L.panels.c_a[j].w * L.sigma[j] * wf;
+                SrcPk sp;
+                sp.xx = pk(off.x, off.x); sp.yy = pk(off.y, off.y); sp.zz = pk(off.z, off.z); sp.qq = pk(w, w);
+                s_off[c][k] = sp;
+                if (k == 0) {
+                    const float4 ca = L.panels.c_a[j], cl = L.panels.c_lo[j];
+                    s_cell[c][0] = make_float4(ca.x, ca.y, ca.z, g0.w);
+                    s_cell[c][1] = make_float4(cl.x, cl.y, cl.z, 0.f);
+                }
+            }
+            __syncthreads();
+            u64 AX[2], AY[2], AZ[2], AV[2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
+            for (int c = 0; c < (warp_live ? ng : 0); ++c) {
+                const float4 ch = s_cell[c][0], cl = s_cell[c][1];
+                // exact target - centroid per pack; targets within h get a
+                // 1e30 m^2 softening, i.e. no term here (theirs is the closed form)
+                u64 DX[2], DY[2], DZ[2], EP[2];
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    DX[p] = sub2(sub2(TX[p], pk(ch.x, ch.x)), pk(cl.x, cl.x));
+                    DY[p] = sub2(sub2(TY[p], pk(ch.y, ch.y)), pk(cl.y, cl.y));
+                    DZ[p] = sub2(sub2(TZ[p], pk(ch.z, ch.z)), pk(cl.z, cl.z));
+                    u64 d2 = fma2(DZ[p], DZ[p], fma2(DY[p], DY[p], mul2(DX[p], DX[p])));
+                    float da, db;
+                    upk(d2, da, db);
+                    EP[p] = pk(da < ch.w ? 1e30f : 0.0f, db < ch.w ? 1e30f : 0.0f);
+                }
+#pragma unroll 4
+                for (int k = 0; k < NQ_PTS; ++k) {
+                    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&s_off[c][k].xx);
+                    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&s_off[c][k].zz);
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        u64 dx = sub2(DX[p], a.x);
+                        u64 dy = sub2(DY[p], a.y);
+                        u64 dz = sub2(DZ[p], b.x);
+                        u64 r2 = fma2(dx, dx, EP[p]);
+                        r2 = fma2(dy, dy, r2);
+                        r2 = fma2(dz, dz, r2);
+                        float ra, rb;
+                        upk(r2, ra, rb);
+                        u64 inv = pk(rsq(ra), rsq(rb));
+                        u64 s = mul2(b.y, inv);
+                        u64 s3 = mul2(s, mul2(inv, inv));
+                        AX[p] = fma2(dx, s3, AX[p]);
+                        AY[p] = fma2(dy, s3, AY[p]);
+                        AZ[p] = fma2(dz, s3, AZ[p]);
+                        if (WANT_V) AV[p] = add2(AV[p], s);
+                    }
+                }
+            }
+            if (COUNT && tid == 0) cntQ += ng;
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float a0, a1;
+                upk(AX[p], a0, a1); two_sum_acc(S[2 * p][0], C[2 * p][0], a0); two_sum_acc(S[2 * p + 1][0], C[2 * p + 1][0], a1);
+                upk(AY[p], a0, a1); two_sum_acc(S[2 * p][1], C[2 * p][1], a0); two_sum_acc(S[2 * p + 1][1], C[2 * p + 1][1], a1);
+                upk(AZ[p], a0, a1); two_sum_acc(S[2 * p][2], C[2 * p][2], a0); two_sum_acc(S[2 * p + 1][2], C[2 * p + 1][2], a1);
+                if (WANT_V) { upk(AV[p], a0, a1); two_sum_acc(S[2 * p][3], C[2 * p][3], a0); two_sum_acc(S[2 * p + 1][3], C[2 * p + 1][3], a1); }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CT_TPT; ++k) {
+        if (ti[k] < 0) continue;
+        float4 e;
+        e.x = (float)((double)S[k][0] + (double)C[k][0]);
+        e.y = (float)((double)S[k][1] + (double)C[k][1]);
+        e.z = (float)((double)S[k][2] + (double)C[k][2]);
+        e.w = WANT_V ? (float)((double)S[k][3] + (double)C[k][3]) : 0.f;
+        L.E_out[ti[k]] = e;
+    }
+    if (COUNT && L.counters && tid == 0) atomicAdd(&L.counters[3], cntQ);
+}
+
+// far cells as quadrature-point sources, in the block's frame
+template <bool WANT_V, bool COUNT>
+__global__ void __launch_bounds__(CT_THREADS)
+cell_kernel(FieldLaunch L)
+{
+    __shared__ SrcPk s_pts[CT_MAXPTS];
+    __shared__ PanTile s_pan[CT_CHUNK];
+    __shared__ int s_n[CT_CHUNK], s_off[CT_CHUNK + 1];
+    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
+    int base, end;
+    if (!block_range(L, nt, base, end)) return;
+    float tx[CT_TPT], ty[CT_TPT], tz[CT_TPT];
+    int ti[CT_TPT];
+    BlockFrame F;
+    block_targets(L, end, base, tx, ty, tz, ti, F);
+    // warps whose target slots are all padding skip the arithmetic
+    const bool warp_live = base + (int)(threadIdx.x & ~31u) < end;
+    const float3 o = F.o;
+    float S[CT_TPT][4], C[CT_TPT][4];
+#pragma unroll
+    for (int k = 0; k < CT_TPT; ++k) {
+        int ic = ti[k] >= 0 ? ti[k] : 0;
+        float4 e = L.E_out[ic];                    // near part + e_ext
+        S[k][0] = e.x; S[k][1] = e.y; S[k][2] = e.z; S[k][3] = WANT_V ? e.w : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) C[k][c] = 0.f;
+    }
+    u64 TX[2], TY[2], TZ[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        TX[p] = pk(tx[2 * p] - o.x, tx[2 * p + 1] - o.x);
+        TY[p] = pk(ty[2 * p] - o.y, ty[2 * p + 1] - o.y);
+        TZ[p] = pk(tz[2 * p] - o.z, tz[2 * p + 1] - o.z);
+    }
+    unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0;
+    const int np = L.panels.np;
+    const int tid = threadIdx.x;
+    for (int pb = 0; pb < np; pb += CT_CHUNK) {
+        __syncthreads();
+        if (tid < 32) {
+            // warp 0: tier of each cell of the chunk, point counts, offsets
+            const int j = pb + tid;
+            int n = 0;
+            if (j < np) {
+                const float4 ca = L.panels.c_a[j], cl = L.panels.c_lo[j];
+                const float sg = L.sigma[j];
+                PanTile t;
+                t.cq = make_float4((ca.x - o.x) + cl.x, (ca.y - o.y) + cl.y, (ca.z - o.z) + cl.z, ca.w * sg);
+                t.g0 = L.panels.g0_h[j];
+                t.g1 = L.panels.g1[j];
+                t.g2 = L.panels.g2[j];
+                s_pan[tid] = t;
+                const float h2 = t.g0.w;
+                if (!cell_is_near(ca, h2, F)) {
+                    const float d2 = box_d2(ca.x, ca.y, ca.z, F.lo, F.hi);
+                    n = d2 >= TIER_1PT_H2 * h2 ? 1 : d2 >= TIER_3PT_H2 * h2 ? 3 : d2 >= TIER_7PT_H2 * h2 ? 7 : 28;
+                }
+            }
+            int inc = n;
+            for (int q = 1; q < 32; q <<= 1) {
+                int v = __shfl_up_sync(0xffffffffu, inc, q);
+                if (tid >= q) inc += v;
+            }
+            s_n[tid] = n;
+            s_off[tid] = inc - n;
+            if (tid == 31) s_off[CT_CHUNK] = inc;
+        }
+        __syncthreads();
+        const int npts = s_off[CT_CHUNK];
+        // emit: 4 threads per cell
+        {
+            const int c = tid >> 2, sub = tid & 3;
+            const int n = s_n[c];
+            if (n) {
+                const PanTile t = s_pan[c];
+                const float q = t.cq.w;
+                const float3 G0 = make_float3(t.g0.x, t.g0.y, t.g0.z), G1 = make_float3(t.g1.x, t.g1.y, t.g1.z),
+                             G2 = make_float3(t.g2.x, t.g2.y, t.g2.z);
+                for (int k = sub; k < n; k += 4) {
+                    float3 off;
+                    float w;
+                    if (n == 1) { off = make_float3(0.f, 0.f, 0.f); w = q; }
+                    else if (n == 3) {
+                        const float3 g = k == 0 ? G0 : (k == 1 ? G1 : G2);
+                        off = make_float3(0.5f * g.x, 0.5f * g.y, 0.5f * g.z);
+                        w = q * (1.0f / 3.0f);
+                    } else {
+                        float wf;
+                        rule_point(n == 7 ? 0 : 1, k, G0, G1, G2, off, wf);
+                        w = q * wf;
+                    }
+                    const float px = t.cq.x + off.x, py = t.cq.y + off.y, pz = t.cq.z + off.z;
+                    SrcPk sp;
+                    sp.xx = pk(px, px); sp.yy = pk(py, py); sp.zz = pk(pz, pz); sp.qq = pk(w, w);
+                    s_pts[s_off[c] + k] = sp;
+                }
+            }
+            const int pad = (npts + 3) & ~3;
+            if (tid < pad - npts) {
+                SrcPk sp;
+                sp.xx = sp.yy = sp.zz = pk(1e18f, 1e18f);
+                sp.qq = pk(0.f, 0.f);
+                s_pts[npts + tid] = sp;
+            }
+        }
+        if (COUNT && tid < 32) {
+            const int n = s_n[tid];
+            cnt1 += n == 1; cnt3 += n == 3; cnt7 += n >= 7;
+        }
+        __syncthreads();
+        const int npad = warp_live ? (npts + 3) & ~3 : 0;
+        if (npad == 0) continue;
+        u64 AX[2], AY[2], AZ[2], AV[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
+#pragma unroll 4
+        for (int jj = 0; jj < npad; ++jj) {
+            const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&s_pts[jj].xx);
+            const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&s_pts[jj].zz);
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                u64 dx = sub2(TX[p], a.x);
+                u64 dy = sub2(TY[p], a.y);
+                u64 dz = sub2(TZ[p], b.x);
+                u64 r2 = mul2(dx, dx);
+                r2 = fma2(dy, dy, r2);
+                r2 = fma2(dz, dz, r2);
+                float ra, rb;
+                upk(r2, ra, rb);
+                u64 inv = pk(rsq(ra), rsq(rb));
+                u64 s = mul2(b.y, inv);
+                u64 s3 = mul2(s, mul2(inv, inv));
+                AX[p] = fma2(dx, s3, AX[p]);
+                AY[p] = fma2(dy, s3, AY[p]);
+                AZ[p] = fma2(dz, s3, AZ[p]);
+                if (WANT_V) AV[p] = add2(AV[p], s);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            float a0, a1;
+            upk(AX[p], a0, a1); two_sum_acc(S[2 * p][0], C[2 * p][0], a0); two_sum_acc(S[2 * p + 1][0], C[2 * p + 1][0], a1);
+            upk(AY[p], a0, a1); two_sum_acc(S[2 * p][1], C[2 * p][1], a0); two_sum_acc(S[2 * p + 1][1], C[2 * p + 1][1], a1);
+            upk(AZ[p], a0, a1); two_sum_acc(S[2 * p][2], C[2 * p][2], a0); two_sum_acc(S[2 * p + 1][2], C[2 * p + 1][2], a1);
+            if (WANT_V) { upk(AV[p], a0, a1); two_sum_acc(S[2 * p][3], C[2 * p][3], a0); two_sum_acc(S[2 * p + 1][3], C[2 * p + 1][3], a1); }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < CT_TPT; ++k) {
+        if (ti[k] < 0) continue;
+        float4 e;
+        e.x = (float)((double)S[k][0] + (double)C[k][0]);
+        e.y = (float)((double)S[k][1] + (double)C[k][1]);
+        e.z = (float)((double)S[k][2] + (double)C[k][2]);
+        e.w = WANT_V ? (float)((double)S[k][3] + (double)C[k][3]) : 0.f;
+        L.E_out[ti[k]] = e;
+    }
+    if (COUNT && L.counters) {
+        atomicAdd(&L.counters[1], cnt1);
+        atomicAdd(&L.counters[2], cnt3);
+        atomicAdd(&L.counters[3], cnt7);
+    }
+}
+
+// ---------------------------------------------------------------- all-pairs kernel
+// E_out[i] = init + k_C sum_{p != i} q_p (r_i - r_p) / (|r_i - r_p|^2 + eps^2)^(3/2)
+// init = E_out[i] when the cell kernels ran first (ADD), else e_ext.
+// The compensated accumulators and the recombination proposals live in shared
+// memory (touched once per tile / rarely), which keeps the register count low
+// enough for FT_MINB resident blocks per SM.
+#define FT_MINB 6
+
+template <bool WANT_V, bool RECOMB, bool ADD>
+__global__ void __launch_bounds__(FT_THREADS, FT_MINB)
+nbody_kernel(FieldLaunch L)
+{
+    __shared__ SrcPk s_src[FT_SRC_TILE];
+    __shared__ float s_acc[2][4][FT_TPT][FT_THREADS];          // [S|C][component][target][thread]
+    __shared__ unsigned long long s_best[RECOMB ? FT_TPT : 1][FT_THREADS];
+
+    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
+    const int ns = L.ns_dev ? *L.ns_dev : L.ns;
+    const int base = blockIdx.x * FT_BLOCK_TARGETS;
+    if (base >= nt) return;
+    const int tid = threadIdx.x;
+    constexpr int NC = WANT_V ? 4 : 3;
+
+    float rc2f[FT_TPT];
+    u64 TX[2], TY[2], TZ[2];
+#pragma unroll
+    for (int k = 0; k < FT_TPT; ++k) {
+        int i = base + k * FT_THREADS + tid;
+        int ic = i < nt ? i : (nt - 1);
+        float4 p = L.targets[ic];
+        if (k & 1) {
+            TX[k >> 1] = pk(__uint_as_float((uint32_t)TX[k >> 1]), p.x);
+            TY[k >> 1] = pk(__uint_as_float((uint32_t)TY[k >> 1]), p.y);
+            TZ[k >> 1] = pk(__uint_as_float((uint32_t)TZ[k >> 1]), p.z);
+        } else {
+            TX[k >> 1] = (u64)__float_as_uint(p.x);
+            TY[k >> 1] = (u64)__float_as_uint(p.y);
+            TZ[k >> 1] = (u64)__float_as_uint(p.z);
+        }
+        float e[4];
+        if (ADD) {
+            float4 q = L.E_out[ic];
+            e[0] = q.x; e[1] = q.y; e[2] = q.z; e[3] = q.w;
+        } else {
+            e[0] = L.e_ext.x; e[1] = L.e_ext.y; e[2] = L.e_ext.z; e[3] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { s_acc[0][c][k][tid] = e[c]; s_acc[1][c][k][tid] = 0.f; }
+        rc2f[k] = -1.0f;
+        if (RECOMB) {
+            s_best[RECOMB ? k : 0][tid] = ~0ull;
+            if (i < nt && L.species[i] == OBEM_ELECTRON)
+                rc2f[k] = (L.rc2 + L.eps2) * (1.0f + 3.814697265625e-06f) + 1e-30f;
+        }
+    }
+
+    const float kC = (float)OBEM_KC;
+    const u64 EPS2 = pk(L.eps2, L.eps2);
     for (int sb = 0; sb < ns; sb += FT_SRC_TILE) {
         __syncthreads();
 #pragma unroll
@@ -472,6 +885,7 @@ nbody_kernel(FieldLaunch L)
         }
         __syncthreads();
         const bool diag = L.self_exclude && sb < base + FT_BLOCK_TARGETS && base < sb + FT_SRC_TILE;
+        float part[FT_TPT][4];
         if (!diag) {
             u64 AX[2], AY[2], AZ[2], AV[2];
 #pragma unroll
@@ -509,11 +923,14 @@ nbody_kernel(FieldLaunch L)
 #pragma unroll
                         for (int k = 0; k < FT_TPT; ++k) {
                             if (rc2f[k] < 0.f) continue;
-                            float ddx = __fsub_rn(tx[k], sx), ddy = __fsub_rn(ty[k], sy), ddz = __fsub_rn(tz[k], sz);
+                            float txk, tyk, tzk, t2;
+                            if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
+                            else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
+                            float ddx = __fsub_rn(txk, sx), ddy = __fsub_rn(tyk, sy), ddz = __fsub_rn(tzk, sz);
                             float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
                             if (d2 <= L.rc2) {
                                 u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
-                                if (key < best[k]) best[k] = key;
+                                if (key < s_best[RECOMB ? k : 0][tid]) s_best[RECOMB ? k : 0][tid] = key;
                             }
                         }
                     }
@@ -521,17 +938,15 @@ nbody_kernel(FieldLaunch L)
             }
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
-                float a0, a1;
-                upk(AX[p], a0, a1); two_sum_acc(S[2 * p][0], C[2 * p][0], a0); two_sum_acc(S[2 * p + 1][0], C[2 * p + 1][0], a1);
-                upk(AY[p], a0, a1); two_sum_acc(S[2 * p][1], C[2 * p][1], a0); two_sum_acc(S[2 * p + 1][1], C[2 * p + 1][1], a1);
-                upk(AZ[p], a0, a1); two_sum_acc(S[2 * p][2], C[2 * p][2], a0); two_sum_acc(S[2 * p + 1][2], C[2 * p + 1][2], a1);
-                if (WANT_V) { upk(AV[p], a0, a1); two_sum_acc(S[2 * p][3], C[2 * p][3], a0); two_sum_acc(S[2 * p + 1][3], C[2 * p + 1][3], a1); }
+                upk(AX[p], part[2 * p][0], part[2 * p + 1][0]);
+                upk(AY[p], part[2 * p][1], part[2 * p + 1][1]);
+                upk(AZ[p], part[2 * p][2], part[2 * p + 1][2]);
+                upk(AV[p], part[2 * p][3], part[2 * p + 1][3]);
             }
         } else {
             // tile holding some of this block's own targets: skip the self pair
-            float P[FT_TPT][4];
 #pragma unroll
-            for (int k = 0; k < FT_TPT; ++k) { P[k][0] = P[k][1] = P[k][2] = P[k][3] = 0.f; }
+            for (int k = 0; k < FT_TPT; ++k) { part[k][0] = part[k][1] = part[k][2] = part[k][3] = 0.f; }
             for (int jj = 0; jj < FT_SRC_TILE; ++jj) {
                 const int j = sb + jj;
                 float sx, sy, sz, sq, dum;
@@ -540,30 +955,39 @@ nbody_kernel(FieldLaunch L)
 #pragma unroll
                 for (int k = 0; k < FT_TPT; ++k) {
                     if (j == base + k * FT_THREADS + tid) continue;
-                    float dx = __fsub_rn(tx[k], sx), dy = __fsub_rn(ty[k], sy), dz = __fsub_rn(tz[k], sz);
+                    float txk, tyk, tzk, t2;
+                    if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
+                    else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
+                    float dx = __fsub_rn(txk, sx), dy = __fsub_rn(tyk, sy), dz = __fsub_rn(tzk, sz);
                     float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, L.eps2)));
                     float inv = rsq(r2);
                     float s = sq * inv;
                     float s3 = s * (inv * inv);
-                    P[k][0] = fmaf(dx, s3, P[k][0]);
-                    P[k][1] = fmaf(dy, s3, P[k][1]);
-                    P[k][2] = fmaf(dz, s3, P[k][2]);
-                    P[k][3] += s;
+                    part[k][0] = fmaf(dx, s3, part[k][0]);
+                    part[k][1] = fmaf(dy, s3, part[k][1]);
+                    part[k][2] = fmaf(dz, s3, part[k][2]);
+                    part[k][3] += s;
                     if (RECOMB && r2 < rc2f[k] && j < ns && L.species[j] == OBEM_CATION &&
                         !(L.birth[j] != 0u && L.birth[j] == L.step)) {
                         float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                         if (d2 <= L.rc2) {
                             u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
-                            if (key < best[k]) best[k] = key;
+                            if (key < s_best[RECOMB ? k : 0][tid]) s_best[RECOMB ? k : 0][tid] = key;
                         }
                     }
                 }
             }
-#pragma unroll
-            for (int k = 0; k < FT_TPT; ++k)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) two_sum_acc(S[k][c], C[k][c], P[k][c]);
         }
+        // fold the tile's partial sums into the compensated accumulators
+#pragma unroll
+        for (int k = 0; k < FT_TPT; ++k)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                float sv = s_acc[0][c][k][tid], cv = s_acc[1][c][k][tid];
+                two_sum_acc(sv, cv, part[k][c]);
+                s_acc[0][c][k][tid] = sv;
+                s_acc[1][c][k][tid] = cv;
+            }
     }
 
 #pragma unroll
@@ -571,12 +995,12 @@ nbody_kernel(FieldLaunch L)
         int i = base + k * FT_THREADS + tid;
         if (i >= nt) continue;
         float4 e;
-        e.x = (float)((double)S[k][0] + (double)C[k][0]);
-        e.y = (float)((double)S[k][1] + (double)C[k][1]);
-        e.z = (float)((double)S[k][2] + (double)C[k][2]);
-        e.w = WANT_V ? (float)((double)S[k][3] + (double)C[k][3]) : 0.f;
+        e.x = (float)((double)s_acc[0][0][k][tid] + (double)s_acc[1][0][k][tid]);
+        e.y = (float)((double)s_acc[0][1][k][tid] + (double)s_acc[1][1][k][tid]);
+        e.z = (float)((double)s_acc[0][2][k][tid] + (double)s_acc[1][2][k][tid]);
+        e.w = WANT_V ? (float)((double)s_acc[0][3][k][tid] + (double)s_acc[1][3][k][tid]) : 0.f;
         L.E_out[i] = e;
-        if (RECOMB) L.prop[i] = best[k];
+        if (RECOMB) L.prop[i] = s_best[RECOMB ? k : 0][tid];
     }
 }
 
@@ -615,11 +1039,22 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             const int nb = (capacity_targets + 255) / 256;
             bin_count_kernel<<<nb, 256, 0, s>>>(L, lo, sc, ctx->s_code, ctx->s_hist);
             bin_scan_kernel<<<1, 1024, 0, s>>>(ctx->s_hist);
+            block_list_kernel<<<1, 1024, 0, s>>>(ctx->s_hist, L.nt, L.nt_dev, (int2 *)L.blocks, (int32_t *)L.nblocks);
             bin_scatter_kernel<<<nb, 256, 0, s>>>(L, ctx->s_code, ctx->s_hist, (int32_t *)L.perm);
             OBEM_LAUNCH(ctx);
-            if (L.events) ctx->launches += 3;
+            if (L.events) ctx->launches += 4;
         }
-        dim3 cgrid((capacity_targets + CT_BLOCK - 1) / CT_BLOCK);
+        const int nsuper = capacity_targets < OBEM_NSUPER ? capacity_targets : OBEM_NSUPER;
+        dim3 cgrid((capacity_targets + CT_BLOCK - 1) / CT_BLOCK + (L.blocks ? nsuper : 0));
+        if (L.events) cudaEventRecord(L.events[4], s);
+        if (L.want_v) {
+            if (L.counters) { near_closed_kernel<true, true><<<cgrid, CT_THREADS, 0, s>>>(L); near_quad_kernel<true, true><<<cgrid, CT_THREADS, 0, s>>>(L); }
+            else { near_closed_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L); near_quad_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L); }
+        } else {
+            if (L.counters) { near_closed_kernel<false, true><<<cgrid, CT_THREADS, 0, s>>>(L); near_quad_kernel<false, true><<<cgrid, CT_THREADS, 0, s>>>(L); }
+            else { near_closed_kernel<false, false><<<cgrid, CT_THREADS, 0, s>>>(L); near_quad_kernel<false, false><<<cgrid, CT_THREADS, 0, s>>>(L); }
+        }
+        if (L.events) cudaEventRecord(L.events[5], s);
         if (L.want_v) {
             if (L.counters) cell_kernel<true, true><<<cgrid, CT_THREADS, 0, s>>>(L);
             else cell_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L);
@@ -628,7 +1063,7 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             else cell_kernel<false, false><<<cgrid, CT_THREADS, 0, s>>>(L);
         }
         OBEM_LAUNCH(ctx);
-        if (L.events) ctx->launches++;
+        if (L.events) ctx->launches += 3;
     }
     if (L.events) cudaEventRecord(L.events[1], s);
     if (charges) {

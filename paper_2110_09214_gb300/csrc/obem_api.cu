@@ -28,10 +28,10 @@ static void free_mesh(obem_ctx *c)
     c->h_kind = c->h_group = NULL;
     c->h_tri = c->h_em = c->h_ep = NULL;
     free_dev(c->d_c_a); free_dev(c->d_g0_h); free_dev(c->d_g1); free_dev(c->d_g2);
-    free_dev(c->d_nrm); free_dev(c->d_v64); free_dev(c->d_kind); free_dev(c->d_group);
+    free_dev(c->d_nrm); free_dev(c->d_c_lo); free_dev(c->d_v64); free_dev(c->d_kind); free_dev(c->d_group);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
-    c->d_c_a = c->d_g0_h = c->d_g1 = c->d_g2 = c->d_nrm = NULL;
+    c->d_c_a = c->d_g0_h = c->d_g1 = c->d_g2 = c->d_nrm = c->d_c_lo = NULL;
     c->d_v64 = NULL;
     c->d_kind = c->d_group = NULL;
     c->d_A = c->d_LU = NULL;
@@ -93,6 +93,8 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->s_code, sizeof(uint32_t) * cap);
     ALLOC(c->s_perm, sizeof(int32_t) * cap);
     ALLOC(c->s_hist, sizeof(int32_t) * OBEM_NBINS);
+    ALLOC(c->s_blocks, sizeof(int2) * ((size_t)cap / 512 + 2 + (cap < OBEM_NSUPER ? cap : OBEM_NSUPER)));
+    ALLOC(c->s_nblocks, sizeof(int32_t) * (OBEM_NSUPER + 8));
 #undef ALLOC
     (void)bytes;
     *out = c;
@@ -107,10 +109,10 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->s_E); free_dev(c->s_prop); free_dev(c->s_ionkey); free_dev(c->s_keep);
     free_dev(c->s_nsp); free_dev(c->s_blk); free_dev(c->s_ctl); free_dev(c->o_pos);
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
-    free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist);
+    free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->prof_ev) {
-        for (int i = 0; i < 4 * OBEM_PROF_MAX; ++i) cudaEventDestroy(c->prof_ev[i]);
+        for (int i = 0; i < OBEM_PROF_EV * OBEM_PROF_MAX; ++i) cudaEventDestroy(c->prof_ev[i]);
         free(c->prof_ev);
     }
     free_dev(c->d_counters);
@@ -121,8 +123,8 @@ extern "C" int obem_profile(obem_ctx *c, int32_t enable)
 {
     if (!c) return OBEM_ERR_ARG;
     if (enable && !c->prof_ev) {
-        c->prof_ev = (cudaEvent_t *)calloc(4 * OBEM_PROF_MAX, sizeof(cudaEvent_t));
-        for (int i = 0; i < 4 * OBEM_PROF_MAX; ++i) OBEM_CUDA(c, cudaEventCreate(&c->prof_ev[i]));
+        c->prof_ev = (cudaEvent_t *)calloc(OBEM_PROF_EV * OBEM_PROF_MAX, sizeof(cudaEvent_t));
+        for (int i = 0; i < OBEM_PROF_EV * OBEM_PROF_MAX; ++i) OBEM_CUDA(c, cudaEventCreate(&c->prof_ev[i]));
         OBEM_CUDA(c, cudaMalloc((void **)&c->d_counters, sizeof(unsigned long long) * 5));
     }
     if (enable) {
@@ -138,18 +140,19 @@ extern "C" int obem_profile(obem_ctx *c, int32_t enable)
 extern "C" int obem_stage_times(obem_ctx *c, double *ms, int64_t *counts)
 {
     if (!c || !ms || !counts) return OBEM_ERR_ARG;
-    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+    for (int k = 0; k < 5; ++k) ms[k] = 0.0;
     for (int k = 0; k < 7; ++k) counts[k] = 0;
     if (!c->prof_ev) return OBEM_OK;
     int n = c->prof_n < OBEM_PROF_MAX ? c->prof_n : OBEM_PROF_MAX;
     for (int r = 0; r < n; ++r) {
-        cudaEvent_t *e = c->prof_ev + 4 * r;
+        cudaEvent_t *e = c->prof_ev + OBEM_PROF_EV * r;
         OBEM_CUDA(c, cudaEventSynchronize(e[3]));
         float t;
         OBEM_CUDA(c, cudaEventElapsedTime(&t, e[0], e[1])); ms[0] += t;
         OBEM_CUDA(c, cudaEventElapsedTime(&t, e[1], e[2])); ms[1] += t;
         OBEM_CUDA(c, cudaEventElapsedTime(&t, e[2], e[3])); ms[2] += t;
         OBEM_CUDA(c, cudaEventElapsedTime(&t, e[0], e[3])); ms[3] += t;
+        OBEM_CUDA(c, cudaEventElapsedTime(&t, e[4], e[5])); ms[4] += t;
     }
     unsigned long long h[5];
     OBEM_CUDA(c, cudaMemcpy(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost));
@@ -295,6 +298,7 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
     float4 *g1 = (float4 *)malloc(sizeof(float4) * np);
     float4 *g2 = (float4 *)malloc(sizeof(float4) * np);
     float4 *nr = (float4 *)malloc(sizeof(float4) * np);
+    float4 *cl = (float4 *)malloc(sizeof(float4) * np);
     for (int i = 0; i < np; ++i) {
         const double *v = tri + 9 * (size_t)i;
         double cc[3], e1[3], e2[3], nn[3];
@@ -308,7 +312,7 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
         nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
         double a2 = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
         if (!(a2 > 0.0)) {
-            free(ca); free(g0); free(g1); free(g2); free(nr);
+            free(ca); free(g0); free(g1); free(g2); free(nr); free(cl);
             free_mesh(c);
             return obem_fail(c, OBEM_ERR_ARG, "mesh: cell %d is degenerate", i);
         }
@@ -323,6 +327,8 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
         g1[i] = make_float4((float)(v[3] - cc[0]), (float)(v[4] - cc[1]), (float)(v[5] - cc[2]), 0.f);
         g2[i] = make_float4((float)(v[6] - cc[0]), (float)(v[7] - cc[1]), (float)(v[8] - cc[2]), 0.f);
         nr[i] = make_float4((float)(nn[0] / a2), (float)(nn[1] / a2), (float)(nn[2] / a2), (float)kind[i]);
+        cl[i] = make_float4((float)(cc[0] - (double)ca[i].x), (float)(cc[1] - (double)ca[i].y),
+                            (float)(cc[2] - (double)ca[i].z), 0.f);
     }
     int rc = OBEM_OK;
     size_t f4 = sizeof(float4) * np;
@@ -338,11 +344,12 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
     UP(c->d_g1, g1, f4);
     UP(c->d_g2, g2, f4);
     UP(c->d_nrm, nr, f4);
+    UP(c->d_c_lo, cl, f4);
     UP(c->d_v64, tri, sizeof(double) * 9 * np);
     UP(c->d_kind, kind, sizeof(int) * np);
     UP(c->d_group, group, sizeof(int) * np);
 #undef UP
-    free(ca); free(g0); free(g1); free(g2); free(nr);
+    free(ca); free(g0); free(g1); free(g2); free(nr); free(cl);
     if (rc == OBEM_OK && cudaMalloc((void **)&c->d_sigma, sizeof(float) * np) != cudaSuccess)
         rc = obem_fail(c, OBEM_ERR_CUDA, "mesh: sigma allocation failed");
     if (rc != OBEM_OK) free_mesh(c);
@@ -353,6 +360,7 @@ static PanelsDev panels_of(const obem_ctx *c)
 {
     PanelsDev p;
     p.c_a = c->d_c_a; p.g0_h = c->d_g0_h; p.g1 = c->d_g1; p.g2 = c->d_g2; p.nrm = c->d_nrm;
+    p.c_lo = c->d_c_lo;
     p.v64 = c->d_v64;
     p.np = c->np;
     return p;
@@ -407,6 +415,8 @@ extern "C" int obem_field_eval(obem_ctx *c, const float *targets, int32_t nt, co
     // the scratch holds a spatial order for up to `capacity` targets; larger
     // calls keep the given order (same results, slower cell kernel)
     L.perm = (sigma && nt <= c->cap) ? c->s_perm : NULL;
+    L.blocks = L.perm ? c->s_blocks : NULL;
+    L.nblocks = L.perm ? c->s_nblocks : NULL;
     return obem_launch_field(c, L, nt, (cudaStream_t)stream);
 }
 
@@ -427,9 +437,11 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
     int partners_done = 0;
     cudaEvent_t *ev = NULL;
     if (c->prof_on) {
-        ev = c->prof_ev + 4 * (c->prof_n % OBEM_PROF_MAX);
+        ev = c->prof_ev + OBEM_PROF_EV * (c->prof_n % OBEM_PROF_MAX);
         if (c->prof_n < OBEM_PROF_MAX) c->prof_n++;
         cudaEventRecord(ev[0], s);
+        cudaEventRecord(ev[4], s);
+        cudaEventRecord(ev[5], s);
     }
     int want_cells = (c->cfg.flags & OBEM_STEP_CELL_FIELD) && c->sigma_valid;
     int want_nbody = (c->cfg.flags & OBEM_STEP_SPACE_CHARGE) != 0;
@@ -447,6 +459,8 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         L.sigma = want_cells ? c->d_sigma : NULL;
         L.panels = panels_of(c);
         L.perm = want_cells ? c->s_perm : NULL;
+        L.blocks = want_cells ? c->s_blocks : NULL;
+        L.nblocks = want_cells ? c->s_nblocks : NULL;
         L.E_out = c->s_E;
         L.e_ext = make_float3((float)c->cfg.e_ext[0], (float)c->cfg.e_ext[1], (float)c->cfg.e_ext[2]);
         L.want_v = 0;

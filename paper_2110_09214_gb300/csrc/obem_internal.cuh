@@ -50,8 +50,10 @@ struct GasDev {
 //   g2   = (v2 - c, 0)
 //   v64  = FP64 vertices [np][9] for the near-field closed form
 //   nrm  = (nx, ny, nz, kind)
+//   c_lo = centroid - float(centroid), so that (c_a.xyz + c_lo.xyz) carries the
+//          centroid to ~2^-48 relative (differences to nearby targets stay exact)
 struct PanelsDev {
-    const float4 *c_a, *g0_h, *g1, *g2, *nrm;
+    const float4 *c_a, *g0_h, *g1, *g2, *nrm, *c_lo;
     const double *v64;
     int np;
 };
@@ -78,7 +80,7 @@ struct obem_ctx {
     int np, n_groups;
     int *h_kind, *h_group;
     double *h_tri, *h_em, *h_ep;
-    float4 *d_c_a, *d_g0_h, *d_g1, *d_g2, *d_nrm;
+    float4 *d_c_a, *d_g0_h, *d_g1, *d_g2, *d_nrm, *d_c_lo;
     double *d_v64;
     int *d_kind, *d_group;
     float bbox_lo[3], bbox_hi[3];   // of the cell vertices (target binning grid)
@@ -106,19 +108,22 @@ struct obem_ctx {
     uint32_t *o_id, *o_birth;
     uint8_t *o_sp;
     int cap;
-    // target binning (Morton order of a 64^3 grid) for the cell kernel
+    // target binning (Morton order of a 64^3 grid) for the cell kernels
     uint32_t *s_code;
     int32_t *s_perm;
     int32_t *s_hist;
+    int2 *s_blocks;        // cell-kernel blocks: (first sorted target, count)
+    int32_t *s_nblocks;    // [1] number of blocks, [2..] scan scratch
     // stage timing (obem_profile)
     int prof_on;
     int prof_n;                      // recorded steps (ring of OBEM_PROF_MAX)
-    cudaEvent_t *prof_ev;            // [OBEM_PROF_MAX][4]
+    cudaEvent_t *prof_ev;            // [OBEM_PROF_MAX][OBEM_PROF_EV]
     unsigned long long *d_counters;  // [5] pairs, 1pt, 3pt, 7pt, closed form
     long long launches;              // kernels launched by recorded steps
     long long steps_recorded;
 };
 #define OBEM_PROF_MAX 256
+#define OBEM_PROF_EV 6   // step start, after cells, after pairs, step end, near start, near end
 
 // ---------------------------------------------------------------- error helpers
 int obem_fail(obem_ctx *ctx, int code, const char *fmt, ...);
@@ -161,13 +166,19 @@ struct FieldLaunch {
     unsigned long long *prop;
     // optional tier counters [5]: charge pairs, 1-point, 3-point, 7-point, closed-form
     unsigned long long *counters;
-    // optional events: [1] recorded after the cell kernel, [2] after the all-pairs kernel
+    // optional events: [1] after the cell kernels, [2] after the all-pairs kernel,
+    // [4] / [5] around the near-cell kernel
     cudaEvent_t *events;
-    // cell kernel: target order (spatially binned) or NULL for the given order
+    // cell kernels: target order (spatially binned) or NULL for the given order,
+    // and the block list over that order (NULL: blocks of CT_BLOCK in order)
     const int32_t *perm;
+    const int2 *blocks;
+    const int32_t *nblocks;
 };
 #define OBEM_BINS_PER_AXIS 64
 #define OBEM_NBINS (OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS)
+#define OBEM_SUPER_SHIFT 3                        // super-bin = 2 x 2 x 2 bins
+#define OBEM_NSUPER (OBEM_NBINS >> OBEM_SUPER_SHIFT)
 int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets, cudaStream_t s);
 
 // step.cu
