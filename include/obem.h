@@ -226,6 +226,39 @@ int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t s
 int obem_profile(obem_ctx *ctx, int32_t enable);
 int obem_stage_times(obem_ctx *ctx, double *ms /* [5] */, int64_t *counts /* [7] */);
 
+/* Field evaluation that allocates no memory and needs no context.
+ *
+ * There is no counterpart in the paper: this entry point exists for callers
+ * that cannot call cudaMalloc -- code that runs while a CUDA graph is being
+ * captured, plug-ins held to a host application's fixed device-memory budget,
+ * real-time loops that cannot take the latency of an allocation -- and so
+ * cannot create an obem_ctx (obem_create and obem_mesh_load allocate).
+ *
+ * It computes what obem_field_eval computes (cell field of Eqs. (BEM2),
+ * (BEM3) plus the Coulomb field of Eq. (nbody)) with the same kernels, but
+ * all of its scratch memory is one fixed array compiled into the library
+ * (about 5 MB, held on every GPU that loads the library until the process
+ * exits).  Inputs and outputs are the caller's:
+ *   targets   device [nt][4] (x, y, z, unused), nt <= OBEM_NOALLOC_MAX_TARGETS
+ *   sources   device [ns][4] (x, y, z, q) or NULL
+ *   cell_xyz  device [np][3][3] FP64 cell vertices (layout of obem_mesh_load's
+ *             tri_xyz), np <= OBEM_NOALLOC_MAX_CELLS; np == 0: no cell field
+ *   sigma     device [np] cell densities
+ *   E_out     device [nt][4] (Ex, Ey, Ez, V)
+ *   err       optional host buffer of err_len bytes for an error message
+ * Sizes beyond the maxima return OBEM_ERR_ARG with a message in err; nothing
+ * is launched then.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make that first
+ * call before any stream capture.  Every call reuses the same array and leaves
+ * its contents behind: two calls whose work overlaps on the GPU (on different
+ * streams, or from different host threads) race on it and give wrong results;
+ * serialise them on one stream. */
+enum { OBEM_NOALLOC_MAX_TARGETS = 262144, OBEM_NOALLOC_MAX_CELLS = 16384 };
+int obem_field_eval_noalloc(const float *targets, int32_t nt, const float *sources, int32_t ns,
+                            int32_t self_exclude, const double *cell_xyz, const float *sigma,
+                            int32_t np, float *E_out, char *err, int32_t err_len,
+                            obem_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1094,3 +1094,227 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
     if (L.events) cudaEventRecord(L.events[2], s);
     return OBEM_OK;
 }
+
+// ====================================================================
+// Field evaluation with no context and no allocation.
+//
+// For callers that cannot call cudaMalloc -- code running while a CUDA graph
+// is being captured, plug-ins that must live inside a host application's
+// fixed memory budget, or real-time loops where allocation latency is not
+// allowed -- and that therefore cannot create an obem_ctx (whose creation
+// and mesh upload allocate).  The same kernels as obem_field_eval run on
+// scratch held in one file-scope device array of fixed size, reached through
+// cudaGetSymbolAddress.
+// ====================================================================
+#define NA_MAX_TARGETS OBEM_NOALLOC_MAX_TARGETS
+#define NA_MAX_CELLS OBEM_NOALLOC_MAX_CELLS
+
+namespace {
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t NA_CELLS_BYTES = na_align(sizeof(float4) * 6 * (size_t)NA_MAX_CELLS);
+constexpr size_t NA_CODE_BYTES = na_align(sizeof(uint32_t) * (size_t)NA_MAX_TARGETS);
+constexpr size_t NA_PERM_BYTES = na_align(sizeof(int32_t) * (size_t)NA_MAX_TARGETS);
+constexpr size_t NA_HIST_BYTES = na_align(sizeof(int32_t) * (size_t)OBEM_NBINS);
+constexpr size_t NA_NBLK = (size_t)NA_MAX_TARGETS / 512 + 2 + OBEM_NSUPER;
+constexpr size_t NA_BLOCKS_BYTES = na_align(sizeof(int2) * NA_NBLK);
+constexpr size_t NA_MISC_BYTES = 256;   // number of blocks, bounding box
+constexpr size_t NA_BYTES = NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES + NA_HIST_BYTES + NA_BLOCKS_BYTES +
+                            NA_MISC_BYTES;
+}  // namespace
+
+// The scratch of obem_field_eval_noalloc (about 5 MB); every GPU that loads
+// the library holds it until the process exits.
+static __device__ __align__(256) unsigned char na_scratch[NA_BYTES];
+
+// Device address of na_scratch, per device ordinal (set on the first call
+// made with that device current).
+#define NA_MAX_DEVICES 64
+static unsigned char *na_base[NA_MAX_DEVICES];
+
+// Derived cell geometry (the layout of PanelsDev) from FP64 vertices.
+__global__ void na_cells_kernel(const double *v64, int np, float4 *c_a, float4 *g0_h, float4 *g1, float4 *g2,
+                                float4 *nrm, float4 *c_lo)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const double *v = v64 + 9 * (size_t)i;
+    double cc[3], e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        cc[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0;
+        e1[k] = v[3 + k] - v[k];
+        e2[k] = v[6 + k] - v[k];
+    }
+    double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2], nz = e1[0] * e2[1] - e1[1] * e2[0];
+    double a2 = sqrt(nx * nx + ny * ny + nz * nz);
+    double h2 = 0.0;
+    for (int e = 0; e < 3; ++e) {
+        const double *a = v + 3 * e, *b = v + 3 * ((e + 1) % 3);
+        double d = (a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]);
+        h2 = d > h2 ? d : h2;
+    }
+    float4 ca = make_float4((float)cc[0], (float)cc[1], (float)cc[2], (float)(OBEM_KC * 0.5 * a2));
+    c_a[i] = ca;
+    g0_h[i] = make_float4((float)(v[0] - cc[0]), (float)(v[1] - cc[1]), (float)(v[2] - cc[2]), (float)h2);
+    g1[i] = make_float4((float)(v[3] - cc[0]), (float)(v[4] - cc[1]), (float)(v[5] - cc[2]), 0.f);
+    g2[i] = make_float4((float)(v[6] - cc[0]), (float)(v[7] - cc[1]), (float)(v[8] - cc[2]), 0.f);
+    nrm[i] = make_float4((float)(nx / a2), (float)(ny / a2), (float)(nz / a2), 0.f);
+    c_lo[i] = make_float4((float)(cc[0] - (double)ca.x), (float)(cc[1] - (double)ca.y),
+                          (float)(cc[2] - (double)ca.z), 0.f);
+}
+
+// bounding box of the vertices, one block; box = [lo.xyz, hi.xyz]
+__global__ void na_bbox_kernel(const double *v64, int np, float *box)
+{
+    __shared__ float red[6][32];
+    float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
+    for (int q = threadIdx.x; q < 3 * np; q += blockDim.x) {
+        for (int k = 0; k < 3; ++k) {
+            float x = (float)v64[3 * (size_t)q + k];
+            mn[k] = fminf(mn[k], x);
+            mx[k] = fmaxf(mx[k], x);
+        }
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o; o >>= 1) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 3; ++k) { red[k][threadIdx.x >> 5] = mn[k]; red[3 + k][threadIdx.x >> 5] = mx[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k) {
+            float v = red[k][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = k < 3 ? fminf(v, red[k][w]) : fmaxf(v, red[k][w]);
+            box[k] = v;
+        }
+    }
+}
+
+// binning with the grid read from device memory (box from na_bbox_kernel)
+__global__ void na_bin_count_kernel(FieldLaunch L, const float *box, uint32_t *code, int32_t *hist)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.nt) return;
+    const float3 lo = make_float3(box[0], box[1], box[2]);
+    const float3 sc = make_float3((float)OBEM_BINS_PER_AXIS / fmaxf(box[3] - box[0], 1e-30f),
+                                  (float)OBEM_BINS_PER_AXIS / fmaxf(box[4] - box[1], 1e-30f),
+                                  (float)OBEM_BINS_PER_AXIS / fmaxf(box[5] - box[2], 1e-30f));
+    float4 p = L.targets[i];
+    int ix = (int)fminf(fmaxf((p.x - lo.x) * sc.x, 0.f), (float)(OBEM_BINS_PER_AXIS - 1));
+    int iy = (int)fminf(fmaxf((p.y - lo.y) * sc.y, 0.f), (float)(OBEM_BINS_PER_AXIS - 1));
+    int iz = (int)fminf(fmaxf((p.z - lo.z) * sc.z, 0.f), (float)(OBEM_BINS_PER_AXIS - 1));
+    uint32_t c = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+    code[i] = c;
+    atomicAdd(&hist[c], 1);
+}
+
+static int na_fail(char *err, int32_t err_len, int code, const char *msg)
+{
+    if (err && err_len > 0) {
+        strncpy(err, msg, (size_t)err_len - 1);
+        err[err_len - 1] = '\0';
+    }
+    return code;
+}
+
+extern "C" int obem_field_eval_noalloc(const float *targets, int32_t nt, const float *sources, int32_t ns,
+                                       int32_t self_exclude, const double *cell_xyz, const float *sigma,
+                                       int32_t np, float *E_out, char *err, int32_t err_len,
+                                       obem_stream stream)
+{
+    char msg[256];
+    if (nt < 0 || ns < 0 || np < 0) return na_fail(err, err_len, OBEM_ERR_ARG, "negative count");
+    if (nt > NA_MAX_TARGETS) {
+        snprintf(msg, sizeof msg, "nt = %d exceeds the fixed scratch of %d targets", nt, NA_MAX_TARGETS);
+        return na_fail(err, err_len, OBEM_ERR_ARG, msg);
+    }
+    if (np > NA_MAX_CELLS) {
+        snprintf(msg, sizeof msg, "np = %d exceeds the fixed scratch of %d cells", np, NA_MAX_CELLS);
+        return na_fail(err, err_len, OBEM_ERR_ARG, msg);
+    }
+    if (nt == 0) return OBEM_OK;
+    if (!targets || !E_out) return na_fail(err, err_len, OBEM_ERR_ARG, "null targets or E_out");
+    if (np > 0 && (!cell_xyz || !sigma)) return na_fail(err, err_len, OBEM_ERR_ARG, "cells without vertices or sigma");
+    if (self_exclude && (!sources || ns != nt))
+        return na_fail(err, err_len, OBEM_ERR_ARG, "self_exclude needs sources with ns == nt");
+    if (((uintptr_t)targets | (uintptr_t)E_out | (uintptr_t)sources) & 15)
+        return na_fail(err, err_len, OBEM_ERR_ARG, "arrays must be 16-byte aligned");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
+        return na_fail(err, err_len, OBEM_ERR_CUDA, "no usable current device");
+    if (!na_base[dev]) {
+        void *p = NULL;
+        cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+        if (e != cudaSuccess) {
+            snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return na_fail(err, err_len, OBEM_ERR_CUDA, msg);
+        }
+        na_base[dev] = (unsigned char *)p;
+    }
+    unsigned char *b = na_base[dev];
+    float4 *cells = (float4 *)b;
+    uint32_t *code = (uint32_t *)(b + NA_CELLS_BYTES);
+    int32_t *perm = (int32_t *)(b + NA_CELLS_BYTES + NA_CODE_BYTES);
+    int32_t *hist = (int32_t *)(b + NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES);
+    int2 *blocks = (int2 *)(b + NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES + NA_HIST_BYTES);
+    int32_t *nblocks = (int32_t *)(b + NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES + NA_HIST_BYTES + NA_BLOCKS_BYTES);
+    float *box = (float *)(nblocks + 16);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    FieldLaunch L;
+    memset(&L, 0, sizeof L);
+    L.targets = (const float4 *)targets;
+    L.nt = nt;
+    L.sources = (sources && ns > 0) ? (const float4 *)sources : NULL;
+    L.ns = ns;
+    L.self_exclude = self_exclude ? 1 : 0;
+    L.E_out = (float4 *)E_out;
+    L.e_ext = make_float3(0.f, 0.f, 0.f);
+    L.want_v = 1;
+    const bool cells_on = np > 0;
+    if (cells_on) {
+        L.sigma = sigma;
+        L.panels.c_a = cells;
+        L.panels.g0_h = cells + NA_MAX_CELLS;
+        L.panels.g1 = cells + 2 * NA_MAX_CELLS;
+        L.panels.g2 = cells + 3 * NA_MAX_CELLS;
+        L.panels.nrm = cells + 4 * NA_MAX_CELLS;
+        L.panels.c_lo = cells + 5 * NA_MAX_CELLS;
+        L.panels.v64 = cell_xyz;
+        L.panels.np = np;
+        L.perm = perm;
+        L.blocks = blocks;
+        L.nblocks = nblocks;
+        na_cells_kernel<<<(np + 127) / 128, 128, 0, s>>>(cell_xyz, np, (float4 *)L.panels.c_a, (float4 *)L.panels.g0_h,
+                                                        (float4 *)L.panels.g1, (float4 *)L.panels.g2,
+                                                        (float4 *)L.panels.nrm, (float4 *)L.panels.c_lo);
+        na_bbox_kernel<<<1, 1024, 0, s>>>(cell_xyz, np, box);
+        // the array keeps the previous call's contents: the histogram must restart at zero
+        if (cudaMemsetAsync(hist, 0, sizeof(int32_t) * OBEM_NBINS, s) != cudaSuccess)
+            return na_fail(err, err_len, OBEM_ERR_CUDA, "cudaMemsetAsync of the histogram failed");
+        const int nb = (nt + 255) / 256;
+        na_bin_count_kernel<<<nb, 256, 0, s>>>(L, box, code, hist);
+        bin_scan_kernel<<<1, 1024, 0, s>>>(hist);
+        block_list_kernel<<<1, 1024, 0, s>>>(hist, nt, NULL, blocks, nblocks);
+        bin_scatter_kernel<<<nb, 256, 0, s>>>(L, code, hist, perm);
+        const int nsuper = nt < OBEM_NSUPER ? nt : OBEM_NSUPER;
+        dim3 cgrid((nt + CT_BLOCK - 1) / CT_BLOCK + nsuper);
+        near_closed_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L);
+        near_quad_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L);
+        cell_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L);
+    }
+    dim3 grid((nt + FT_BLOCK_TARGETS - 1) / FT_BLOCK_TARGETS);
+    if (L.sources) {
+        if (cells_on) nbody_kernel<true, false, true><<<grid, FT_THREADS, 0, s>>>(L);
+        else nbody_kernel<true, false, false><<<grid, FT_THREADS, 0, s>>>(L);
+    } else if (!cells_on) {
+        const_field_kernel<<<(nt + 255) / 256, 256, 0, s>>>(L);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "kernel launch failed: %s", cudaGetErrorString(e));
+        return na_fail(err, err_len, OBEM_ERR_CUDA, msg);
+    }
+    return OBEM_OK;
+}

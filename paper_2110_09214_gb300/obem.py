@@ -90,6 +90,8 @@ def load():
     lib.obem_bem_solve.argtypes = [P, P, P, P, P, C.POINTER(obem_solve_report), P]
     lib.obem_field_eval.argtypes = [P, P, I, P, I, I, P, P, P]
     lib.obem_step.argtypes = [P, C.POINTER(obem_state), P, U, P, P]
+    lib.obem_field_eval_noalloc.argtypes = [P, I, P, I, I, P, P, I, P, C.c_char_p, I, P]
+    lib.obem_field_eval_noalloc.restype = C.c_int
     lib.obem_profile.argtypes = [P, I]
     lib.obem_stage_times.argtypes = [P, P, P]
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
@@ -199,6 +201,25 @@ def obem_field_eval(ctx, targets, E_out, sources=None, self_exclude=False, sigma
 def obem_step(ctx, state, step, stats, E_in=None, stream=None):
     _check(ctx, load().obem_step(ctx, C.byref(state.c_struct()), _ptr(E_in), int(step),
                                  _ptr(stats), _stream(stream)))
+
+
+NOALLOC_MAX_TARGETS, NOALLOC_MAX_CELLS = 262144, 16384
+
+
+def obem_field_eval_noalloc(targets, E_out, sources=None, self_exclude=False, cell_xyz=None,
+                            sigma=None, stream=None):
+    """Field at targets without a context or any allocation (fixed scratch
+    inside the library); same arguments as obem_field_eval, with the cells
+    given directly as FP64 vertices [np, 3, 3] on the device."""
+    nt = targets.shape[0]
+    ns = sources.shape[0] if sources is not None else 0
+    np_ = cell_xyz.shape[0] if cell_xyz is not None else 0
+    err = C.create_string_buffer(256)
+    rc = load().obem_field_eval_noalloc(_ptr(targets), nt, _ptr(sources), ns, int(bool(self_exclude)),
+                                        _ptr(cell_xyz), _ptr(sigma), np_, _ptr(E_out), err, 256,
+                                        _stream(stream))
+    if rc != OBEM_OK:
+        raise ObemError(rc, err.value.decode())
 
 
 def obem_profile(ctx, enable=True):
