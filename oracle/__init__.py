@@ -10,7 +10,8 @@ swarm-parameter fits of Sec. 4.1 (Eqs. (vd), (diffusion), (townsend)).
 
 Parity status of each function (see the test-suite for the pins):
   tri_integrals, panel_field, nbody_field, assemble, bem_solve, influence_rhs,
-  philox, step, swarm fits: pinned.
+  philox, step, swarm fits, tri_jacobian, field_jacobian, field_backward:
+  pinned.
   Swarm parameters of the synthetic argon-like gas: parity unpinned (no closed
   form; only GPU-vs-oracle agreement within 3 sigma and the Maxwell-model
   limits are checked).
@@ -50,6 +51,9 @@ def lib():
         _lib.or_tri_geometry.argtypes = [P, P, P, P]
         _lib.or_panel_field.argtypes = [I, P, P, I, P, P, P]
         _lib.or_nbody_field.argtypes = [I, P, I, P, I, C.c_double, P, P]
+        _lib.or_tri_jacobian.argtypes = [P, P, P]
+        _lib.or_field_jacobian.argtypes = [I, P, P, I, P, I, P, I, P]
+        _lib.or_field_backward.argtypes = [I, P, P, I, P, I, P, I, P, P, P, P]
         _lib.or_assemble.argtypes = [I, P, P, P, P, P]
         _lib.or_solve_gepp.argtypes = [I, P, P]
         _lib.or_solve_gepp.restype = I
@@ -111,6 +115,49 @@ def nbody_field(pts, src, self_exclude=False, soft=0.0):
     lib().or_nbody_field(len(pts), _p(pts), len(src), _p(src), int(self_exclude),
                          float(soft), _p(E), _p(V))
     return E, V
+
+
+def tri_jacobian(v, r):
+    """J[a, b] = dF_a/dr_b of the unit-density cell field F (closed form)."""
+    v = _c(v, np.float64).reshape(9)
+    r = _c(r, np.float64).reshape(3)
+    J = np.zeros(9)
+    lib().or_tri_jacobian(_p(v), _p(r), _p(J))
+    return J.reshape(3, 3)
+
+
+def _field_inputs(tri, sigma, pts, src):
+    tri = _c(np.zeros((0, 3, 3)) if tri is None else tri, np.float64).reshape(-1, 9)
+    sigma = _c(np.zeros(0) if sigma is None else sigma, np.float64).reshape(-1)
+    if len(sigma) == 0:
+        tri = tri[:0]
+    pts = _c(pts, np.float64).reshape(-1, 3)
+    src = _c(np.zeros((0, 4)) if src is None else src, np.float64).reshape(-1, 4)
+    return tri, sigma, pts, src
+
+
+def field_jacobian(tri, sigma, pts, src=None, self_exclude=False):
+    """dE/dr at pts (nt x 3 x 3) of cells with densities sigma plus point
+    charges src (derivatives of Eqs. (BEM3), (nbody))."""
+    tri, sigma, pts, src = _field_inputs(tri, sigma, pts, src)
+    J = np.zeros((len(pts), 9))
+    lib().or_field_jacobian(len(sigma), _p(tri), _p(sigma), len(pts), _p(pts), len(src), _p(src),
+                            int(self_exclude), _p(J))
+    return J.reshape(-1, 3, 3)
+
+
+def field_backward(tri, sigma, pts, src, self_exclude, g):
+    """Vector-Jacobian product of the field evaluation (E, V) at pts for the
+    upstream gradient g (nt x 4): returns dL/dsigma (np), dL/dpts (nt x 3)
+    and dL/dsrc (ns x 4: position, charge)."""
+    tri, sigma, pts, src = _field_inputs(tri, sigma, pts, src)
+    g = _c(g, np.float64).reshape(-1, 4)
+    ds = np.zeros(len(sigma))
+    dp = np.zeros((len(pts), 3))
+    dq = np.zeros((len(src), 4))
+    lib().or_field_backward(len(sigma), _p(tri), _p(sigma), len(pts), _p(pts), len(src), _p(src),
+                            int(self_exclude), _p(g), _p(ds), _p(dp), _p(dq))
+    return ds, dp, dq
 
 
 def assemble(mesh):

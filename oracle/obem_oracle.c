@@ -174,6 +174,192 @@ void or_nbody_field(int nt, const double *pts, int ns, const double *src,
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Derivatives of the field (backward / adjoint evaluation of Eqs. (BEM2),    */
+/* (BEM3), (nbody)).  The paper does not differentiate its field; these are   */
+/* the derivatives of the closed forms above, written out.                    */
+/* ------------------------------------------------------------------------- */
+
+/* Gradient, with respect to the observation point r, of the edge term
+ * L = ln((R+ + l+)/(R- + l-)) of or_tri_integrals.  With a = v - r for either
+ * end, l = a.lhat, and w the part of a perpendicular to the edge (the same
+ * vector at both ends):  grad(R + l) = -(a/R + lhat) and
+ * (a/R + lhat)/(R + l) = lhat/R + w/(R (R + l)), hence
+ *   grad L = lhat (1/R- - 1/R+) + w (g(R-, l-) - g(R+, l+)),  g = 1/(R (R + l)).
+ * R + l is formed without cancellation in each of the three cases that
+ * edge_log distinguishes (foot of r before, past, or on the edge). */
+static void edge_log_grad(const double *lhat, const double *w, double lm, double lp,
+                          double Rm, double Rp, double R0sq, double *g)
+{
+    double cw;
+    if (lm >= 0.0)
+        cw = 1.0 / (Rm * (Rm + lm)) - 1.0 / (Rp * (Rp + lp));
+    else if (lp <= 0.0)   /* the same edge walked backwards: L = ln((R- - l-)/(R+ - l+)) */
+        cw = -(1.0 / (Rm * (Rm - lm)) - 1.0 / (Rp * (Rp - lp)));
+    else                  /* 1/(R- (R- + l-)) = (R- - l-)/(R- R0^2) */
+        cw = (Rm - lm) / (Rm * R0sq) - 1.0 / (Rp * (Rp + lp));
+    double cl = 1.0 / Rm - 1.0 / Rp;
+    for (int k = 0; k < 3; ++k) g[k] = cl * lhat[k] + cw * w[k];
+}
+
+/*
+ * Jacobian J[a][b] = dF_a/dr_b of F(r) = int_T (r - r')/|r - r'|^3 dA' (unit
+ * density), row-major.  From F = Omega n + sum_edges u_i L_i:
+ *   J = n (grad Omega)^T + sum_i u_i (grad L_i)^T.
+ * The gradient of the solid angle of a flat polygon is the Biot-Savart line
+ * integral of a unit current around its boundary; for the straight edge from
+ * v_i to v_j it is
+ *   (lhat x w) / R0^2 * (l+/R+ - l-/R-),
+ * and when l- and l+ have the same sign the bracket is rewritten as
+ *   R0^2 (l+^2 - l-^2) / ((l+ R- + l- R+) R- R+)
+ * so that R0^2 cancels (no loss of digits near the edge's line).  F = -grad
+ * phi, so J is symmetric, and off the triangle trace(J) = 0 (Laplace).
+ * Defined for r off the closed triangle.
+ */
+void or_tri_jacobian(const double *v, const double *r, double *J)
+{
+    double e1[3], e2[3], nn[3], n[3], a[3][3], R[3];
+    for (int k = 0; k < 3; ++k) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
+    cross3(e1, e2, nn);
+    double a2 = norm3(nn);
+    for (int k = 0; k < 3; ++k) n[k] = nn[k] / a2;
+    for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 3; ++k) a[i][k] = v[3 * i + k] - r[k];
+        R[i] = norm3(a[i]);
+    }
+    double h = -dot3(a[0], n);
+    double gOm[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 9; ++k) J[k] = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3;
+        double ed[3], lhat[3], uhat[3], w[3], gL[3], lw[3];
+        for (int k = 0; k < 3; ++k) ed[k] = v[3 * j + k] - v[3 * i + k];
+        double len = norm3(ed);
+        for (int k = 0; k < 3; ++k) lhat[k] = ed[k] / len;
+        cross3(lhat, n, uhat);
+        double lm = dot3(a[i], lhat), lp = dot3(a[j], lhat);
+        for (int k = 0; k < 3; ++k) w[k] = a[i][k] - lm * lhat[k];
+        double p0 = dot3(a[i], uhat);
+        double R0sq = p0 * p0 + h * h;
+        edge_log_grad(lhat, w, lm, lp, R[i], R[j], R0sq, gL);
+        for (int ia = 0; ia < 3; ++ia)
+            for (int ib = 0; ib < 3; ++ib) J[3 * ia + ib] += uhat[ia] * gL[ib];
+        cross3(lhat, w, lw);
+        double c;
+        if (lm * lp > 0.0)
+            c = (lp * lp - lm * lm) / ((lp * R[i] + lm * R[j]) * R[i] * R[j]);
+        else
+            c = (lp / R[j] - lm / R[i]) / R0sq;
+        for (int k = 0; k < 3; ++k) gOm[k] += c * lw[k];
+    }
+    for (int ia = 0; ia < 3; ++ia)
+        for (int ib = 0; ib < 3; ++ib) J[3 * ia + ib] += n[ia] * gOm[ib];
+}
+
+/* Jacobian of the total field at nt points, d E / d r (row-major 3x3 each):
+ *   k_C sum_j sigma_j J_j(r) + k_C sum_{p != t} q_p (I/d^3 - 3 d d^T/d^5),
+ * d = r - r_p (the derivative of Eq. (nbody)'s pair term); pairs at zero
+ * distance are skipped as in or_nbody_field.  tri/sigma or src may be empty. */
+void or_field_jacobian(int np, const double *tri, const double *sigma, int nt, const double *pts,
+                       int ns, const double *src, int self_exclude, double *Jout)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int t = 0; t < nt; ++t) {
+        const double *r = pts + 3 * (size_t)t;
+        double acc[9] = {0};
+        for (int j = 0; j < np; ++j) {
+            double Jj[9];
+            or_tri_jacobian(tri + 9 * (size_t)j, r, Jj);
+            for (int k = 0; k < 9; ++k) acc[k] += sigma[j] * Jj[k];
+        }
+        for (int p = 0; p < ns; ++p) {
+            if (self_exclude && p == t) continue;
+            const double *s = src + 4 * (size_t)p;
+            double d[3] = {r[0] - s[0], r[1] - s[1], r[2] - s[2]};
+            double d2 = dot3(d, d);
+            if (d2 == 0.0) continue;
+            double id = 1.0 / sqrt(d2), id3 = id * id * id, id5 = id3 * id * id;
+            for (int ia = 0; ia < 3; ++ia)
+                for (int ib = 0; ib < 3; ++ib)
+                    acc[3 * ia + ib] += s[3] * ((ia == ib ? id3 : 0.0) - 3.0 * d[ia] * d[ib] * id5);
+        }
+        for (int k = 0; k < 9; ++k) Jout[9 * (size_t)t + k] = OR_KC * acc[k];
+    }
+}
+
+/*
+ * Backward (vector-Jacobian product) of the field evaluation
+ *   E_t = k_C sum_j sigma_j F_j(x_t) + k_C sum_{p != t} q_p (x_t - y_p)/|x_t - y_p|^3
+ *   V_t = k_C sum_j sigma_j phi_j(x_t) + k_C sum_{p != t} q_p / |x_t - y_p|
+ * for L with dL/d(E_t, V_t) = g_t = (gE_t, gV_t) (g: nt x 4):
+ *   dL/dsigma_j = k_C sum_t gE_t . F_j(x_t) + gV_t phi_j(x_t)
+ *   dL/dx_t     = (dE_t/dx_t)^T gE_t - gV_t E_t          (grad V = -E)
+ *   dL/dy_p     = k_C q_p sum_t -T(d)^T gE_t + gV_t d/|d|^3,  d = x_t - y_p
+ *   dL/dq_p     = k_C sum_t gE_t . d/|d|^3 + gV_t/|d|
+ * with T(d) = I/|d|^3 - 3 d d^T/|d|^5.  Any output may be NULL.  dpts is
+ * nt x 3, dsrc is ns x 4 (position gradient, charge gradient).
+ */
+void or_field_backward(int np, const double *tri, const double *sigma, int nt, const double *pts,
+                       int ns, const double *src, int self_exclude, const double *g,
+                       double *dsigma, double *dpts, double *dsrc)
+{
+    if (dsigma) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int j = 0; j < np; ++j) {
+            double acc = 0.0;
+            for (int t = 0; t < nt; ++t) {
+                double phi, F[3];
+                or_tri_integrals(tri + 9 * (size_t)j, pts + 3 * (size_t)t, &phi, F);
+                const double *gt = g + 4 * (size_t)t;
+                acc += gt[0] * F[0] + gt[1] * F[1] + gt[2] * F[2] + gt[3] * phi;
+            }
+            dsigma[j] = OR_KC * acc;
+        }
+    }
+    if (dpts) {
+        double *J = (double *)malloc(sizeof(double) * 9 * (size_t)(nt > 0 ? nt : 1));
+        double *E = (double *)malloc(sizeof(double) * 3 * (size_t)(nt > 0 ? nt : 1));
+        double *E2 = (double *)malloc(sizeof(double) * 3 * (size_t)(nt > 0 ? nt : 1));
+        or_field_jacobian(np, tri, sigma, nt, pts, ns, src, self_exclude, J);
+        for (int k = 0; k < 3 * nt; ++k) E[k] = 0.0;
+        if (np > 0) or_panel_field(np, tri, sigma, nt, pts, E, NULL);
+        if (ns > 0) {
+            or_nbody_field(nt, pts, ns, src, self_exclude, 0.0, E2, NULL);
+            for (int k = 0; k < 3 * nt; ++k) E[k] += E2[k];
+        }
+        for (int t = 0; t < nt; ++t) {
+            const double *gt = g + 4 * (size_t)t;
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int a = 0; a < 3; ++a) s += J[9 * (size_t)t + 3 * a + b] * gt[a];
+                dpts[3 * (size_t)t + b] = s - gt[3] * E[3 * (size_t)t + b];
+            }
+        }
+        free(J); free(E); free(E2);
+    }
+    if (dsrc) {
+#pragma omp parallel for schedule(static)
+        for (int p = 0; p < ns; ++p) {
+            const double *s = src + 4 * (size_t)p;
+            double gy[3] = {0, 0, 0}, gq = 0.0;
+            for (int t = 0; t < nt; ++t) {
+                if (self_exclude && p == t) continue;
+                const double *x = pts + 3 * (size_t)t, *gt = g + 4 * (size_t)t;
+                double d[3] = {x[0] - s[0], x[1] - s[1], x[2] - s[2]};
+                double d2 = dot3(d, d);
+                if (d2 == 0.0) continue;
+                double id = 1.0 / sqrt(d2), id3 = id * id * id, id5 = id3 * id * id;
+                double dg = dot3(d, gt);
+                for (int b = 0; b < 3; ++b)
+                    gy[b] += -(gt[b] * id3 - 3.0 * d[b] * dg * id5) + gt[3] * d[b] * id3;
+                gq += dg * id3 + gt[3] * id;
+            }
+            for (int b = 0; b < 3; ++b) dsrc[4 * (size_t)p + b] = OR_KC * s[3] * gy[b];
+            dsrc[4 * (size_t)p + 3] = OR_KC * gq;
+        }
+    }
+}
+
 /*
  * Dense BEM matrix, Eqs. (BEMpot), (BEMfld), (matrixBEM), row-major n x n.
  *   electrode (ed) rows:   A_ij = Q_ij = k_C phi_j(r_i)
