@@ -190,6 +190,35 @@ int obem_field_eval(obem_ctx *ctx, const float *targets, int32_t nt, const float
                     int32_t ns, int32_t self_exclude, const float *sigma, float *E_out,
                     obem_stream stream);
 
+/* Backward (vector-Jacobian product) of obem_field_eval, for training or
+ * optimisation through the field.  The paper does not differentiate its
+ * field; this is the derivative of Eqs. (BEM2), (BEM3), (nbody) as
+ * obem_field_eval evaluates them.  Given dL_dE = dL/d(Ex, Ey, Ez, V) per
+ * target (device [nt][4]), with d = x_t - y_p:
+ *   dL_dsigma[j]      = k_C sum_t gE_t . int_Cj (x_t - r')/|x_t - r'|^3 dA'
+ *                                 + gV_t int_Cj dA'/|x_t - r'|
+ *   dL_dtargets[t]    = (dE_t/dx_t)^T gE_t - gV_t E_t      (x, y, z, 0)
+ *   dL_dsources[p]    = k_C q_p sum_t [-(I/|d|^3 - 3 d d^T/|d|^5) gE_t
+ *                                      + gV_t d/|d|^3]        (x, y, z)
+ *                       and k_C sum_t gE_t . d/|d|^3 + gV_t/|d|   (w: dL/dq_p)
+ * targets, sources, self_exclude and sigma mean what they mean in
+ * obem_field_eval (sigma is needed only for the cell part of dL_dtargets;
+ * dL_dsigma needs a loaded mesh but not sigma).  Outputs: device arrays, each
+ * may be NULL to skip it: dL_dsigma [n_panels], dL_dtargets [nt][4],
+ * dL_dsources [ns][4] (needs sources).  With self_exclude the target-role and
+ * source-role gradients of a charge are returned separately (add them for
+ * the total).  Pairs at zero distance are skipped.  Cells near a target
+ * (closer than 1.5 longest edges for dL_dtargets, 1 for dL_dsigma) use the
+ * FP64 closed form and its Jacobian; farther cells use quadrature tiers.
+ * Errors: OBEM_ERR_ARG for negative sizes, missing inputs, self_exclude
+ * without sources of size nt, dL_dsources without sources, or arrays not
+ * 16-byte aligned; OBEM_ERR_STATE for sigma or dL_dsigma without a mesh.
+ * Allocates nothing and does not synchronise. */
+int obem_field_eval_backward(obem_ctx *ctx, const float *targets, int32_t nt, const float *sources,
+                             int32_t ns, int32_t self_exclude, const float *sigma, const float *dL_dE,
+                             float *dL_dsigma, float *dL_dtargets, float *dL_dsources,
+                             obem_stream stream);
+
 /* One tracking step of all charges in st (Sec. 3.2 - 3.3):
  *   1. field at the step-start positions: E_in (device [capacity][4]) if not
  *      NULL, else evaluated here (cell field with the current sigma and/or

@@ -21,6 +21,7 @@ UNITS = {
     "field.cu": [],
     "step.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "bem.cu": [],
+    "backward.cu": [],
 }
 
 

@@ -18,9 +18,20 @@
 //   d >=   h     7-point rule on 16 sub-triangles       (<= 1.3e-6)
 //   d <    h     closed form in FP64 (edge logarithms + solid angle)
 #include "obem_internal.cuh"
+#include "field_common.cuh"
 
 #define FT_THREADS 128
-#define FT_TPT 4
+#ifndef FT_TPT
+#define FT_TPT 4                    // targets per thread (even)
+#endif
+#ifndef FT_MINB
+#define FT_MINB 6                   // resident blocks per SM the register budget is cut for
+#endif
+#ifndef FT_UNROLL
+#define FT_UNROLL 4                 // source-loop unrolling of the all-pairs kernel
+#endif
+#define FT_PRAGMA(x) _Pragma(#x)
+#define FT_UNROLL_BY(n) FT_PRAGMA(unroll n)
 #define FT_BLOCK_TARGETS (FT_THREADS * FT_TPT)
 #define FT_SRC_TILE 256
 #define FT_PAN_TILE 64
@@ -29,132 +40,10 @@
 #define TIER_3PT_H2 256.0f
 #define TIER_7PT_H2 9.0f
 
-typedef unsigned long long u64;
 
-// ------------------------------------------------------------------ packed f32x2
-__device__ __forceinline__ u64 pk(float a, float b)
-{
-    u64 r;
-    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(u64 v, float &a, float &b)
-{
-    asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b)
-{
-    u64 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b)
-{
-    u64 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b)
-{
-    u64 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
-{
-    u64 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ float rsq(float x)
-{
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 
-// error-free sum s + e = a + b (Knuth TwoSum), e accumulated into c
-__device__ __forceinline__ void two_sum_acc(float &s, float &c, float b)
-{
-    float t = __fadd_rn(s, b);
-    float z = __fsub_rn(t, s);
-    float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(b, z));
-    s = t;
-    c = __fadd_rn(c, e);
-}
 
-// ------------------------------------------------------------------ FP64 closed form
-// Potential and field of a unit uniform density on a flat triangle at r:
-// phi = sum_i p0_i L_i - h Omega,  F = Omega n + sum_i u_i L_i, with the edge
-// integrals L_i = ln((R+ + l+)/(R- + l-)) evaluated without cancellation and
-// Omega the signed solid angle (Van Oosterom & Strackee); principal value in
-// the cell's plane.
-__device__ __noinline__ void tri_closed_form(const double *v, double rx, double ry, double rz, double &phi,
-                                double &Fx, double &Fy, double &Fz)
-{
-    double e1x = v[3] - v[0], e1y = v[4] - v[1], e1z = v[5] - v[2];
-    double e2x = v[6] - v[0], e2y = v[7] - v[1], e2z = v[8] - v[2];
-    double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
-    double a2 = sqrt(nx * nx + ny * ny + nz * nz);
-    nx /= a2; ny /= a2; nz /= a2;
-    double ax[3], ay[3], az[3], R[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        ax[i] = v[3 * i] - rx;
-        ay[i] = v[3 * i + 1] - ry;
-        az[i] = v[3 * i + 2] - rz;
-        R[i] = sqrt(ax[i] * ax[i] + ay[i] * ay[i] + az[i] * az[i]);
-    }
-    double h = -(ax[0] * nx + ay[0] * ny + az[0] * nz);
-    double ps = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        int j = (i + 1) % 3;
-        double dx = v[3 * j] - v[3 * i], dy = v[3 * j + 1] - v[3 * i + 1], dz = v[3 * j + 2] - v[3 * i + 2];
-        double len = sqrt(dx * dx + dy * dy + dz * dz);
-        dx /= len; dy /= len; dz /= len;
-        double ux = dy * nz - dz * ny, uy = dz * nx - dx * nz, uz = dx * ny - dy * nx;
-        double lm = ax[i] * dx + ay[i] * dy + az[i] * dz;
-        double lp = ax[j] * dx + ay[j] * dy + az[j] * dz;
-        double p0 = ax[i] * ux + ay[i] * uy + az[i] * uz;
-        double L;
-        if (lm >= 0.0) L = log((R[j] + lp) / (R[i] + lm));
-        else if (lp <= 0.0) L = log((R[i] - lm) / (R[j] - lp));
-        else L = log((R[j] + lp) * (R[i] - lm) / (p0 * p0 + h * h));
-        if (p0 != 0.0) ps += p0 * L;
-        fx += ux * L; fy += uy * L; fz += uz * L;
-    }
-    double D = R[0] * R[1] * R[2] + (ax[0] * ax[1] + ay[0] * ay[1] + az[0] * az[1]) * R[2]
-             + (ax[0] * ax[2] + ay[0] * ay[2] + az[0] * az[2]) * R[1]
-             + (ax[1] * ax[2] + ay[1] * ay[2] + az[1] * az[2]) * R[0];
-    double Om = (h == 0.0) ? 0.0 : 2.0 * atan2(a2 * h, D);
-    phi = ps - h * Om;
-    Fx = fx + Om * nx;
-    Fy = fy + Om * ny;
-    Fz = fz + Om * nz;
-}
 
-// one FP32 quadrature point of weight w (already k_C sigma A w_i)
-__device__ __forceinline__ void qpoint(float tx, float ty, float tz, float px, float py, float pz,
-                                       float w, float &ax, float &ay, float &az, float &av)
-{
-    float dx = tx - px, dy = ty - py, dz = tz - pz;
-    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    float inv = rsq(r2);
-    float s = w * inv;
-    float s3 = s * (inv * inv);
-    ax = fmaf(dx, s3, ax);
-    ay = fmaf(dy, s3, ay);
-    az = fmaf(dz, s3, az);
-    av += s;
-}
-
-// Dunavant degree-5 rule, points c + t (v_k - c)
-#define D7_W0 0.225f
-#define D7_W1 0.132394152788506f
-#define D7_W2 0.125939180544827f
-#define D7_T1 (-0.410426192315345f)
-#define D7_T2 0.696140478029631f
 
 struct __align__(16) PanTile {
     float4 cq;   // cx, cy, cz, q = k_C sigma A
@@ -295,43 +184,7 @@ __global__ void bin_scatter_kernel(FieldLaunch L, const uint32_t *code, int32_t 
 #define TIER_28PT_H2 2.25f          // d >= 1.5 h
 #define FRAME_H 0.05f               // a cell needs h >= FRAME_H * frame scale to be far
 
-// sub-triangle s of the midpoint subdivision of (A, B, C): 0 the middle one,
-// 1..3 the corner ones at A, B, C
-__device__ __forceinline__ void subtri(int s, float3 &A, float3 &B, float3 &C)
-{
-    const float3 ab = make_float3(0.5f * (A.x + B.x), 0.5f * (A.y + B.y), 0.5f * (A.z + B.z));
-    const float3 bc = make_float3(0.5f * (B.x + C.x), 0.5f * (B.y + C.y), 0.5f * (B.z + C.z));
-    const float3 ca = make_float3(0.5f * (C.x + A.x), 0.5f * (C.y + A.y), 0.5f * (C.z + A.z));
-    if (s == 0) { A = ab; B = bc; C = ca; }
-    else if (s == 1) { B = ab; C = ca; }
-    else if (s == 2) { A = B; B = bc; C = ab; }
-    else { A = C; B = ca; C = bc; }
-}
 
-// Point k of the 7-point rule applied to the 4^level sub-triangles of the
-// cell with vertex offsets g0, g1, g2 (from its centroid): offset and weight
-// fraction of the point.
-__device__ __forceinline__ void rule_point(int level, int k, float3 g0, float3 g1, float3 g2, float3 &off,
-                                           float &wf)
-{
-    int sub = k / 7;
-    const int m = k % 7;
-    float3 A = g0, B = g1, C = g2;
-    float scale = 1.0f;
-    for (int l = level - 1; l >= 0; --l) {
-        int s = (sub >> (2 * l)) & 3;
-        subtri(s, A, B, C);
-        scale *= 0.25f;
-    }
-    const float3 sc = make_float3((A.x + B.x + C.x) * (1.0f / 3.0f), (A.y + B.y + C.y) * (1.0f / 3.0f),
-                                  (A.z + B.z + C.z) * (1.0f / 3.0f));
-    if (m == 0) { off = sc; wf = scale * D7_W0; return; }
-    const int v = (m - 1) % 3;
-    const float t = m <= 3 ? D7_T1 : D7_T2;
-    const float3 V = v == 0 ? A : (v == 1 ? B : C);
-    off = make_float3(fmaf(t, V.x - sc.x, sc.x), fmaf(t, V.y - sc.y, sc.y), fmaf(t, V.z - sc.z, sc.z));
-    wf = scale * (m <= 3 ? D7_W1 : D7_W2);
-}
 
 // squared distance from point c to the box [lo, hi]
 __device__ __forceinline__ float box_d2(float cx, float cy, float cz, float3 lo, float3 hi)
@@ -811,17 +664,19 @@ cell_kernel(FieldLaunch L)
 // ---------------------------------------------------------------- all-pairs kernel
 // E_out[i] = init + k_C sum_{p != i} q_p (r_i - r_p) / (|r_i - r_p|^2 + eps^2)^(3/2)
 // init = E_out[i] when the cell kernels ran first (ADD), else e_ext.
-// The compensated accumulators and the recombination proposals live in shared
-// memory (touched once per tile / rarely), which keeps the register count low
-// enough for FT_MINB resident blocks per SM.
-#define FT_MINB 6
+// One CTA per block of FT_BLOCK_TARGETS targets; each thread holds FT_TPT
+// targets as FT_NP packs of two.  The compensated accumulators and the
+// recombination proposals live in shared memory (touched once per tile /
+// rarely), which keeps the register count low enough for FT_MINB resident
+// blocks per SM.
+#define FT_NP (FT_TPT / 2)
 
 template <bool WANT_V, bool RECOMB, bool ADD>
 __global__ void __launch_bounds__(FT_THREADS, FT_MINB)
 nbody_kernel(FieldLaunch L)
 {
     __shared__ SrcPk s_src[FT_SRC_TILE];
-    __shared__ float s_acc[2][4][FT_TPT][FT_THREADS];          // [S|C][component][target][thread]
+    __shared__ float s_acc[2][WANT_V ? 4 : 3][FT_TPT][FT_THREADS];   // [S|C][component][target][thread]
     __shared__ unsigned long long s_best[RECOMB ? FT_TPT : 1][FT_THREADS];
 
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
@@ -831,8 +686,8 @@ nbody_kernel(FieldLaunch L)
     const int tid = threadIdx.x;
     constexpr int NC = WANT_V ? 4 : 3;
 
-    float rc2f[FT_TPT];
-    u64 TX[2], TY[2], TZ[2];
+    uint32_t emask = 0;   // bit k: target k is an electron (looks for a partner)
+    u64 TX[FT_NP], TY[FT_NP], TZ[FT_NP];
 #pragma unroll
     for (int k = 0; k < FT_TPT; ++k) {
         int i = base + k * FT_THREADS + tid;
@@ -856,16 +711,17 @@ nbody_kernel(FieldLaunch L)
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) { s_acc[0][c][k][tid] = e[c]; s_acc[1][c][k][tid] = 0.f; }
-        rc2f[k] = -1.0f;
         if (RECOMB) {
             s_best[RECOMB ? k : 0][tid] = ~0ull;
-            if (i < nt && L.species[i] == OBEM_ELECTRON)
-                rc2f[k] = (L.rc2 + L.eps2) * (1.0f + 3.814697265625e-06f) + 1e-30f;
+            if (i < nt && L.species[i] == OBEM_ELECTRON) emask |= 1u << k;
         }
     }
 
     const float kC = (float)OBEM_KC;
     const u64 EPS2 = pk(L.eps2, L.eps2);
+    // candidate filter for the partner search: softened r^2 below this (a
+    // little above rc^2 + eps^2, so no pair within rc is missed to rounding)
+    const float RCF = RECOMB ? (L.rc2 + L.eps2) * (1.0f + 3.814697265625e-06f) + 1e-30f : -1.0f;
     for (int sb = 0; sb < ns; sb += FT_SRC_TILE) {
         __syncthreads();
 #pragma unroll
@@ -887,16 +743,16 @@ nbody_kernel(FieldLaunch L)
         const bool diag = L.self_exclude && sb < base + FT_BLOCK_TARGETS && base < sb + FT_SRC_TILE;
         float part[FT_TPT][4];
         if (!diag) {
-            u64 AX[2], AY[2], AZ[2], AV[2];
+            u64 AX[FT_NP], AY[FT_NP], AZ[FT_NP], AV[FT_NP];
 #pragma unroll
-            for (int p = 0; p < 2; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
-#pragma unroll 4
+            for (int p = 0; p < FT_NP; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
+            FT_UNROLL_BY(FT_UNROLL)
             for (int jj = 0; jj < FT_SRC_TILE; ++jj) {
                 const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&s_src[jj].xx);
                 const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&s_src[jj].zz);
                 bool hit = false;
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
+                for (int p = 0; p < FT_NP; ++p) {
                     u64 dx = sub2(TX[p], a.x);
                     u64 dy = sub2(TY[p], a.y);
                     u64 dz = sub2(TZ[p], b.x);
@@ -905,7 +761,7 @@ nbody_kernel(FieldLaunch L)
                     r2 = fma2(dz, dz, r2);
                     float ra, rb;
                     upk(r2, ra, rb);
-                    if (RECOMB) hit |= (ra < rc2f[2 * p]) | (rb < rc2f[2 * p + 1]);
+                    if (RECOMB) hit |= (ra < RCF) | (rb < RCF);
                     u64 inv = pk(rsq(ra), rsq(rb));
                     u64 s = mul2(b.y, inv);
                     u64 s3 = mul2(s, mul2(inv, inv));
@@ -914,7 +770,7 @@ nbody_kernel(FieldLaunch L)
                     AZ[p] = fma2(dz, s3, AZ[p]);
                     if (WANT_V) AV[p] = add2(AV[p], s);
                 }
-                if (RECOMB && hit) {
+                if (RECOMB && hit && emask) {
                     // rare: binary32 distance without contraction, and the partner rules
                     const int j = sb + jj;
                     float sx, sy, sz, dum;
@@ -922,7 +778,7 @@ nbody_kernel(FieldLaunch L)
                     if (j < ns && L.species[j] == OBEM_CATION && !(L.birth[j] != 0u && L.birth[j] == L.step)) {
 #pragma unroll
                         for (int k = 0; k < FT_TPT; ++k) {
-                            if (rc2f[k] < 0.f) continue;
+                            if (!((emask >> k) & 1u)) continue;
                             float txk, tyk, tzk, t2;
                             if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
                             else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
@@ -937,11 +793,11 @@ nbody_kernel(FieldLaunch L)
                 }
             }
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
+            for (int p = 0; p < FT_NP; ++p) {
                 upk(AX[p], part[2 * p][0], part[2 * p + 1][0]);
                 upk(AY[p], part[2 * p][1], part[2 * p + 1][1]);
                 upk(AZ[p], part[2 * p][2], part[2 * p + 1][2]);
-                upk(AV[p], part[2 * p][3], part[2 * p + 1][3]);
+                if (WANT_V) upk(AV[p], part[2 * p][3], part[2 * p + 1][3]);
             }
         } else {
             // tile holding some of this block's own targets: skip the self pair
@@ -967,7 +823,7 @@ nbody_kernel(FieldLaunch L)
                     part[k][1] = fmaf(dy, s3, part[k][1]);
                     part[k][2] = fmaf(dz, s3, part[k][2]);
                     part[k][3] += s;
-                    if (RECOMB && r2 < rc2f[k] && j < ns && L.species[j] == OBEM_CATION &&
+                    if (RECOMB && ((emask >> k) & 1u) && r2 < RCF && j < ns && L.species[j] == OBEM_CATION &&
                         !(L.birth[j] != 0u && L.birth[j] == L.step)) {
                         float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                         if (d2 <= L.rc2) {
@@ -998,7 +854,7 @@ nbody_kernel(FieldLaunch L)
         e.x = (float)((double)s_acc[0][0][k][tid] + (double)s_acc[1][0][k][tid]);
         e.y = (float)((double)s_acc[0][1][k][tid] + (double)s_acc[1][1][k][tid]);
         e.z = (float)((double)s_acc[0][2][k][tid] + (double)s_acc[1][2][k][tid]);
-        e.w = WANT_V ? (float)((double)s_acc[0][3][k][tid] + (double)s_acc[1][3][k][tid]) : 0.f;
+        e.w = WANT_V ? (float)((double)s_acc[0][NC - 1][k][tid] + (double)s_acc[1][NC - 1][k][tid]) : 0.f;
         L.E_out[i] = e;
         if (RECOMB) L.prop[i] = s_best[RECOMB ? k : 0][tid];
     }

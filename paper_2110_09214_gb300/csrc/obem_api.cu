@@ -420,6 +420,47 @@ extern "C" int obem_field_eval(obem_ctx *c, const float *targets, int32_t nt, co
     return obem_launch_field(c, L, nt, (cudaStream_t)stream);
 }
 
+extern "C" int obem_field_eval_backward(obem_ctx *c, const float *targets, int32_t nt, const float *sources,
+                                        int32_t ns, int32_t self_exclude, const float *sigma,
+                                        const float *dL_dE, float *dL_dsigma, float *dL_dtargets,
+                                        float *dL_dsources, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (nt < 0 || (sources && ns < 0)) return obem_fail(c, OBEM_ERR_ARG, "field backward: negative count");
+    if (self_exclude && (!sources || ns != nt))
+        return obem_fail(c, OBEM_ERR_ARG, "field backward: self_exclude needs sources with ns == nt");
+    if (dL_dsources && !sources)
+        return obem_fail(c, OBEM_ERR_ARG, "field backward: dL_dsources needs sources");
+    if ((sigma || dL_dsigma) && c->np < 1)
+        return obem_fail(c, OBEM_ERR_STATE, "field backward: sigma or dL_dsigma given but no mesh loaded");
+    if (nt > 0 && (!targets || !dL_dE))
+        return obem_fail(c, OBEM_ERR_ARG, "field backward: null targets or dL_dE");
+    if (((uintptr_t)targets | (uintptr_t)sources | (uintptr_t)dL_dE | (uintptr_t)dL_dtargets |
+         (uintptr_t)dL_dsources) & 15)
+        return obem_fail(c, OBEM_ERR_ARG, "field backward: arrays must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nt == 0) {
+        // sums over no targets
+        if (dL_dsigma) OBEM_CUDA(c, cudaMemsetAsync(dL_dsigma, 0, sizeof(float) * (size_t)c->np, s));
+        if (dL_dsources && ns > 0) OBEM_CUDA(c, cudaMemsetAsync(dL_dsources, 0, sizeof(float) * 4 * (size_t)ns, s));
+        return OBEM_OK;
+    }
+    BwArgs A;
+    memset(&A, 0, sizeof A);
+    A.targets = targets;
+    A.nt = nt;
+    A.sources = (sources && ns > 0) ? sources : NULL;
+    A.ns = A.sources ? ns : 0;
+    A.self_exclude = self_exclude ? 1 : 0;
+    A.sigma = sigma;
+    A.panels = panels_of(c);
+    A.dL_dE = dL_dE;
+    A.dL_dsigma = dL_dsigma;
+    A.dL_dtargets = dL_dtargets;
+    A.dL_dsources = dL_dsources;
+    return obem_launch_backward(c, A, s);
+}
+
 extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, uint32_t step,
                          obem_step_stats *stats, obem_stream stream)
 {

@@ -181,6 +181,20 @@ struct FieldLaunch {
 #define OBEM_NSUPER (OBEM_NBINS >> OBEM_SUPER_SHIFT)
 int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets, cudaStream_t s);
 
+// backward.cu
+struct BwArgs {
+    const float *targets;
+    int nt;
+    const float *sources;
+    int ns;
+    int self_exclude;
+    const float *sigma;
+    PanelsDev panels;
+    const float *dL_dE;
+    float *dL_dsigma, *dL_dtargets, *dL_dsources;
+};
+int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s);
+
 // step.cu
 // partners_done: the field pass already proposed recombination partners
 int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,

@@ -11,6 +11,7 @@ import ctypes as C
 import os
 
 import numpy as np
+import torch
 
 from . import build as _build
 
@@ -89,13 +90,14 @@ def load():
     lib.obem_bem_assemble.argtypes = [P, I, P]
     lib.obem_bem_solve.argtypes = [P, P, P, P, P, C.POINTER(obem_solve_report), P]
     lib.obem_field_eval.argtypes = [P, P, I, P, I, I, P, P, P]
+    lib.obem_field_eval_backward.argtypes = [P, P, I, P, I, I, P, P, P, P, P, P]
     lib.obem_step.argtypes = [P, C.POINTER(obem_state), P, U, P, P]
     lib.obem_field_eval_noalloc.argtypes = [P, I, P, I, I, P, P, I, P, C.c_char_p, I, P]
     lib.obem_field_eval_noalloc.restype = C.c_int
     lib.obem_profile.argtypes = [P, I]
     lib.obem_stage_times.argtypes = [P, P, P]
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
-              "obem_bem_solve", "obem_field_eval", "obem_step", "obem_profile",
+              "obem_bem_solve", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
               "obem_stage_times"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
@@ -196,6 +198,56 @@ def obem_field_eval(ctx, targets, E_out, sources=None, self_exclude=False, sigma
     _check(ctx, load().obem_field_eval(ctx, _ptr(targets), nt, _ptr(sources), ns,
                                        int(bool(self_exclude)), _ptr(sigma), _ptr(E_out),
                                        _stream(stream)))
+
+
+def obem_field_eval_backward(ctx, targets, dL_dE, sources=None, self_exclude=False, sigma=None,
+                             dL_dsigma=None, dL_dtargets=None, dL_dsources=None, stream=None):
+    """Vector-Jacobian product of obem_field_eval: writes dL/dsigma [n_panels],
+    dL/dtargets [nt, 4] (x, y, z, 0) and dL/dsources [ns, 4] (x, y, z, q)
+    into whichever output tensors are given."""
+    nt = targets.shape[0]
+    ns = sources.shape[0] if sources is not None else 0
+    _check(ctx, load().obem_field_eval_backward(ctx, _ptr(targets), nt, _ptr(sources), ns,
+                                                int(bool(self_exclude)), _ptr(sigma), _ptr(dL_dE),
+                                                _ptr(dL_dsigma), _ptr(dL_dtargets), _ptr(dL_dsources),
+                                                _stream(stream)))
+
+
+class FieldEval(torch.autograd.Function):
+    """E = field_eval(targets, sources, sigma) as a differentiable op: the
+    forward is obem_field_eval, the backward obem_field_eval_backward.
+    Gradients flow to targets[:, :3], sources[:, :4] (position and charge)
+    and sigma."""
+
+    @staticmethod
+    def forward(fctx, ctx, targets, sources, sigma, self_exclude):
+        out = torch.empty((targets.shape[0], 4), dtype=torch.float32, device=targets.device)
+        obem_field_eval(ctx, targets, out, sources=sources, self_exclude=self_exclude, sigma=sigma,
+                        stream=torch.cuda.current_stream(targets.device))
+        fctx.ctx = ctx
+        fctx.self_exclude = self_exclude
+        fctx.save_for_backward(targets, sources, sigma)
+        return out
+
+    @staticmethod
+    def backward(fctx, grad):
+        targets, sources, sigma = fctx.saved_tensors
+        need_t, need_s, need_sg = fctx.needs_input_grad[1:4]
+        dev = targets.device
+        grad = grad.contiguous().float()
+        dt = torch.empty((targets.shape[0], 4), dtype=torch.float32, device=dev) if need_t else None
+        ds = torch.empty((sources.shape[0], 4), dtype=torch.float32, device=dev) \
+            if (need_s and sources is not None) else None
+        dsg = torch.empty_like(sigma) if (need_sg and sigma is not None) else None
+        obem_field_eval_backward(fctx.ctx, targets, grad, sources=sources, self_exclude=fctx.self_exclude,
+                                 sigma=sigma, dL_dsigma=dsg, dL_dtargets=dt, dL_dsources=ds,
+                                 stream=torch.cuda.current_stream(dev))
+        return None, dt, ds, dsg, None
+
+
+def field_eval(ctx, targets, sources=None, sigma=None, self_exclude=False):
+    """Differentiable field and potential [nt, 4] at targets (see FieldEval)."""
+    return FieldEval.apply(ctx, targets, sources, sigma, bool(self_exclude))
 
 
 def obem_step(ctx, state, step, stats, E_in=None, stream=None):
