@@ -176,6 +176,21 @@ int obem_bem_solve(obem_ctx *ctx, const double *group_voltage, const float *sigm
                    const float *drhs, float *sigma_out, obem_solve_report *rep,
                    obem_stream stream);
 
+/* Adjoint of obem_bem_solve, for gradients through the solve.  Given
+ * dL_dsigma = dL/dsigma (device [n_panels]), solves A^T mu = dL/dsigma with
+ * the stored factors (transposed triangular solves, iterative refinement
+ * with FP64 residuals on the equilibrated matrix); mu = dL/db is the
+ * gradient with respect to the right-hand side b of Eq. (matrixBEM): on a
+ * dielectric cell it is dL/d sigma_free, on every cell dL/d drhs.
+ * dL_dgroup_voltage: host [n_groups] or NULL, receives sum of mu over the
+ * electrode cells of each group (dL/dV_k); dL_db: device [n_panels] or
+ * NULL.  rep may be NULL.  The paper keeps the factorisation to re-solve for
+ * new right-hand sides (Sec. 2.2); the adjoint is the same reuse with the
+ * transposed factors.  OBEM_ERR_STATE before obem_bem_assemble.  Allocates
+ * scratch and synchronises `stream` (a set-up call, like the solve). */
+int obem_bem_solve_adjoint(obem_ctx *ctx, const float *dL_dsigma, double *dL_dgroup_voltage,
+                           float *dL_db, obem_solve_report *rep, obem_stream stream);
+
 /* Field and potential at nt points (Eqs. (BEM2), (BEM3), (nbody)):
  *   E(r) = k_C sum_j sigma_j int_Cj (r - r')/|r - r'|^3 dA'
  *        + k_C sum_p q_p (r - r_p)/|r - r_p|^3

@@ -10,8 +10,8 @@ swarm-parameter fits of Sec. 4.1 (Eqs. (vd), (diffusion), (townsend)).
 
 Parity status of each function (see the test-suite for the pins):
   tri_integrals, panel_field, nbody_field, assemble, bem_solve, influence_rhs,
-  philox, step, swarm fits, tri_jacobian, field_jacobian, field_backward:
-  pinned.
+  philox, step, swarm fits, tri_jacobian, field_jacobian, field_backward,
+  bem_solve_adjoint: pinned.
   Swarm parameters of the synthetic argon-like gas: parity unpinned (no closed
   form; only GPU-vs-oracle agreement within 3 sigma and the Maxwell-model
   limits are checked).
@@ -199,6 +199,19 @@ def solve(A, b, force_gepp=False):
 def bem_solve(mesh, sigma_free=None, drhs=None, group_voltage=None):
     A = assemble(mesh)
     return solve(A, bem_rhs(mesh, sigma_free, drhs, group_voltage))
+
+
+def bem_solve_adjoint(mesh, g_sigma):
+    """Adjoint of bem_solve for L with dL/dsigma = g_sigma: mu = A^-T g_sigma
+    is dL/db for the right-hand side b of Eq. (matrixBEM) (so it is dL/d
+    sigma_free on dielectric cells and dL/d drhs everywhere), and dL/dV_k is
+    the sum of mu over the electrode cells of group k.  Returns (mu, dL/dV)."""
+    A = assemble(mesh)
+    mu = solve(np.ascontiguousarray(A.T), np.asarray(g_sigma, np.float64))
+    ed = mesh.kind == 0
+    dV = np.zeros(len(mesh.group_voltage))
+    np.add.at(dV, mesh.group[ed], mu[ed])
+    return mu, dV
 
 
 def influence_rhs(mesh, src):

@@ -675,3 +675,252 @@ int obem_solve_system(obem_ctx *c, const double *gv, const float *sigma_free, co
         return obem_fail(c, OBEM_ERR_NOT_CONVERGED, "refinement stopped at backward error %.3e after %d iterations", be, it);
     return OBEM_OK;
 }
+
+// ====================================================================
+// Adjoint of the solve: mu = A^-T g (g = dL/dsigma) is dL/db for the right-hand
+// side of Eq. (matrixBEM).  With the row-equilibrated matrix At = D A and its
+// factors P At = L U:  A^T mu = g  <=>  At^T nu = g,  mu = D nu,  and
+// At^T = U^T L^T P, so each refinement step solves U^T z = r (forward),
+// L^T w = z (backward, unit diagonal) and undoes the row swaps (nu = P^-1 w).
+// The residual g - At^T nu is accumulated in FP64 from the stored FP32 At.
+// ====================================================================
+#define ADJ_SPLIT 16           // row ranges of the transposed residual
+
+// part[s][j] = sum over rows i of range s of At[i][j] x[i]; one thread per column
+__global__ void residual_t_part_kernel(const float *A, const double *x, double *part, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    const int i0 = (int)((long long)n * s / ADJ_SPLIT), i1 = (int)((long long)n * (s + 1) / ADJ_SPLIT);
+    if (j >= n) return;
+    double a0 = 0.0, a1 = 0.0;
+    int i = i0;
+    for (; i + 1 < i1; i += 2) {
+        a0 += (double)A[(size_t)i * n + j] * x[i];
+        a1 += (double)A[(size_t)(i + 1) * n + j] * x[i + 1];
+    }
+    if (i < i1) a0 += (double)A[(size_t)i * n + j] * x[i];
+    part[(size_t)s * n + j] = a0 + a1;
+}
+
+// r = b - sum_s part[s]  (ranges added in order)
+__global__ void residual_t_fold_kernel(const double *part, const double *b, double *r, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int q = 0; q < ADJ_SPLIT; ++q) s += part[(size_t)q * n + j];
+    r[j] = b[j] - s;
+}
+
+// colsum[j] = sum_i |At[i][j]|  (for the transposed system's infinity norm)
+__global__ void colsum_kernel(const float *A, double *colsum, int n)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += fabs((double)A[(size_t)i * n + j]);
+    colsum[j] = s;
+}
+
+__global__ void max_kernel(const double *v, int n, double *out)
+{
+    __shared__ double s[256];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a = fmax(a, v[i]);
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+__global__ void load_adjoint_kernel(const float *g, double *b, double *x, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    b[i] = (double)g[i];
+    x[i] = 0.0;
+}
+
+// y = r / sc in FP32 (sc = max|r|)
+__global__ void scale_to_float_kernel(const double *r, float *y, int n, const double *norms)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double sc = norms[0] > 0 ? norms[0] : 1.0;
+    y[i] = (float)(r[i] / sc);
+}
+
+// undo the factorisation's row swaps (applied in forward order by the
+// factorisation, so undone in reverse order)
+__global__ void unpermute_kernel(float *y, const int *piv, int n)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int i = n - 1; i >= 0; --i) {
+        int p = piv[i];
+        if (p != i) { float t = y[i]; y[i] = y[p]; y[p] = t; }
+    }
+}
+
+// Diagonal block [k, k+kb) of a transposed triangular solve: upper_unit = 0
+// solves with U^T (lower, U's diagonal, forward), upper_unit = 1 with L^T
+// (upper, unit diagonal, backward).  T holds the transposed block.
+__global__ void trsv_t_block_kernel(const float *LU, float *y, int n, int k, int kb, int upper_unit)
+{
+    __shared__ float T[LU_NB][LU_NB + 1];
+    __shared__ float yb[LU_NB];
+    for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
+        const int c = t / kb, r = t % kb;                    // coalesced along r
+        T[r][c] = LU[(size_t)(k + c) * n + k + r];
+    }
+    const int r = threadIdx.x;
+    if (r < kb) yb[r] = y[k + r];
+    __syncthreads();
+    if (!upper_unit) {
+        for (int q = 0; q < kb; ++q) {
+            if (r == q) yb[q] = yb[q] / T[q][q];
+            __syncthreads();
+            if (r > q && r < kb) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
+            __syncthreads();
+        }
+    } else {
+        for (int q = kb - 1; q >= 0; --q) {
+            if (r < q) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
+            __syncthreads();
+        }
+    }
+    if (r < kb) y[k + r] = yb[r];
+}
+
+// y[row] -= sum_q LU[k+q][row] y[k+q] for rows in [r0, r1); one thread per row
+// (the factors' rows k..k+kb are read along their length: coalesced)
+__global__ void trsv_t_update_kernel(const float *LU, float *y, int n, int k, int kb, int r0, int r1)
+{
+    __shared__ float yk[LU_NB];
+    if (threadIdx.x < kb) yk[threadIdx.x] = y[k + threadIdx.x];
+    __syncthreads();
+    const int row = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= r1) return;
+    float s = 0.f;
+    for (int q = 0; q < kb; ++q) s = fmaf(LU[(size_t)(k + q) * n + row], yk[q], s);
+    y[row] -= s;
+}
+
+static int lu_solve_t(obem_ctx *c, float *y, cudaStream_t s)
+{
+    const int n = c->np;
+    for (int k = 0; k < n; k += LU_NB) {
+        const int kb = n - k < LU_NB ? n - k : LU_NB;
+        trsv_t_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 0);
+        if (k + kb < n)
+            trsv_t_update_kernel<<<(n - k - kb + 255) / 256, 256, 0, s>>>(c->d_LU, y, n, k, kb, k + kb, n);
+    }
+    for (int k = ((n - 1) / LU_NB) * LU_NB; k >= 0; k -= LU_NB) {
+        const int kb = n - k < LU_NB ? n - k : LU_NB;
+        trsv_t_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 1);
+        if (k > 0) trsv_t_update_kernel<<<(k + 255) / 256, 256, 0, s>>>(c->d_LU, y, n, k, kb, 0, k);
+    }
+    OBEM_LAUNCH(c);
+    return OBEM_OK;
+}
+
+int obem_solve_adjoint(obem_ctx *c, const float *g, double *dL_dgv, float *dL_db, obem_solve_report *rep,
+                       cudaStream_t s)
+{
+    const int n = c->np;
+    double *b = c->d_work64, *x = b + n, *r = x + n, *nrm = r + n;
+    float *y = c->d_work32;
+    double *part = NULL, *col = NULL, *mu = NULL;
+    int rc = OBEM_OK, it = 0, status = OBEM_ERR_NOT_CONVERGED;
+    double be = 1.0, be_prev = 2.0, a1 = 0.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+#define ADJ_CUDA(call)                                                                             \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            rc = obem_fail(c, OBEM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+            goto done;                                                                             \
+        }                                                                                          \
+    } while (0)
+    ADJ_CUDA(cudaMalloc((void **)&part, sizeof(double) * (size_t)ADJ_SPLIT * n));
+    ADJ_CUDA(cudaMalloc((void **)&col, sizeof(double) * ((size_t)n + 1)));
+    colsum_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_A, col, n);
+    max_kernel<<<1, 256, 0, s>>>(col, n, col + n);
+    load_adjoint_kernel<<<(n + 255) / 256, 256, 0, s>>>(g, b, x, n);
+    ADJ_CUDA(cudaGetLastError());
+    ADJ_CUDA(cudaMemcpyAsync(&a1, col + n, sizeof(double), cudaMemcpyDeviceToHost, s));
+    for (; it <= 30; ++it) {
+        residual_t_part_kernel<<<dim3((n + 255) / 256, ADJ_SPLIT), 256, 0, s>>>(c->d_A, x, part, n);
+        residual_t_fold_kernel<<<(n + 255) / 256, 256, 0, s>>>(part, b, r, n);
+        norms_kernel<<<1, 256, 0, s>>>(r, x, b, n, nrm);
+        ADJ_CUDA(cudaGetLastError());
+        double h[3];
+        ADJ_CUDA(cudaMemcpyAsync(h, nrm, sizeof h, cudaMemcpyDeviceToHost, s));
+        ADJ_CUDA(cudaStreamSynchronize(s));
+        be = h[0] / (a1 * h[1] + h[2] + 1e-300);
+        if (be < 1e-12 || (be < 1e-9 && be > 0.5 * be_prev)) { status = OBEM_OK; break; }
+        be_prev = be;
+        if (it == 30) break;
+        scale_to_float_kernel<<<(n + 255) / 256, 256, 0, s>>>(r, y, n, nrm);
+        ADJ_CUDA(cudaGetLastError());
+        rc = lu_solve_t(c, y, s);
+        if (rc != OBEM_OK) goto done;
+        unpermute_kernel<<<1, 32, 0, s>>>(y, c->d_piv, n);
+        axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, nrm, n);
+        ADJ_CUDA(cudaGetLastError());
+    }
+    // mu = D nu: the row scale of the equilibrated system
+    mu = (double *)malloc(sizeof(double) * (size_t)n);
+    {
+        double *ds = (double *)malloc(sizeof(double) * (size_t)n);
+        if (!mu || !ds) { free(ds); rc = obem_fail(c, OBEM_ERR_ARG, "adjoint: host allocation failed"); goto done; }
+        ADJ_CUDA(cudaMemcpyAsync(mu, x, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        ADJ_CUDA(cudaMemcpyAsync(ds, c->d_rowscale, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        ADJ_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; ++i) mu[i] *= ds[i];
+        free(ds);
+    }
+    if (dL_dgv) {
+        for (int k = 0; k < c->n_groups; ++k) dL_dgv[k] = 0.0;
+        for (int i = 0; i < n; ++i)
+            if (c->h_kind[i] == OBEM_CELL_ELECTRODE && c->h_group[i] >= 0 && c->h_group[i] < c->n_groups)
+                dL_dgv[c->h_group[i]] += mu[i];
+    }
+    if (dL_db) {
+        float *hf = (float *)malloc(sizeof(float) * (size_t)n);
+        if (!hf) { rc = obem_fail(c, OBEM_ERR_ARG, "adjoint: host allocation failed"); goto done; }
+        for (int i = 0; i < n; ++i) hf[i] = (float)mu[i];
+        cudaError_t e = cudaMemcpyAsync(dL_db, hf, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        free(hf);
+        ADJ_CUDA(e);
+    }
+    cudaEventRecord(e1, s);
+    ADJ_CUDA(cudaStreamSynchronize(s));
+    if (rep) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        rep->iterations = it;
+        rep->status = status;
+        rep->backward_error = be;
+        rep->factor_ms = c->factor_ms;
+        rep->solve_ms = ms;
+    }
+    if (status != OBEM_OK)
+        rc = obem_fail(c, OBEM_ERR_NOT_CONVERGED, "adjoint refinement stopped at backward error %.3e after %d iterations",
+                       be, it);
+done:
+#undef ADJ_CUDA
+    free(mu);
+    if (part) cudaFree(part);
+    if (col) cudaFree(col);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}

@@ -386,6 +386,15 @@ extern "C" int obem_bem_solve(obem_ctx *c, const double *gv, const float *sigma_
     return obem_solve_system(c, gv, sigma_free, drhs, sigma_out, rep, (cudaStream_t)stream);
 }
 
+extern "C" int obem_bem_solve_adjoint(obem_ctx *c, const float *dL_dsigma, double *dL_dgroup_voltage,
+                                      float *dL_db, obem_solve_report *rep, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (!c->factored) return obem_fail(c, OBEM_ERR_STATE, "solve adjoint: call obem_bem_assemble first");
+    if (!dL_dsigma) return obem_fail(c, OBEM_ERR_ARG, "solve adjoint: dL_dsigma is NULL");
+    return obem_solve_adjoint(c, dL_dsigma, dL_dgroup_voltage, dL_db, rep, (cudaStream_t)stream);
+}
+
 extern "C" int obem_field_eval(obem_ctx *c, const float *targets, int32_t nt, const float *sources,
                                int32_t ns, int32_t self_exclude, const float *sigma, float *E_out,
                                obem_stream stream)

@@ -204,3 +204,5 @@ int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint3
 int obem_assemble_and_factor(obem_ctx *ctx, int precision, cudaStream_t s);
 int obem_solve_system(obem_ctx *ctx, const double *gv, const float *sigma_free, const float *drhs,
                       float *sigma_out, obem_solve_report *rep, cudaStream_t s);
+int obem_solve_adjoint(obem_ctx *ctx, const float *g, double *dL_dgv, float *dL_db, obem_solve_report *rep,
+                       cudaStream_t s);

@@ -89,6 +89,7 @@ def load():
     lib.obem_mesh_load.argtypes = [P, I, P, P, P, P, P, I]
     lib.obem_bem_assemble.argtypes = [P, I, P]
     lib.obem_bem_solve.argtypes = [P, P, P, P, P, C.POINTER(obem_solve_report), P]
+    lib.obem_bem_solve_adjoint.argtypes = [P, P, P, P, C.POINTER(obem_solve_report), P]
     lib.obem_field_eval.argtypes = [P, P, I, P, I, I, P, P, P]
     lib.obem_field_eval_backward.argtypes = [P, P, I, P, I, I, P, P, P, P, P, P]
     lib.obem_step.argtypes = [P, C.POINTER(obem_state), P, U, P, P]
@@ -97,7 +98,7 @@ def load():
     lib.obem_profile.argtypes = [P, I]
     lib.obem_stage_times.argtypes = [P, P, P]
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
-              "obem_bem_solve", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
+              "obem_bem_solve", "obem_bem_solve_adjoint", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
               "obem_stage_times"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
@@ -189,6 +190,47 @@ def obem_bem_solve(ctx, group_voltage, sigma_out, sigma_free=None, drhs=None, st
     return {"iterations": rep.iterations, "status": rep.status,
             "backward_error": rep.backward_error, "factor_ms": rep.factor_ms,
             "solve_ms": rep.solve_ms, "rc": rc}
+
+
+def obem_bem_solve_adjoint(ctx, dL_dsigma, n_groups, dL_db=None, stream=None):
+    """Adjoint of obem_bem_solve: returns (dL/dV [n_groups] float64 numpy,
+    report) and writes dL/db into dL_db (device [n_panels]) if given."""
+    dv = np.zeros(max(int(n_groups), 1), np.float64)
+    rep = obem_solve_report()
+    _check(ctx, load().obem_bem_solve_adjoint(ctx, _ptr(dL_dsigma), dv.ctypes.data_as(C.c_void_p),
+                                              _ptr(dL_db), C.byref(rep), _stream(stream)))
+    return dv[:int(n_groups)], rep
+
+
+class BemSolve(torch.autograd.Function):
+    """sigma = bem_solve(V, sigma_free, drhs) as a differentiable op (the
+    context must hold the factors of the loaded mesh).  group_voltage is a
+    float64 CPU tensor [n_groups]; sigma_free and drhs are device tensors
+    [n_panels] or None.  The backward is obem_bem_solve_adjoint."""
+
+    @staticmethod
+    def forward(fctx, ctx, group_voltage, sigma_free, drhs, n_panels):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        sigma = torch.empty(int(n_panels), dtype=torch.float32, device=dev)
+        gv = group_voltage.detach().to("cpu", torch.float64).contiguous().numpy()
+        obem_bem_solve(ctx, gv, sigma, sigma_free=sigma_free, drhs=drhs)
+        fctx.ctx = ctx
+        fctx.n_groups = int(group_voltage.numel())
+        return sigma
+
+    @staticmethod
+    def backward(fctx, grad):
+        grad = grad.contiguous().float()
+        need_v, need_f, need_d = fctx.needs_input_grad[1:4]
+        db = torch.empty_like(grad) if (need_f or need_d) else None
+        dv, _ = obem_bem_solve_adjoint(fctx.ctx, grad, fctx.n_groups, dL_db=db)
+        gv = torch.from_numpy(dv.copy()) if need_v else None
+        return None, gv, db if need_f else None, db if need_d else None, None
+
+
+def bem_solve(ctx, group_voltage, n_panels, sigma_free=None, drhs=None):
+    """Differentiable BEM solve (see BemSolve)."""
+    return BemSolve.apply(ctx, group_voltage, sigma_free, drhs, n_panels)
 
 
 def obem_field_eval(ctx, targets, E_out, sources=None, self_exclude=False, sigma=None,

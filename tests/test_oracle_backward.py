@@ -163,3 +163,80 @@ def test_field_backward_self_exclusion():
     # vector leaves the pair sum unchanged, so the gradients add up to zero
     tot = dp.sum(axis=0) + dq[:, :3].sum(axis=0)
     assert np.abs(tot).max() <= 1e-9 * np.abs(dp).max()
+
+
+# ----------------------------------------------------------------------------
+# adjoint of the BEM solve: sigma depends linearly on (V, sigma_free, drhs),
+# so the gradient of L = g . sigma is exact from solves with unit inputs
+# ----------------------------------------------------------------------------
+def _sphere_mesh():
+    return inputs.dielectric_sphere_in_plates(radius=1e-3, level=1, eps_r=4.0, side=2e-2, gap=1e-2, n_plate=4)
+
+
+def test_bem_adjoint_voltage_gradient_is_exact_by_linearity():
+    mesh = _sphere_mesh()
+    rng = np.random.default_rng(6)
+    g = rng.normal(0, 1.0, mesh.n)
+    mu, dV = oracle.bem_solve_adjoint(mesh, g)
+    ng = len(mesh.group_voltage)
+    assert ng >= 2
+    for k in range(ng):
+        e = np.zeros(ng)
+        e[k] = 1.0
+        ref = float(g @ oracle.bem_solve(mesh, group_voltage=e))
+        assert abs(dV[k] - ref) <= 1e-9 * max(abs(ref), np.abs(dV).max())
+
+
+def test_bem_adjoint_free_density_and_rhs_gradient():
+    mesh = _sphere_mesh()
+    rng = np.random.default_rng(7)
+    g = rng.normal(0, 1.0, mesh.n)
+    mu, _ = oracle.bem_solve_adjoint(mesh, g)
+    zero_v = np.zeros(len(mesh.group_voltage))
+    dd = np.flatnonzero(mesh.kind == 1)
+    ed = np.flatnonzero(mesh.kind == 0)
+    assert len(dd) > 0 and len(ed) > 0
+    for i in (dd[0], dd[len(dd) // 2], ed[3]):
+        e = np.zeros(mesh.n)
+        e[i] = 1.0
+        # a unit free density on a dielectric cell, or a unit rhs correction
+        if mesh.kind[i] == 1:
+            ref = float(g @ oracle.bem_solve(mesh, sigma_free=e, group_voltage=zero_v))
+            assert abs(mu[i] - ref) <= 1e-9 * np.abs(mu).max()
+        ref = float(g @ oracle.bem_solve(mesh, drhs=e, group_voltage=zero_v))
+        assert abs(mu[i] - ref) <= 1e-9 * np.abs(mu).max()
+
+
+def _probe_line(mesh, n=64):
+    """Probe points on a line across the sphere-in-plates chamber, off every
+    surface (the loss of the differentiable-field workload: mean |E|^2)."""
+    c = np.array([1e-2, 1e-2, 5e-3])
+    t = np.linspace(-1.0, 1.0, n)
+    return c + np.column_stack([4e-3 * t, 1.5e-3 + 0 * t, 4e-3 * t])
+
+
+def _probe_loss(mesh, V, pts):
+    sigma = oracle.bem_solve(mesh, group_voltage=V)
+    E, _ = oracle.panel_field(mesh.tri, sigma, pts)
+    return float((E ** 2).sum(axis=1).mean()), sigma, E
+
+
+def test_probe_loss_voltage_gradient_matches_central_differences():
+    """dL/dV of L = mean |E|^2 at probes, E from sigma = solve(V): the
+    oracle's chain (field backward, then the adjoint solve) against FP64
+    central differences with h = 1e-4 relative.  L is quadratic in V, so the
+    central difference is exact up to rounding."""
+    mesh = _sphere_mesh()
+    pts = _probe_line(mesh)
+    V = np.array([-300.0, 1000.0])
+    L, sigma, E = _probe_loss(mesh, V, pts)
+    g = np.column_stack([2.0 * E / len(pts), np.zeros(len(pts))])
+    dsig, _, _ = oracle.field_backward(mesh.tri, sigma, pts, None, False, g)
+    _, dV = oracle.bem_solve_adjoint(mesh, dsig)
+    for k in range(2):
+        h = 1e-4 * abs(V[k])
+        Vp, Vm = V.copy(), V.copy()
+        Vp[k] += h
+        Vm[k] -= h
+        fd = (_probe_loss(mesh, Vp, pts)[0] - _probe_loss(mesh, Vm, pts)[0]) / (2 * h)
+        assert abs(dV[k] - fd) <= 1e-7 * np.abs(dV).max()
