@@ -30,7 +30,31 @@ sys.path.insert(0, ROOT)
 METRIC = "electron-steps/s & field pair-evals/s (1e6 charges, 60k panels), % FP32 peak"
 UNIT = "electron-steps/s"
 FLOPS_PER_PAIR = 18          # 3 sub, 3 fma (r^2), 3 mul, 3 fma (E): FFMA counted as 2
+LANE_OPS_PER_PAIR = 12       # FP32-pipe lane operations per pair (+ 1 rsqrt)
 FP32_LANES_PER_SM = 128
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "nbody_kernel_dram_traffic.json")
+
+
+def _file_sha256(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def nbody_traffic_per_launch(n_targets):
+    """DRAM bytes per launch of the all-pairs kernel from the committed ncu
+    record (bytes per target x targets; the sources are re-read from L2, so
+    traffic grows with the targets only), or None when the kernel source has
+    changed since the counters were taken."""
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+        src = os.path.join(ROOT, rec["source"])
+        if _file_sha256(src) != rec["source_sha256"]:
+            return None
+        return rec["dram_bytes_per_target"] * n_targets
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _args():
@@ -136,9 +160,14 @@ def cpu_baseline(mesh, ch, gas, trk, seconds, rng_seed=0):
         oracle.step(sub, (E1 + E2).astype(np.float32), 0, int(ch.id.max()) + 1, gas, trk, 4 * S + 64)
         return time.perf_counter() - t0
 
-    t = run(8)
-    S = int(max(8, min(len(el), 8 * seconds / max(t, 1e-3))))
-    t = run(S)
+    # calibrate on growing samples: a few targets leave most host cores idle,
+    # so the cost per electron is only linear once every core has work
+    S, t = 8, run(8)
+    for frac in (0.05, 1.0, 1.0):
+        if frac == 1.0 and t >= 0.66 * seconds:
+            break
+        S = int(max(8, min(len(el), S * frac * seconds / max(t, 1e-3))))
+        t = run(S)
     return {"value": S / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": "%d sampled electrons: FP64 field from all %d cells and all %d charges, "
                       "plus their binary32 step (%.1f s)" % (S, mesh.n, ch.n, t)}
@@ -261,6 +290,14 @@ def run_ours(a, ws, rank, local):
     kern_s = prof["pairs_ms"] / 1e3
     achieved = FLOPS_PER_PAIR * pairs / kern_s / 1e12 if kern_s > 0 else 0.0
     peak_load = sms * FP32_LANES_PER_SM * 2 * (clk.get("sm_mhz") or sm_max) * 1e6 / 1e12
+    # measured FP32 rate of this GPU right after the timed region (FFMA2 chains)
+    alu = obem.obem_alu_rates(ctx)
+    peak_meas = alu["fp32_tflops"]
+    # the kernel's FP32-pipe rate against the measured ceiling of its own mix
+    # (12 lane-ops per rsqrt), both per SM per clock at the clock under load
+    mhz_load = clk.get("sm_mhz") or alu["sm_mhz"]
+    lane_rate = LANE_OPS_PER_PAIR * pairs / kern_s / sms / (mhz_load * 1e6) if kern_s > 0 else 0.0
+    traffic = nbody_traffic_per_launch(ch.n)
     # ---- end to end: state from pinned host memory and back, every step
     e2e = None
     if not a.no_e2e:
@@ -295,9 +332,21 @@ def run_ours(a, ws, rank, local):
         "cell_evals_per_step": {"centroid": prof["cells_1pt"] / a.steps, "3pt": prof["cells_3pt"] / a.steps,
                                 "7pt": prof["cells_7pt"] / a.steps, "closed_form": prof["cells_closed"] / a.steps},
         "roofline": {"bound": "alu", "kernel": "nbody_kernel (all-pairs field)", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                     "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (sms, sm_max),
-                     "traffic": None},
+                     "peak": peak_meas, "unit": "TFLOP/s", "frac": achieved / peak_meas if peak_meas else None,
+                     "peak_source": "measured: packed f32x2 FMA chains on all %d SMs at %.0f MHz "
+                                    "(obem_alu_rates, run after the timed region)" % (sms, alu["sm_mhz"]),
+                     "peak_nominal": peak,
+                     "frac_of_nominal": achieved / peak if peak else None,
+                     "nominal_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (sms, sm_max),
+                     "mix_ceiling": {"kernel_lane_ops_per_sm_clk": lane_rate,
+                                     "measured_mix12_lane_ops_per_sm_clk": alu["mix12_lane_ops_per_sm_clk"],
+                                     "frac": lane_rate / alu["mix12_lane_ops_per_sm_clk"]
+                                     if alu["mix12_lane_ops_per_sm_clk"] else None,
+                                     "rsqrt_per_sm_clk": alu["rsqrt_per_sm_clk"]},
+                     "traffic": traffic,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per target, "
+                                       "scaled to %d targets (%s)" % (ch.n, os.path.relpath(TRAFFIC_RECORD, ROOT))
+                                       if traffic is not None else "no ncu record for the current kernel source"},
         "clocks": clk,
         "gpu_launches": prof["launches"],
         "e2e": e2e,

@@ -22,6 +22,7 @@ UNITS = {
     "step.cu": ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"],
     "bem.cu": [],
     "backward.cu": [],
+    "peak.cu": [],
 }
 
 

@@ -96,10 +96,11 @@ def load():
     lib.obem_field_eval_noalloc.argtypes = [P, I, P, I, I, P, P, I, P, C.c_char_p, I, P]
     lib.obem_field_eval_noalloc.restype = C.c_int
     lib.obem_profile.argtypes = [P, I]
+    lib.obem_alu_rates.argtypes = [P, P, P]
     lib.obem_stage_times.argtypes = [P, P, P]
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
               "obem_bem_solve", "obem_bem_solve_adjoint", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
-              "obem_stage_times"):
+              "obem_stage_times", "obem_alu_rates"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -314,6 +315,14 @@ def obem_field_eval_noalloc(targets, E_out, sources=None, self_exclude=False, ce
                                         _stream(stream))
     if rc != OBEM_OK:
         raise ObemError(rc, err.value.decode())
+
+
+def obem_alu_rates(ctx, stream=None):
+    """Measured FP32 / rsqrt rates of the GPU (see include/obem.h)."""
+    out = np.zeros(5, np.float64)
+    _check(ctx, load().obem_alu_rates(ctx, out.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return {"fp32_tflops": out[0], "fp32_lane_ops_per_sm_clk": out[1], "rsqrt_per_sm_clk": out[2],
+            "mix12_lane_ops_per_sm_clk": out[3], "sm_mhz": out[4]}
 
 
 def obem_profile(ctx, enable=True):
