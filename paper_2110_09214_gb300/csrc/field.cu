@@ -860,6 +860,408 @@ nbody_kernel(FieldLaunch L)
     }
 }
 
+// ---------------------------------------------------------------- symmetric all-pairs kernel
+// When the targets are the sources (self_exclude), every unordered pair is
+// evaluated once and its reaction is applied to the other charge (Newton's
+// third law): per ordered pair 8 FP32 lane-operations and half an rsqrt
+// instead of 12 and one.
+//
+// Charges are cut into tiles of SY_T = 1024.  Item (I, d) pairs tile I with
+// tile J = (I + d) mod n for d = 0 .. h_I (d = 0: the tile with itself, done
+// as ordered pairs); with h_I = floor(n/2), minus one for I >= n/2 when n is
+// even, every unordered tile pair occurs exactly once.  A work unit is SY_CH
+// consecutive items of one row; persistent blocks take units from a counter.
+// Inside an off-diagonal item each warp holds 256 targets (8 per lane, four
+// f32x2 packs) and walks the 1024 sources of tile J in rounds of 32: the 32
+// sources sit one per lane and rotate around the warp by shuffles, carrying
+// their own reaction sums, so no reduction is needed; the four warps take
+// different 32-source groups in every round and add their sums into shared
+// memory in a fixed order.  Every unit writes its target-side sums (Ipart) and
+// every item its source-side sums (Jpart) to slots of its own, and
+// nbsym_fold_kernel adds them per charge in a fixed order: the result does
+// not depend on which block ran which unit.  Recombination proposals in both
+// directions go through atomicMin on (d^2, index) keys (order-independent).
+#define SY_THREADS 128
+#define SY_NI 8
+#define SY_NP (SY_NI / 2)
+#define SY_T (SY_THREADS * SY_NI)
+#define SY_CH 16
+#define SY_FOLD 8              // rounds (of 32 sources) between compensated folds
+#define SY_DTILE 256           // staged sources of the d = 0 item
+
+struct SymGeom {
+    int n, hmax, nch;
+};
+__host__ __device__ inline SymGeom sym_geom(int nt)
+{
+    SymGeom g;
+    g.n = (nt + SY_T - 1) / SY_T;
+    g.hmax = g.n / 2;
+    g.nch = (g.hmax + 1 + SY_CH - 1) / SY_CH;
+    return g;
+}
+// off-diagonal items of row I
+__host__ __device__ inline int sym_h(const SymGeom &g, int I)
+{
+    if (g.n & 1) return g.hmax;
+    return I < g.n / 2 ? g.hmax : g.hmax - 1;
+}
+
+size_t obem_sym_jpart_floats(int capacity)
+{
+    const SymGeom g = sym_geom(capacity);
+    return (size_t)g.n * (g.hmax + 1) * 4 * SY_T;
+}
+size_t obem_sym_ipart_floats(int capacity)
+{
+    const SymGeom g = sym_geom(capacity);
+    return (size_t)g.n * g.nch * 8 * SY_T;
+}
+
+__device__ __forceinline__ bool sym_cation_ok(const FieldLaunch &L, int j)
+{
+    return L.species[j] == OBEM_CATION && !(L.birth[j] != 0u && L.birth[j] == L.step);
+}
+
+// binary32 squared distance without contraction (the recombination rule)
+__device__ __forceinline__ float sym_d2(float ax, float ay, float az, float bx, float by, float bz)
+{
+    const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// dynamic shared memory of nbsym_kernel: target-side S and C [NC][SY_NI][SY_THREADS]
+// each, source-side S and C [NC][SY_T] each (reused as the d = 0 staging
+// tile), proposal keys [SY_NI][SY_THREADS]
+__host__ __device__ constexpr size_t sym_smem(int nc, bool recomb)
+{
+    return (size_t)2 * nc * SY_NI * SY_THREADS * 4 + (size_t)2 * nc * SY_T * 4 +
+           (recomb ? (size_t)SY_NI * SY_THREADS * 8 : 0);
+}
+
+template <bool WANT_V, bool RECOMB>
+__global__ void __launch_bounds__(SY_THREADS, 3)
+nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
+{
+    constexpr int NC = WANT_V ? 4 : 3;
+    extern __shared__ __align__(16) unsigned char sy_smem[];
+    typedef float TS[SY_NI][SY_THREADS];
+    TS *s_S = reinterpret_cast<TS *>(sy_smem);                                   // [NC]
+    TS *s_C = s_S + NC;                                                           // [NC]
+    float *s_jS = reinterpret_cast<float *>(s_C + NC);                            // [NC * SY_T]
+    float *s_jC = s_jS + NC * SY_T;
+    SrcPk *s_src = reinterpret_cast<SrcPk *>(s_jS);
+    typedef unsigned long long TB[SY_THREADS];
+    TB *s_best = reinterpret_cast<TB *>(s_jC + NC * SY_T);                        // [SY_NI] (RECOMB)
+    __shared__ int s_unit;
+
+    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
+    if (nt <= 0) return;
+    const SymGeom G = sym_geom(nt);
+    const int units = G.n * G.nch;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float kC = (float)OBEM_KC;
+    const u64 EPS2 = pk(L.eps2, L.eps2);
+    const float RCF = RECOMB ? (L.rc2 + L.eps2) * (1.0f + 3.814697265625e-06f) + 1e-30f : -1.0f;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int unit = s_unit;
+        if (unit >= units) break;
+        const int I = unit / G.nch, kch = unit % G.nch;
+        const int d0 = kch * SY_CH, d1 = min(d0 + SY_CH, sym_h(G, I) + 1);
+        const int base = I * SY_T;
+        // targets of tile I: 8 per thread (k * 128 + tid), four packs
+        u64 TX[SY_NP], TY[SY_NP], TZ[SY_NP], QI[SY_NP];
+        uint32_t emask = 0, cmask = 0;
+#pragma unroll
+        for (int k = 0; k < SY_NI; ++k) {
+            const int i = base + k * SY_THREADS + tid;
+            // position from the targets, charge from the sources (the same charges)
+            const float4 p = i < nt ? L.targets[i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+            const float kq = i < nt ? kC * L.sources[i].w : 0.f;
+            if (k & 1) {
+                TX[k >> 1] = pk(__uint_as_float((uint32_t)TX[k >> 1]), p.x);
+                TY[k >> 1] = pk(__uint_as_float((uint32_t)TY[k >> 1]), p.y);
+                TZ[k >> 1] = pk(__uint_as_float((uint32_t)TZ[k >> 1]), p.z);
+                QI[k >> 1] = pk(__uint_as_float((uint32_t)QI[k >> 1]), kq);
+            } else {
+                TX[k >> 1] = (u64)__float_as_uint(p.x);
+                TY[k >> 1] = (u64)__float_as_uint(p.y);
+                TZ[k >> 1] = (u64)__float_as_uint(p.z);
+                QI[k >> 1] = (u64)__float_as_uint(kq);
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c) { s_S[c][k][tid] = 0.f; s_C[c][k][tid] = 0.f; }
+            if (RECOMB) {
+                s_best[k][tid] = ~0ull;
+                if (i < nt && L.species[i] == OBEM_ELECTRON) emask |= 1u << k;
+                if (i < nt && sym_cation_ok(L, i)) cmask |= 1u << k;
+            }
+        }
+        for (int d = d0; d < d1; ++d) {
+            const int J = I + d < G.n ? I + d : I + d - G.n;
+            const int jb = J * SY_T;
+            if (d == 0) {
+                // ordered pairs inside tile I, self pair skipped; target side only
+                for (int sb = 0; sb < SY_T; sb += SY_DTILE) {
+                    __syncthreads();
+                    for (int l = tid; l < SY_DTILE; l += SY_THREADS) {
+                        const int j = jb + sb + l;
+                        SrcPk sp;
+                        if (j < nt) {
+                            const float4 s = L.sources[j];
+                            const float kq = kC * s.w;
+                            sp.xx = pk(s.x, s.x); sp.yy = pk(s.y, s.y); sp.zz = pk(s.z, s.z); sp.qq = pk(kq, kq);
+                        } else {
+                            sp.xx = sp.yy = sp.zz = pk(2e18f, 2e18f);
+                            sp.qq = pk(0.f, 0.f);
+                        }
+                        s_src[l] = sp;
+                    }
+                    __syncthreads();
+                    float part[SY_NI][4];
+#pragma unroll
+                    for (int k = 0; k < SY_NI; ++k) part[k][0] = part[k][1] = part[k][2] = part[k][3] = 0.f;
+                    for (int jj = 0; jj < SY_DTILE; ++jj) {
+                        const int j = jb + sb + jj;
+                        float sx, sy, sz, sq, dum;
+                        upk(s_src[jj].xx, sx, dum); upk(s_src[jj].yy, sy, dum);
+                        upk(s_src[jj].zz, sz, dum); upk(s_src[jj].qq, sq, dum);
+#pragma unroll
+                        for (int k = 0; k < SY_NI; ++k) {
+                            const int i = base + k * SY_THREADS + tid;
+                            if (j == i) continue;
+                            float txk, tyk, tzk, t2;
+                            if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
+                            else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
+                            const float dx = __fsub_rn(txk, sx), dy = __fsub_rn(tyk, sy), dz = __fsub_rn(tzk, sz);
+                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, L.eps2)));
+                            const float inv = rsq(r2);
+                            const float s = sq * inv;
+                            const float s3 = s * (inv * inv);
+                            part[k][0] = fmaf(dx, s3, part[k][0]);
+                            part[k][1] = fmaf(dy, s3, part[k][1]);
+                            part[k][2] = fmaf(dz, s3, part[k][2]);
+                            part[k][3] += s;
+                            if (RECOMB && ((emask >> k) & 1u) && r2 < RCF && j < nt && sym_cation_ok(L, j)) {
+                                const float d2 = sym_d2(txk, tyk, tzk, sx, sy, sz);
+                                if (d2 <= L.rc2) {
+                                    const u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
+                                    if (key < s_best[k][tid]) s_best[k][tid] = key;
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < SY_NI; ++k)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            float sv = s_S[c][k][tid], cv = s_C[c][k][tid];
+                            two_sum_acc(sv, cv, part[k][c]);
+                            s_S[c][k][tid] = sv;
+                            s_C[c][k][tid] = cv;
+                        }
+                }
+                continue;
+            }
+            // off-diagonal item: source-side sums of tile J, compensated, in shared memory
+            __syncthreads();
+            for (int l = tid; l < 2 * NC * SY_T; l += SY_THREADS) s_jS[l] = 0.f;   // s_jS and s_jC
+            __syncthreads();
+            u64 AX[SY_NP], AY[SY_NP], AZ[SY_NP], AV[SY_NP];
+#pragma unroll
+            for (int p = 0; p < SY_NP; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
+            for (int r = 0; r < 32; ++r) {
+                const int grp = (r + 8 * warp) & 31;
+                const int j0 = jb + grp * 32;
+                float4 sj = j0 + lane < nt ? L.sources[j0 + lane] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
+                float jx = sj.x, jy = sj.y, jz = sj.z, jq = kC * sj.w;
+                float ax = 0.f, ay = 0.f, az = 0.f, av = 0.f;
+                for (int s = 0; s < 32; ++s) {
+                    const u64 JX = pk(jx, jx), JY = pk(jy, jy), JZ = pk(jz, jz), JQ = pk(jq, jq);
+                    u64 PX = 0ull, PY = 0ull, PZ = 0ull, PV = 0ull;
+                    bool hit = false;
+#pragma unroll
+                    for (int p = 0; p < SY_NP; ++p) {
+                        const u64 dx = sub2(TX[p], JX);
+                        const u64 dy = sub2(TY[p], JY);
+                        const u64 dz = sub2(TZ[p], JZ);
+                        u64 r2 = fma2(dx, dx, EPS2);
+                        r2 = fma2(dy, dy, r2);
+                        r2 = fma2(dz, dz, r2);
+                        float ra, rb;
+                        upk(r2, ra, rb);
+                        if (RECOMB) hit |= (ra < RCF) | (rb < RCF);
+                        const u64 inv = pk(rsq(ra), rsq(rb));
+                        const u64 inv3 = mul2(mul2(inv, inv), inv);
+                        const u64 si = mul2(JQ, inv3);
+                        const u64 sjp = mul2(QI[p], inv3);
+                        AX[p] = fma2(dx, si, AX[p]);
+                        AY[p] = fma2(dy, si, AY[p]);
+                        AZ[p] = fma2(dz, si, AZ[p]);
+                        PX = fma2(dx, sjp, PX);
+                        PY = fma2(dy, sjp, PY);
+                        PZ = fma2(dz, sjp, PZ);
+                        if (WANT_V) {
+                            AV[p] = fma2(JQ, inv, AV[p]);
+                            PV = fma2(QI[p], inv, PV);
+                        }
+                    }
+                    if (RECOMB && hit) {
+                        // rare: the exact binary32 distance and both directions of the partner rule
+                        const int j = j0 + ((lane + s) & 31);
+                        const bool j_el = j < nt && L.species[j] == OBEM_ELECTRON;
+                        const bool j_ca = j < nt && sym_cation_ok(L, j);
+#pragma unroll
+                        for (int k = 0; k < SY_NI; ++k) {
+                            const int i = base + k * SY_THREADS + tid;
+                            const bool ie = (emask >> k) & 1u, ic = (cmask >> k) & 1u;
+                            if (!((ie && j_ca) || (ic && j_el))) continue;
+                            float txk, tyk, tzk, t2;
+                            if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
+                            else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
+                            if (ie && j_ca) {
+                                const float d2 = sym_d2(txk, tyk, tzk, jx, jy, jz);
+                                if (d2 <= L.rc2) {
+                                    const u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
+                                    if (key < s_best[k][tid]) s_best[k][tid] = key;
+                                }
+                            } else {
+                                const float d2 = sym_d2(jx, jy, jz, txk, tyk, tzk);
+                                if (d2 <= L.rc2)
+                                    atomicMin(&L.prop[j], ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)i);
+                            }
+                        }
+                    }
+                    float a, b;
+                    upk(PX, a, b); ax += a + b;
+                    upk(PY, a, b); ay += a + b;
+                    upk(PZ, a, b); az += a + b;
+                    if (WANT_V) { upk(PV, a, b); av += a + b; }
+                    // pass the source and its sums to the next lane
+                    const int src = (lane + 1) & 31;
+                    jx = __shfl_sync(0xffffffffu, jx, src);
+                    jy = __shfl_sync(0xffffffffu, jy, src);
+                    jz = __shfl_sync(0xffffffffu, jz, src);
+                    jq = __shfl_sync(0xffffffffu, jq, src);
+                    ax = __shfl_sync(0xffffffffu, ax, src);
+                    ay = __shfl_sync(0xffffffffu, ay, src);
+                    az = __shfl_sync(0xffffffffu, az, src);
+                    if (WANT_V) av = __shfl_sync(0xffffffffu, av, src);
+                }
+                // after 32 passes the sums are back with their source: add this warp's part
+                {
+                    const int jl = grp * 32 + lane;
+                    float sv, cv;
+                    sv = s_jS[0 * SY_T + jl]; cv = s_jC[0 * SY_T + jl]; two_sum_acc(sv, cv, ax);
+                    s_jS[0 * SY_T + jl] = sv; s_jC[0 * SY_T + jl] = cv;
+                    sv = s_jS[1 * SY_T + jl]; cv = s_jC[1 * SY_T + jl]; two_sum_acc(sv, cv, ay);
+                    s_jS[1 * SY_T + jl] = sv; s_jC[1 * SY_T + jl] = cv;
+                    sv = s_jS[2 * SY_T + jl]; cv = s_jC[2 * SY_T + jl]; two_sum_acc(sv, cv, az);
+                    s_jS[2 * SY_T + jl] = sv; s_jC[2 * SY_T + jl] = cv;
+                    if (WANT_V) {
+                        sv = s_jS[3 * SY_T + jl]; cv = s_jC[3 * SY_T + jl]; two_sum_acc(sv, cv, av);
+                        s_jS[3 * SY_T + jl] = sv; s_jC[3 * SY_T + jl] = cv;
+                    }
+                }
+                if ((r + 1) % SY_FOLD == 0) {
+#pragma unroll
+                    for (int p = 0; p < SY_NP; ++p) {
+                        float a, b;
+                        float sv, cv;
+#define SY_FOLD1(Acc, c)                                                                   \
+    upk(Acc[p], a, b);                                                                     \
+    sv = s_S[c][2 * p][tid]; cv = s_C[c][2 * p][tid]; two_sum_acc(sv, cv, a);              \
+    s_S[c][2 * p][tid] = sv; s_C[c][2 * p][tid] = cv;                                      \
+    sv = s_S[c][2 * p + 1][tid]; cv = s_C[c][2 * p + 1][tid]; two_sum_acc(sv, cv, b);      \
+    s_S[c][2 * p + 1][tid] = sv; s_C[c][2 * p + 1][tid] = cv;                              \
+    Acc[p] = 0ull;
+                        SY_FOLD1(AX, 0)
+                        SY_FOLD1(AY, 1)
+                        SY_FOLD1(AZ, 2)
+                        if (WANT_V) { SY_FOLD1(AV, NC - 1) }
+#undef SY_FOLD1
+                    }
+                }
+                __syncthreads();
+            }
+            // the item's source-side sums (S + C) to its own slot
+            float *jp = jpart + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
+            for (int l = tid; l < NC * SY_T; l += SY_THREADS) jp[l] = s_jS[l] + s_jC[l];
+        }
+        // the unit's target-side sums (S and C) to its own slot
+        float *ip = ipart + ((size_t)I * G.nch + kch) * 8 * SY_T;
+#pragma unroll
+        for (int k = 0; k < SY_NI; ++k)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                ip[(2 * c) * SY_T + k * SY_THREADS + tid] = s_S[c][k][tid];
+                ip[(2 * c + 1) * SY_T + k * SY_THREADS + tid] = s_C[c][k][tid];
+            }
+        if (RECOMB) {
+#pragma unroll
+            for (int k = 0; k < SY_NI; ++k) {
+                const int i = base + k * SY_THREADS + tid;
+                const u64 b = s_best[k][tid];
+                if (i < nt && b != ~0ull) atomicMin(&L.prop[i], b);
+            }
+        }
+    }
+}
+
+// E_out[t] = init + target-side sums of t's row + minus the source-side sums of
+// every item whose second tile holds t, added in a fixed order (FP64).
+template <bool WANT_V>
+__global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float *ipart, int add)
+{
+    constexpr int NC = WANT_V ? 4 : 3;
+    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const SymGeom G = sym_geom(nt);
+    const int T = t / SY_T, w = t % SY_T;
+    double e[4] = {0.0, 0.0, 0.0, 0.0};
+    if (add) {
+        const float4 q = L.E_out[t];
+        e[0] = q.x; e[1] = q.y; e[2] = q.z; e[3] = q.w;
+    } else {
+        e[0] = L.e_ext.x; e[1] = L.e_ext.y; e[2] = L.e_ext.z;
+    }
+    for (int k = 0; k < G.nch; ++k) {
+        const float *ip = ipart + ((size_t)T * G.nch + k) * 8 * SY_T;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) e[c] += (double)ip[(2 * c) * SY_T + w] + (double)ip[(2 * c + 1) * SY_T + w];
+    }
+    for (int d = 1; d <= G.hmax; ++d) {
+        const int I = T - d >= 0 ? T - d : T - d + G.n;
+        if (d > sym_h(G, I)) continue;
+        const float *jp = jpart + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) e[c] += (c < 3 ? -1.0 : 1.0) * (double)jp[c * SY_T + w];
+    }
+    L.E_out[t] = make_float4((float)e[0], (float)e[1], (float)e[2], WANT_V ? (float)e[3] : 0.f);
+}
+
+// occupancy-limited persistent grid of the symmetric kernel
+int obem_sym_grid(int device)
+{
+    int sms = 0, best = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    void (*ks[])(FieldLaunch, float *, float *, int *) = {nbsym_kernel<true, false>, nbsym_kernel<false, true>,
+                                                          nbsym_kernel<false, false>};
+    const size_t sm[] = {sym_smem(4, false), sym_smem(3, true), sym_smem(3, false)};
+    for (int q = 0; q < 3; ++q) {
+        if (cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks[q], SY_THREADS, sm[q]) != cudaSuccess) return 0;
+        best = (best == 0 || occ < best) ? occ : best;
+    }
+    return sms * (best > 0 ? best : 1);
+}
+
 // counters[0] += nt * (ns - self pairs): the pairs of the all-pairs kernel
 __global__ void pair_count_kernel(FieldLaunch L)
 {
@@ -929,7 +1331,26 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             if (L.events) ctx->launches++;
         }
         const bool rec = L.prop != NULL;
-        if (L.want_v) {
+        // self_exclude: the targets are the sources (same charges, nt == ns)
+        const bool sym = ctx->sym_jpart && L.self_exclude && capacity_targets <= ctx->sym_cap &&
+                         (L.want_v ? !rec : true);
+        if (sym) {
+            if (rec) OBEM_CUDA(ctx, cudaMemsetAsync(L.prop, 0xff, sizeof(unsigned long long) * capacity_targets, s));
+            OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
+            const dim3 sg(ctx->sym_grid);
+            if (L.want_v)
+                nbsym_kernel<true, false><<<sg, SY_THREADS, sym_smem(4, false), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
+            else if (rec)
+                nbsym_kernel<false, true><<<sg, SY_THREADS, sym_smem(3, true), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
+            else
+                nbsym_kernel<false, false><<<sg, SY_THREADS, sym_smem(3, false), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
+            OBEM_LAUNCH(ctx);
+            const int fb = (capacity_targets + 255) / 256;
+            if (L.want_v) nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, cells ? 1 : 0);
+            else nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, cells ? 1 : 0);
+            OBEM_LAUNCH(ctx);
+            if (L.events) ctx->launches += 2;
+        } else if (L.want_v) {
             if (cells) nbody_kernel<true, false, true><<<grid, FT_THREADS, 0, s>>>(L);
             else nbody_kernel<true, false, false><<<grid, FT_THREADS, 0, s>>>(L);
         } else if (rec) {
@@ -939,8 +1360,10 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             if (cells) nbody_kernel<false, false, true><<<grid, FT_THREADS, 0, s>>>(L);
             else nbody_kernel<false, false, false><<<grid, FT_THREADS, 0, s>>>(L);
         }
-        OBEM_LAUNCH(ctx);
-        if (L.events) ctx->launches++;
+        if (!sym) {
+            OBEM_LAUNCH(ctx);
+            if (L.events) ctx->launches++;
+        }
     }
     if (!cells && !charges) {
         const_field_kernel<<<(capacity_targets + 255) / 256, 256, 0, s>>>(L);

@@ -96,6 +96,26 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->s_blocks, sizeof(int2) * ((size_t)cap / 512 + 2 + (cap < OBEM_NSUPER ? cap : OBEM_NSUPER)));
     ALLOC(c->s_nblocks, sizeof(int32_t) * (OBEM_NSUPER + 8));
 #undef ALLOC
+    // partial sums of the symmetric all-pairs kernel: they grow as capacity^2,
+    // so they are kept only within a quarter of the free memory (and 64 GB)
+    {
+        const size_t jb = sizeof(float) * obem_sym_jpart_floats(cap), ib = sizeof(float) * obem_sym_ipart_floats(cap);
+        size_t fr = 0, tot = 0;
+        c->sym_grid = obem_sym_grid(c->device);
+        if (c->sym_grid > 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess && jb + ib <= fr / 4 &&
+            jb + ib <= ((size_t)64 << 30)) {
+            if (cudaMalloc((void **)&c->sym_jpart, jb) != cudaSuccess ||
+                cudaMalloc((void **)&c->sym_ipart, ib) != cudaSuccess ||
+                cudaMalloc((void **)&c->sym_counter, sizeof(int)) != cudaSuccess) {
+                free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
+                c->sym_jpart = c->sym_ipart = NULL;
+                c->sym_counter = NULL;
+                cudaGetLastError();
+            } else {
+                c->sym_cap = cap;
+            }
+        }
+    }
     (void)bytes;
     *out = c;
     return OBEM_OK;
@@ -110,6 +130,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->s_nsp); free_dev(c->s_blk); free_dev(c->s_ctl); free_dev(c->o_pos);
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
+    free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->prof_ev) {
         for (int i = 0; i < OBEM_PROF_EV * OBEM_PROF_MAX; ++i) cudaEventDestroy(c->prof_ev[i]);

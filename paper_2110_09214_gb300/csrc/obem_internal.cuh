@@ -114,6 +114,12 @@ struct obem_ctx {
     int32_t *s_hist;
     int2 *s_blocks;        // cell-kernel blocks: (first sorted target, count)
     int32_t *s_nblocks;    // [1] number of blocks, [2..] scan scratch
+    // symmetric all-pairs kernel (targets == sources): per-item source-side and
+    // per-unit target-side partial sums, work counter, persistent grid; NULL
+    // when they did not fit the memory budget (the one-sided kernel runs)
+    float *sym_jpart, *sym_ipart;
+    int *sym_counter;
+    int sym_grid, sym_cap;
     // stage timing (obem_profile)
     int prof_on;
     int prof_n;                      // recorded steps (ring of OBEM_PROF_MAX)
@@ -180,6 +186,9 @@ struct FieldLaunch {
 #define OBEM_SUPER_SHIFT 3                        // super-bin = 2 x 2 x 2 bins
 #define OBEM_NSUPER (OBEM_NBINS >> OBEM_SUPER_SHIFT)
 int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets, cudaStream_t s);
+size_t obem_sym_jpart_floats(int capacity);
+size_t obem_sym_ipart_floats(int capacity);
+int obem_sym_grid(int device);
 
 // backward.cu
 struct BwArgs {

@@ -36,11 +36,15 @@ def _gpu_field(ctx, tgt, src=None, self_exclude=False, sigma=None):
     return out.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("n", [1, 2, 33, 511, 512, 513, 1000, 3001])
-def test_nbody_self_exclude(n):
+@pytest.mark.parametrize("symmetric", [False, True])
+@pytest.mark.parametrize("n", [1, 2, 33, 511, 512, 513, 1000, 1025, 2048, 3001, 4096, 6000])
+def test_nbody_self_exclude(n, symmetric):
+    """Both all-pairs kernels: the one-sided one (context capacity below nt)
+    and the symmetric one (each pair once, reaction to the other charge;
+    tiles of 1024: 1..6 tiles, odd and even counts, ragged tails)."""
     rng = np.random.default_rng(n)
     src = _charges(rng, n, pairs=n // 10)
-    ctx = _ctx()
+    ctx = _ctx(cap=max(n, 16) if symmetric else 16)
     try:
         got = _gpu_field(ctx, src, src, self_exclude=True)
     finally:
@@ -159,15 +163,16 @@ def test_empty_and_bad_arguments():
         obem.obem_destroy(ctx)
 
 
-def test_full_size_gem_sampled():
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_full_size_gem_sampled(symmetric):
     """The headline workload at full size -- 60k cells, 1e6 charges -- in the
-    launch configuration of the bench; the oracle computes 64 sampled
-    targets one by one."""
+    launch configuration of the bench (symmetric all-pairs kernel) and with
+    the one-sided kernel; the oracle computes 64 sampled targets one by one."""
     mesh, gas, ch, trk, g = inputs.config_gem(seed=1, n=1_000_000)
     cen = mesh.tri.mean(axis=1)
     sigma = (1e-6 * (1.0 + 0.3 * np.sin(cen[:, 0] / 1e-4)) *
              np.where(mesh.kind == 0, np.where(mesh.group % 2 == 0, 1.0, -1.0), 0.3)).astype(np.float32)
-    ctx = _ctx()
+    ctx = _ctx(cap=ch.n if symmetric else 16)
     try:
         obem.obem_mesh_load(ctx, mesh)
         got = _gpu_field(ctx, ch.pos_q, ch.pos_q, self_exclude=True, sigma=sigma)

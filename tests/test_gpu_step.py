@@ -159,6 +159,47 @@ def test_exempt_and_tie_rules_on_gpu():
     assert sorted(out.id.tolist()) == [6, 7, 8]
 
 
+@pytest.mark.parametrize("n", [9, 1500, 5000])
+def test_fused_partner_search_matches_oracle(n):
+    """Recombination partners proposed inside the fused all-pairs kernel (the
+    symmetric one: each pair once, both directions of the partner rule):
+    binary32 positions alone decide them, so the charges removed must be
+    exactly the oracle's, whatever the field."""
+    gas = inputs.maxwell_gas(0.0, 40.0)
+    gas.nuc[:] = 0.0
+    gas.nu_ion = 0.0
+    trk = inputs.Tracking(dt=1e-12, seed=1, z_lo=-1, z_hi=1, beta=1e-13)
+    trk.softening = 1e-9
+    rc = (3 * 1e-13 * 1e-12 / (4 * math.pi)) ** (1 / 3)
+    rng = np.random.default_rng(n)
+    ne = (n + 1) // 2
+    pe = rng.uniform(0, 5e-5, (ne, 3))
+    pc = rng.uniform(0, 5e-5, (n - ne, 3))
+    k = (n - ne) // 2
+    near = rng.integers(0, ne, k)
+    off = rng.normal(0, 1.0, (k, 3))
+    off *= (rng.uniform(0.2, 1.3, k) * rc / np.linalg.norm(off, axis=1))[:, None]
+    pc[:k] = pe[near] + off
+    pos = np.concatenate([pe, pc])
+    perm = rng.permutation(n)                  # electrons and cations interleaved in memory
+    sp = np.concatenate([np.zeros(ne, np.uint8), np.ones(n - ne, np.uint8)])[perm]
+    ch = inputs.make_charges(pos[perm], np.zeros((n, 3)), sp)
+    cap = n + 16
+    g = GpuRun(gas, trk, cap, flags=obem.OBEM_STEP_SPACE_CHARGE)
+    try:
+        g.upload(ch)
+        gs = g.step(5)
+        out, _ = g.state()
+    finally:
+        g.close()
+    p64 = ch.pos_q.astype(np.float64)
+    Eo = oracle.nbody_field(p64[:, :3], p64, True, trk.softening)[0].astype(np.float32)
+    st, cur, _, os_ = oracle.step(ch, Eo, 5, n, gas, trk, cap)
+    assert st == 0 and gs["status"] == 0
+    assert gs["recombined_pairs"] == os_["recombined_pairs"] > 0
+    assert np.array_equal(np.sort(out.id), np.sort(cur.id))
+
+
 def test_capacity_overflow_is_all_or_nothing():
     gas = inputs.maxwell_gas(1e12, 40.0)
     gas.kind = np.array([inputs.P_IONISATION], np.int32)
