@@ -671,13 +671,12 @@ cell_kernel(FieldLaunch L)
 // blocks per SM.
 #define FT_NP (FT_TPT / 2)
 
-template <bool WANT_V, bool RECOMB, bool ADD>
+template <bool WANT_V, bool ADD>
 __global__ void __launch_bounds__(FT_THREADS, FT_MINB)
 nbody_kernel(FieldLaunch L)
 {
     __shared__ SrcPk s_src[FT_SRC_TILE];
     __shared__ float s_acc[2][WANT_V ? 4 : 3][FT_TPT][FT_THREADS];   // [S|C][component][target][thread]
-    __shared__ unsigned long long s_best[RECOMB ? FT_TPT : 1][FT_THREADS];
 
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
     const int ns = L.ns_dev ? *L.ns_dev : L.ns;
@@ -686,7 +685,6 @@ nbody_kernel(FieldLaunch L)
     const int tid = threadIdx.x;
     constexpr int NC = WANT_V ? 4 : 3;
 
-    uint32_t emask = 0;   // bit k: target k is an electron (looks for a partner)
     u64 TX[FT_NP], TY[FT_NP], TZ[FT_NP];
 #pragma unroll
     for (int k = 0; k < FT_TPT; ++k) {
@@ -711,17 +709,10 @@ nbody_kernel(FieldLaunch L)
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) { s_acc[0][c][k][tid] = e[c]; s_acc[1][c][k][tid] = 0.f; }
-        if (RECOMB) {
-            s_best[RECOMB ? k : 0][tid] = ~0ull;
-            if (i < nt && L.species[i] == OBEM_ELECTRON) emask |= 1u << k;
-        }
     }
 
     const float kC = (float)OBEM_KC;
     const u64 EPS2 = pk(L.eps2, L.eps2);
-    // candidate filter for the partner search: softened r^2 below this (a
-    // little above rc^2 + eps^2, so no pair within rc is missed to rounding)
-    const float RCF = RECOMB ? (L.rc2 + L.eps2) * (1.0f + 3.814697265625e-06f) + 1e-30f : -1.0f;
     for (int sb = 0; sb < ns; sb += FT_SRC_TILE) {
         __syncthreads();
 #pragma unroll
@@ -750,7 +741,6 @@ nbody_kernel(FieldLaunch L)
             for (int jj = 0; jj < FT_SRC_TILE; ++jj) {
                 const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&s_src[jj].xx);
                 const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&s_src[jj].zz);
-                bool hit = false;
 #pragma unroll
                 for (int p = 0; p < FT_NP; ++p) {
                     u64 dx = sub2(TX[p], a.x);
@@ -761,7 +751,6 @@ nbody_kernel(FieldLaunch L)
                     r2 = fma2(dz, dz, r2);
                     float ra, rb;
                     upk(r2, ra, rb);
-                    if (RECOMB) hit |= (ra < RCF) | (rb < RCF);
                     u64 inv = pk(rsq(ra), rsq(rb));
                     u64 s = mul2(b.y, inv);
                     u64 s3 = mul2(s, mul2(inv, inv));
@@ -769,27 +758,6 @@ nbody_kernel(FieldLaunch L)
                     AY[p] = fma2(dy, s3, AY[p]);
                     AZ[p] = fma2(dz, s3, AZ[p]);
                     if (WANT_V) AV[p] = add2(AV[p], s);
-                }
-                if (RECOMB && hit && emask) {
-                    // rare: binary32 distance without contraction, and the partner rules
-                    const int j = sb + jj;
-                    float sx, sy, sz, dum;
-                    upk(a.x, sx, dum); upk(a.y, sy, dum); upk(b.x, sz, dum);
-                    if (j < ns && L.species[j] == OBEM_CATION && !(L.birth[j] != 0u && L.birth[j] == L.step)) {
-#pragma unroll
-                        for (int k = 0; k < FT_TPT; ++k) {
-                            if (!((emask >> k) & 1u)) continue;
-                            float txk, tyk, tzk, t2;
-                            if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
-                            else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
-                            float ddx = __fsub_rn(txk, sx), ddy = __fsub_rn(tyk, sy), ddz = __fsub_rn(tzk, sz);
-                            float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz));
-                            if (d2 <= L.rc2) {
-                                u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
-                                if (key < s_best[RECOMB ? k : 0][tid]) s_best[RECOMB ? k : 0][tid] = key;
-                            }
-                        }
-                    }
                 }
             }
 #pragma unroll
@@ -823,14 +791,6 @@ nbody_kernel(FieldLaunch L)
                     part[k][1] = fmaf(dy, s3, part[k][1]);
                     part[k][2] = fmaf(dz, s3, part[k][2]);
                     part[k][3] += s;
-                    if (RECOMB && ((emask >> k) & 1u) && r2 < RCF && j < ns && L.species[j] == OBEM_CATION &&
-                        !(L.birth[j] != 0u && L.birth[j] == L.step)) {
-                        float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                        if (d2 <= L.rc2) {
-                            u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
-                            if (key < s_best[RECOMB ? k : 0][tid]) s_best[RECOMB ? k : 0][tid] = key;
-                        }
-                    }
                 }
             }
         }
@@ -856,7 +816,6 @@ nbody_kernel(FieldLaunch L)
         e.z = (float)((double)s_acc[0][2][k][tid] + (double)s_acc[1][2][k][tid]);
         e.w = WANT_V ? (float)((double)s_acc[0][NC - 1][k][tid] + (double)s_acc[1][NC - 1][k][tid]) : 0.f;
         L.E_out[i] = e;
-        if (RECOMB) L.prop[i] = s_best[RECOMB ? k : 0][tid];
     }
 }
 
@@ -864,7 +823,8 @@ nbody_kernel(FieldLaunch L)
 // When the targets are the sources (self_exclude), every unordered pair is
 // evaluated once and its reaction is applied to the other charge (Newton's
 // third law): per ordered pair 8 FP32 lane-operations and half an rsqrt
-// instead of 12 and one.
+// instead of 12 and one.  (The recombination partner search runs separately,
+// by spatial hashing, in the step.)
 //
 // Charges are cut into tiles of SY_T = 1024.  Item (I, d) pairs tile I with
 // tile J = (I + d) mod n for d = 0 .. h_I (d = 0: the tile with itself, done
@@ -879,8 +839,7 @@ nbody_kernel(FieldLaunch L)
 // memory in a fixed order.  Every unit writes its target-side sums (Ipart) and
 // every item its source-side sums (Jpart) to slots of its own, and
 // nbsym_fold_kernel adds them per charge in a fixed order: the result does
-// not depend on which block ran which unit.  Recombination proposals in both
-// directions go through atomicMin on (d^2, index) keys (order-independent).
+// not depend on which block ran which unit.
 #define SY_THREADS 128
 #define SY_NI 8
 #define SY_NP (SY_NI / 2)
@@ -918,28 +877,14 @@ size_t obem_sym_ipart_floats(int capacity)
     return (size_t)g.n * g.nch * 8 * SY_T;
 }
 
-__device__ __forceinline__ bool sym_cation_ok(const FieldLaunch &L, int j)
-{
-    return L.species[j] == OBEM_CATION && !(L.birth[j] != 0u && L.birth[j] == L.step);
-}
-
-// binary32 squared distance without contraction (the recombination rule)
-__device__ __forceinline__ float sym_d2(float ax, float ay, float az, float bx, float by, float bz)
-{
-    const float dx = __fsub_rn(ax, bx), dy = __fsub_rn(ay, by), dz = __fsub_rn(az, bz);
-    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-}
-
 // dynamic shared memory of nbsym_kernel: target-side S and C [NC][SY_NI][SY_THREADS]
-// each, source-side S and C [NC][SY_T] each (reused as the d = 0 staging
-// tile), proposal keys [SY_NI][SY_THREADS]
-__host__ __device__ constexpr size_t sym_smem(int nc, bool recomb)
+// each, source-side S and C [NC][SY_T] each (reused as the d = 0 staging tile)
+__host__ __device__ constexpr size_t sym_smem(int nc)
 {
-    return (size_t)2 * nc * SY_NI * SY_THREADS * 4 + (size_t)2 * nc * SY_T * 4 +
-           (recomb ? (size_t)SY_NI * SY_THREADS * 8 : 0);
+    return (size_t)2 * nc * SY_NI * SY_THREADS * 4 + (size_t)2 * nc * SY_T * 4;
 }
 
-template <bool WANT_V, bool RECOMB>
+template <bool WANT_V>
 __global__ void __launch_bounds__(SY_THREADS, 3)
 nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
 {
@@ -951,8 +896,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
     float *s_jS = reinterpret_cast<float *>(s_C + NC);                            // [NC * SY_T]
     float *s_jC = s_jS + NC * SY_T;
     SrcPk *s_src = reinterpret_cast<SrcPk *>(s_jS);
-    typedef unsigned long long TB[SY_THREADS];
-    TB *s_best = reinterpret_cast<TB *>(s_jC + NC * SY_T);                        // [SY_NI] (RECOMB)
     __shared__ int s_unit;
 
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
@@ -962,7 +905,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float kC = (float)OBEM_KC;
     const u64 EPS2 = pk(L.eps2, L.eps2);
-    const float RCF = RECOMB ? (L.rc2 + L.eps2) * (1.0f + 3.814697265625e-06f) + 1e-30f : -1.0f;
 
     for (;;) {
         __syncthreads();
@@ -975,7 +917,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
         const int base = I * SY_T;
         // targets of tile I: 8 per thread (k * 128 + tid), four packs
         u64 TX[SY_NP], TY[SY_NP], TZ[SY_NP], QI[SY_NP];
-        uint32_t emask = 0, cmask = 0;
 #pragma unroll
         for (int k = 0; k < SY_NI; ++k) {
             const int i = base + k * SY_THREADS + tid;
@@ -995,11 +936,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) { s_S[c][k][tid] = 0.f; s_C[c][k][tid] = 0.f; }
-            if (RECOMB) {
-                s_best[k][tid] = ~0ull;
-                if (i < nt && L.species[i] == OBEM_ELECTRON) emask |= 1u << k;
-                if (i < nt && sym_cation_ok(L, i)) cmask |= 1u << k;
-            }
         }
         for (int d = d0; d < d1; ++d) {
             const int J = I + d < G.n ? I + d : I + d - G.n;
@@ -1046,13 +982,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                             part[k][1] = fmaf(dy, s3, part[k][1]);
                             part[k][2] = fmaf(dz, s3, part[k][2]);
                             part[k][3] += s;
-                            if (RECOMB && ((emask >> k) & 1u) && r2 < RCF && j < nt && sym_cation_ok(L, j)) {
-                                const float d2 = sym_d2(txk, tyk, tzk, sx, sy, sz);
-                                if (d2 <= L.rc2) {
-                                    const u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
-                                    if (key < s_best[k][tid]) s_best[k][tid] = key;
-                                }
-                            }
                         }
                     }
 #pragma unroll
@@ -1083,7 +1012,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                 for (int s = 0; s < 32; ++s) {
                     const u64 JX = pk(jx, jx), JY = pk(jy, jy), JZ = pk(jz, jz), JQ = pk(jq, jq);
                     u64 PX = 0ull, PY = 0ull, PZ = 0ull, PV = 0ull;
-                    bool hit = false;
 #pragma unroll
                     for (int p = 0; p < SY_NP; ++p) {
                         const u64 dx = sub2(TX[p], JX);
@@ -1094,7 +1022,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                         r2 = fma2(dz, dz, r2);
                         float ra, rb;
                         upk(r2, ra, rb);
-                        if (RECOMB) hit |= (ra < RCF) | (rb < RCF);
                         const u64 inv = pk(rsq(ra), rsq(rb));
                         const u64 inv3 = mul2(mul2(inv, inv), inv);
                         const u64 si = mul2(JQ, inv3);
@@ -1108,32 +1035,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                         if (WANT_V) {
                             AV[p] = fma2(JQ, inv, AV[p]);
                             PV = fma2(QI[p], inv, PV);
-                        }
-                    }
-                    if (RECOMB && hit) {
-                        // rare: the exact binary32 distance and both directions of the partner rule
-                        const int j = j0 + ((lane + s) & 31);
-                        const bool j_el = j < nt && L.species[j] == OBEM_ELECTRON;
-                        const bool j_ca = j < nt && sym_cation_ok(L, j);
-#pragma unroll
-                        for (int k = 0; k < SY_NI; ++k) {
-                            const int i = base + k * SY_THREADS + tid;
-                            const bool ie = (emask >> k) & 1u, ic = (cmask >> k) & 1u;
-                            if (!((ie && j_ca) || (ic && j_el))) continue;
-                            float txk, tyk, tzk, t2;
-                            if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
-                            else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
-                            if (ie && j_ca) {
-                                const float d2 = sym_d2(txk, tyk, tzk, jx, jy, jz);
-                                if (d2 <= L.rc2) {
-                                    const u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)j;
-                                    if (key < s_best[k][tid]) s_best[k][tid] = key;
-                                }
-                            } else {
-                                const float d2 = sym_d2(jx, jy, jz, txk, tyk, tzk);
-                                if (d2 <= L.rc2)
-                                    atomicMin(&L.prop[j], ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)i);
-                            }
                         }
                     }
                     float a, b;
@@ -1201,14 +1102,6 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                 ip[(2 * c) * SY_T + k * SY_THREADS + tid] = s_S[c][k][tid];
                 ip[(2 * c + 1) * SY_T + k * SY_THREADS + tid] = s_C[c][k][tid];
             }
-        if (RECOMB) {
-#pragma unroll
-            for (int k = 0; k < SY_NI; ++k) {
-                const int i = base + k * SY_THREADS + tid;
-                const u64 b = s_best[k][tid];
-                if (i < nt && b != ~0ull) atomicMin(&L.prop[i], b);
-            }
-        }
     }
 }
 
@@ -1250,10 +1143,9 @@ int obem_sym_grid(int device)
 {
     int sms = 0, best = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    void (*ks[])(FieldLaunch, float *, float *, int *) = {nbsym_kernel<true, false>, nbsym_kernel<false, true>,
-                                                          nbsym_kernel<false, false>};
-    const size_t sm[] = {sym_smem(4, false), sym_smem(3, true), sym_smem(3, false)};
-    for (int q = 0; q < 3; ++q) {
+    void (*ks[])(FieldLaunch, float *, float *, int *) = {nbsym_kernel<true>, nbsym_kernel<false>};
+    const size_t sm[] = {sym_smem(4), sym_smem(3)};
+    for (int q = 0; q < 2; ++q) {
         if (cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]) != cudaSuccess)
             return 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks[q], SY_THREADS, sm[q]) != cudaSuccess) return 0;
@@ -1330,20 +1222,15 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             OBEM_LAUNCH(ctx);
             if (L.events) ctx->launches++;
         }
-        const bool rec = L.prop != NULL;
         // self_exclude: the targets are the sources (same charges, nt == ns)
-        const bool sym = ctx->sym_jpart && L.self_exclude && capacity_targets <= ctx->sym_cap &&
-                         (L.want_v ? !rec : true);
+        const bool sym = ctx->sym_jpart && L.self_exclude && capacity_targets <= ctx->sym_cap;
         if (sym) {
-            if (rec) OBEM_CUDA(ctx, cudaMemsetAsync(L.prop, 0xff, sizeof(unsigned long long) * capacity_targets, s));
             OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
             const dim3 sg(ctx->sym_grid);
             if (L.want_v)
-                nbsym_kernel<true, false><<<sg, SY_THREADS, sym_smem(4, false), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
-            else if (rec)
-                nbsym_kernel<false, true><<<sg, SY_THREADS, sym_smem(3, true), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
+                nbsym_kernel<true><<<sg, SY_THREADS, sym_smem(4), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
             else
-                nbsym_kernel<false, false><<<sg, SY_THREADS, sym_smem(3, false), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
+                nbsym_kernel<false><<<sg, SY_THREADS, sym_smem(3), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
             OBEM_LAUNCH(ctx);
             const int fb = (capacity_targets + 255) / 256;
             if (L.want_v) nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, cells ? 1 : 0);
@@ -1351,14 +1238,11 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             OBEM_LAUNCH(ctx);
             if (L.events) ctx->launches += 2;
         } else if (L.want_v) {
-            if (cells) nbody_kernel<true, false, true><<<grid, FT_THREADS, 0, s>>>(L);
-            else nbody_kernel<true, false, false><<<grid, FT_THREADS, 0, s>>>(L);
-        } else if (rec) {
-            if (cells) nbody_kernel<false, true, true><<<grid, FT_THREADS, 0, s>>>(L);
-            else nbody_kernel<false, true, false><<<grid, FT_THREADS, 0, s>>>(L);
+            if (cells) nbody_kernel<true, true><<<grid, FT_THREADS, 0, s>>>(L);
+            else nbody_kernel<true, false><<<grid, FT_THREADS, 0, s>>>(L);
         } else {
-            if (cells) nbody_kernel<false, false, true><<<grid, FT_THREADS, 0, s>>>(L);
-            else nbody_kernel<false, false, false><<<grid, FT_THREADS, 0, s>>>(L);
+            if (cells) nbody_kernel<false, true><<<grid, FT_THREADS, 0, s>>>(L);
+            else nbody_kernel<false, false><<<grid, FT_THREADS, 0, s>>>(L);
         }
         if (!sym) {
             OBEM_LAUNCH(ctx);
@@ -1585,8 +1469,8 @@ extern "C" int obem_field_eval_noalloc(const float *targets, int32_t nt, const f
     }
     dim3 grid((nt + FT_BLOCK_TARGETS - 1) / FT_BLOCK_TARGETS);
     if (L.sources) {
-        if (cells_on) nbody_kernel<true, false, true><<<grid, FT_THREADS, 0, s>>>(L);
-        else nbody_kernel<true, false, false><<<grid, FT_THREADS, 0, s>>>(L);
+        if (cells_on) nbody_kernel<true, true><<<grid, FT_THREADS, 0, s>>>(L);
+        else nbody_kernel<true, false><<<grid, FT_THREADS, 0, s>>>(L);
     } else if (!cells_on) {
         const_field_kernel<<<(nt + 255) / 256, 256, 0, s>>>(L);
     }

@@ -95,6 +95,11 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->s_hist, sizeof(int32_t) * OBEM_NBINS);
     ALLOC(c->s_blocks, sizeof(int2) * ((size_t)cap / 512 + 2 + (cap < OBEM_NSUPER ? cap : OBEM_NSUPER)));
     ALLOC(c->s_nblocks, sizeof(int32_t) * (OBEM_NSUPER + 8));
+    ALLOC(c->ph_count, sizeof(int32_t) * ((size_t)1 << 20));
+    ALLOC(c->ph_start, sizeof(int32_t) * (((size_t)1 << 20) + 1));
+    ALLOC(c->ph_cursor, sizeof(int32_t) * ((size_t)1 << 20));
+    ALLOC(c->ph_bucket, sizeof(int32_t) * cap);
+    ALLOC(c->ph_sorted, sizeof(int32_t) * cap);
 #undef ALLOC
     // partial sums of the symmetric all-pairs kernel: they grow as capacity^2,
     // so they are kept only within a quarter of the free memory (and 64 GB)
@@ -108,6 +113,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
                 cudaMalloc((void **)&c->sym_ipart, ib) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_counter, sizeof(int)) != cudaSuccess) {
                 free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
+    free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted);
                 c->sym_jpart = c->sym_ipart = NULL;
                 c->sym_counter = NULL;
                 cudaGetLastError();
@@ -131,6 +137,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
     free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
+    free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->prof_ev) {
         for (int i = 0; i < OBEM_PROF_EV * OBEM_PROF_MAX; ++i) cudaEventDestroy(c->prof_ev[i]);
@@ -505,7 +512,6 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         return obem_fail(c, OBEM_ERR_ARG, "step: pos_q / vel / E_in must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     const float4 *E = (const float4 *)E_in;
-    int partners_done = 0;
     cudaEvent_t *ev = NULL;
     if (c->prof_on) {
         ev = c->prof_ev + OBEM_PROF_EV * (c->prof_n % OBEM_PROF_MAX);
@@ -537,22 +543,14 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         L.want_v = 0;
         if (ev) L.counters = c->d_counters;
         L.events = ev;
-        if (c->gas.recomb_on) {
-            L.species = st->species;
-            L.birth = st->birth;
-            L.step = step;
-            L.rc2 = c->gas.rc2;
-            L.prop = c->s_prop;
-        }
         int rc = obem_launch_field(c, L, st->capacity, s);
         if (rc != OBEM_OK) return rc;
         E = c->s_E;
-        partners_done = want_nbody && c->gas.recomb_on;
     } else if (ev) {
         cudaEventRecord(ev[1], s);
         cudaEventRecord(ev[2], s);
     }
-    int rc = obem_launch_step(c, st, E, step, stats, s, partners_done);
+    int rc = obem_launch_step(c, st, E, step, stats, s);
     if (ev) cudaEventRecord(ev[3], s);
     return rc;
 }

@@ -118,6 +118,9 @@ struct obem_ctx {
     // per-unit target-side partial sums, work counter, persistent grid; NULL
     // when they did not fit the memory budget (the one-sided kernel runs)
     float *sym_jpart, *sym_ipart;
+    // partner search: hash-bucket counts / starts / cursors, bucket of each
+    // charge, cations sorted by bucket
+    int32_t *ph_count, *ph_start, *ph_cursor, *ph_bucket, *ph_sorted;
     int *sym_counter;
     int sym_grid, sym_cap;
     // stage timing (obem_profile)
@@ -164,12 +167,6 @@ struct FieldLaunch {
     float4 *E_out;
     float3 e_ext;
     int want_v;
-    // recombination partner search
-    const uint8_t *species;
-    const uint32_t *birth;
-    uint32_t step;
-    float rc2;
-    unsigned long long *prop;
     // optional tier counters [5]: charge pairs, 1-point, 3-point, 7-point, closed-form
     unsigned long long *counters;
     // optional events: [1] after the cell kernels, [2] after the all-pairs kernel,
@@ -205,9 +202,8 @@ struct BwArgs {
 int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s);
 
 // step.cu
-// partners_done: the field pass already proposed recombination partners
 int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,
-                     obem_step_stats *stats, cudaStream_t s, int partners_done);
+                     obem_step_stats *stats, cudaStream_t s);
 
 // bem.cu
 int obem_assemble_and_factor(obem_ctx *ctx, int precision, cudaStream_t s);

@@ -294,26 +294,113 @@ __global__ void init_kernel(obem_step_stats *stats, StepCtl *ctl, const obem_sta
     }
 }
 
-// nearest-cation search without a field pass (used when the field is given)
-__global__ void partner_kernel(const obem_state st, GasDev g, uint32_t step, u64 *prop)
+// ---------------------------------------------------------------- partner search
+// Nearest eligible cation within R_c for every electron, by spatial hashing:
+// cells of edge h = R_c (1 + 1e-5) are hashed into PH_BUCKETS buckets, the
+// eligible cations (not created in the previous step) are counting-sorted by
+// bucket, and each electron scans the buckets of its 27 neighbouring cells,
+// keeping the smallest (binary32 d^2, index) key with d^2 <= R_c^2.  Every
+// cation within R_c lies in one of those cells and hash collisions only add
+// candidates that the distance test rejects, so the result is the exact
+// minimum over all cations (the same key as a brute-force scan, whatever the
+// order in a bucket).  Cell coordinates are computed in FP64 (exact floor to
+// ~1e-8 of a cell at metre-scale positions).
+#define PH_BUCKETS (1 << 20)
+
+__device__ __forceinline__ uint32_t ph_hash(long long cx, long long cy, long long cz)
+{
+    const uint32_t h = ((uint32_t)cx * 73856093u) ^ ((uint32_t)cy * 19349663u) ^ ((uint32_t)cz * 83492791u);
+    return h & (PH_BUCKETS - 1);
+}
+
+__device__ __forceinline__ long long ph_coord(float x, double inv_h)
+{
+    const double c = floor((double)x * inv_h);
+    return (long long)fmin(fmax(c, -4.0e18), 4.0e18);   // in range for the conversion
+}
+__device__ __forceinline__ void ph_cell(float4 p, double inv_h, long long &cx, long long &cy, long long &cz)
+{
+    cx = ph_coord(p.x, inv_h);
+    cy = ph_coord(p.y, inv_h);
+    cz = ph_coord(p.z, inv_h);
+}
+
+__global__ void ph_count_kernel(const obem_state st, uint32_t step, double inv_h, int32_t *bucket_of,
+                                int32_t *count)
 {
     const int n = cur_n(st);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t b = st.birth[i];
+    if (st.species[i] != OBEM_CATION || (b != 0u && b == step)) { bucket_of[i] = -1; return; }
+    long long cx, cy, cz;
+    ph_cell(reinterpret_cast<const float4 *>(st.pos_q)[i], inv_h, cx, cy, cz);
+    const uint32_t h = ph_hash(cx, cy, cz);
+    bucket_of[i] = (int32_t)h;
+    atomicAdd(&count[h], 1);
+}
+
+// start = exclusive scan of count (PH_BUCKETS + 1 entries), cursor = start;
+// one block of 1024 threads, each scanning PH_BUCKETS / 1024 contiguous entries
+__global__ void __launch_bounds__(1024) ph_scan_kernel(const int32_t *count, int32_t *start, int32_t *cursor)
+{
+    __shared__ int32_t s_sum[1024];
+    constexpr int PER = PH_BUCKETS / 1024;
+    const int t = threadIdx.x, b0 = t * PER;
+    int32_t acc = 0;
+    for (int k = 0; k < PER; ++k) acc += count[b0 + k];
+    s_sum[t] = acc;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int32_t v = t >= o ? s_sum[t - o] : 0;
+        __syncthreads();
+        s_sum[t] += v;
+        __syncthreads();
+    }
+    int32_t run = s_sum[t] - acc;
+    for (int k = 0; k < PER; ++k) {
+        start[b0 + k] = run;
+        cursor[b0 + k] = run;
+        run += count[b0 + k];
+    }
+    if (t == 1023) start[PH_BUCKETS] = run;
+}
+
+__global__ void ph_scatter_kernel(const obem_state st, const int32_t *bucket_of, int32_t *cursor, int32_t *sorted)
+{
+    const int n = cur_n(st);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t h = bucket_of[i];
+    if (h < 0) return;
+    sorted[atomicAdd(&cursor[h], 1)] = i;
+}
+
+__global__ void ph_query_kernel(const obem_state st, GasDev g, double inv_h, const int32_t *start,
+                                const int32_t *sorted, u64 *prop)
+{
+    const int n = cur_n(st);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     u64 best = ~0ull;
     if (st.species[i] == OBEM_ELECTRON) {
-        float4 pe = reinterpret_cast<const float4 *>(st.pos_q)[i];
-        for (int c = 0; c < n; ++c) {
-            if (st.species[c] != OBEM_CATION) continue;
-            uint32_t b = st.birth[c];
-            if (b != 0u && b == step) continue;
-            float4 pc = reinterpret_cast<const float4 *>(st.pos_q)[c];
-            float dx = pe.x - pc.x, dy = pe.y - pc.y, dz = pe.z - pc.z;
-            float d2 = dx * dx + dy * dy + dz * dz;
-            if (!(d2 <= g.rc2)) continue;
-            u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)c;
-            if (key < best) best = key;
-        }
+        const float4 pe = reinterpret_cast<const float4 *>(st.pos_q)[i];
+        long long cx, cy, cz;
+        ph_cell(pe, inv_h, cx, cy, cz);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const uint32_t h = ph_hash(cx + dx, cy + dy, cz + dz);
+                    for (int k = start[h]; k < start[h + 1]; ++k) {
+                        const int c = sorted[k];
+                        const float4 pc = reinterpret_cast<const float4 *>(st.pos_q)[c];
+                        const float ex = pe.x - pc.x, ey = pe.y - pc.y, ez = pe.z - pc.z;
+                        const float d2 = ex * ex + ey * ey + ez * ez;
+                        if (!(d2 <= g.rc2)) continue;
+                        const u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)c;
+                        if (key < best) best = key;
+                    }
+                }
     }
     prop[i] = best;
 }
@@ -566,7 +653,7 @@ moments_kernel(const obem_state st, obem_step_stats *stats)
 }
 
 int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32_t step,
-                     obem_step_stats *stats, cudaStream_t s, int partners_done)
+                     obem_step_stats *stats, cudaStream_t s)
 {
     const obem_state st = *stp;
     const int cap = st.capacity;
@@ -575,9 +662,16 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
     init_kernel<<<1, 32, 0, s>>>(stats, c->s_ctl, st);
     OBEM_LAUNCH(c);
     if (g.recomb_on) {
-        if (!partners_done) {
-            partner_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, step, c->s_prop);
+        if (g.rc2 > 0.f) {
+            const double inv_h = 1.0 / (sqrt((double)g.rc2) * (1.0 + 1e-5));
+            OBEM_CUDA(c, cudaMemsetAsync(c->ph_count, 0, sizeof(int32_t) * PH_BUCKETS, s));
+            ph_count_kernel<<<nblk, ST_THREADS, 0, s>>>(st, step, inv_h, c->ph_bucket, c->ph_count);
+            ph_scan_kernel<<<1, 1024, 0, s>>>(c->ph_count, c->ph_start, c->ph_cursor);
+            ph_scatter_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->ph_bucket, c->ph_cursor, c->ph_sorted);
+            ph_query_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, inv_h, c->ph_start, c->ph_sorted, c->s_prop);
             OBEM_LAUNCH(c);
+        } else {
+            OBEM_CUDA(c, cudaMemsetAsync(c->s_prop, 0xFF, sizeof(u64) * (size_t)cap, s));
         }
         OBEM_CUDA(c, cudaMemsetAsync(c->s_ionkey, 0xFF, sizeof(u64) * (size_t)cap, s));
         resolve_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_prop, c->s_ionkey);
@@ -599,6 +693,6 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
     OBEM_LAUNCH(c);
     moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats);
     OBEM_LAUNCH(c);
-    if (c->prof_on) c->launches += 8 + (g.recomb_on ? (partners_done ? 1 : 2) : 0);
+    if (c->prof_on) c->launches += 8 + (g.recomb_on ? 5 : 0);
     return OBEM_OK;
 }
