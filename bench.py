@@ -42,18 +42,27 @@ def _file_sha256(path):
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def nbody_traffic_per_launch(n_targets):
+def sym_items(n_charges, tile=1024):
+    """Off-diagonal tile pairs of the symmetric all-pairs kernel (each
+    writes one source-side partial of 12 B per charge of its tile)."""
+    n = (n_charges + tile - 1) // tile
+    h = n // 2
+    return n * h - (n // 2 if n % 2 == 0 else 0)
+
+
+def nbody_traffic_per_launch(n_charges):
     """DRAM bytes per launch of the all-pairs kernel from the committed ncu
-    record (bytes per target x targets; the sources are re-read from L2, so
-    traffic grows with the targets only), or None when the kernel source has
-    changed since the counters were taken."""
+    record, or None when the kernel source has changed since the counters were
+    taken.  The record gives bytes per tile pair (the partial sums written,
+    which dominate) and bytes per charge (positions, sources re-read from L2);
+    a launch is scaled by both."""
     try:
         with open(TRAFFIC_RECORD) as f:
             rec = json.load(f)
         src = os.path.join(ROOT, rec["source"])
         if _file_sha256(src) != rec["source_sha256"]:
             return None
-        return rec["dram_bytes_per_target"] * n_targets
+        return rec["dram_bytes_per_item"] * sym_items(n_charges) + rec["dram_bytes_per_charge"] * n_charges
     except (OSError, KeyError, ValueError):
         return None
 
@@ -70,6 +79,7 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-fieldmap", action="store_true")
     return p.parse_args()
 
 
@@ -308,6 +318,9 @@ def run_ours(a, ws, rank, local):
     obem.obem_destroy(ctx)
     if rank != 0:
         return
+    fmap = None
+    if ws == 1 and not a.no_fieldmap:
+        fmap = fieldmap_timing(dev)
     cpu = None
     if ws == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(mesh, ch, gas, trk, a.cpu_seconds)
@@ -355,8 +368,41 @@ def run_ours(a, ws, rank, local):
         "gpu_launches": prof["launches"],
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "fieldmap": fmap,
     }
     print(json.dumps(line), flush=True)
+
+
+def fieldmap_timing(dev, n_grid=256):
+    """The static field map at the size of the paper's grid timings (Sec. 2.4:
+    a 256^3 grid, two parallel plates of 8,192 cells in total): build time of
+    obem_fieldmap_build.  Plates 1 cm x 1 cm, 1 cm apart, 64 x 32 x 2
+    triangles each, sigma from the GPU solve; grid over the gap, 0.2 mm clear
+    of the plates."""
+    import torch
+    from paper_2110_09214_gb300 import inputs, obem
+    mesh = inputs.parallel_plates(1e-2, 1e-2, 64, 0.0, 1000.0, ny=32)
+    ctx = obem.obem_create(capacity=16, dt=1e-12)
+    try:
+        obem.obem_mesh_load(ctx, mesh)
+        obem.obem_bem_assemble(ctx, obem.OBEM_LU_FP32)
+        sigma = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+        obem.obem_bem_solve(ctx, mesh.group_voltage, sigma)
+        lo, hi, dims = [0.0, 0.0, 2e-4], [1e-2, 1e-2, 1e-2 - 2e-4], [n_grid] * 3
+        obem.obem_fieldmap_build(ctx, lo, hi, [16, 16, 16], sigma)      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        obem.obem_fieldmap_build(ctx, lo, hi, dims, sigma)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    finally:
+        obem.obem_destroy(ctx)
+    nodes = n_grid ** 3
+    return {"grid": dims, "cells": int(mesh.n), "nodes": nodes, "seconds": t,
+            "cell_pair_evals_per_s": nodes * mesh.n / t,
+            "geometry": "two 1 cm plates 1 cm apart, 64x32x2 triangles each; grid over the gap",
+            "paper_context": "Sec. 2.4 table: 256^3 grid, 8,192 cells, 37 s on one V100-era GPU "
+                             "(their geometry and precision are not stated; context only)"}
 
 
 def run_e2e(ctx, st, steps, step0, dev):

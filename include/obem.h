@@ -70,7 +70,9 @@ enum {
 /* obem_step feature flags */
 enum {
     OBEM_STEP_SPACE_CHARGE = 1,   /* add the all-pairs Coulomb field, Eq. (nbody) */
-    OBEM_STEP_CELL_FIELD = 2      /* add the BEM cell field, Eq. (BEM3), with the current sigma */
+    OBEM_STEP_CELL_FIELD = 2,     /* add the BEM cell field, Eq. (BEM3), with the current sigma */
+    OBEM_STEP_FIELD_MAP = 4       /* take the cell field from the static map (obem_fieldmap_build),
+                                     interpolated trilinearly; replaces OBEM_STEP_CELL_FIELD */
 };
 
 typedef struct obem_config {
@@ -234,10 +236,28 @@ int obem_field_eval_backward(obem_ctx *ctx, const float *targets, int32_t nt, co
                              float *dL_dsigma, float *dL_dtargets, float *dL_dsources,
                              obem_stream stream);
 
+/* Static field map (Sec. 2.4: the field precomputed on a grid and
+ * interpolated during tracking, the "static" option of Sec. 3.2): evaluates
+ * the cell field and potential of Eqs. (BEM3), (BEM2) with densities sigma
+ * (device [n_panels]) at the nodes lo + (i, j, k) * (hi - lo) / (dims - 1),
+ * 0 <= i < dims[0] etc. (lo, hi: host [3] metres; dims: host [3], each >= 2),
+ * and keeps them in the context (16 bytes per node, padded to multiples of 8
+ * per axis; a previous map is replaced).  OBEM_ERR_STATE without a mesh,
+ * OBEM_ERR_ARG for bad bounds or dims.  Allocates and synchronises `stream`. */
+int obem_fieldmap_build(obem_ctx *ctx, const double *lo, const double *hi, const int32_t *dims,
+                        const float *sigma, obem_stream stream);
+
+/* Trilinear interpolation of the map at n points (device [n][4], x y z
+ * used) into E_out (device [n][4]: Ex, Ey, Ez, V); points outside the map's
+ * box take the value at the nearest point of the box.  OBEM_ERR_STATE without
+ * a map.  Allocates nothing, does not synchronise. */
+int obem_fieldmap_eval(obem_ctx *ctx, const float *points, int32_t n, float *E_out, obem_stream stream);
+
 /* One tracking step of all charges in st (Sec. 3.2 - 3.3):
  *   1. field at the step-start positions: E_in (device [capacity][4]) if not
- *      NULL, else evaluated here (cell field with the current sigma and/or
- *      softened all-pairs field as cfg.flags say, plus cfg.e_ext);
+ *      NULL, else evaluated here (cell field with the current sigma, or from
+ *      the static map with OBEM_STEP_FIELD_MAP, and/or the softened all-pairs
+ *      field, as cfg.flags say, plus cfg.e_ext);
  *   2. recombination: every electron proposes its nearest cation within R_c
  *      (binary32 squared distance, ties to the lower id; cations created in
  *      the previous step exempt), every cation accepts the proposer with the

@@ -11,7 +11,7 @@ swarm-parameter fits of Sec. 4.1 (Eqs. (vd), (diffusion), (townsend)).
 Parity status of each function (see the test-suite for the pins):
   tri_integrals, panel_field, nbody_field, assemble, bem_solve, influence_rhs,
   philox, step, swarm fits, tri_jacobian, field_jacobian, field_backward,
-  bem_solve_adjoint: pinned.
+  bem_solve_adjoint, grid_nodes, trilinear: pinned.
   Swarm parameters of the synthetic argon-like gas: parity unpinned (no closed
   form; only GPU-vs-oracle agreement within 3 sigma and the Maxwell-model
   limits are checked).
@@ -52,6 +52,7 @@ def lib():
         _lib.or_panel_field.argtypes = [I, P, P, I, P, P, P]
         _lib.or_nbody_field.argtypes = [I, P, I, P, I, C.c_double, P, P]
         _lib.or_tri_jacobian.argtypes = [P, P, P]
+        _lib.or_trilinear.argtypes = [I, I, I, P, P, I, P, I, P, P]
         _lib.or_field_jacobian.argtypes = [I, P, P, I, P, I, P, I, P]
         _lib.or_field_backward.argtypes = [I, P, P, I, P, I, P, I, P, P, P, P]
         _lib.or_assemble.argtypes = [I, P, P, P, P, P]
@@ -158,6 +159,29 @@ def field_backward(tri, sigma, pts, src, self_exclude, g):
     lib().or_field_backward(len(sigma), _p(tri), _p(sigma), len(pts), _p(pts), len(src), _p(src),
                             int(self_exclude), _p(g), _p(ds), _p(dp), _p(dq))
     return ds, dp, dq
+
+
+def grid_nodes(lo, hi, dims):
+    """Nodes lo + (i, j, k) (hi - lo) / (dims - 1) of a regular grid, x fastest
+    ([nz * ny * nx, 3]) -- the static field map's nodes (Sec. 2.4)."""
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    step = (hi - lo) / (np.asarray(dims) - 1)
+    k, j, i = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    return np.column_stack([lo[0] + i.ravel() * step[0], lo[1] + j.ravel() * step[1], lo[2] + k.ravel() * step[2]])
+
+
+def trilinear(values, lo, hi, dims, pts):
+    """Trilinear interpolation of node values ([n_nodes, nc], x fastest) at
+    pts; points outside the box are moved to the nearest point of the box."""
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    step = (hi - lo) / (np.asarray(dims) - 1)
+    values = _c(values, np.float64)
+    nc = values.shape[1] if values.ndim == 2 else 1
+    pts = _c(pts, np.float64).reshape(-1, 3)
+    out = np.zeros((len(pts), nc))
+    lib().or_trilinear(int(dims[0]), int(dims[1]), int(dims[2]), _p(_c(lo, np.float64)), _p(_c(step, np.float64)),
+                       nc, _p(values), len(pts), _p(pts), _p(out))
+    return out
 
 
 def assemble(mesh):

@@ -360,6 +360,36 @@ void or_field_backward(int np, const double *tri, const double *sigma, int nt, c
     }
 }
 
+/* Trilinear interpolation on a regular grid (the static field map of
+ * Sec. 2.4): values[((k * ny) + j) * nx + i][nc] at lo + (i, j, k) * step;
+ * a point outside the grid's box is moved to the nearest point of the box.
+ * Within a grid cell with fractional coordinates (tx, ty, tz):
+ *   f = sum over the 8 corners of prod_a (t_a or 1 - t_a) * value(corner). */
+void or_trilinear(int nx, int ny, int nz, const double *lo, const double *step, int nc, const double *values,
+                  int n, const double *pts, double *out)
+{
+    const int dims[3] = {nx, ny, nz};
+    for (int p = 0; p < n; ++p) {
+        int i0[3];
+        double t[3];
+        for (int a = 0; a < 3; ++a) {
+            double f = (pts[3 * (size_t)p + a] - lo[a]) / step[a];
+            if (f < 0.0) f = 0.0;
+            if (f > dims[a] - 1) f = dims[a] - 1;
+            i0[a] = (int)floor(f);
+            if (i0[a] > dims[a] - 2) i0[a] = dims[a] - 2;
+            t[a] = f - i0[a];
+        }
+        for (int c = 0; c < nc; ++c) out[(size_t)p * nc + c] = 0.0;
+        for (int corner = 0; corner < 8; ++corner) {
+            const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+            const double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
+            const size_t node = ((size_t)(i0[2] + dz) * ny + (i0[1] + dy)) * nx + (i0[0] + dx);
+            for (int c = 0; c < nc; ++c) out[(size_t)p * nc + c] += w * values[node * nc + c];
+        }
+    }
+}
+
 /*
  * Dense BEM matrix, Eqs. (BEMpot), (BEMfld), (matrixBEM), row-major n x n.
  *   electrode (ed) rows:   A_ij = Q_ij = k_C phi_j(r_i)

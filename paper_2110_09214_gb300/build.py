@@ -23,6 +23,7 @@ UNITS = {
     "bem.cu": [],
     "backward.cu": [],
     "peak.cu": [],
+    "fieldmap.cu": [],
 }
 
 

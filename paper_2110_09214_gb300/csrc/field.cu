@@ -832,7 +832,7 @@ nbody_kernel(FieldLaunch L)
 // even, every unordered tile pair occurs exactly once.  A work unit is SY_CH
 // consecutive items of one row; persistent blocks take units from a counter.
 // Inside an off-diagonal item each warp holds 256 targets (8 per lane, four
-// f32x2 packs) and walks the 1024 sources of tile J in rounds of 32: the 32
+// f32x2 packs) and walks the sources of tile J in rounds of 32: the 32
 // sources sit one per lane and rotate around the warp by shuffles, carrying
 // their own reaction sums, so no reduction is needed; the four warps take
 // different 32-source groups in every round and add their sums into shared
@@ -840,10 +840,17 @@ nbody_kernel(FieldLaunch L)
 // every item its source-side sums (Jpart) to slots of its own, and
 // nbsym_fold_kernel adds them per charge in a fixed order: the result does
 // not depend on which block ran which unit.
+#ifndef SY_THREADS
 #define SY_THREADS 128
+#endif
+#ifndef SY_MINB
+#define SY_MINB 3              // resident blocks per SM the register budget is cut for
+#endif
 #define SY_NI 8
 #define SY_NP (SY_NI / 2)
 #define SY_T (SY_THREADS * SY_NI)
+#define SY_WARPS (SY_THREADS / 32)
+#define SY_NG (SY_T / 32)      // 32-source groups of a tile (rounds of an item)
 #define SY_CH 16
 #define SY_FOLD 8              // rounds (of 32 sources) between compensated folds
 #define SY_DTILE 256           // staged sources of the d = 0 item
@@ -885,7 +892,7 @@ __host__ __device__ constexpr size_t sym_smem(int nc)
 }
 
 template <bool WANT_V>
-__global__ void __launch_bounds__(SY_THREADS, 3)
+__global__ void __launch_bounds__(SY_THREADS, SY_MINB)
 nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
 {
     constexpr int NC = WANT_V ? 4 : 3;
@@ -1003,8 +1010,8 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
             u64 AX[SY_NP], AY[SY_NP], AZ[SY_NP], AV[SY_NP];
 #pragma unroll
             for (int p = 0; p < SY_NP; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
-            for (int r = 0; r < 32; ++r) {
-                const int grp = (r + 8 * warp) & 31;
+            for (int r = 0; r < SY_NG; ++r) {
+                const int grp = (r + (SY_NG / SY_WARPS) * warp) % SY_NG;   // distinct per warp in a round
                 const int j0 = jb + grp * 32;
                 float4 sj = j0 + lane < nt ? L.sources[j0 + lane] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
                 float jx = sj.x, jy = sj.y, jz = sj.z, jq = kC * sj.w;
@@ -1177,6 +1184,7 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
     dim3 grid((capacity_targets + FT_BLOCK_TARGETS - 1) / FT_BLOCK_TARGETS);
     const bool cells = L.sigma != NULL && L.panels.np > 0;
     const bool charges = L.sources != NULL;
+    const bool add = cells || L.add_init;      // E_out holds a field the all-pairs sum adds to
     if (cells) {
         if (L.perm) {
             // spatial order of the targets for the cell kernel
@@ -1233,15 +1241,15 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
                 nbsym_kernel<false><<<sg, SY_THREADS, sym_smem(3), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
             OBEM_LAUNCH(ctx);
             const int fb = (capacity_targets + 255) / 256;
-            if (L.want_v) nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, cells ? 1 : 0);
-            else nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, cells ? 1 : 0);
+            if (L.want_v) nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0);
+            else nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0);
             OBEM_LAUNCH(ctx);
             if (L.events) ctx->launches += 2;
         } else if (L.want_v) {
-            if (cells) nbody_kernel<true, true><<<grid, FT_THREADS, 0, s>>>(L);
+            if (add) nbody_kernel<true, true><<<grid, FT_THREADS, 0, s>>>(L);
             else nbody_kernel<true, false><<<grid, FT_THREADS, 0, s>>>(L);
         } else {
-            if (cells) nbody_kernel<false, true><<<grid, FT_THREADS, 0, s>>>(L);
+            if (add) nbody_kernel<false, true><<<grid, FT_THREADS, 0, s>>>(L);
             else nbody_kernel<false, false><<<grid, FT_THREADS, 0, s>>>(L);
         }
         if (!sym) {
@@ -1249,7 +1257,7 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             if (L.events) ctx->launches++;
         }
     }
-    if (!cells && !charges) {
+    if (!cells && !charges && !L.add_init) {
         const_field_kernel<<<(capacity_targets + 255) / 256, 256, 0, s>>>(L);
         OBEM_LAUNCH(ctx);
         if (L.events) ctx->launches++;

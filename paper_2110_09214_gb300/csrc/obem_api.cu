@@ -114,6 +114,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
                 cudaMalloc((void **)&c->sym_counter, sizeof(int)) != cudaSuccess) {
                 free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
     free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted);
+    free_dev(c->fm.nodes);
                 c->sym_jpart = c->sym_ipart = NULL;
                 c->sym_counter = NULL;
                 cudaGetLastError();
@@ -138,6 +139,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
     free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
     free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted);
+    free_dev(c->fm.nodes);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->prof_ev) {
         for (int i = 0; i < OBEM_PROF_EV * OBEM_PROF_MAX; ++i) cudaEventDestroy(c->prof_ev[i]);
@@ -498,6 +500,53 @@ extern "C" int obem_field_eval_backward(obem_ctx *c, const float *targets, int32
     return obem_launch_backward(c, A, s);
 }
 
+extern "C" int obem_fieldmap_build(obem_ctx *c, const double *lo, const double *hi, const int32_t *dims,
+                                   const float *sigma, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (c->np < 1) return obem_fail(c, OBEM_ERR_STATE, "field map: no mesh loaded");
+    if (!lo || !hi || !dims || !sigma) return obem_fail(c, OBEM_ERR_ARG, "field map: null argument");
+    size_t total = 1;
+    int pad[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!(hi[a] > lo[a]) || dims[a] < 2 || dims[a] > (1 << 16))
+            return obem_fail(c, OBEM_ERR_ARG, "field map: axis %d needs lo < hi and 2 <= dims <= 65536", a);
+        pad[a] = (dims[a] + 7) / 8 * 8;
+        total *= (size_t)pad[a];
+    }
+    if (total > ((size_t)1 << 31)) return obem_fail(c, OBEM_ERR_ARG, "field map: more than 2^31 nodes");
+    free_dev(c->fm.nodes);
+    memset(&c->fm, 0, sizeof c->fm);
+    float4 *nodes = NULL;
+    OBEM_CUDA(c, cudaMalloc((void **)&nodes, sizeof(float4) * total));
+    c->fm.nodes = nodes;
+    c->fm.nx = dims[0]; c->fm.ny = dims[1]; c->fm.nz = dims[2];
+    c->fm.px = pad[0]; c->fm.py = pad[1]; c->fm.pz = pad[2];
+    for (int a = 0; a < 3; ++a) {
+        c->fm.lo[a] = lo[a];
+        c->fm.step[a] = (hi[a] - lo[a]) / (double)(dims[a] - 1);
+    }
+    int rc = obem_fieldmap_build_nodes(c, sigma, (cudaStream_t)stream);
+    if (rc != OBEM_OK) {
+        free_dev(c->fm.nodes);
+        memset(&c->fm, 0, sizeof c->fm);
+    }
+    return rc;
+}
+
+extern "C" int obem_fieldmap_eval(obem_ctx *c, const float *points, int32_t n, float *E_out, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (!c->fm.nodes) return obem_fail(c, OBEM_ERR_STATE, "field map: call obem_fieldmap_build first");
+    if (n < 0) return obem_fail(c, OBEM_ERR_ARG, "field map: negative count");
+    if (n == 0) return OBEM_OK;
+    if (!points || !E_out) return obem_fail(c, OBEM_ERR_ARG, "field map: null points or E_out");
+    if (((uintptr_t)points | (uintptr_t)E_out) & 15)
+        return obem_fail(c, OBEM_ERR_ARG, "field map: arrays must be 16-byte aligned");
+    return obem_fieldmap_interp(c, (const float4 *)points, NULL, n, (float4 *)E_out, make_float3(0.f, 0.f, 0.f),
+                                (cudaStream_t)stream);
+}
+
 extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, uint32_t step,
                          obem_step_stats *stats, obem_stream stream)
 {
@@ -520,9 +569,19 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         cudaEventRecord(ev[4], s);
         cudaEventRecord(ev[5], s);
     }
-    int want_cells = (c->cfg.flags & OBEM_STEP_CELL_FIELD) && c->sigma_valid;
+    const int want_map = (c->cfg.flags & OBEM_STEP_FIELD_MAP) != 0;
+    if (want_map && !E && !c->fm.nodes)
+        return obem_fail(c, OBEM_ERR_STATE, "step: OBEM_STEP_FIELD_MAP without obem_fieldmap_build");
+    int want_cells = !want_map && (c->cfg.flags & OBEM_STEP_CELL_FIELD) && c->sigma_valid;
     int want_nbody = (c->cfg.flags & OBEM_STEP_SPACE_CHARGE) != 0;
     if (!E) {
+        const float3 e_ext = make_float3((float)c->cfg.e_ext[0], (float)c->cfg.e_ext[1], (float)c->cfg.e_ext[2]);
+        if (want_map) {
+            // cell field (+ e_ext) from the map; the all-pairs sum adds to it
+            int rc = obem_fieldmap_interp(c, (const float4 *)st->pos_q, st->n, st->capacity, c->s_E, e_ext, s);
+            if (rc != OBEM_OK) return rc;
+            if (c->prof_on) c->launches++;
+        }
         FieldLaunch L;
         memset(&L, 0, sizeof L);
         L.targets = (const float4 *)st->pos_q;
@@ -539,7 +598,8 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         L.blocks = want_cells ? c->s_blocks : NULL;
         L.nblocks = want_cells ? c->s_nblocks : NULL;
         L.E_out = c->s_E;
-        L.e_ext = make_float3((float)c->cfg.e_ext[0], (float)c->cfg.e_ext[1], (float)c->cfg.e_ext[2]);
+        L.e_ext = e_ext;
+        L.add_init = want_map;
         L.want_v = 0;
         if (ev) L.counters = c->d_counters;
         L.events = ev;

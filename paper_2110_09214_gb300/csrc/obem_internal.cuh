@@ -58,6 +58,15 @@ struct PanelsDev {
     int np;
 };
 
+// Static field map: cell field on a regular grid (valid nx x ny x nz nodes,
+// stored padded to px x py x pz in bricks of 8^3), node (i, j, k) at
+// lo + (i, j, k) * step.
+struct FieldMapDev {
+    float4 *nodes;
+    int nx, ny, nz, px, py, pz;
+    double lo[3], step[3];
+};
+
 // Device-resident control block of one obem_step call.
 struct StepCtl {
     int32_t abort;        // non-zero: do not commit
@@ -121,6 +130,8 @@ struct obem_ctx {
     // partner search: hash-bucket counts / starts / cursors, bucket of each
     // charge, cations sorted by bucket
     int32_t *ph_count, *ph_start, *ph_cursor, *ph_bucket, *ph_sorted;
+    // static field map (nodes == NULL until obem_fieldmap_build)
+    FieldMapDev fm;
     int *sym_counter;
     int sym_grid, sym_cap;
     // stage timing (obem_profile)
@@ -177,6 +188,8 @@ struct FieldLaunch {
     const int32_t *perm;
     const int2 *blocks;
     const int32_t *nblocks;
+    // E_out already holds a field to add to (e.g. the interpolated map)
+    int add_init;
 };
 #define OBEM_BINS_PER_AXIS 64
 #define OBEM_NBINS (OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS)
@@ -186,6 +199,11 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
 size_t obem_sym_jpart_floats(int capacity);
 size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);
+
+// fieldmap.cu
+int obem_fieldmap_build_nodes(obem_ctx *ctx, const float *sigma, cudaStream_t s);
+int obem_fieldmap_interp(obem_ctx *ctx, const float4 *pts, const int32_t *n_dev, int n, float4 *out, float3 e_ext,
+                         cudaStream_t s);
 
 // backward.cu
 struct BwArgs {

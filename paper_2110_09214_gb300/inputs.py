@@ -79,12 +79,13 @@ def rect_plate(x0, x1, y0, y1, z, nx, ny, up=True):
     return np.asarray(tris, np.float64)
 
 
-def parallel_plates(side=1e-2, gap=1e-3, n=16, v_low=0.0, v_high=100.0) -> Mesh:
-    """Two side x side plates at z=0 (v_low) and z=gap (v_high), n*n*2
-    triangles each (the Sec. 2.4 timing set-up and the swarm chambers of
-    Sec. 4.1)."""
-    lo = rect_plate(0, side, 0, side, 0.0, n, n, up=True)
-    hi = rect_plate(0, side, 0, side, gap, n, n, up=False)
+def parallel_plates(side=1e-2, gap=1e-3, n=16, v_low=0.0, v_high=100.0, ny=None) -> Mesh:
+    """Two side x side plates at z=0 (v_low) and z=gap (v_high), n*ny*2
+    triangles each (ny = n by default; the Sec. 2.4 timing set-up and the
+    swarm chambers of Sec. 4.1)."""
+    ny = n if ny is None else ny
+    lo = rect_plate(0, side, 0, side, 0.0, n, ny, up=True)
+    hi = rect_plate(0, side, 0, side, gap, n, ny, up=False)
     tri, kind, group, em, ep = _concat([(lo, KIND_ELECTRODE, 0, 1.0, 1.0),
                                         (hi, KIND_ELECTRODE, 1, 1.0, 1.0)])
     return Mesh(tri, kind, group, em, ep, np.array([v_low, v_high], np.float64))

@@ -19,7 +19,7 @@ OBEM_OK = 0
 OBEM_ERR_ARG, OBEM_ERR_CUDA, OBEM_ERR_STATE, OBEM_ERR_SINGULAR = -1, -2, -3, -4
 OBEM_ERR_NOT_CONVERGED, OBEM_ERR_CAPACITY, OBEM_ERR_TIMEOUT, OBEM_ERR_TRIALS = -5, -6, -7, -8
 OBEM_LU_FP32, OBEM_LU_TF32, OBEM_LU_BF16, OBEM_LU_BF16X9 = 0, 1, 2, 3
-OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD = 1, 2
+OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD, OBEM_STEP_FIELD_MAP = 1, 2, 4
 
 
 class ObemError(RuntimeError):
@@ -97,10 +97,12 @@ def load():
     lib.obem_field_eval_noalloc.restype = C.c_int
     lib.obem_profile.argtypes = [P, I]
     lib.obem_alu_rates.argtypes = [P, P, P]
+    lib.obem_fieldmap_build.argtypes = [P, P, P, P, P, P]
+    lib.obem_fieldmap_eval.argtypes = [P, P, I, P, P]
     lib.obem_stage_times.argtypes = [P, P, P]
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
               "obem_bem_solve", "obem_bem_solve_adjoint", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
-              "obem_stage_times", "obem_alu_rates"):
+              "obem_stage_times", "obem_alu_rates", "obem_fieldmap_build", "obem_fieldmap_eval"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -323,6 +325,19 @@ def obem_alu_rates(ctx, stream=None):
     _check(ctx, load().obem_alu_rates(ctx, out.ctypes.data_as(C.c_void_p), _stream(stream)))
     return {"fp32_tflops": out[0], "fp32_lane_ops_per_sm_clk": out[1], "rsqrt_per_sm_clk": out[2],
             "mix12_lane_ops_per_sm_clk": out[3], "sm_mhz": out[4], "mix16_lane_ops_per_sm_clk": out[5]}
+
+
+def obem_fieldmap_build(ctx, lo, hi, dims, sigma, stream=None):
+    """Static field map of the cell field on a regular grid (see include/obem.h)."""
+    lo = np.ascontiguousarray(lo, np.float64)
+    hi = np.ascontiguousarray(hi, np.float64)
+    dims = np.ascontiguousarray(dims, np.int32)
+    _check(ctx, load().obem_fieldmap_build(ctx, lo.ctypes.data_as(C.c_void_p), hi.ctypes.data_as(C.c_void_p),
+                                           dims.ctypes.data_as(C.c_void_p), _ptr(sigma), _stream(stream)))
+
+
+def obem_fieldmap_eval(ctx, points, E_out, stream=None):
+    _check(ctx, load().obem_fieldmap_eval(ctx, _ptr(points), points.shape[0], _ptr(E_out), _stream(stream)))
 
 
 def obem_profile(ctx, enable=True):

@@ -240,3 +240,29 @@ def test_probe_loss_voltage_gradient_matches_central_differences():
         Vm[k] -= h
         fd = (_probe_loss(mesh, Vp, pts)[0] - _probe_loss(mesh, Vm, pts)[0]) / (2 * h)
         assert abs(dV[k] - fd) <= 1e-7 * np.abs(dV).max()
+
+
+# ----------------------------------------------------------------------------
+# static field map: trilinear interpolation
+# ----------------------------------------------------------------------------
+def test_trilinear_is_exact_for_trilinear_functions_and_nodes():
+    lo, hi, dims = np.array([-1.0, 0.5, 2.0]), np.array([3.0, 1.5, 2.7]), (7, 4, 5)
+    nodes = oracle.grid_nodes(lo, hi, dims)
+    assert nodes.shape == (7 * 4 * 5, 3)
+    assert np.allclose(nodes[0], lo) and np.allclose(nodes[-1], hi)
+    c = np.array([0.3, -1.2, 2.5, 0.7, -0.4, 1.1, 0.9, -2.0])
+
+    def f(p):
+        x, y, z = p[:, 0], p[:, 1], p[:, 2]
+        return c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * y + c[5] * y * z + c[6] * x * z + c[7] * x * y * z
+    vals = np.column_stack([f(nodes), 2.0 * f(nodes)])
+    rng = np.random.default_rng(8)
+    pts = rng.uniform(lo, hi, (500, 3))
+    got = oracle.trilinear(vals, lo, hi, dims, pts)
+    assert np.abs(got[:, 0] - f(pts)).max() <= 1e-12 * np.abs(f(pts)).max()
+    assert np.abs(got[:, 1] - 2 * f(pts)).max() <= 1e-12 * np.abs(f(pts)).max()
+    assert np.abs(oracle.trilinear(vals, lo, hi, dims, nodes) - vals).max() <= 1e-12 * np.abs(vals).max()
+    # outside the box: the value at the nearest point of the box
+    out = np.array([[-5.0, 1.0, 2.3], [10.0, 10.0, 10.0]])
+    near = np.clip(out, lo, hi)
+    assert np.allclose(oracle.trilinear(vals, lo, hi, dims, out), oracle.trilinear(vals, lo, hi, dims, near))
