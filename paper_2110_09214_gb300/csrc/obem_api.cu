@@ -100,6 +100,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->ph_cursor, sizeof(int32_t) * ((size_t)1 << 20));
     ALLOC(c->ph_bucket, sizeof(int32_t) * cap);
     ALLOC(c->ph_sorted, sizeof(int32_t) * cap);
+    ALLOC(c->ph_bsum, sizeof(int32_t) * (1024 + 1));
 #undef ALLOC
     // partial sums of the symmetric all-pairs kernel: they grow as capacity^2,
     // so they are kept only within a quarter of the free memory (and 64 GB)
@@ -113,7 +114,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
                 cudaMalloc((void **)&c->sym_ipart, ib) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_counter, sizeof(int)) != cudaSuccess) {
                 free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
-    free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted);
+    free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted); free_dev(c->ph_bsum);
     free_dev(c->fm.nodes);
                 c->sym_jpart = c->sym_ipart = NULL;
                 c->sym_counter = NULL;
@@ -138,7 +139,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
     free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
-    free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted);
+    free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted); free_dev(c->ph_bsum);
     free_dev(c->fm.nodes);
     if (c->cublas) cublasDestroy(c->cublas);
     if (c->prof_ev) {

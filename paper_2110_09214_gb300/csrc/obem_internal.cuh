@@ -129,7 +129,7 @@ struct obem_ctx {
     float *sym_jpart, *sym_ipart;
     // partner search: hash-bucket counts / starts / cursors, bucket of each
     // charge, cations sorted by bucket
-    int32_t *ph_count, *ph_start, *ph_cursor, *ph_bucket, *ph_sorted;
+    int32_t *ph_count, *ph_start, *ph_cursor, *ph_bucket, *ph_sorted, *ph_bsum;
     // static field map (nodes == NULL until obem_fieldmap_build)
     FieldMapDev fm;
     int *sym_counter;

@@ -340,30 +340,61 @@ __global__ void ph_count_kernel(const obem_state st, uint32_t step, double inv_h
     atomicAdd(&count[h], 1);
 }
 
-// start = exclusive scan of count (PH_BUCKETS + 1 entries), cursor = start;
-// one block of 1024 threads, each scanning PH_BUCKETS / 1024 contiguous entries
-__global__ void __launch_bounds__(1024) ph_scan_kernel(const int32_t *count, int32_t *start, int32_t *cursor)
+// start = exclusive scan of count (PH_BUCKETS + 1 entries), cursor = start, in
+// three passes: sums of 1024-bucket blocks, scan of the block sums, scan
+// within each block plus its offset.
+#define PH_BLK 1024
+#define PH_NBLK (PH_BUCKETS / PH_BLK)
+
+// inclusive scan of one value per thread over a 1024-thread block
+__device__ __forceinline__ int32_t ph_block_scan(int32_t v, int32_t *s_warp)
 {
-    __shared__ int32_t s_sum[1024];
-    constexpr int PER = PH_BUCKETS / 1024;
-    const int t = threadIdx.x, b0 = t * PER;
-    int32_t acc = 0;
-    for (int k = 0; k < PER; ++k) acc += count[b0 + k];
-    s_sum[t] = acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) s_warp[warp] = v;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int32_t v = t >= o ? s_sum[t - o] : 0;
-        __syncthreads();
-        s_sum[t] += v;
-        __syncthreads();
+    if (warp == 0) {
+        int32_t w = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        s_warp[lane] = w;
     }
-    int32_t run = s_sum[t] - acc;
-    for (int k = 0; k < PER; ++k) {
-        start[b0 + k] = run;
-        cursor[b0 + k] = run;
-        run += count[b0 + k];
-    }
-    if (t == 1023) start[PH_BUCKETS] = run;
+    __syncthreads();
+    return v + (warp > 0 ? s_warp[warp - 1] : 0);
+}
+
+__global__ void __launch_bounds__(PH_BLK) ph_blocksum_kernel(const int32_t *count, int32_t *bsum)
+{
+    __shared__ int32_t s_warp[32];
+    const int32_t v = ph_block_scan(count[blockIdx.x * PH_BLK + threadIdx.x], s_warp);
+    if (threadIdx.x == PH_BLK - 1) bsum[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(PH_BLK) ph_scan_sums_kernel(int32_t *bsum)
+{
+    __shared__ int32_t s_warp[32];
+    const int32_t v = bsum[threadIdx.x];
+    const int32_t inc = ph_block_scan(v, s_warp);
+    __syncthreads();
+    bsum[threadIdx.x] = inc - v;                 // exclusive offsets
+    if (threadIdx.x == PH_BLK - 1) bsum[PH_NBLK] = inc;
+}
+
+__global__ void __launch_bounds__(PH_BLK) ph_scan_apply_kernel(const int32_t *count, const int32_t *bsum,
+                                                                  int32_t *start, int32_t *cursor)
+{
+    __shared__ int32_t s_warp[32];
+    const int i = blockIdx.x * PH_BLK + threadIdx.x;
+    const int32_t v = count[i];
+    const int32_t ex = ph_block_scan(v, s_warp) - v + bsum[blockIdx.x];
+    start[i] = ex;
+    cursor[i] = ex;
+    if (i == PH_BUCKETS - 1) start[PH_BUCKETS] = bsum[PH_NBLK];
 }
 
 __global__ void ph_scatter_kernel(const obem_state st, const int32_t *bucket_of, int32_t *cursor, int32_t *sorted)
@@ -666,7 +697,9 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
             const double inv_h = 1.0 / (sqrt((double)g.rc2) * (1.0 + 1e-5));
             OBEM_CUDA(c, cudaMemsetAsync(c->ph_count, 0, sizeof(int32_t) * PH_BUCKETS, s));
             ph_count_kernel<<<nblk, ST_THREADS, 0, s>>>(st, step, inv_h, c->ph_bucket, c->ph_count);
-            ph_scan_kernel<<<1, 1024, 0, s>>>(c->ph_count, c->ph_start, c->ph_cursor);
+            ph_blocksum_kernel<<<PH_NBLK, PH_BLK, 0, s>>>(c->ph_count, c->ph_bsum);
+            ph_scan_sums_kernel<<<1, PH_BLK, 0, s>>>(c->ph_bsum);
+            ph_scan_apply_kernel<<<PH_NBLK, PH_BLK, 0, s>>>(c->ph_count, c->ph_bsum, c->ph_start, c->ph_cursor);
             ph_scatter_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->ph_bucket, c->ph_cursor, c->ph_sorted);
             ph_query_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, inv_h, c->ph_start, c->ph_sorted, c->s_prop);
             OBEM_LAUNCH(c);
@@ -693,6 +726,6 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
     OBEM_LAUNCH(c);
     moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats);
     OBEM_LAUNCH(c);
-    if (c->prof_on) c->launches += 8 + (g.recomb_on ? 5 : 0);
+    if (c->prof_on) c->launches += 8 + (g.recomb_on ? 7 : 0);
     return OBEM_OK;
 }
