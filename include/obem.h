@@ -71,8 +71,11 @@ enum {
 enum {
     OBEM_STEP_SPACE_CHARGE = 1,   /* add the all-pairs Coulomb field, Eq. (nbody) */
     OBEM_STEP_CELL_FIELD = 2,     /* add the BEM cell field, Eq. (BEM3), with the current sigma */
-    OBEM_STEP_FIELD_MAP = 4       /* take the cell field from the static map (obem_fieldmap_build),
+    OBEM_STEP_FIELD_MAP = 4,      /* take the cell field from the static map (obem_fieldmap_build),
                                      interpolated trilinearly; replaces OBEM_STEP_CELL_FIELD */
+    OBEM_STEP_PROB_COLLISION = 8  /* the paper's collision sampling (Sec. 3.3.1): one interaction test
+                                     per step, probability 1 - exp(-nu_tot(eps) dt), after the step's
+                                     flight; default: exact null-collision trials */
 };
 
 typedef struct obem_config {

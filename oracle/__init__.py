@@ -272,8 +272,8 @@ def iso_dir(ua, ub):
 def _prm(gas, trk):
     seed = int(trk.seed)
     return np.array([trk.dt, gas.T, gas.N, gas.M_amu, gas.nu_ion, trk.z_lo, trk.z_hi,
-                     trk.beta, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, trk.trial_cap],
-                    np.float64)
+                     trk.beta, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, trk.trial_cap,
+                     getattr(trk, "coll_mode", 0)], np.float64)
 
 
 def _gas_arrays(gas):

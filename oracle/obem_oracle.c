@@ -604,6 +604,7 @@ typedef struct {
     float dt_f, nu_max_e, nu_ion_f, half_nu_ion, E_therm, v_th_ion, qm[3], K_e, K_ion,
           two_m_over_M, KCE, N_f, z_lo_f, z_hi_f, rc2, ion_thr;
     int recomb_on;
+    int coll_mode;     /* 0: null-collision trials; 1: the paper's per-step probability */
 } or_gas;
 
 /* Derived constants: each is computed in FP64 from the primary parameters and
@@ -685,12 +686,158 @@ typedef struct {
 
 typedef struct { float p[3], v[3]; float pi[3], vi[3]; uint32_t parent; } spawn_rec;
 
+/* Collision frequency of process j for an electron of energy eps and speed
+ * (linear interpolation in energy on the float grid, zero below threshold). */
+static float nu_proc(const or_gas *g, int j, float eps, float speed, int lo, float w)
+{
+    if (g->pmode[j] == 1) return g->nuc[j];
+    float Ns = g->N_f * speed;
+    float s0 = g->xs[(size_t)j * g->n_e + lo];
+    float s1 = g->xs[(size_t)j * g->n_e + lo + 1];
+    float ds = s1 - s0;
+    float sg = s0 + w * ds;
+    if (eps < g->thr[j]) sg = 0.0f;
+    return Ns * sg;
+}
+
+/* grid segment and interpolation weight of energy eps */
+static void egrid_locate(const or_gas *g, float eps, int *lo_out, float *w_out)
+{
+    int lo = 0, hi = g->n_e - 1;
+    float w;
+    if (eps < g->egrid[0]) { lo = 0; w = 0.0f; }
+    else if (eps >= g->egrid[g->n_e - 1]) { lo = g->n_e - 2; w = 1.0f; }
+    else {
+        while (hi - lo > 1) { int mid = (lo + hi) / 2; if (g->egrid[mid] <= eps) lo = mid; else hi = mid; }
+        w = (eps - g->egrid[lo]) / (g->egrid[lo + 1] - g->egrid[lo]);
+    }
+    *lo_out = lo;
+    *w_out = w;
+}
+
+/* One collision trial of the charge at its current state (Sec. 3.3.1-3.3.3):
+ * with x uniform in [0, scale), process j is taken when x < nu_1 + ... + nu_j
+ * (none: a null collision).  Returns 0 when nothing happened (null, or an
+ * ionisation without the energy for it), 1 after a collision, 2 when the
+ * flight ends (attachment, or the spawn records are full: fr->status). */
+static int collide(const or_gas *g, uint32_t id, uint32_t step, uint32_t k, const uint32_t *r, float x,
+                   float *p, float *v, uint8_t *sp, spawn_rec *recs, int rec_cap, flight_result *fr)
+{
+    uint32_t key[2] = {g->seed_lo, g->seed_hi};
+    float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    float speed = sqrtf(v2);
+    float d[3];
+    if (*sp == SP_ELECTRON) {
+        float eps = g->K_e * v2;
+        int lo;
+        float w;
+        egrid_locate(g, eps, &lo, &w);
+        float cum = 0.0f;
+        int proc = -1;
+        for (int j = 0; j < g->n_proc; ++j) {
+            cum = cum + nu_proc(g, j, eps, speed, lo, w);
+            if (x < cum) { proc = j; break; }
+        }
+        if (proc < 0) return 0;                     /* null collision */
+        int kind = g->pkind[proc];
+        if (kind == K_ELASTIC) {
+            iso_dir(r[2], r[3], d);
+            float cosx = 0.0f;
+            if (speed > 0.0f) cosx = (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) / speed;
+            float om = 1.0f - cosx;
+            float loss = g->two_m_over_M * om;
+            float f = 1.0f - loss;
+            float sn = speed * sqrtf(f);
+            v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
+            fr->collisions += 1;
+        } else if (kind == K_EXCITATION) {
+            float e2 = eps - g->thr[proc];
+            if (e2 < 0.0f) e2 = 0.0f;
+            float sn = sqrtf(e2 / g->K_e);
+            iso_dir(r[2], r[3], d);
+            v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
+            fr->collisions += 1;
+        } else if (kind == K_IONISATION) {
+            float er = eps - g->thr[proc];
+            er = er - g->E_therm;
+            if (!(er > 0.0f)) return 0;             /* not enough energy: null */
+            if (fr->n_out_sp >= rec_cap) { fr->status = ST_CAPACITY; return 2; }
+            float half = 0.5f * er;
+            float sn = sqrtf(half / g->K_e);
+            iso_dir(r[2], r[3], d);
+            float rr = g->KCE / (2.0f * er);
+            float o[3] = {rr * d[0], rr * d[1], rr * d[2]};
+            spawn_rec *sr = &recs[fr->n_out_sp];
+            float pn[3], pp[3];
+            for (int c = 0; c < 3; ++c) { pn[c] = p[c] + o[c]; pp[c] = p[c] - o[c]; }
+            if (pn[0] == p[0] && pn[1] == p[1] && pn[2] == p[2]) {
+                int ax = 0;
+                float ad0 = fabsf(d[0]), ad1 = fabsf(d[1]), ad2 = fabsf(d[2]);
+                if (ad1 > ad0) ax = 1;
+                if (ad2 > (ax == 1 ? ad1 : ad0)) ax = 2;
+                pn[ax] = ulp_step(p[ax], d[ax]);
+                pp[ax] = ulp_step(p[ax], -d[ax]);
+            }
+            uint32_t ctr[4] = {id, step, k, 1u};
+            uint32_t r2[4];
+            or_philox4x32_10(ctr, key, r2);
+            float di[3];
+            iso_dir(r2[0], r2[1], di);
+            for (int c = 0; c < 3; ++c) {
+                sr->pi[c] = p[c];
+                sr->vi[c] = g->v_th_ion * di[c];
+                sr->p[c] = pn[c];
+                sr->v[c] = sn * d[c];
+                p[c] = pp[c];
+                v[c] = -sn * d[c];
+            }
+            fr->n_out_sp += 1;
+            fr->collisions += 1;
+        } else { /* K_ATTACHMENT: the electron becomes an anion in place */
+            iso_dir(r[2], r[3], d);
+            for (int c = 0; c < 3; ++c) v[c] = g->v_th_ion * d[c];
+            *sp = SP_ANION;
+            fr->attached = 1;
+            fr->collisions += 1;
+            return 2;
+        }
+    } else {
+        /* ions: constant frequency, half isotropic elastic (speed kept),
+         * half charge exchange (fresh thermal velocity) */
+        iso_dir(r[2], r[3], d);
+        float sn = (x < g->half_nu_ion) ? speed : g->v_th_ion;
+        v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
+        fr->collisions += 1;
+    }
+    return 1;
+}
+
+/* Ballistic flight under the constant acceleration a for time fl (Sec. 3.2.5
+ * Euler stepper: the field of the step start), then the absorbing planes. */
+static int flight(const or_gas *g, float *p, float *v, const float *a, const float *ha, float fl)
+{
+    for (int c = 0; c < 3; ++c) {
+        float w = ha[c] * fl;
+        float x = v[c] + w;
+        float y = x * fl;
+        p[c] = p[c] + y;
+        float dv = a[c] * fl;
+        v[c] = v[c] + dv;
+    }
+    return p[2] <= g->z_lo_f || p[2] >= g->z_hi_f;
+}
+
 /*
- * Flight and null-collision trials of one charge over one step dt under the
- * step-start field E (Sec. 3.2.5 Euler stepper: one field evaluation per step;
- * Sec. 3.3.1 collision sampling, replaced by the exact null-collision method
- * of the cited Skullerud 1968).  The charge's state (p, v, species) is updated
- * in place; ionisations append spawn records (Sec. 3.3.3, Eq. (distIoni)).
+ * Flight and collisions of one charge over one step dt under the step-start
+ * field E (Sec. 3.2.5 Euler stepper: one field evaluation per step).  The
+ * charge's state (p, v, species) is updated in place; ionisations append
+ * spawn records (Sec. 3.3.3, Eq. (distIoni)).  Collision sampling:
+ *   coll_mode 0 -- exact null-collision trials (Skullerud 1968, cited in
+ *     Sec. 3.3.1): exponential waiting times -ln(U)/nu_max, process j taken
+ *     with probability nu_j(eps)/nu_max at each trial;
+ *   coll_mode 1 -- the paper's own scheme (Sec. 3.3.1): flight over the whole
+ *     step, then one interaction with probability 1 - exp(-nu_tot(eps) dt),
+ *     i.e. when -ln(U) < nu_tot dt, of type j with probability nu_j/nu_tot.
  */
 static void fly_one(const or_gas *g, uint32_t id, uint32_t step, float *p, float *v,
                     uint8_t *sp, const float *E, spawn_rec *recs, int rec_cap,
@@ -701,6 +848,30 @@ static void fly_one(const or_gas *g, uint32_t id, uint32_t step, float *p, float
     float qm = g->qm[s];
     float a[3] = {qm * E[0], qm * E[1], qm * E[2]};
     float ha[3] = {0.5f * a[0], 0.5f * a[1], 0.5f * a[2]};
+    if (g->coll_mode == 1) {
+        if (flight(g, p, v, a, ha, g->dt_f)) { fr->dead = 1; return; }
+        uint32_t ctr[4] = {id, step, 1u, 0u};
+        uint32_t r[4];
+        or_philox4x32_10(ctr, key, r);
+        fr->trials += 1;
+        float nu_tot;
+        if (s == SP_ELECTRON) {
+            float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            float speed = sqrtf(v2);
+            float eps = g->K_e * v2;
+            int lo;
+            float w;
+            egrid_locate(g, eps, &lo, &w);
+            nu_tot = 0.0f;
+            for (int j = 0; j < g->n_proc; ++j) nu_tot = nu_tot + nu_proc(g, j, eps, speed, lo, w);
+        } else {
+            nu_tot = g->nu_ion_f;
+        }
+        float pr = nu_tot * g->dt_f;
+        if (!(neg_log_u(r[0]) < pr)) return;        /* no interaction in this step */
+        collide(g, id, step, 1u, r, u01(r[1]) * nu_tot, p, v, sp, recs, rec_cap, fr);
+        return;
+    }
     float numax = (s == SP_ELECTRON) ? g->nu_max_e : g->nu_ion_f;
     float t = 0.0f;
     uint32_t k = 0;
@@ -718,122 +889,11 @@ static void fly_one(const or_gas *g, uint32_t id, uint32_t step, float *p, float
         }
         float tn = t + tau;
         float fl = (tn >= g->dt_f) ? (g->dt_f - t) : tau;
-        for (int c = 0; c < 3; ++c) {
-            float w = ha[c] * fl;
-            float x = v[c] + w;
-            float y = x * fl;
-            p[c] = p[c] + y;
-            float dv = a[c] * fl;
-            v[c] = v[c] + dv;
-        }
-        if (p[2] <= g->z_lo_f || p[2] >= g->z_hi_f) { fr->dead = 1; return; }
+        if (flight(g, p, v, a, ha, fl)) { fr->dead = 1; return; }
         if (tn >= g->dt_f) return;
         t = tn;
         fr->trials += 1;
-        /* collision trial at time t */
-        float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        float speed = sqrtf(v2);
-        float x = u01(r[1]) * numax;
-        float d[3];
-        if (s == SP_ELECTRON) {
-            float eps = g->K_e * v2;
-            int lo = 0, hi = g->n_e - 1;
-            float w;
-            if (eps < g->egrid[0]) { lo = 0; w = 0.0f; }
-            else if (eps >= g->egrid[g->n_e - 1]) { lo = g->n_e - 2; w = 1.0f; }
-            else {
-                while (hi - lo > 1) { int mid = (lo + hi) / 2; if (g->egrid[mid] <= eps) lo = mid; else hi = mid; }
-                w = (eps - g->egrid[lo]) / (g->egrid[lo + 1] - g->egrid[lo]);
-            }
-            float Ns = g->N_f * speed;
-            float cum = 0.0f;
-            int proc = -1;
-            for (int j = 0; j < g->n_proc; ++j) {
-                float nu;
-                if (g->pmode[j] == 1) {
-                    nu = g->nuc[j];
-                } else {
-                    float s0 = g->xs[(size_t)j * g->n_e + lo];
-                    float s1 = g->xs[(size_t)j * g->n_e + lo + 1];
-                    float ds = s1 - s0;
-                    float sg = s0 + w * ds;
-                    if (eps < g->thr[j]) sg = 0.0f;
-                    nu = Ns * sg;
-                }
-                cum = cum + nu;
-                if (x < cum) { proc = j; break; }
-            }
-            if (proc < 0) continue;                     /* null collision */
-            int kind = g->pkind[proc];
-            if (kind == K_ELASTIC) {
-                iso_dir(r[2], r[3], d);
-                float cosx = 0.0f;
-                if (speed > 0.0f) cosx = (v[0] * d[0] + v[1] * d[1] + v[2] * d[2]) / speed;
-                float om = 1.0f - cosx;
-                float loss = g->two_m_over_M * om;
-                float f = 1.0f - loss;
-                float sn = speed * sqrtf(f);
-                v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
-                fr->collisions += 1;
-            } else if (kind == K_EXCITATION) {
-                float e2 = eps - g->thr[proc];
-                if (e2 < 0.0f) e2 = 0.0f;
-                float sn = sqrtf(e2 / g->K_e);
-                iso_dir(r[2], r[3], d);
-                v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
-                fr->collisions += 1;
-            } else if (kind == K_IONISATION) {
-                float er = eps - g->thr[proc];
-                er = er - g->E_therm;
-                if (!(er > 0.0f)) continue;             /* not enough energy: null */
-                if (fr->n_out_sp >= rec_cap) { fr->status = ST_CAPACITY; return; }
-                float half = 0.5f * er;
-                float sn = sqrtf(half / g->K_e);
-                iso_dir(r[2], r[3], d);
-                float rr = g->KCE / (2.0f * er);
-                float o[3] = {rr * d[0], rr * d[1], rr * d[2]};
-                spawn_rec *sr = &recs[fr->n_out_sp];
-                float pn[3], pp[3];
-                for (int c = 0; c < 3; ++c) { pn[c] = p[c] + o[c]; pp[c] = p[c] - o[c]; }
-                if (pn[0] == p[0] && pn[1] == p[1] && pn[2] == p[2]) {
-                    int ax = 0;
-                    float ad0 = fabsf(d[0]), ad1 = fabsf(d[1]), ad2 = fabsf(d[2]);
-                    if (ad1 > ad0) ax = 1;
-                    if (ad2 > (ax == 1 ? ad1 : ad0)) ax = 2;
-                    pn[ax] = ulp_step(p[ax], d[ax]);
-                    pp[ax] = ulp_step(p[ax], -d[ax]);
-                }
-                uint32_t ctr[4] = {id, step, k, 1u};
-                uint32_t r2[4];
-                or_philox4x32_10(ctr, key, r2);
-                float di[3];
-                iso_dir(r2[0], r2[1], di);
-                for (int c = 0; c < 3; ++c) {
-                    sr->pi[c] = p[c];
-                    sr->vi[c] = g->v_th_ion * di[c];
-                    sr->p[c] = pn[c];
-                    sr->v[c] = sn * d[c];
-                    p[c] = pp[c];
-                    v[c] = -sn * d[c];
-                }
-                fr->n_out_sp += 1;
-                fr->collisions += 1;
-            } else { /* K_ATTACHMENT: the electron becomes an anion in place */
-                iso_dir(r[2], r[3], d);
-                for (int c = 0; c < 3; ++c) v[c] = g->v_th_ion * d[c];
-                *sp = SP_ANION;
-                fr->attached = 1;
-                fr->collisions += 1;
-                return;
-            }
-        } else {
-            /* ions: constant frequency, half isotropic elastic (speed kept),
-             * half charge exchange (fresh thermal velocity) */
-            iso_dir(r[2], r[3], d);
-            float sn = (x < g->half_nu_ion) ? speed : g->v_th_ion;
-            v[0] = sn * d[0]; v[1] = sn * d[1]; v[2] = sn * d[2];
-            fr->collisions += 1;
-        }
+        if (collide(g, id, step, k, r, u01(r[1]) * numax, p, v, sp, recs, rec_cap, fr) == 2) return;
     }
 }
 
@@ -872,6 +932,7 @@ int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
     g.dt = prm[0]; g.T = prm[1]; g.N = prm[2]; g.M_amu = prm[3]; g.nu_ion = prm[4];
     g.z_lo = prm[5]; g.z_hi = prm[6]; g.beta = prm[7];
     g.seed_lo = (uint32_t)prm[8]; g.seed_hi = (uint32_t)prm[9]; g.trial_cap = (int)prm[10];
+    g.coll_mode = (int)prm[11];
     g.n_proc = n_proc; g.n_e = n_e; g.egrid = egrid; g.xs = xs; g.pkind = pkind; g.pmode = pmode;
     g.thr = thr; g.nuc = nuc;
     gas_derive(&g);

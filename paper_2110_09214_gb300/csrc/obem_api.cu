@@ -220,6 +220,7 @@ static void derive_gas(obem_ctx *c)
     g.seed_lo = (uint32_t)(cf.seed & 0xFFFFFFFFu);
     g.seed_hi = (uint32_t)(cf.seed >> 32);
     g.trial_cap = cf.trial_cap;
+    g.coll_mode = (cf.flags & OBEM_STEP_PROB_COLLISION) ? 1 : 0;
     g.recomb_on = cf.beta >= 0.0;
     double rc = 0.0;
     if (cf.beta > 0.0) rc = cbrt(3.0 * cf.beta * cf.dt / (4.0 * OBEM_PI));

@@ -41,6 +41,7 @@ struct GasDev {
     int recomb_on;
     uint32_t seed_lo, seed_hi;
     int trial_cap;
+    int coll_mode;        // 0: null-collision trials; 1: per-step probability (OBEM_STEP_PROB_COLLISION)
 };
 
 // Cell geometry in the layout of the field kernels (structure of arrays).

@@ -123,16 +123,164 @@ __device__ __forceinline__ float next_toward(float x, float dir)
     return __int_as_float(up == pos ? b + 1 : b - 1);
 }
 
+// grid segment and weight of energy eps (linear interpolation in energy)
+__device__ __forceinline__ void egrid_locate(const GasDev &g, float eps, int &lo, float &w)
+{
+    int hi = g.n_e - 1;
+    lo = 0;
+    if (eps < __ldg(&g.egrid[0])) { lo = 0; w = 0.0f; }
+    else if (eps >= __ldg(&g.egrid[g.n_e - 1])) { lo = g.n_e - 2; w = 1.0f; }
+    else {
+        while (hi - lo > 1) {
+            int mid = (lo + hi) / 2;
+            if (__ldg(&g.egrid[mid]) <= eps) lo = mid; else hi = mid;
+        }
+        float e0 = __ldg(&g.egrid[lo]), e1 = __ldg(&g.egrid[lo + 1]);
+        w = (eps - e0) / (e1 - e0);
+    }
+}
+
+// collision frequency of process j (zero below its threshold)
+__device__ __forceinline__ float nu_proc(const GasDev &g, int j, float eps, float Ns, int lo, float w)
+{
+    if (g.mode[j] == OBEM_MODE_CONST) return g.nuc[j];
+    const float *row = g.xs + (size_t)j * g.n_e;
+    float s0 = __ldg(&row[lo]);
+    float s1 = __ldg(&row[lo + 1]);
+    float ds = s1 - s0;
+    float sg = s0 + w * ds;
+    if (eps < g.thr[j]) sg = 0.0f;
+    return Ns * sg;
+}
+
 // ------------------------------------------------------------------ one charge
 struct FlightOut {
     int dead, attached, nsp, collisions, trials, overflow;
 };
 
+// One collision trial at the charge's current state: with x uniform in
+// [0, scale), process j is taken when x < nu_1 + ... + nu_j (none: null).
+// Returns 0 when nothing happened (null, or ionisation without the energy),
+// 1 after a collision, 2 when the flight ends (attachment).
+template <bool EMIT>
+__device__ int collide(const GasDev &g, uint32_t id, uint32_t step, uint32_t k, const uint4 &r, float x,
+                       float3 &p, float3 &v, uint8_t &sp, FlightOut &fo, float4 *o_pos, float4 *o_vel,
+                       uint32_t *o_id, uint32_t *o_birth, uint8_t *o_sp, int sbase, uint32_t id_base)
+{
+    float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
+    float speed = sqrtf(v2);
+    if (sp == OBEM_ELECTRON) {
+        float eps = g.K_e * v2;
+        int lo;
+        float w;
+        egrid_locate(g, eps, lo, w);
+        float Ns = g.N * speed;
+        float cum = 0.0f;
+        int proc = -1;
+        for (int j = 0; j < g.n_proc; ++j) {
+            cum = cum + nu_proc(g, j, eps, Ns, lo, w);
+            if (x < cum) { proc = j; break; }
+        }
+        if (proc < 0) return 0;
+        const int kind = g.kind[proc];
+        if (kind == OBEM_P_ELASTIC) {
+            float3 d = isotropic(r.z, r.w);
+            float cosx = 0.0f;
+            if (speed > 0.0f) cosx = (v.x * d.x + v.y * d.y + v.z * d.z) / speed;
+            float om = 1.0f - cosx;
+            float loss = g.two_m_over_M * om;
+            float f = 1.0f - loss;
+            float sn = speed * sqrtf(f);
+            v = make_float3(sn * d.x, sn * d.y, sn * d.z);
+            fo.collisions += 1;
+        } else if (kind == OBEM_P_EXCITATION) {
+            float e2 = eps - g.thr[proc];
+            if (e2 < 0.0f) e2 = 0.0f;
+            float sn = sqrtf(e2 / g.K_e);
+            float3 d = isotropic(r.z, r.w);
+            v = make_float3(sn * d.x, sn * d.y, sn * d.z);
+            fo.collisions += 1;
+        } else if (kind == OBEM_P_IONISATION) {
+            float er = eps - g.thr[proc];
+            er = er - g.E_therm;
+            if (!(er > 0.0f)) return 0;
+            float half = 0.5f * er;
+            float sn = sqrtf(half / g.K_e);
+            float3 d = isotropic(r.z, r.w);
+            float rr = g.KCE / (2.0f * er);
+            float ox = rr * d.x, oy = rr * d.y, oz = rr * d.z;
+            float3 pn = make_float3(p.x + ox, p.y + oy, p.z + oz);
+            float3 pp = make_float3(p.x - ox, p.y - oy, p.z - oz);
+            if (pn.x == p.x && pn.y == p.y && pn.z == p.z) {
+                int axi = 0;
+                float a0 = fabsf(d.x), a1 = fabsf(d.y), a2 = fabsf(d.z);
+                if (a1 > a0) axi = 1;
+                if (a2 > (axi == 1 ? a1 : a0)) axi = 2;
+                if (axi == 0) { pn.x = next_toward(p.x, d.x); pp.x = next_toward(p.x, -d.x); }
+                else if (axi == 1) { pn.y = next_toward(p.y, d.y); pp.y = next_toward(p.y, -d.y); }
+                else { pn.z = next_toward(p.z, d.z); pp.z = next_toward(p.z, -d.z); }
+            }
+            if (EMIT) {
+                uint4 r2 = philox4x32_10(make_uint4(id, step, k, 1u), g.seed_lo, g.seed_hi);
+                float3 di = isotropic(r2.x, r2.y);
+                int slot = sbase + 2 * fo.nsp;
+                o_pos[slot] = make_float4(pn.x, pn.y, pn.z, -(float)OBEM_QE);
+                o_vel[slot] = make_float4(sn * d.x, sn * d.y, sn * d.z, 0.0f);
+                o_id[slot] = id_base + (uint32_t)(2 * fo.nsp);
+                o_birth[slot] = step + 1u;
+                o_sp[slot] = OBEM_ELECTRON;
+                o_pos[slot + 1] = make_float4(p.x, p.y, p.z, (float)OBEM_QE);
+                o_vel[slot + 1] = make_float4(g.v_th_ion * di.x, g.v_th_ion * di.y, g.v_th_ion * di.z, 0.0f);
+                o_id[slot + 1] = id_base + (uint32_t)(2 * fo.nsp + 1);
+                o_birth[slot + 1] = step + 1u;
+                o_sp[slot + 1] = OBEM_CATION;
+            }
+            p = pp;
+            v = make_float3(-sn * d.x, -sn * d.y, -sn * d.z);
+            fo.nsp += 1;
+            fo.collisions += 1;
+        } else {
+            float3 d = isotropic(r.z, r.w);
+            v = make_float3(g.v_th_ion * d.x, g.v_th_ion * d.y, g.v_th_ion * d.z);
+            sp = OBEM_ANION;
+            fo.attached = 1;
+            fo.collisions += 1;
+            return 2;
+        }
+    } else {
+        float3 d = isotropic(r.z, r.w);
+        float sn = (x < g.half_nu_ion) ? speed : g.v_th_ion;
+        v = make_float3(sn * d.x, sn * d.y, sn * d.z);
+        fo.collisions += 1;
+    }
+    return 1;
+}
+
+// ballistic flight for time fl under acceleration a (half a in h); returns
+// true when the charge crossed an absorbing plane
+__device__ __forceinline__ bool flight(const GasDev &g, float3 &p, float3 &v, float ax, float ay, float az,
+                                       float hx, float hy, float hz, float fl)
+{
+    {
+        float w = hx * fl; float xx = v.x + w; float y = xx * fl; p.x = p.x + y; float dv = ax * fl; v.x = v.x + dv;
+    }
+    {
+        float w = hy * fl; float xx = v.y + w; float y = xx * fl; p.y = p.y + y; float dv = ay * fl; v.y = v.y + dv;
+    }
+    {
+        float w = hz * fl; float xx = v.z + w; float y = xx * fl; p.z = p.z + y; float dv = az * fl; v.z = v.z + dv;
+    }
+    return p.z <= g.z_lo || p.z >= g.z_hi;
+}
+
 // Flight of charge i over one step under the field E (Euler in the field,
-// exact ballistic motion between trials), null-collision trials at
-// exponential waiting times -ln(U)/nu_max, process chosen with probability
-// nu_j(eps)/nu_max, ionisation products at the distance of Eq. (distIoni).
-// When emit is set, spawned pairs are written to o_* at slots sbase, sbase+1...
+// exact ballistic motion between trials).  Collision sampling: null-collision
+// trials at exponential waiting times -ln(U)/nu_max, process j with
+// probability nu_j(eps)/nu_max (coll_mode 0); or the paper's per-step scheme
+// (coll_mode 1): flight over the whole step, then one interaction when
+// -ln(U) < nu_tot(eps) dt, of type j with probability nu_j/nu_tot.
+// Ionisation products at the distance of Eq. (distIoni).  When EMIT is set,
+// spawned pairs are written to o_* at slots sbase, sbase+1...
 template <bool EMIT>
 __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, float3 &v, uint8_t &sp,
                     float3 E, FlightOut &fo, float4 *o_pos, float4 *o_vel, uint32_t *o_id,
@@ -142,6 +290,30 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
     const float qm = g.qm[s];
     const float ax = qm * E.x, ay = qm * E.y, az = qm * E.z;
     const float hx = 0.5f * ax, hy = 0.5f * ay, hz = 0.5f * az;
+    if (g.coll_mode == 1) {
+        if (flight(g, p, v, ax, ay, az, hx, hy, hz, g.dt)) { fo.dead = 1; return; }
+        const uint4 r = philox4x32_10(make_uint4(id, step, 1u, 0u), g.seed_lo, g.seed_hi);
+        fo.trials += 1;
+        float nu_tot;
+        if (s == OBEM_ELECTRON) {
+            float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
+            float speed = sqrtf(v2);
+            float eps = g.K_e * v2;
+            int lo;
+            float w;
+            egrid_locate(g, eps, lo, w);
+            float Ns = g.N * speed;
+            nu_tot = 0.0f;
+            for (int j = 0; j < g.n_proc; ++j) nu_tot = nu_tot + nu_proc(g, j, eps, Ns, lo, w);
+        } else {
+            nu_tot = g.nu_ion;
+        }
+        float pr = nu_tot * g.dt;
+        if (!(neg_log_unif(r.x) < pr)) return;
+        collide<EMIT>(g, id, step, 1u, r, unif01(r.y) * nu_tot, p, v, sp, fo, o_pos, o_vel, o_id, o_birth,
+                      o_sp, sbase, id_base);
+        return;
+    }
     const float numax = (s == OBEM_ELECTRON) ? g.nu_max_e : g.nu_ion;
     float t = 0.0f;
     uint32_t k = 0;
@@ -158,127 +330,13 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
         }
         float tn = t + tau;
         float fl = (tn >= g.dt) ? (g.dt - t) : tau;
-        {
-            float w = hx * fl; float xx = v.x + w; float y = xx * fl; p.x = p.x + y; float dv = ax * fl; v.x = v.x + dv;
-        }
-        {
-            float w = hy * fl; float xx = v.y + w; float y = xx * fl; p.y = p.y + y; float dv = ay * fl; v.y = v.y + dv;
-        }
-        {
-            float w = hz * fl; float xx = v.z + w; float y = xx * fl; p.z = p.z + y; float dv = az * fl; v.z = v.z + dv;
-        }
-        if (p.z <= g.z_lo || p.z >= g.z_hi) { fo.dead = 1; return; }
+        if (flight(g, p, v, ax, ay, az, hx, hy, hz, fl)) { fo.dead = 1; return; }
         if (tn >= g.dt) return;
         t = tn;
         fo.trials += 1;
-        float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
-        float speed = sqrtf(v2);
-        float x = unif01(r.y) * numax;
-        if (s == OBEM_ELECTRON) {
-            float eps = g.K_e * v2;
-            int lo = 0, hi = g.n_e - 1;
-            float w;
-            if (eps < __ldg(&g.egrid[0])) { lo = 0; w = 0.0f; }
-            else if (eps >= __ldg(&g.egrid[g.n_e - 1])) { lo = g.n_e - 2; w = 1.0f; }
-            else {
-                while (hi - lo > 1) {
-                    int mid = (lo + hi) / 2;
-                    if (__ldg(&g.egrid[mid]) <= eps) lo = mid; else hi = mid;
-                }
-                float e0 = __ldg(&g.egrid[lo]), e1 = __ldg(&g.egrid[lo + 1]);
-                w = (eps - e0) / (e1 - e0);
-            }
-            float Ns = g.N * speed;
-            float cum = 0.0f;
-            int proc = -1;
-            for (int j = 0; j < g.n_proc; ++j) {
-                float nu;
-                if (g.mode[j] == OBEM_MODE_CONST) {
-                    nu = g.nuc[j];
-                } else {
-                    const float *row = g.xs + (size_t)j * g.n_e;
-                    float s0 = __ldg(&row[lo]);
-                    float s1 = __ldg(&row[lo + 1]);
-                    float ds = s1 - s0;
-                    float sg = s0 + w * ds;
-                    if (eps < g.thr[j]) sg = 0.0f;
-                    nu = Ns * sg;
-                }
-                cum = cum + nu;
-                if (x < cum) { proc = j; break; }
-            }
-            if (proc < 0) continue;
-            const int kind = g.kind[proc];
-            if (kind == OBEM_P_ELASTIC) {
-                float3 d = isotropic(r.z, r.w);
-                float cosx = 0.0f;
-                if (speed > 0.0f) cosx = (v.x * d.x + v.y * d.y + v.z * d.z) / speed;
-                float om = 1.0f - cosx;
-                float loss = g.two_m_over_M * om;
-                float f = 1.0f - loss;
-                float sn = speed * sqrtf(f);
-                v = make_float3(sn * d.x, sn * d.y, sn * d.z);
-                fo.collisions += 1;
-            } else if (kind == OBEM_P_EXCITATION) {
-                float e2 = eps - g.thr[proc];
-                if (e2 < 0.0f) e2 = 0.0f;
-                float sn = sqrtf(e2 / g.K_e);
-                float3 d = isotropic(r.z, r.w);
-                v = make_float3(sn * d.x, sn * d.y, sn * d.z);
-                fo.collisions += 1;
-            } else if (kind == OBEM_P_IONISATION) {
-                float er = eps - g.thr[proc];
-                er = er - g.E_therm;
-                if (!(er > 0.0f)) continue;
-                float half = 0.5f * er;
-                float sn = sqrtf(half / g.K_e);
-                float3 d = isotropic(r.z, r.w);
-                float rr = g.KCE / (2.0f * er);
-                float ox = rr * d.x, oy = rr * d.y, oz = rr * d.z;
-                float3 pn = make_float3(p.x + ox, p.y + oy, p.z + oz);
-                float3 pp = make_float3(p.x - ox, p.y - oy, p.z - oz);
-                if (pn.x == p.x && pn.y == p.y && pn.z == p.z) {
-                    int axi = 0;
-                    float a0 = fabsf(d.x), a1 = fabsf(d.y), a2 = fabsf(d.z);
-                    if (a1 > a0) axi = 1;
-                    if (a2 > (axi == 1 ? a1 : a0)) axi = 2;
-                    if (axi == 0) { pn.x = next_toward(p.x, d.x); pp.x = next_toward(p.x, -d.x); }
-                    else if (axi == 1) { pn.y = next_toward(p.y, d.y); pp.y = next_toward(p.y, -d.y); }
-                    else { pn.z = next_toward(p.z, d.z); pp.z = next_toward(p.z, -d.z); }
-                }
-                if (EMIT) {
-                    uint4 r2 = philox4x32_10(make_uint4(id, step, k, 1u), g.seed_lo, g.seed_hi);
-                    float3 di = isotropic(r2.x, r2.y);
-                    int slot = sbase + 2 * fo.nsp;
-                    o_pos[slot] = make_float4(pn.x, pn.y, pn.z, -(float)OBEM_QE);
-                    o_vel[slot] = make_float4(sn * d.x, sn * d.y, sn * d.z, 0.0f);
-                    o_id[slot] = id_base + (uint32_t)(2 * fo.nsp);
-                    o_birth[slot] = step + 1u;
-                    o_sp[slot] = OBEM_ELECTRON;
-                    o_pos[slot + 1] = make_float4(p.x, p.y, p.z, (float)OBEM_QE);
-                    o_vel[slot + 1] = make_float4(g.v_th_ion * di.x, g.v_th_ion * di.y, g.v_th_ion * di.z, 0.0f);
-                    o_id[slot + 1] = id_base + (uint32_t)(2 * fo.nsp + 1);
-                    o_birth[slot + 1] = step + 1u;
-                    o_sp[slot + 1] = OBEM_CATION;
-                }
-                p = pp;
-                v = make_float3(-sn * d.x, -sn * d.y, -sn * d.z);
-                fo.nsp += 1;
-                fo.collisions += 1;
-            } else {
-                float3 d = isotropic(r.z, r.w);
-                v = make_float3(g.v_th_ion * d.x, g.v_th_ion * d.y, g.v_th_ion * d.z);
-                sp = OBEM_ANION;
-                fo.attached = 1;
-                fo.collisions += 1;
-                return;
-            }
-        } else {
-            float3 d = isotropic(r.z, r.w);
-            float sn = (x < g.half_nu_ion) ? speed : g.v_th_ion;
-            v = make_float3(sn * d.x, sn * d.y, sn * d.z);
-            fo.collisions += 1;
-        }
+        if (collide<EMIT>(g, id, step, k, r, unif01(r.y) * numax, p, v, sp, fo, o_pos, o_vel, o_id, o_birth,
+                          o_sp, sbase, id_base) == 2)
+            return;
     }
 }
 

@@ -433,6 +433,7 @@ class Tracking:
     beta: float = -1.0          # recombination rate coefficient (m^3/s); <0 off, 0 -> Eq. distRecomb
     trial_cap: int = 256
     softening: float = 1e-9     # Plummer length for the N-body field in the dynamics
+    coll_mode: int = 0          # 0: null-collision trials; 1: the paper's per-step probability
 
 
 # --------------------------------------------------------------------------

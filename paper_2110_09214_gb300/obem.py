@@ -19,7 +19,7 @@ OBEM_OK = 0
 OBEM_ERR_ARG, OBEM_ERR_CUDA, OBEM_ERR_STATE, OBEM_ERR_SINGULAR = -1, -2, -3, -4
 OBEM_ERR_NOT_CONVERGED, OBEM_ERR_CAPACITY, OBEM_ERR_TIMEOUT, OBEM_ERR_TRIALS = -5, -6, -7, -8
 OBEM_LU_FP32, OBEM_LU_TF32, OBEM_LU_BF16, OBEM_LU_BF16X9 = 0, 1, 2, 3
-OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD, OBEM_STEP_FIELD_MAP = 1, 2, 4
+OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD, OBEM_STEP_FIELD_MAP, OBEM_STEP_PROB_COLLISION = 1, 2, 4, 8
 
 
 class ObemError(RuntimeError):

@@ -78,8 +78,8 @@ def _assert_same_counts(gs, os_):
     assert gs["status"] == 0
 
 
-def _run_pair(ch, gas, trk, E_fn, steps, capacity, next_id=None):
-    g = GpuRun(gas, trk, capacity)
+def _run_pair(ch, gas, trk, E_fn, steps, capacity, next_id=None, flags=0):
+    g = GpuRun(gas, trk, capacity, flags=flags)
     try:
         g.upload(ch, next_id)
         cur, nid = ch, (ch.pos_q.shape[0] if next_id is None else next_id)
@@ -133,6 +133,29 @@ def test_argon_like_ionisation_attachment_recombination_bit_exact():
     E_fn = lambda c: base[None, :] + rng.normal(0, 2e5, (c.pos_q.shape[0], 3))
     fin = _run_pair(ch, gas, trk, E_fn, 8, 8000, next_id=ch.n + 100)
     assert fin.pos_q.shape[0] > 0
+
+
+@pytest.mark.parametrize("gas_kind", ["maxwell", "argon"])
+def test_per_step_probability_scheme_bit_exact(gas_kind):
+    """OBEM_STEP_PROB_COLLISION (the paper's own collision sampling, one
+    interaction test per step) against the oracle's same scheme: identical
+    states, decisions and counts."""
+    if gas_kind == "maxwell":
+        mesh, gas, ch, trk = inputs.config_small_plates(seed=2, n=1000)
+        trk.softening = 1e-9
+        trk.coll_mode = 1
+        sig = oracle.bem_solve(mesh)
+        E_fn = lambda c: oracle.field_at_charges(c, mesh, sig, trk.softening)
+        _run_pair(ch, gas, trk, E_fn, 15, 1200, flags=obem.OBEM_STEP_PROB_COLLISION)
+    else:
+        gas = inputs.argon_like_gas()
+        trk = inputs.Tracking(dt=1e-13, seed=7, z_lo=0.0, z_hi=2e-3, beta=1e-13, coll_mode=1)
+        ch = _hot_mixture(7)
+        rng = np.random.default_rng(11)
+        base = np.array([0.0, 0.0, -3e6])
+        E_fn = lambda c: base[None, :] + rng.normal(0, 2e5, (c.pos_q.shape[0], 3))
+        fin = _run_pair(ch, gas, trk, E_fn, 8, 8000, next_id=ch.n + 100, flags=obem.OBEM_STEP_PROB_COLLISION)
+        assert fin.pos_q.shape[0] > 0
 
 
 def test_exempt_and_tie_rules_on_gpu():

@@ -500,3 +500,36 @@ def test_swarm_fits_exact():
     assert abs(oracle.drift_velocity(t, 3e4 * t + 1e-6) - 3e4) < 1e-6
     assert abs(oracle.diffusion_coefficient(t, 2 * 0.05 * t) - 0.05) < 1e-12
     assert abs(oracle.townsend_alpha(t, 10 * np.exp(2e10 * t), 4e4) - 5e5) < 1e-3
+
+
+# ----------------------------------------------------------------------------
+# the paper's per-step collision probability (Sec. 3.3.1), coll_mode = 1
+# ----------------------------------------------------------------------------
+def test_per_step_scheme_collision_fraction_and_drift():
+    """Maxwell model (constant nu, isotropic elastic, infinite gas mass: the
+    speed is kept and the mean velocity after a collision is zero).  One step:
+    a charge collides with probability P = 1 - exp(-nu dt) and exactly one
+    test is made per charge.  Steady state: <v_z> at the start of a step
+    obeys v = (1 - P)(v + a dt), i.e. v = (1 - P) a dt / P."""
+    nu, dt = 1e12, 3e-13
+    P = 1.0 - math.exp(-nu * dt)
+    gas = inputs.maxwell_gas(nu, 0.0)
+    trk = inputs.Tracking(dt=dt, seed=3, z_lo=-1.0, z_hi=1.0, beta=-1.0, coll_mode=1)
+    n = 20000
+    rng = np.random.default_rng(1)
+    ch = inputs.make_charges(rng.uniform(-1e-4, 1e-4, (n, 3)), inputs.maxwellian(rng, n, 0.1, ME),
+                             np.zeros(n, np.uint8))
+    st, out, _, stats = oracle.step(ch, np.zeros((n, 3), np.float32), 0, n, gas, trk, n + 16)
+    assert st == 0 and stats["trials"] == n
+    frac = stats["collisions"] / n
+    assert abs(frac - P) <= 5 * math.sqrt(P * (1 - P) / n)
+    # drift to the steady state under a uniform field
+    Ez = -1e5
+    a = E * -Ez / ME                     # electron acceleration along z: -e E_z / m
+    field = np.tile(np.array([[0.0, 0.0, Ez]], np.float32), (n, 1))
+    cur = ch
+    for s_ in range(60):
+        st, cur, _, _ = oracle.step(cur, field, s_, n, gas, trk, n + 16)
+    vz = cur.vel[:, 2].astype(np.float64)
+    expect = (1 - P) * np.float32(a) * dt / P
+    assert abs(vz.mean() - expect) <= 5 * vz.std() / math.sqrt(n)
