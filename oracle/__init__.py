@@ -11,7 +11,7 @@ swarm-parameter fits of Sec. 4.1 (Eqs. (vd), (diffusion), (townsend)).
 Parity status of each function (see the test-suite for the pins):
   tri_integrals, panel_field, nbody_field, assemble, bem_solve, influence_rhs,
   philox, step, swarm fits, tri_jacobian, field_jacobian, field_backward,
-  bem_solve_adjoint, grid_nodes, trilinear: pinned.
+  bem_solve_adjoint, grid_nodes, trilinear, nbody_nn: pinned.
   Swarm parameters of the synthetic argon-like gas: parity unpinned (no closed
   form; only GPU-vs-oracle agreement within 3 sigma and the Maxwell-model
   limits are checked).
@@ -53,6 +53,7 @@ def lib():
         _lib.or_nbody_field.argtypes = [I, P, I, P, I, C.c_double, P, P]
         _lib.or_tri_jacobian.argtypes = [P, P, P]
         _lib.or_trilinear.argtypes = [I, I, I, P, P, I, P, I, P, P]
+        _lib.or_nbody_nn.argtypes = [I, P, I, C.c_double, P]
         _lib.or_field_jacobian.argtypes = [I, P, P, I, P, I, P, I, P]
         _lib.or_field_backward.argtypes = [I, P, P, I, P, I, P, I, P, P, P, P]
         _lib.or_assemble.argtypes = [I, P, P, P, P, P]
@@ -182,6 +183,16 @@ def trilinear(values, lo, hi, dims, pts):
     lib().or_trilinear(int(dims[0]), int(dims[1]), int(dims[2]), _p(_c(lo, np.float64)), _p(_c(step, np.float64)),
                        nc, _p(values), len(pts), _p(pts), _p(out))
     return out
+
+
+def nbody_nn(src, grid, soft=0.0):
+    """Approximate N-body field at the charges (Sec. 3.2.4 nearest-neighbour
+    option): exact over the 27 cells around each charge, per-sign charge
+    centres of the other cells (grid^3 cells over the bounding box)."""
+    src = _c(src, np.float64).reshape(-1, 4)
+    E = np.zeros((len(src), 3))
+    lib().or_nbody_nn(len(src), _p(src), int(grid), float(soft), _p(E))
+    return E
 
 
 def assemble(mesh):

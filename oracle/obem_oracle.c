@@ -391,6 +391,101 @@ void or_trilinear(int nx, int ny, int nz, const double *lo, const double *step, 
 }
 
 /*
+ * Approximate N-body field (Sec. 3.2.4, the nearest-neighbour "NN" option):
+ * the exact Coulomb sum of Eq. (nbody) over the charges close to a particle,
+ * the charge centres of the farther ones.  The paper describes it in one
+ * sentence; the reading here:
+ *   - cubic cells of edge W / G, W the largest extent of the charges'
+ *     bounding box (G x G x G cells cover it); the cell of a charge is
+ *     floor((x - lo) * (G / W)) per axis in binary32 (one rounding per
+ *     operation; clamped to 0..G-1), so that both implementations put a
+ *     charge in the same cell;
+ *   - near: the exact (softened) pair sum over the charges of the 27 cells
+ *     around the particle's cell, itself excluded;
+ *   - far: every other cell contributes its positive and its negative charge
+ *     separately, each as the total charge placed at its charge-weighted
+ *     centre (one "centre of charges" per sign keeps a neutral cell of
+ *     electrons and ions meaningful).
+ * src: [x, y, z, q] per charge (binary32 values); E: [n][3], FP64.
+ */
+void or_nbody_nn(int n, const double *src, int G, double soft, double *E)
+{
+    if (n <= 0) return;
+    float lo[3], hi[3], inv[3], wmax = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = hi[a] = (float)src[a];
+        for (int i = 1; i < n; ++i) {
+            float x = (float)src[4 * (size_t)i + a];
+            if (x < lo[a]) lo[a] = x;
+            if (x > hi[a]) hi[a] = x;
+        }
+        float w = hi[a] - lo[a];
+        if (w > wmax) wmax = w;
+    }
+    if (!(wmax > 0.0f)) wmax = 1.0f;
+    for (int a = 0; a < 3; ++a) inv[a] = (float)G / wmax;
+    const int ncell = G * G * G;
+    int *cell = (int *)malloc(sizeof(int) * (size_t)n);
+    int *cc = (int *)malloc(sizeof(int) * 3 * (size_t)n);
+    double *agg = (double *)calloc((size_t)ncell * 8, sizeof(double));   /* [cell][sign][x y z q] */
+    for (int i = 0; i < n; ++i) {
+        int c3[3];
+        for (int a = 0; a < 3; ++a) {
+            float x = (float)src[4 * (size_t)i + a];
+            float t = (x - lo[a]) * inv[a];
+            int k = (int)floorf(t);
+            if (k < 0) k = 0;
+            if (k > G - 1) k = G - 1;
+            c3[a] = k;
+            cc[3 * (size_t)i + a] = k;
+        }
+        int c = (c3[2] * G + c3[1]) * G + c3[0];
+        cell[i] = c;
+        double q = src[4 * (size_t)i + 3];
+        double *ag = agg + (size_t)c * 8 + (q >= 0.0 ? 0 : 4);
+        for (int a = 0; a < 3; ++a) ag[a] += q * src[4 * (size_t)i + a];
+        ag[3] += q;
+    }
+    for (int c = 0; c < 2 * ncell; ++c) {
+        double *ag = agg + (size_t)c * 4;
+        if (ag[3] != 0.0) for (int a = 0; a < 3; ++a) ag[a] /= ag[3];
+    }
+    const double s2 = soft * soft;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < n; ++i) {
+        const double *r = src + 4 * (size_t)i;
+        const int *ci = cc + 3 * (size_t)i;
+        double e[3] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < n; ++j) {                 /* near: charges of the 27 cells around */
+            if (j == i) continue;
+            const int *cj = cc + 3 * (size_t)j;
+            if (abs(cj[0] - ci[0]) > 1 || abs(cj[1] - ci[1]) > 1 || abs(cj[2] - ci[2]) > 1) continue;
+            const double *q = src + 4 * (size_t)j;
+            double d[3] = {r[0] - q[0], r[1] - q[1], r[2] - q[2]};
+            double d2 = dot3(d, d) + s2;
+            if (d2 == 0.0) continue;
+            double w = q[3] / (d2 * sqrt(d2));
+            for (int a = 0; a < 3; ++a) e[a] += w * d[a];
+        }
+        for (int c = 0; c < ncell; ++c) {             /* far: charge centres of the other cells */
+            int cx = c % G, cy = (c / G) % G, cz = c / (G * G);
+            if (abs(cx - ci[0]) <= 1 && abs(cy - ci[1]) <= 1 && abs(cz - ci[2]) <= 1) continue;
+            for (int sg = 0; sg < 2; ++sg) {
+                const double *ag = agg + (size_t)c * 8 + 4 * sg;
+                if (ag[3] == 0.0) continue;
+                double d[3] = {r[0] - ag[0], r[1] - ag[1], r[2] - ag[2]};
+                double d2 = dot3(d, d) + s2;
+                double w = ag[3] / (d2 * sqrt(d2));
+                for (int a = 0; a < 3; ++a) e[a] += w * d[a];
+            }
+        }
+        for (int a = 0; a < 3; ++a) E[3 * (size_t)i + a] = OR_KC * e[a];
+    }
+    (void)cell;
+    free(cell); free(cc); free(agg);
+}
+
+/*
  * Dense BEM matrix, Eqs. (BEMpot), (BEMfld), (matrixBEM), row-major n x n.
  *   electrode (ed) rows:   A_ij = Q_ij = k_C phi_j(r_i)
  *   dielectric (dd) rows:  A_ij = W_ij = (er+ + er-)/2 delta_ij

@@ -533,3 +533,43 @@ def test_per_step_scheme_collision_fraction_and_drift():
     vz = cur.vel[:, 2].astype(np.float64)
     expect = (1 - P) * np.float32(a) * dt / P
     assert abs(vz.mean() - expect) <= 5 * vz.std() / math.sqrt(n)
+
+
+# ----------------------------------------------------------------------------
+# approximate N-body (Sec. 3.2.4 nearest-neighbour option)
+# ----------------------------------------------------------------------------
+def _cloud(n, seed):
+    rng = np.random.default_rng(seed)
+    p = np.concatenate([rng.normal(0, 1e-5, (n // 2, 3)), rng.normal([4e-5, 0, 1e-4], 1e-5, (n - n // 2, 3))])
+    q = rng.choice([-E, E], n)
+    return np.column_stack([p, q]).astype(np.float32).astype(np.float64)
+
+
+def test_nn_with_one_or_two_cells_per_axis_is_exact():
+    """With 1 or 2 cells per axis every cell is a neighbour of every other:
+    the approximation reduces to the exact sum of Eq. (nbody)."""
+    src = _cloud(700, 1)
+    ref = oracle.nbody_field(src[:, :3], src, True, 1e-9)[0]
+    for G in (1, 2):
+        got = oracle.nbody_nn(src, G, 1e-9)
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_nn_far_cells_are_exact_for_point_like_cells():
+    """Charges on a lattice of spacing two cells (no two in neighbouring
+    cells; one lattice site holds two equal charges at the same point): every
+    far cell's charge centre is exactly its charge, so the approximation must
+    equal the exact sum of Eq. (nbody) -- a check of the cell assignment, the
+    neighbour exclusion and the per-sign aggregation."""
+    K, h = 5, 1e-5
+    rng = np.random.default_rng(4)
+    g = np.arange(K) * 2 * h
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    p = np.column_stack([X.ravel(), Y.ravel(), Z.ravel()])
+    q = rng.choice([-E, E], len(p))
+    p = np.concatenate([p, p[7:8]])
+    q = np.concatenate([q, q[7:8]])
+    src = np.column_stack([p, q]).astype(np.float32).astype(np.float64)
+    exact = oracle.nbody_field(src[:, :3], src, True, 0.0)[0]
+    nn = oracle.nbody_nn(src, 2 * K - 1, 0.0)      # cell edge 8h/9: site i in cell floor(2.25 i)
+    assert np.abs(nn - exact).max() <= 1e-12 * np.abs(exact).max()
