@@ -59,12 +59,22 @@ def nbody_traffic_per_launch(n_charges):
     try:
         with open(TRAFFIC_RECORD) as f:
             rec = json.load(f)
-        src = os.path.join(ROOT, rec["source"])
-        if _file_sha256(src) != rec["source_sha256"]:
+        if kernel_source_sha256(rec["source"], rec["section_begin"], rec["section_end"]) != rec["source_sha256"]:
             return None
         return rec["dram_bytes_per_item"] * sym_items(n_charges) + rec["dram_bytes_per_charge"] * n_charges
     except (OSError, KeyError, ValueError):
         return None
+
+
+def kernel_source_sha256(source, begin, end):
+    """sha256 of the kernel's own source text: from the line holding `begin`
+    up to (not including) the line holding `end`."""
+    import hashlib
+    with open(os.path.join(ROOT, source)) as f:
+        text = f.read()
+    i = text.index(begin)
+    j = text.index(end, i)
+    return hashlib.sha256(text[i:j].encode()).hexdigest()
 
 
 def _args():
@@ -80,6 +90,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-fieldmap", action="store_true")
+    p.add_argument("--no-nn", action="store_true")
     return p.parse_args()
 
 
@@ -315,6 +326,12 @@ def run_ours(a, ws, rank, local):
         for key, v in snap.items():
             getattr(st, key).copy_(v)
         e2e = run_e2e(ctx, st, a.steps, step + a.steps, dev)
+    nnres = None
+    if ws == 1 and not a.no_nn:
+        for key, v in snap.items():
+            getattr(st, key).copy_(v)
+        n_now = int(st.download()[0].pos_q.shape[0])
+        nnres = nn_timing(ctx, st.pos_q[:n_now], dev, trk.softening)
     obem.obem_destroy(ctx)
     if rank != 0:
         return
@@ -369,8 +386,39 @@ def run_ours(a, ws, rank, local):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fieldmap": fmap,
+        "nbody_nn": nnres,
     }
     print(json.dumps(line), flush=True)
+
+
+def nn_timing(ctx, pos_q, dev, soft, grids=(16, 32)):
+    """The approximate N-body field (Sec. 3.2.4 "NN" option) on the headline
+    charges: time per evaluation and accuracy against the exact all-pairs
+    sum -- the share of charges whose field is within 5 % (the paper's
+    criterion: 96.8 % of ~1e6 charges in its worst case)."""
+    import torch
+    from paper_2110_09214_gb300 import obem
+    n = pos_q.shape[0]
+    exact = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    obem.obem_field_eval(ctx, pos_q, exact, sources=pos_q, self_exclude=True)
+    out = {}
+    for G in grids:
+        E = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        obem.obem_nbody_nn_eval(ctx, pos_q, E, G, 0.0)           # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        obem.obem_nbody_nn_eval(ctx, pos_q, E, G, 0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rel = (torch.linalg.norm(E[:, :3] - exact[:, :3], dim=1) /
+               torch.linalg.norm(exact[:, :3], dim=1).clamp_min(1e-30))
+        out["grid_%d" % G] = {"ms": ms, "within_5pct": float((rel < 0.05).float().mean()),
+                              "median_rel_err": float(rel.median())}
+    out["charges"] = n
+    out["exact_reference"] = "symmetric all-pairs field, no softening"
+    return out
 
 
 def fieldmap_timing(dev, n_grid=256):

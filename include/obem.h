@@ -73,16 +73,21 @@ enum {
     OBEM_STEP_CELL_FIELD = 2,     /* add the BEM cell field, Eq. (BEM3), with the current sigma */
     OBEM_STEP_FIELD_MAP = 4,      /* take the cell field from the static map (obem_fieldmap_build),
                                      interpolated trilinearly; replaces OBEM_STEP_CELL_FIELD */
-    OBEM_STEP_PROB_COLLISION = 8  /* the paper's collision sampling (Sec. 3.3.1): one interaction test
+    OBEM_STEP_PROB_COLLISION = 8, /* the paper's collision sampling (Sec. 3.3.1): one interaction test
                                      per step, probability 1 - exp(-nu_tot(eps) dt), after the step's
                                      flight; default: exact null-collision trials */
+    OBEM_STEP_NBODY_NN = 16       /* the paper's approximate N-body field (Sec. 3.2.4, "NN"; see
+                                     obem_nbody_nn_eval) instead of the exact all-pairs sum, with
+                                     obem_config.nn_grid cells per axis */
 };
+
+enum { OBEM_NN_GMAX = 64 };        /* largest nn_grid */
 
 typedef struct obem_config {
     int32_t capacity;       /* largest number of charges obem_step will hold */
     int32_t trial_cap;      /* max null-collision trials per charge per step, 1..256 */
     int32_t flags;          /* OBEM_STEP_* */
-    int32_t reserved;
+    int32_t nn_grid;        /* cells per axis of the approximate N-body field, 1..64 (0: 16) */
     double dt;              /* tracking step (s) */
     uint64_t seed;          /* Philox4x32-10 key */
     double softening;       /* Plummer length of the N-body field in obem_step (m); 0 = exact */
@@ -255,6 +260,21 @@ int obem_fieldmap_build(obem_ctx *ctx, const double *lo, const double *hi, const
  * box take the value at the nearest point of the box.  OBEM_ERR_STATE without
  * a map.  Allocates nothing, does not synchronise. */
 int obem_fieldmap_eval(obem_ctx *ctx, const float *points, int32_t n, float *E_out, obem_stream stream);
+
+/* Approximate N-body field at n charges (Sec. 3.2.4, the paper's "NN"
+ * option): the exact softened Coulomb sum of Eq. (nbody) over the charges in
+ * the 27 cells around each charge (itself excluded), and for every other cell
+ * its positive and its negative charge, each at its charge-weighted centre.
+ * Cells: grid^3 cubes of edge W / grid over the charges' bounding box (W its
+ * largest extent); a charge's cell is floor((x - lo) * (grid / W)) per axis in
+ * binary32.  pos_q: device [n][4] (x, y, z, q); E_out: device [n][4]
+ * (Ex, Ey, Ez, 0).  grid: 1..OBEM_NN_GMAX.  softening: Plummer length (m).
+ * Repeatable to binary32 rounding, not bit for bit: the charges of a cell
+ * are summed in the order a counting sort with atomics leaves them (the exact
+ * all-pairs field is bit-reproducible).  Allocates nothing, does not
+ * synchronise. */
+int obem_nbody_nn_eval(obem_ctx *ctx, const float *pos_q, int32_t n, int32_t grid, double softening,
+                       float *E_out, obem_stream stream);
 
 /* One tracking step of all charges in st (Sec. 3.2 - 3.3):
  *   1. field at the step-start positions: E_in (device [capacity][4]) if not

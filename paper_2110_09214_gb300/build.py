@@ -24,6 +24,7 @@ UNITS = {
     "backward.cu": [],
     "peak.cu": [],
     "fieldmap.cu": [],
+    "nn.cu": [],
 }
 
 

@@ -1231,8 +1231,14 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             if (L.events) ctx->launches++;
         }
         // self_exclude: the targets are the sources (same charges, nt == ns)
-        const bool sym = ctx->sym_jpart && L.self_exclude && capacity_targets <= ctx->sym_cap;
-        if (sym) {
+        const bool nn = L.nn_grid > 0 && L.self_exclude;
+        const bool sym = !nn && ctx->sym_jpart && L.self_exclude && capacity_targets <= ctx->sym_cap;
+        if (nn) {
+            int rc = obem_launch_nbody_nn(ctx, L.sources, L.nt_dev, capacity_targets, L.nn_grid, L.eps2, L.E_out,
+                                          L.e_ext, add ? 1 : 0, s);
+            if (rc != OBEM_OK) return rc;
+            if (L.events) ctx->launches += 7;
+        } else if (sym) {
             OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
             const dim3 sg(ctx->sym_grid);
             if (L.want_v)
@@ -1252,7 +1258,7 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             if (add) nbody_kernel<false, true><<<grid, FT_THREADS, 0, s>>>(L);
             else nbody_kernel<false, false><<<grid, FT_THREADS, 0, s>>>(L);
         }
-        if (!sym) {
+        if (!sym && !nn) {
             OBEM_LAUNCH(ctx);
             if (L.events) ctx->launches++;
         }

@@ -57,6 +57,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     *out = NULL;
     if (cfg->capacity < 1 || cfg->capacity > (1 << 30)) return OBEM_ERR_ARG;
     if (cfg->trial_cap < 1 || cfg->trial_cap > OBEM_MAX_TRIALS) return OBEM_ERR_ARG;
+    if (cfg->nn_grid < 0 || cfg->nn_grid > OBEM_NN_GMAX) return OBEM_ERR_ARG;
     if (!(cfg->dt > 0.0) || !(cfg->softening >= 0.0) || !(cfg->z_lo < cfg->z_hi)) return OBEM_ERR_ARG;
     obem_ctx *c = (obem_ctx *)calloc(1, sizeof(obem_ctx));
     if (!c) return OBEM_ERR_ARG;
@@ -101,6 +102,13 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->ph_bucket, sizeof(int32_t) * cap);
     ALLOC(c->ph_sorted, sizeof(int32_t) * cap);
     ALLOC(c->ph_bsum, sizeof(int32_t) * (1024 + 1));
+    ALLOC(c->nn_bbox, sizeof(int) * 8);
+    ALLOC(c->nn_cell, sizeof(int32_t) * cap);
+    ALLOC(c->nn_sorted, sizeof(int32_t) * cap);
+    ALLOC(c->nn_count, sizeof(int32_t) * (size_t)OBEM_NN_GMAX * OBEM_NN_GMAX * OBEM_NN_GMAX);
+    ALLOC(c->nn_start, sizeof(int32_t) * ((size_t)OBEM_NN_GMAX * OBEM_NN_GMAX * OBEM_NN_GMAX + 1));
+    ALLOC(c->nn_cursor, sizeof(int32_t) * (size_t)OBEM_NN_GMAX * OBEM_NN_GMAX * OBEM_NN_GMAX);
+    ALLOC(c->nn_agg, sizeof(float4) * 2 * (size_t)OBEM_NN_GMAX * OBEM_NN_GMAX * OBEM_NN_GMAX);
 #undef ALLOC
     // partial sums of the symmetric all-pairs kernel: they grow as capacity^2,
     // so they are kept only within a quarter of the free memory (and 64 GB)
@@ -116,6 +124,8 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
                 free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
     free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted); free_dev(c->ph_bsum);
     free_dev(c->fm.nodes);
+    free_dev(c->nn_bbox); free_dev(c->nn_cell); free_dev(c->nn_sorted); free_dev(c->nn_count);
+    free_dev(c->nn_start); free_dev(c->nn_cursor); free_dev(c->nn_agg);
                 c->sym_jpart = c->sym_ipart = NULL;
                 c->sym_counter = NULL;
                 cudaGetLastError();
@@ -502,6 +512,22 @@ extern "C" int obem_field_eval_backward(obem_ctx *c, const float *targets, int32
     return obem_launch_backward(c, A, s);
 }
 
+extern "C" int obem_nbody_nn_eval(obem_ctx *c, const float *pos_q, int32_t n, int32_t grid, double softening,
+                                  float *E_out, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (n < 0 || n > c->cap) return obem_fail(c, OBEM_ERR_ARG, "nbody NN: n %d outside 0..%d (capacity)", n, c->cap);
+    if (grid < 1 || grid > OBEM_NN_GMAX)
+        return obem_fail(c, OBEM_ERR_ARG, "nbody NN: grid %d outside 1..%d", grid, OBEM_NN_GMAX);
+    if (!(softening >= 0.0)) return obem_fail(c, OBEM_ERR_ARG, "nbody NN: negative softening");
+    if (n == 0) return OBEM_OK;
+    if (!pos_q || !E_out) return obem_fail(c, OBEM_ERR_ARG, "nbody NN: null pos_q or E_out");
+    if (((uintptr_t)pos_q | (uintptr_t)E_out) & 15)
+        return obem_fail(c, OBEM_ERR_ARG, "nbody NN: arrays must be 16-byte aligned");
+    return obem_launch_nbody_nn(c, (const float4 *)pos_q, NULL, n, grid, (float)(softening * softening),
+                                (float4 *)E_out, make_float3(0.f, 0.f, 0.f), 0, (cudaStream_t)stream);
+}
+
 extern "C" int obem_fieldmap_build(obem_ctx *c, const double *lo, const double *hi, const int32_t *dims,
                                    const float *sigma, obem_stream stream)
 {
@@ -602,6 +628,7 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         L.E_out = c->s_E;
         L.e_ext = e_ext;
         L.add_init = want_map;
+        L.nn_grid = (c->cfg.flags & OBEM_STEP_NBODY_NN) ? (c->cfg.nn_grid > 0 ? c->cfg.nn_grid : 16) : 0;
         L.want_v = 0;
         if (ev) L.counters = c->d_counters;
         L.events = ev;

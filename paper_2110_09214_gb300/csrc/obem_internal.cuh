@@ -133,6 +133,11 @@ struct obem_ctx {
     int32_t *ph_count, *ph_start, *ph_cursor, *ph_bucket, *ph_sorted, *ph_bsum;
     // static field map (nodes == NULL until obem_fieldmap_build)
     FieldMapDev fm;
+    // approximate N-body: bounding box, cell of each charge, cell counts /
+    // starts / cursors, charges sorted by cell, per-cell charge centres
+    int *nn_bbox;
+    int32_t *nn_cell, *nn_sorted, *nn_count, *nn_start, *nn_cursor;
+    float4 *nn_agg;
     int *sym_counter;
     int sym_grid, sym_cap;
     // stage timing (obem_profile)
@@ -191,6 +196,8 @@ struct FieldLaunch {
     const int32_t *nblocks;
     // E_out already holds a field to add to (e.g. the interpolated map)
     int add_init;
+    // > 0: the charges' field by the approximate N-body method on this grid
+    int nn_grid;
 };
 #define OBEM_BINS_PER_AXIS 64
 #define OBEM_NBINS (OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS)
@@ -200,6 +207,10 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
 size_t obem_sym_jpart_floats(int capacity);
 size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);
+
+// nn.cu
+int obem_launch_nbody_nn(obem_ctx *c, const float4 *pos, const int32_t *n_dev, int n, int G, float eps2,
+                         float4 *E_out, float3 e_ext, int add, cudaStream_t s);
 
 // fieldmap.cu
 int obem_fieldmap_build_nodes(obem_ctx *ctx, const float *sigma, cudaStream_t s);

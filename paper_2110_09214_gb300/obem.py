@@ -20,6 +20,7 @@ OBEM_ERR_ARG, OBEM_ERR_CUDA, OBEM_ERR_STATE, OBEM_ERR_SINGULAR = -1, -2, -3, -4
 OBEM_ERR_NOT_CONVERGED, OBEM_ERR_CAPACITY, OBEM_ERR_TIMEOUT, OBEM_ERR_TRIALS = -5, -6, -7, -8
 OBEM_LU_FP32, OBEM_LU_TF32, OBEM_LU_BF16, OBEM_LU_BF16X9 = 0, 1, 2, 3
 OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD, OBEM_STEP_FIELD_MAP, OBEM_STEP_PROB_COLLISION = 1, 2, 4, 8
+OBEM_STEP_NBODY_NN, OBEM_NN_GMAX = 16, 64
 
 
 class ObemError(RuntimeError):
@@ -30,7 +31,7 @@ class ObemError(RuntimeError):
 
 class obem_config(C.Structure):
     _fields_ = [("capacity", C.c_int32), ("trial_cap", C.c_int32), ("flags", C.c_int32),
-                ("reserved", C.c_int32), ("dt", C.c_double), ("seed", C.c_uint64),
+                ("nn_grid", C.c_int32), ("dt", C.c_double), ("seed", C.c_uint64),
                 ("softening", C.c_double), ("z_lo", C.c_double), ("z_hi", C.c_double),
                 ("beta", C.c_double), ("e_ext", C.c_double * 3)]
 
@@ -98,11 +99,13 @@ def load():
     lib.obem_profile.argtypes = [P, I]
     lib.obem_alu_rates.argtypes = [P, P, P]
     lib.obem_fieldmap_build.argtypes = [P, P, P, P, P, P]
+    lib.obem_nbody_nn_eval.argtypes = [P, P, I, I, C.c_double, P, P]
     lib.obem_fieldmap_eval.argtypes = [P, P, I, P, P]
     lib.obem_stage_times.argtypes = [P, P, P]
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
               "obem_bem_solve", "obem_bem_solve_adjoint", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
-              "obem_stage_times", "obem_alu_rates", "obem_fieldmap_build", "obem_fieldmap_eval"):
+              "obem_stage_times", "obem_alu_rates", "obem_fieldmap_build", "obem_fieldmap_eval",
+              "obem_nbody_nn_eval"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -132,9 +135,9 @@ def _host(a, dtype):
 # ---------------------------------------------------------------- entry points
 def obem_create(capacity, dt, seed=1, softening=0.0, z_lo=-1.0, z_hi=1.0, beta=-1.0,
                 trial_cap=256, flags=OBEM_STEP_SPACE_CHARGE | OBEM_STEP_CELL_FIELD,
-                e_ext=(0.0, 0.0, 0.0)):
+                e_ext=(0.0, 0.0, 0.0), nn_grid=0):
     cfg = obem_config(capacity=int(capacity), trial_cap=int(trial_cap), flags=int(flags),
-                      reserved=0, dt=float(dt), seed=int(seed), softening=float(softening),
+                      nn_grid=int(nn_grid), dt=float(dt), seed=int(seed), softening=float(softening),
                       z_lo=float(z_lo), z_hi=float(z_hi), beta=float(beta),
                       e_ext=(C.c_double * 3)(*[float(x) for x in e_ext]))
     ctx = C.c_void_p()
@@ -338,6 +341,12 @@ def obem_fieldmap_build(ctx, lo, hi, dims, sigma, stream=None):
 
 def obem_fieldmap_eval(ctx, points, E_out, stream=None):
     _check(ctx, load().obem_fieldmap_eval(ctx, _ptr(points), points.shape[0], _ptr(E_out), _stream(stream)))
+
+
+def obem_nbody_nn_eval(ctx, pos_q, E_out, grid, softening=0.0, stream=None):
+    """Approximate N-body field at the charges (see include/obem.h)."""
+    _check(ctx, load().obem_nbody_nn_eval(ctx, _ptr(pos_q), pos_q.shape[0], int(grid), float(softening),
+                                          _ptr(E_out), _stream(stream)))
 
 
 def obem_profile(ctx, enable=True):

@@ -538,7 +538,7 @@ def test_per_step_scheme_collision_fraction_and_drift():
 # ----------------------------------------------------------------------------
 # approximate N-body (Sec. 3.2.4 nearest-neighbour option)
 # ----------------------------------------------------------------------------
-def _cloud(n, seed):
+def _nn_cloud(n, seed):
     rng = np.random.default_rng(seed)
     p = np.concatenate([rng.normal(0, 1e-5, (n // 2, 3)), rng.normal([4e-5, 0, 1e-4], 1e-5, (n - n // 2, 3))])
     q = rng.choice([-E, E], n)
@@ -548,7 +548,7 @@ def _cloud(n, seed):
 def test_nn_with_one_or_two_cells_per_axis_is_exact():
     """With 1 or 2 cells per axis every cell is a neighbour of every other:
     the approximation reduces to the exact sum of Eq. (nbody)."""
-    src = _cloud(700, 1)
+    src = _nn_cloud(700, 1)
     ref = oracle.nbody_field(src[:, :3], src, True, 1e-9)[0]
     for G in (1, 2):
         got = oracle.nbody_nn(src, G, 1e-9)
