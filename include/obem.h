@@ -76,9 +76,11 @@ enum {
     OBEM_STEP_PROB_COLLISION = 8, /* the paper's collision sampling (Sec. 3.3.1): one interaction test
                                      per step, probability 1 - exp(-nu_tot(eps) dt), after the step's
                                      flight; default: exact null-collision trials */
-    OBEM_STEP_NBODY_NN = 16       /* the paper's approximate N-body field (Sec. 3.2.4, "NN"; see
+    OBEM_STEP_NBODY_NN = 16,      /* the paper's approximate N-body field (Sec. 3.2.4, "NN"; see
                                      obem_nbody_nn_eval) instead of the exact all-pairs sum, with
                                      obem_config.nn_grid cells per axis */
+    OBEM_STEP_SURFACE_HITS = 32   /* cells absorb the charges whose sub-flight chords cross them and
+                                     count their charge (charging-up, Sec. 3.2.3; obem_surface_charge) */
 };
 
 enum { OBEM_NN_GMAX = 64 };        /* largest nn_grid */
@@ -260,6 +262,18 @@ int obem_fieldmap_build(obem_ctx *ctx, const double *lo, const double *hi, const
  * box take the value at the nearest point of the box.  OBEM_ERR_STATE without
  * a map.  Allocates nothing, does not synchronise. */
 int obem_fieldmap_eval(obem_ctx *ctx, const float *points, int32_t n, float *E_out, obem_stream stream);
+
+/* Charging-up (Sec. 3.2.3, Eq. (charge-up)).  With OBEM_STEP_SURFACE_HITS,
+ * obem_step tests the chord of every ballistic sub-flight against the loaded
+ * cells (Moller-Trumbore in binary32; the earliest crossing, ties to the
+ * lower cell index): a charge crossing a cell is absorbed there and its
+ * charge (+-1 e) is added to the cell's count when the step commits.  This
+ * call reads the counts: sigma_free (device [n_panels] or NULL) receives the
+ * free surface density e * count / area on dielectric cells (0 on electrode
+ * cells) to pass to obem_bem_solve; counts (host [n_panels] or NULL) the raw
+ * counts; reset != 0 zeroes them afterwards.  OBEM_ERR_STATE without a mesh.
+ * Synchronises `stream` when counts is given. */
+int obem_surface_charge(obem_ctx *ctx, float *sigma_free, int64_t *counts, int32_t reset, obem_stream stream);
 
 /* Approximate N-body field at n charges (Sec. 3.2.4, the paper's "NN"
  * option): the exact softened Coulomb sum of Eq. (nbody) over the charges in

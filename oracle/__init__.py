@@ -63,7 +63,7 @@ def lib():
         _lib.or_philox4x32_10.argtypes = [P, P, P]
         _lib.or_gas_constants.argtypes = [P, I, I, P, P, P, P, P, P, P]
         _lib.or_step.argtypes = [I, P, P, P, P, P, P, U, U, P, I, I, P, P, P, P, P, P,
-                                 I, P, P, P, P, P, P, P, P]
+                                 I, P, P, P, P, P, P, P, P, I, P, P]
         _lib.or_step.restype = I
         _lib.or_neg_log_u.argtypes = [U]
         _lib.or_neg_log_u.restype = C.c_float
@@ -284,7 +284,8 @@ def _prm(gas, trk):
     seed = int(trk.seed)
     return np.array([trk.dt, gas.T, gas.N, gas.M_amu, gas.nu_ion, trk.z_lo, trk.z_hi,
                      trk.beta, seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF, trk.trial_cap,
-                     getattr(trk, "coll_mode", 0)], np.float64)
+                     getattr(trk, "coll_mode", 0), 1 if getattr(trk, "surface_hits", False) else 0],
+                    np.float64)
 
 
 def _gas_arrays(gas):
@@ -302,9 +303,12 @@ def gas_constants(gas, trk):
     return dict(zip(keys, out.tolist()))
 
 
-def step(ch, E, step_index, next_id, gas, trk, capacity=None):
+def step(ch, E, step_index, next_id, gas, trk, capacity=None, mesh=None, deposits=None):
     """One tracking step (binary32 decisions).  Returns (status, charges_out,
-    next_id_out, stats dict)."""
+    next_id_out, stats dict).  With trk.surface_hits and a mesh, charges whose
+    sub-flight chords cross a cell are absorbed there and counted (in units
+    of e, by sign) into deposits (int64 [n_cells], updated in place when the
+    step commits)."""
     from types import SimpleNamespace
     n = ch.pos_q.shape[0]
     cap = int(capacity if capacity is not None else max(4 * n + 64, 64))
@@ -324,10 +328,15 @@ def step(ch, E, step_index, next_id, gas, trk, capacity=None):
     ids = _c(ch.id, np.uint32)
     birth = _c(ch.birth, np.uint32)
     sp = _c(ch.species, np.uint8)
+    tri9 = _c(np.zeros((0, 9)) if mesh is None else np.asarray(mesh.tri).reshape(-1, 9), np.float32)
+    if deposits is None:
+        deposits = np.zeros(len(tri9), np.int64)
+    assert deposits.dtype == np.int64 and deposits.flags.c_contiguous and len(deposits) == len(tri9)
     st = lib().or_step(n, _p(pos), _p(vel), _p(ids), _p(birth), _p(sp), _p(E),
                        int(step_index), int(next_id), _p(prm), gas.n_proc, len(eg), _p(eg),
                        _p(xs), _p(kind), _p(mode), _p(thr), _p(nuc), cap, _p(o_pos), _p(o_vel),
-                       _p(o_id), _p(o_birth), _p(o_sp), _p(o_n), _p(o_next), _p(stats))
+                       _p(o_id), _p(o_birth), _p(o_sp), _p(o_n), _p(o_next), _p(stats),
+                       len(tri9), _p(tri9), _p(deposits))
     m = int(o_n[0]) if st == ST_OK else 0
     out = SimpleNamespace(pos_q=o_pos[:m].copy(), vel=o_vel[:m].copy(), id=o_id[:m].copy(),
                           birth=o_birth[:m].copy(), species=o_sp[:m].copy(), n=m)

@@ -700,6 +700,10 @@ typedef struct {
           two_m_over_M, KCE, N_f, z_lo_f, z_hi_f, rc2, ion_thr;
     int recomb_on;
     int coll_mode;     /* 0: null-collision trials; 1: the paper's per-step probability */
+    /* cells that absorb charges crossing them (charging-up): binary32
+     * vertices [ntri][9]; hit_on = 0: only the planes z_lo / z_hi absorb */
+    int hit_on, ntri;
+    const float *tri9;
 } or_gas;
 
 /* Derived constants: each is computed in FP64 from the primary parameters and
@@ -777,9 +781,43 @@ typedef struct {
     int collisions;
     int trials;
     int status;
+    int hit_cell;      /* cell that absorbed the charge, or -1 */
 } flight_result;
 
 typedef struct { float p[3], v[3]; float pi[3], vi[3]; uint32_t parent; } spawn_rec;
+
+/* First cell crossed by the straight segment a -> b (the chord of one
+ * ballistic sub-flight), by the Moller-Trumbore ray-triangle test evaluated
+ * in binary32 with this operation order (the decision is shared with the GPU
+ * bit for bit): edges e1 = v1 - v0, e2 = v2 - v0, d = b - a, h = d x e2,
+ * det = e1.h (0: parallel, no hit), s = a - v0, u = (s.h)/det in [0, 1],
+ * q = s x e1, v = (d.q)/det >= 0 with u + v <= 1, t = (e2.q)/det in [0, 1].
+ * The smallest t wins, ties to the lower cell index.  Returns the cell or -1. */
+static int seg_hit(const or_gas *g, const float *a, const float *b)
+{
+    int best = -1;
+    float bt = 0.0f;
+    const float d0 = b[0] - a[0], d1 = b[1] - a[1], d2 = b[2] - a[2];
+    for (int k = 0; k < g->ntri; ++k) {
+        const float *v = g->tri9 + 9 * (size_t)k;
+        const float e10 = v[3] - v[0], e11 = v[4] - v[1], e12 = v[5] - v[2];
+        const float e20 = v[6] - v[0], e21 = v[7] - v[1], e22 = v[8] - v[2];
+        const float h0 = d1 * e22 - d2 * e21, h1 = d2 * e20 - d0 * e22, h2 = d0 * e21 - d1 * e20;
+        const float det = e10 * h0 + e11 * h1 + e12 * h2;
+        if (det == 0.0f) continue;
+        const float inv = 1.0f / det;
+        const float s0 = a[0] - v[0], s1 = a[1] - v[1], s2 = a[2] - v[2];
+        const float u = (s0 * h0 + s1 * h1 + s2 * h2) * inv;
+        if (!(u >= 0.0f && u <= 1.0f)) continue;
+        const float q0 = s1 * e12 - s2 * e11, q1 = s2 * e10 - s0 * e12, q2 = s0 * e11 - s1 * e10;
+        const float w = (d0 * q0 + d1 * q1 + d2 * q2) * inv;
+        if (!(w >= 0.0f && u + w <= 1.0f)) continue;
+        const float t = (e20 * q0 + e21 * q1 + e22 * q2) * inv;
+        if (!(t >= 0.0f && t <= 1.0f)) continue;
+        if (best < 0 || t < bt) { best = k; bt = t; }
+    }
+    return best;
+}
 
 /* Collision frequency of process j for an electron of energy eps and speed
  * (linear interpolation in energy on the float grid, zero below threshold). */
@@ -926,7 +964,10 @@ static int flight(const or_gas *g, float *p, float *v, const float *a, const flo
  * Flight and collisions of one charge over one step dt under the step-start
  * field E (Sec. 3.2.5 Euler stepper: one field evaluation per step).  The
  * charge's state (p, v, species) is updated in place; ionisations append
- * spawn records (Sec. 3.3.3, Eq. (distIoni)).  Collision sampling:
+ * spawn records (Sec. 3.3.3, Eq. (distIoni)).  A charge is absorbed where
+ * the chord of a sub-flight crosses a cell (when cells absorb: charging-up,
+ * Sec. 3.2.3) or where it ends beyond a plane z_lo / z_hi.  Collision
+ * sampling:
  *   coll_mode 0 -- exact null-collision trials (Skullerud 1968, cited in
  *     Sec. 3.3.1): exponential waiting times -ln(U)/nu_max, process j taken
  *     with probability nu_j(eps)/nu_max at each trial;
@@ -944,7 +985,10 @@ static void fly_one(const or_gas *g, uint32_t id, uint32_t step, float *p, float
     float a[3] = {qm * E[0], qm * E[1], qm * E[2]};
     float ha[3] = {0.5f * a[0], 0.5f * a[1], 0.5f * a[2]};
     if (g->coll_mode == 1) {
-        if (flight(g, p, v, a, ha, g->dt_f)) { fr->dead = 1; return; }
+        const float p0[3] = {p[0], p[1], p[2]};
+        const int crossed = flight(g, p, v, a, ha, g->dt_f);
+        if (g->hit_on && (fr->hit_cell = seg_hit(g, p0, p)) >= 0) { fr->dead = 1; return; }
+        if (crossed) { fr->dead = 1; return; }
         uint32_t ctr[4] = {id, step, 1u, 0u};
         uint32_t r[4];
         or_philox4x32_10(ctr, key, r);
@@ -984,7 +1028,10 @@ static void fly_one(const or_gas *g, uint32_t id, uint32_t step, float *p, float
         }
         float tn = t + tau;
         float fl = (tn >= g->dt_f) ? (g->dt_f - t) : tau;
-        if (flight(g, p, v, a, ha, fl)) { fr->dead = 1; return; }
+        const float p0[3] = {p[0], p[1], p[2]};
+        const int crossed = flight(g, p, v, a, ha, fl);
+        if (g->hit_on && (fr->hit_cell = seg_hit(g, p0, p)) >= 0) { fr->dead = 1; return; }
+        if (crossed) { fr->dead = 1; return; }
         if (tn >= g->dt_f) return;
         t = tn;
         fr->trials += 1;
@@ -1020,7 +1067,8 @@ int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
             int n_proc, int n_e, const float *egrid, const float *xs, const int *pkind,
             const int *pmode, const float *thr, const float *nuc,
             int cap, float *o_pos_q, float *o_vel, uint32_t *o_id, uint32_t *o_birth,
-            uint8_t *o_species, int *o_n, uint32_t *o_next_id, double *stats)
+            uint8_t *o_species, int *o_n, uint32_t *o_next_id, double *stats,
+            int ntri, const float *tri9, int64_t *deposits)
 {
     or_gas g;
     memset(&g, 0, sizeof g);
@@ -1028,6 +1076,9 @@ int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
     g.z_lo = prm[5]; g.z_hi = prm[6]; g.beta = prm[7];
     g.seed_lo = (uint32_t)prm[8]; g.seed_hi = (uint32_t)prm[9]; g.trial_cap = (int)prm[10];
     g.coll_mode = (int)prm[11];
+    g.hit_on = prm[12] != 0.0 && ntri > 0;
+    g.ntri = ntri;
+    g.tri9 = tri9;
     g.n_proc = n_proc; g.n_e = n_e; g.egrid = egrid; g.xs = xs; g.pkind = pkind; g.pmode = pmode;
     g.thr = thr; g.nuc = nuc;
     gas_derive(&g);
@@ -1077,7 +1128,9 @@ int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
     spawn_rec *recs = malloc(sizeof(spawn_rec) * rec_cap_total);
     int n_rec = 0;
     int status = ST_OK, absorbed = 0, attached = 0, collisions = 0, trials = 0;
+    int *hit = malloc(sizeof(int) * ((size_t)n + 1));
     for (int i = 0; i < n; ++i) {
+        hit[i] = -1;
         memcpy(np_ + 4 * (size_t)i, pos_q + 4 * (size_t)i, sizeof(float) * 4);
         memcpy(nv_ + 4 * (size_t)i, vel + 4 * (size_t)i, sizeof(float) * 4);
         nsp[i] = species[i];
@@ -1085,10 +1138,11 @@ int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
         spawn_rec local[OR_MAX_TRIALS];
         flight_result fr;
         memset(&fr, 0, sizeof fr);
+        fr.hit_cell = -1;
         fly_one(&g, id[i], step, np_ + 4 * (size_t)i, nv_ + 4 * (size_t)i, &nsp[i],
                 E + 3 * (size_t)i, local, OR_MAX_TRIALS, &fr);
         if (fr.status != ST_OK) { status = fr.status; break; }
-        if (fr.dead) { gone[i] = 2; absorbed += 1; }
+        if (fr.dead) { gone[i] = 2; absorbed += 1; hit[i] = fr.hit_cell; }
         attached += fr.attached;
         collisions += fr.collisions;
         trials += fr.trials;
@@ -1109,9 +1163,14 @@ int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
     stats[9] = collisions; stats[10] = trials; stats[11] = n_new;
     if (status == ST_OK && n_new > cap) status = ST_CAPACITY;
     if (status != ST_OK) {
-        free(gone); free(np_); free(nv_); free(nsp); free(recs);
+        free(gone); free(np_); free(nv_); free(nsp); free(recs); free(hit);
         return status;
     }
+    /* charges collected by cells (Eq. (charge-up) works with their sum per
+     * cell), committed with the step */
+    if (deposits)
+        for (int i = 0; i < n; ++i)
+            if (hit[i] >= 0) deposits[hit[i]] += pos_q[4 * (size_t)i + 3] > 0.0f ? 1 : -1;
     /* 4. compaction */
     int o = 0;
     for (int i = 0; i < n; ++i) {
@@ -1150,7 +1209,7 @@ int or_step(int n, const float *pos_q, const float *vel, const uint32_t *id,
             for (int c = 0; c < 3; ++c) { stats[18 + c] += pp[c]; stats[21 + c] += (double)pp[c] * pp[c]; }
         }
     }
-    free(gone); free(np_); free(nv_); free(nsp); free(recs);
+    free(gone); free(np_); free(nv_); free(nsp); free(recs); free(hit);
     return ST_OK;
 }
 

@@ -31,6 +31,11 @@ static void free_mesh(obem_ctx *c)
     free_dev(c->d_nrm); free_dev(c->d_c_lo); free_dev(c->d_v64); free_dev(c->d_kind); free_dev(c->d_group);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
+    free_dev(c->d_tri9); free_dev(c->d_hstart); free_dev(c->d_htri); free_dev(c->d_area); free_dev(c->d_deposit);
+    c->d_tri9 = NULL;
+    c->d_hstart = c->d_htri = NULL;
+    c->d_area = NULL;
+    c->d_deposit = NULL;
     c->d_c_a = c->d_g0_h = c->d_g1 = c->d_g2 = c->d_nrm = c->d_c_lo = NULL;
     c->d_v64 = NULL;
     c->d_kind = c->d_group = NULL;
@@ -103,6 +108,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->ph_sorted, sizeof(int32_t) * cap);
     ALLOC(c->ph_bsum, sizeof(int32_t) * (1024 + 1));
     ALLOC(c->nn_bbox, sizeof(int) * 8);
+    ALLOC(c->s_hit, sizeof(int32_t) * cap);
     ALLOC(c->nn_cell, sizeof(int32_t) * cap);
     ALLOC(c->nn_sorted, sizeof(int32_t) * cap);
     ALLOC(c->nn_count, sizeof(int32_t) * (size_t)OBEM_NN_GMAX * OBEM_NN_GMAX * OBEM_NN_GMAX);
@@ -124,6 +130,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
                 free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
     free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted); free_dev(c->ph_bsum);
     free_dev(c->fm.nodes);
+    free_dev(c->s_hit);
     free_dev(c->nn_bbox); free_dev(c->nn_cell); free_dev(c->nn_sorted); free_dev(c->nn_count);
     free_dev(c->nn_start); free_dev(c->nn_cursor); free_dev(c->nn_agg);
                 c->sym_jpart = c->sym_ipart = NULL;
@@ -390,6 +397,87 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
     UP(c->d_v64, tri, sizeof(double) * 9 * np);
     UP(c->d_kind, kind, sizeof(int) * np);
     UP(c->d_group, group, sizeof(int) * np);
+    // charging-up: binary32 vertices, areas, and a uniform grid over the
+    // cells (cubic grid cells of about two mean cell sizes, at most 256 per
+    // axis; each cell listed in every grid cell its bounding box touches,
+    // padded by one grid cell on every side)
+    {
+        float *t9 = (float *)malloc(sizeof(float) * 9 * np);
+        double *ar = (double *)malloc(sizeof(double) * np);
+        double mean_h = 0.0;
+        for (int i = 0; i < np; ++i) {
+            const double *v = tri + 9 * (size_t)i;
+            for (int k = 0; k < 9; ++k) t9[9 * (size_t)i + k] = (float)v[k];
+            double e1[3], e2[3];
+            for (int k = 0; k < 3; ++k) { e1[k] = v[3 + k] - v[k]; e2[k] = v[6 + k] - v[k]; }
+            const double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2],
+                         nz = e1[0] * e2[1] - e1[1] * e2[0];
+            ar[i] = 0.5 * sqrt(nx * nx + ny * ny + nz * nz);
+            mean_h += sqrt(2.0 * ar[i]);
+        }
+        mean_h /= np;
+        float ext = 0.0f;
+        for (int k = 0; k < 3; ++k) {
+            c->h_hlo[k] = c->bbox_lo[k];
+            ext = fmaxf(ext, c->bbox_hi[k] - c->bbox_lo[k]);
+        }
+        float cellw = (float)(2.0 * mean_h);
+        if (!(cellw > ext / 256.0f)) cellw = ext / 256.0f;
+        if (!(cellw > 0.0f)) cellw = 1.0f;
+        c->h_hinv = 1.0f / cellw;
+        size_t ncell = 1;
+        for (int k = 0; k < 3; ++k) {
+            int d = (int)floorf((c->bbox_hi[k] - c->h_hlo[k]) * c->h_hinv) + 1;
+            c->h_hdim[k] = d < 1 ? 1 : (d > 256 ? 256 : d);
+            ncell *= (size_t)c->h_hdim[k];
+        }
+        auto coord = [&](float x, int k) {
+            int q = (int)floorf((x - c->h_hlo[k]) * c->h_hinv);
+            return q < 0 ? 0 : (q > c->h_hdim[k] - 1 ? c->h_hdim[k] - 1 : q);
+        };
+        int32_t *cnt = (int32_t *)calloc(ncell + 1, sizeof(int32_t));
+        for (int pass = 0; pass < 2; ++pass) {
+            int32_t *lst = NULL;
+            if (pass == 1) {
+                for (size_t q = 0, run = 0; q <= ncell; ++q) { int32_t t = cnt[q]; cnt[q] = (int32_t)run; run += t; }
+                lst = (int32_t *)malloc(sizeof(int32_t) * ((size_t)cnt[ncell] + 1));
+            }
+            int32_t *cur = pass == 1 ? (int32_t *)malloc(sizeof(int32_t) * (ncell + 1)) : NULL;
+            if (cur) memcpy(cur, cnt, sizeof(int32_t) * (ncell + 1));
+            for (int i = 0; i < np; ++i) {
+                int lo3[3], hi3[3];
+                for (int k = 0; k < 3; ++k) {
+                    float mn = t9[9 * (size_t)i + k], mx = mn;
+                    for (int v = 1; v < 3; ++v) {
+                        mn = fminf(mn, t9[9 * (size_t)i + 3 * v + k]);
+                        mx = fmaxf(mx, t9[9 * (size_t)i + 3 * v + k]);
+                    }
+                    lo3[k] = coord(mn, k) - 1; hi3[k] = coord(mx, k) + 1;
+                    if (lo3[k] < 0) lo3[k] = 0;
+                    if (hi3[k] > c->h_hdim[k] - 1) hi3[k] = c->h_hdim[k] - 1;
+                }
+                for (int z = lo3[2]; z <= hi3[2]; ++z)
+                    for (int y = lo3[1]; y <= hi3[1]; ++y)
+                        for (int x = lo3[0]; x <= hi3[0]; ++x) {
+                            size_t q = ((size_t)z * c->h_hdim[1] + y) * c->h_hdim[0] + x;
+                            if (pass == 0) cnt[q] += 1;
+                            else lst[cur[q]++] = i;
+                        }
+            }
+            if (pass == 1) {
+                UP(c->d_htri, lst, sizeof(int32_t) * ((size_t)cnt[ncell] + 1));
+                UP(c->d_hstart, cnt, sizeof(int32_t) * (ncell + 1));
+                free(lst);
+                free(cur);
+            }
+        }
+        UP(c->d_tri9, t9, sizeof(float) * 9 * np);
+        UP(c->d_area, ar, sizeof(double) * np);
+        free(cnt); free(t9); free(ar);
+        if (rc == OBEM_OK && (cudaMalloc((void **)&c->d_deposit, sizeof(long long) * np) != cudaSuccess ||
+                              cudaMemset(c->d_deposit, 0, sizeof(long long) * np) != cudaSuccess))
+            rc = obem_fail(c, OBEM_ERR_CUDA, "mesh: deposit allocation failed");
+    }
 #undef UP
     free(ca); free(g0); free(g1); free(g2); free(nr); free(cl);
     if (rc == OBEM_OK && cudaMalloc((void **)&c->d_sigma, sizeof(float) * np) != cudaSuccess)
@@ -510,6 +598,24 @@ extern "C" int obem_field_eval_backward(obem_ctx *c, const float *targets, int32
     A.dL_dtargets = dL_dtargets;
     A.dL_dsources = dL_dsources;
     return obem_launch_backward(c, A, s);
+}
+
+extern "C" int obem_surface_charge(obem_ctx *c, float *sigma_free, int64_t *counts, int32_t reset,
+                                   obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (c->np < 1 || !c->d_deposit) return obem_fail(c, OBEM_ERR_STATE, "surface charge: no mesh loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sigma_free) {
+        int rc = obem_launch_surface_sigma(c, sigma_free, s);
+        if (rc != OBEM_OK) return rc;
+    }
+    if (counts) {
+        OBEM_CUDA(c, cudaMemcpyAsync(counts, c->d_deposit, sizeof(long long) * c->np, cudaMemcpyDeviceToHost, s));
+        OBEM_CUDA(c, cudaStreamSynchronize(s));
+    }
+    if (reset) OBEM_CUDA(c, cudaMemsetAsync(c->d_deposit, 0, sizeof(long long) * c->np, s));
+    return OBEM_OK;
 }
 
 extern "C" int obem_nbody_nn_eval(obem_ctx *c, const float *pos_q, int32_t n, int32_t grid, double softening,

@@ -42,6 +42,12 @@ struct GasDev {
     uint32_t seed_lo, seed_hi;
     int trial_cap;
     int coll_mode;        // 0: null-collision trials; 1: per-step probability (OBEM_STEP_PROB_COLLISION)
+    // cells absorbing the charges crossing them (OBEM_STEP_SURFACE_HITS)
+    int hit_on;
+    const float *tri9;    // binary32 vertices [np][9]
+    const int32_t *hstart, *htri;   // uniform grid over the cells: CSR lists of cells per grid cell
+    float hlo[3], hinv;
+    int hdim[3];
 };
 
 // Cell geometry in the layout of the field kernels (structure of arrays).
@@ -133,6 +139,15 @@ struct obem_ctx {
     int32_t *ph_count, *ph_start, *ph_cursor, *ph_bucket, *ph_sorted, *ph_bsum;
     // static field map (nodes == NULL until obem_fieldmap_build)
     FieldMapDev fm;
+    // charging-up: binary32 vertices, uniform grid over the cells, cell
+    // areas, charges deposited per cell (units of e) and per-step hits
+    float *d_tri9;
+    int32_t *d_hstart, *d_htri;
+    float h_hlo[3], h_hinv;
+    int h_hdim[3];
+    double *d_area;
+    long long *d_deposit;
+    int32_t *s_hit;
     // approximate N-body: bounding box, cell of each charge, cell counts /
     // starts / cursors, charges sorted by cell, per-cell charge centres
     int *nn_bbox;
@@ -234,6 +249,7 @@ int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s);
 // step.cu
 int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,
                      obem_step_stats *stats, cudaStream_t s);
+int obem_launch_surface_sigma(obem_ctx *ctx, float *sigma_free, cudaStream_t s);
 
 // bem.cu
 int obem_assemble_and_factor(obem_ctx *ctx, int precision, cudaStream_t s);

@@ -156,6 +156,7 @@ __device__ __forceinline__ float nu_proc(const GasDev &g, int j, float eps, floa
 // ------------------------------------------------------------------ one charge
 struct FlightOut {
     int dead, attached, nsp, collisions, trials, overflow;
+    int hit_cell;         // cell that absorbed the charge, or -1
 };
 
 // One collision trial at the charge's current state: with x uniform in
@@ -256,6 +257,57 @@ __device__ int collide(const GasDev &g, uint32_t id, uint32_t step, uint32_t k, 
     return 1;
 }
 
+// First cell crossed by the segment a -> b (the chord of one sub-flight), by
+// the Moller-Trumbore test in binary32 with the oracle's operation order
+// (this file is compiled without contraction): edges e1 = v1 - v0,
+// e2 = v2 - v0, d = b - a, h = d x e2, det = e1.h (0: no hit), s = a - v0,
+// u = (s.h)/det in [0, 1], q = s x e1, v = (d.q)/det >= 0 with u + v <= 1,
+// t = (e2.q)/det in [0, 1]; smallest t, ties to the lower cell index.  Only
+// the cells listed in the grid cells the segment's bounding box touches are
+// tested (every cell is listed in all grid cells its own box touches, plus
+// one on every side).  Returns the cell or -1.
+__device__ int seg_hit(const GasDev &g, float3 a, float3 b)
+{
+    int lo[3], hi[3];
+    const float mn[3] = {fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z)};
+    const float mx[3] = {fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float t0 = (mn[k] - g.hlo[k]) * g.hinv, t1 = (mx[k] - g.hlo[k]) * g.hinv;
+        if (!(t1 >= -1.0f) || !(t0 <= (float)g.hdim[k])) return -1;   // outside the grid (or NaN)
+        lo[k] = max(0, min(g.hdim[k] - 1, (int)floorf(t0)));
+        hi[k] = max(0, min(g.hdim[k] - 1, (int)floorf(t1)));
+    }
+    const float d0 = b.x - a.x, d1 = b.y - a.y, d2 = b.z - a.z;
+    int best = -1;
+    float bt = 0.0f;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                const int q = (z * g.hdim[1] + y) * g.hdim[0] + x;
+                for (int m = g.hstart[q]; m < g.hstart[q + 1]; ++m) {
+                    const int k = g.htri[m];
+                    const float *v = g.tri9 + 9 * (size_t)k;
+                    const float e10 = v[3] - v[0], e11 = v[4] - v[1], e12 = v[5] - v[2];
+                    const float e20 = v[6] - v[0], e21 = v[7] - v[1], e22 = v[8] - v[2];
+                    const float h0 = d1 * e22 - d2 * e21, h1 = d2 * e20 - d0 * e22, h2 = d0 * e21 - d1 * e20;
+                    const float det = e10 * h0 + e11 * h1 + e12 * h2;
+                    if (det == 0.0f) continue;
+                    const float inv = 1.0f / det;
+                    const float s0 = a.x - v[0], s1 = a.y - v[1], s2 = a.z - v[2];
+                    const float u = (s0 * h0 + s1 * h1 + s2 * h2) * inv;
+                    if (!(u >= 0.0f && u <= 1.0f)) continue;
+                    const float q0 = s1 * e12 - s2 * e11, q1 = s2 * e10 - s0 * e12, q2 = s0 * e11 - s1 * e10;
+                    const float w = (d0 * q0 + d1 * q1 + d2 * q2) * inv;
+                    if (!(w >= 0.0f && u + w <= 1.0f)) continue;
+                    const float t = (e20 * q0 + e21 * q1 + e22 * q2) * inv;
+                    if (!(t >= 0.0f && t <= 1.0f)) continue;
+                    if (best < 0 || t < bt || (t == bt && k < best)) { best = k; bt = t; }
+                }
+            }
+    return best;
+}
+
 // ballistic flight for time fl under acceleration a (half a in h); returns
 // true when the charge crossed an absorbing plane
 __device__ __forceinline__ bool flight(const GasDev &g, float3 &p, float3 &v, float ax, float ay, float az,
@@ -279,7 +331,9 @@ __device__ __forceinline__ bool flight(const GasDev &g, float3 &p, float3 &v, fl
 // probability nu_j(eps)/nu_max (coll_mode 0); or the paper's per-step scheme
 // (coll_mode 1): flight over the whole step, then one interaction when
 // -ln(U) < nu_tot(eps) dt, of type j with probability nu_j/nu_tot.
-// Ionisation products at the distance of Eq. (distIoni).  When EMIT is set,
+// Ionisation products at the distance of Eq. (distIoni).  A charge is
+// absorbed where a sub-flight's chord crosses a cell (g.hit_on: charging-up)
+// or where it ends beyond a plane z_lo / z_hi.  When EMIT is set,
 // spawned pairs are written to o_* at slots sbase, sbase+1...
 template <bool EMIT>
 __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, float3 &v, uint8_t &sp,
@@ -291,7 +345,10 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
     const float ax = qm * E.x, ay = qm * E.y, az = qm * E.z;
     const float hx = 0.5f * ax, hy = 0.5f * ay, hz = 0.5f * az;
     if (g.coll_mode == 1) {
-        if (flight(g, p, v, ax, ay, az, hx, hy, hz, g.dt)) { fo.dead = 1; return; }
+        const float3 p0 = p;
+        const bool crossed = flight(g, p, v, ax, ay, az, hx, hy, hz, g.dt);
+        if (g.hit_on && (fo.hit_cell = seg_hit(g, p0, p)) >= 0) { fo.dead = 1; return; }
+        if (crossed) { fo.dead = 1; return; }
         const uint4 r = philox4x32_10(make_uint4(id, step, 1u, 0u), g.seed_lo, g.seed_hi);
         fo.trials += 1;
         float nu_tot;
@@ -330,7 +387,10 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
         }
         float tn = t + tau;
         float fl = (tn >= g.dt) ? (g.dt - t) : tau;
-        if (flight(g, p, v, ax, ay, az, hx, hy, hz, fl)) { fo.dead = 1; return; }
+        const float3 p0 = p;
+        const bool crossed = flight(g, p, v, ax, ay, az, hx, hy, hz, fl);
+        if (g.hit_on && (fo.hit_cell = seg_hit(g, p0, p)) >= 0) { fo.dead = 1; return; }
+        if (crossed) { fo.dead = 1; return; }
         if (tn >= g.dt) return;
         t = tn;
         fo.trials += 1;
@@ -535,12 +595,13 @@ __device__ __forceinline__ T block_sum(T v, T *sh)
 __global__ void __launch_bounds__(ST_THREADS)
 count_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, const u64 *prop,
              const u64 *ionkey, int32_t *keep, int32_t *nsp, int32_t *blk, obem_step_stats *stats,
-             StepCtl *ctl)
+             StepCtl *ctl, int32_t *s_hit)
 {
     __shared__ long long sh[ST_THREADS / 32];
     const int n = cur_n(st);
     int i = blockIdx.x * ST_THREADS + threadIdx.x;
     int kp = 0, ns = 0, absorbed = 0, attached = 0, coll = 0, rec = 0, ovf = 0;
+    int hit = -1;
     long long trials = 0;
     if (i < n) {
         uint8_t s = st.species[i];
@@ -551,9 +612,10 @@ count_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, cons
             float4 vv = reinterpret_cast<const float4 *>(st.vel)[i];
             float4 e = E[i];
             float3 p = make_float3(pq.x, pq.y, pq.z), v = make_float3(vv.x, vv.y, vv.z);
-            FlightOut fo = {0, 0, 0, 0, 0, 0};
+            FlightOut fo = {0, 0, 0, 0, 0, 0, -1};
             fly<false>(g, st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, NULL, NULL, NULL,
                        NULL, NULL, 0, 0u);
+            if (g.hit_on) hit = fo.hit_cell >= 0 ? (fo.hit_cell << 1) | (pq.w > 0.0f ? 1 : 0) : -1;
             kp = !fo.dead;
             ns = fo.nsp;
             absorbed = fo.dead;
@@ -564,6 +626,7 @@ count_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, cons
         }
         keep[i] = kp;
         nsp[i] = ns;
+        if (g.hit_on) s_hit[i] = hit;
     }
     long long t;
     t = block_sum<long long>(kp, sh);
@@ -667,7 +730,7 @@ write_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, cons
     float4 vv = reinterpret_cast<const float4 *>(st.vel)[i];
     float4 e = E[i];
     float3 p = make_float3(pq.x, pq.y, pq.z), v = make_float3(vv.x, vv.y, vv.z);
-    FlightOut fo = {0, 0, 0, 0, 0, 0};
+    FlightOut fo = {0, 0, 0, 0, 0, 0, -1};
     const int sbase = ctl->n_keep + 2 * out_spawn;
     const uint32_t id_base = *st.next_id + (uint32_t)(2 * out_spawn);
     fly<true>(g, st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, o_pos, o_vel, o_id, o_birth,
@@ -701,6 +764,36 @@ __global__ void finish_kernel(const obem_state st, const StepCtl *ctl)
     if (threadIdx.x != 0 || ctl->abort) return;
     *st.n = ctl->n_keep + 2 * ctl->n_spawn;
     *st.next_id = *st.next_id + (uint32_t)(2 * ctl->n_spawn);
+}
+
+// charges absorbed by cells this step: deposits[cell] += +-1 (units of e),
+// only when the step commits (run before the count of charges is updated)
+__global__ void deposit_kernel(const obem_state st, const StepCtl *ctl, const int32_t *s_hit,
+                               unsigned long long *deposit)
+{
+    if (ctl->abort) return;
+    const int n = cur_n(st);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t h = s_hit[i];
+    if (h >= 0) atomicAdd(&deposit[h >> 1], (h & 1) ? 1ull : ~0ull);   // +1 or -1 (two's complement)
+}
+
+// free surface density of Eq. (charge-up): e * deposits / area on dielectric
+// cells, 0 on electrode cells
+__global__ void surface_sigma_kernel(const long long *deposit, const double *area, const int *kind, int np,
+                                     float *sigma_free)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    sigma_free[i] = kind[i] == OBEM_CELL_DIELECTRIC ? (float)(OBEM_QE * (double)deposit[i] / area[i]) : 0.0f;
+}
+
+int obem_launch_surface_sigma(obem_ctx *c, float *sigma_free, cudaStream_t s)
+{
+    surface_sigma_kernel<<<(c->np + 255) / 256, 256, 0, s>>>(c->d_deposit, c->d_area, c->d_kind, c->np, sigma_free);
+    OBEM_LAUNCH(c);
+    return OBEM_OK;
 }
 
 __global__ void __launch_bounds__(ST_THREADS)
@@ -748,6 +841,14 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
     const int cap = st.capacity;
     const int nblk = (cap + ST_THREADS - 1) / ST_THREADS;
     GasDev g = c->gas;
+    g.hit_on = (c->cfg.flags & OBEM_STEP_SURFACE_HITS) && c->np > 0 && c->d_tri9;
+    if (g.hit_on) {
+        g.tri9 = c->d_tri9;
+        g.hstart = c->d_hstart;
+        g.htri = c->d_htri;
+        for (int k = 0; k < 3; ++k) { g.hlo[k] = c->h_hlo[k]; g.hdim[k] = c->h_hdim[k]; }
+        g.hinv = c->h_hinv;
+    }
     init_kernel<<<1, 32, 0, s>>>(stats, c->s_ctl, st);
     OBEM_LAUNCH(c);
     if (g.recomb_on) {
@@ -769,7 +870,7 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
         OBEM_LAUNCH(c);
     }
     count_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, E, step, c->s_prop, c->s_ionkey, c->s_keep,
-                                             c->s_nsp, c->s_blk, stats, c->s_ctl);
+                                             c->s_nsp, c->s_blk, stats, c->s_ctl, c->s_hit);
     OBEM_LAUNCH(c);
     scan_kernel<<<1, 1024, 0, s>>>(st, c->s_blk, stats, c->s_ctl, cap < c->cap ? cap : c->cap);
     OBEM_LAUNCH(c);
@@ -780,10 +881,14 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
     commit_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_ctl, c->o_pos, c->o_vel, c->o_id, c->o_birth,
                                               c->o_sp);
     OBEM_LAUNCH(c);
+    if (g.hit_on) {
+        deposit_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_ctl, c->s_hit, (unsigned long long *)c->d_deposit);
+        OBEM_LAUNCH(c);
+    }
     finish_kernel<<<1, 32, 0, s>>>(st, c->s_ctl);
     OBEM_LAUNCH(c);
     moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats);
     OBEM_LAUNCH(c);
-    if (c->prof_on) c->launches += 8 + (g.recomb_on ? 7 : 0);
+    if (c->prof_on) c->launches += 8 + (g.recomb_on ? 7 : 0) + (g.hit_on ? 1 : 0);
     return OBEM_OK;
 }

@@ -434,6 +434,7 @@ class Tracking:
     trial_cap: int = 256
     softening: float = 1e-9     # Plummer length for the N-body field in the dynamics
     coll_mode: int = 0          # 0: null-collision trials; 1: the paper's per-step probability
+    surface_hits: bool = False  # cells absorb the charges crossing them (charging-up)
 
 
 # --------------------------------------------------------------------------

@@ -20,7 +20,7 @@ OBEM_ERR_ARG, OBEM_ERR_CUDA, OBEM_ERR_STATE, OBEM_ERR_SINGULAR = -1, -2, -3, -4
 OBEM_ERR_NOT_CONVERGED, OBEM_ERR_CAPACITY, OBEM_ERR_TIMEOUT, OBEM_ERR_TRIALS = -5, -6, -7, -8
 OBEM_LU_FP32, OBEM_LU_TF32, OBEM_LU_BF16, OBEM_LU_BF16X9 = 0, 1, 2, 3
 OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD, OBEM_STEP_FIELD_MAP, OBEM_STEP_PROB_COLLISION = 1, 2, 4, 8
-OBEM_STEP_NBODY_NN, OBEM_NN_GMAX = 16, 64
+OBEM_STEP_NBODY_NN, OBEM_NN_GMAX, OBEM_STEP_SURFACE_HITS = 16, 64, 32
 
 
 class ObemError(RuntimeError):
@@ -100,12 +100,13 @@ def load():
     lib.obem_alu_rates.argtypes = [P, P, P]
     lib.obem_fieldmap_build.argtypes = [P, P, P, P, P, P]
     lib.obem_nbody_nn_eval.argtypes = [P, P, I, I, C.c_double, P, P]
+    lib.obem_surface_charge.argtypes = [P, P, P, I, P]
     lib.obem_fieldmap_eval.argtypes = [P, P, I, P, P]
     lib.obem_stage_times.argtypes = [P, P, P]
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
               "obem_bem_solve", "obem_bem_solve_adjoint", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
               "obem_stage_times", "obem_alu_rates", "obem_fieldmap_build", "obem_fieldmap_eval",
-              "obem_nbody_nn_eval"):
+              "obem_nbody_nn_eval", "obem_surface_charge"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -347,6 +348,15 @@ def obem_nbody_nn_eval(ctx, pos_q, E_out, grid, softening=0.0, stream=None):
     """Approximate N-body field at the charges (see include/obem.h)."""
     _check(ctx, load().obem_nbody_nn_eval(ctx, _ptr(pos_q), pos_q.shape[0], int(grid), float(softening),
                                           _ptr(E_out), _stream(stream)))
+
+
+def obem_surface_charge(ctx, n_panels, sigma_free=None, reset=False, stream=None):
+    """Charges collected by the cells (units of e, int64 numpy [n_panels]);
+    writes e * count / area of the dielectric cells into sigma_free if given."""
+    counts = np.zeros(int(n_panels), np.int64)
+    _check(ctx, load().obem_surface_charge(ctx, _ptr(sigma_free), counts.ctypes.data_as(C.c_void_p),
+                                           int(bool(reset)), _stream(stream)))
+    return counts
 
 
 def obem_profile(ctx, enable=True):

@@ -573,3 +573,53 @@ def test_nn_far_cells_are_exact_for_point_like_cells():
     exact = oracle.nbody_field(src[:, :3], src, True, 0.0)[0]
     nn = oracle.nbody_nn(src, 2 * K - 1, 0.0)      # cell edge 8h/9: site i in cell floor(2.25 i)
     assert np.abs(nn - exact).max() <= 1e-12 * np.abs(exact).max()
+
+
+# ----------------------------------------------------------------------------
+# charging-up: cells absorb the charges crossing them (Eq. (charge-up))
+# ----------------------------------------------------------------------------
+def test_surface_hits_absorb_at_the_crossed_cell_and_count_deposits():
+    """Two dielectric cells forming the square [0, 1 mm]^2 at z = 0, no field,
+    no collisions: a charge whose step carries it through the square is
+    absorbed by the cell that contains the exact (FP64) crossing point; one
+    that stops short, or passes beside the square, survives; deposits count
+    e per charge with its sign."""
+    L = 1e-3
+    tri = np.array([[[0, 0, 0], [L, 0, 0], [L, L, 0]], [[0, 0, 0], [L, L, 0], [0, L, 0]]], np.float64)
+    mesh = inputs.Mesh(tri, np.array([1, 1], np.int32), np.array([-1, -1], np.int32), np.ones(2), np.full(2, 3.5),
+                       np.zeros(0))
+    gas = inputs.maxwell_gas(0.0, 40.0)
+    gas.nuc[:] = 0.0
+    gas.nu_ion = 0.0
+    trk = inputs.Tracking(dt=1e-12, seed=1, z_lo=-1.0, z_hi=1.0, beta=-1.0, surface_hits=True)
+    rng = np.random.default_rng(3)
+    n = 400
+    xy = rng.uniform(-0.2 * L, 1.2 * L, (n, 2))
+    z0 = rng.uniform(1e-7, 3e-6, n)
+    vz = -rng.uniform(1e5, 2e6, n)                 # displacement 1e-7 .. 2e-6 m in one step
+    pos = np.column_stack([xy, z0])
+    vel = np.column_stack([np.zeros((n, 2)), vz])
+    sp = rng.integers(0, 2, n).astype(np.uint8)
+    ch = inputs.make_charges(pos, vel, sp)
+    dep = np.zeros(2, np.int64)
+    st, out, _, stats = oracle.step(ch, np.zeros((n, 3), np.float32), 0, n, gas, trk, n + 16, mesh=mesh, deposits=dep)
+    assert st == 0
+    p32 = ch.pos_q[:, :3].astype(np.float64)
+    v32 = ch.vel[:, :3].astype(np.float64)
+    z_end = p32[:, 2] + v32[:, 2] * trk.dt
+    inside = (p32[:, 0] >= 0) & (p32[:, 0] <= L) & (p32[:, 1] >= 0) & (p32[:, 1] <= L)
+    reach = z_end <= 0.0
+    margin = (np.minimum.reduce([p32[:, 0], L - p32[:, 0], p32[:, 1], L - p32[:, 1]]) > 1e-9) & \
+             (np.abs(z_end) > 1e-12)
+    absorbed = ~np.isin(ch.id, out.id)
+    sure = margin & (np.abs(p32[:, 0] - p32[:, 1]) > 1e-9)
+    assert np.array_equal(absorbed[sure], (inside & reach)[sure])
+    assert stats["absorbed"] == absorbed.sum()
+    # which cell: x > y lies in cell 0, x < y in cell 1
+    q = np.where(sp == 1, 1, -1)
+    hit = absorbed & sure
+    exp0 = q[hit & (p32[:, 0] > p32[:, 1])].sum()
+    exp1 = q[hit & (p32[:, 0] < p32[:, 1])].sum()
+    on_edge = absorbed & ~sure
+    assert dep.sum() == q[absorbed].sum()
+    assert abs(dep[0] - exp0) + abs(dep[1] - exp1) <= np.abs(q[on_edge]).sum()
