@@ -111,7 +111,7 @@ __global__ void bin_scan_kernel(int32_t *hist)
     }
 }
 
-// Blocks of the cell kernels: the targets of one super-bin (2 x 2 x 2 bins,
+// Blocks of the cell kernels: the targets of one super-bin (4 x 4 x 4 bins,
 // contiguous in the sorted order) are cut into blocks of at most CT_BLOCK_N,
 // so a block never spans distant bins.  One block of 1024 threads; reads the
 // scanned histogram (bin start offsets) before the scatter advances it.
@@ -121,8 +121,9 @@ __global__ void block_list_kernel(const int32_t *start, int nt_host, const int32
 {
     __shared__ int32_t part[1024];
     const int nt = nt_dev ? *nt_dev : nt_host;
-    const int per = OBEM_NSUPER / 1024;
-    int cnt[OBEM_NSUPER / 1024];
+    constexpr int PER = OBEM_NSUPER >= 1024 ? OBEM_NSUPER / 1024 : 1;
+    const int per = OBEM_NSUPER >= 1024 ? PER : (threadIdx.x < OBEM_NSUPER ? 1 : 0);
+    int cnt[PER];
     int32_t s = 0;
     for (int q = 0; q < per; ++q) {
         const int sb = threadIdx.x * per + q;

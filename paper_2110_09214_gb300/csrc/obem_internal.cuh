@@ -216,7 +216,7 @@ struct FieldLaunch {
 };
 #define OBEM_BINS_PER_AXIS 64
 #define OBEM_NBINS (OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS)
-#define OBEM_SUPER_SHIFT 3                        // super-bin = 2 x 2 x 2 bins
+#define OBEM_SUPER_SHIFT 6                        // super-bin = 4 x 4 x 4 bins
 #define OBEM_NSUPER (OBEM_NBINS >> OBEM_SUPER_SHIFT)
 int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets, cudaStream_t s);
 size_t obem_sym_jpart_floats(int capacity);
