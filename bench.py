@@ -246,6 +246,7 @@ def run_ours(a, ws, rank, local):
     st.upload(ch)
     n_start = int((ch.species == 0).sum())
     stats = [obem.new_stats() for _ in range(max(a.steps, a.warmup) + 1)]
+    stats_c = obem.new_stats()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     step = 0
     for _ in range(a.warmup):
@@ -261,7 +262,7 @@ def run_ours(a, ws, rank, local):
     # each timed step is one pass over the 1e6-charge workload
     snap = {k: getattr(st, k).clone() for k in ("pos_q", "vel", "id", "birth", "species", "scalars")}
     clocks = Clocks(local)
-    obem.obem_profile(ctx, True)
+    obem.obem_profile(ctx, obem.OBEM_PROFILE_TIMES)      # stage events; uncounted kernels
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -281,7 +282,16 @@ def run_ours(a, ws, rank, local):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     prof = obem.obem_stage_times(ctx)
+    # evaluation counts: one more pass over the same snapshot (untimed), in
+    # the counting kernels; every timed step did the same evaluations
+    for key, v in snap.items():
+        getattr(st, key).copy_(v)
+    obem.obem_profile(ctx, True)
+    obem.obem_step(ctx, st, step, stats_c)
+    cnt = obem.obem_stage_times(ctx)
     obem.obem_profile(ctx, False)
+    for key in ("charge_pairs", "cells_1pt", "cells_3pt", "cells_7pt", "cells_closed"):
+        prof[key] = cnt[key] * a.steps
     sts = [obem.read_stats(stats[k]) for k in range(a.steps)]
     for s_ in sts:
         assert s_["status"] == 0, "timed step failed: %s" % s_

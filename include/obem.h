@@ -328,7 +328,10 @@ int obem_alu_rates(obem_ctx *ctx, double *out, obem_stream stream);
 
 /* Stage timing of obem_step, for measurement (not part of the method).
  * obem_profile(ctx, 1) starts recording CUDA events on the step's stream
- * around its stages (up to 256 steps are kept; older ones are dropped);
+ * around its stages (up to 256 steps are kept; older ones are dropped) and
+ * counting the evaluations below (the cell kernels then run in their counting
+ * variants, a few per cent slower); obem_profile(ctx, OBEM_PROFILE_TIMES)
+ * records the events only (counts[2..6] stay 0);
  * obem_stage_times() waits for the recorded events and returns, summed over
  * the recorded steps:
  *   ms[0] cell field (binning + near + far kernels), ms[1] all-pairs field
@@ -338,6 +341,7 @@ int obem_alu_rates(obem_ctx *ctx, double *out, obem_stream stream);
  *   counts[2] charge pairs of the all-pairs kernel,
  *   counts[3..6] cell evaluations by tier (centroid, 3-point, 7-point, closed form).
  * Recording is then reset.  obem_profile(ctx, 0) stops recording. */
+#define OBEM_PROFILE_TIMES 2
 int obem_profile(obem_ctx *ctx, int32_t enable);
 int obem_stage_times(obem_ctx *ctx, double *ms /* [5] */, int64_t *counts /* [7] */);
 

@@ -274,16 +274,13 @@ __device__ __forceinline__ bool cell_is_near(float4 ca, float h2, const BlockFra
     return box_d2(ca.x, ca.y, ca.z, F.lo, F.hi) < TIER_28PT_H2 * h2 || h2 < (FRAME_H * FRAME_H) * F.scale2;
 }
 
-// FP64 closed form of one cell, added into P
-__device__ __noinline__ void closed_into(const double *v, float tx, float ty, float tz, float sg, float *P)
+// FP64 closed form of one cell at one target, times k_C sigma (FP32 result)
+__device__ __noinline__ float4 closed_val(const double *v, float tx, float ty, float tz, float sg)
 {
     double phi, Fx, Fy, Fz;
     tri_closed_form(v, (double)tx, (double)ty, (double)tz, phi, Fx, Fy, Fz);
     const double kq = OBEM_KC * (double)sg;
-    P[0] += (float)(kq * Fx);
-    P[1] += (float)(kq * Fy);
-    P[2] += (float)(kq * Fz);
-    P[3] += (float)(kq * phi);
+    return make_float4((float)(kq * Fx), (float)(kq * Fy), (float)(kq * Fz), (float)(kq * phi));
 }
 
 // deterministic compaction of the near cells of [pb, pb + NEAR_CHUNK) into list
@@ -311,13 +308,43 @@ __device__ __forceinline__ void diff_exact(float t, float chi, float clo, float 
     d = (t - chi) - clo;
 }
 
-// near cells, targets within h of them: FP64 closed form; E_out = e_ext + that
+// near cells, targets within h of them: FP64 closed form; E_out = e_ext + that.
+// Few targets of a warp lie within h of a given cell, and a warp-wide FP64
+// instruction costs the same with one lane active as with 32, so the (target,
+// cell) pairs are queued per warp and evaluated 32 at a time.  Queue order is
+// (cell, target slot, lane) and each lane adds its results in queue order:
+// the sums are deterministic.
+#define NC_Q 64                     // per-warp queue (< 32 left after a flush, + 32 appended)
+__device__ __forceinline__ void nc_flush(const FieldLaunch &L, int n, const float4 *qp, const int *qt, float4 *res,
+                                         float (*P)[4])
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        const float4 e = qp[lane];
+        const int j = __float_as_int(e.w);
+        res[lane] = closed_val(L.panels.v64 + 9 * (size_t)j, e.x, e.y, e.z, L.sigma[j]);
+    }
+    __syncwarp();
+    for (int e = 0; e < n; ++e) {
+        const int t = qt[e];
+        if ((t & 31) != lane) continue;
+        const float4 r = res[e];
+#pragma unroll
+        for (int k = 0; k < CT_TPT; ++k)
+            if ((t >> 5) == k) { P[k][0] += r.x; P[k][1] += r.y; P[k][2] += r.z; P[k][3] += r.w; }
+    }
+    __syncwarp();
+}
+
 template <bool WANT_V, bool COUNT>
 __global__ void __launch_bounds__(CT_THREADS)
 near_closed_kernel(FieldLaunch L)
 {
     __shared__ int s_list[NEAR_CHUNK];
     __shared__ int s_cnt[CT_THREADS / 32];
+    __shared__ float4 s_qp[CT_THREADS / 32][NC_Q];     // target position, cell index (bits)
+    __shared__ int s_qt[CT_THREADS / 32][NC_Q];        // target slot << 5 | owner lane
+    __shared__ float4 s_res[CT_THREADS / 32][32];
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
     int base, end;
     if (!block_range(L, nt, base, end)) return;
@@ -325,35 +352,55 @@ near_closed_kernel(FieldLaunch L)
     int ti[CT_TPT];
     BlockFrame F;
     block_targets(L, end, base, tx, ty, tz, ti, F);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *qp = s_qp[warp], *res = s_res[warp];
+    int *qt = s_qt[warp];
     // warps whose target slots are all padding skip the arithmetic
     const bool warp_live = base + (int)(threadIdx.x & ~31u) < end;
-    float S[CT_TPT][4], C[CT_TPT][4];
+    float S[CT_TPT][4], C[CT_TPT][4], P[CT_TPT][4];
 #pragma unroll
     for (int k = 0; k < CT_TPT; ++k)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) { S[k][c] = 0.f; C[k][c] = 0.f; }
+        for (int c = 0; c < 4; ++c) { S[k][c] = 0.f; C[k][c] = 0.f; P[k][c] = 0.f; }
     unsigned long long cntA = 0;
+    int nq = 0;                                         // queued pairs (warp-uniform)
     for (int pb = 0; pb < L.panels.np; pb += NEAR_CHUNK) {
         const int tot = near_list(L, pb, F, s_list, s_cnt);
         if (tot == 0) continue;
-        float P[CT_TPT][4];
-#pragma unroll
-        for (int k = 0; k < CT_TPT; ++k) { P[k][0] = P[k][1] = P[k][2] = P[k][3] = 0.f; }
         for (int q = 0; q < (warp_live ? tot : 0); ++q) {
             const int j = s_list[q];
             const float4 ca = L.panels.c_a[j], cl = L.panels.c_lo[j];
             const float h2 = L.panels.g0_h[j].w;
 #pragma unroll
             for (int k = 0; k < CT_TPT; ++k) {
-                if (ti[k] < 0) continue;
                 float dx, dy, dz;
                 diff_exact(tx[k], ca.x, cl.x, dx); diff_exact(ty[k], ca.y, cl.y, dy); diff_exact(tz[k], ca.z, cl.z, dz);
-                if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < h2) {
-                    closed_into(L.panels.v64 + 9 * (size_t)j, tx[k], ty[k], tz[k], L.sigma[j], P[k]);
+                const bool hit = ti[k] >= 0 && fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < h2;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (bal == 0u) continue;
+                if (hit) {
+                    const int e = nq + __popc(bal & ((1u << lane) - 1u));
+                    qp[e] = make_float4(tx[k], ty[k], tz[k], __int_as_float(j));
+                    qt[e] = (k << 5) | lane;
                     if (COUNT) ++cntA;
+                }
+                nq += __popc(bal);
+                __syncwarp();
+                if (nq >= 32) {
+                    nc_flush(L, 32, qp, qt, res, P);
+                    nq -= 32;
+                    if (lane < nq) { qp[lane] = qp[32 + lane]; qt[lane] = qt[32 + lane]; }
+                    __syncwarp();
                 }
             }
         }
+#pragma unroll
+        for (int k = 0; k < CT_TPT; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { two_sum_acc(S[k][c], C[k][c], P[k][c]); P[k][c] = 0.f; }
+    }
+    if (nq > 0) {
+        nc_flush(L, nq, qp, qt, res, P);
 #pragma unroll
         for (int k = 0; k < CT_TPT; ++k)
 #pragma unroll

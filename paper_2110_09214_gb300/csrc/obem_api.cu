@@ -181,7 +181,7 @@ extern "C" int obem_profile(obem_ctx *c, int32_t enable)
         c->launches = 0;
         c->steps_recorded = 0;
     }
-    c->prof_on = enable ? 1 : 0;
+    c->prof_on = enable == OBEM_PROFILE_TIMES ? OBEM_PROFILE_TIMES : (enable ? 1 : 0);
     return OBEM_OK;
 }
 
@@ -736,7 +736,7 @@ extern "C" int obem_step(obem_ctx *c, const obem_state *st, const float *E_in, u
         L.add_init = want_map;
         L.nn_grid = (c->cfg.flags & OBEM_STEP_NBODY_NN) ? (c->cfg.nn_grid > 0 ? c->cfg.nn_grid : 16) : 0;
         L.want_v = 0;
-        if (ev) L.counters = c->d_counters;
+        if (ev && c->prof_on == 1) L.counters = c->d_counters;     // tier counters (counting kernels)
         L.events = ev;
         int rc = obem_launch_field(c, L, st->capacity, s);
         if (rc != OBEM_OK) return rc;

@@ -359,8 +359,14 @@ def obem_surface_charge(ctx, n_panels, sigma_free=None, reset=False, stream=None
     return counts
 
 
+OBEM_PROFILE_TIMES = 2
+
+
 def obem_profile(ctx, enable=True):
-    _check(ctx, load().obem_profile(ctx, int(bool(enable))))
+    """True: stage events and evaluation counters; OBEM_PROFILE_TIMES: stage
+    events only (the uncounted kernels run); False: off."""
+    mode = OBEM_PROFILE_TIMES if (enable is not True and enable == OBEM_PROFILE_TIMES) else int(bool(enable))
+    _check(ctx, load().obem_profile(ctx, mode))
 
 
 def obem_stage_times(ctx):
