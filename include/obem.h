@@ -314,7 +314,7 @@ int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t s
 
 /* Measured ALU rates of the context's GPU, for the roofline of the FP32-bound
  * field kernels (not part of the method).  Runs dependent-chain kernels on
- * every SM for a few milliseconds each and writes out[6] (host):
+ * every SM for a few milliseconds each and writes out[7] (host):
  *   out[0] FP32 TFLOP/s of packed f32x2 FMA chains (2 flops per lane-op),
  *   out[1] FP32 lane-operations per SM per clock (same run),
  *   out[2] rsqrt.approx per SM per clock,
@@ -322,7 +322,9 @@ int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t s
  *          one rsqrt (the one-sided all-pairs kernel's mix),
  *   out[4] the SM clock during the FMA run (MHz),
  *   out[5] the same as out[3] for sixteen lane-operations per rsqrt (the
- *          symmetric all-pairs kernel's mix).
+ *          symmetric all-pairs kernel's mix),
+ *   out[6] the same for fourteen (the symmetric kernel on tiles of one charge
+ *          value).
  * Allocates scratch and synchronises `stream`. */
 int obem_alu_rates(obem_ctx *ctx, double *out, obem_stream stream);
 

@@ -939,9 +939,98 @@ __host__ __device__ constexpr size_t sym_smem(int nc)
     return (size_t)2 * nc * SY_NI * SY_THREADS * 4 + (size_t)2 * nc * SY_T * 4;
 }
 
+// The kernel runs on a copy of the charges ordered by charge value: negative
+// charges first, each class in index order (a stable partition).  Then every
+// tile but the one holding the boundary (and the padded last tile) has one
+// charge value, and for a pair of such tiles the charges factor out of the
+// sums: the inner loop accumulates inv^3 d and the tile's k_C q multiplies the
+// sums once (two multiplications fewer per pair).
+#define SP_BLOCK 1024
+int obem_sym_part_blocks(int capacity) { return (capacity + SP_BLOCK - 1) / SP_BLOCK; }
+int obem_sym_tiles(int capacity) { return sym_geom(capacity).n; }
+
+// negative charges per block of SP_BLOCK slots
+__global__ void sym_part_count_kernel(const float4 *src, int nt, const int32_t *nt_dev, int32_t *bcnt)
+{
+    const int n = nt_dev ? *nt_dev : nt;
+    const int i = blockIdx.x * SP_BLOCK + threadIdx.x;
+    const int c = __syncthreads_count(i < n && src[i].w < 0.f);
+    if (threadIdx.x == 0) bcnt[blockIdx.x] = c;
+}
+
+// exclusive scan of the nb block counts in place, total in bcnt[nb]; one block of 1024
+__global__ void sym_part_scan_kernel(int32_t *bcnt, int nb)
+{
+    __shared__ int32_t part[1024];
+    const int per = (nb + 1023) / 1024, b0 = threadIdx.x * per;
+    int32_t s = 0;
+    for (int q = 0; q < per; ++q)
+        if (b0 + q < nb) s += bcnt[b0 + q];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - s;
+    for (int q = 0; q < per; ++q)
+        if (b0 + q < nb) {
+            const int32_t c = bcnt[b0 + q];
+            bcnt[b0 + q] = run;
+            run += c;
+        }
+    if (threadIdx.x == 1023) bcnt[nb] = part[1023];
+}
+
+// sorted[dst] = (position of target i, charge of source i), perm[dst] = i
+__global__ void sym_part_scatter_kernel(const float4 *tgt, const float4 *src, int nt, const int32_t *nt_dev,
+                                        const int32_t *bcnt, int nb, float4 *sorted, int32_t *perm)
+{
+    __shared__ int32_t wneg[SP_BLOCK / 32];
+    const int n = nt_dev ? *nt_dev : nt;
+    const int i = blockIdx.x * SP_BLOCK + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    float q = 0.f;
+    if (i < n) { p = tgt[i]; q = src[i].w; }
+    const bool neg = i < n && q < 0.f;
+    const unsigned bal = __ballot_sync(0xffffffffu, neg);
+    if (lane == 0) wneg[warp] = __popc(bal);
+    __syncthreads();
+    int rneg = __popc(bal & ((1u << lane) - 1u));        // negative charges before i in the block
+    for (int w = 0; w < warp; ++w) rneg += wneg[w];
+    if (i < n) {
+        const int negoff = bcnt[blockIdx.x];
+        const int dst = neg ? negoff + rneg
+                            : bcnt[nb] + (blockIdx.x * SP_BLOCK - negoff) + ((int)threadIdx.x - rneg);
+        sorted[dst] = make_float4(p.x, p.y, p.z, q);
+        perm[dst] = i;
+    }
+}
+
+// per tile of SY_T sorted slots: the common charge, or NaN; slots past n count as 0
+__global__ void sym_tileq_kernel(const float4 *sorted, int nt, const int32_t *nt_dev, float *tileq)
+{
+    const int n = nt_dev ? *nt_dev : nt;
+    const int base = blockIdx.x * SY_T;
+    if (base >= n) return;
+    const float q0 = sorted[base].w;
+    bool same = true;
+    for (int k = threadIdx.x; k < SY_T; k += blockDim.x) {
+        const int i = base + k;
+        same = same && ((i < n ? sorted[i].w : 0.f) == q0);
+    }
+    same = __syncthreads_and(same);
+    if (threadIdx.x == 0) tileq[blockIdx.x] = same ? q0 : __int_as_float(0x7fc00000);
+}
+
+template <bool B> struct SyBool { static constexpr bool value = B; };
+
 template <bool WANT_V>
 __global__ void __launch_bounds__(SY_THREADS, SY_MINB)
-nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
+nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const float *tileq)
 {
     constexpr int NC = WANT_V ? 4 : 3;
     extern __shared__ __align__(16) unsigned char sy_smem[];
@@ -1058,11 +1147,17 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
             u64 AX[SY_NP], AY[SY_NP], AZ[SY_NP], AV[SY_NP];
 #pragma unroll
             for (int p = 0; p < SY_NP; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
+            // one charge value in each tile: k_C q factored out of the loop
+            const float qJ = tileq[J], qI = tileq[I];
+            const bool uni = qJ == qJ && qI == qI;
+            const float afac = uni ? kC * qJ : 1.f, pfac = uni ? kC * qI : 1.f;
+            auto rounds = [&](auto uni_c) {
+            constexpr bool UNI = decltype(uni_c)::value;
             for (int r = 0; r < SY_NG; ++r) {
                 const int grp = (r + (SY_NG / SY_WARPS) * warp) % SY_NG;   // distinct per warp in a round
                 const int j0 = jb + grp * 32;
                 float4 sj = j0 + lane < nt ? L.sources[j0 + lane] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
-                float jx = sj.x, jy = sj.y, jz = sj.z, jq = kC * sj.w;
+                float jx = sj.x, jy = sj.y, jz = sj.z, jq = UNI ? 0.f : kC * sj.w;
                 float ax = 0.f, ay = 0.f, az = 0.f, av = 0.f;
                 for (int s = 0; s < 32; ++s) {
                     const u64 JX = pk(jx, jx), JY = pk(jy, jy), JZ = pk(jz, jz), JQ = pk(jq, jq);
@@ -1079,8 +1174,8 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                         upk(r2, ra, rb);
                         const u64 inv = pk(rsq(ra), rsq(rb));
                         const u64 inv3 = mul2(mul2(inv, inv), inv);
-                        const u64 si = mul2(JQ, inv3);
-                        const u64 sjp = mul2(QI[p], inv3);
+                        const u64 si = UNI ? inv3 : mul2(JQ, inv3);
+                        const u64 sjp = UNI ? inv3 : mul2(QI[p], inv3);
                         AX[p] = fma2(dx, si, AX[p]);
                         AY[p] = fma2(dy, si, AY[p]);
                         AZ[p] = fma2(dz, si, AZ[p]);
@@ -1088,8 +1183,8 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                         PY = fma2(dy, sjp, PY);
                         PZ = fma2(dz, sjp, PZ);
                         if (WANT_V) {
-                            AV[p] = fma2(JQ, inv, AV[p]);
-                            PV = fma2(QI[p], inv, PV);
+                            AV[p] = UNI ? add2(AV[p], inv) : fma2(JQ, inv, AV[p]);
+                            PV = UNI ? add2(PV, inv) : fma2(QI[p], inv, PV);
                         }
                     }
                     float a, b;
@@ -1102,12 +1197,13 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                     jx = __shfl_sync(0xffffffffu, jx, src);
                     jy = __shfl_sync(0xffffffffu, jy, src);
                     jz = __shfl_sync(0xffffffffu, jz, src);
-                    jq = __shfl_sync(0xffffffffu, jq, src);
+                    if (!UNI) jq = __shfl_sync(0xffffffffu, jq, src);
                     ax = __shfl_sync(0xffffffffu, ax, src);
                     ay = __shfl_sync(0xffffffffu, ay, src);
                     az = __shfl_sync(0xffffffffu, az, src);
                     if (WANT_V) av = __shfl_sync(0xffffffffu, av, src);
                 }
+                if (UNI) { ax *= pfac; ay *= pfac; az *= pfac; av *= pfac; }
                 // after 32 passes the sums are back with their source: add this warp's part
                 {
                     const int jl = grp * 32 + lane;
@@ -1130,6 +1226,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                         float sv, cv;
 #define SY_FOLD1(Acc, c)                                                                   \
     upk(Acc[p], a, b);                                                                     \
+    if (UNI) { a *= afac; b *= afac; }                                                     \
     sv = s_S[c][2 * p][tid]; cv = s_C[c][2 * p][tid]; two_sum_acc(sv, cv, a);              \
     s_S[c][2 * p][tid] = sv; s_C[c][2 * p][tid] = cv;                                      \
     sv = s_S[c][2 * p + 1][tid]; cv = s_C[c][2 * p + 1][tid]; two_sum_acc(sv, cv, b);      \
@@ -1144,6 +1241,9 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
                 }
                 __syncthreads();
             }
+            };
+            if (uni) rounds(SyBool<true>{});
+            else rounds(SyBool<false>{});
             // the item's source-side sums (S + C) to its own slot
             float *jp = jpart + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
             for (int l = tid; l < NC * SY_T; l += SY_THREADS) jp[l] = s_jS[l] + s_jC[l];
@@ -1163,7 +1263,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter)
 // E_out[t] = init + target-side sums of t's row + minus the source-side sums of
 // every item whose second tile holds t, added in a fixed order (FP64).
 template <bool WANT_V>
-__global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float *ipart, int add)
+__global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float *ipart, int add, const int32_t *perm)
 {
     constexpr int NC = WANT_V ? 4 : 3;
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
@@ -1171,9 +1271,10 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
     if (t >= nt) return;
     const SymGeom G = sym_geom(nt);
     const int T = t / SY_T, w = t % SY_T;
+    const int o = perm ? perm[t] : t;                  // sorted slot t is charge o
     double e[4] = {0.0, 0.0, 0.0, 0.0};
     if (add) {
-        const float4 q = L.E_out[t];
+        const float4 q = L.E_out[o];
         e[0] = q.x; e[1] = q.y; e[2] = q.z; e[3] = q.w;
     } else {
         e[0] = L.e_ext.x; e[1] = L.e_ext.y; e[2] = L.e_ext.z;
@@ -1190,7 +1291,7 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
 #pragma unroll
         for (int c = 0; c < NC; ++c) e[c] += (c < 3 ? -1.0 : 1.0) * (double)jp[c * SY_T + w];
     }
-    L.E_out[t] = make_float4((float)e[0], (float)e[1], (float)e[2], WANT_V ? (float)e[3] : 0.f);
+    L.E_out[o] = make_float4((float)e[0], (float)e[1], (float)e[2], WANT_V ? (float)e[3] : 0.f);
 }
 
 // occupancy-limited persistent grid of the symmetric kernel
@@ -1198,7 +1299,7 @@ int obem_sym_grid(int device)
 {
     int sms = 0, best = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    void (*ks[])(FieldLaunch, float *, float *, int *) = {nbsym_kernel<true>, nbsym_kernel<false>};
+    void (*ks[])(FieldLaunch, float *, float *, int *, const float *) = {nbsym_kernel<true>, nbsym_kernel<false>};
     const size_t sm[] = {sym_smem(4), sym_smem(3)};
     for (int q = 0; q < 2; ++q) {
         if (cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]) != cudaSuccess)
@@ -1287,18 +1388,32 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             if (rc != OBEM_OK) return rc;
             if (L.events) ctx->launches += 7;
         } else if (sym) {
+            // charges ordered by charge value (stable), per-tile common charge
+            const int nb = obem_sym_part_blocks(capacity_targets);
+            sym_part_count_kernel<<<nb, SP_BLOCK, 0, s>>>(L.sources, L.nt, L.nt_dev, ctx->sym_bcnt);
+            sym_part_scan_kernel<<<1, 1024, 0, s>>>(ctx->sym_bcnt, nb);
+            sym_part_scatter_kernel<<<nb, SP_BLOCK, 0, s>>>(L.targets, L.sources, L.nt, L.nt_dev, ctx->sym_bcnt, nb,
+                                                           ctx->sym_sorted, ctx->sym_perm);
+            sym_tileq_kernel<<<obem_sym_tiles(capacity_targets), 256, 0, s>>>(ctx->sym_sorted, L.nt, L.nt_dev,
+                                                                             ctx->sym_tileq);
+            OBEM_LAUNCH(ctx);
+            FieldLaunch Ls = L;
+            Ls.targets = ctx->sym_sorted;
+            Ls.sources = ctx->sym_sorted;
             OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
             const dim3 sg(ctx->sym_grid);
             if (L.want_v)
-                nbsym_kernel<true><<<sg, SY_THREADS, sym_smem(4), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
+                nbsym_kernel<true><<<sg, SY_THREADS, sym_smem(4), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
+                                                                      ctx->sym_tileq);
             else
-                nbsym_kernel<false><<<sg, SY_THREADS, sym_smem(3), s>>>(L, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter);
+                nbsym_kernel<false><<<sg, SY_THREADS, sym_smem(3), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
+                                                                       ctx->sym_tileq);
             OBEM_LAUNCH(ctx);
             const int fb = (capacity_targets + 255) / 256;
-            if (L.want_v) nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0);
-            else nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0);
+            if (L.want_v) nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm);
+            else nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm);
             OBEM_LAUNCH(ctx);
-            if (L.events) ctx->launches += 2;
+            if (L.events) ctx->launches += 6;
         } else if (L.want_v) {
             if (add) nbody_kernel<true, true><<<grid, FT_THREADS, 0, s>>>(L);
             else nbody_kernel<true, false><<<grid, FT_THREADS, 0, s>>>(L);

@@ -154,6 +154,10 @@ struct obem_ctx {
     int32_t *nn_cell, *nn_sorted, *nn_count, *nn_start, *nn_cursor;
     float4 *nn_agg;
     int *sym_counter;
+    float4 *sym_sorted;      // charges ordered by charge value (negative first)
+    int32_t *sym_perm;       // sorted slot -> state index
+    int32_t *sym_bcnt;       // per-block counts / offsets of the partition
+    float *sym_tileq;        // per tile: the common charge of its slots, NaN if they differ
     int sym_grid, sym_cap;
     // stage timing (obem_profile)
     int prof_on;
@@ -222,6 +226,8 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
 size_t obem_sym_jpart_floats(int capacity);
 size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);
+int obem_sym_part_blocks(int capacity);
+int obem_sym_tiles(int capacity);
 
 // nn.cu
 int obem_launch_nbody_nn(obem_ctx *c, const float4 *pos, const int32_t *n_dev, int n, int G, float eps2,

@@ -1,7 +1,8 @@
 // Measured ALU rates of this GPU, for the roofline of the FP32-bound field
 // kernels (not part of the method): dependent chains of packed f32x2 FMAs,
 // of rsqrt.approx, and the all-pairs kernels' mixes (twelve FP32 lane-operations
-// per rsqrt one-sided, sixteen per rsqrt symmetric), on every SM at once.  Rates per SM per clock come from the
+// per rsqrt one-sided; sixteen per rsqrt symmetric, fourteen when the tiles'
+// charges factor out), on every SM at once.  Rates per SM per clock come from the
 // blocks' own clock64 spans; the TFLOP/s figure from CUDA events.
 #include "obem_internal.cuh"
 #include "field_common.cuh"
@@ -10,7 +11,7 @@
 #define PK_BLOCKS_PER_SM 4      // 4 x 256 threads x <= 64 registers: one wave
 #define PK_CHAINS 8
 
-template <int MODE>   // 0: packed FMA chains, 1: rsqrt chains, 2 / 3: 6 / 8 packed FMAs (12 / 16 lane-ops) per rsqrt
+template <int MODE>   // 0: packed FMA chains, 1: rsqrt chains, 2 / 3 / 4: 6 / 8 / 7 packed FMAs (12 / 16 / 14 lane-ops) per rsqrt
 __global__ void __launch_bounds__(PK_THREADS, PK_BLOCKS_PER_SM) alu_rate_kernel(int iters, float *sink,
                                                                                long long *cycles)
 {
@@ -32,7 +33,8 @@ __global__ void __launch_bounds__(PK_THREADS, PK_BLOCKS_PER_SM) alu_rate_kernel(
                 if (MODE >= 2) {
                     P[i] = fma2(P[i], m, a); P[i] = fma2(P[i], m, a); P[i] = fma2(P[i], m, a);
                     P[i] = fma2(P[i], m, a); P[i] = fma2(P[i], m, a); P[i] = fma2(P[i], m, a);
-                    if (MODE == 3) { P[i] = fma2(P[i], m, a); P[i] = fma2(P[i], m, a); }
+                    if (MODE >= 3) P[i] = fma2(P[i], m, a);
+                    if (MODE == 3) P[i] = fma2(P[i], m, a);
                     S[i] = rsq(S[i]);
                 }
             }
@@ -72,7 +74,7 @@ static int alu_rate(obem_ctx *c, int sms, float *sink, long long *cyc, long long
     long long mx = 1;
     for (int b = 0; b < blocks; ++b) mx = hcyc[b] > mx ? hcyc[b] : mx;
     // operations per thread: FP32 lane-ops for modes 0 and 2, rsqrt for mode 1
-    const double ops = (double)iters * 8 * PK_CHAINS * (MODE == 0 ? 2 : MODE == 1 ? 1 : MODE == 2 ? 12 : 16);
+    const double ops = (double)iters * 8 * PK_CHAINS * (MODE == 0 ? 2 : MODE == 1 ? 1 : MODE == 2 ? 12 : MODE == 3 ? 16 : 14);
     const double total = ops * (double)blocks * PK_THREADS;
     per_sm_clk = total / sms / (double)mx;
     per_s = total / (ms * 1e-3);
@@ -94,12 +96,13 @@ extern "C" int obem_alu_rates(obem_ctx *c, double *out, obem_stream stream)
         return obem_fail(c, OBEM_ERR_CUDA, "alu rates: allocation failed");
     }
     long long *hcyc = (long long *)malloc(sizeof(long long) * blocks);
-    double r0, f0, r1, f1, r2, f2, r3, f3;
+    double r0, f0, r1, f1, r2, f2, r3, f3, r4, f4;
     int rc = hcyc ? OBEM_OK : OBEM_ERR_ARG;
     if (rc == OBEM_OK) rc = alu_rate<0>(c, sms, sink, cyc, hcyc, s, r0, f0);
     if (rc == OBEM_OK) rc = alu_rate<1>(c, sms, sink, cyc, hcyc, s, r1, f1);
     if (rc == OBEM_OK) rc = alu_rate<2>(c, sms, sink, cyc, hcyc, s, r2, f2);
     if (rc == OBEM_OK) rc = alu_rate<3>(c, sms, sink, cyc, hcyc, s, r3, f3);
+    if (rc == OBEM_OK) rc = alu_rate<4>(c, sms, sink, cyc, hcyc, s, r4, f4);
     if (rc == OBEM_OK) {
         out[0] = 2.0 * f0 / 1e12;     // FP32 TFLOP/s of packed FMA chains (2 flops per lane-op)
         out[1] = r0;                  // FP32 lane-ops per SM per clock
@@ -107,6 +110,7 @@ extern "C" int obem_alu_rates(obem_ctx *c, double *out, obem_stream stream)
         out[3] = r2;                  // FP32 lane-ops per SM per clock in the 12:1 mix with rsqrt
         out[4] = f0 / (r0 * sms) / 1e6;   // SM clock during the FMA run, MHz
         out[5] = r3;                  // FP32 lane-ops per SM per clock in the 16:1 mix with rsqrt
+        out[6] = r4;                  // FP32 lane-ops per SM per clock in the 14:1 mix with rsqrt
     }
     free(hcyc);
     cudaFree(sink);

@@ -325,10 +325,11 @@ def obem_field_eval_noalloc(targets, E_out, sources=None, self_exclude=False, ce
 
 def obem_alu_rates(ctx, stream=None):
     """Measured FP32 / rsqrt rates of the GPU (see include/obem.h)."""
-    out = np.zeros(6, np.float64)
+    out = np.zeros(7, np.float64)
     _check(ctx, load().obem_alu_rates(ctx, out.ctypes.data_as(C.c_void_p), _stream(stream)))
     return {"fp32_tflops": out[0], "fp32_lane_ops_per_sm_clk": out[1], "rsqrt_per_sm_clk": out[2],
-            "mix12_lane_ops_per_sm_clk": out[3], "sm_mhz": out[4], "mix16_lane_ops_per_sm_clk": out[5]}
+            "mix12_lane_ops_per_sm_clk": out[3], "sm_mhz": out[4], "mix16_lane_ops_per_sm_clk": out[5],
+            "mix14_lane_ops_per_sm_clk": out[6]}
 
 
 def obem_fieldmap_build(ctx, lo, hi, dims, sigma, stream=None):

@@ -58,6 +58,35 @@ def test_nbody_self_exclude(n, symmetric):
     assert potential_err(got[:, 3], Vref, Vabs) <= FIELD_TOL
 
 
+@pytest.mark.parametrize("case", ["one_sign", "three_values", "shuffled"])
+def test_symmetric_charge_classes(case):
+    """The symmetric kernel runs on the charges ordered by charge value and
+    factors k_C q out of tile pairs with one charge value: all tiles of one
+    value (4096 electrons), charges -e / +e / +2e (tiles of +e and +2e mixed),
+    and the same charges in another order giving the same fields."""
+    rng = np.random.default_rng(11)
+    n = 4096 if case == "one_sign" else 5000
+    src = _charges(rng, n, pairs=n // 10)
+    if case == "one_sign":
+        src[:, 3] = -E
+    elif case == "three_values":
+        src[:, 3] = rng.choice([-E, E, 2 * E], n).astype(np.float32)
+    ctx = _ctx(cap=n)
+    try:
+        got = _gpu_field(ctx, src, src, self_exclude=True)
+        if case == "shuffled":
+            order = rng.permutation(n)
+            got2 = _gpu_field(ctx, src[order], src[order], self_exclude=True)
+    finally:
+        obem.obem_destroy(ctx)
+    Eref, Vref = oracle.nbody_field(src[:, :3].astype(np.float64), src.astype(np.float64), True)
+    Vabs = oracle.nbody_field(src[:, :3].astype(np.float64), np.abs(src.astype(np.float64)), True)[1]
+    assert guarded_rel_err(got[:, :3], Eref) <= FIELD_TOL
+    assert potential_err(got[:, 3], Vref, Vabs) <= FIELD_TOL
+    if case == "shuffled":
+        assert guarded_rel_err(got2[:, :3], Eref[order]) <= FIELD_TOL
+
+
 @pytest.mark.parametrize("nt,ns", [(700, 1500), (1, 300), (1025, 257)])
 def test_nbody_separate_targets(nt, ns):
     rng = np.random.default_rng(nt + ns)
