@@ -93,6 +93,8 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-fieldmap", action="store_true")
     p.add_argument("--no-nn", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-chambers", type=int, default=256)
     return p.parse_args()
 
 
@@ -350,6 +352,9 @@ def run_ours(a, ws, rank, local):
     fmap = None
     if ws == 1 and not a.no_fieldmap:
         fmap = fieldmap_timing(dev)
+    bres = None
+    if ws == 1 and not a.no_batch:
+        bres = batch_timing(dev, a.batch_chambers)
     cpu = None
     if ws == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(mesh, ch, gas, trk, a.cpu_seconds)
@@ -399,6 +404,7 @@ def run_ours(a, ws, rank, local):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fieldmap": fmap,
+        "batched_sweep": bres,
         "nbody_nn": nnres,
     }
     print(json.dumps(line), flush=True)
@@ -431,6 +437,134 @@ def nn_timing(ctx, pos_q, dev, soft, grids=(16, 32)):
                               "median_rel_err": float(rel.median())}
     out["charges"] = n
     out["exact_reference"] = "symmetric all-pairs field, no softening"
+    return out
+
+
+def batch_timing(dev, n_chambers=256, steps=3, swarm_steps=12):
+    """The batched sweep: n_chambers independent parallel-plate chambers
+    (gaps 0.5-3 mm, fields 0.1-30 kV/cm, 1e2-1e5 charges log-uniform, 1024-4096
+    cells each, argon-like gas), every chamber's cell densities from its own
+    GPU solve.  Times one step of every chamber (field + tracking) as the
+    captured CUDA graph of the batched step, after the autotuner picked the
+    cell block size, and the same work as the plain single-instance form (one
+    context per chamber, obem_step one after the other) from the same states;
+    both start every timed step from the same snapshot.  Swarm parameters per
+    chamber (Eqs. (vd), (diffusion), (townsend)) from a short batched run."""
+    import torch
+    from paper_2110_09214_gb300 import inputs, obem, swarm
+    chambers = inputs.config_batch(seed=1, n_chambers=n_chambers)
+    gas = inputs.argon_like_gas()
+    flags = obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD
+    # Plummer length 0.1 um: with 1 nm the pairs that ionisations place ~1 nm
+    # apart (Eq. (distIoni)) drive their electrons to keV energies in one 1 ps
+    # step of step-start field, and the avalanches run away
+    soft = 1e-7
+    t0 = time.perf_counter()
+    caps = [max(2 * c.charges.n, 1024) for c in chambers]
+    ctxs, sts, sig = [], [], []
+    for c, cap in zip(chambers, caps):
+        ctx = obem.obem_create(capacity=cap, dt=c.trk.dt, seed=c.trk.seed, softening=soft, z_lo=c.trk.z_lo,
+                               z_hi=c.trk.z_hi, beta=c.trk.beta, flags=flags)
+        obem.obem_gas_load(ctx, gas)
+        obem.obem_mesh_load(ctx, c.mesh)
+        obem.obem_bem_assemble(ctx, obem.OBEM_LU_FP32)
+        sg = torch.empty(c.mesh.n, dtype=torch.float32, device=dev)
+        obem.obem_bem_solve(ctx, c.mesh.group_voltage, sg)
+        st = obem.DeviceState(cap)
+        st.upload(c.charges)
+        ctxs.append(ctx)
+        sts.append(st)
+        sig.append(sg.cpu().numpy())
+    t_setup = time.perf_counter() - t0
+    bctx = obem.obem_create(capacity=16, dt=1e-12, softening=soft, beta=1e-13, flags=flags)
+    obem.obem_gas_load(bctx, gas)
+    b = obem.Batch(bctx, caps, [c.trk.z_lo for c in chambers], [c.trk.z_hi for c in chambers],
+                   [c.trk.seed for c in chambers])
+    out = {}
+    try:
+        for k, c in enumerate(chambers):
+            b.cells(k, c.mesh.tri, sig[k])
+        bst = b.state()
+        bst.upload([c.charges for c in chambers])
+        snap_b = {k: getattr(bst, k).clone() for k in ("pos_q", "vel", "id", "birth", "species", "n", "next_id")}
+        snap_s = [{k: getattr(st, k).clone() for k in ("pos_q", "vel", "id", "birth", "species", "scalars")}
+                  for st in sts]
+        tune = b.autotune(bst, reps=2)
+        step = torch.zeros(1, dtype=torch.int32, device=dev)
+        stats = obem.new_batch_stats(n_chambers)
+        sstats = [obem.new_stats() for _ in chambers]
+
+        def restore_b():
+            for k, v in snap_b.items():
+                getattr(bst, k).copy_(v)
+            step.zero_()
+
+        def restore_s():
+            for st, sn in zip(sts, snap_s):
+                for k, v in sn.items():
+                    getattr(st, k).copy_(v)
+
+        def timed(fn, restore):
+            tot = 0.0
+            for r in range(steps + 1):                 # first round warms up (and captures)
+                restore()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                if r:
+                    tot += e0.elapsed_time(e1)
+            return tot / steps
+
+        ms_b = timed(lambda: b.step_graph(bst, step, stats), restore_b)
+        gsb = obem.read_batch_stats(stats, n_chambers)
+        assert all(g["status"] == 0 for g in gsb), "batched step failed"
+
+        def single():
+            for ctx, st, ss in zip(ctxs, sts, sstats):
+                obem.obem_step(ctx, st, 0, ss)
+        ms_s = timed(single, restore_s)
+        for ss in sstats:
+            assert obem.read_stats(ss)["status"] == 0, "single-instance step failed"
+        n = np.array([c.charges.n for c in chambers], np.float64)
+        npan = np.array([c.mesh.n for c in chambers], np.float64)
+        ne = np.array([int((c.charges.species == 0).sum()) for c in chambers], np.float64)
+        pairs = float((n * (n - 1)).sum() + (n * npan).sum())
+        # per-chamber swarm parameters from a short batched run
+        restore_b()
+        hist = [[] for _ in chambers]
+        for _ in range(swarm_steps):
+            b.step_graph(bst, step, stats)
+            for k, g in enumerate(obem.read_batch_stats(stats, n_chambers)):
+                hist[k].append(g)
+        sw = [swarm.swarm_params(h, 1e-12) for h in hist]
+        vd = np.array([x[0] for x in sw])
+        out = {
+            "chambers": n_chambers, "charges": int(n.sum()), "electrons": int(ne.sum()), "cells": int(npan.sum()),
+            "charges_min_max": [int(n.min()), int(n.max())],
+            "pair_evals_per_step": pairs,
+            "batched_graph_ms_per_step": ms_b,
+            "single_instance_ms_per_step": ms_s,
+            "speedup_vs_single_instance": ms_s / ms_b if ms_b > 0 else None,
+            "electron_steps_per_s": float(ne.sum()) / (ms_b * 1e-3),
+            "field_pair_evals_per_s": pairs / (ms_b * 1e-3),
+            "autotune": tune,
+            "setup_s": t_setup,
+            "swarm": {"steps": swarm_steps, "drift_velocity_m_s_median": float(np.median(vd)),
+                      "per_chamber_first4": [{"e_kv_cm": round(chambers[k].e_kv_cm, 3),
+                                              "vd_m_s": sw[k][0], "dl_m2_s": sw[k][1], "alpha_1_m": sw[k][2]}
+                                             for k in range(min(4, n_chambers))]},
+            "note": "same chambers, same charges, same GPU; both forms compute the fused field (cells + "
+                    "all-pairs, FP32) and the tracking step; the single-instance form runs one context per "
+                    "chamber in sequence",
+        }
+    finally:
+        b.destroy()
+        obem.obem_destroy(bctx)
+        for ctx in ctxs:
+            obem.obem_destroy(ctx)
     return out
 
 

@@ -380,6 +380,61 @@ int obem_field_eval_noalloc(const float *targets, int32_t nt, const float *sourc
                             int32_t np, float *E_out, char *err, int32_t err_len,
                             obem_stream stream);
 
+/* Batch of independent chambers (many chambers with uneven charge counts
+ * stepped together, e.g. a sweep of the parallel-plate counter of Sec. 4.1
+ * over gaps and fields).  Each chamber is the method of obem_step on its own:
+ * the field at a charge is the cell field of its chamber's cells (Eq. (BEM3))
+ * plus the Coulomb field of the other charges of its chamber (Eq. (nbody)),
+ * and the tracking step (Secs. 3.2-3.3) draws from its chamber's Philox key
+ * and its own id, so a chamber evolves bit for bit as it would alone given
+ * the same field.  Every stage is one launch for all chambers.
+ *
+ * The charges live in one concatenated state (obem_state): chamber c owns
+ * slots [seg_off[c], seg_off[c + 1]) of every array, with its capacity
+ * rounded up to a multiple of 1024 (it may fill the whole segment), and its
+ * live charges are the first n[c] of them; st->n and st->next_id are device
+ * arrays of n_chambers entries and st->capacity is seg_off[n_chambers].
+ *
+ * obem_batch_create: the batch borrows ctx (which must outlive it) for the gas
+ *   (obem_gas_load first), dt, softening, beta, trial_cap, e_ext and flags
+ *   (only OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD and
+ *   OBEM_STEP_PROB_COLLISION are allowed); per chamber (host arrays
+ *   [n_chambers]): capacity >= 1, absorbing planes z_lo < z_hi, Philox key.
+ *   Allocates every buffer the steps need.
+ * obem_batch_layout: seg_off (host int64 [n_chambers + 1]).
+ * obem_batch_cells: chamber's cells (host FP64 [n_cells][3][3], layout of
+ *   obem_mesh_load) and their densities (host [n_cells], C/m^2, e.g. from
+ *   obem_bem_solve on a context holding that chamber's mesh); copied; the
+ *   next field / step uploads them (synchronously: not during stream capture).
+ * obem_batch_field_eval: E_out device [slots][4] (Ex, Ey, Ez, 0) at every live
+ *   slot; other slots untouched.
+ * obem_batch_step: one step of every chamber (field computed unless E_in,
+ *   device [slots][4], is given); the step index is the device scalar *step,
+ *   advanced by one when the batch commits; stats device [n_chambers].  If any
+ *   chamber fails (OBEM_ERR_CAPACITY / OBEM_ERR_TRIALS in its stats), no
+ *   chamber commits and the others report OBEM_ERR_STATE.  Allocates nothing.
+ * obem_batch_step_graph: the same fused step, captured once into a CUDA graph
+ *   (per set of state, step and stats pointers) and replayed on `stream`.
+ * obem_batch_autotune: times the field for cell-kernel blocks of 128, 256 and
+ *   512 targets on the current charges (best of reps runs each) and keeps the
+ *   fastest; out host [4]: chosen size, its time (ms), the time at 512, 0.
+ *   The size changes the field by rounding only (the quadrature tier of a cell
+ *   is chosen per block).  obem_batch_set_block sets it directly (32..512). */
+typedef struct obem_batch obem_batch;
+int obem_batch_create(obem_batch **batch, obem_ctx *ctx, int32_t n_chambers, const int32_t *capacity,
+                      const double *z_lo, const double *z_hi, const uint64_t *seed);
+void obem_batch_destroy(obem_batch *batch);
+int obem_batch_layout(const obem_batch *batch, int64_t *seg_off);
+int obem_batch_cells(obem_batch *batch, int32_t chamber, int32_t n_cells, const double *tri_xyz,
+                     const float *sigma);
+int obem_batch_field_eval(obem_batch *batch, const obem_state *st, float *E_out, obem_stream stream);
+int obem_batch_step(obem_batch *batch, const obem_state *st, const float *E_in, uint32_t *step,
+                    obem_step_stats *stats, obem_stream stream);
+int obem_batch_step_graph(obem_batch *batch, const obem_state *st, uint32_t *step, obem_step_stats *stats,
+                          obem_stream stream);
+int obem_batch_autotune(obem_batch *batch, const obem_state *st, int32_t reps, double *out, obem_stream stream);
+int obem_batch_set_block(obem_batch *batch, int32_t cells_per_block);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@ UNITS = {
     "peak.cu": [],
     "fieldmap.cu": [],
     "nn.cu": [],
+    "batch.cu": [],
 }
 
 

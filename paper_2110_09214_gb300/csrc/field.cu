@@ -218,6 +218,19 @@ __device__ __forceinline__ bool block_range(const FieldLaunch &L, int nt, int &b
     return base < nt;
 }
 
+// This block's cells [poff, poff + np) of the cell arrays: all cells, or in a
+// batch of chambers the cells of the block's chamber.
+__device__ __forceinline__ void block_cells(const FieldLaunch &L, int &poff, int &np)
+{
+    poff = 0;
+    np = L.panels.np;
+    if (L.block_cham) {
+        const int2 r = L.cham_pan[L.block_cham[blockIdx.x]];
+        poff = r.x;
+        np = r.y;
+    }
+}
+
 // Targets of this block (binned order, absolute coordinates) and its frame.
 // Target slot k of thread t is base + k * CT_THREADS + t.
 __device__ __forceinline__ void block_targets(const FieldLaunch &L, int end, int base, float *tx, float *ty,
@@ -283,21 +296,22 @@ __device__ __noinline__ float4 closed_val(const double *v, float tx, float ty, f
     return make_float4((float)(kq * Fx), (float)(kq * Fy), (float)(kq * Fz), (float)(kq * phi));
 }
 
-// deterministic compaction of the near cells of [pb, pb + NEAR_CHUNK) into list
-__device__ __forceinline__ int near_list(const FieldLaunch &L, int pb, const BlockFrame &F, int *list, int *cnt)
+// deterministic compaction of the near cells of [pb, pb + NEAR_CHUNK) of the
+// block's cells into list (as indices of the cell arrays)
+__device__ __forceinline__ int near_list(const FieldLaunch &L, int poff, int np, int pb, const BlockFrame &F,
+                                         int *list, int *cnt)
 {
-    const int np = L.panels.np;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = pb + threadIdx.x;
     bool near = false;
-    if (j < np) near = cell_is_near(L.panels.c_a[j], L.panels.g0_h[j].w, F);
+    if (j < np) near = cell_is_near(L.panels.c_a[poff + j], L.panels.g0_h[poff + j].w, F);
     const unsigned bal = __ballot_sync(0xffffffffu, near);
     __syncthreads();
     if (lane == 0) cnt[warp] = __popc(bal);
     __syncthreads();
     int off = 0, tot = 0;
     for (int w = 0; w < CT_THREADS / 32; ++w) { if (w < warp) off += cnt[w]; tot += cnt[w]; }
-    if (near) list[off + __popc(bal & ((1u << lane) - 1u))] = j;
+    if (near) list[off + __popc(bal & ((1u << lane) - 1u))] = poff + j;
     __syncthreads();
     return tot;
 }
@@ -352,6 +366,8 @@ near_closed_kernel(FieldLaunch L)
     int ti[CT_TPT];
     BlockFrame F;
     block_targets(L, end, base, tx, ty, tz, ti, F);
+    int poff, np;
+    block_cells(L, poff, np);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *qp = s_qp[warp], *res = s_res[warp];
     int *qt = s_qt[warp];
@@ -364,8 +380,8 @@ near_closed_kernel(FieldLaunch L)
         for (int c = 0; c < 4; ++c) { S[k][c] = 0.f; C[k][c] = 0.f; P[k][c] = 0.f; }
     unsigned long long cntA = 0;
     int nq = 0;                                         // queued pairs (warp-uniform)
-    for (int pb = 0; pb < L.panels.np; pb += NEAR_CHUNK) {
-        const int tot = near_list(L, pb, F, s_list, s_cnt);
+    for (int pb = 0; pb < np; pb += NEAR_CHUNK) {
+        const int tot = near_list(L, poff, np, pb, F, s_list, s_cnt);
         if (tot == 0) continue;
         for (int q = 0; q < (warp_live ? tot : 0); ++q) {
             const int j = s_list[q];
@@ -436,6 +452,8 @@ near_quad_kernel(FieldLaunch L)
     int ti[CT_TPT];
     BlockFrame F;
     block_targets(L, end, base, tx, ty, tz, ti, F);
+    int poff, np;
+    block_cells(L, poff, np);
     const bool warp_live = base + (int)(threadIdx.x & ~31u) < end;
     float S[CT_TPT][4], C[CT_TPT][4];
 #pragma unroll
@@ -454,8 +472,8 @@ near_quad_kernel(FieldLaunch L)
         TZ[p] = pk(tz[2 * p], tz[2 * p + 1]);
     }
     unsigned long long cntQ = 0;
-    for (int pb = 0; pb < L.panels.np; pb += NEAR_CHUNK) {
-        const int tot = near_list(L, pb, F, s_list, s_cnt);
+    for (int pb = 0; pb < np; pb += NEAR_CHUNK) {
+        const int tot = near_list(L, poff, np, pb, F, s_list, s_cnt);
         for (int g = 0; g < tot; g += NQ_CELLS) {
             const int ng = min(NQ_CELLS, tot - g);
             __syncthreads();
@@ -546,7 +564,7 @@ near_quad_kernel(FieldLaunch L)
 }
 
 // far cells as quadrature-point sources, in the block's frame
-template <bool WANT_V, bool COUNT>
+template <bool WANT_V, bool COUNT, bool BATCH = false>
 __global__ void __launch_bounds__(CT_THREADS)
 cell_kernel(FieldLaunch L)
 {
@@ -580,15 +598,16 @@ cell_kernel(FieldLaunch L)
         TZ[p] = pk(tz[2 * p] - o.z, tz[2 * p + 1] - o.z);
     }
     unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0;
-    const int np = L.panels.np;
+    int poff = 0, np = L.panels.np;
+    if (BATCH) block_cells(L, poff, np);
     const int tid = threadIdx.x;
     for (int pb = 0; pb < np; pb += CT_CHUNK) {
         __syncthreads();
         if (tid < 32) {
             // warp 0: tier of each cell of the chunk, point counts, offsets
-            const int j = pb + tid;
+            const int j = poff + pb + tid;
             int n = 0;
-            if (j < np) {
+            if (pb + tid < np) {
                 const float4 ca = L.panels.c_a[j], cl = L.panels.c_lo[j];
                 const float sg = L.sigma[j];
                 PanTile t;
@@ -949,88 +968,152 @@ __host__ __device__ constexpr size_t sym_smem(int nc)
 int obem_sym_part_blocks(int capacity) { return (capacity + SP_BLOCK - 1) / SP_BLOCK; }
 int obem_sym_tiles(int capacity) { return sym_geom(capacity).n; }
 
-// negative charges per block of SP_BLOCK slots
-__global__ void sym_part_count_kernel(const float4 *src, int nt, const int32_t *nt_dev, int32_t *bcnt)
+// Partition and tiles of one set of charges (SymBatch.nb == 0: the launch's
+// targets, nt or *nt_dev of them) or of a batch of chambers (chamber c holds
+// slots [seg_off[c], seg_off[c + 1]), n[c] live, offsets multiples of SY_T):
+// slot block b (SP_BLOCK == SY_T slots) belongs to chamber c, whose live
+// charges are slots [off, off + n).
+__device__ __forceinline__ void sym_block_range(const SymBatch &SB, int nt, const int32_t *nt_dev, int b, int &c,
+                                                int &off, int &n)
 {
-    const int n = nt_dev ? *nt_dev : nt;
-    const int i = blockIdx.x * SP_BLOCK + threadIdx.x;
-    const int c = __syncthreads_count(i < n && src[i].w < 0.f);
-    if (threadIdx.x == 0) bcnt[blockIdx.x] = c;
+    if (SB.nb) {
+        c = SB.slot_cham[b];
+        off = SB.seg_off[c];
+        n = SB.n[c];
+    } else {
+        c = 0;
+        off = 0;
+        n = nt_dev ? *nt_dev : nt;
+    }
 }
 
-// exclusive scan of the nb block counts in place, total in bcnt[nb]; one block of 1024
-__global__ void sym_part_scan_kernel(int32_t *bcnt, int nb)
+// negative charges per block of SP_BLOCK slots
+__global__ void sym_part_count_kernel(const float4 *src, int nt, const int32_t *nt_dev, SymBatch SB, int32_t *bcnt)
+{
+    int c, off, n;
+    sym_block_range(SB, nt, nt_dev, blockIdx.x, c, off, n);
+    const int i = blockIdx.x * SP_BLOCK + threadIdx.x;
+    const int cnt = __syncthreads_count(i - off < n && src[i].w < 0.f);
+    if (threadIdx.x == 0) bcnt[blockIdx.x] = cnt;
+}
+
+// exclusive scan of the block counts of one chamber (one block of 1024 per
+// chamber; the blocks [0, nb) when there is no batch), in place; the
+// chamber's total to tot[c]
+__global__ void sym_part_scan_kernel(int32_t *bcnt, int nb, SymBatch SB, int32_t *tot)
 {
     __shared__ int32_t part[1024];
-    const int per = (nb + 1023) / 1024, b0 = threadIdx.x * per;
+    int b0 = 0, b1 = nb;
+    if (SB.nb) {
+        b0 = SB.seg_off[blockIdx.x] / SP_BLOCK;
+        b1 = SB.seg_off[blockIdx.x + 1] / SP_BLOCK;
+    }
+    const int m = b1 - b0;
+    const int per = (m + 1023) / 1024, q0 = b0 + threadIdx.x * per;
     int32_t s = 0;
     for (int q = 0; q < per; ++q)
-        if (b0 + q < nb) s += bcnt[b0 + q];
+        if (q0 + q < b1) s += bcnt[q0 + q];
     part[threadIdx.x] = s;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
         __syncthreads();
         part[threadIdx.x] += v;
         __syncthreads();
     }
     int32_t run = part[threadIdx.x] - s;
     for (int q = 0; q < per; ++q)
-        if (b0 + q < nb) {
-            const int32_t c = bcnt[b0 + q];
-            bcnt[b0 + q] = run;
-            run += c;
+        if (q0 + q < b1) {
+            const int32_t v = bcnt[q0 + q];
+            bcnt[q0 + q] = run;
+            run += v;
         }
-    if (threadIdx.x == 1023) bcnt[nb] = part[1023];
+    if (threadIdx.x == 1023) tot[blockIdx.x] = part[1023];
 }
 
 // sorted[dst] = (position of target i, charge of source i), perm[dst] = i
+// (slots of the concatenated arrays; each chamber sorted within its segment)
 __global__ void sym_part_scatter_kernel(const float4 *tgt, const float4 *src, int nt, const int32_t *nt_dev,
-                                        const int32_t *bcnt, int nb, float4 *sorted, int32_t *perm)
+                                        SymBatch SB, const int32_t *bcnt, const int32_t *tot, float4 *sorted,
+                                        int32_t *perm)
 {
     __shared__ int32_t wneg[SP_BLOCK / 32];
-    const int n = nt_dev ? *nt_dev : nt;
-    const int i = blockIdx.x * SP_BLOCK + threadIdx.x;
+    int c, off, n;
+    sym_block_range(SB, nt, nt_dev, blockIdx.x, c, off, n);
+    const int i = blockIdx.x * SP_BLOCK + threadIdx.x;      // slot
+    const int li = i - off;                                  // index in the chamber
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     float q = 0.f;
-    if (i < n) { p = tgt[i]; q = src[i].w; }
-    const bool neg = i < n && q < 0.f;
+    if (li < n) { p = tgt[i]; q = src[i].w; }
+    const bool neg = li < n && q < 0.f;
     const unsigned bal = __ballot_sync(0xffffffffu, neg);
     if (lane == 0) wneg[warp] = __popc(bal);
     __syncthreads();
     int rneg = __popc(bal & ((1u << lane) - 1u));        // negative charges before i in the block
     for (int w = 0; w < warp; ++w) rneg += wneg[w];
-    if (i < n) {
+    if (li < n) {
         const int negoff = bcnt[blockIdx.x];
-        const int dst = neg ? negoff + rneg
-                            : bcnt[nb] + (blockIdx.x * SP_BLOCK - negoff) + ((int)threadIdx.x - rneg);
-        sorted[dst] = make_float4(p.x, p.y, p.z, q);
-        perm[dst] = i;
+        const int lb = blockIdx.x * SP_BLOCK - off;          // the block's first index in the chamber
+        const int dst = neg ? negoff + rneg : tot[c] + (lb - negoff) + ((int)threadIdx.x - rneg);
+        sorted[off + dst] = make_float4(p.x, p.y, p.z, q);
+        perm[off + dst] = i;
     }
 }
 
 // per tile of SY_T sorted slots: the common charge, or NaN; slots past n count as 0
-__global__ void sym_tileq_kernel(const float4 *sorted, int nt, const int32_t *nt_dev, float *tileq)
+__global__ void sym_tileq_kernel(const float4 *sorted, int nt, const int32_t *nt_dev, SymBatch SB, float *tileq)
 {
-    const int n = nt_dev ? *nt_dev : nt;
+    int c, off, n;
+    sym_block_range(SB, nt, nt_dev, blockIdx.x, c, off, n);
     const int base = blockIdx.x * SY_T;
-    if (base >= n) return;
+    if (base - off >= n) return;
     const float q0 = sorted[base].w;
     bool same = true;
     for (int k = threadIdx.x; k < SY_T; k += blockDim.x) {
         const int i = base + k;
-        same = same && ((i < n ? sorted[i].w : 0.f) == q0);
+        same = same && ((i - off < n ? sorted[i].w : 0.f) == q0);
     }
     same = __syncthreads_and(same);
     if (threadIdx.x == 0) tileq[blockIdx.x] = same ? q0 : __int_as_float(0x7fc00000);
 }
 
+// units of every chamber of a batch and their offsets (one block)
+__global__ void sym_units_kernel(SymBatch SB)
+{
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < SB.nb; c0 += 1024) {
+        const int c = c0 + threadIdx.x;
+        int32_t u = 0;
+        if (c < SB.nb && SB.n[c] > 0) {
+            const SymGeom G = sym_geom(SB.n[c]);
+            u = G.n * G.nch;
+        }
+        // inclusive block scan
+        __shared__ int32_t part[1024];
+        part[threadIdx.x] = u;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+            __syncthreads();
+            part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (c < SB.nb) SB.uoff[c] = carry + part[threadIdx.x] - u;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) SB.uoff[SB.nb] = carry;
+}
+
 template <bool B> struct SyBool { static constexpr bool value = B; };
 
-template <bool WANT_V>
+template <bool WANT_V, bool BATCH>
 __global__ void __launch_bounds__(SY_THREADS, SY_MINB)
-nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const float *tileq)
+nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const float *tileq, SymBatch SB)
 {
     constexpr int NC = WANT_V ? 4 : 3;
     extern __shared__ __align__(16) unsigned char sy_smem[];
@@ -1040,33 +1123,65 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
     float *s_jS = reinterpret_cast<float *>(s_C + NC);                            // [NC * SY_T]
     float *s_jC = s_jS + NC * SY_T;
     SrcPk *s_src = reinterpret_cast<SrcPk *>(s_jS);
-    __shared__ int s_unit;
+    __shared__ int s_unit, s_off, s_nt;
+    __shared__ long long s_joff, s_ioff;
 
-    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
-    if (nt <= 0) return;
-    const SymGeom G = sym_geom(nt);
-    const int units = G.n * G.nch;
+    // one set of charges: nt of them, units fixed; a batch: per unit, its
+    // chamber's slots [s_off, s_off + s_nt) and partial-sum offsets
+    int units, nt0 = 0;
+    SymGeom G0;
+    if (BATCH) {
+        units = SB.uoff[SB.nb];
+    } else {
+        nt0 = L.nt_dev ? *L.nt_dev : L.nt;
+        if (nt0 <= 0) return;
+        G0 = sym_geom(nt0);
+        units = G0.n * G0.nch;
+    }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float kC = (float)OBEM_KC;
     const u64 EPS2 = pk(L.eps2, L.eps2);
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_unit = atomicAdd(counter, 1);
+        if (tid == 0) {
+            const int u = atomicAdd(counter, 1);
+            if (BATCH) {
+                int lu = -1;
+                if (u < units) {
+                    int lo = 0, hi = SB.nb;              // uoff[lo] <= u < uoff[hi]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (SB.uoff[mid] <= u) lo = mid; else hi = mid;
+                    }
+                    lu = u - SB.uoff[lo];
+                    s_off = SB.seg_off[lo];
+                    s_nt = SB.n[lo];
+                    s_joff = SB.joff[lo];
+                    s_ioff = SB.ioff[lo];
+                }
+                s_unit = lu;
+            } else {
+                s_unit = u < units ? u : -1;
+            }
+        }
         __syncthreads();
         const int unit = s_unit;
-        if (unit >= units) break;
+        if (unit < 0) break;
+        const int off = BATCH ? s_off : 0;
+        const int lim = BATCH ? off + s_nt : nt0;        // end of the live slots
+        const SymGeom G = BATCH ? sym_geom(s_nt) : G0;
         const int I = unit / G.nch, kch = unit % G.nch;
         const int d0 = kch * SY_CH, d1 = min(d0 + SY_CH, sym_h(G, I) + 1);
-        const int base = I * SY_T;
+        const int base = off + I * SY_T;
         // targets of tile I: 8 per thread (k * 128 + tid), four packs
         u64 TX[SY_NP], TY[SY_NP], TZ[SY_NP], QI[SY_NP];
 #pragma unroll
         for (int k = 0; k < SY_NI; ++k) {
             const int i = base + k * SY_THREADS + tid;
             // position from the targets, charge from the sources (the same charges)
-            const float4 p = i < nt ? L.targets[i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-            const float kq = i < nt ? kC * L.sources[i].w : 0.f;
+            const float4 p = i < lim ? L.targets[i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
+            const float kq = i < lim ? kC * L.sources[i].w : 0.f;
             if (k & 1) {
                 TX[k >> 1] = pk(__uint_as_float((uint32_t)TX[k >> 1]), p.x);
                 TY[k >> 1] = pk(__uint_as_float((uint32_t)TY[k >> 1]), p.y);
@@ -1083,7 +1198,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
         }
         for (int d = d0; d < d1; ++d) {
             const int J = I + d < G.n ? I + d : I + d - G.n;
-            const int jb = J * SY_T;
+            const int jb = off + J * SY_T;
             if (d == 0) {
                 // ordered pairs inside tile I, self pair skipped; target side only
                 for (int sb = 0; sb < SY_T; sb += SY_DTILE) {
@@ -1091,7 +1206,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
                     for (int l = tid; l < SY_DTILE; l += SY_THREADS) {
                         const int j = jb + sb + l;
                         SrcPk sp;
-                        if (j < nt) {
+                        if (j < lim) {
                             const float4 s = L.sources[j];
                             const float kq = kC * s.w;
                             sp.xx = pk(s.x, s.x); sp.yy = pk(s.y, s.y); sp.zz = pk(s.z, s.z); sp.qq = pk(kq, kq);
@@ -1148,7 +1263,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
 #pragma unroll
             for (int p = 0; p < SY_NP; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
             // one charge value in each tile: k_C q factored out of the loop
-            const float qJ = tileq[J], qI = tileq[I];
+            const float qJ = tileq[off / SY_T + J], qI = tileq[off / SY_T + I];
             const bool uni = qJ == qJ && qI == qI;
             const float afac = uni ? kC * qJ : 1.f, pfac = uni ? kC * qI : 1.f;
             auto rounds = [&](auto uni_c) {
@@ -1156,7 +1271,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
             for (int r = 0; r < SY_NG; ++r) {
                 const int grp = (r + (SY_NG / SY_WARPS) * warp) % SY_NG;   // distinct per warp in a round
                 const int j0 = jb + grp * 32;
-                float4 sj = j0 + lane < nt ? L.sources[j0 + lane] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
+                float4 sj = j0 + lane < lim ? L.sources[j0 + lane] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
                 float jx = sj.x, jy = sj.y, jz = sj.z, jq = UNI ? 0.f : kC * sj.w;
                 float ax = 0.f, ay = 0.f, az = 0.f, av = 0.f;
                 for (int s = 0; s < 32; ++s) {
@@ -1245,11 +1360,11 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
             if (uni) rounds(SyBool<true>{});
             else rounds(SyBool<false>{});
             // the item's source-side sums (S + C) to its own slot
-            float *jp = jpart + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
+            float *jp = jpart + (BATCH ? s_joff : 0) + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
             for (int l = tid; l < NC * SY_T; l += SY_THREADS) jp[l] = s_jS[l] + s_jC[l];
         }
         // the unit's target-side sums (S and C) to its own slot
-        float *ip = ipart + ((size_t)I * G.nch + kch) * 8 * SY_T;
+        float *ip = ipart + (BATCH ? s_ioff : 0) + ((size_t)I * G.nch + kch) * 8 * SY_T;
 #pragma unroll
         for (int k = 0; k < SY_NI; ++k)
 #pragma unroll
@@ -1261,16 +1376,30 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
 }
 
 // E_out[t] = init + target-side sums of t's row + minus the source-side sums of
-// every item whose second tile holds t, added in a fixed order (FP64).
+// every item whose second tile holds t, added in a fixed order (FP64).  t is a
+// slot of the sorted copy; perm[t] the charge it holds.
 template <bool WANT_V>
-__global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float *ipart, int add, const int32_t *perm)
+__global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float *ipart, int add, const int32_t *perm,
+                                  SymBatch SB)
 {
     constexpr int NC = WANT_V ? 4 : 3;
-    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+    int nt, off = 0;
+    long long joff = 0, ioff = 0;
+    if (SB.nb) {
+        if (t >= SB.seg_off[SB.nb]) return;
+        const int c = SB.slot_cham[t / OBEM_SEG_ALIGN];
+        off = SB.seg_off[c];
+        nt = SB.n[c];
+        joff = SB.joff[c];
+        ioff = SB.ioff[c];
+    } else {
+        nt = L.nt_dev ? *L.nt_dev : L.nt;
+    }
+    const int lt = t - off;
+    if (lt >= nt) return;
     const SymGeom G = sym_geom(nt);
-    const int T = t / SY_T, w = t % SY_T;
+    const int T = lt / SY_T, w = lt % SY_T;
     const int o = perm ? perm[t] : t;                  // sorted slot t is charge o
     double e[4] = {0.0, 0.0, 0.0, 0.0};
     if (add) {
@@ -1280,16 +1409,27 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
         e[0] = L.e_ext.x; e[1] = L.e_ext.y; e[2] = L.e_ext.z;
     }
     for (int k = 0; k < G.nch; ++k) {
-        const float *ip = ipart + ((size_t)T * G.nch + k) * 8 * SY_T;
+        const float *ip = ipart + ioff + ((size_t)T * G.nch + k) * 8 * SY_T;
 #pragma unroll
         for (int c = 0; c < NC; ++c) e[c] += (double)ip[(2 * c) * SY_T + w] + (double)ip[(2 * c + 1) * SY_T + w];
     }
-    for (int d = 1; d <= G.hmax; ++d) {
-        const int I = T - d >= 0 ? T - d : T - d + G.n;
-        if (d > sym_h(G, I)) continue;
-        const float *jp = jpart + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
+    // the items (I, d) with I + d = T (mod n): four loads in flight per round
+    constexpr int FU = 4;
+    for (int d0 = 1; d0 <= G.hmax; d0 += FU) {
+        float v[FU][NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) e[c] += (c < 3 ? -1.0 : 1.0) * (double)jp[c * SY_T + w];
+        for (int u = 0; u < FU; ++u) {
+            const int d = d0 + u;
+            const int I = T - d >= 0 ? T - d : T - d + G.n;
+            const bool ok = d <= G.hmax && d <= sym_h(G, I);
+            const float *jp = jpart + joff + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[u][c] = ok ? jp[c * SY_T + w] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < FU; ++u)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) e[c] += (c < 3 ? -1.0 : 1.0) * (double)v[u][c];
     }
     L.E_out[o] = make_float4((float)e[0], (float)e[1], (float)e[2], WANT_V ? (float)e[3] : 0.f);
 }
@@ -1299,9 +1439,10 @@ int obem_sym_grid(int device)
 {
     int sms = 0, best = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    void (*ks[])(FieldLaunch, float *, float *, int *, const float *) = {nbsym_kernel<true>, nbsym_kernel<false>};
-    const size_t sm[] = {sym_smem(4), sym_smem(3)};
-    for (int q = 0; q < 2; ++q) {
+    void (*ks[])(FieldLaunch, float *, float *, int *, const float *, SymBatch) = {
+        nbsym_kernel<true, false>, nbsym_kernel<false, false>, nbsym_kernel<false, true>};
+    const size_t sm[] = {sym_smem(4), sym_smem(3), sym_smem(3)};
+    for (int q = 0; q < 3; ++q) {
         if (cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]) != cudaSuccess)
             return 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks[q], SY_THREADS, sm[q]) != cudaSuccess) return 0;
@@ -1390,11 +1531,13 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
         } else if (sym) {
             // charges ordered by charge value (stable), per-tile common charge
             const int nb = obem_sym_part_blocks(capacity_targets);
-            sym_part_count_kernel<<<nb, SP_BLOCK, 0, s>>>(L.sources, L.nt, L.nt_dev, ctx->sym_bcnt);
-            sym_part_scan_kernel<<<1, 1024, 0, s>>>(ctx->sym_bcnt, nb);
-            sym_part_scatter_kernel<<<nb, SP_BLOCK, 0, s>>>(L.targets, L.sources, L.nt, L.nt_dev, ctx->sym_bcnt, nb,
-                                                           ctx->sym_sorted, ctx->sym_perm);
-            sym_tileq_kernel<<<obem_sym_tiles(capacity_targets), 256, 0, s>>>(ctx->sym_sorted, L.nt, L.nt_dev,
+            SymBatch SB;
+            memset(&SB, 0, sizeof SB);
+            sym_part_count_kernel<<<nb, SP_BLOCK, 0, s>>>(L.sources, L.nt, L.nt_dev, SB, ctx->sym_bcnt);
+            sym_part_scan_kernel<<<1, 1024, 0, s>>>(ctx->sym_bcnt, nb, SB, ctx->sym_bcnt + nb);
+            sym_part_scatter_kernel<<<nb, SP_BLOCK, 0, s>>>(L.targets, L.sources, L.nt, L.nt_dev, SB, ctx->sym_bcnt,
+                                                           ctx->sym_bcnt + nb, ctx->sym_sorted, ctx->sym_perm);
+            sym_tileq_kernel<<<obem_sym_tiles(capacity_targets), 256, 0, s>>>(ctx->sym_sorted, L.nt, L.nt_dev, SB,
                                                                              ctx->sym_tileq);
             OBEM_LAUNCH(ctx);
             FieldLaunch Ls = L;
@@ -1403,15 +1546,17 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
             const dim3 sg(ctx->sym_grid);
             if (L.want_v)
-                nbsym_kernel<true><<<sg, SY_THREADS, sym_smem(4), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
-                                                                      ctx->sym_tileq);
+                nbsym_kernel<true, false><<<sg, SY_THREADS, sym_smem(4), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
+                                                                      ctx->sym_tileq, SB);
             else
-                nbsym_kernel<false><<<sg, SY_THREADS, sym_smem(3), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
-                                                                       ctx->sym_tileq);
+                nbsym_kernel<false, false><<<sg, SY_THREADS, sym_smem(3), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
+                                                                       ctx->sym_tileq, SB);
             OBEM_LAUNCH(ctx);
             const int fb = (capacity_targets + 255) / 256;
-            if (L.want_v) nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm);
-            else nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm);
+            if (L.want_v)
+                nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm, SB);
+            else
+                nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm, SB);
             OBEM_LAUNCH(ctx);
             if (L.events) ctx->launches += 6;
         } else if (L.want_v) {
@@ -1432,6 +1577,111 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
         if (L.events) ctx->launches++;
     }
     if (L.events) cudaEventRecord(L.events[2], s);
+    return OBEM_OK;
+}
+
+// ====================================================================
+// Batch of chambers.
+
+size_t obem_sym_sizes(int capacity, size_t *ipart_floats)
+{
+    *ipart_floats = obem_sym_ipart_floats(capacity);
+    return obem_sym_jpart_floats(capacity);
+}
+
+// cell-kernel blocks of every chamber: ceil(n[c] / cut) blocks of consecutive
+// live slots each (one block of 1024 threads)
+__global__ void bt_blocks_kernel(FieldBatch F, int2 *blocks, int32_t *block_cham, int32_t *nblocks)
+{
+    __shared__ int32_t part[1024];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < F.nb; c0 += 1024) {
+        const int c = c0 + threadIdx.x;
+        const int n = c < F.nb ? F.sym.n[c] : 0;
+        const int k = (n + F.cut - 1) / F.cut;
+        part[threadIdx.x] = k;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+            __syncthreads();
+            part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        int b = carry + part[threadIdx.x] - k;
+        const int off = c < F.nb ? F.sym.seg_off[c] : 0;
+        for (int q = 0; q < k; ++q, ++b) {
+            blocks[b] = make_int2(off + q * F.cut, min(F.cut, n - q * F.cut));
+            block_cham[b] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nblocks = carry;
+}
+
+__global__ void bt_const_field_kernel(FieldBatch F, float4 *E_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= F.slots) return;
+    const int c = F.sym.slot_cham[i / OBEM_SEG_ALIGN];
+    if (i - F.sym.seg_off[c] >= F.sym.n[c]) return;
+    E_out[i] = make_float4(F.e_ext.x, F.e_ext.y, F.e_ext.z, 0.f);
+}
+
+int obem_launch_field_batch(obem_ctx *ctx, const FieldBatch &F, const float4 *pos_q, float4 *E_out, cudaStream_t s)
+{
+    if (F.cut < 32 || F.cut > CT_BLOCK) return obem_fail(ctx, OBEM_ERR_ARG, "batch: cell block size outside 32..512");
+    FieldLaunch L;
+    memset(&L, 0, sizeof L);
+    L.targets = pos_q;
+    L.nt = F.slots;
+    L.sources = pos_q;
+    L.self_exclude = 1;
+    L.eps2 = F.eps2;
+    L.E_out = E_out;
+    L.e_ext = F.e_ext;
+    L.want_v = 0;
+    if (F.cells) {
+        L.sigma = F.sigma;
+        L.panels = F.panels;
+        L.blocks = F.blocks;
+        L.nblocks = F.nblocks;
+        L.block_cham = F.block_cham;
+        L.cham_pan = F.cham_pan;
+        bt_blocks_kernel<<<1, 1024, 0, s>>>(F, F.blocks, F.block_cham, F.nblocks);
+        OBEM_LAUNCH(ctx);
+        const dim3 cg(F.max_blocks);
+        near_closed_kernel<false, false><<<cg, CT_THREADS, 0, s>>>(L);
+        near_quad_kernel<false, false><<<cg, CT_THREADS, 0, s>>>(L);
+        cell_kernel<false, false, true><<<cg, CT_THREADS, 0, s>>>(L);
+        OBEM_LAUNCH(ctx);
+    }
+    if (F.charges) {
+        const int nsb = F.slots / SP_BLOCK;
+        sym_part_count_kernel<<<nsb, SP_BLOCK, 0, s>>>(pos_q, 0, NULL, F.sym, F.bcnt);
+        sym_part_scan_kernel<<<F.nb, 1024, 0, s>>>(F.bcnt, 0, F.sym, F.sym.negtot);
+        sym_part_scatter_kernel<<<nsb, SP_BLOCK, 0, s>>>(pos_q, pos_q, 0, NULL, F.sym, F.bcnt, F.sym.negtot, F.sorted,
+                                                        F.perm);
+        sym_tileq_kernel<<<nsb, 256, 0, s>>>(F.sorted, 0, NULL, F.sym, F.tileq);
+        sym_units_kernel<<<1, 1024, 0, s>>>(F.sym);
+        OBEM_LAUNCH(ctx);
+        FieldLaunch Ls = L;
+        Ls.targets = F.sorted;
+        Ls.sources = F.sorted;
+        OBEM_CUDA(ctx, cudaMemsetAsync(F.counter, 0, sizeof(int), s));
+        nbsym_kernel<false, true><<<F.sym_grid, SY_THREADS, sym_smem(3), s>>>(Ls, F.jpart, F.ipart, F.counter, F.tileq,
+                                                                       F.sym);
+        OBEM_LAUNCH(ctx);
+        nbsym_fold_kernel<false><<<F.slots / 256, 256, 0, s>>>(L, F.jpart, F.ipart, F.cells ? 1 : 0, F.perm, F.sym);
+        OBEM_LAUNCH(ctx);
+    }
+    if (!F.cells && !F.charges) {
+        bt_const_field_kernel<<<F.slots / 256, 256, 0, s>>>(F, E_out);
+        OBEM_LAUNCH(ctx);
+    }
     return OBEM_OK;
 }
 

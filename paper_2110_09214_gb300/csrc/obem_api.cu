@@ -315,6 +315,43 @@ extern "C" int obem_gas_load(obem_ctx *c, const obem_gas *gs)
     return OBEM_OK;
 }
 
+// Cell geometry in the layout of the field kernels (see PanelsDev) from FP64
+// vertices; kind may be NULL (electrode).  Returns the first degenerate cell,
+// or -1.
+int obem_cell_layout(const double *tri, const int32_t *kind, int np, float4 *ca, float4 *g0, float4 *g1,
+                     float4 *g2, float4 *nr, float4 *cl)
+{
+    for (int i = 0; i < np; ++i) {
+        const double *v = tri + 9 * (size_t)i;
+        double cc[3], e1[3], e2[3], nn[3];
+        for (int k = 0; k < 3; ++k) {
+            cc[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0;
+            e1[k] = v[3 + k] - v[k];
+            e2[k] = v[6 + k] - v[k];
+        }
+        nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double a2 = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+        if (!(a2 > 0.0)) return i;
+        double h2 = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            const double *a = v + 3 * e, *b = v + 3 * ((e + 1) % 3);
+            double d = (a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]);
+            if (d > h2) h2 = d;
+        }
+        ca[i] = make_float4((float)cc[0], (float)cc[1], (float)cc[2], (float)(OBEM_KC * 0.5 * a2));
+        g0[i] = make_float4((float)(v[0] - cc[0]), (float)(v[1] - cc[1]), (float)(v[2] - cc[2]), (float)h2);
+        g1[i] = make_float4((float)(v[3] - cc[0]), (float)(v[4] - cc[1]), (float)(v[5] - cc[2]), 0.f);
+        g2[i] = make_float4((float)(v[6] - cc[0]), (float)(v[7] - cc[1]), (float)(v[8] - cc[2]), 0.f);
+        nr[i] = make_float4((float)(nn[0] / a2), (float)(nn[1] / a2), (float)(nn[2] / a2),
+                            (float)(kind ? kind[i] : OBEM_CELL_ELECTRODE));
+        cl[i] = make_float4((float)(cc[0] - (double)ca[i].x), (float)(cc[1] - (double)ca[i].y),
+                            (float)(cc[2] - (double)ca[i].z), 0.f);
+    }
+    return -1;
+}
+
 extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const int32_t *kind,
                               const int32_t *group, const double *em, const double *ep,
                               int32_t n_groups)
@@ -356,36 +393,11 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
     float4 *g2 = (float4 *)malloc(sizeof(float4) * np);
     float4 *nr = (float4 *)malloc(sizeof(float4) * np);
     float4 *cl = (float4 *)malloc(sizeof(float4) * np);
-    for (int i = 0; i < np; ++i) {
-        const double *v = tri + 9 * (size_t)i;
-        double cc[3], e1[3], e2[3], nn[3];
-        for (int k = 0; k < 3; ++k) {
-            cc[k] = (v[k] + v[3 + k] + v[6 + k]) / 3.0;
-            e1[k] = v[3 + k] - v[k];
-            e2[k] = v[6 + k] - v[k];
-        }
-        nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
-        nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
-        nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
-        double a2 = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-        if (!(a2 > 0.0)) {
-            free(ca); free(g0); free(g1); free(g2); free(nr); free(cl);
-            free_mesh(c);
-            return obem_fail(c, OBEM_ERR_ARG, "mesh: cell %d is degenerate", i);
-        }
-        double h2 = 0.0;
-        for (int e = 0; e < 3; ++e) {
-            const double *a = v + 3 * e, *b = v + 3 * ((e + 1) % 3);
-            double d = (a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]);
-            if (d > h2) h2 = d;
-        }
-        ca[i] = make_float4((float)cc[0], (float)cc[1], (float)cc[2], (float)(OBEM_KC * 0.5 * a2));
-        g0[i] = make_float4((float)(v[0] - cc[0]), (float)(v[1] - cc[1]), (float)(v[2] - cc[2]), (float)h2);
-        g1[i] = make_float4((float)(v[3] - cc[0]), (float)(v[4] - cc[1]), (float)(v[5] - cc[2]), 0.f);
-        g2[i] = make_float4((float)(v[6] - cc[0]), (float)(v[7] - cc[1]), (float)(v[8] - cc[2]), 0.f);
-        nr[i] = make_float4((float)(nn[0] / a2), (float)(nn[1] / a2), (float)(nn[2] / a2), (float)kind[i]);
-        cl[i] = make_float4((float)(cc[0] - (double)ca[i].x), (float)(cc[1] - (double)ca[i].y),
-                            (float)(cc[2] - (double)ca[i].z), 0.f);
+    const int bad = obem_cell_layout(tri, kind, np, ca, g0, g1, g2, nr, cl);
+    if (bad >= 0) {
+        free(ca); free(g0); free(g1); free(g2); free(nr); free(cl);
+        free_mesh(c);
+        return obem_fail(c, OBEM_ERR_ARG, "mesh: cell %d is degenerate", bad);
     }
     int rc = OBEM_OK;
     size_t f4 = sizeof(float4) * np;

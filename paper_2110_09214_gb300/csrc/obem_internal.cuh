@@ -82,6 +82,38 @@ struct StepCtl {
     int32_t trial_overflow;
 };
 
+// What differs between the chambers of a batch in the tracking step: Philox
+// key and electrode planes
+struct ChamberP {
+    uint32_t seed_lo, seed_hi;
+    float z_lo, z_hi;
+};
+
+// A batch of chambers as the batched step kernels see it (see SymBatch for the
+// slot layout; blocks of 256 slots belong to one chamber)
+struct StepBatch {
+    int nb;
+    const int32_t *seg_off;      // [nb + 1]
+    const int32_t *blk_cham;     // [seg_off[nb] / 256]
+    int32_t *n;                  // [nb] live charges
+    uint32_t *next_id;           // [nb]
+    const ChamberP *cham;        // [nb]
+    obem_step_stats *stats;      // [nb]
+    StepCtl *ctl;                // [nb]
+    int32_t *abort;              // [1]
+    uint32_t *step;              // [1] step index, advanced when the batch commits
+};
+
+// scratch of the batched step, sized for the batch's slots
+struct BtScratch {
+    unsigned long long *prop, *ionkey;
+    int32_t *keep, *nsp, *blk;
+    float4 *o_pos, *o_vel;
+    uint32_t *o_id, *o_birth;
+    uint8_t *o_sp;
+    int32_t *ph_bucket, *ph_count, *ph_start, *ph_cursor, *ph_sorted, *ph_bsum;
+};
+
 struct obem_ctx {
     obem_config cfg;
     char err[512];
@@ -217,12 +249,61 @@ struct FieldLaunch {
     int add_init;
     // > 0: the charges' field by the approximate N-body method on this grid
     int nn_grid;
+    // batch of chambers: chamber of every block of the block list, and each
+    // chamber's (first cell, cell count) in the concatenated cell arrays
+    const int32_t *block_cham;
+    const int2 *cham_pan;
+};
+// A batch of independent chambers in one concatenated charge state, as the
+// symmetric all-pairs kernels see it (nb == 0: no batch).  Chamber c holds
+// slots [seg_off[c], seg_off[c + 1]) (multiples of OBEM_SEG_ALIGN), its first
+// n[c] live; slot_cham[k] is the chamber of slots [k, k + 1) * OBEM_SEG_ALIGN.
+#define OBEM_SEG_ALIGN 1024
+struct SymBatch {
+    int nb;
+    const int32_t *seg_off;      // [nb + 1]
+    const int32_t *n;            // [nb]
+    const int32_t *slot_cham;    // [seg_off[nb] / OBEM_SEG_ALIGN]
+    const long long *joff, *ioff;   // [nb] offsets (floats) of the chamber's partial sums
+    int32_t *uoff;               // [nb + 1] work units before each chamber (written per launch)
+    int32_t *negtot;             // [nb] negative charges per chamber (written per launch)
 };
 #define OBEM_BINS_PER_AXIS 64
 #define OBEM_NBINS (OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS)
 #define OBEM_SUPER_SHIFT 6                        // super-bin = 4 x 4 x 4 bins
 #define OBEM_NSUPER (OBEM_NBINS >> OBEM_SUPER_SHIFT)
 int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets, cudaStream_t s);
+int obem_launch_step_batch(obem_ctx *c, const obem_state *st, const StepBatch &B, const BtScratch &W,
+                           const float4 *E, cudaStream_t s);
+
+// Field of a batch of chambers at every live slot: the cells of the slot's
+// chamber plus the other charges of its chamber (symmetric all-pairs kernel on
+// the chamber's tiles; one persistent launch for every chamber's work).
+struct FieldBatch {
+    int nb, slots;               // chambers, slots (seg_off[nb])
+    int cut;                     // targets per cell-kernel block, <= 512
+    int max_blocks;              // sum over chambers of ceil(capacity / cut)
+    int cells, charges;          // cell part, all-pairs part
+    float eps2;
+    float3 e_ext;
+    PanelsDev panels;            // concatenated cells of every chamber
+    const float *sigma;
+    const int2 *cham_pan;        // [nb] (first cell, cell count)
+    int2 *blocks;                // [max_blocks] cell-kernel blocks (scratch)
+    int32_t *block_cham, *nblocks;
+    SymBatch sym;
+    float *jpart, *ipart;
+    float4 *sorted;
+    int32_t *perm, *bcnt;
+    float *tileq;
+    int *counter;
+    int sym_grid;
+};
+int obem_launch_field_batch(obem_ctx *ctx, const FieldBatch &F, const float4 *pos_q, float4 *E_out,
+                            cudaStream_t s);
+size_t obem_sym_sizes(int capacity, size_t *ipart_floats);
+int obem_cell_layout(const double *tri, const int32_t *kind, int np, float4 *ca, float4 *g0, float4 *g1,
+                     float4 *g2, float4 *nr, float4 *cl);
 size_t obem_sym_jpart_floats(int capacity);
 size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);

@@ -154,6 +154,13 @@ __device__ __forceinline__ float nu_proc(const GasDev &g, int j, float eps, floa
 }
 
 // ------------------------------------------------------------------ one charge
+__device__ __forceinline__ ChamberP chamber_of(const GasDev &g)
+{
+    ChamberP c;
+    c.seed_lo = g.seed_lo; c.seed_hi = g.seed_hi; c.z_lo = g.z_lo; c.z_hi = g.z_hi;
+    return c;
+}
+
 struct FlightOut {
     int dead, attached, nsp, collisions, trials, overflow;
     int hit_cell;         // cell that absorbed the charge, or -1
@@ -164,7 +171,7 @@ struct FlightOut {
 // Returns 0 when nothing happened (null, or ionisation without the energy),
 // 1 after a collision, 2 when the flight ends (attachment).
 template <bool EMIT>
-__device__ int collide(const GasDev &g, uint32_t id, uint32_t step, uint32_t k, const uint4 &r, float x,
+__device__ int collide(const GasDev &g, const ChamberP &cp, uint32_t id, uint32_t step, uint32_t k, const uint4 &r, float x,
                        float3 &p, float3 &v, uint8_t &sp, FlightOut &fo, float4 *o_pos, float4 *o_vel,
                        uint32_t *o_id, uint32_t *o_birth, uint8_t *o_sp, int sbase, uint32_t id_base)
 {
@@ -222,7 +229,7 @@ __device__ int collide(const GasDev &g, uint32_t id, uint32_t step, uint32_t k, 
                 else { pn.z = next_toward(p.z, d.z); pp.z = next_toward(p.z, -d.z); }
             }
             if (EMIT) {
-                uint4 r2 = philox4x32_10(make_uint4(id, step, k, 1u), g.seed_lo, g.seed_hi);
+                uint4 r2 = philox4x32_10(make_uint4(id, step, k, 1u), cp.seed_lo, cp.seed_hi);
                 float3 di = isotropic(r2.x, r2.y);
                 int slot = sbase + 2 * fo.nsp;
                 o_pos[slot] = make_float4(pn.x, pn.y, pn.z, -(float)OBEM_QE);
@@ -310,7 +317,7 @@ __device__ int seg_hit(const GasDev &g, float3 a, float3 b)
 
 // ballistic flight for time fl under acceleration a (half a in h); returns
 // true when the charge crossed an absorbing plane
-__device__ __forceinline__ bool flight(const GasDev &g, float3 &p, float3 &v, float ax, float ay, float az,
+__device__ __forceinline__ bool flight(const GasDev &g, const ChamberP &cp, float3 &p, float3 &v, float ax, float ay, float az,
                                        float hx, float hy, float hz, float fl)
 {
     {
@@ -322,7 +329,7 @@ __device__ __forceinline__ bool flight(const GasDev &g, float3 &p, float3 &v, fl
     {
         float w = hz * fl; float xx = v.z + w; float y = xx * fl; p.z = p.z + y; float dv = az * fl; v.z = v.z + dv;
     }
-    return p.z <= g.z_lo || p.z >= g.z_hi;
+    return p.z <= cp.z_lo || p.z >= cp.z_hi;
 }
 
 // Flight of charge i over one step under the field E (Euler in the field,
@@ -336,7 +343,7 @@ __device__ __forceinline__ bool flight(const GasDev &g, float3 &p, float3 &v, fl
 // or where it ends beyond a plane z_lo / z_hi.  When EMIT is set,
 // spawned pairs are written to o_* at slots sbase, sbase+1...
 template <bool EMIT>
-__device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, float3 &v, uint8_t &sp,
+__device__ void fly(const GasDev &g, const ChamberP &cp, uint32_t id, uint32_t step, float3 &p, float3 &v, uint8_t &sp,
                     float3 E, FlightOut &fo, float4 *o_pos, float4 *o_vel, uint32_t *o_id,
                     uint32_t *o_birth, uint8_t *o_sp, int sbase, uint32_t id_base)
 {
@@ -346,10 +353,10 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
     const float hx = 0.5f * ax, hy = 0.5f * ay, hz = 0.5f * az;
     if (g.coll_mode == 1) {
         const float3 p0 = p;
-        const bool crossed = flight(g, p, v, ax, ay, az, hx, hy, hz, g.dt);
+        const bool crossed = flight(g, cp, p, v, ax, ay, az, hx, hy, hz, g.dt);
         if (g.hit_on && (fo.hit_cell = seg_hit(g, p0, p)) >= 0) { fo.dead = 1; return; }
         if (crossed) { fo.dead = 1; return; }
-        const uint4 r = philox4x32_10(make_uint4(id, step, 1u, 0u), g.seed_lo, g.seed_hi);
+        const uint4 r = philox4x32_10(make_uint4(id, step, 1u, 0u), cp.seed_lo, cp.seed_hi);
         fo.trials += 1;
         float nu_tot;
         if (s == OBEM_ELECTRON) {
@@ -367,7 +374,7 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
         }
         float pr = nu_tot * g.dt;
         if (!(neg_log_unif(r.x) < pr)) return;
-        collide<EMIT>(g, id, step, 1u, r, unif01(r.y) * nu_tot, p, v, sp, fo, o_pos, o_vel, o_id, o_birth,
+        collide<EMIT>(g, cp, id, step, 1u, r, unif01(r.y) * nu_tot, p, v, sp, fo, o_pos, o_vel, o_id, o_birth,
                       o_sp, sbase, id_base);
         return;
     }
@@ -380,7 +387,7 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
         if (numax > 0.0f) {
             k += 1u;
             if ((int)k > g.trial_cap) { fo.overflow = 1; return; }
-            r = philox4x32_10(make_uint4(id, step, k, 0u), g.seed_lo, g.seed_hi);
+            r = philox4x32_10(make_uint4(id, step, k, 0u), cp.seed_lo, cp.seed_hi);
             tau = neg_log_unif(r.x) / numax;
         } else {
             tau = __int_as_float(0x7f800000);
@@ -388,13 +395,13 @@ __device__ void fly(const GasDev &g, uint32_t id, uint32_t step, float3 &p, floa
         float tn = t + tau;
         float fl = (tn >= g.dt) ? (g.dt - t) : tau;
         const float3 p0 = p;
-        const bool crossed = flight(g, p, v, ax, ay, az, hx, hy, hz, fl);
+        const bool crossed = flight(g, cp, p, v, ax, ay, az, hx, hy, hz, fl);
         if (g.hit_on && (fo.hit_cell = seg_hit(g, p0, p)) >= 0) { fo.dead = 1; return; }
         if (crossed) { fo.dead = 1; return; }
         if (tn >= g.dt) return;
         t = tn;
         fo.trials += 1;
-        if (collide<EMIT>(g, id, step, k, r, unif01(r.y) * numax, p, v, sp, fo, o_pos, o_vel, o_id, o_birth,
+        if (collide<EMIT>(g, cp, id, step, k, r, unif01(r.y) * numax, p, v, sp, fo, o_pos, o_vel, o_id, o_birth,
                           o_sp, sbase, id_base) == 2)
             return;
     }
@@ -613,7 +620,7 @@ count_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, cons
             float4 e = E[i];
             float3 p = make_float3(pq.x, pq.y, pq.z), v = make_float3(vv.x, vv.y, vv.z);
             FlightOut fo = {0, 0, 0, 0, 0, 0, -1};
-            fly<false>(g, st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, NULL, NULL, NULL,
+            fly<false>(g, chamber_of(g), st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, NULL, NULL, NULL,
                        NULL, NULL, 0, 0u);
             if (g.hit_on) hit = fo.hit_cell >= 0 ? (fo.hit_cell << 1) | (pq.w > 0.0f ? 1 : 0) : -1;
             kp = !fo.dead;
@@ -733,7 +740,7 @@ write_kernel(const obem_state st, GasDev g, const float4 *E, uint32_t step, cons
     FlightOut fo = {0, 0, 0, 0, 0, 0, -1};
     const int sbase = ctl->n_keep + 2 * out_spawn;
     const uint32_t id_base = *st.next_id + (uint32_t)(2 * out_spawn);
-    fly<true>(g, st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, o_pos, o_vel, o_id, o_birth,
+    fly<true>(g, chamber_of(g), st.id[i], step, p, v, s, make_float3(e.x, e.y, e.z), fo, o_pos, o_vel, o_id, o_birth,
               o_sp, sbase, id_base);
     if (kp) {
         o_pos[out_keep] = make_float4(p.x, p.y, p.z, pq.w);
@@ -890,5 +897,392 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
     moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats);
     OBEM_LAUNCH(c);
     if (c->prof_on) c->launches += 8 + (g.recomb_on ? 7 : 0) + (g.hit_on ? 1 : 0);
+    return OBEM_OK;
+}
+
+// ====================================================================
+// Batch of independent chambers.  Chamber c holds slots [seg_off[c],
+// seg_off[c + 1]) of one concatenated state (multiples of OBEM_SEG_ALIGN, so
+// each block of ST_THREADS slots belongs to one chamber), its first n[c]
+// live.  The passes of the single step, each one launch for every chamber;
+// a charge meets only charges of its own chamber, and its draws are keyed by
+// its chamber's seed and its own id, so every chamber evolves exactly as it
+// would alone.  The step index is read from the device and advanced by the
+// last pass: the launch sequence can be captured once in a CUDA graph and
+// replayed step after step.  If any chamber fails (capacity, trials), no
+// chamber commits.
+
+// chamber of the block, its first slot, its live charges; slot i's index in it
+struct BtSlot {
+    int c, off, n, li;
+};
+__device__ __forceinline__ BtSlot bt_slot(const StepBatch &B)
+{
+    BtSlot r;
+    r.c = B.blk_cham[blockIdx.x];
+    r.off = B.seg_off[r.c];
+    r.n = B.n[r.c];
+    r.li = blockIdx.x * ST_THREADS + threadIdx.x - r.off;
+    return r;
+}
+
+__global__ void bt_init_kernel(StepBatch B)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *B.abort = 0;
+    if (c >= B.nb) return;
+    memset(&B.stats[c], 0, sizeof(obem_step_stats));
+    memset(&B.ctl[c], 0, sizeof(StepCtl));
+    B.stats[c].n_before = B.n[c];
+}
+
+__device__ __forceinline__ uint32_t bt_hash(long long cx, long long cy, long long cz, int c)
+{
+    return (ph_hash(cx, cy, cz) ^ ((uint32_t)c * 0x9E3779B1u)) & (PH_BUCKETS - 1);
+}
+
+__global__ void bt_ph_count_kernel(const obem_state st, StepBatch B, double inv_h, int32_t *bucket_of, int32_t *count)
+{
+    const BtSlot q = bt_slot(B);
+    if (q.li >= q.n) return;
+    const int i = q.off + q.li;
+    const uint32_t step = *B.step;
+    const uint32_t b = st.birth[i];
+    if (st.species[i] != OBEM_CATION || (b != 0u && b == step)) { bucket_of[i] = -1; return; }
+    long long cx, cy, cz;
+    ph_cell(reinterpret_cast<const float4 *>(st.pos_q)[i], inv_h, cx, cy, cz);
+    const uint32_t h = bt_hash(cx, cy, cz, q.c);
+    bucket_of[i] = (int32_t)h;
+    atomicAdd(&count[h], 1);
+}
+
+__global__ void bt_ph_scatter_kernel(const obem_state st, StepBatch B, const int32_t *bucket_of, int32_t *cursor,
+                                     int32_t *sorted)
+{
+    const BtSlot q = bt_slot(B);
+    if (q.li >= q.n) return;
+    const int i = q.off + q.li;
+    const int32_t h = bucket_of[i];
+    if (h < 0) return;
+    sorted[atomicAdd(&cursor[h], 1)] = i;
+}
+
+// nearest eligible cation of the same chamber (keys carry slots: within a
+// chamber, slot order is index order, so ties resolve as in a single step)
+__global__ void bt_ph_query_kernel(const obem_state st, StepBatch B, GasDev g, double inv_h, const int32_t *start,
+                                   const int32_t *sorted, u64 *prop)
+{
+    const BtSlot q = bt_slot(B);
+    if (q.li >= q.n) return;
+    const int i = q.off + q.li;
+    u64 best = ~0ull;
+    if (st.species[i] == OBEM_ELECTRON) {
+        const float4 pe = reinterpret_cast<const float4 *>(st.pos_q)[i];
+        long long cx, cy, cz;
+        ph_cell(pe, inv_h, cx, cy, cz);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const uint32_t h = bt_hash(cx + dx, cy + dy, cz + dz, q.c);
+                    for (int k = start[h]; k < start[h + 1]; ++k) {
+                        const int c = sorted[k];
+                        if (c < q.off || c >= q.off + q.n) continue;      // another chamber
+                        const float4 pc = reinterpret_cast<const float4 *>(st.pos_q)[c];
+                        const float ex = pe.x - pc.x, ey = pe.y - pc.y, ez = pe.z - pc.z;
+                        const float d2 = ex * ex + ey * ey + ez * ez;
+                        if (!(d2 <= g.rc2)) continue;
+                        const u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)(uint32_t)c;
+                        if (key < best) best = key;
+                    }
+                }
+    }
+    prop[i] = best;
+}
+
+__global__ void bt_resolve_kernel(const obem_state st, StepBatch B, const u64 *prop, u64 *ionkey)
+{
+    const BtSlot q = bt_slot(B);
+    if (q.li >= q.n) return;
+    const int i = q.off + q.li;
+    const u64 pr = prop[i];
+    if (pr == ~0ull || st.species[i] != OBEM_ELECTRON) return;
+    const uint32_t ion = (uint32_t)(pr & 0xFFFFFFFFu);
+    atomicMin(&ionkey[ion], (pr & 0xFFFFFFFF00000000ull) | (u64)(uint32_t)i);
+}
+
+__global__ void __launch_bounds__(ST_THREADS)
+bt_count_kernel(const obem_state st, StepBatch B, GasDev g, const float4 *E, const u64 *prop, const u64 *ionkey,
+                int32_t *keep, int32_t *nsp, int32_t *blk)
+{
+    __shared__ long long sh[ST_THREADS / 32];
+    const BtSlot q = bt_slot(B);
+    const uint32_t step = *B.step;
+    int kp = 0, ns = 0, absorbed = 0, attached = 0, coll = 0, rec = 0, ovf = 0;
+    long long trials = 0;
+    if (q.li < q.n) {
+        const int i = q.off + q.li;
+        const uint8_t s = st.species[i];
+        if (recombined(i, s, prop, ionkey, g.recomb_on)) {
+            rec = (s == OBEM_CATION);
+        } else {
+            const float4 pq = reinterpret_cast<const float4 *>(st.pos_q)[i];
+            const float4 vv = reinterpret_cast<const float4 *>(st.vel)[i];
+            const float4 e = E[i];
+            float3 p = make_float3(pq.x, pq.y, pq.z), v = make_float3(vv.x, vv.y, vv.z);
+            uint8_t sp = s;
+            FlightOut fo = {0, 0, 0, 0, 0, 0, -1};
+            fly<false>(g, B.cham[q.c], st.id[i], step, p, v, sp, make_float3(e.x, e.y, e.z), fo, NULL, NULL, NULL,
+                       NULL, NULL, 0, 0u);
+            kp = !fo.dead;
+            ns = fo.nsp;
+            absorbed = fo.dead;
+            attached = fo.attached;
+            coll = fo.collisions;
+            trials = fo.trials;
+            ovf = fo.overflow;
+        }
+        keep[i] = kp;
+        nsp[i] = ns;
+    }
+    obem_step_stats *stt = &B.stats[q.c];
+    long long t;
+    t = block_sum<long long>(kp, sh);
+    if (threadIdx.x == 0) blk[2 * blockIdx.x] = (int32_t)t;
+    t = block_sum<long long>(ns, sh);
+    if (threadIdx.x == 0) blk[2 * blockIdx.x + 1] = (int32_t)t;
+    t = block_sum<long long>(absorbed, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stt->absorbed, (int)t);
+    t = block_sum<long long>(attached, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stt->attached, (int)t);
+    t = block_sum<long long>(coll, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stt->collisions, (int)t);
+    t = block_sum<long long>(rec, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(&stt->recombined_pairs, (int)t);
+    t = block_sum<long long>(trials, sh);
+    if (threadIdx.x == 0 && t) atomicAdd((unsigned long long *)&stt->trials, (unsigned long long)t);
+    t = block_sum<long long>(ovf, sh);
+    if (threadIdx.x == 0 && t) atomicOr(&B.ctl[q.c].trial_overflow, 1);
+}
+
+// one block per chamber: exclusive scan of its blocks' (keep, spawn) totals,
+// capacity and trial checks
+__global__ void bt_scan_kernel(StepBatch B, int32_t *blk)
+{
+    __shared__ int32_t sk[1024], ss[1024];
+    __shared__ int32_t carry_k, carry_s;
+    const int c = blockIdx.x;
+    const int n = B.n[c];
+    const int b0 = B.seg_off[c] / ST_THREADS;
+    const int nb = (n + ST_THREADS - 1) / ST_THREADS;
+    const int cap = B.seg_off[c + 1] - B.seg_off[c];
+    if (threadIdx.x == 0) { carry_k = 0; carry_s = 0; }
+    __syncthreads();
+    for (int c0 = 0; c0 < nb; c0 += 1024) {
+        const int b = c0 + threadIdx.x;
+        const int vk = b < nb ? blk[2 * (b0 + b)] : 0;
+        const int vs = b < nb ? blk[2 * (b0 + b) + 1] : 0;
+        sk[threadIdx.x] = vk;
+        ss[threadIdx.x] = vs;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int ak = threadIdx.x >= o ? sk[threadIdx.x - o] : 0;
+            const int as = threadIdx.x >= o ? ss[threadIdx.x - o] : 0;
+            __syncthreads();
+            sk[threadIdx.x] += ak;
+            ss[threadIdx.x] += as;
+            __syncthreads();
+        }
+        if (b < nb) {
+            blk[2 * (b0 + b)] = carry_k + sk[threadIdx.x] - vk;
+            blk[2 * (b0 + b) + 1] = carry_s + ss[threadIdx.x] - vs;
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) { carry_k += sk[1023]; carry_s += ss[1023]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        StepCtl *ctl = &B.ctl[c];
+        obem_step_stats *stt = &B.stats[c];
+        const long long total = (long long)carry_k + 2ll * carry_s;
+        ctl->n_keep = carry_k;
+        ctl->n_spawn = carry_s;
+        stt->spawned_pairs = carry_s;
+        stt->required_capacity = total > 0x7fffffff ? 0x7fffffff : (int)total;
+        if (ctl->trial_overflow) {
+            stt->status = OBEM_ERR_TRIALS;
+            atomicOr(B.abort, 1);
+        } else if (total > cap) {
+            stt->status = OBEM_ERR_CAPACITY;
+            atomicOr(B.abort, 1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(ST_THREADS)
+bt_write_kernel(const obem_state st, StepBatch B, GasDev g, const float4 *E, const u64 *prop, const u64 *ionkey,
+                const int32_t *keep, const int32_t *nsp, const int32_t *blk, float4 *o_pos, float4 *o_vel,
+                uint32_t *o_id, uint32_t *o_birth, uint8_t *o_sp)
+{
+    __shared__ int32_t wk[ST_THREADS / 32], ws[ST_THREADS / 32];
+    if (*B.abort) return;
+    const BtSlot q = bt_slot(B);
+    const uint32_t step = *B.step;
+    const int i = q.off + q.li;
+    int kp = 0, ns = 0;
+    if (q.li < q.n) { kp = keep[i]; ns = nsp[i]; }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int ik = kp, is = ns;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, ik, o);
+        const int b = __shfl_up_sync(0xffffffffu, is, o);
+        if (lane >= o) { ik += a; is += b; }
+    }
+    if (lane == 31) { wk[warp] = ik; ws[warp] = is; }
+    __syncthreads();
+    int pk_ = 0, ps_ = 0;
+    for (int w = 0; w < warp; ++w) { pk_ += wk[w]; ps_ += ws[w]; }
+    if (q.li >= q.n || (!kp && !ns)) return;
+    const int out_keep = blk[2 * blockIdx.x] + pk_ + ik - kp;
+    const int out_spawn = blk[2 * blockIdx.x + 1] + ps_ + is - ns;
+    const uint8_t s = st.species[i];
+    const float4 pq = reinterpret_cast<const float4 *>(st.pos_q)[i];
+    const float4 vv = reinterpret_cast<const float4 *>(st.vel)[i];
+    const float4 e = E[i];
+    float3 p = make_float3(pq.x, pq.y, pq.z), v = make_float3(vv.x, vv.y, vv.z);
+    uint8_t sp = s;
+    FlightOut fo = {0, 0, 0, 0, 0, 0, -1};
+    const int sbase = q.off + B.ctl[q.c].n_keep + 2 * out_spawn;
+    const uint32_t id_base = B.next_id[q.c] + (uint32_t)(2 * out_spawn);
+    fly<true>(g, B.cham[q.c], st.id[i], step, p, v, sp, make_float3(e.x, e.y, e.z), fo, o_pos, o_vel, o_id,
+              o_birth, o_sp, sbase, id_base);
+    if (kp) {
+        const int o = q.off + out_keep;
+        o_pos[o] = make_float4(p.x, p.y, p.z, pq.w);
+        o_vel[o] = make_float4(v.x, v.y, v.z, vv.w);
+        o_id[o] = st.id[i];
+        o_birth[o] = st.birth[i];
+        o_sp[o] = sp;                    // after the flight (attachment makes an anion)
+    }
+}
+
+__global__ void bt_commit_kernel(const obem_state st, StepBatch B, const float4 *o_pos, const float4 *o_vel,
+                                 const uint32_t *o_id, const uint32_t *o_birth, const uint8_t *o_sp)
+{
+    if (*B.abort) return;
+    const BtSlot q = bt_slot(B);
+    const StepCtl &ctl = B.ctl[q.c];
+    if (q.li >= ctl.n_keep + 2 * ctl.n_spawn) return;
+    const int i = q.off + q.li;
+    reinterpret_cast<float4 *>(st.pos_q)[i] = o_pos[i];
+    reinterpret_cast<float4 *>(st.vel)[i] = o_vel[i];
+    st.id[i] = o_id[i];
+    st.birth[i] = o_birth[i];
+    st.species[i] = o_sp[i];
+}
+
+// per chamber: new counts (or, when any chamber failed, the chambers that did
+// not fail report OBEM_ERR_STATE: nothing was committed); the step index
+// advances when the batch committed
+__global__ void bt_finish_kernel(StepBatch B)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ab = *B.abort != 0;
+    if (c == 0 && !ab) *B.step += 1u;
+    if (c >= B.nb) return;
+    obem_step_stats *stt = &B.stats[c];
+    if (ab) {
+        if (stt->status == OBEM_OK) stt->status = OBEM_ERR_STATE;
+        stt->n_after = stt->n_before;
+        return;
+    }
+    const StepCtl &ctl = B.ctl[c];
+    B.n[c] = ctl.n_keep + 2 * ctl.n_spawn;
+    B.next_id[c] = B.next_id[c] + (uint32_t)(2 * ctl.n_spawn);
+    stt->n_after = B.n[c];
+}
+
+__global__ void __launch_bounds__(ST_THREADS)
+bt_moments_kernel(const obem_state st, StepBatch B)
+{
+    __shared__ double shd[ST_THREADS / 32];
+    __shared__ long long shl[ST_THREADS / 32];
+    const BtSlot q = bt_slot(B);
+    obem_step_stats *stats = &B.stats[q.c];
+    int ne = 0, nc = 0, na = 0;
+    double se[3] = {0, 0, 0}, s2e[3] = {0, 0, 0}, si[3] = {0, 0, 0}, s2i[3] = {0, 0, 0}, en = 0.0;
+    if (q.li < q.n) {
+        const int i = q.off + q.li;
+        const uint8_t s = st.species[i];
+        const float4 p = reinterpret_cast<const float4 *>(st.pos_q)[i];
+        const double x[3] = {p.x, p.y, p.z};
+        if (s == OBEM_ELECTRON) {
+            ne = 1;
+            for (int c = 0; c < 3; ++c) { se[c] = x[c]; s2e[c] = x[c] * x[c]; }
+            const float4 v = reinterpret_cast<const float4 *>(st.vel)[i];
+            const double v2 = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
+            en = 0.5 * OBEM_ME * v2 / OBEM_QE;
+        } else {
+            if (s == OBEM_CATION) nc = 1; else na = 1;
+            for (int c = 0; c < 3; ++c) { si[c] = x[c]; s2i[c] = x[c] * x[c]; }
+        }
+    }
+    long long t;
+    t = block_sum<long long>(ne, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_electron, (int)t);
+    t = block_sum<long long>(nc, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_cation, (int)t);
+    t = block_sum<long long>(na, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_anion, (int)t);
+    double d;
+    for (int c = 0; c < 3; ++c) {
+        d = block_sum<double>(se[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum_e[c], d);
+        d = block_sum<double>(s2e[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum2_e[c], d);
+        d = block_sum<double>(si[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum_i[c], d);
+        d = block_sum<double>(s2i[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum2_i[c], d);
+    }
+    d = block_sum<double>(en, shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum_energy_e, d);
+}
+
+// The whole batched step on stream s.  Scratch (BtScratch) is sized for the
+// batch's slots; E holds the field at every live slot.
+int obem_launch_step_batch(obem_ctx *c, const obem_state *stp, const StepBatch &B, const BtScratch &W,
+                           const float4 *E, cudaStream_t s)
+{
+    const obem_state st = *stp;
+    const int slots = st.capacity;
+    const int nblk = slots / ST_THREADS;
+    GasDev g = c->gas;
+    g.hit_on = 0;
+    const int cb = (B.nb + 255) / 256;
+    bt_init_kernel<<<cb, 256, 0, s>>>(B);
+    OBEM_LAUNCH(c);
+    if (g.recomb_on) {
+        if (g.rc2 > 0.f) {
+            const double inv_h = 1.0 / (sqrt((double)g.rc2) * (1.0 + 1e-5));
+            OBEM_CUDA(c, cudaMemsetAsync(W.ph_count, 0, sizeof(int32_t) * PH_BUCKETS, s));
+            bt_ph_count_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, inv_h, W.ph_bucket, W.ph_count);
+            ph_blocksum_kernel<<<PH_NBLK, PH_BLK, 0, s>>>(W.ph_count, W.ph_bsum);
+            ph_scan_sums_kernel<<<1, PH_BLK, 0, s>>>(W.ph_bsum);
+            ph_scan_apply_kernel<<<PH_NBLK, PH_BLK, 0, s>>>(W.ph_count, W.ph_bsum, W.ph_start, W.ph_cursor);
+            bt_ph_scatter_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, W.ph_bucket, W.ph_cursor, W.ph_sorted);
+            bt_ph_query_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, g, inv_h, W.ph_start, W.ph_sorted, W.prop);
+            OBEM_LAUNCH(c);
+        } else {
+            OBEM_CUDA(c, cudaMemsetAsync(W.prop, 0xFF, sizeof(u64) * (size_t)slots, s));
+        }
+        OBEM_CUDA(c, cudaMemsetAsync(W.ionkey, 0xFF, sizeof(u64) * (size_t)slots, s));
+        bt_resolve_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, W.prop, W.ionkey);
+        OBEM_LAUNCH(c);
+    }
+    bt_count_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, g, E, W.prop, W.ionkey, W.keep, W.nsp, W.blk);
+    OBEM_LAUNCH(c);
+    bt_scan_kernel<<<B.nb, 1024, 0, s>>>(B, W.blk);
+    OBEM_LAUNCH(c);
+    bt_write_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, g, E, W.prop, W.ionkey, W.keep, W.nsp, W.blk, W.o_pos,
+                                                W.o_vel, W.o_id, W.o_birth, W.o_sp);
+    OBEM_LAUNCH(c);
+    bt_commit_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, W.o_pos, W.o_vel, W.o_id, W.o_birth, W.o_sp);
+    OBEM_LAUNCH(c);
+    bt_finish_kernel<<<cb, 256, 0, s>>>(B);
+    OBEM_LAUNCH(c);
+    bt_moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B);
+    OBEM_LAUNCH(c);
     return OBEM_OK;
 }

@@ -482,6 +482,39 @@ def avalanche_snapshot(rng, n, gap=2e-3, side=1e-2):
     return make_charges(pos[perm], vel[perm], sp[perm])
 
 
+@dataclasses.dataclass
+class Chamber:
+    """One chamber of the batched sweep."""
+    mesh: Mesh
+    charges: Charges
+    trk: Tracking
+    e_kv_cm: float
+    n_plate: int
+
+
+def config_batch(seed=1, n_chambers=256, n_min=100, n_max=100_000, n_plate=(16, 32), side=1e-2):
+    """Batched sweep of independent parallel-plate chambers, uneven sizes.
+    Chamber i draws from its own generator (seed + i): gap ~ U(0.5, 3) mm,
+    field ~ logU(0.1, 30) kV/cm (lower plate 0 V, upper plate E * gap),
+    charges ~ logU(n_min, n_max) as an avalanche-shaped cloud (half electrons,
+    half cations) with z kept inside (2 %, 98 %) of the gap, plates of
+    n x n x 2 triangles each with n ~ U{n_plate}; Philox key 1 + i; argon-like
+    gas (config 2), beta = 1e-7 cm^3/s, dt = 1 ps."""
+    out = []
+    for i in range(n_chambers):
+        rng = np.random.default_rng(seed + i)
+        gap = rng.uniform(0.5e-3, 3e-3)
+        e = 10.0 ** rng.uniform(np.log10(0.1), np.log10(30.0))
+        n = int(round(10.0 ** rng.uniform(np.log10(n_min), np.log10(n_max))))
+        npl = int(rng.integers(n_plate[0], n_plate[1] + 1))
+        mesh = parallel_plates(side, gap, npl, 0.0, e * 1e5 * gap)
+        ch = avalanche_snapshot(rng, n, gap=gap, side=side)
+        ch.pos_q[:, 2] = np.clip(ch.pos_q[:, 2], 0.02 * gap, 0.98 * gap).astype(np.float32)
+        trk = Tracking(dt=1e-12, seed=1 + i, z_lo=0.0, z_hi=gap, beta=1e-13)
+        out.append(Chamber(mesh=mesh, charges=ch, trk=trk, e_kv_cm=e, n_plate=npl))
+    return out
+
+
 def config_gem(seed=1, n=1_000_000, target_panels=60000, geo: GemGeometry | None = None):
     """Single-GEM unit patch meshed into target_panels triangles; n charges
     (half electrons, half cations) in Gaussian clouds (sigma 20 um) on the

@@ -103,6 +103,19 @@ def load():
     lib.obem_surface_charge.argtypes = [P, P, P, I, P]
     lib.obem_fieldmap_eval.argtypes = [P, P, I, P, P]
     lib.obem_stage_times.argtypes = [P, P, P]
+    lib.obem_batch_create.argtypes = [C.POINTER(P), P, I, P, P, P, P]
+    lib.obem_batch_destroy.argtypes = [P]
+    lib.obem_batch_destroy.restype = None
+    lib.obem_batch_layout.argtypes = [P, P]
+    lib.obem_batch_cells.argtypes = [P, I, I, P, P]
+    lib.obem_batch_field_eval.argtypes = [P, C.POINTER(obem_state), P, P]
+    lib.obem_batch_step.argtypes = [P, C.POINTER(obem_state), P, P, P, P]
+    lib.obem_batch_step_graph.argtypes = [P, C.POINTER(obem_state), P, P, P]
+    lib.obem_batch_autotune.argtypes = [P, C.POINTER(obem_state), I, P, P]
+    lib.obem_batch_set_block.argtypes = [P, I]
+    for f in ("obem_batch_create", "obem_batch_layout", "obem_batch_cells", "obem_batch_field_eval",
+              "obem_batch_step", "obem_batch_step_graph", "obem_batch_autotune", "obem_batch_set_block"):
+        getattr(lib, f).restype = C.c_int
     for f in ("obem_create", "obem_gas_load", "obem_mesh_load", "obem_bem_assemble",
               "obem_bem_solve", "obem_bem_solve_adjoint", "obem_field_eval", "obem_field_eval_backward", "obem_step", "obem_profile",
               "obem_stage_times", "obem_alu_rates", "obem_fieldmap_build", "obem_fieldmap_eval",
@@ -437,3 +450,152 @@ def read_stats(stats):
     for k in ("sum_e", "sum2_e", "sum_i", "sum2_i"):
         out[k] = list(out[k])
     return out
+
+
+# ---------------------------------------------------------------- batch of chambers
+class BatchState:
+    """Concatenated charge arrays of a batch of chambers (torch CUDA tensors in
+    the layout of obem_state): chamber c owns slots [seg_off[c], seg_off[c+1]);
+    n and next_id are per-chamber device arrays."""
+
+    def __init__(self, seg_off, device="cuda"):
+        import torch
+        self.seg_off = np.asarray(seg_off, np.int64)
+        self.nb = len(self.seg_off) - 1
+        S = int(self.seg_off[-1])
+        self.capacity = S
+        self.pos_q = torch.zeros((S, 4), dtype=torch.float32, device=device)
+        self.vel = torch.zeros((S, 4), dtype=torch.float32, device=device)
+        self.id = torch.zeros(S, dtype=torch.int32, device=device)
+        self.birth = torch.zeros(S, dtype=torch.int32, device=device)
+        self.species = torch.zeros(S, dtype=torch.uint8, device=device)
+        self.n = torch.zeros(self.nb, dtype=torch.int32, device=device)
+        self.next_id = torch.zeros(self.nb, dtype=torch.int32, device=device)
+
+    def c_struct(self):
+        return obem_state(pos_q=self.pos_q.data_ptr(), vel=self.vel.data_ptr(), id=self.id.data_ptr(),
+                          birth=self.birth.data_ptr(), species=self.species.data_ptr(), n=self.n.data_ptr(),
+                          next_id=self.next_id.data_ptr(), capacity=self.capacity)
+
+    def host_arrays(self, chambers, next_ids=None):
+        """Host copies of the arrays for a list of charge sets (one per chamber)."""
+        S = self.capacity
+        pos = np.zeros((S, 4), np.float32)
+        vel = np.zeros((S, 4), np.float32)
+        ids = np.zeros(S, np.uint32)
+        birth = np.zeros(S, np.uint32)
+        sp = np.zeros(S, np.uint8)
+        n = np.zeros(self.nb, np.int32)
+        nid = np.zeros(self.nb, np.uint32)
+        for c, ch in enumerate(chambers):
+            m = ch.pos_q.shape[0]
+            o = int(self.seg_off[c])
+            if m > self.seg_off[c + 1] - o:
+                raise ValueError("chamber %d: %d charges exceed its segment" % (c, m))
+            pos[o:o + m] = ch.pos_q
+            vel[o:o + m] = ch.vel
+            ids[o:o + m] = ch.id
+            birth[o:o + m] = ch.birth
+            sp[o:o + m] = ch.species
+            n[c] = m
+            nid[c] = m if next_ids is None else next_ids[c]
+        return pos, vel, ids, birth, sp, n, nid
+
+    def upload(self, chambers, next_ids=None):
+        import torch
+        pos, vel, ids, birth, sp, n, nid = self.host_arrays(chambers, next_ids)
+        self.pos_q.copy_(torch.from_numpy(pos))
+        self.vel.copy_(torch.from_numpy(vel))
+        self.id.copy_(torch.from_numpy(ids.view(np.int32)))
+        self.birth.copy_(torch.from_numpy(birth.view(np.int32)))
+        self.species.copy_(torch.from_numpy(sp))
+        self.n.copy_(torch.from_numpy(n))
+        self.next_id.copy_(torch.from_numpy(nid.view(np.int32)))
+
+    def download(self):
+        """Per chamber: (charges, next_id)."""
+        from types import SimpleNamespace
+        n = self.n.cpu().numpy()
+        nid = self.next_id.cpu().numpy().view(np.uint32)
+        pos, vel = self.pos_q.cpu().numpy(), self.vel.cpu().numpy()
+        ids, birth = self.id.cpu().numpy().view(np.uint32), self.birth.cpu().numpy().view(np.uint32)
+        sp = self.species.cpu().numpy()
+        out = []
+        for c in range(self.nb):
+            o, m = int(self.seg_off[c]), int(n[c])
+            out.append((SimpleNamespace(pos_q=pos[o:o + m].copy(), vel=vel[o:o + m].copy(), id=ids[o:o + m].copy(),
+                                        birth=birth[o:o + m].copy(), species=sp[o:o + m].copy(), n=m),
+                        int(nid[c])))
+        return out
+
+
+def new_batch_stats(nb, device="cuda"):
+    import torch
+    return torch.zeros(nb * STATS_BYTES, dtype=torch.uint8, device=device)
+
+
+def read_batch_stats(stats, nb):
+    raw = stats.cpu().numpy().tobytes()
+    out = []
+    for c in range(nb):
+        s = obem_step_stats.from_buffer_copy(raw[c * STATS_BYTES:(c + 1) * STATS_BYTES])
+        d = {f: getattr(s, f) for f, _ in obem_step_stats._fields_}
+        for k in ("sum_e", "sum2_e", "sum_i", "sum2_i"):
+            d[k] = list(d[k])
+        out.append(d)
+    return out
+
+
+class Batch:
+    """obem_batch_* (include/obem.h): chambers stepped together, borrowing ctx
+    (gas and step settings); per chamber capacity, planes and seed."""
+
+    def __init__(self, ctx, capacity, z_lo, z_hi, seed):
+        capacity = _host(capacity, np.int32)
+        self.nb = len(capacity)
+        self.ctx = ctx
+        z_lo, z_hi = _host(z_lo, np.float64), _host(z_hi, np.float64)
+        seed = _host(seed, np.uint64)
+        h = C.c_void_p()
+        _check(ctx, load().obem_batch_create(C.byref(h), ctx, self.nb, capacity.ctypes.data_as(C.c_void_p),
+                                             z_lo.ctypes.data_as(C.c_void_p), z_hi.ctypes.data_as(C.c_void_p),
+                                             seed.ctypes.data_as(C.c_void_p)))
+        self.h = h
+        off = np.zeros(self.nb + 1, np.int64)
+        _check(ctx, load().obem_batch_layout(h, off.ctypes.data_as(C.c_void_p)))
+        self.seg_off = off
+
+    def destroy(self):
+        if self.h:
+            load().obem_batch_destroy(self.h)
+            self.h = None
+
+    def state(self, device="cuda"):
+        return BatchState(self.seg_off, device)
+
+    def cells(self, chamber, tri, sigma):
+        tri = _host(tri, np.float64)
+        sigma = _host(sigma, np.float32)
+        _check(self.ctx, load().obem_batch_cells(self.h, int(chamber), int(tri.shape[0]),
+                                                 tri.ctypes.data_as(C.c_void_p), sigma.ctypes.data_as(C.c_void_p)))
+
+    def field_eval(self, st, E_out, stream=None):
+        _check(self.ctx, load().obem_batch_field_eval(self.h, C.byref(st.c_struct()), _ptr(E_out), _stream(stream)))
+
+    def step(self, st, step, stats, E_in=None, stream=None):
+        """step: device uint32/int32 scalar tensor (advanced on commit)."""
+        _check(self.ctx, load().obem_batch_step(self.h, C.byref(st.c_struct()), _ptr(E_in), _ptr(step), _ptr(stats),
+                                                _stream(stream)))
+
+    def step_graph(self, st, step, stats, stream=None):
+        _check(self.ctx, load().obem_batch_step_graph(self.h, C.byref(st.c_struct()), _ptr(step), _ptr(stats),
+                                                      _stream(stream)))
+
+    def autotune(self, st, reps=3, stream=None):
+        out = np.zeros(4, np.float64)
+        _check(self.ctx, load().obem_batch_autotune(self.h, C.byref(st.c_struct()), int(reps),
+                                                    out.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return {"cells_per_block": int(out[0]), "ms": float(out[1]), "ms_512": float(out[2])}
+
+    def set_block(self, cells_per_block):
+        _check(self.ctx, load().obem_batch_set_block(self.h, int(cells_per_block)))
