@@ -95,6 +95,7 @@ def _args():
     p.add_argument("--no-nn", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-chambers", type=int, default=256)
+    p.add_argument("--batch-only", action="store_true")
     return p.parse_args()
 
 
@@ -654,6 +655,11 @@ def main():
     ws, rank, local = _dist()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.batch_only:
+        # the batched sweep alone (for profiling it): one JSON object
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"batched_sweep": batch_timing("cuda:%d" % local, a.batch_chambers)}))
     else:
         run_ours(a, ws, rank, local)
 
