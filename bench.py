@@ -434,8 +434,11 @@ def nn_timing(ctx, pos_q, dev, soft, grids=(16, 32)):
         ms = e0.elapsed_time(e1)
         rel = (torch.linalg.norm(E[:, :3] - exact[:, :3], dim=1) /
                torch.linalg.norm(exact[:, :3], dim=1).clamp_min(1e-30))
+        bad_nn = int((~torch.isfinite(E[:, :3])).any(dim=1).sum())
+        bad_ex = int((~torch.isfinite(exact[:, :3])).any(dim=1).sum())
         out["grid_%d" % G] = {"ms": ms, "within_5pct": float((rel < 0.05).float().mean()),
-                              "median_rel_err": float(rel.median())}
+                              "median_rel_err": float(rel.nanmedian()),
+                              "non_finite": {"nn": bad_nn, "exact": bad_ex}}
     out["charges"] = n
     out["exact_reference"] = "symmetric all-pairs field, no softening"
     return out

@@ -921,6 +921,14 @@ nbody_kernel(FieldLaunch L)
 #define SY_CH 16
 #define SY_FOLD 8              // rounds (of 32 sources) between compensated folds
 #define SY_DTILE 256           // staged sources of the d = 0 item
+// The kernel works on positions scaled by 2^40 and charges (k_C q) by 2^80:
+// inv = 1/r then carries 2^-40 and inv^3 2^-120, which keeps every product
+// finite down to r ~ 1e-20 m (unscaled, inv^3 overflows below 1.4e-13 m); each
+// k_C q inv^3 d comes out unscaled, the potential k_C q inv carries 2^40.
+// Power-of-two scaling is exact: the results are those of the unscaled sums.
+#define SY_XS 1099511627776.0f               // 2^40
+#define SY_QS 1208925819614629174706176.0f   // 2^80
+#define SY_VS 9.094947017729282e-13f         // 2^-40
 
 struct SymGeom {
     int n, hmax, nch;
@@ -1056,7 +1064,7 @@ __global__ void sym_part_scatter_kernel(const float4 *tgt, const float4 *src, in
         const int negoff = bcnt[blockIdx.x];
         const int lb = blockIdx.x * SP_BLOCK - off;          // the block's first index in the chamber
         const int dst = neg ? negoff + rneg : tot[c] + (lb - negoff) + ((int)threadIdx.x - rneg);
-        sorted[off + dst] = make_float4(p.x, p.y, p.z, q);
+        sorted[off + dst] = make_float4(p.x * SY_XS, p.y * SY_XS, p.z * SY_XS, q);   // positions x 2^40
         perm[off + dst] = i;
     }
 }
@@ -1139,7 +1147,9 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
         units = G0.n * G0.nch;
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float kC = (float)OBEM_KC;
+    // k_C x 2^80 (kCs q is k_C q scaled exactly); L.eps2 comes in the scaled
+    // positions' units (x 2^80) from the launch
+    const float kCs = (float)OBEM_KC * SY_QS;
     const u64 EPS2 = pk(L.eps2, L.eps2);
 
     for (;;) {
@@ -1181,7 +1191,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
             const int i = base + k * SY_THREADS + tid;
             // position from the targets, charge from the sources (the same charges)
             const float4 p = i < lim ? L.targets[i] : make_float4(1e18f, 1e18f, 1e18f, 0.f);
-            const float kq = i < lim ? kC * L.sources[i].w : 0.f;
+            const float kq = i < lim ? kCs * L.sources[i].w : 0.f;
             if (k & 1) {
                 TX[k >> 1] = pk(__uint_as_float((uint32_t)TX[k >> 1]), p.x);
                 TY[k >> 1] = pk(__uint_as_float((uint32_t)TY[k >> 1]), p.y);
@@ -1208,7 +1218,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
                         SrcPk sp;
                         if (j < lim) {
                             const float4 s = L.sources[j];
-                            const float kq = kC * s.w;
+                            const float kq = kCs * s.w;
                             sp.xx = pk(s.x, s.x); sp.yy = pk(s.y, s.y); sp.zz = pk(s.z, s.z); sp.qq = pk(kq, kq);
                         } else {
                             sp.xx = sp.yy = sp.zz = pk(2e18f, 2e18f);
@@ -1243,6 +1253,10 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
                             part[k][3] += s;
                         }
                     }
+                    if (WANT_V) {
+#pragma unroll
+                        for (int k = 0; k < SY_NI; ++k) part[k][3] *= SY_VS;
+                    }
 #pragma unroll
                     for (int k = 0; k < SY_NI; ++k)
 #pragma unroll
@@ -1265,14 +1279,17 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
             // one charge value in each tile: k_C q factored out of the loop
             const float qJ = tileq[off / SY_T + J], qI = tileq[off / SY_T + I];
             const bool uni = qJ == qJ && qI == qI;
-            const float afac = uni ? kC * qJ : 1.f, pfac = uni ? kC * qI : 1.f;
+            // factors applied once per sum: k_C q of the tile (field) when the charge
+            // is factored out, and the potential's 2^-40
+            const float afac = uni ? kCs * qJ : 1.f, pfac = uni ? kCs * qI : 1.f;
+            const float afac_v = uni ? (kCs * qJ) * SY_VS : SY_VS, pfac_v = uni ? (kCs * qI) * SY_VS : SY_VS;
             auto rounds = [&](auto uni_c) {
             constexpr bool UNI = decltype(uni_c)::value;
             for (int r = 0; r < SY_NG; ++r) {
                 const int grp = (r + (SY_NG / SY_WARPS) * warp) % SY_NG;   // distinct per warp in a round
                 const int j0 = jb + grp * 32;
                 float4 sj = j0 + lane < lim ? L.sources[j0 + lane] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
-                float jx = sj.x, jy = sj.y, jz = sj.z, jq = UNI ? 0.f : kC * sj.w;
+                float jx = sj.x, jy = sj.y, jz = sj.z, jq = UNI ? 0.f : kCs * sj.w;
                 float ax = 0.f, ay = 0.f, az = 0.f, av = 0.f;
                 for (int s = 0; s < 32; ++s) {
                     const u64 JX = pk(jx, jx), JY = pk(jy, jy), JZ = pk(jz, jz), JQ = pk(jq, jq);
@@ -1318,7 +1335,8 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
                     az = __shfl_sync(0xffffffffu, az, src);
                     if (WANT_V) av = __shfl_sync(0xffffffffu, av, src);
                 }
-                if (UNI) { ax *= pfac; ay *= pfac; az *= pfac; av *= pfac; }
+                if (UNI) { ax *= pfac; ay *= pfac; az *= pfac; }
+                if (WANT_V) av *= pfac_v;
                 // after 32 passes the sums are back with their source: add this warp's part
                 {
                     const int jl = grp * 32 + lane;
@@ -1341,7 +1359,8 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
                         float sv, cv;
 #define SY_FOLD1(Acc, c)                                                                   \
     upk(Acc[p], a, b);                                                                     \
-    if (UNI) { a *= afac; b *= afac; }                                                     \
+    if (c == NC - 1 && WANT_V) { a *= afac_v; b *= afac_v; }                               \
+    else if (UNI) { a *= afac; b *= afac; }                                                \
     sv = s_S[c][2 * p][tid]; cv = s_C[c][2 * p][tid]; two_sum_acc(sv, cv, a);              \
     s_S[c][2 * p][tid] = sv; s_C[c][2 * p][tid] = cv;                                      \
     sv = s_S[c][2 * p + 1][tid]; cv = s_C[c][2 * p + 1][tid]; two_sum_acc(sv, cv, b);      \
@@ -1543,6 +1562,7 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             FieldLaunch Ls = L;
             Ls.targets = ctx->sym_sorted;
             Ls.sources = ctx->sym_sorted;
+            Ls.eps2 = L.eps2 * SY_QS;                    // the sorted copy's positions are x 2^40
             OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
             const dim3 sg(ctx->sym_grid);
             if (L.want_v)
@@ -1671,6 +1691,7 @@ int obem_launch_field_batch(obem_ctx *ctx, const FieldBatch &F, const float4 *po
         FieldLaunch Ls = L;
         Ls.targets = F.sorted;
         Ls.sources = F.sorted;
+        Ls.eps2 = L.eps2 * SY_QS;                        // the sorted copy's positions are x 2^40
         OBEM_CUDA(ctx, cudaMemsetAsync(F.counter, 0, sizeof(int), s));
         nbsym_kernel<false, true><<<F.sym_grid, SY_THREADS, sym_smem(3), s>>>(Ls, F.jpart, F.ipart, F.counter, F.tileq,
                                                                        F.sym);
