@@ -99,6 +99,18 @@ def _args():
     return p.parse_args()
 
 
+def reduce_over_ranks(ms, counts, device):
+    """Whole-job figures of N replicas: the slowest rank's timed region (max)
+    and the work of all ranks (sum), over the initialised process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([float(c) for c in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(tot)
+    return float(t.item()), [float(x) for x in tot.tolist()]
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -308,17 +320,10 @@ def run_ours(a, ws, rank, local):
     electron_steps = float(sum(e_counts))
     pairs = prof["charge_pairs"]
     cell_evals = prof["cells_1pt"] + prof["cells_3pt"] + prof["cells_7pt"] + prof["cells_closed"]
+    charge_steps, pair_evals = float(sum(c_counts)), float(pairs + cell_evals)
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([electron_steps, float(sum(c_counts)), float(pairs + cell_evals)],
-                           dtype=torch.float64, device=dev)
-        dist.all_reduce(tot)
-        electron_steps, charge_steps, pair_evals = [float(x) for x in tot.tolist()]
-    else:
-        charge_steps, pair_evals = float(sum(c_counts)), float(pairs + cell_evals)
+        ms, (electron_steps, charge_steps, pair_evals) = reduce_over_ranks(
+            ms, [electron_steps, charge_steps, pair_evals], dev)
     sec = ms / 1e3
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
