@@ -1432,8 +1432,13 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
 #pragma unroll
         for (int c = 0; c < NC; ++c) e[c] += (double)ip[(2 * c) * SY_T + w] + (double)ip[(2 * c + 1) * SY_T + w];
     }
-    // the items (I, d) with I + d = T (mod n): four loads in flight per round
+    // the items (I, d) with I + d = T (mod n): four loads in flight per round,
+    // added in order into compensated binary32 sums (TwoSum: ~2^-48 relative,
+    // like FP64, on the FP32 pipe; GB300's FP64 pipe would take ~5 ms here)
     constexpr int FU = 4;
+    float js[NC], jc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) { js[c] = 0.f; jc[c] = 0.f; }
     for (int d0 = 1; d0 <= G.hmax; d0 += FU) {
         float v[FU][NC];
 #pragma unroll
@@ -1448,8 +1453,10 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
 #pragma unroll
         for (int u = 0; u < FU; ++u)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) e[c] += (c < 3 ? -1.0 : 1.0) * (double)v[u][c];
+            for (int c = 0; c < NC; ++c) two_sum_acc(js[c], jc[c], c < 3 ? -v[u][c] : v[u][c]);
     }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) e[c] += (double)js[c] + (double)jc[c];
     L.E_out[o] = make_float4((float)e[0], (float)e[1], (float)e[2], WANT_V ? (float)e[3] : 0.f);
 }
 
