@@ -149,13 +149,104 @@ __global__ void block_list_kernel(const int32_t *start, int nt_host, const int32
     if (threadIdx.x == 1023) nblocks[0] = part[1023];
 }
 
-__global__ void bin_scatter_kernel(FieldLaunch L, const uint32_t *code, int32_t *hist, int32_t *perm)
+// Target order of the cell kernels: a stable LSD radix sort of the bin codes
+// (three passes of 6-bit digits over the 18-bit Morton code), so that each
+// bin's targets keep their index order.  The order, hence every block's
+// membership and every sum, is the same on every run (an atomic scatter would
+// order each bin by the race).
+#define RS_RADIX 64
+#define RS_BLOCK 1024
+int obem_binsort_blocks(int capacity) { return (capacity + RS_BLOCK - 1) / RS_BLOCK; }
+
+// digit counts of each block of RS_BLOCK keys: rh[digit * nblk + block]
+__global__ void rs_hist_kernel(const uint32_t *key, int nt, const int32_t *nt_dev, int shift, int nblk, int32_t *rh)
 {
-    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nt) return;
-    int pos = atomicAdd(&hist[code[i]], 1);
-    perm[pos] = i;
+    __shared__ int32_t h[RS_RADIX];
+    const int n = nt_dev ? *nt_dev : nt;
+    if (threadIdx.x < RS_RADIX) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * RS_BLOCK + threadIdx.x;
+    if (i < n) atomicAdd(&h[(key[i] >> shift) & (RS_RADIX - 1)], 1);
+    __syncthreads();
+    if (threadIdx.x < RS_RADIX) rh[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of m counts in place (one block of 1024 threads)
+__global__ void rs_scan_kernel(int32_t *a, int m)
+{
+    __shared__ int32_t part[1024];
+    const int per = (m + 1023) / 1024, q0 = threadIdx.x * per;
+    int32_t sum = 0;
+    for (int q = 0; q < per; ++q)
+        if (q0 + q < m) sum += a[q0 + q];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - sum;
+    for (int q = 0; q < per; ++q)
+        if (q0 + q < m) {
+            const int32_t v = a[q0 + q];
+            a[q0 + q] = run;
+            run += v;
+        }
+}
+
+// stable scatter by digit: within a block, rank = earlier keys of the same
+// digit (warps in order, lanes in order); vin NULL: the values are the indices
+__global__ void __launch_bounds__(RS_BLOCK) rs_scatter_kernel(const uint32_t *kin, const int32_t *vin, uint32_t *kout,
+                                                              int32_t *vout, int nt, const int32_t *nt_dev, int shift,
+                                                              int nblk, const int32_t *rh)
+{
+    __shared__ int32_t wc[RS_BLOCK / 32][RS_RADIX];
+    const int n = nt_dev ? *nt_dev : nt;
+    const int i = blockIdx.x * RS_BLOCK + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < (RS_BLOCK / 32) * RS_RADIX; q += RS_BLOCK) (&wc[0][0])[q] = 0;
+    __syncthreads();
+    const bool live = i < n;
+    const uint32_t k = live ? kin[i] : 0u;
+    const int32_t v = live ? (vin ? vin[i] : i) : 0;
+    const int dg = (int)((k >> shift) & (RS_RADIX - 1));
+    const unsigned peers = __match_any_sync(0xffffffffu, live ? dg : RS_RADIX);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (live && rank == 0) wc[warp][dg] = __popc(peers);
+    __syncthreads();
+    if (threadIdx.x < RS_RADIX) {
+        int32_t run = 0;
+        for (int w = 0; w < RS_BLOCK / 32; ++w) {
+            const int32_t c = wc[w][threadIdx.x];
+            wc[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (live) {
+        const int dst = rh[dg * nblk + blockIdx.x] + wc[warp][dg] + rank;
+        kout[dst] = k;
+        vout[dst] = v;
+    }
+}
+
+// perm = target indices sorted by code, index order within a code; code is
+// overwritten; tk / tv scratch of capacity entries, rh of RS_RADIX * nblk + 1
+static void binsort(const uint32_t *code_in, uint32_t *code, int32_t *perm, uint32_t *tk, int32_t *tv, int32_t *rh,
+                    int nt, const int32_t *nt_dev, int capacity, cudaStream_t s)
+{
+    const int nblk = obem_binsort_blocks(capacity);
+    const uint32_t *kin[3] = {code_in, tk, code};
+    const int32_t *vin[3] = {NULL, perm, tv};
+    uint32_t *kout[3] = {tk, code, tk};
+    int32_t *vout[3] = {perm, tv, perm};
+    for (int p = 0; p < 3; ++p) {
+        rs_hist_kernel<<<nblk, RS_BLOCK, 0, s>>>(kin[p], nt, nt_dev, 6 * p, nblk, rh);
+        rs_scan_kernel<<<1, 1024, 0, s>>>(rh, RS_RADIX * nblk);
+        rs_scatter_kernel<<<nblk, RS_BLOCK, 0, s>>>(kin[p], vin[p], kout[p], vout[p], nt, nt_dev, 6 * p, nblk, rh);
+    }
 }
 
 // ---------------------------------------------------------------- cell field kernels
@@ -1514,9 +1605,10 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             bin_count_kernel<<<nb, 256, 0, s>>>(L, lo, sc, ctx->s_code, ctx->s_hist);
             bin_scan_kernel<<<1, 1024, 0, s>>>(ctx->s_hist);
             block_list_kernel<<<1, 1024, 0, s>>>(ctx->s_hist, L.nt, L.nt_dev, (int2 *)L.blocks, (int32_t *)L.nblocks);
-            bin_scatter_kernel<<<nb, 256, 0, s>>>(L, ctx->s_code, ctx->s_hist, (int32_t *)L.perm);
+            binsort(ctx->s_code, ctx->s_code, (int32_t *)L.perm, ctx->s_tk, ctx->s_tv, ctx->s_rh, L.nt, L.nt_dev,
+                    capacity_targets, s);
             OBEM_LAUNCH(ctx);
-            if (L.events) ctx->launches += 4;
+            if (L.events) ctx->launches += 12;
         }
         const int nsuper = capacity_targets < OBEM_NSUPER ? capacity_targets : OBEM_NSUPER;
         dim3 cgrid((capacity_targets + CT_BLOCK - 1) / CT_BLOCK + (L.blocks ? nsuper : 0));
@@ -1736,8 +1828,11 @@ constexpr size_t NA_HIST_BYTES = na_align(sizeof(int32_t) * (size_t)OBEM_NBINS);
 constexpr size_t NA_NBLK = (size_t)NA_MAX_TARGETS / 512 + 2 + OBEM_NSUPER;
 constexpr size_t NA_BLOCKS_BYTES = na_align(sizeof(int2) * NA_NBLK);
 constexpr size_t NA_MISC_BYTES = 256;   // number of blocks, bounding box
+constexpr size_t NA_TK_BYTES = na_align(sizeof(uint32_t) * (size_t)NA_MAX_TARGETS);    // bin sort scratch
+constexpr size_t NA_TV_BYTES = na_align(sizeof(int32_t) * (size_t)NA_MAX_TARGETS);
+constexpr size_t NA_RH_BYTES = na_align(sizeof(int32_t) * (64 * ((size_t)NA_MAX_TARGETS / 1024 + 1) + 1));
 constexpr size_t NA_BYTES = NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES + NA_HIST_BYTES + NA_BLOCKS_BYTES +
-                            NA_MISC_BYTES;
+                            NA_MISC_BYTES + NA_TK_BYTES + NA_TV_BYTES + NA_RH_BYTES;
 }  // namespace
 
 // The scratch of obem_field_eval_noalloc (about 5 MB); every GPU that loads
@@ -1877,6 +1972,11 @@ extern "C" int obem_field_eval_noalloc(const float *targets, int32_t nt, const f
     int32_t *hist = (int32_t *)(b + NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES);
     int2 *blocks = (int2 *)(b + NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES + NA_HIST_BYTES);
     int32_t *nblocks = (int32_t *)(b + NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES + NA_HIST_BYTES + NA_BLOCKS_BYTES);
+    unsigned char *b2 = b + NA_CELLS_BYTES + NA_CODE_BYTES + NA_PERM_BYTES + NA_HIST_BYTES + NA_BLOCKS_BYTES +
+                        NA_MISC_BYTES;
+    uint32_t *na_tk = (uint32_t *)b2;
+    int32_t *na_tv = (int32_t *)(b2 + NA_TK_BYTES);
+    int32_t *na_rh = (int32_t *)(b2 + NA_TK_BYTES + NA_TV_BYTES);
     float *box = (float *)(nblocks + 16);
     cudaStream_t s = (cudaStream_t)stream;
 
@@ -1915,7 +2015,7 @@ extern "C" int obem_field_eval_noalloc(const float *targets, int32_t nt, const f
         na_bin_count_kernel<<<nb, 256, 0, s>>>(L, box, code, hist);
         bin_scan_kernel<<<1, 1024, 0, s>>>(hist);
         block_list_kernel<<<1, 1024, 0, s>>>(hist, nt, NULL, blocks, nblocks);
-        bin_scatter_kernel<<<nb, 256, 0, s>>>(L, code, hist, perm);
+        binsort(code, code, perm, na_tk, na_tv, na_rh, nt, NULL, nt, s);
         const int nsuper = nt < OBEM_NSUPER ? nt : OBEM_NSUPER;
         dim3 cgrid((nt + CT_BLOCK - 1) / CT_BLOCK + nsuper);
         near_closed_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L);

@@ -98,6 +98,9 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->o_sp, cap);
     ALLOC(c->s_code, sizeof(uint32_t) * cap);
     ALLOC(c->s_perm, sizeof(int32_t) * cap);
+    ALLOC(c->s_tk, sizeof(uint32_t) * cap);
+    ALLOC(c->s_tv, sizeof(int32_t) * cap);
+    ALLOC(c->s_rh, sizeof(int32_t) * (64 * (size_t)obem_binsort_blocks(cap) + 1));
     ALLOC(c->s_hist, sizeof(int32_t) * OBEM_NBINS);
     ALLOC(c->s_blocks, sizeof(int2) * ((size_t)cap / 512 + 2 + (cap < OBEM_NSUPER ? cap : OBEM_NSUPER)));
     ALLOC(c->s_nblocks, sizeof(int32_t) * (OBEM_NSUPER + 8));
@@ -159,6 +162,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->s_nsp); free_dev(c->s_blk); free_dev(c->s_ctl); free_dev(c->o_pos);
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
+    free_dev(c->s_tk); free_dev(c->s_tv); free_dev(c->s_rh);
     free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
     free_dev(c->sym_sorted); free_dev(c->sym_perm); free_dev(c->sym_bcnt); free_dev(c->sym_tileq);
     free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted); free_dev(c->ph_bsum);

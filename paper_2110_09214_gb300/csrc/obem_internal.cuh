@@ -186,6 +186,8 @@ struct obem_ctx {
     int32_t *nn_cell, *nn_sorted, *nn_count, *nn_start, *nn_cursor;
     float4 *nn_agg;
     int *sym_counter;
+    uint32_t *s_tk;          // stable bin sort scratch: keys, values, digit counts
+    int32_t *s_tv, *s_rh;
     float4 *sym_sorted;      // charges ordered by charge value (negative first)
     int32_t *sym_perm;       // sorted slot -> state index
     int32_t *sym_bcnt;       // per-block counts / offsets of the partition
@@ -308,6 +310,7 @@ size_t obem_sym_jpart_floats(int capacity);
 size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);
 int obem_sym_part_blocks(int capacity);
+int obem_binsort_blocks(int capacity);
 int obem_sym_tiles(int capacity);
 
 // nn.cu

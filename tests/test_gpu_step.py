@@ -390,3 +390,91 @@ def test_swarm_parameters_agree_within_3_sigma():
         se = math.sqrt(g_.var(ddof=1) / len(g_) + o_.var(ddof=1) / len(o_))
         assert abs(g_.mean() - o_.mean()) <= 3 * se + 1e-12 * abs(o_.mean()), (g_, o_)
     assert np.all(G[0] > 0)
+
+
+def test_checkpoint_resume_bit_identical():
+    """Checkpoint / resume: the charge arrays, next_id and the step index are
+    the whole state (draws are keyed by id and step).  Six fused steps (cells
+    + all-pairs field evaluated inside obem_step, ionisation, recombination)
+    equal three steps, a host copy of the state, a new context loaded with it,
+    and three more steps -- bit for bit."""
+    mesh, gas, _, trk = inputs.config_avalanche(seed=4, e_kv_cm=30.0, n_seed=100, n_plate=8)
+    ch = _hot_mixture(4)
+    trk.softening = 1e-7
+    flags = obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD
+
+    def run(steps, start, state, nid):
+        g = GpuRun(gas, trk, 16384, flags=flags, mesh=mesh)
+        try:
+            g.solve()
+            g.upload(state, nid)
+            for s in range(start, start + steps):
+                assert g.step(s)["status"] == 0
+            return g.state()
+        finally:
+            g.close()
+
+    full, nid_full = run(6, 0, ch, ch.n)
+    half, nid_half = run(3, 0, ch, ch.n)
+    resumed, nid_res = run(3, 3, half, nid_half)
+    _assert_same_state(full, resumed)
+    assert nid_full == nid_res and full.n > ch.n
+
+
+def test_batch_checkpoint_resume_bit_identical():
+    """The same for a batch of chambers: the concatenated arrays, per-chamber
+    n / next_id and the device step index, saved to the host after two steps
+    and loaded into a new batch, continue exactly as the uninterrupted run."""
+    gas = inputs.argon_like_gas()
+    chs = []
+    for k, gap in enumerate([1e-3, 2e-3, 1.5e-3]):
+        mesh = inputs.parallel_plates(1e-2, gap, 4, 0.0, 25.0 * 1e5 * gap)
+        rng = np.random.default_rng(30 + k)
+        c = inputs.avalanche_snapshot(rng, [300, 1200, 50][k], gap=gap)
+        c.pos_q[:, 2] = np.clip(c.pos_q[:, 2], 0.05 * gap, 0.95 * gap).astype(np.float32)
+        chs.append((mesh, c, gap, oracle.bem_solve(mesh).astype(np.float32)))
+    ctx = obem.obem_create(capacity=16, dt=1e-12, softening=1e-7, beta=1e-13,
+                           flags=obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD)
+    obem.obem_gas_load(ctx, gas)
+
+    def batch():
+        b = obem.Batch(ctx, [4096] * 3, [0.0] * 3, [c[2] for c in chs], [11, 12, 13])
+        for k, c in enumerate(chs):
+            b.cells(k, c[0].tri, c[3])
+        return b
+
+    def steps(b, st, step, n):
+        stats = obem.new_batch_stats(3)
+        for _ in range(n):
+            b.step_graph(st, step, stats)
+        torch.cuda.synchronize()
+        assert all(g["status"] == 0 for g in obem.read_batch_stats(stats, 3))
+
+    try:
+        b1 = batch()
+        st1 = b1.state()
+        st1.upload([c[1] for c in chs])
+        s1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+        steps(b1, st1, s1, 4)
+        full = st1.download()
+        b1.destroy()
+        b2 = batch()
+        st2 = b2.state()
+        st2.upload([c[1] for c in chs])
+        s2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+        steps(b2, st2, s2, 2)
+        ckpt = st2.download(), int(s2.item())                 # host checkpoint
+        b2.destroy()
+        b3 = batch()
+        st3 = b3.state()
+        st3.upload([x[0] for x in ckpt[0]], next_ids=[x[1] for x in ckpt[0]])
+        s3 = torch.full((1,), ckpt[1], dtype=torch.int32, device="cuda")
+        steps(b3, st3, s3, 2)
+        res = st3.download()
+        b3.destroy()
+    finally:
+        obem.obem_destroy(ctx)
+    assert int(s3.item()) == 4
+    for k in range(3):
+        _assert_same_state(full[k][0], res[k][0])
+        assert full[k][1] == res[k][1]
