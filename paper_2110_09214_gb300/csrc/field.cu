@@ -1381,10 +1381,11 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
                 const int j0 = jb + grp * 32;
                 float4 sj = j0 + lane < lim ? L.sources[j0 + lane] : make_float4(2e18f, 2e18f, 2e18f, 0.f);
                 float jx = sj.x, jy = sj.y, jz = sj.z, jq = UNI ? 0.f : kCs * sj.w;
-                float ax = 0.f, ay = 0.f, az = 0.f, av = 0.f;
+                // the source's reaction sums travel with it as f32x2 packs (the two
+                // halves are added once it is back): the FMAs accumulate into them
+                u64 PX = 0ull, PY = 0ull, PZ = 0ull, PV = 0ull;
                 for (int s = 0; s < 32; ++s) {
                     const u64 JX = pk(jx, jx), JY = pk(jy, jy), JZ = pk(jz, jz), JQ = pk(jq, jq);
-                    u64 PX = 0ull, PY = 0ull, PZ = 0ull, PV = 0ull;
 #pragma unroll
                     for (int p = 0; p < SY_NP; ++p) {
                         const u64 dx = sub2(TX[p], JX);
@@ -1410,21 +1411,24 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
                             PV = UNI ? add2(PV, inv) : fma2(QI[p], inv, PV);
                         }
                     }
-                    float a, b;
-                    upk(PX, a, b); ax += a + b;
-                    upk(PY, a, b); ay += a + b;
-                    upk(PZ, a, b); az += a + b;
-                    if (WANT_V) { upk(PV, a, b); av += a + b; }
                     // pass the source and its sums to the next lane
                     const int src = (lane + 1) & 31;
                     jx = __shfl_sync(0xffffffffu, jx, src);
                     jy = __shfl_sync(0xffffffffu, jy, src);
                     jz = __shfl_sync(0xffffffffu, jz, src);
                     if (!UNI) jq = __shfl_sync(0xffffffffu, jq, src);
-                    ax = __shfl_sync(0xffffffffu, ax, src);
-                    ay = __shfl_sync(0xffffffffu, ay, src);
-                    az = __shfl_sync(0xffffffffu, az, src);
-                    if (WANT_V) av = __shfl_sync(0xffffffffu, av, src);
+                    PX = __shfl_sync(0xffffffffu, PX, src);
+                    PY = __shfl_sync(0xffffffffu, PY, src);
+                    PZ = __shfl_sync(0xffffffffu, PZ, src);
+                    if (WANT_V) PV = __shfl_sync(0xffffffffu, PV, src);
+                }
+                float ax, ay, az, av = 0.f;
+                {
+                    float a, b;
+                    upk(PX, a, b); ax = a + b;
+                    upk(PY, a, b); ay = a + b;
+                    upk(PZ, a, b); az = a + b;
+                    if (WANT_V) { upk(PV, a, b); av = a + b; }
                 }
                 if (UNI) { ax *= pfac; ay *= pfac; az *= pfac; }
                 if (WANT_V) av *= pfac_v;
