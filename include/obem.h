@@ -341,7 +341,8 @@ int obem_alu_rates(obem_ctx *ctx, double *out, obem_stream stream);
  *   ms[3] whole obem_step, ms[4] the near-cell kernel alone (part of ms[0]);
  *   counts[0] steps recorded, counts[1] kernels launched by those steps,
  *   counts[2] charge pairs of the all-pairs kernel,
- *   counts[3..6] cell evaluations by tier (centroid, 3-point, 7-point, closed form).
+ *   counts[3..6] cell evaluations by tier (centroid, 3 to 6 points, 7 or more
+ *   points including the near-cell rule, closed form).
  * Recording is then reset.  obem_profile(ctx, 0) stops recording. */
 #define OBEM_PROFILE_TIMES 2
 int obem_profile(obem_ctx *ctx, int32_t enable);
