@@ -332,14 +332,19 @@ __device__ __forceinline__ void block_cells(const FieldLaunch &L, int &poff, int
 
 // Targets of this block (binned order, absolute coordinates) and its frame.
 // Target slot k of thread t is base + k * CT_THREADS + t.
+// CONTIG: warp w holds the block's targets w * 32 * CT_TPT ... (consecutive in
+// the binned order, so each warp's box is compact) and wlo / whi get it.
+template <bool CONTIG = false>
 __device__ __forceinline__ void block_targets(const FieldLaunch &L, int end, int base, float *tx, float *ty,
-                                              float *tz, int *ti, BlockFrame &F)
+                                              float *tz, int *ti, BlockFrame &F, float3 *wlo = NULL,
+                                              float3 *whi = NULL)
 {
     __shared__ float red[6][CT_THREADS / 32];
     float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
 #pragma unroll
     for (int k = 0; k < CT_TPT; ++k) {
-        int i = base + k * CT_THREADS + threadIdx.x;
+        int i = CONTIG ? base + (int)(threadIdx.x & ~31u) * CT_TPT + k * 32 + (int)(threadIdx.x & 31u)
+                       : base + k * CT_THREADS + threadIdx.x;
         int ic = i < end ? i : (end - 1);
         ti[k] = L.perm ? L.perm[ic] : ic;
         float4 p = L.targets[ti[k]];
@@ -354,6 +359,10 @@ __device__ __forceinline__ void block_targets(const FieldLaunch &L, int end, int
             mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], q));
             mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], q));
         }
+    if (CONTIG) {
+        *wlo = make_float3(mn[0], mn[1], mn[2]);
+        *whi = make_float3(mx[0], mx[1], mx[2]);
+    }
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
         for (int c = 0; c < 3; ++c) { red[c][w] = mn[c]; red[3 + c][w] = mx[c]; }
@@ -542,6 +551,7 @@ near_quad_kernel(FieldLaunch L)
     __shared__ int s_list[NEAR_CHUNK];
     __shared__ int s_cnt[CT_THREADS / 32];
     __shared__ SrcPk s_off[NQ_CELLS][NQ_PTS];                // offsets from the centroid, weight
+    __shared__ SrcPk s_off28[NQ_CELLS][28];                   // the same cells' 28-point rule
     __shared__ float4 s_cell[NQ_CELLS][2];                    // (c_hi, h^2), (c_lo, 0)
     const int nt = L.nt_dev ? *L.nt_dev : L.nt;
     int base, end;
@@ -550,10 +560,11 @@ near_quad_kernel(FieldLaunch L)
     float tx[CT_TPT], ty[CT_TPT], tz[CT_TPT];
     int ti[CT_TPT];
     BlockFrame F;
-    block_targets(L, end, base, tx, ty, tz, ti, F);
+    float3 wlo, whi;                       // this warp's box: its targets are consecutive
+    block_targets<true>(L, end, base, tx, ty, tz, ti, F, &wlo, &whi);
     int poff, np;
     block_cells(L, poff, np);
-    const bool warp_live = base + (int)(threadIdx.x & ~31u) < end;
+    const bool warp_live = base + (int)(threadIdx.x & ~31u) * CT_TPT < end;
     float S[CT_TPT][4], C[CT_TPT][4];
 #pragma unroll
     for (int k = 0; k < CT_TPT; ++k) {
@@ -576,19 +587,22 @@ near_quad_kernel(FieldLaunch L)
         for (int g = 0; g < tot; g += NQ_CELLS) {
             const int ng = min(NQ_CELLS, tot - g);
             __syncthreads();
-            // quadrature offsets of the group's cells, 112 points each
-            for (int t = tid; t < ng * NQ_PTS; t += CT_THREADS) {
-                const int c = t / NQ_PTS, k = t % NQ_PTS;
+            // quadrature offsets of the group's cells: 112 and 28 points each
+            for (int t = tid; t < ng * (NQ_PTS + 28); t += CT_THREADS) {
+                const int c = t / (NQ_PTS + 28), kk = t % (NQ_PTS + 28);
+                const bool fine = kk < NQ_PTS;
+                const int k = fine ? kk : kk - NQ_PTS;
                 const int j = s_list[g + c];
                 const float4 g0 = L.panels.g0_h[j], g1 = L.panels.g1[j], g2 = L.panels.g2[j];
                 float3 off;
                 float wf;
-                rule_point(2, k, make_float3(g0.x, g0.y, g0.z), make_float3(g1.x, g1.y, g1.z),
+                rule_point(fine ? 2 : 1, k, make_float3(g0.x, g0.y, g0.z), make_float3(g1.x, g1.y, g1.z),
                            make_float3(g2.x, g2.y, g2.z), off, wf);
                 const float w = L.panels.c_a[j].w * L.sigma[j] * wf;
                 SrcPk sp;
                 sp.xx = pk(off.x, off.x); sp.yy = pk(off.y, off.y); sp.zz = pk(off.z, off.z); sp.qq = pk(w, w);
-                s_off[c][k] = sp;
+                if (fine) s_off[c][k] = sp;
+                else s_off28[c][k] = sp;
                 if (k == 0) {
                     const float4 ca = L.panels.c_a[j], cl = L.panels.c_lo[j];
                     s_cell[c][0] = make_float4(ca.x, ca.y, ca.z, g0.w);
@@ -601,6 +615,11 @@ near_quad_kernel(FieldLaunch L)
             for (int p = 0; p < 2; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
             for (int c = 0; c < (warp_live ? ng : 0); ++c) {
                 const float4 ch = s_cell[c][0], cl = s_cell[c][1];
+                // the 28-point rule (2.6e-6 at 1.5 h) when this warp's whole box is
+                // at least 1.5 h from the centroid, else the 112-point rule (warp-uniform)
+                const bool coarse = box_d2(ch.x + cl.x, ch.y + cl.y, ch.z + cl.z, wlo, whi) >= TIER_28PT_H2 * ch.w;
+                const SrcPk *qp = coarse ? s_off28[c] : s_off[c];
+                const int nqp = coarse ? 28 : NQ_PTS;
                 // exact target - centroid per pack; targets within h get a
                 // 1e30 m^2 softening, i.e. no term here (theirs is the closed form)
                 u64 DX[2], DY[2], DZ[2], EP[2];
@@ -615,9 +634,9 @@ near_quad_kernel(FieldLaunch L)
                     EP[p] = pk(da < ch.w ? 1e30f : 0.0f, db < ch.w ? 1e30f : 0.0f);
                 }
 #pragma unroll 4
-                for (int k = 0; k < NQ_PTS; ++k) {
-                    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&s_off[c][k].xx);
-                    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&s_off[c][k].zz);
+                for (int k = 0; k < nqp; ++k) {
+                    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&qp[k].xx);
+                    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&qp[k].zz);
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
                         u64 dx = sub2(DX[p], a.x);
