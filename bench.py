@@ -97,6 +97,8 @@ def _args():
     p.add_argument("--no-bem-precisions", action="store_true")
     p.add_argument("--batch-chambers", type=int, default=256)
     p.add_argument("--batch-only", action="store_true")
+    p.add_argument("--batch-skip-single", action="store_true",
+                   help="batched sweep without the single-instance comparison (for profiling)")
     return p.parse_args()
 
 
@@ -462,7 +464,7 @@ def nn_timing(ctx, pos_q, dev, soft, grids=(16, 32)):
     return out
 
 
-def batch_timing(dev, n_chambers=256, steps=3, swarm_steps=12):
+def batch_timing(dev, n_chambers=256, steps=3, swarm_steps=12, single=True):
     """The batched sweep: n_chambers independent parallel-plate chambers
     (gaps 0.5-3 mm, fields 0.1-30 kV/cm, 1e2-1e5 charges log-uniform, 1024-4096
     cells each, argon-like gas), every chamber's cell densities from its own
@@ -544,12 +546,14 @@ def batch_timing(dev, n_chambers=256, steps=3, swarm_steps=12):
         gsb = obem.read_batch_stats(stats, n_chambers)
         assert all(g["status"] == 0 for g in gsb), "batched step failed"
 
-        def single():
+        def one_by_one():
             for ctx, st, ss in zip(ctxs, sts, sstats):
                 obem.obem_step(ctx, st, 0, ss)
-        ms_s = timed(single, restore_s)
-        for ss in sstats:
-            assert obem.read_stats(ss)["status"] == 0, "single-instance step failed"
+        ms_s = None
+        if single:
+            ms_s = timed(one_by_one, restore_s)
+            for ss in sstats:
+                assert obem.read_stats(ss)["status"] == 0, "single-instance step failed"
         n = np.array([c.charges.n for c in chambers], np.float64)
         npan = np.array([c.mesh.n for c in chambers], np.float64)
         ne = np.array([int((c.charges.species == 0).sum()) for c in chambers], np.float64)
@@ -569,7 +573,7 @@ def batch_timing(dev, n_chambers=256, steps=3, swarm_steps=12):
             "pair_evals_per_step": pairs,
             "batched_graph_ms_per_step": ms_b,
             "single_instance_ms_per_step": ms_s,
-            "speedup_vs_single_instance": ms_s / ms_b if ms_b > 0 else None,
+            "speedup_vs_single_instance": ms_s / ms_b if ms_b > 0 and ms_s else None,
             "electron_steps_per_s": float(ne.sum()) / (ms_b * 1e-3),
             "field_pair_evals_per_s": pairs / (ms_b * 1e-3),
             "autotune": tune,
@@ -717,7 +721,8 @@ def main():
         # the batched sweep alone (for profiling it): one JSON object
         import torch
         torch.cuda.set_device(local)
-        print(json.dumps({"batched_sweep": batch_timing("cuda:%d" % local, a.batch_chambers)}))
+        print(json.dumps({"batched_sweep": batch_timing("cuda:%d" % local, a.batch_chambers,
+                                                        single=not a.batch_skip_single)}))
     else:
         run_ours(a, ws, rank, local)
 

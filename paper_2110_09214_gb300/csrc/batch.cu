@@ -28,7 +28,7 @@ struct obem_batch {
     // cells of every chamber, concatenated
     int np_total;
     float4 *d_c_a, *d_g0_h, *d_g1, *d_g2, *d_nrm, *d_c_lo;
-    double *d_v64;
+    double *d_v64, *d_geo64;
     float *d_sigma;
     int2 *d_cham_pan;
     // field scratch
@@ -57,9 +57,9 @@ static void bfree(void *p)
 static void free_cells(obem_batch *b)
 {
     bfree(b->d_c_a); bfree(b->d_g0_h); bfree(b->d_g1); bfree(b->d_g2); bfree(b->d_nrm); bfree(b->d_c_lo);
-    bfree(b->d_v64); bfree(b->d_sigma);
+    bfree(b->d_v64); bfree(b->d_geo64); bfree(b->d_sigma);
     b->d_c_a = b->d_g0_h = b->d_g1 = b->d_g2 = b->d_nrm = b->d_c_lo = NULL;
-    b->d_v64 = NULL;
+    b->d_v64 = b->d_geo64 = NULL;
     b->d_sigma = NULL;
     b->np_total = 0;
 }
@@ -261,6 +261,9 @@ static int upload_cells(obem_batch *b)
         BUP(b->d_nrm, nr.data(), f4);
         BUP(b->d_c_lo, cl.data(), f4);
         BUP(b->d_v64, v64.data(), sizeof(double) * 9 * (size_t)np);
+        std::vector<double> geo((size_t)OBEM_GEO64 * np);
+        obem_cell_geo64(v64.data(), np, geo.data());
+        BUP(b->d_geo64, geo.data(), sizeof(double) * geo.size());
         BUP(b->d_sigma, sg.data(), sizeof(float) * np);
     }
     if (rc == OBEM_OK &&
@@ -320,6 +323,7 @@ static FieldBatch field_args(obem_batch *b, const obem_state *st)
     F.panels.nrm = b->d_nrm;
     F.panels.c_lo = b->d_c_lo;
     F.panels.v64 = b->d_v64;
+    F.panels.geo = b->d_geo64;
     F.panels.np = b->np_total;
     F.sigma = b->d_sigma;
     F.cham_pan = b->d_cham_pan;

@@ -518,7 +518,7 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     PanelsDev P;
     P.c_a = c->d_c_a; P.g0_h = c->d_g0_h; P.g1 = c->d_g1; P.g2 = c->d_g2; P.nrm = c->d_nrm;
     P.c_lo = c->d_c_lo;
-    P.v64 = c->d_v64; P.np = n;
+    P.v64 = c->d_v64; P.geo = c->d_geo64; P.np = n;
     double *d_em = NULL, *d_ep = NULL;
     OBEM_CUDA(c, cudaMalloc((void **)&d_em, sizeof(double) * n));
     OBEM_CUDA(c, cudaMalloc((void **)&d_ep, sizeof(double) * n));

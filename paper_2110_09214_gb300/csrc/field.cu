@@ -396,10 +396,11 @@ __device__ __forceinline__ bool cell_is_near(float4 ca, float h2, const BlockFra
 }
 
 // FP64 closed form of one cell at one target, times k_C sigma (FP32 result)
-__device__ __noinline__ float4 closed_val(const double *v, float tx, float ty, float tz, float sg)
+__device__ __noinline__ float4 closed_val(const double *v, const double *g, float tx, float ty, float tz, float sg)
 {
     double phi, Fx, Fy, Fz;
-    tri_closed_form(v, (double)tx, (double)ty, (double)tz, phi, Fx, Fy, Fz);
+    if (g) tri_closed_form_g(v, g, (double)tx, (double)ty, (double)tz, phi, Fx, Fy, Fz);
+    else tri_closed_form(v, (double)tx, (double)ty, (double)tz, phi, Fx, Fy, Fz);
     const double kq = OBEM_KC * (double)sg;
     return make_float4((float)(kq * Fx), (float)(kq * Fy), (float)(kq * Fz), (float)(kq * phi));
 }
@@ -444,7 +445,8 @@ __device__ __forceinline__ void nc_flush(const FieldLaunch &L, int n, const floa
     if (lane < n) {
         const float4 e = qp[lane];
         const int j = __float_as_int(e.w);
-        res[lane] = closed_val(L.panels.v64 + 9 * (size_t)j, e.x, e.y, e.z, L.sigma[j]);
+        res[lane] = closed_val(L.panels.v64 + 9 * (size_t)j,
+                               L.panels.geo ? L.panels.geo + (size_t)OBEM_GEO64 * j : NULL, e.x, e.y, e.z, L.sigma[j]);
     }
     __syncwarp();
     for (int e = 0; e < n; ++e) {

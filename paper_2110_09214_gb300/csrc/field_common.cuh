@@ -111,6 +111,49 @@ static __device__ __noinline__ void tri_closed_form(const double *v, double rx, 
     Fz = fz + Om * nz;
 }
 
+// The same closed form with the cell's geometry precomputed in FP64 (g: unit
+// normal, twice the area, unit edge vectors and in-plane edge normals, the
+// layout of OBEM_GEO64): per evaluation only the vertex offsets, their
+// lengths, the edge logarithms and the solid angle remain.
+static __device__ __noinline__ void tri_closed_form_g(const double *v, const double *g, double rx, double ry,
+                                                      double rz, double &phi, double &Fx, double &Fy, double &Fz)
+{
+    const double nx = g[0], ny = g[1], nz = g[2], a2 = g[3];
+    double ax[3], ay[3], az[3], R[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        ax[i] = v[3 * i] - rx;
+        ay[i] = v[3 * i + 1] - ry;
+        az[i] = v[3 * i + 2] - rz;
+        R[i] = sqrt(ax[i] * ax[i] + ay[i] * ay[i] + az[i] * az[i]);
+    }
+    const double h = -(ax[0] * nx + ay[0] * ny + az[0] * nz);
+    double ps = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3;
+        const double *e = g + 4 + 6 * i;
+        const double dx = e[0], dy = e[1], dz = e[2], ux = e[3], uy = e[4], uz = e[5];
+        const double lm = ax[i] * dx + ay[i] * dy + az[i] * dz;
+        const double lp = ax[j] * dx + ay[j] * dy + az[j] * dz;
+        const double p0 = ax[i] * ux + ay[i] * uy + az[i] * uz;
+        double L;
+        if (lm >= 0.0) L = log((R[j] + lp) / (R[i] + lm));
+        else if (lp <= 0.0) L = log((R[i] - lm) / (R[j] - lp));
+        else L = log((R[j] + lp) * (R[i] - lm) / (p0 * p0 + h * h));
+        if (p0 != 0.0) ps += p0 * L;
+        fx += ux * L; fy += uy * L; fz += uz * L;
+    }
+    const double D = R[0] * R[1] * R[2] + (ax[0] * ax[1] + ay[0] * ay[1] + az[0] * az[1]) * R[2]
+                   + (ax[0] * ax[2] + ay[0] * ay[2] + az[0] * az[2]) * R[1]
+                   + (ax[1] * ax[2] + ay[1] * ay[2] + az[1] * az[2]) * R[0];
+    const double Om = (h == 0.0) ? 0.0 : 2.0 * atan2(a2 * h, D);
+    phi = ps - h * Om;
+    Fx = fx + Om * nx;
+    Fy = fy + Om * ny;
+    Fz = fz + Om * nz;
+}
+
 // one FP32 quadrature point of weight w (already k_C sigma A w_i)
 __device__ __forceinline__ void qpoint(float tx, float ty, float tz, float px, float py, float pz,
                                        float w, float &ax, float &ay, float &az, float &av)

@@ -104,7 +104,8 @@ int obem_fieldmap_build_nodes(obem_ctx *c, const float *sigma, cudaStream_t s)
         L.nt = count;
         L.sigma = sigma;
         L.panels.c_a = c->d_c_a; L.panels.g0_h = c->d_g0_h; L.panels.g1 = c->d_g1; L.panels.g2 = c->d_g2;
-        L.panels.nrm = c->d_nrm; L.panels.c_lo = c->d_c_lo; L.panels.v64 = c->d_v64; L.panels.np = c->np;
+        L.panels.nrm = c->d_nrm; L.panels.c_lo = c->d_c_lo; L.panels.v64 = c->d_v64; L.panels.geo = c->d_geo64;
+        L.panels.np = c->np;
         L.E_out = c->fm.nodes + first;
         L.e_ext = make_float3(0.f, 0.f, 0.f);
         L.want_v = 1;

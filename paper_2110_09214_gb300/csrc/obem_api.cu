@@ -29,6 +29,7 @@ static void free_mesh(obem_ctx *c)
     c->h_tri = c->h_em = c->h_ep = NULL;
     free_dev(c->d_c_a); free_dev(c->d_g0_h); free_dev(c->d_g1); free_dev(c->d_g2);
     free_dev(c->d_nrm); free_dev(c->d_c_lo); free_dev(c->d_v64); free_dev(c->d_kind); free_dev(c->d_group);
+    free_dev(c->d_geo64);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
     free_dev(c->d_tri9); free_dev(c->d_hstart); free_dev(c->d_htri); free_dev(c->d_area); free_dev(c->d_deposit);
@@ -319,6 +320,35 @@ extern "C" int obem_gas_load(obem_ctx *c, const obem_gas *gs)
     return OBEM_OK;
 }
 
+// FP64 geometry of each cell for the closed form: unit normal n, twice the
+// area |(v1 - v0) x (v2 - v0)|, and for each edge i -> i+1 its unit vector and
+// its in-plane normal (edge x n); OBEM_GEO64 doubles per cell.
+void obem_cell_geo64(const double *tri, int np, double *geo)
+{
+    for (int i = 0; i < np; ++i) {
+        const double *v = tri + 9 * (size_t)i;
+        double *g = geo + (size_t)OBEM_GEO64 * i;
+        const double e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+        const double e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        const double a2 = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int k = 0; k < 3; ++k) n[k] /= a2;
+        g[0] = n[0]; g[1] = n[1]; g[2] = n[2]; g[3] = a2;
+        for (int e = 0; e < 3; ++e) {
+            const int j = (e + 1) % 3;
+            double d[3] = {v[3 * j] - v[3 * e], v[3 * j + 1] - v[3 * e + 1], v[3 * j + 2] - v[3 * e + 2]};
+            const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int k = 0; k < 3; ++k) d[k] /= len;
+            double *gd = g + 4 + 6 * e;
+            gd[0] = d[0]; gd[1] = d[1]; gd[2] = d[2];
+            gd[3] = d[1] * n[2] - d[2] * n[1];
+            gd[4] = d[2] * n[0] - d[0] * n[2];
+            gd[5] = d[0] * n[1] - d[1] * n[0];
+        }
+        g[22] = 0.0; g[23] = 0.0;
+    }
+}
+
 // Cell geometry in the layout of the field kernels (see PanelsDev) from FP64
 // vertices; kind may be NULL (electrode).  Returns the first degenerate cell,
 // or -1.
@@ -419,6 +449,15 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
     UP(c->d_nrm, nr, f4);
     UP(c->d_c_lo, cl, f4);
     UP(c->d_v64, tri, sizeof(double) * 9 * np);
+    {
+        double *geo = (double *)malloc(sizeof(double) * OBEM_GEO64 * np);
+        if (!geo) rc = obem_fail(c, OBEM_ERR_ARG, "mesh: host allocation failed");
+        else {
+            obem_cell_geo64(tri, np, geo);
+            UP(c->d_geo64, geo, sizeof(double) * OBEM_GEO64 * np);
+            free(geo);
+        }
+    }
     UP(c->d_kind, kind, sizeof(int) * np);
     UP(c->d_group, group, sizeof(int) * np);
     // charging-up: binary32 vertices, areas, and a uniform grid over the
@@ -516,6 +555,7 @@ static PanelsDev panels_of(const obem_ctx *c)
     p.c_a = c->d_c_a; p.g0_h = c->d_g0_h; p.g1 = c->d_g1; p.g2 = c->d_g2; p.nrm = c->d_nrm;
     p.c_lo = c->d_c_lo;
     p.v64 = c->d_v64;
+    p.geo = c->d_geo64;
     p.np = c->np;
     return p;
 }

@@ -62,8 +62,13 @@ struct GasDev {
 struct PanelsDev {
     const float4 *c_a, *g0_h, *g1, *g2, *nrm, *c_lo;
     const double *v64;
+    // FP64 geometry of each cell for the closed form, OBEM_GEO64 doubles per
+    // cell (unit normal, twice the area, unit edge vectors and in-plane edge
+    // normals), or NULL (then computed per evaluation)
+    const double *geo;
     int np;
 };
+#define OBEM_GEO64 24
 
 // Static field map: cell field on a regular grid (valid nx x ny x nz nodes,
 // stored padded to px x py x pz in bricks of 8^3), node (i, j, k) at
@@ -130,6 +135,7 @@ struct obem_ctx {
     double *h_tri, *h_em, *h_ep;
     float4 *d_c_a, *d_g0_h, *d_g1, *d_g2, *d_nrm, *d_c_lo;
     double *d_v64;
+    double *d_geo64;         // [np][OBEM_GEO64] closed-form geometry
     int *d_kind, *d_group;
     float bbox_lo[3], bbox_hi[3];   // of the cell vertices (target binning grid)
     // BEM
@@ -306,6 +312,7 @@ int obem_launch_field_batch(obem_ctx *ctx, const FieldBatch &F, const float4 *po
 size_t obem_sym_sizes(int capacity, size_t *ipart_floats);
 int obem_cell_layout(const double *tri, const int32_t *kind, int np, float4 *ca, float4 *g0, float4 *g1,
                      float4 *g2, float4 *nr, float4 *cl);
+void obem_cell_geo64(const double *tri, int np, double *geo);
 size_t obem_sym_jpart_floats(int capacity);
 size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);
