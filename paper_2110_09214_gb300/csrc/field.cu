@@ -1,22 +1,23 @@
-// Field at points: BEM cell field (Eq. (BEM3), (BEM2)) + all-pairs Coulomb
-// field of point charges (Eq. (nbody)), and -- in the tracking step -- the
-// nearest-cation search that feeds electron-ion recombination (Sec. 3.3.3).
+// Field at points: BEM cell field (Eqs. (BEM3), (BEM2)) + all-pairs Coulomb
+// field of point charges (Eq. (nbody)), the step's fused field, and the batch
+// of chambers' field.
 //
-// Layout: each thread owns FT_TPT targets (two packs of two, processed with
-// the packed f32x2 instructions of sm_100+), a block owns FT_THREADS*FT_TPT
-// consecutive targets.  Sources are staged through shared memory in tiles of
-// FT_SRC_TILE charges stored as duplicated pairs (x,x)(y,y)(z,z)(kq,kq), so a
-// packed instruction serves two targets against one source.  Every tile's
-// FP32 partial sum is folded into a compensated (TwoSum) accumulator.
+// Charges.  When the targets are the charges themselves (every step) the
+// symmetric kernel evaluates each unordered pair once and applies the
+// reaction to the other charge: tiles of 1024 charges paired cyclically,
+// persistent blocks taking work units from a counter, sources rotated around
+// the warp with their reaction sums, partial sums in slots of their own folded
+// per charge in a fixed order (deterministic).  It runs on a copy of the
+// charges ordered by charge value so that k_C q factors out of most tile
+// pairs.  Separate targets and sources use the one-sided kernel: FT_TPT
+// targets per thread as f32x2 packs, sources staged through shared memory as
+// duplicated pairs, compensated (TwoSum) folds of every tile.
 //
-// Cell field tiers, chosen per (target, cell) from the distance d to the
-// centroid and the longest edge h:
-//   d >= 200 h   centroid rule                          (<= 3.4e-6 relative per cell)
-//   d >=  16 h   3-point degree-2 rule                  (<= 2.7e-6)
-//   d >=   3 h   7-point degree-5 rule                  (<= 1.8e-6)
-//   d >= 1.5 h   7-point rule on 4 midpoint sub-triangles  (<= 2.2e-6)
-//   d >=   h     7-point rule on 16 sub-triangles       (<= 1.3e-6)
-//   d <    h     closed form in FP64 (edge logarithms + solid angle)
+// Cells.  Targets are ordered along a 64^3 Morton grid (stable radix sort) and
+// cut into blocks of <= 512; per block, cells near its box get the FP64
+// closed form (targets within h) and a 112- or 28-point rule, the others one
+// of the quadrature tiers listed at TIER_*_H2 below, emitted as point sources
+// into the same packed loop as the charges.
 #include "obem_internal.cuh"
 #include "field_common.cuh"
 
@@ -263,15 +264,17 @@ static void binsort(const uint32_t *code_in, uint32_t *code, int32_t *perm, uint
 // if its centroid is closer than 1.5 h to the bounding box of the block's
 // targets (or if the block is so spread out that its frame cannot resolve the
 // cell); the test is the same function in all three kernels.
-//   near_closed_kernel  near cells, targets with d < h: FP64 closed form;
-//                       writes E_out = e_ext + these terms
+//   near_closed_kernel  near cells, targets with d < h: FP64 closed form
+//                       (pairs queued per warp, 32 per evaluation); writes
+//                       E_out = e_ext + these terms
 //   near_quad_kernel    near cells, all other targets: 7-point rule on 16
-//                       sub-triangles (<= 1.3e-6 for d >= h), uniform for the
-//                       block, target-centroid differences exact
-//   cell_kernel         far cells: 1 / 3 / 7 / 28 quadrature points chosen by
-//                       the distance to the box, emitted as point sources in a
-//                       frame centred on the block and consumed by the packed
-//                       f32x2 loop
+//                       sub-triangles (<= 2.7e-6 for d >= h), or on 4 (28
+//                       points, 2.6e-6 for d >= 1.5 h) for a warp whose whole
+//                       box is 1.5 h away; target-centroid differences exact
+//   cell_kernel         far cells: 1 / 3 / 4 / 6 / 7 / 28 quadrature points
+//                       chosen by the distance to the box, emitted as point
+//                       sources in a frame centred on the block and consumed
+//                       by the packed f32x2 loop
 #define CT_THREADS 128
 #define CT_TPT 4
 #define CT_BLOCK (CT_THREADS * CT_TPT)
