@@ -1,5 +1,6 @@
 // Host side of the C ABI: context, gas and mesh loading, argument checks and
-// dispatch to the kernels of field.cu, step.cu and bem.cu.
+// dispatch to the kernels of field.cu, step.cu, bem.cu, backward.cu,
+// fieldmap.cu, nn.cu and peak.cu (the batch of chambers is in batch.cu).
 #include <math.h>
 #include <stdarg.h>
 #include <stdlib.h>

@@ -9,7 +9,7 @@
 //
 // Passes (all stream-ordered, nothing synchronises):
 //   init      zero the stats and the control block
-//   partners  (only when the field kernel did not search them) nearest cation
+//   partners  nearest eligible cation of every electron (spatial hash, ph_*)
 //   resolve   each proposing electron atomicMin's (d^2, e) into its cation
 //   count     simulate every charge without writing: survivors, spawn counts,
 //             per-block totals for the scan
@@ -18,6 +18,7 @@
 //             and spawned charges to their final slots in scratch
 //   commit    copy scratch to the caller's arrays, update n and next_id
 //   moments   species counts and cloud moments of the new state
+// The bt_* kernels at the end run the same passes for a batch of chambers.
 #include "obem_internal.cuh"
 
 #define ST_THREADS 256
