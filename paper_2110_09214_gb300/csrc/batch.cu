@@ -76,7 +76,7 @@ extern "C" void obem_batch_destroy(obem_batch *b)
     BtScratch &W = b->W;
     bfree(W.prop); bfree(W.ionkey); bfree(W.keep); bfree(W.nsp); bfree(W.blk); bfree(W.o_pos); bfree(W.o_vel);
     bfree(W.o_id); bfree(W.o_birth); bfree(W.o_sp); bfree(W.ph_bucket); bfree(W.ph_count); bfree(W.ph_start);
-    bfree(W.ph_cursor); bfree(W.ph_sorted); bfree(W.ph_bsum);
+    bfree(W.ph_cursor); bfree(W.ph_sorted); bfree(W.ph_bsum); bfree(W.mpart);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
@@ -188,6 +188,7 @@ extern "C" int obem_batch_create(obem_batch **out, obem_ctx *ctx, int32_t n_cham
     BALLOC(W.ph_cursor, sizeof(int32_t) * OBEM_PH_BUCKETS);
     BALLOC(W.ph_sorted, sizeof(int32_t) * S);
     BALLOC(W.ph_bsum, sizeof(int32_t) * (OBEM_PH_BUCKETS / 1024 + 1));
+    BALLOC(W.mpart, sizeof(double) * 13 * (S / 256));
     if (rc == OBEM_OK) {
         std::vector<int2> pan(nb, make_int2(0, 0));
         if (cudaMemcpy(b->d_cham_pan, pan.data(), sizeof(int2) * nb, cudaMemcpyHostToDevice) != cudaSuccess)

@@ -92,6 +92,7 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->s_keep, sizeof(int32_t) * cap);
     ALLOC(c->s_nsp, sizeof(int32_t) * cap);
     ALLOC(c->s_blk, sizeof(int32_t) * 4 * max_blocks);
+    ALLOC(c->s_mpart, sizeof(double) * 13 * max_blocks);
     ALLOC(c->s_ctl, sizeof(StepCtl));
     ALLOC(c->o_pos, sizeof(float4) * cap);
     ALLOC(c->o_vel, sizeof(float4) * cap);
@@ -161,7 +162,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_mesh(c);
     free_dev(c->d_egrid); free_dev(c->d_xs);
     free_dev(c->s_E); free_dev(c->s_prop); free_dev(c->s_ionkey); free_dev(c->s_keep);
-    free_dev(c->s_nsp); free_dev(c->s_blk); free_dev(c->s_ctl); free_dev(c->o_pos);
+    free_dev(c->s_nsp); free_dev(c->s_blk); free_dev(c->s_ctl); free_dev(c->o_pos); free_dev(c->s_mpart);
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
     free_dev(c->s_tk); free_dev(c->s_tv); free_dev(c->s_rh);

@@ -117,6 +117,7 @@ struct BtScratch {
     uint32_t *o_id, *o_birth;
     uint8_t *o_sp;
     int32_t *ph_bucket, *ph_count, *ph_start, *ph_cursor, *ph_sorted, *ph_bsum;
+    double *mpart;           // per-block partial moments (13 per block of 256 slots)
 };
 
 struct obem_ctx {
@@ -157,6 +158,7 @@ struct obem_ctx {
     unsigned long long *s_prop, *s_ionkey;
     int32_t *s_keep, *s_nsp;
     int32_t *s_blk;       // per-block sums / offsets (2 * max_blocks)
+    double *s_mpart;      // per-block partial moments (13 * max_blocks)
     StepCtl *s_ctl;
     float4 *o_pos, *o_vel;
     uint32_t *o_id, *o_birth;

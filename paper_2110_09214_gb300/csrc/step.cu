@@ -804,42 +804,82 @@ int obem_launch_surface_sigma(obem_ctx *c, float *sigma_free, cudaStream_t s)
     return OBEM_OK;
 }
 
-__global__ void __launch_bounds__(ST_THREADS)
-moments_kernel(const obem_state st, obem_step_stats *stats)
+// Cloud moments of the new state.  Counts go to the stats by integer atomics
+// (exact in any order); the FP64 sums are reduced per block and the blocks'
+// partial sums added by moments_fold_kernel in block order, so the moments
+// are the same on every run.
+#define NMOM 13    // sum_e[3], sum2_e[3], sum_i[3], sum2_i[3], sum_energy_e
+
+__device__ void moments_block(const obem_state &st, int i, bool live, obem_step_stats *stats, double *part)
 {
     __shared__ double shd[ST_THREADS / 32];
     __shared__ long long shl[ST_THREADS / 32];
-    const int n = cur_n(st);
-    int i = blockIdx.x * ST_THREADS + threadIdx.x;
     int ne = 0, nc = 0, na = 0;
-    double se[3] = {0, 0, 0}, s2e[3] = {0, 0, 0}, si[3] = {0, 0, 0}, s2i[3] = {0, 0, 0}, en = 0.0;
-    if (i < n) {
-        uint8_t s = st.species[i];
-        float4 p = reinterpret_cast<const float4 *>(st.pos_q)[i];
-        double x[3] = {p.x, p.y, p.z};
+    double v[NMOM];
+#pragma unroll
+    for (int f = 0; f < NMOM; ++f) v[f] = 0.0;
+    if (live) {
+        const uint8_t s = st.species[i];
+        const float4 p = reinterpret_cast<const float4 *>(st.pos_q)[i];
+        const double x[3] = {p.x, p.y, p.z};
         if (s == OBEM_ELECTRON) {
             ne = 1;
-            for (int c = 0; c < 3; ++c) { se[c] = x[c]; s2e[c] = x[c] * x[c]; }
-            float4 v = reinterpret_cast<const float4 *>(st.vel)[i];
-            double v2 = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
-            en = 0.5 * OBEM_ME * v2 / OBEM_QE;
+            for (int c = 0; c < 3; ++c) { v[c] = x[c]; v[3 + c] = x[c] * x[c]; }
+            const float4 u = reinterpret_cast<const float4 *>(st.vel)[i];
+            const double v2 = (double)u.x * u.x + (double)u.y * u.y + (double)u.z * u.z;
+            v[12] = 0.5 * OBEM_ME * v2 / OBEM_QE;
         } else {
             if (s == OBEM_CATION) nc = 1; else na = 1;
-            for (int c = 0; c < 3; ++c) { si[c] = x[c]; s2i[c] = x[c] * x[c]; }
+            for (int c = 0; c < 3; ++c) { v[6 + c] = x[c]; v[9 + c] = x[c] * x[c]; }
         }
     }
     long long t;
     t = block_sum<long long>(ne, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_electron, (int)t);
     t = block_sum<long long>(nc, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_cation, (int)t);
     t = block_sum<long long>(na, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_anion, (int)t);
-    double d;
-    for (int c = 0; c < 3; ++c) {
-        d = block_sum<double>(se[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum_e[c], d);
-        d = block_sum<double>(s2e[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum2_e[c], d);
-        d = block_sum<double>(si[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum_i[c], d);
-        d = block_sum<double>(s2i[c], shd); if (threadIdx.x == 0) atomicAdd(&stats->sum2_i[c], d);
+    for (int f = 0; f < NMOM; ++f) {
+        const double d = block_sum<double>(v[f], shd);
+        if (threadIdx.x == 0) part[f] = d;
     }
-    d = block_sum<double>(en, shd); if (threadIdx.x == 0) atomicAdd(&stats->sum_energy_e, d);
+}
+
+__global__ void __launch_bounds__(ST_THREADS)
+moments_kernel(const obem_state st, obem_step_stats *stats, double *part)
+{
+    const int n = cur_n(st);
+    const int i = blockIdx.x * ST_THREADS + threadIdx.x;
+    if (blockIdx.x * ST_THREADS >= n) return;            // a block with no charge adds nothing
+    moments_block(st, i, i < n, stats, part + (size_t)NMOM * blockIdx.x);
+}
+
+// sum of the nb blocks' partial sums from part (NMOM per block), in block
+// order within each thread's stride and a fixed tree across threads (1024)
+__device__ void moments_fold(const double *part, int nb, obem_step_stats *stats)
+{
+    __shared__ double red[1024];
+    double *dst[NMOM] = {&stats->sum_e[0], &stats->sum_e[1], &stats->sum_e[2], &stats->sum2_e[0],
+                         &stats->sum2_e[1], &stats->sum2_e[2], &stats->sum_i[0], &stats->sum_i[1],
+                         &stats->sum_i[2], &stats->sum2_i[0], &stats->sum2_i[1], &stats->sum2_i[2],
+                         &stats->sum_energy_e};
+    for (int f = 0; f < NMOM; ++f) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[(size_t)NMOM * b + f];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *dst[f] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) moments_fold_kernel(const obem_state st, const double *part,
+                                                            obem_step_stats *stats)
+{
+    const int n = cur_n(st);
+    moments_fold(part, (n + ST_THREADS - 1) / ST_THREADS, stats);
 }
 
 int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32_t step,
@@ -895,9 +935,10 @@ int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32
     }
     finish_kernel<<<1, 32, 0, s>>>(st, c->s_ctl);
     OBEM_LAUNCH(c);
-    moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats);
+    moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats, c->s_mpart);
+    moments_fold_kernel<<<1, 1024, 0, s>>>(st, c->s_mpart, stats);
     OBEM_LAUNCH(c);
-    if (c->prof_on) c->launches += 8 + (g.recomb_on ? 7 : 0) + (g.hit_on ? 1 : 0);
+    if (c->prof_on) c->launches += 9 + (g.recomb_on ? 7 : 0) + (g.hit_on ? 1 : 0);
     return OBEM_OK;
 }
 
@@ -1203,42 +1244,19 @@ __global__ void bt_finish_kernel(StepBatch B)
 }
 
 __global__ void __launch_bounds__(ST_THREADS)
-bt_moments_kernel(const obem_state st, StepBatch B)
+bt_moments_kernel(const obem_state st, StepBatch B, double *part)
 {
-    __shared__ double shd[ST_THREADS / 32];
-    __shared__ long long shl[ST_THREADS / 32];
     const BtSlot q = bt_slot(B);
-    obem_step_stats *stats = &B.stats[q.c];
-    int ne = 0, nc = 0, na = 0;
-    double se[3] = {0, 0, 0}, s2e[3] = {0, 0, 0}, si[3] = {0, 0, 0}, s2i[3] = {0, 0, 0}, en = 0.0;
-    if (q.li < q.n) {
-        const int i = q.off + q.li;
-        const uint8_t s = st.species[i];
-        const float4 p = reinterpret_cast<const float4 *>(st.pos_q)[i];
-        const double x[3] = {p.x, p.y, p.z};
-        if (s == OBEM_ELECTRON) {
-            ne = 1;
-            for (int c = 0; c < 3; ++c) { se[c] = x[c]; s2e[c] = x[c] * x[c]; }
-            const float4 v = reinterpret_cast<const float4 *>(st.vel)[i];
-            const double v2 = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
-            en = 0.5 * OBEM_ME * v2 / OBEM_QE;
-        } else {
-            if (s == OBEM_CATION) nc = 1; else na = 1;
-            for (int c = 0; c < 3; ++c) { si[c] = x[c]; s2i[c] = x[c] * x[c]; }
-        }
-    }
-    long long t;
-    t = block_sum<long long>(ne, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_electron, (int)t);
-    t = block_sum<long long>(nc, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_cation, (int)t);
-    t = block_sum<long long>(na, shl); if (threadIdx.x == 0 && t) atomicAdd(&stats->n_anion, (int)t);
-    double d;
-    for (int c = 0; c < 3; ++c) {
-        d = block_sum<double>(se[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum_e[c], d);
-        d = block_sum<double>(s2e[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum2_e[c], d);
-        d = block_sum<double>(si[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum_i[c], d);
-        d = block_sum<double>(s2i[c], shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum2_i[c], d);
-    }
-    d = block_sum<double>(en, shd); if (threadIdx.x == 0 && d != 0.0) atomicAdd(&stats->sum_energy_e, d);
+    if (q.li - (int)threadIdx.x >= q.n) return;          // a block past the chamber's charges
+    moments_block(st, q.off + q.li, q.li < q.n, &B.stats[q.c], part + (size_t)NMOM * blockIdx.x);
+}
+
+// one block per chamber: its blocks' partial sums in block order
+__global__ void __launch_bounds__(1024) bt_moments_fold_kernel(StepBatch B, const double *part)
+{
+    const int c = blockIdx.x;
+    const int b0 = B.seg_off[c] / ST_THREADS;
+    moments_fold(part + (size_t)NMOM * b0, (B.n[c] + ST_THREADS - 1) / ST_THREADS, &B.stats[c]);
 }
 
 // The whole batched step on stream s.  Scratch (BtScratch) is sized for the
@@ -1283,7 +1301,8 @@ int obem_launch_step_batch(obem_ctx *c, const obem_state *stp, const StepBatch &
     OBEM_LAUNCH(c);
     bt_finish_kernel<<<cb, 256, 0, s>>>(B);
     OBEM_LAUNCH(c);
-    bt_moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B);
+    bt_moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, B, W.mpart);
+    bt_moments_fold_kernel<<<B.nb, 1024, 0, s>>>(B, W.mpart);
     OBEM_LAUNCH(c);
     return OBEM_OK;
 }

@@ -409,16 +409,21 @@ def test_checkpoint_resume_bit_identical():
             g.solve()
             g.upload(state, nid)
             for s in range(start, start + steps):
-                assert g.step(s)["status"] == 0
-            return g.state()
+                last = g.step(s)
+                assert last["status"] == 0
+            return g.state(), last
         finally:
             g.close()
 
-    full, nid_full = run(6, 0, ch, ch.n)
-    half, nid_half = run(3, 0, ch, ch.n)
-    resumed, nid_res = run(3, 3, half, nid_half)
+    (full, nid_full), st_full = run(6, 0, ch, ch.n)
+    (half, nid_half), _ = run(3, 0, ch, ch.n)
+    (resumed, nid_res), st_res = run(3, 3, half, nid_half)
     _assert_same_state(full, resumed)
     assert nid_full == nid_res and full.n > ch.n
+    # the step's observables too: FP64 moments are folded in block order
+    for k in ("sum_e", "sum2_e", "sum_i", "sum2_i"):
+        assert st_full[k] == st_res[k], k
+    assert st_full["sum_energy_e"] == st_res["sum_energy_e"]
 
 
 def test_batch_checkpoint_resume_bit_identical():
