@@ -63,7 +63,7 @@ enum { OBEM_ELECTRON = 0, OBEM_CATION = 1, OBEM_ANION = 2 };
 enum {
     OBEM_LU_FP32 = 0,   /* FP32 on the CUDA cores */
     OBEM_LU_TF32 = 1,   /* TF32 tensor cores, FP32 accumulation */
-    OBEM_LU_BF16 = 2,   /* BF16 tensor cores, FP32 accumulation */
+    OBEM_LU_BF16 = 2,   /* panels rounded to BF16, BF16 tensor cores, FP32 accumulation */
     OBEM_LU_BF16X9 = 3  /* FP32-accurate BF16x9 emulation on the tensor cores */
 };
 

@@ -15,9 +15,13 @@
 //                       laswp_kernel   row swaps outside the panel
 //                       trsm_kernel    U12 = L11^-1 A12
 //                       cuBLAS GEMM    A22 -= L21 U12 (FP32 / TF32 / BF16 /
-//                                      BF16x9 per the requested precision)
+//                                      BF16x9 per the requested precision;
+//                                      for BF16 the two panels are first
+//                                      rounded to BF16 by panels_bf16_kernel,
+//                                      products accumulated in FP32)
 //   solve             y = L^-1 P b, x = U^-1 y (blocked, FP32 factors) inside
 //                     iterative refinement with FP64 residuals r = b - A x
+#include <cuda_bf16.h>
 #include <math.h>
 #include <vector>
 
@@ -473,8 +477,41 @@ __global__ void to_float_kernel(const double *x, float *a, float *b, int n)
     if (b) b[i] = v;
 }
 
+// Rounds the operands of one trailing update to BF16 (round to nearest even):
+// U12 = rows k..k+kb-1, columns k+kb..n-1 into Ub[j * ldu + i] (row j, column
+// k+kb+i), and L21 = rows k+kb..n-1, columns k..k+kb-1 into Lb[q * kb + p]
+// (row k+kb+q, column k+p).  One thread per element; the reads run along the
+// rows of A.
+__global__ void panels_bf16_kernel(const float *__restrict__ A, int n, int k, int kb, int M, int ldu,
+                                   __nv_bfloat16 *__restrict__ Ub, __nv_bfloat16 *__restrict__ Lb)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nu = (size_t)kb * M;
+    if (t < nu) {
+        const int j = (int)(t / M), i = (int)(t % M);
+        Ub[(size_t)j * ldu + i] = __float2bfloat16_rn(A[(size_t)(k + j) * n + k + kb + i]);
+    } else if (t < 2 * nu) {
+        const size_t u = t - nu;
+        const int q = (int)(u / kb), p = (int)(u % kb);
+        Lb[u] = __float2bfloat16_rn(A[(size_t)(k + kb + q) * n + k + p]);
+    }
+}
+
+// Elements of the BF16 panel scratch for n cells: Ub (LU_NB rows of ldu >= M,
+// ldu a multiple of 8 so that every column starts on 16 bytes) then Lb.
+static size_t bf16_panel_elems(int n)
+{
+    const size_t ldu = ((size_t)n + 7) / 8 * 8;
+    return (size_t)LU_NB * ldu + (size_t)n * LU_NB;
+}
+
 // ------------------------------------------------------------------ host drivers
-static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int kb, cudaStream_t s)
+// A22 -= L21 U12 for the panel at column k (width kb).  A is row-major; cuBLAS
+// sees it column-major, i.e. transposed, so the call computes
+// A22^T -= U12^T L21^T with U12 as its first operand.  bf16 is the scratch of
+// bf16_panel_elems(n) elements (used only for OBEM_LU_BF16).
+static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int kb,
+                       __nv_bfloat16 *bf16, cudaStream_t s)
 {
     const int M = n - k - kb;
     if (M <= 0) return OBEM_OK;
@@ -482,9 +519,22 @@ static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int k
     float *A22 = A + (size_t)(k + kb) * n + (k + kb);
     float *L21 = A + (size_t)(k + kb) * n + k;
     float *U12 = A + (size_t)k * n + (k + kb);
+    if (precision == OBEM_LU_BF16) {
+        // BF16 operands, FP32 products and accumulation, FP32 A22
+        const int ldu = (M + 7) / 8 * 8;
+        __nv_bfloat16 *Ub = bf16, *Lb = bf16 + (size_t)kb * ldu;
+        const size_t tot = 2 * (size_t)kb * M;
+        panels_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, n, k, kb, M, ldu, Ub, Lb);
+        OBEM_LAUNCH(c);
+        cublasStatus_t st = cublasGemmEx(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, M, M, kb, &alpha, Ub,
+                                         CUDA_R_16BF, ldu, Lb, CUDA_R_16BF, kb, &beta, A22, CUDA_R_32F, n,
+                                         CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+        if (st != CUBLAS_STATUS_SUCCESS)
+            return obem_fail(c, OBEM_ERR_CUDA, "cublasGemmEx (BF16) failed (status %d)", (int)st);
+        return OBEM_OK;
+    }
     cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
     if (precision == OBEM_LU_TF32) ct = CUBLAS_COMPUTE_32F_FAST_TF32;
-    else if (precision == OBEM_LU_BF16) ct = CUBLAS_COMPUTE_32F_FAST_16BF;
     else if (precision == OBEM_LU_BF16X9) ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
     cublasStatus_t st = cublasGemmEx(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, M, M, kb, &alpha, U12,
                                      CUDA_R_32F, n, L21, CUDA_R_32F, n, &beta, A22, CUDA_R_32F, n, ct,
@@ -549,6 +599,10 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     int *grow = (int *)(c->d_work32 + 1024);
     float *gpiv = c->d_work32 + 2048;
     float *gdiag = c->d_work32 + 2048 + LU_NB;
+    __nv_bfloat16 *bf16 = NULL;
+    if (precision == OBEM_LU_BF16)
+        OBEM_CUDA(c, cudaMalloc((void **)&bf16, sizeof(__nv_bfloat16) * bf16_panel_elems(n)));
+    struct FreeOnExit { void *p; ~FreeOnExit() { if (p) cudaFree(p); } } bf16_guard{bf16};
     for (int k = 0; k < n; k += LU_NB) {
         const int kb = n - k < LU_NB ? n - k : LU_NB;
         const int rows = n - k;
@@ -575,7 +629,7 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
         if (k + kb < n) {
             trsm_kernel<<<(n - k - kb + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, 0, s>>>(c->d_LU, n, k, kb);
             OBEM_LAUNCH(c);
-            int rc = gemm_update(c, precision, c->d_LU, n, k, kb, s);
+            int rc = gemm_update(c, precision, c->d_LU, n, k, kb, bf16, s);
             if (rc != OBEM_OK) return rc;
         }
     }

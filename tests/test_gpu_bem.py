@@ -80,13 +80,16 @@ def test_dielectric_sphere_with_rhs_correction():
     _check(mesh, sig, A, drhs.astype(np.float32).astype(np.float64), ref)
 
 
-def test_gem_patch_mixed_electrode_dielectric():
+@pytest.mark.parametrize("precision", [obem.OBEM_LU_FP32, obem.OBEM_LU_BF16])
+def test_gem_patch_mixed_electrode_dielectric(precision):
+    """Mixed electrode / dielectric rows; with BF16 panels the refinement
+    (FP64 residuals) must recover the FP32 solution's accuracy."""
     g = inputs.GemGeometry(rings=1)
     mesh = inputs.gem_mesh(g, n_theta=24, n_r=3, n_zc=1, n_zk=6, n_plane=10)
     A = oracle.assemble(mesh)
     b = oracle.bem_rhs(mesh)
     ref = oracle.solve(A, b)
-    sig, rep = _gpu_solve(mesh)
+    sig, rep = _gpu_solve(mesh, precision)
     assert rep["status"] == 0
     _check(mesh, sig, A, b, ref, fwd_tol=1e-3)
     # field from the GPU solution vs the oracle's, in the holes
