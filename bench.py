@@ -95,6 +95,7 @@ def _args():
     p.add_argument("--no-nn", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-bem-precisions", action="store_true")
+    p.add_argument("--no-avalanche", action="store_true")
     p.add_argument("--batch-chambers", type=int, default=256)
     p.add_argument("--batch-only", action="store_true")
     p.add_argument("--batch-skip-single", action="store_true",
@@ -376,6 +377,9 @@ def run_ours(a, ws, rank, local):
     bemp = None
     if ws == 1 and not a.no_bem_precisions:
         bemp = bem_precision_timing(mesh, dev)
+    aval = None
+    if ws == 1 and not a.no_avalanche:
+        aval = avalanche_timing(dev)
     cpu = None
     if ws == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(mesh, ch, gas, trk, a.cpu_seconds)
@@ -427,6 +431,7 @@ def run_ours(a, ws, rank, local):
         "batched_sweep": bres,
         "bem_precisions": bemp,
         "nbody_nn": nnres,
+        "avalanche_snapshots": aval,
     }
     print(json.dumps(line), flush=True)
 
@@ -628,6 +633,68 @@ def bem_precision_timing(mesh, dev):
     out["cells"] = int(mesh.n)
     out["note"] = ("trailing updates through cuBLAS in the named arithmetic; pivoting panels, triangular solves "
                    "and the FP64 residuals of the refinement are this library's kernels")
+    return out
+
+
+def avalanche_timing(dev, sizes=(10_000, 100_000, 1_000_000), steps=5, warmup=3, e_kv_cm=10.0):
+    """Fused-step throughput on the parallel-plate avalanche counter (2 mm gap,
+    1 cm plates of 32 x 32 x 2 triangles: 4096 cells, argon-like gas, beta =
+    1e-7 cm^3/s, 10 kV/cm) at fixed snapshot sizes: an avalanche-shaped cloud
+    of n charges (half electrons, half cations).  After the warm-up steps every
+    timed step restarts from the same state (device copy) after a 256 MiB L2
+    flush, both inside the timed region."""
+    import torch
+    from paper_2110_09214_gb300 import inputs, obem
+    mesh, gas, _, trk = inputs.config_avalanche(seed=1, e_kv_cm=e_kv_cm)
+    trk.softening = 1e-9
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {"cells": int(mesh.n), "field_kv_cm": e_kv_cm, "steps": steps, "warmup": warmup,
+           "l2": "flushed (256 MiB write) before every timed step"}
+    for n in sizes:
+        ch = inputs.avalanche_snapshot(np.random.default_rng(100 + n), n, gap=trk.z_hi)
+        cap = int(n * 1.6) + 1024
+        ctx = obem.obem_create(capacity=cap, dt=trk.dt, seed=trk.seed, softening=trk.softening,
+                               z_lo=trk.z_lo, z_hi=trk.z_hi, beta=trk.beta, trial_cap=256,
+                               flags=obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD)
+        try:
+            obem.obem_gas_load(ctx, gas)
+            obem.obem_mesh_load(ctx, mesh)
+            obem.obem_bem_assemble(ctx, obem.OBEM_LU_FP32)
+            sigma = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+            obem.obem_bem_solve(ctx, mesh.group_voltage, sigma)
+            st = obem.DeviceState(cap)
+            st.upload(ch)
+            stats = [obem.new_stats() for _ in range(steps + 1)]
+            for k in range(warmup):
+                obem.obem_step(ctx, st, k, stats[steps])
+            torch.cuda.synchronize()
+            w = obem.read_stats(stats[steps])
+            assert w["status"] == 0, "avalanche warm-up step failed: %s" % w
+            snap = {k: getattr(st, k).clone() for k in ("pos_q", "vel", "id", "birth", "species", "scalars")}
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record()
+            for k in range(steps):
+                flush.zero_()
+                for key, v in snap.items():
+                    getattr(st, key).copy_(v, non_blocking=True)
+                obem.obem_step(ctx, st, warmup + k, stats[k])
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / steps
+            sts = [obem.read_stats(stats[k]) for k in range(steps)]
+            for s_ in sts:
+                assert s_["status"] == 0, "avalanche timed step failed: %s" % s_
+        finally:
+            obem.obem_destroy(ctx)
+        nc = sts[0]["n_before"]
+        ne = w["n_electron"]
+        out["n_%d" % n] = {"charges": nc, "electrons": ne, "ms_per_step": ms,
+                           "electron_steps_per_s": ne / (ms / 1e3),
+                           "charge_steps_per_s": nc / (ms / 1e3),
+                           "pair_evals_per_step": float(nc) * (nc - 1) + float(nc) * mesh.n,
+                           "spawned_pairs_per_step": sts[0]["spawned_pairs"]}
     return out
 
 

@@ -570,8 +570,11 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     P.c_lo = c->d_c_lo;
     P.v64 = c->d_v64; P.geo = c->d_geo64; P.np = n;
     double *d_em = NULL, *d_ep = NULL;
+    struct FreeOnExit { void *p; ~FreeOnExit() { if (p) cudaFree(p); } };
     OBEM_CUDA(c, cudaMalloc((void **)&d_em, sizeof(double) * n));
+    FreeOnExit em_guard{d_em};
     OBEM_CUDA(c, cudaMalloc((void **)&d_ep, sizeof(double) * n));
+    FreeOnExit ep_guard{d_ep};
     OBEM_CUDA(c, cudaMemcpyAsync(d_em, c->h_em, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     OBEM_CUDA(c, cudaMemcpyAsync(d_ep, c->h_ep, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     dim3 ag(n, (n + 127) / 128);
@@ -582,8 +585,6 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     std::vector<double> rn(n);
     OBEM_CUDA(c, cudaMemcpyAsync(rn.data(), d_rownorm, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     OBEM_CUDA(c, cudaStreamSynchronize(s));
-    cudaFree(d_em);
-    cudaFree(d_ep);
     c->a_norm_inf = 0.0;
     for (int i = 0; i < n; ++i) c->a_norm_inf = rn[i] > c->a_norm_inf ? rn[i] : c->a_norm_inf;
     // --- factorisation
@@ -602,7 +603,7 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     __nv_bfloat16 *bf16 = NULL;
     if (precision == OBEM_LU_BF16)
         OBEM_CUDA(c, cudaMalloc((void **)&bf16, sizeof(__nv_bfloat16) * bf16_panel_elems(n)));
-    struct FreeOnExit { void *p; ~FreeOnExit() { if (p) cudaFree(p); } } bf16_guard{bf16};
+    FreeOnExit bf16_guard{bf16};
     for (int k = 0; k < n; k += LU_NB) {
         const int kb = n - k < LU_NB ? n - k : LU_NB;
         const int rows = n - k;
