@@ -96,6 +96,7 @@ def _args():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-bem-precisions", action="store_true")
     p.add_argument("--no-avalanche", action="store_true")
+    p.add_argument("--avalanche-only", action="store_true")
     p.add_argument("--batch-chambers", type=int, default=256)
     p.add_argument("--batch-only", action="store_true")
     p.add_argument("--batch-skip-single", action="store_true",
@@ -673,6 +674,7 @@ def avalanche_timing(dev, sizes=(10_000, 100_000, 1_000_000), steps=5, warmup=3,
             snap = {k: getattr(st, k).clone() for k in ("pos_q", "vel", "id", "birth", "species", "scalars")}
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
+            obem.obem_profile(ctx, obem.OBEM_PROFILE_TIMES)      # stage events; uncounted kernels
             torch.cuda.synchronize()
             ev0.record()
             for k in range(steps):
@@ -683,6 +685,7 @@ def avalanche_timing(dev, sizes=(10_000, 100_000, 1_000_000), steps=5, warmup=3,
             ev1.record()
             torch.cuda.synchronize()
             ms = ev0.elapsed_time(ev1) / steps
+            prof = obem.obem_stage_times(ctx)
             sts = [obem.read_stats(stats[k]) for k in range(steps)]
             for s_ in sts:
                 assert s_["status"] == 0, "avalanche timed step failed: %s" % s_
@@ -694,7 +697,12 @@ def avalanche_timing(dev, sizes=(10_000, 100_000, 1_000_000), steps=5, warmup=3,
                            "electron_steps_per_s": ne / (ms / 1e3),
                            "charge_steps_per_s": nc / (ms / 1e3),
                            "pair_evals_per_step": float(nc) * (nc - 1) + float(nc) * mesh.n,
-                           "spawned_pairs_per_step": sts[0]["spawned_pairs"]}
+                           "spawned_pairs_per_step": sts[0]["spawned_pairs"],
+                           "stage_ms_per_step": {"cells": prof["cell_ms"] / steps,
+                                                 "cells_near": prof["near_ms"] / steps,
+                                                 "pairs": prof["pairs_ms"] / steps,
+                                                 "step": prof["step_ms"] / steps},
+                           "launches_per_step": prof["launches"] / steps}
     return out
 
 
@@ -784,6 +792,10 @@ def main():
     ws, rank, local = _dist()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.avalanche_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"avalanche_snapshots": avalanche_timing("cuda:%d" % local)}))
     elif a.batch_only:
         # the batched sweep alone (for profiling it): one JSON object
         import torch
