@@ -1038,10 +1038,8 @@ nbody_kernel(FieldLaunch L)
 // Charges are cut into tiles of SY_T = 1024.  Item (I, d) pairs tile I with
 // tile J = (I + d) mod n for d = 0 .. h_I (d = 0: the tile with itself, done
 // as ordered pairs); with h_I = floor(n/2), minus one for I >= n/2 when n is
-// even, every unordered tile pair occurs exactly once.  A work unit is up to
-// SY_CH consecutive items of one row (fewer for one set of a few thousand
-// charges, so that its units still spread over the SMs: sym_geom_one);
-// persistent blocks take units from a counter.
+// even, every unordered tile pair occurs exactly once.  A work unit is SY_CH
+// consecutive items of one row; persistent blocks take units from a counter.
 // Inside an off-diagonal item each warp holds 256 targets (8 per lane, four
 // f32x2 packs) and walks the sources of tile J in rounds of 32: the 32
 // sources sit one per lane and rotate around the warp by shuffles, carrying
@@ -1063,7 +1061,6 @@ nbody_kernel(FieldLaunch L)
 #define SY_WARPS (SY_THREADS / 32)
 #define SY_NG (SY_T / 32)      // 32-source groups of a tile (rounds of an item)
 #define SY_CH 16
-#define SY_UNITS_MIN 1024      // one set of charges: units are made finer below this count
 #define SY_FOLD 8              // rounds (of 32 sources) between compensated folds
 #define SY_DTILE 256           // staged sources of the d = 0 item
 // The kernel works on positions scaled by 2^40 and charges (k_C q) by 2^80:
@@ -1076,27 +1073,14 @@ nbody_kernel(FieldLaunch L)
 #define SY_VS 9.094947017729282e-13f         // 2^-40
 
 struct SymGeom {
-    int n, hmax, ch, nch;      // tiles, items per row - 1, items per unit, units per row
+    int n, hmax, nch;
 };
-__host__ __device__ inline SymGeom sym_geom_ch(int nt, int ch)
+__host__ __device__ inline SymGeom sym_geom(int nt)
 {
     SymGeom g;
     g.n = (nt + SY_T - 1) / SY_T;
     g.hmax = g.n / 2;
-    g.ch = ch;
-    g.nch = (g.hmax + 1 + ch - 1) / ch;
-    return g;
-}
-// a chamber of a batch: units of SY_CH items (the chambers' units together
-// keep the SMs busy)
-__host__ __device__ inline SymGeom sym_geom(int nt) { return sym_geom_ch(nt, SY_CH); }
-// one set of charges: SY_CH items per unit, halved (down to one) while there
-// are fewer than SY_UNITS_MIN units, e.g. 10 tiles: 60 one-item units instead
-// of 10 six-item ones for 456 resident blocks
-__host__ __device__ inline SymGeom sym_geom_one(int nt)
-{
-    SymGeom g = sym_geom_ch(nt, SY_CH);
-    while (g.ch > 1 && g.n * g.nch < SY_UNITS_MIN) g = sym_geom_ch(nt, g.ch >> 1);
+    g.nch = (g.hmax + 1 + SY_CH - 1) / SY_CH;
     return g;
 }
 // off-diagonal items of row I
@@ -1111,16 +1095,10 @@ size_t obem_sym_jpart_floats(int capacity)
     const SymGeom g = sym_geom(capacity);
     return (size_t)g.n * (g.hmax + 1) * 4 * SY_T;
 }
-// one set of charges: the most units any count up to capacity can have
 size_t obem_sym_ipart_floats(int capacity)
 {
-    const int nmax = sym_geom(capacity).n;
-    size_t units = 0;
-    for (int t = 1; t <= nmax; ++t) {
-        const SymGeom g = sym_geom_one(t * SY_T);
-        units = (size_t)g.n * g.nch > units ? (size_t)g.n * g.nch : units;
-    }
-    return units * 8 * SY_T;
+    const SymGeom g = sym_geom(capacity);
+    return (size_t)g.n * g.nch * 8 * SY_T;
 }
 
 // dynamic shared memory of nbsym_kernel: target-side S and C [NC][SY_NI][SY_THREADS]
@@ -1307,7 +1285,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
     } else {
         nt0 = L.nt_dev ? *L.nt_dev : L.nt;
         if (nt0 <= 0) return;
-        G0 = sym_geom_one(nt0);
+        G0 = sym_geom(nt0);
         units = G0.n * G0.nch;
     }
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1346,7 +1324,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
         const int lim = BATCH ? off + s_nt : nt0;        // end of the live slots
         const SymGeom G = BATCH ? sym_geom(s_nt) : G0;
         const int I = unit / G.nch, kch = unit % G.nch;
-        const int d0 = kch * G.ch, d1 = min(d0 + G.ch, sym_h(G, I) + 1);
+        const int d0 = kch * SY_CH, d1 = min(d0 + SY_CH, sym_h(G, I) + 1);
         const int base = off + I * SY_T;
         // targets of tile I: 8 per thread (k * 128 + tid), four packs
         u64 TX[SY_NP], TY[SY_NP], TZ[SY_NP], QI[SY_NP];
@@ -1585,7 +1563,7 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
     }
     const int lt = t - off;
     if (lt >= nt) return;
-    const SymGeom G = SB.nb ? sym_geom(nt) : sym_geom_one(nt);
+    const SymGeom G = sym_geom(nt);
     const int T = lt / SY_T, w = lt % SY_T;
     const int o = perm ? perm[t] : t;                  // sorted slot t is charge o
     double e[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1781,8 +1759,7 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
 
 size_t obem_sym_sizes(int capacity, size_t *ipart_floats)
 {
-    const SymGeom g = sym_geom(capacity);
-    *ipart_floats = (size_t)g.n * g.nch * 8 * SY_T;
+    *ipart_floats = obem_sym_ipart_floats(capacity);
     return obem_sym_jpart_floats(capacity);
 }
 
