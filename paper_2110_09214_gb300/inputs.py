@@ -247,6 +247,33 @@ def _wall(cx, cy, z0, z1, r0, r1, n_th, n_z, inward):
     return tri
 
 
+def _gem_foil(g: GemGeometry, z0, n_theta, n_r, n_zc, n_zk):
+    """Cells of one GEM foil centred at z = z0: the copper of its top and
+    bottom layers (faces and hole walls) and the biconical kapton hole walls."""
+    ap = g.pitch / 2.0
+    r_out, r_in = g.d_outer / 2, g.d_inner / 2
+    zk = g.t_kapton / 2
+    zc = zk + g.t_copper
+    top, bot, kap = [], [], []
+    for cx, cy in g.hole_centres():
+        top += _ring_face(cx, cy, z0 + zc, r_out, ap, n_theta, n_r, up=True)
+        top += _ring_face(cx, cy, z0 + zk, r_out, ap, n_theta, n_r, up=False)
+        bot += _ring_face(cx, cy, z0 - zk, r_out, ap, n_theta, n_r, up=True)
+        bot += _ring_face(cx, cy, z0 - zc, r_out, ap, n_theta, n_r, up=False)
+        top += list(_wall(cx, cy, z0 + zk, z0 + zc, r_out, r_out, n_theta, n_zc, inward=True))
+        bot += list(_wall(cx, cy, z0 - zc, z0 - zk, r_out, r_out, n_theta, n_zc, inward=True))
+        half = n_zk // 2
+        kap += list(_wall(cx, cy, z0 - zk, z0, r_out, r_in, n_theta, half, inward=True))
+        kap += list(_wall(cx, cy, z0, z0 + zk, r_in, r_out, n_theta, n_zk - half, inward=True))
+    return np.asarray(top, np.float64), np.asarray(bot, np.float64), np.asarray(kap, np.float64)
+
+
+def _plane_half_width(g: GemGeometry):
+    cen = g.hole_centres()
+    ext = np.abs(cen).max(axis=0) + g.pitch
+    return float(ext.max())
+
+
 def gem_mesh(geo: GemGeometry | None = None, n_theta=48, n_r=4, n_zc=2, n_zk=12,
              n_plane=20) -> Mesh:
     """Single-GEM patch: copper (top/bottom faces and hole walls of both
@@ -254,32 +281,15 @@ def gem_mesh(geo: GemGeometry | None = None, n_theta=48, n_r=4, n_zc=2, n_zk=12,
     side), and the drift and induction planes (Sec. 4.2 geometry; sizes of the
     CERN design).  Electrode groups as in GemGeometry.voltages()."""
     g = geo or GemGeometry()
-    ap = g.pitch / 2.0
-    r_out, r_in = g.d_outer / 2, g.d_inner / 2
-    zk = g.t_kapton / 2
-    zc = zk + g.t_copper
-    parts = []
-    top, bot, kap = [], [], []
-    for cx, cy in g.hole_centres():
-        top += _ring_face(cx, cy, zc, r_out, ap, n_theta, n_r, up=True)
-        top += _ring_face(cx, cy, zk, r_out, ap, n_theta, n_r, up=False)
-        bot += _ring_face(cx, cy, -zk, r_out, ap, n_theta, n_r, up=True)
-        bot += _ring_face(cx, cy, -zc, r_out, ap, n_theta, n_r, up=False)
-        top += list(_wall(cx, cy, zk, zc, r_out, r_out, n_theta, n_zc, inward=True))
-        bot += list(_wall(cx, cy, -zc, -zk, r_out, r_out, n_theta, n_zc, inward=True))
-        half = n_zk // 2
-        kap += list(_wall(cx, cy, -zk, 0.0, r_out, r_in, n_theta, half, inward=True))
-        kap += list(_wall(cx, cy, 0.0, zk, r_in, r_out, n_theta, n_zk - half, inward=True))
-    cen = g.hole_centres()
-    ext = np.abs(cen).max(axis=0) + g.pitch
-    L = float(ext.max())
+    top, bot, kap = _gem_foil(g, 0.0, n_theta, n_r, n_zc, n_zk)
+    L = _plane_half_width(g)
     drift = rect_plate(-L, L, -L, L, g.z_drift, n_plane, n_plane, up=False)
     anode = rect_plate(-L, L, -L, L, g.z_anode, n_plane, n_plane, up=True)
     parts = [(drift, KIND_ELECTRODE, 0, 1.0, 1.0),
-             (np.asarray(top, np.float64), KIND_ELECTRODE, 1, 1.0, 1.0),
-             (np.asarray(bot, np.float64), KIND_ELECTRODE, 2, 1.0, 1.0),
+             (top, KIND_ELECTRODE, 1, 1.0, 1.0),
+             (bot, KIND_ELECTRODE, 2, 1.0, 1.0),
              (anode, KIND_ELECTRODE, 3, 1.0, 1.0),
-             (np.asarray(kap, np.float64), KIND_DIELECTRIC, -1, g.eps_kapton, 1.0)]
+             (kap, KIND_DIELECTRIC, -1, g.eps_kapton, 1.0)]
     tri, kind, group, em, ep = _concat(parts)
     return Mesh(tri, kind, group, em, ep, g.voltages())
 
@@ -289,22 +299,29 @@ def gem_triangle_count(holes, n_theta, n_r, n_zc, n_zk, n_plane):
         + 2 * n_plane * n_plane * 2
 
 
-def gem_mesh_target(target=60000, geo: GemGeometry | None = None, tol=0.01) -> Mesh:
-    """GEM patch with a triangle count within tol of target (mesh resolution
-    chosen by a small search over the angular / radial / plane divisions)."""
-    g = geo or GemGeometry()
-    holes = len(g.hole_centres())
+def _resolution_search(target, count, tol):
+    """(n_theta, n_r, n_zk, n_plane) whose triangle count(n_theta, n_r, n_zc=2,
+    n_zk, n_plane) is within tol of target, hole walls as square as possible."""
     best = None
     for n_theta in range(24, 145, 12):
         for n_r in range(2, 9):
             for n_zk in range(4, 25, 2):
                 for n_plane in range(8, 41, 2):
-                    c = gem_triangle_count(holes, n_theta, n_r, 2, n_zk, n_plane)
+                    c = count(n_theta, n_r, 2, n_zk, n_plane)
                     err = abs(c - target) / target
                     score = (err > tol, abs(n_theta / (4 * n_zk) - 1.0), err)
                     if best is None or score < best[0]:
                         best = (score, (n_theta, n_r, n_zk, n_plane))
-    n_theta, n_r, n_zk, n_plane = best[1]
+    return best[1]
+
+
+def gem_mesh_target(target=60000, geo: GemGeometry | None = None, tol=0.01) -> Mesh:
+    """GEM patch with a triangle count within tol of target (mesh resolution
+    chosen by a small search over the angular / radial / plane divisions)."""
+    g = geo or GemGeometry()
+    holes = len(g.hole_centres())
+    n_theta, n_r, n_zk, n_plane = _resolution_search(
+        target, lambda *a: gem_triangle_count(holes, *a), tol)
     return gem_mesh(g, n_theta=n_theta, n_r=n_r, n_zc=2, n_zk=n_zk, n_plane=n_plane)
 
 
@@ -321,6 +338,98 @@ def gem_inside_solid(geo: GemGeometry, pts):
     in_foil = np.abs(z) < zc
     wall = np.where(np.abs(z) < zk, r_in + (r_out - r_in) * np.abs(z) / zk, r_out)
     return in_foil & (r >= wall)
+
+
+@dataclasses.dataclass
+class DoubleGemGeometry:
+    """Two foils of the single-GEM design stacked along z, their mid-planes
+    `spacing` apart (upper foil at +spacing/2), the drift plane gap_drift above
+    the upper foil's copper, the anode gap_induction below the lower foil's,
+    and a transfer field e_transfer between the foils."""
+    foil: GemGeometry = dataclasses.field(default_factory=GemGeometry)
+    spacing: float = 2e-3
+    e_transfer: float = 3e5       # V/m (3 kV/cm)
+
+    @property
+    def z_upper(self):
+        return self.spacing / 2
+
+    @property
+    def z_lower(self):
+        return -self.spacing / 2
+
+    @property
+    def z_drift(self):
+        return self.z_upper + self.foil.z_top + self.foil.gap_drift
+
+    @property
+    def z_anode(self):
+        return self.z_lower - self.foil.z_top - self.foil.gap_induction
+
+    def voltages(self):
+        """Groups: 0 drift plane, 1 / 2 upper foil top / bottom copper, 3 / 4
+        lower foil top / bottom copper, 5 anode (0 V)."""
+        f = self.foil
+        v5 = 0.0
+        v4 = v5 - f.e_induction * f.gap_induction
+        v3 = v4 - f.dv_gem
+        v2 = v3 - self.e_transfer * (self.spacing - 2 * f.z_top)
+        v1 = v2 - f.dv_gem
+        v0 = v1 - f.e_drift * f.gap_drift
+        return np.array([v0, v1, v2, v3, v4, v5], np.float64)
+
+
+def double_gem_mesh(geo: DoubleGemGeometry | None = None, n_theta=48, n_r=4, n_zc=2, n_zk=12,
+                    n_plane=20) -> Mesh:
+    """Double-GEM stack: both foils meshed as in gem_mesh (copper electrodes,
+    kapton hole walls as dd cells), the drift plane and the anode.  Electrode
+    groups as in DoubleGemGeometry.voltages()."""
+    d = geo or DoubleGemGeometry()
+    g = d.foil
+    t1, b1, k1 = _gem_foil(g, d.z_upper, n_theta, n_r, n_zc, n_zk)
+    t2, b2, k2 = _gem_foil(g, d.z_lower, n_theta, n_r, n_zc, n_zk)
+    L = _plane_half_width(g)
+    drift = rect_plate(-L, L, -L, L, d.z_drift, n_plane, n_plane, up=False)
+    anode = rect_plate(-L, L, -L, L, d.z_anode, n_plane, n_plane, up=True)
+    parts = [(drift, KIND_ELECTRODE, 0, 1.0, 1.0),
+             (t1, KIND_ELECTRODE, 1, 1.0, 1.0),
+             (b1, KIND_ELECTRODE, 2, 1.0, 1.0),
+             (t2, KIND_ELECTRODE, 3, 1.0, 1.0),
+             (b2, KIND_ELECTRODE, 4, 1.0, 1.0),
+             (anode, KIND_ELECTRODE, 5, 1.0, 1.0),
+             (np.concatenate([k1, k2]), KIND_DIELECTRIC, -1, g.eps_kapton, 1.0)]
+    tri, kind, group, em, ep = _concat(parts)
+    return Mesh(tri, kind, group, em, ep, d.voltages())
+
+
+def double_gem_triangle_count(holes, n_theta, n_r, n_zc, n_zk, n_plane):
+    return 2 * (gem_triangle_count(holes, n_theta, n_r, n_zc, n_zk, n_plane) - 2 * n_plane * n_plane * 2) \
+        + 2 * n_plane * n_plane * 2
+
+
+def double_gem_mesh_target(target=120000, geo: DoubleGemGeometry | None = None, tol=0.01) -> Mesh:
+    """Double-GEM stack with a triangle count within tol of target."""
+    d = geo or DoubleGemGeometry()
+    holes = len(d.foil.hole_centres())
+    n_theta, n_r, n_zk, n_plane = _resolution_search(
+        target, lambda *a: double_gem_triangle_count(holes, *a), tol)
+    return double_gem_mesh(d, n_theta=n_theta, n_r=n_r, n_zc=2, n_zk=n_zk, n_plane=n_plane)
+
+
+def double_gem_inside_solid(geo: DoubleGemGeometry, pts):
+    """True where a point lies inside copper or kapton of either foil."""
+    pts = np.asarray(pts, np.float64)
+    up = pts - np.array([0.0, 0.0, geo.z_upper])
+    lo = pts - np.array([0.0, 0.0, geo.z_lower])
+    return gem_inside_solid(geo.foil, up) | gem_inside_solid(geo.foil, lo)
+
+
+def probe_line(geo: DoubleGemGeometry, n=4096, centre=(0.0, 0.0)):
+    """n points on the axis of the hole at `centre`, at the midpoints of n
+    equal steps from the anode to the drift plane (none on a plane; the axis
+    runs through the holes, so none inside a solid)."""
+    z = geo.z_anode + (np.arange(n) + 0.5) * ((geo.z_drift - geo.z_anode) / n)
+    return np.column_stack([np.full(n, centre[0]), np.full(n, centre[1]), z])
 
 
 # --------------------------------------------------------------------------
@@ -538,3 +647,33 @@ def config_gem(seed=1, n=1_000_000, target_panels=60000, geo: GemGeometry | None
     ch = make_charges(pts, vel, sp)
     trk = Tracking(dt=1e-12, seed=seed, z_lo=g.z_anode, z_hi=g.z_drift, beta=1e-13)
     return mesh, argon_like_gas(), ch, trk, g
+
+
+def config_double_gem(seed=1, n=100_000, target_panels=120_000, n_probe=4096,
+                      geo: DoubleGemGeometry | None = None):
+    """Double-GEM stack (two single-GEM foils 2 mm apart) meshed into
+    target_panels triangles; n charges (half electrons, half cations) in
+    Gaussian clouds (sigma 20 um) on the hole axes of either foil, points
+    inside copper or kapton rejected; a probe line of n_probe points through
+    the central hole's axis from the anode to the drift plane."""
+    d = geo or DoubleGemGeometry()
+    mesh = double_gem_mesh_target(target_panels, d)
+    rng = np.random.default_rng(seed)
+    cen = d.foil.hole_centres()
+    zf = np.array([d.z_upper, d.z_lower])
+    pts = np.empty((0, 3))
+    while len(pts) < n:
+        m = int((n - len(pts)) * 1.3) + 16
+        h = rng.integers(0, len(cen), m)
+        f = rng.integers(0, 2, m)
+        p = np.column_stack([cen[h, 0], cen[h, 1], zf[f]]) + rng.normal(0, 20e-6, (m, 3))
+        p = p[~double_gem_inside_solid(d, p)]
+        pts = np.concatenate([pts, p])
+    pts = pts[:n]
+    ne = n // 2
+    sp = np.concatenate([np.zeros(ne, np.uint8), np.ones(n - ne, np.uint8)])
+    sp = sp[rng.permutation(n)]
+    vel = np.where((sp == SP_ELECTRON)[:, None], maxwellian(rng, n, 1.0, M_ELECTRON), 0.0)
+    ch = make_charges(pts, vel, sp)
+    trk = Tracking(dt=1e-12, seed=seed, z_lo=d.z_anode, z_hi=d.z_drift, beta=1e-13)
+    return mesh, argon_like_gas(), ch, trk, d, probe_line(d, n_probe)
