@@ -97,6 +97,9 @@ def _args():
     p.add_argument("--no-bem-precisions", action="store_true")
     p.add_argument("--no-avalanche", action="store_true")
     p.add_argument("--avalanche-only", action="store_true")
+    p.add_argument("--double-gem", action="store_true",
+                   help="also time the double-GEM gradient and charging-up workload (~120k cells)")
+    p.add_argument("--double-gem-only", action="store_true")
     p.add_argument("--batch-chambers", type=int, default=256)
     p.add_argument("--batch-only", action="store_true")
     p.add_argument("--batch-skip-single", action="store_true",
@@ -381,6 +384,9 @@ def run_ours(a, ws, rank, local):
     aval = None
     if ws == 1 and not a.no_avalanche:
         aval = avalanche_timing(dev)
+    dgem = None
+    if ws == 1 and a.double_gem:
+        dgem = double_gem_timing(dev, precision=a.precision)
     cpu = None
     if ws == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(mesh, ch, gas, trk, a.cpu_seconds)
@@ -433,6 +439,7 @@ def run_ours(a, ws, rank, local):
         "bem_precisions": bemp,
         "nbody_nn": nnres,
         "avalanche_snapshots": aval,
+        "double_gem": dgem,
     }
     print(json.dumps(line), flush=True)
 
@@ -706,6 +713,103 @@ def avalanche_timing(dev, sizes=(10_000, 100_000, 1_000_000), steps=5, warmup=3,
     return out
 
 
+def double_gem_timing(dev, steps=100, precision="bf16", n_charges=100_000, n_probe=4096):
+    """The differentiable field and charging-up on the double-GEM stack (two
+    single-GEM foils 2 mm apart, ~120k cells, 1e5 charges, a 4096-point probe
+    line through the central hole's axis): BEM set-up in the given LU
+    arithmetic; the gradient of L = mean |E|^2 on the probe line with respect
+    to the cell densities, the charges (positions and q) and the six electrode
+    voltages (adjoint solve); `steps` fused steps with surface hits, then the
+    collected charge turned into free density and the system re-solved."""
+    import torch
+    from paper_2110_09214_gb300 import inputs, obem
+    prec = {"fp32": obem.OBEM_LU_FP32, "tf32": obem.OBEM_LU_TF32, "bf16": obem.OBEM_LU_BF16,
+            "bf16x9": obem.OBEM_LU_BF16X9}[precision]
+    mesh, gas, ch, trk, d, probe = inputs.config_double_gem(seed=1, n=n_charges, n_probe=n_probe)
+    trk.softening = 1e-9
+    cap = 8 * ch.n + 1024        # room for the avalanche in the holes' field over `steps` steps
+    ng = len(mesh.group_voltage)
+    ctx = obem.obem_create(capacity=cap, dt=trk.dt, seed=trk.seed, softening=trk.softening,
+                           z_lo=trk.z_lo, z_hi=trk.z_hi, beta=trk.beta, trial_cap=256,
+                           flags=obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD
+                           | obem.OBEM_STEP_SURFACE_HITS)
+    out = {"cells": int(mesh.n), "charges": int(ch.n), "probe_points": int(n_probe), "lu": precision,
+           "geometry": "two single-GEM foils (19 holes each) 2 mm apart, drift 2 / transfer 3 / "
+                       "induction 3 kV/cm, 400 V per foil"}
+
+    def ev_ms(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    try:
+        obem.obem_gas_load(ctx, gas)
+        obem.obem_mesh_load(ctx, mesh)
+        t0 = time.perf_counter()
+        obem.obem_bem_assemble(ctx, prec)
+        out["assemble_factor_s"] = time.perf_counter() - t0
+        sigma = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+        rep = obem.obem_bem_solve(ctx, mesh.group_voltage, sigma)
+        out["solve"] = {k: rep[k] for k in ("iterations", "backward_error", "factor_ms", "solve_ms")}
+        # ---- gradient of the probe loss
+        tgt = torch.zeros((n_probe, 4), dtype=torch.float32, device=dev)
+        tgt[:, :3] = torch.from_numpy(probe.astype(np.float32)).to(dev)
+        src = torch.from_numpy(ch.pos_q).to(dev)
+        E = torch.empty((n_probe, 4), dtype=torch.float32, device=dev)
+        obem.obem_field_eval(ctx, tgt, E, sources=src, sigma=sigma)          # warm-up
+        fwd_ms, _ = ev_ms(lambda: obem.obem_field_eval(ctx, tgt, E, sources=src, sigma=sigma))
+        gE = torch.zeros_like(E)
+        gE[:, :3] = 2.0 * E[:, :3] / n_probe
+        dsig = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+        dsrc = torch.empty((ch.n, 4), dtype=torch.float32, device=dev)
+        obem.obem_field_eval_backward(ctx, tgt, gE, sources=src, sigma=sigma, dL_dsigma=dsig, dL_dsources=dsrc)
+        bwd_ms, _ = ev_ms(lambda: obem.obem_field_eval_backward(ctx, tgt, gE, sources=src, sigma=sigma,
+                                                                 dL_dsigma=dsig, dL_dsources=dsrc))
+        adj_ms, (dV, arep) = ev_ms(lambda: obem.obem_bem_solve_adjoint(ctx, dsig, ng))
+        loss = float((E[:, :3].double() ** 2).sum(dim=1).mean())
+        out["gradient"] = {"loss_V2_per_m2": loss, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+                           "adjoint_solve_ms": adj_ms, "adjoint_iterations": arep.iterations,
+                           "dL_dV": [float(x) for x in dV],
+                           "finite": bool(torch.isfinite(dsig).all() and torch.isfinite(dsrc).all()
+                                          and np.all(np.isfinite(dV)))}
+        # ---- charging-up: steps with surface hits, the collected charge as
+        # free density on the dielectric cells, re-solve
+        st = obem.DeviceState(cap)
+        st.upload(ch)
+        stats = [obem.new_stats(dev) for _ in range(steps)]
+        obem.obem_surface_charge(ctx, mesh.n, reset=True)
+
+        def run_steps():
+            for k in range(steps):
+                obem.obem_step(ctx, st, k, stats[k])
+
+        step_ms, _ = ev_ms(run_steps)
+        sts = [obem.read_stats(s) for s in stats]
+        bad = [k for k, s_ in enumerate(sts) if s_["status"] != 0]
+        sf = torch.zeros(mesh.n, dtype=torch.float32, device=dev)
+        counts = obem.obem_surface_charge(ctx, mesh.n, sigma_free=sf)
+        sig2 = torch.empty_like(sigma)
+        res_ms, rep2 = ev_ms(lambda: obem.obem_bem_solve(ctx, mesh.group_voltage, sig2, sigma_free=sf))
+        dd = mesh.kind == inputs.KIND_DIELECTRIC
+        out["charging_up"] = {"steps": steps, "ms_per_step": step_ms / steps,
+                              "first_failed_step": bad[0] if bad else None,
+                              "status": sts[bad[0]]["status"] if bad else 0,
+                              "charges_first_last": [sts[0]["n_before"], sts[-1]["n_after"]],
+                              "collected_e": int(np.abs(counts).sum()),
+                              "dielectric_cells_charged": int(((counts != 0) & dd).sum()),
+                              "resolve_ms": res_ms, "resolve_iterations": rep2["iterations"],
+                              "resolve_backward_error": rep2["backward_error"],
+                              "sigma_change_rel": float((sig2 - sigma).abs().max() / sigma.abs().max())}
+    finally:
+        obem.obem_destroy(ctx)
+    return out
+
+
 def fieldmap_timing(dev, n_grid=256):
     """The static field map at the size of the paper's grid timings (Sec. 2.4:
     a 256^3 grid, two parallel plates of 8,192 cells in total): build time of
@@ -792,6 +896,10 @@ def main():
     ws, rank, local = _dist()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.double_gem_only:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"double_gem": double_gem_timing("cuda:%d" % local, precision=a.precision)}))
     elif a.avalanche_only:
         import torch
         torch.cuda.set_device(local)

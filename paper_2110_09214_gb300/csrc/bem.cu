@@ -609,6 +609,16 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
         const int rows = n - k;
         int G = (rows + 31) / 32;
         if (G > nsm) G = nsm;
+        // above ~nsm x 787 rows (about 120k cells) one chunk per SM no longer
+        // fits a CTA's shared memory: m = 2, 3, 4 co-resident CTAs per SM,
+        // each chunk within 1/m of the SM's 224 KB (the occupancy check
+        // below rejects a size that still does not fit)
+        const size_t row_b = sizeof(float) * (size_t)(kb + 1);
+        if ((size_t)((rows + G - 1) / G) * row_b > 200 * 1024)
+            for (int m = 2; m <= 4; ++m) {
+                G = m * nsm;
+                if ((size_t)((rows + G - 1) / G) * row_b <= (size_t)224 * 1024 / m) break;
+            }
         if (G > 1000) G = 1000;
         int R = (rows + G - 1) / G;
         G = (rows + R - 1) / R;
