@@ -96,7 +96,7 @@ extern "C" int obem_alu_rates(obem_ctx *c, double *out, obem_stream stream)
         return obem_fail(c, OBEM_ERR_CUDA, "alu rates: allocation failed");
     }
     long long *hcyc = (long long *)malloc(sizeof(long long) * blocks);
-    double r0, f0, r1, f1, r2, f2, r3, f3, r4, f4;
+    double r0 = 0, f0 = 0, r1 = 0, f1 = 0, r2 = 0, f2 = 0, r3 = 0, f3 = 0, r4 = 0, f4 = 0;
     int rc = hcyc ? OBEM_OK : OBEM_ERR_ARG;
     if (rc == OBEM_OK) rc = alu_rate<0>(c, sms, sink, cyc, hcyc, s, r0, f0);
     if (rc == OBEM_OK) rc = alu_rate<1>(c, sms, sink, cyc, hcyc, s, r1, f1);
