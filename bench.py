@@ -100,6 +100,8 @@ def _args():
     p.add_argument("--double-gem", action="store_true",
                    help="also time the double-GEM gradient and charging-up workload (~120k cells)")
     p.add_argument("--double-gem-only", action="store_true")
+    p.add_argument("--cell-groups", action="store_true",
+                   help="far cells in fitted groups (OBEM_STEP_CELL_GROUPS) on the headline workload")
     p.add_argument("--batch-chambers", type=int, default=256)
     p.add_argument("--batch-only", action="store_true")
     p.add_argument("--batch-skip-single", action="store_true",
@@ -268,7 +270,8 @@ def run_ours(a, ws, rank, local):
     cap = int(ch.n * 1.6) + 1024
     ctx = obem.obem_create(capacity=cap, dt=trk.dt, seed=trk.seed, softening=trk.softening,
                            z_lo=trk.z_lo, z_hi=trk.z_hi, beta=trk.beta, trial_cap=256,
-                           flags=obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD)
+                           flags=obem.OBEM_STEP_SPACE_CHARGE | obem.OBEM_STEP_CELL_FIELD
+                           | (obem.OBEM_STEP_CELL_GROUPS if a.cell_groups else 0))
     obem.obem_gas_load(ctx, gas)
     obem.obem_mesh_load(ctx, mesh)
     t0 = time.perf_counter()
@@ -398,6 +401,7 @@ def run_ours(a, ws, rank, local):
         "config": {"workload": workload_name(mesh, ch),
                    "cells": mesh.n, "charges": ch.n, "l2": "flushed (256 MiB write) before every timed step",
                    "bem_precision": a.precision, "bem_assemble_factor_s": round(t_asm, 3),
+                   "cell_groups": bool(a.cell_groups),
                    "bem_factor_ms": rep["factor_ms"], "bem_solve_ms": rep["solve_ms"],
                    "bem_ir_iterations": rep["iterations"], "bem_backward_error": rep["backward_error"]},
         "charge_steps_per_s": charge_steps / sec,

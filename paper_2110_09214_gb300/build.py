@@ -26,6 +26,7 @@ UNITS = {
     "fieldmap.cu": [],
     "nn.cu": [],
     "batch.cu": [],
+    "cellgroup.cu": [],
 }
 
 

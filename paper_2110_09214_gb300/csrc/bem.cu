@@ -729,6 +729,7 @@ int obem_solve_system(obem_ctx *c, const double *gv, const float *sigma_free, co
     cudaEventDestroy(e1);
     cudaFree(d_gv);
     c->sigma_valid = 1;
+    c->sigma_ver++;
     if (rep) {
         rep->iterations = it;
         rep->status = status;

@@ -870,6 +870,221 @@ cell_kernel(FieldLaunch L)
     }
 }
 
+// ---------------------------------------------------------------- far cells in groups
+// cell_kernel with the cells visited group by group (CellGroups): a group
+// whose centre is at least sqrt(OBEM_GRP_THETA2) radii from the block's box,
+// and none of whose cells is too small for the block's frame, is emitted as
+// its OBEM_GRP_M equivalent charges; any other group's cells take the
+// per-cell tiers of cell_kernel.  A separated group holds no near cell: its
+// cells' centroids are >= 7 R from the box and no edge is longer than 2 R,
+// so each is > 3 h away, and its smallest h^2 passes the frame test; the
+// near kernels and this one therefore split the cells as with cell_kernel.
+// Points are gathered in s_pts and consumed by the packed loop when the
+// buffer is full, in group order (deterministic).
+template <bool WANT_V, bool COUNT>
+__global__ void __launch_bounds__(CT_THREADS)
+cell_group_kernel(FieldLaunch L, CellGroups G)
+{
+    __shared__ SrcPk s_pts[CT_MAXPTS];
+    __shared__ PanTile s_pan[CT_CHUNK];
+    __shared__ int s_n[CT_CHUNK], s_off[CT_CHUNK + 1];
+    static_assert(OBEM_GRP_K == CT_CHUNK, "a non-separated group is one per-cell round");
+    static_assert(OBEM_GRP_M <= CT_THREADS, "one thread per equivalent charge");
+    const int nt = L.nt_dev ? *L.nt_dev : L.nt;
+    int base, end;
+    if (!block_range(L, nt, base, end)) return;
+    float tx[CT_TPT], ty[CT_TPT], tz[CT_TPT];
+    int ti[CT_TPT];
+    BlockFrame F;
+    block_targets(L, end, base, tx, ty, tz, ti, F);
+    const bool warp_live = base + (int)(threadIdx.x & ~31u) < end;
+    const float3 o = F.o;
+    float S[CT_TPT][4], C[CT_TPT][4];
+#pragma unroll
+    for (int k = 0; k < CT_TPT; ++k) {
+        int ic = ti[k] >= 0 ? ti[k] : 0;
+        float4 e = L.E_out[ic];                    // near part + e_ext
+        S[k][0] = e.x; S[k][1] = e.y; S[k][2] = e.z; S[k][3] = WANT_V ? e.w : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) C[k][c] = 0.f;
+    }
+    u64 TX[2], TY[2], TZ[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        TX[p] = pk(tx[2 * p] - o.x, tx[2 * p + 1] - o.x);
+        TY[p] = pk(ty[2 * p] - o.y, ty[2 * p + 1] - o.y);
+        TZ[p] = pk(tz[2 * p] - o.z, tz[2 * p + 1] - o.z);
+    }
+    unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0;
+    const int np = L.panels.np;
+    const int tid = threadIdx.x;
+    int npend = 0;                                 // points waiting in s_pts[0, npend)
+    // the packed loop over s_pts[0, n) (padded to a multiple of 4); every
+    // thread calls it, and it leaves s_pts free for reuse
+    auto consume = [&](int n) {
+        const int npad = (n + 3) & ~3;
+        if (tid < npad - n) {
+            SrcPk sp;
+            sp.xx = sp.yy = sp.zz = pk(1e18f, 1e18f);
+            sp.qq = pk(0.f, 0.f);
+            s_pts[n + tid] = sp;
+        }
+        __syncthreads();
+        if (warp_live && npad > 0) {
+            u64 AX[2], AY[2], AZ[2], AV[2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) AX[p] = AY[p] = AZ[p] = AV[p] = 0ull;
+#pragma unroll 4
+            for (int jj = 0; jj < npad; ++jj) {
+                const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&s_pts[jj].xx);
+                const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&s_pts[jj].zz);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    u64 dx = sub2(TX[p], a.x);
+                    u64 dy = sub2(TY[p], a.y);
+                    u64 dz = sub2(TZ[p], b.x);
+                    u64 r2 = mul2(dx, dx);
+                    r2 = fma2(dy, dy, r2);
+                    r2 = fma2(dz, dz, r2);
+                    float ra, rb;
+                    upk(r2, ra, rb);
+                    u64 inv = pk(rsq(ra), rsq(rb));
+                    u64 sq = mul2(b.y, inv);
+                    u64 s3 = mul2(sq, mul2(inv, inv));
+                    AX[p] = fma2(dx, s3, AX[p]);
+                    AY[p] = fma2(dy, s3, AY[p]);
+                    AZ[p] = fma2(dz, s3, AZ[p]);
+                    if (WANT_V) AV[p] = add2(AV[p], sq);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float a0, a1;
+                upk(AX[p], a0, a1); two_sum_acc(S[2 * p][0], C[2 * p][0], a0); two_sum_acc(S[2 * p + 1][0], C[2 * p + 1][0], a1);
+                upk(AY[p], a0, a1); two_sum_acc(S[2 * p][1], C[2 * p][1], a0); two_sum_acc(S[2 * p + 1][1], C[2 * p + 1][1], a1);
+                upk(AZ[p], a0, a1); two_sum_acc(S[2 * p][2], C[2 * p][2], a0); two_sum_acc(S[2 * p + 1][2], C[2 * p + 1][2], a1);
+                if (WANT_V) { upk(AV[p], a0, a1); two_sum_acc(S[2 * p][3], C[2 * p][3], a0); two_sum_acc(S[2 * p + 1][3], C[2 * p + 1][3], a1); }
+            }
+        }
+        __syncthreads();
+    };
+    for (int g = 0; g < G.ng; ++g) {
+        const float4 cr = G.cr[g];
+        const float gd2 = box_d2(cr.x, cr.y, cr.z, F.lo, F.hi);
+        const bool sep = gd2 >= OBEM_GRP_THETA2 * (cr.w * cr.w) && G.h2min[g] >= (FRAME_H * FRAME_H) * F.scale2;
+        if (sep) {
+            // the group as its equivalent charges at c + R u_k
+            if (npend + OBEM_GRP_M > CT_MAXPTS - 4) { consume(npend); npend = 0; }
+            if (tid < OBEM_GRP_M) {
+                const float4 u = G.u[tid];
+                const float w = G.q[(size_t)g * OBEM_GRP_M + tid];
+                const float px = (cr.x - o.x) + cr.w * u.x, py = (cr.y - o.y) + cr.w * u.y,
+                            pz = (cr.z - o.z) + cr.w * u.z;
+                SrcPk sp;
+                sp.xx = pk(px, px); sp.yy = pk(py, py); sp.zz = pk(pz, pz); sp.qq = pk(w, w);
+                s_pts[npend + tid] = sp;
+            }
+            npend += OBEM_GRP_M;
+            continue;
+        }
+        // the group's cells with the per-cell tiers (as one round of cell_kernel)
+        __syncthreads();
+        if (tid < 32) {
+            const int slot = g * OBEM_GRP_K + tid;
+            int n = 0;
+            if (slot < np) {
+                const int j = G.perm[slot];
+                const float4 ca = L.panels.c_a[j], cl = L.panels.c_lo[j];
+                const float sg = L.sigma[j];
+                PanTile t;
+                t.cq = make_float4((ca.x - o.x) + cl.x, (ca.y - o.y) + cl.y, (ca.z - o.z) + cl.z, ca.w * sg);
+                t.g0 = L.panels.g0_h[j];
+                t.g1 = L.panels.g1[j];
+                t.g2 = L.panels.g2[j];
+                s_pan[tid] = t;
+                const float h2 = t.g0.w;
+                if (!cell_is_near(ca, h2, F)) {
+                    const float d2 = box_d2(ca.x, ca.y, ca.z, F.lo, F.hi);
+                    n = d2 >= TIER_1PT_H2 * h2 ? 1 : d2 >= TIER_3PT_H2 * h2 ? 3 : d2 >= TIER_4PT_H2 * h2 ? 4
+                      : d2 >= TIER_6PT_H2 * h2 ? 6 : d2 >= TIER_7PT_H2 * h2 ? 7 : 28;
+                }
+            }
+            int inc = n;
+            for (int q = 1; q < 32; q <<= 1) {
+                int v = __shfl_up_sync(0xffffffffu, inc, q);
+                if (tid >= q) inc += v;
+            }
+            s_n[tid] = n;
+            s_off[tid] = inc - n;
+            if (tid == 31) s_off[CT_CHUNK] = inc;
+        }
+        __syncthreads();
+        const int npts = s_off[CT_CHUNK];
+        if (npend + npts > CT_MAXPTS - 4) { consume(npend); npend = 0; }
+        {
+            const int c = tid >> 2, sub = tid & 3;
+            const int n = s_n[c];
+            if (n) {
+                const PanTile t = s_pan[c];
+                const float q = t.cq.w;
+                const float3 G0 = make_float3(t.g0.x, t.g0.y, t.g0.z), G1 = make_float3(t.g1.x, t.g1.y, t.g1.z),
+                             G2 = make_float3(t.g2.x, t.g2.y, t.g2.z);
+                for (int k = sub; k < n; k += 4) {
+                    float3 off;
+                    float w;
+                    if (n == 1) { off = make_float3(0.f, 0.f, 0.f); w = q; }
+                    else if (n == 3) {
+                        const float3 gk = k == 0 ? G0 : (k == 1 ? G1 : G2);
+                        off = make_float3(0.5f * gk.x, 0.5f * gk.y, 0.5f * gk.z);
+                        w = q * (1.0f / 3.0f);
+                    } else if (n == 4) {
+                        if (k == 0) { off = make_float3(0.f, 0.f, 0.f); w = q * (-27.0f / 48.0f); }
+                        else {
+                            const float3 gk = k == 1 ? G0 : (k == 2 ? G1 : G2);
+                            off = make_float3(0.4f * gk.x, 0.4f * gk.y, 0.4f * gk.z);
+                            w = q * (25.0f / 48.0f);
+                        }
+                    } else if (n == 6) {
+                        const float3 gk = (k % 3) == 0 ? G0 : ((k % 3) == 1 ? G1 : G2);
+                        const float sgk = k < 3 ? -0.33784547274789500f : 0.72527135947068800f;
+                        off = make_float3(sgk * gk.x, sgk * gk.y, sgk * gk.z);
+                        w = q * (k < 3 ? 0.223381589678011f : 0.109951743655322f);
+                    } else {
+                        float wf;
+                        rule_point(n == 7 ? 0 : 1, k, G0, G1, G2, off, wf);
+                        w = q * wf;
+                    }
+                    const float px = t.cq.x + off.x, py = t.cq.y + off.y, pz = t.cq.z + off.z;
+                    SrcPk sp;
+                    sp.xx = pk(px, px); sp.yy = pk(py, py); sp.zz = pk(pz, pz); sp.qq = pk(w, w);
+                    s_pts[npend + s_off[c] + k] = sp;
+                }
+            }
+        }
+        if (COUNT && tid < 32) {
+            const int n = s_n[tid];
+            cnt1 += n == 1; cnt3 += n >= 3 && n <= 6; cnt7 += n >= 7;
+        }
+        npend += npts;
+    }
+    consume(npend);
+#pragma unroll
+    for (int k = 0; k < CT_TPT; ++k) {
+        if (ti[k] < 0) continue;
+        float4 e;
+        e.x = (float)((double)S[k][0] + (double)C[k][0]);
+        e.y = (float)((double)S[k][1] + (double)C[k][1]);
+        e.z = (float)((double)S[k][2] + (double)C[k][2]);
+        e.w = WANT_V ? (float)((double)S[k][3] + (double)C[k][3]) : 0.f;
+        L.E_out[ti[k]] = e;
+    }
+    if (COUNT && L.counters) {
+        atomicAdd(&L.counters[1], cnt1);
+        atomicAdd(&L.counters[2], cnt3);
+        atomicAdd(&L.counters[3], cnt7);
+    }
+}
+
 // ---------------------------------------------------------------- all-pairs kernel
 // E_out[i] = init + k_C sum_{p != i} q_p (r_i - r_p) / (|r_i - r_p|^2 + eps^2)^(3/2)
 // init = E_out[i] when the cell kernels ran first (ADD), else e_ext.
@@ -1676,7 +1891,22 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             else { near_closed_kernel<false, false><<<cgrid, CT_THREADS, 0, s>>>(L); near_quad_kernel<false, false><<<cgrid, CT_THREADS, 0, s>>>(L); }
         }
         if (L.events) cudaEventRecord(L.events[5], s);
-        if (L.want_v) {
+        // far cells in groups: the context's own cells, one set of targets
+        const bool grouped = ctx->ngrp > 0 && L.panels.c_a == ctx->d_c_a && !L.block_cham;
+        if (grouped) {
+            CellGroups G;
+            int fitted = 0;
+            int rc = obem_cell_groups_fit(ctx, L.sigma, s, &G, &fitted);
+            if (rc != OBEM_OK) return rc;
+            if (L.events) ctx->launches += fitted;
+            if (L.want_v) {
+                if (L.counters) cell_group_kernel<true, true><<<cgrid, CT_THREADS, 0, s>>>(L, G);
+                else cell_group_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L, G);
+            } else {
+                if (L.counters) cell_group_kernel<false, true><<<cgrid, CT_THREADS, 0, s>>>(L, G);
+                else cell_group_kernel<false, false><<<cgrid, CT_THREADS, 0, s>>>(L, G);
+            }
+        } else if (L.want_v) {
             if (L.counters) cell_kernel<true, true><<<cgrid, CT_THREADS, 0, s>>>(L);
             else cell_kernel<true, false><<<cgrid, CT_THREADS, 0, s>>>(L);
         } else {

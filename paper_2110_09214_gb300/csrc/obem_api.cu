@@ -31,6 +31,7 @@ static void free_mesh(obem_ctx *c)
     free_dev(c->d_c_a); free_dev(c->d_g0_h); free_dev(c->d_g1); free_dev(c->d_g2);
     free_dev(c->d_nrm); free_dev(c->d_c_lo); free_dev(c->d_v64); free_dev(c->d_kind); free_dev(c->d_group);
     free_dev(c->d_geo64);
+    obem_cell_groups_free(c);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
     free_dev(c->d_tri9); free_dev(c->d_hstart); free_dev(c->d_htri); free_dev(c->d_area); free_dev(c->d_deposit);
@@ -544,6 +545,8 @@ extern "C" int obem_mesh_load(obem_ctx *c, int32_t np, const double *tri, const 
             rc = obem_fail(c, OBEM_ERR_CUDA, "mesh: deposit allocation failed");
     }
 #undef UP
+    if (rc == OBEM_OK && (c->cfg.flags & OBEM_STEP_CELL_GROUPS))
+        rc = obem_cell_groups_build(c, tri, g0, np);
     free(ca); free(g0); free(g1); free(g2); free(nr); free(cl);
     if (rc == OBEM_OK && cudaMalloc((void **)&c->d_sigma, sizeof(float) * np) != cudaSuccess)
         rc = obem_fail(c, OBEM_ERR_CUDA, "mesh: sigma allocation failed");

@@ -152,6 +152,19 @@ struct obem_ctx {
     double a_norm_inf;
     float *d_sigma;      // current sigma [np]
     int sigma_valid;
+    unsigned long long sigma_ver;   // bumped whenever d_sigma is rewritten
+    // far-cell groups (OBEM_STEP_CELL_GROUPS; ngrp == 0: not built)
+    int ngrp;
+    int32_t *d_grp_perm;
+    float4 *d_grp_cr;
+    float *d_grp_h2min;
+    float4 *d_grp_u;
+    float *d_grp_q;
+    double *d_grp_c64;   // [ngrp][4] centre and radius as the binary32 values, in FP64
+    double *d_grp_v;     // [OBEM_GRP_CHECK][3] unit directions of the check points
+    double *d_grp_pinv;  // [OBEM_GRP_M][OBEM_GRP_CHECK] least-squares fit for a unit radius
+    const float *grp_fit_sigma;     // sigma the charges in d_grp_q were fitted to (d_sigma only)
+    unsigned long long grp_fit_ver; // and its version
     cublasHandle_t cublas;
     // step scratch (capacity-sized)
     float4 *s_E;
@@ -278,6 +291,29 @@ struct SymBatch {
     int32_t *uoff;               // [nb + 1] work units before each chamber (written per launch)
     int32_t *negtot;             // [nb] negative charges per chamber (written per launch)
 };
+// Far cells in groups (OBEM_STEP_CELL_GROUPS): OBEM_GRP_K cells consecutive
+// in the Morton order of their centroids form a group; for a target block
+// whose box is at least sqrt(OBEM_GRP_THETA2) group radii from the group's
+// centre, the group is replaced by OBEM_GRP_M equivalent point charges on the
+// sphere of the group's radius, fitted in FP64 to the group's potential at
+// OBEM_GRP_CHECK points on a sphere of OBEM_GRP_RC radii.
+#define OBEM_GRP_K 32
+#define OBEM_GRP_M 49
+#define OBEM_GRP_CHECK 147
+#define OBEM_GRP_THETA2 64.0f
+#define OBEM_GRP_RC 2.5
+struct CellGroups {
+    int ng;
+    const int32_t *perm;     // [np] cell indices in group order (group g: [g K, g K + K))
+    const float4 *cr;        // [ng] centre x, y, z and radius (binary32, radius rounded up)
+    const float *h2min;      // [ng] smallest h^2 (longest edge squared) of the group's cells
+    const float4 *u;         // [OBEM_GRP_M] unit directions of the equivalent charges
+    const float *q;          // [ng * OBEM_GRP_M] equivalent charges (k_C q) for the current sigma
+};
+// cellgroup.cu
+int obem_cell_groups_build(obem_ctx *c, const double *tri, const float4 *g0_h, int np);
+void obem_cell_groups_free(obem_ctx *c);
+int obem_cell_groups_fit(obem_ctx *c, const float *sigma, cudaStream_t s, CellGroups *G, int *launched);
 #define OBEM_BINS_PER_AXIS 64
 #define OBEM_NBINS (OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS * OBEM_BINS_PER_AXIS)
 #define OBEM_SUPER_SHIFT 6                        // super-bin = 4 x 4 x 4 bins

@@ -21,6 +21,7 @@ OBEM_ERR_NOT_CONVERGED, OBEM_ERR_CAPACITY, OBEM_ERR_TIMEOUT, OBEM_ERR_TRIALS = -
 OBEM_LU_FP32, OBEM_LU_TF32, OBEM_LU_BF16, OBEM_LU_BF16X9 = 0, 1, 2, 3
 OBEM_STEP_SPACE_CHARGE, OBEM_STEP_CELL_FIELD, OBEM_STEP_FIELD_MAP, OBEM_STEP_PROB_COLLISION = 1, 2, 4, 8
 OBEM_STEP_NBODY_NN, OBEM_NN_GMAX, OBEM_STEP_SURFACE_HITS = 16, 64, 32
+OBEM_STEP_CELL_GROUPS = 64
 
 
 class ObemError(RuntimeError):
