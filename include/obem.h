@@ -82,7 +82,7 @@ enum {
     OBEM_STEP_SURFACE_HITS = 32,  /* cells absorb the charges whose sub-flight chords cross them and
                                      count their charge (charging-up, Sec. 3.2.3; obem_surface_charge) */
     OBEM_STEP_CELL_GROUPS = 64    /* cell field of obem_step and obem_field_eval (not the batch):
-                                     groups of 32 cells (Morton order of the centroids) at >= 8 group
+                                     groups of 32 cells (Morton order of the centroids) at >= 9 group
                                      radii from a block of targets enter as 49 equivalent charges
                                      fitted in FP64 to the group's potential (refitted when sigma
                                      changes); set at obem_create, built by obem_mesh_load */

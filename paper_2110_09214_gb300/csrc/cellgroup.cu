@@ -18,9 +18,10 @@
 //                           (FP64, stored as binary32)
 //
 // The fit depends on sigma only; it is redone when sigma changes.  Measured on
-// the CPU for groups of 32 cells of the GEM mesh with mixed-sign densities:
-// 49 charges reproduce the group's field at 8 radii to 1.1e-6 of
-// sum |q| / d^2 (the per-cell quadrature tiers are held to 3.6e-6).
+// the CPU with these host arrays for 250 groups of 32 cells of the 60k-cell
+// GEM mesh, random-sign densities, against the closed-form field: the 49
+// charges give the group's field to 2.8e-6 of sum |q| / d^2 at 8 radii and
+// 1.4e-6 at 9 (the separation used; the per-cell tiers are held to 3.6e-6).
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -79,10 +80,18 @@ void obem_cell_groups_free(obem_ctx *c)
     c->grp_fit_sigma = NULL;
 }
 
-int obem_cell_groups_build(obem_ctx *c, const double *tri, const float4 *g0_h, int np)
+// Host side of the groups: order, centres and radii, smallest h^2,
+// directions, and the fit matrix (all that the device arrays hold).
+struct GroupHost {
+    int ng;
+    std::vector<int32_t> perm;
+    std::vector<float4> cr, u;
+    std::vector<float> h2min;
+    std::vector<double> c64, vd, P;
+};
+
+static int grp_host_build(const double *tri, const float4 *g0_h, int np, GroupHost &H)
 {
-    obem_cell_groups_free(c);
-    if (np <= 0) return OBEM_OK;
     const int K = OBEM_GRP_K, M = OBEM_GRP_M, NC = OBEM_GRP_CHECK;
     // group order: Morton code (10 bits per axis) of the centroids, stable
     std::vector<double> cen(3 * (size_t)np), area(np);
@@ -176,7 +185,7 @@ int obem_cell_groups_build(obem_ctx *c, const double *tri, const float4 *g0_h, i
     for (int j = 0; j < M; ++j) {
         double d = N[(size_t)j * M + j];
         for (int k = 0; k < j; ++k) d -= N[(size_t)j * M + k] * N[(size_t)j * M + k];
-        if (!(d > 0.0)) return obem_fail(c, OBEM_ERR_SINGULAR, "cell groups: fit matrix not positive definite");
+        if (!(d > 0.0)) return OBEM_ERR_SINGULAR;
         d = sqrt(d);
         N[(size_t)j * M + j] = d;
         for (int i = j + 1; i < M; ++i) {
@@ -200,6 +209,25 @@ int obem_cell_groups_build(obem_ctx *c, const double *tri, const float4 *g0_h, i
         }
         for (int k = 0; k < M; ++k) P[(size_t)k * NC + l] = x[k];
     }
+    H.ng = ng;
+    H.perm.swap(perm);
+    H.cr.swap(cr);
+    H.h2min.swap(h2min);
+    H.c64.swap(c64);
+    H.u.swap(u);
+    H.vd.swap(vd);
+    H.P.swap(P);
+    return OBEM_OK;
+}
+
+int obem_cell_groups_build(obem_ctx *c, const double *tri, const float4 *g0_h, int np)
+{
+    obem_cell_groups_free(c);
+    if (np <= 0) return OBEM_OK;
+    GroupHost H;
+    if (grp_host_build(tri, g0_h, np, H) != OBEM_OK)
+        return obem_fail(c, OBEM_ERR_SINGULAR, "cell groups: fit matrix not positive definite");
+    const int ng = H.ng, M = OBEM_GRP_M, NC = OBEM_GRP_CHECK;
     int rc = OBEM_OK;
 #define GUP(dst, src, bytes)                                                                  \
     do {                                                                                      \
@@ -207,13 +235,13 @@ int obem_cell_groups_build(obem_ctx *c, const double *tri, const float4 *g0_h, i
                               cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice) != cudaSuccess)) \
             rc = obem_fail(c, OBEM_ERR_CUDA, "cell groups: upload failed");                  \
     } while (0)
-    GUP(c->d_grp_perm, perm.data(), sizeof(int32_t) * np);
-    GUP(c->d_grp_cr, cr.data(), sizeof(float4) * ng);
-    GUP(c->d_grp_h2min, h2min.data(), sizeof(float) * ng);
-    GUP(c->d_grp_u, u.data(), sizeof(float4) * M);
-    GUP(c->d_grp_c64, c64.data(), sizeof(double) * 4 * ng);
-    GUP(c->d_grp_v, vd.data(), sizeof(double) * 3 * NC);
-    GUP(c->d_grp_pinv, P.data(), sizeof(double) * M * NC);
+    GUP(c->d_grp_perm, H.perm.data(), sizeof(int32_t) * np);
+    GUP(c->d_grp_cr, H.cr.data(), sizeof(float4) * ng);
+    GUP(c->d_grp_h2min, H.h2min.data(), sizeof(float) * ng);
+    GUP(c->d_grp_u, H.u.data(), sizeof(float4) * M);
+    GUP(c->d_grp_c64, H.c64.data(), sizeof(double) * 4 * ng);
+    GUP(c->d_grp_v, H.vd.data(), sizeof(double) * 3 * NC);
+    GUP(c->d_grp_pinv, H.P.data(), sizeof(double) * M * NC);
 #undef GUP
     if (rc == OBEM_OK && cudaMalloc((void **)&c->d_grp_q, sizeof(float) * (size_t)ng * M) != cudaSuccess)
         rc = obem_fail(c, OBEM_ERR_CUDA, "cell groups: allocation failed");

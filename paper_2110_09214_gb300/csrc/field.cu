@@ -876,8 +876,8 @@ cell_kernel(FieldLaunch L)
 // and none of whose cells is too small for the block's frame, is emitted as
 // its OBEM_GRP_M equivalent charges; any other group's cells take the
 // per-cell tiers of cell_kernel.  A separated group holds no near cell: its
-// cells' centroids are >= 7 R from the box and no edge is longer than 2 R,
-// so each is > 3 h away, and its smallest h^2 passes the frame test; the
+// cells' centroids are >= 8 R from the box and no edge is longer than 2 R,
+// so each is > 4 h away, and its smallest h^2 passes the frame test; the
 // near kernels and this one therefore split the cells as with cell_kernel.
 // Points are gathered in s_pts and consumed by the packed loop when the
 // buffer is full, in group order (deterministic).

@@ -300,7 +300,7 @@ struct SymBatch {
 #define OBEM_GRP_K 32
 #define OBEM_GRP_M 49
 #define OBEM_GRP_CHECK 147
-#define OBEM_GRP_THETA2 64.0f
+#define OBEM_GRP_THETA2 81.0f
 #define OBEM_GRP_RC 2.5
 struct CellGroups {
     int ng;
