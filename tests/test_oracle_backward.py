@@ -266,3 +266,47 @@ def test_trilinear_is_exact_for_trilinear_functions_and_nodes():
     out = np.array([[-5.0, 1.0, 2.3], [10.0, 10.0, 10.0]])
     near = np.clip(out, lo, hi)
     assert np.allclose(oracle.trilinear(vals, lo, hi, dims, out), oracle.trilinear(vals, lo, hi, dims, near))
+
+
+# ----------------------------------------------------------------------------
+# the double-GEM stack (coarse, one hole per foil): six electrode voltages
+# ----------------------------------------------------------------------------
+def _coarse_double_gem():
+    d = inputs.DoubleGemGeometry(foil=inputs.GemGeometry(rings=0))
+    return d, inputs.double_gem_mesh(d, n_theta=12, n_r=2, n_zc=1, n_zk=4, n_plane=6)
+
+
+def test_double_gem_axis_field_is_axial():
+    """The coarse stack is symmetric under a half turn about the hole axis
+    (hexagonal cells, square planes, 12 angular divisions), so on the axis
+    the transverse field of the solved stack vanishes up to rounding."""
+    d, mesh = _coarse_double_gem()
+    sigma = oracle.bem_solve(mesh)
+    pts = inputs.probe_line(d, 64)
+    E, V = oracle.panel_field(mesh.tri, sigma, pts)
+    assert np.abs(E[:, :2]).max() <= 1e-9 * np.abs(E[:, 2]).max()
+    # maximum principle (charge-free gas, potential 0 at infinity, anode at
+    # 0 V): the potential stays within the electrodes' range
+    v = mesh.group_voltage
+    assert np.all(V >= v.min() * (1 + 1e-9)) and np.all(V <= max(v.max(), 0.0) + 1e-9 * np.abs(v).max())
+
+
+def test_double_gem_probe_loss_gradient_in_all_six_voltages():
+    """dL/dV_k (k = drift, two copper layers per foil, anode) of the probe
+    loss on the axis, the oracle's chain against central differences (L is
+    quadratic in V: exact up to rounding)."""
+    d, mesh = _coarse_double_gem()
+    pts = inputs.probe_line(d, 64)
+    V = mesh.group_voltage.copy()
+    L, sigma, E = _probe_loss(mesh, V, pts)
+    g = np.column_stack([2.0 * E / len(pts), np.zeros(len(pts))])
+    dsig, _, _ = oracle.field_backward(mesh.tri, sigma, pts, None, False, g)
+    _, dV = oracle.bem_solve_adjoint(mesh, dsig)
+    assert dV.shape == (6,)
+    h = 1e-4 * np.abs(V).max()
+    for k in range(6):
+        Vp, Vm = V.copy(), V.copy()
+        Vp[k] += h
+        Vm[k] -= h
+        fd = (_probe_loss(mesh, Vp, pts)[0] - _probe_loss(mesh, Vm, pts)[0]) / (2 * h)
+        assert abs(dV[k] - fd) <= 1e-7 * np.abs(dV).max(), (k, dV[k], fd)
