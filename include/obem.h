@@ -333,6 +333,15 @@ int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t s
  * Allocates scratch and synchronises `stream`. */
 int obem_alu_rates(obem_ctx *ctx, double *out, obem_stream stream);
 
+/* Failure-detection self-test of the bounded device wait that the LU panel
+ * factorisation uses between its CTAs (no passage in the paper): two blocks
+ * wait at that grid barrier for a third arrival that never comes; each gives
+ * up after the barrier's poll limit (2^24 polls: a few seconds), records
+ * OBEM_ERR_TIMEOUT in a device status word and returns, leaving the context
+ * usable.  Returns OBEM_OK when the status read back is OBEM_ERR_TIMEOUT,
+ * OBEM_ERR_STATE otherwise.  Allocates a few bytes, synchronises `stream`. */
+int obem_selftest_wait_timeout(obem_ctx *ctx, obem_stream stream);
+
 /* Stage timing of obem_step, for measurement (not part of the method).
  * obem_profile(ctx, 1) starts recording CUDA events on the step's stream
  * around its stages (up to 256 steps are kept; older ones are dropped) and

@@ -215,6 +215,36 @@ __device__ bool grid_barrier(int *flag, unsigned *count, volatile unsigned *gen,
     return ok != 0;
 }
 
+// Failure-detection self-test: the blocks wait at the barrier for one more
+// arrival than there are blocks, so every wait runs out after
+// BARRIER_SPIN_LIMIT polls and records OBEM_ERR_TIMEOUT in flag[0].
+__global__ void barrier_timeout_kernel(int *flag)
+{
+    unsigned *cnt = (unsigned *)&flag[1];
+    volatile unsigned *gen = (volatile unsigned *)&flag[2];
+    grid_barrier(flag, cnt, gen, gridDim.x + 1);
+}
+
+extern "C" int obem_selftest_wait_timeout(obem_ctx *c, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *flag = NULL;
+    OBEM_CUDA(c, cudaMalloc((void **)&flag, sizeof(int) * 8));
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int) * 8, s);
+    if (e == cudaSuccess) {
+        barrier_timeout_kernel<<<2, 32, 0, s>>>(flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flag);
+    if (e != cudaSuccess) return obem_fail(c, OBEM_ERR_CUDA, "wait self-test: %s", cudaGetErrorString(e));
+    if (h != OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_STATE, "wait self-test: status %d, expected a timeout", h);
+    return OBEM_OK;
+}
+
 struct PanelArgs {
     float *A;
     int n, k, kb, rows_per_cta;

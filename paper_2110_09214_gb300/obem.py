@@ -99,6 +99,7 @@ def load():
     lib.obem_field_eval_noalloc.restype = C.c_int
     lib.obem_profile.argtypes = [P, I]
     lib.obem_alu_rates.argtypes = [P, P, P]
+    lib.obem_selftest_wait_timeout.argtypes = [P, P]
     lib.obem_fieldmap_build.argtypes = [P, P, P, P, P, P]
     lib.obem_nbody_nn_eval.argtypes = [P, P, I, I, C.c_double, P, P]
     lib.obem_surface_charge.argtypes = [P, P, P, I, P]
@@ -335,6 +336,13 @@ def obem_field_eval_noalloc(targets, E_out, sources=None, self_exclude=False, ce
                                         _stream(stream))
     if rc != OBEM_OK:
         raise ObemError(rc, err.value.decode())
+
+
+def obem_selftest_wait_timeout(ctx, stream=None):
+    """Failure-detection self-test of the bounded device wait (see
+    include/obem.h): raises ObemError unless the wait ran out and reported
+    OBEM_ERR_TIMEOUT."""
+    _check(ctx, load().obem_selftest_wait_timeout(ctx, _stream(stream)))
 
 
 def obem_alu_rates(ctx, stream=None):
