@@ -66,8 +66,10 @@ static void sphere_points(int n, std::vector<double> &p)
 
 void obem_cell_groups_free(obem_ctx *c)
 {
-    cudaFree(c->d_grp_perm); cudaFree(c->d_grp_cr); cudaFree(c->d_grp_h2min); cudaFree(c->d_grp_u);
-    cudaFree(c->d_grp_q); cudaFree(c->d_grp_c64); cudaFree(c->d_grp_v); cudaFree(c->d_grp_pinv);
+    void *p[] = {c->d_grp_perm, c->d_grp_cr, c->d_grp_h2min, c->d_grp_u, c->d_grp_q, c->d_grp_c64, c->d_grp_v,
+                 c->d_grp_pinv};
+    for (void *q : p)
+        if (q) cudaFree(q);
     c->d_grp_perm = NULL;
     c->d_grp_cr = NULL;
     c->d_grp_h2min = NULL;
