@@ -12,6 +12,9 @@ Parity status of each function (see the test-suite for the pins):
   tri_integrals, panel_field, nbody_field, assemble, bem_solve, influence_rhs,
   philox, step, swarm fits, tri_jacobian, field_jacobian, field_backward,
   bem_solve_adjoint, grid_nodes, trilinear, nbody_nn: pinned.
+  gas_constants and the step on tabulated cross sections (grid lookup,
+  interpolation, thresholds, majorant, excitation and ionisation energetics):
+  pinned by tests/test_oracle_gas_pins.py.
   Swarm parameters of the synthetic argon-like gas: parity unpinned (no closed
   form; only GPU-vs-oracle agreement within 3 sigma and the Maxwell-model
   limits are checked).
