@@ -281,23 +281,28 @@ def run_ours(a, ws, rank, local):
     rep = obem.obem_bem_solve(ctx, mesh.group_voltage, sigma)
     st = obem.DeviceState(cap)
     st.upload(ch)
+    # The timed snapshot is the uploaded workload itself: every warm-up and
+    # every timed step starts from it (restored by a device copy) with the
+    # same step index, so each step does the same work and the workload does
+    # not depend on --warmup.
+    step_index = 0
     n_start = int((ch.species == 0).sum())
+    snap = {k: getattr(st, k).clone() for k in ("pos_q", "vel", "id", "birth", "species", "scalars")}
+
+    def restore():
+        for key, v in snap.items():
+            getattr(st, key).copy_(v, non_blocking=True)
+
     stats = [obem.new_stats() for _ in range(max(a.steps, a.warmup) + 1)]
     stats_c = obem.new_stats()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    step = 0
-    for _ in range(a.warmup):
-        obem.obem_step(ctx, st, step, stats[0])
-        step += 1
+    for k in range(a.warmup):
+        restore()
+        obem.obem_step(ctx, st, step_index, stats[k])
     torch.cuda.synchronize()
-    if a.warmup:
-        w = obem.read_stats(stats[0])
+    for k in range(a.warmup):
+        w = obem.read_stats(stats[k])
         assert w["status"] == 0, "warm-up step failed: %s" % w
-        n_start = w["n_electron"]
-    # ---- device-resident timed region: every step advances the same
-    # post-warm-up snapshot (restored by a device copy before each step), so
-    # each timed step is one pass over the 1e6-charge workload
-    snap = {k: getattr(st, k).clone() for k in ("pos_q", "vel", "id", "birth", "species", "scalars")}
     clocks = Clocks(local)
     obem.obem_profile(ctx, obem.OBEM_PROFILE_TIMES)      # stage events; uncounted kernels
     if ws > 1:
@@ -309,9 +314,8 @@ def run_ours(a, ws, rank, local):
     ev0.record()
     for k in range(a.steps):
         flush.zero_()
-        for key, v in snap.items():
-            getattr(st, key).copy_(v, non_blocking=True)
-        obem.obem_step(ctx, st, step + k, stats[k])
+        restore()
+        obem.obem_step(ctx, st, step_index, stats[k])
     ev1.record()
     torch.cuda.synchronize()
     if ws > 1:
@@ -321,13 +325,13 @@ def run_ours(a, ws, rank, local):
     prof = obem.obem_stage_times(ctx)
     # evaluation counts: one more pass over the same snapshot (untimed), in
     # the counting kernels; every timed step did the same evaluations
-    for key, v in snap.items():
-        getattr(st, key).copy_(v)
+    restore()
     obem.obem_profile(ctx, True)
-    obem.obem_step(ctx, st, step, stats_c)
+    obem.obem_step(ctx, st, step_index, stats_c)
     cnt = obem.obem_stage_times(ctx)
     obem.obem_profile(ctx, False)
-    for key in ("charge_pairs", "cells_1pt", "cells_3pt", "cells_7pt", "cells_closed"):
+    for key in ("charge_pairs", "cells_1pt", "cells_3pt", "cells_7pt", "cells_closed", "cell_points",
+                "cell_pairs_quad"):
         prof[key] = cnt[key] * a.steps
     sts = [obem.read_stats(stats[k]) for k in range(a.steps)]
     for s_ in sts:
@@ -339,8 +343,10 @@ def run_ours(a, ws, rank, local):
     print("bench: profile %s" % prof, file=sys.stderr)
     electron_steps = float(sum(e_counts))
     pairs = prof["charge_pairs"]
-    cell_evals = prof["cells_1pt"] + prof["cells_3pt"] + prof["cells_7pt"] + prof["cells_closed"]
-    charge_steps, pair_evals = float(sum(c_counts)), float(pairs + cell_evals)
+    # field pair evaluations: ordered charge pairs + (target, cell) pairs, the
+    # latter by quadrature or in the closed form
+    cell_pairs = prof["cell_pairs_quad"] + prof["cells_closed"]
+    charge_steps, pair_evals = float(sum(c_counts)), float(pairs + cell_pairs)
     if ws > 1:
         ms, (electron_steps, charge_steps, pair_evals) = reduce_over_ranks(
             ms, [electron_steps, charge_steps, pair_evals], dev)
@@ -360,12 +366,20 @@ def run_ours(a, ws, rank, local):
     mhz_load = clk.get("sm_mhz") or alu["sm_mhz"]
     lane_rate = LANE_OPS_PER_PAIR * pairs / kern_s / sms / (mhz_load * 1e6) if kern_s > 0 else 0.0
     traffic = nbody_traffic_per_launch(ch.n)
+    # whole-step and cell-stage FP32 rates: 18 flops per ordered charge pair
+    # and per (target, quadrature point) evaluation of the cell kernels (the
+    # same pair formula); the FP64 closed form of targets within one cell size
+    # is not counted in FP32 flops
+    cell_s = prof["cell_ms"] / 1e3
+    step_flops = FLOPS_PER_PAIR * (pairs + prof["cell_points"])
+    step_rate = step_flops / sec / 1e12 if sec > 0 else 0.0
+    cell_rate = FLOPS_PER_PAIR * prof["cell_points"] / cell_s / 1e12 if cell_s > 0 else 0.0
     # ---- end to end: state from pinned host memory and back, every step
     e2e = None
     if not a.no_e2e:
         for key, v in snap.items():
             getattr(st, key).copy_(v)
-        e2e = run_e2e(ctx, st, a.steps, step + a.steps, dev)
+        e2e = run_e2e(ctx, st, a.steps, step_index, dev)
     nnres = None
     if ws == 1 and not a.no_nn:
         for key, v in snap.items():
@@ -400,6 +414,8 @@ def run_ours(a, ws, rank, local):
         "data": "synthetic (seeded GEM mesh, charge clouds, argon-like cross sections)",
         "config": {"workload": workload_name(mesh, ch),
                    "cells": mesh.n, "charges": ch.n, "l2": "flushed (256 MiB write) before every timed step",
+                   "snapshot": "every warm-up and timed step starts from the generated workload (restored "
+                               "by a device copy) with step index %d: identical work per step" % step_index,
                    "bem_precision": a.precision, "bem_assemble_factor_s": round(t_asm, 3),
                    "cell_groups": bool(a.cell_groups),
                    "bem_factor_ms": rep["factor_ms"], "bem_solve_ms": rep["solve_ms"],
@@ -411,9 +427,12 @@ def run_ours(a, ws, rank, local):
         "stage_ms_per_step": {"cells": prof["cell_ms"] / a.steps, "cells_near": prof["near_ms"] / a.steps,
                               "pairs": prof["pairs_ms"] / a.steps,
                               "step": prof["step_ms"] / a.steps},
-        "cell_evals_per_step": {"centroid": prof["cells_1pt"] / a.steps, "3_to_6pt": prof["cells_3pt"] / a.steps,
-                                "7pt_or_more": prof["cells_7pt"] / a.steps,
-                                "closed_form": prof["cells_closed"] / a.steps},
+        "cell_evals_per_step": {"target_cell_pairs_quadrature": prof["cell_pairs_quad"] / a.steps,
+                                "target_cell_pairs_closed_form": prof["cells_closed"] / a.steps,
+                                "target_point_evals": prof["cell_points"] / a.steps,
+                                "block_cell_pairs_by_tier": {"centroid": prof["cells_1pt"] / a.steps,
+                                                             "3_to_6pt": prof["cells_3pt"] / a.steps,
+                                                             "7pt_or_more": prof["cells_7pt"] / a.steps}},
         "roofline": {"bound": "alu", "kernel": "nbsym_kernel (symmetric all-pairs field)", "achieved": achieved,
                      "peak": peak_meas, "unit": "TFLOP/s", "frac": achieved / peak_meas if peak_meas else None,
                      "peak_source": "measured: packed f32x2 FMA chains on all %d SMs at %.0f MHz "
@@ -430,6 +449,14 @@ def run_ours(a, ws, rank, local):
                                      "frac": lane_rate / alu["mix14_lane_ops_per_sm_clk"]
                                      if alu["mix14_lane_ops_per_sm_clk"] else None,
                                      "rsqrt_per_sm_clk": alu["rsqrt_per_sm_clk"]},
+                     "step": {"achieved": step_rate, "frac": step_rate / peak_meas if peak_meas else None,
+                              "unit": "TFLOP/s",
+                              "note": "whole fused step (ms_per_step): 18 flops per ordered charge pair and per "
+                                      "(target, quadrature point) of the cell kernels; FP64 closed form not "
+                                      "counted"},
+                     "cells": {"achieved": cell_rate, "frac": cell_rate / peak_meas if peak_meas else None,
+                               "unit": "TFLOP/s", "note": "cell stage (binning, near and far kernels): 18 flops "
+                                                          "per (target, quadrature point)"},
                      "traffic": traffic,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per target, "
                                        "scaled to %d targets (%s)" % (ch.n, os.path.relpath(TRAFFIC_RECORD, ROOT))
@@ -848,7 +875,9 @@ def fieldmap_timing(dev, n_grid=256):
 
 def run_e2e(ctx, st, steps, step0, dev):
     """Same metric through obem_step with the state in pinned host buffers:
-    H2D of the whole state before, D2H of the new state and the stats after."""
+    H2D of the whole state before, D2H of the new state and the stats after.
+    Every step starts from the same host state with the same step index, as
+    the device-resident timing does."""
     import torch
     from paper_2110_09214_gb300 import obem
     cap = st.capacity
@@ -877,7 +906,6 @@ def run_e2e(ctx, st, steps, step0, dev):
         st.scalars.copy_(hs, non_blocking=True)
         h2d += 8
         obem.obem_step(ctx, st, step, stats)
-        step += 1
         m_dev = st.scalars.to("cpu", non_blocking=False)
         m = int(m_dev[0])
         for k in out:

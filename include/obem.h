@@ -355,26 +355,32 @@ int obem_selftest_wait_timeout(obem_ctx *ctx, obem_stream stream);
  *   ms[3] whole obem_step, ms[4] the near-cell kernel alone (part of ms[0]);
  *   counts[0] steps recorded, counts[1] kernels launched by those steps,
  *   counts[2] charge pairs of the all-pairs kernel,
- *   counts[3..6] cell evaluations by tier (centroid, 3 to 6 points, 7 or more
- *   points including the near-cell rule, closed form).
+ *   counts[3..5] (block of targets, cell) pairs of the far-cell kernel by
+ *   quadrature tier (centroid, 3 to 6 points, 7 or more points; counts[5]
+ *   also counts (block, cell) pairs of the near-cell rules),
+ *   counts[6] (target, cell) pairs evaluated in the FP64 closed form,
+ *   counts[7] (target, quadrature point) evaluations of the far- and near-cell
+ *   kernels (a separated cell group's equivalent charges count as points),
+ *   counts[8] (target, cell) pairs evaluated by quadrature.
  * Recording is then reset.  obem_profile(ctx, 0) stops recording. */
 #define OBEM_PROFILE_TIMES 2
 int obem_profile(obem_ctx *ctx, int32_t enable);
-int obem_stage_times(obem_ctx *ctx, double *ms /* [5] */, int64_t *counts /* [7] */);
+int obem_stage_times(obem_ctx *ctx, double *ms /* [5] */, int64_t *counts /* [9] */);
 
 /* Field evaluation that allocates no memory and needs no context.
  *
  * There is no counterpart in the paper: this entry point exists for callers
- * that cannot call cudaMalloc -- code that runs while a CUDA graph is being
- * captured, plug-ins held to a host application's fixed device-memory budget,
- * real-time loops that cannot take the latency of an allocation -- and so
- * cannot create an obem_ctx (obem_create and obem_mesh_load allocate).
+ * that cannot call cudaMalloc -- plug-ins held to a host application's fixed
+ * device-memory budget, real-time loops that cannot take the latency or the
+ * possible failure of an allocation, code whose host framework owns every
+ * allocation -- and so cannot create an obem_ctx (obem_create and
+ * obem_mesh_load allocate).
  *
- * It computes what obem_field_eval computes (cell field of Eqs. (BEM2),
- * (BEM3) plus the Coulomb field of Eq. (nbody)) with the same kernels, but
- * all of its scratch memory is one fixed array compiled into the library
- * (about 5 MB, held on every GPU that loads the library until the process
- * exits).  Inputs and outputs are the caller's:
+ * It computes what obem_field_eval computes (the cell field plus the Coulomb
+ * field of the charges) with the same kernels, but all of its scratch memory
+ * is one fixed array compiled into the library (about 5 MB, held on every
+ * GPU that loads the library until the process exits).  Inputs and outputs
+ * are the caller's:
  *   targets   device [nt][4] (x, y, z, unused), nt <= OBEM_NOALLOC_MAX_TARGETS
  *   sources   device [ns][4] (x, y, z, q) or NULL
  *   cell_xyz  device [np][3][3] FP64 cell vertices (layout of obem_mesh_load's
@@ -384,11 +390,10 @@ int obem_stage_times(obem_ctx *ctx, double *ms /* [5] */, int64_t *counts /* [7]
  *   err       optional host buffer of err_len bytes for an error message
  * Sizes beyond the maxima return OBEM_ERR_ARG with a message in err; nothing
  * is launched then.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current, so make that first
- * call before any stream capture.  Every call reuses the same array and leaves
- * its contents behind: two calls whose work overlaps on the GPU (on different
- * streams, or from different host threads) race on it and give wrong results;
- * serialise them on one stream. */
+ * address (cudaGetSymbolAddress) with that device current.  Every call reuses
+ * the same array and leaves its contents behind: two calls whose work
+ * overlaps on the GPU (on different streams, or from different host threads)
+ * race on it and give wrong results; serialise them on one stream. */
 enum { OBEM_NOALLOC_MAX_TARGETS = 262144, OBEM_NOALLOC_MAX_CELLS = 16384 };
 int obem_field_eval_noalloc(const float *targets, int32_t nt, const float *sources, int32_t ns,
                             int32_t self_exclude, const double *cell_xyz, const float *sigma,

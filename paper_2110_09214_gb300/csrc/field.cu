@@ -586,7 +586,11 @@ near_quad_kernel(FieldLaunch L)
         TY[p] = pk(ty[2 * p], ty[2 * p + 1]);
         TZ[p] = pk(tz[2 * p], tz[2 * p + 1]);
     }
-    unsigned long long cntQ = 0;
+    unsigned long long cntQ = 0, cntP = 0, cntC = 0;
+    int wlive = 0;                                        // live targets of this warp
+    if (COUNT)
+#pragma unroll
+        for (int k = 0; k < CT_TPT; ++k) wlive += __popc(__ballot_sync(0xffffffffu, ti[k] >= 0));
     for (int pb = 0; pb < np; pb += NEAR_CHUNK) {
         const int tot = near_list(L, poff, np, pb, F, s_list, s_cnt);
         for (int g = 0; g < tot; g += NQ_CELLS) {
@@ -625,6 +629,7 @@ near_quad_kernel(FieldLaunch L)
                 const bool coarse = box_d2(ch.x + cl.x, ch.y + cl.y, ch.z + cl.z, wlo, whi) >= TIER_28PT_H2 * ch.w;
                 const SrcPk *qp = coarse ? s_off28[c] : s_off[c];
                 const int nqp = coarse ? 28 : NQ_PTS;
+                if (COUNT && (tid & 31) == 0) { cntP += (unsigned long long)nqp * wlive; cntC += wlive; }
                 // exact target - centroid per pack; targets within h get a
                 // 1e30 m^2 softening, i.e. no term here (theirs is the closed form)
                 u64 DX[2], DY[2], DZ[2], EP[2];
@@ -684,6 +689,7 @@ near_quad_kernel(FieldLaunch L)
         L.E_out[ti[k]] = e;
     }
     if (COUNT && L.counters && tid == 0) atomicAdd(&L.counters[3], cntQ);
+    if (COUNT && L.counters && (tid & 31) == 0) { atomicAdd(&L.counters[5], cntP); atomicAdd(&L.counters[6], cntC); }
 }
 
 // far cells as quadrature-point sources, in the block's frame
@@ -720,7 +726,7 @@ cell_kernel(FieldLaunch L)
         TY[p] = pk(ty[2 * p] - o.y, ty[2 * p + 1] - o.y);
         TZ[p] = pk(tz[2 * p] - o.z, tz[2 * p + 1] - o.z);
     }
-    unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0;
+    unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0, cntP = 0, cntC = 0;
     int poff = 0, np = L.panels.np;
     if (BATCH) block_cells(L, poff, np);
     const int tid = threadIdx.x;
@@ -814,6 +820,8 @@ cell_kernel(FieldLaunch L)
         if (COUNT && tid < 32) {
             const int n = s_n[tid];
             cnt1 += n == 1; cnt3 += n >= 3 && n <= 6; cnt7 += n >= 7;
+            const unsigned nc = __popc(__ballot_sync(0xffffffffu, n > 0));
+            if (tid == 0) { cntP += (unsigned long long)npts * (end - base); cntC += (unsigned long long)nc * (end - base); }
         }
         __syncthreads();
         const int npad = warp_live ? (npts + 3) & ~3 : 0;
@@ -867,6 +875,7 @@ cell_kernel(FieldLaunch L)
         atomicAdd(&L.counters[1], cnt1);
         atomicAdd(&L.counters[2], cnt3);
         atomicAdd(&L.counters[3], cnt7);
+        if (tid == 0) { atomicAdd(&L.counters[5], cntP); atomicAdd(&L.counters[6], cntC); }
     }
 }
 
@@ -915,13 +924,14 @@ cell_group_kernel(FieldLaunch L, CellGroups G)
         TY[p] = pk(ty[2 * p] - o.y, ty[2 * p + 1] - o.y);
         TZ[p] = pk(tz[2 * p] - o.z, tz[2 * p + 1] - o.z);
     }
-    unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0;
+    unsigned long long cnt1 = 0, cnt3 = 0, cnt7 = 0, cntP = 0, cntC = 0;
     const int np = L.panels.np;
     const int tid = threadIdx.x;
     int npend = 0;                                 // points waiting in s_pts[0, npend)
     // the packed loop over s_pts[0, n) (padded to a multiple of 4); every
     // thread calls it, and it leaves s_pts free for reuse
     auto consume = [&](int n) {
+        if (COUNT && tid == 0) cntP += (unsigned long long)n * (end - base);
         const int npad = (n + 3) & ~3;
         if (tid < npad - n) {
             SrcPk sp;
@@ -985,6 +995,7 @@ cell_group_kernel(FieldLaunch L, CellGroups G)
                 s_pts[npend + tid] = sp;
             }
             npend += OBEM_GRP_M;
+            if (COUNT && tid == 0) cntC += (unsigned long long)OBEM_GRP_K * (end - base);
             continue;
         }
         // the group's cells with the per-cell tiers (as one round of cell_kernel)
@@ -1064,6 +1075,8 @@ cell_group_kernel(FieldLaunch L, CellGroups G)
         if (COUNT && tid < 32) {
             const int n = s_n[tid];
             cnt1 += n == 1; cnt3 += n >= 3 && n <= 6; cnt7 += n >= 7;
+            const unsigned nc = __popc(__ballot_sync(0xffffffffu, n > 0));
+            if (tid == 0) cntC += (unsigned long long)nc * (end - base);
         }
         npend += npts;
     }
@@ -1082,6 +1095,7 @@ cell_group_kernel(FieldLaunch L, CellGroups G)
         atomicAdd(&L.counters[1], cnt1);
         atomicAdd(&L.counters[2], cnt3);
         atomicAdd(&L.counters[3], cnt7);
+        if (tid == 0) { atomicAdd(&L.counters[5], cntP); atomicAdd(&L.counters[6], cntC); }
     }
 }
 
@@ -2093,11 +2107,11 @@ int obem_launch_field_batch(obem_ctx *ctx, const FieldBatch &F, const float4 *po
 // ====================================================================
 // Field evaluation with no context and no allocation.
 //
-// For callers that cannot call cudaMalloc -- code running while a CUDA graph
-// is being captured, plug-ins that must live inside a host application's
-// fixed memory budget, or real-time loops where allocation latency is not
-// allowed -- and that therefore cannot create an obem_ctx (whose creation
-// and mesh upload allocate).  The same kernels as obem_field_eval run on
+// For callers that cannot call cudaMalloc -- plug-ins that must live inside a
+// host application's fixed device-memory budget, or real-time loops where
+// the latency or failure of an allocation is not allowed -- and that
+// therefore cannot create an obem_ctx (whose creation and mesh upload
+// allocate).  The same kernels as obem_field_eval run on
 // scratch held in one file-scope device array of fixed size, reached through
 // cudaGetSymbolAddress.
 // ====================================================================

@@ -189,10 +189,10 @@ extern "C" int obem_profile(obem_ctx *c, int32_t enable)
     if (enable && !c->prof_ev) {
         c->prof_ev = (cudaEvent_t *)calloc(OBEM_PROF_EV * OBEM_PROF_MAX, sizeof(cudaEvent_t));
         for (int i = 0; i < OBEM_PROF_EV * OBEM_PROF_MAX; ++i) OBEM_CUDA(c, cudaEventCreate(&c->prof_ev[i]));
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_counters, sizeof(unsigned long long) * 5));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_counters, sizeof(unsigned long long) * OBEM_NCOUNTERS));
     }
     if (enable) {
-        OBEM_CUDA(c, cudaMemset(c->d_counters, 0, sizeof(unsigned long long) * 5));
+        OBEM_CUDA(c, cudaMemset(c->d_counters, 0, sizeof(unsigned long long) * OBEM_NCOUNTERS));
         c->prof_n = 0;
         c->launches = 0;
         c->steps_recorded = 0;
@@ -205,7 +205,7 @@ extern "C" int obem_stage_times(obem_ctx *c, double *ms, int64_t *counts)
 {
     if (!c || !ms || !counts) return OBEM_ERR_ARG;
     for (int k = 0; k < 5; ++k) ms[k] = 0.0;
-    for (int k = 0; k < 7; ++k) counts[k] = 0;
+    for (int k = 0; k < 2 + OBEM_NCOUNTERS; ++k) counts[k] = 0;
     if (!c->prof_ev) return OBEM_OK;
     int n = c->prof_n < OBEM_PROF_MAX ? c->prof_n : OBEM_PROF_MAX;
     for (int r = 0; r < n; ++r) {
@@ -218,11 +218,11 @@ extern "C" int obem_stage_times(obem_ctx *c, double *ms, int64_t *counts)
         OBEM_CUDA(c, cudaEventElapsedTime(&t, e[0], e[3])); ms[3] += t;
         OBEM_CUDA(c, cudaEventElapsedTime(&t, e[4], e[5])); ms[4] += t;
     }
-    unsigned long long h[5];
+    unsigned long long h[OBEM_NCOUNTERS];
     OBEM_CUDA(c, cudaMemcpy(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost));
     counts[0] = n;
     counts[1] = c->launches;
-    for (int k = 0; k < 5; ++k) counts[2 + k] = (int64_t)h[k];
+    for (int k = 0; k < OBEM_NCOUNTERS; ++k) counts[2 + k] = (int64_t)h[k];
     OBEM_CUDA(c, cudaMemset(c->d_counters, 0, sizeof h));
     c->prof_n = 0;
     c->launches = 0;

@@ -22,6 +22,7 @@
 
 #define OBEM_MAX_PROC 32
 #define OBEM_MAX_TRIALS 256
+#define OBEM_NCOUNTERS 7      // evaluation counters of the profiling variants of the field kernels
 
 // ---------------------------------------------------------------- gas constants
 // Everything the step kernels need, passed by value.  The float members are
@@ -218,7 +219,7 @@ struct obem_ctx {
     int prof_on;
     int prof_n;                      // recorded steps (ring of OBEM_PROF_MAX)
     cudaEvent_t *prof_ev;            // [OBEM_PROF_MAX][OBEM_PROF_EV]
-    unsigned long long *d_counters;  // [5] pairs, 1pt, 3pt, 7pt, closed form
+    unsigned long long *d_counters;  // [OBEM_NCOUNTERS]: see FieldLaunch::counters
     long long launches;              // kernels launched by recorded steps
     long long steps_recorded;
 };
@@ -258,7 +259,10 @@ struct FieldLaunch {
     float4 *E_out;
     float3 e_ext;
     int want_v;
-    // optional tier counters [5]: charge pairs, 1-point, 3-point, 7-point, closed-form
+    // optional counters [OBEM_NCOUNTERS]: charge pairs; (target block, cell)
+    // pairs by tier: 1 point, 3-6 points, 7 or more; (target, cell) pairs in
+    // the FP64 closed form; (target, quadrature point) evaluations; (target,
+    // cell) pairs evaluated by quadrature
     unsigned long long *counters;
     // optional events: [1] after the cell kernels, [2] after the all-pairs kernel,
     // [4] / [5] around the near-cell kernel

@@ -395,12 +395,12 @@ def obem_profile(ctx, enable=True):
 def obem_stage_times(ctx):
     """Stage times (ms, summed over the recorded steps) and counters."""
     ms = np.zeros(5, np.float64)
-    cnt = np.zeros(7, np.int64)
+    cnt = np.zeros(9, np.int64)
     _check(ctx, load().obem_stage_times(ctx, ms.ctypes.data, cnt.ctypes.data))
     return {"cell_ms": ms[0], "pairs_ms": ms[1], "step_ms": ms[2], "total_ms": ms[3], "near_ms": ms[4],
             "steps": int(cnt[0]), "launches": int(cnt[1]), "charge_pairs": int(cnt[2]),
             "cells_1pt": int(cnt[3]), "cells_3pt": int(cnt[4]), "cells_7pt": int(cnt[5]),
-            "cells_closed": int(cnt[6])}
+            "cells_closed": int(cnt[6]), "cell_points": int(cnt[7]), "cell_pairs_quad": int(cnt[8])}
 
 
 # ---------------------------------------------------------------- device state

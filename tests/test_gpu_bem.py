@@ -128,3 +128,27 @@ def test_solve_before_assemble_is_a_state_error():
         assert e.value.code == obem.OBEM_ERR_STATE
     finally:
         obem.obem_destroy(ctx)
+
+
+def test_bounded_wait_reports_timeout_and_leaves_the_context_usable():
+    """Failure detection without a fault: the grid barrier that the LU panel
+    factorisation uses between its CTAs is made to wait for one more block
+    than was launched.  Every wait gives up after its poll limit, the kernel
+    records OBEM_ERR_TIMEOUT in its status word and returns (the call reports
+    OBEM_OK when it reads that status back); the same context then assembles,
+    factorises and solves a small system correctly."""
+    mesh = inputs.parallel_plates(1e-2, 1e-3, 8, 0.0, 100.0)
+    ctx = obem.obem_create(capacity=8, dt=1e-12)
+    try:
+        obem.obem_selftest_wait_timeout(ctx)
+        obem.obem_mesh_load(ctx, mesh)
+        obem.obem_bem_assemble(ctx, obem.OBEM_LU_FP32)
+        out = torch.empty(mesh.n, dtype=torch.float32, device="cuda")
+        rep = obem.obem_bem_solve(ctx, mesh.group_voltage, out)
+        assert rep["status"] == 0
+        sig = out.cpu().numpy().astype(np.float64)
+    finally:
+        obem.obem_destroy(ctx)
+    A = oracle.assemble(mesh)
+    b = oracle.bem_rhs(mesh)
+    _check(mesh, sig, A, b, oracle.solve(A, b))

@@ -237,11 +237,35 @@ def test_empty_and_bad_arguments():
         obem.obem_destroy(ctx)
 
 
+def _stratified_sample(mesh, pts, rng, n_near=1024, n_mid=1024, n_rand=2048):
+    """Targets of the full-size workload stratified by their distance d to the
+    nearest cell centroid in units of that cell's longest edge h: up to
+    n_near with d < h (the FP64 closed form and the 112-point rule), up to
+    n_mid with h <= d < 4 h (the 28-point and near rules), and n_rand drawn
+    uniformly from the rest."""
+    from scipy.spatial import cKDTree
+    tri = np.asarray(mesh.tri, np.float64)
+    cen = tri.mean(axis=1)
+    h = np.max(np.linalg.norm(tri - np.roll(tri, 1, axis=1), axis=2), axis=1)
+    d, j = cKDTree(cen).query(np.asarray(pts, np.float64), k=1)
+    r = d / h[j]
+    near = np.flatnonzero(r < 1.0)
+    mid = np.flatnonzero((r >= 1.0) & (r < 4.0))
+    pick = [rng.choice(near, min(n_near, len(near)), replace=False),
+            rng.choice(mid, min(n_mid, len(mid)), replace=False)]
+    rest = np.setdiff1d(np.arange(len(pts)), np.concatenate(pick))
+    pick.append(rng.choice(rest, n_rand, replace=False))
+    return np.sort(np.concatenate(pick)), len(pick[0]), len(pick[1])
+
+
 @pytest.mark.parametrize("symmetric", [False, True])
 def test_full_size_gem_sampled(symmetric):
     """The headline workload at full size -- 60k cells, 1e6 charges -- in the
     launch configuration of the bench (symmetric all-pairs kernel) and with
-    the one-sided kernel; the oracle computes 64 sampled targets one by one."""
+    the one-sided kernel; the oracle computes about 4096 sampled targets, a
+    quarter of them within one cell size of a cell (closed-form and near
+    rules at size).  The guard of the metric is 1e-2 of the rms field over
+    all 1e6 targets (from the GPU field, correct to 1e-5)."""
     mesh, gas, ch, trk, g = inputs.config_gem(seed=1, n=1_000_000)
     cen = mesh.tri.mean(axis=1)
     sigma = (1e-6 * (1.0 + 0.3 * np.sin(cen[:, 0] / 1e-4)) *
@@ -252,16 +276,17 @@ def test_full_size_gem_sampled(symmetric):
         got = _gpu_field(ctx, ch.pos_q, ch.pos_q, self_exclude=True, sigma=sigma)
     finally:
         obem.obem_destroy(ctx)
+    assert np.all(np.isfinite(got))
     rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(ch.n, 64, replace=False))
+    idx, n_near, n_mid = _stratified_sample(mesh, ch.pos_q[:, :3], rng)
+    assert n_near >= 300 and n_mid >= 300
     pts = ch.pos_q[idx, :3].astype(np.float64)
     E1, V1 = oracle.panel_field(mesh.tri, sigma.astype(np.float64), pts)
-    src = ch.pos_q.astype(np.float64)
-    E2 = np.zeros_like(E1)
-    V2 = np.zeros(len(idx))
-    for k, i in enumerate(idx):
-        s = np.delete(src, i, axis=0)
-        e, v = oracle.nbody_field(pts[k:k + 1], s)
-        E2[k], V2[k] = e[0], v[0]
-    assert np.all(np.isfinite(got))
-    assert guarded_rel_err(got[idx, :3], E1 + E2) <= FIELD_TOL
+    # the exact sum over all other charges (the oracle skips the pair at zero
+    # distance, i.e. the target itself)
+    E2, V2 = oracle.nbody_field(pts, ch.pos_q.astype(np.float64), False)
+    ref = E1 + E2
+    rms_all = float(np.sqrt((np.linalg.norm(got[:, :3], axis=1) ** 2).mean()))
+    den = np.maximum(np.linalg.norm(ref, axis=1), 1e-2 * rms_all)
+    err = np.linalg.norm(got[idx, :3] - ref, axis=1) / den
+    assert err.max() <= FIELD_TOL, (err.max(), int(np.argmax(err)))

@@ -1,8 +1,9 @@
 """obem_field_eval_noalloc: the field entry point for callers that cannot
-allocate device memory (e.g. while a CUDA graph is being captured, or under a
-fixed memory budget) and therefore have no obem_ctx.  It must give what
-obem_field_eval gives, call after call, although every call reuses the same
-fixed scratch array inside the library."""
+allocate device memory (a fixed device-memory budget owned by a host
+application, loops that cannot take an allocation's latency) and therefore
+have no obem_ctx.  It must give what obem_field_eval gives, call after call,
+although every call reuses the same fixed scratch array inside the library,
+and it must leave the device's free memory unchanged."""
 import numpy as np
 import pytest
 import torch
@@ -53,10 +54,14 @@ def test_noalloc_matches_field_eval_on_two_calls_in_a_row():
     t = torch.from_numpy(src).cuda()
     cells = torch.from_numpy(np.ascontiguousarray(mesh.tri, np.float64)).cuda()
     sg = torch.from_numpy(sigma).cuda()
-    for _ in range(2):
+    for k in range(2):
         out = torch.full((len(src), 4), float("nan"), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         obem.obem_field_eval_noalloc(t, out, sources=t, self_exclude=True, cell_xyz=cells, sigma=sg)
         torch.cuda.synchronize()
+        if k == 1:                     # the first call may load the kernels' code
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(got))
         assert guarded_rel_err(got[:, :3], ref[:, :3]) <= FIELD_TOL
