@@ -63,7 +63,8 @@ enum { OBEM_ELECTRON = 0, OBEM_CATION = 1, OBEM_ANION = 2 };
 enum {
     OBEM_LU_FP32 = 0,   /* FP32 on the CUDA cores */
     OBEM_LU_TF32 = 1,   /* TF32 tensor cores, FP32 accumulation */
-    OBEM_LU_BF16 = 2,   /* panels rounded to BF16, BF16 tensor cores, FP32 accumulation */
+    OBEM_LU_BF16 = 2,   /* recursive LU, every trailing update a hand-written tcgen05 GEMM:
+                           BF16 operands, FP32 accumulation into the FP32 factors */
     OBEM_LU_BF16X9 = 3  /* FP32-accurate BF16x9 emulation on the tensor cores */
 };
 
@@ -332,6 +333,19 @@ int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t s
  *          value).
  * Allocates scratch and synchronises `stream`. */
 int obem_alu_rates(obem_ctx *ctx, double *out, obem_stream stream);
+
+/* The trailing update of the BF16 LU factorisation on the tensor cores, as a
+ * plain call (a building block of obem_bem_assemble with OBEM_LU_BF16, for
+ * tests and measurement; the paper's dense solve, Sec. 2.2, Eq. (matrixBEM)):
+ *   C[M][N] -= A[M][K] B[K][N]
+ * C, A, B: device FP32 row-major arrays with leading dimensions ldc >= N,
+ * lda >= K, ldb >= N (elements).  The operands are rounded to BF16 (round to
+ * nearest even) and the products accumulated in FP32 by tcgen05.mma in
+ * 128 x 256 tiles.  Uses the context's BF16 scratch (grown here: allocates)
+ * and synchronises `stream`.  OBEM_ERR_ARG for bad sizes; OBEM_ERR_TIMEOUT if
+ * a bounded wait of the pipeline ran out (C is then undefined). */
+int obem_tc_gemm(obem_ctx *ctx, float *C, int64_t ldc, const float *A, int64_t lda, const float *B, int64_t ldb,
+                 int32_t M, int32_t N, int32_t K, obem_stream stream);
 
 /* Failure-detection self-test of the bounded device wait that the LU panel
  * factorisation uses between its CTAs (no passage in the paper): two blocks

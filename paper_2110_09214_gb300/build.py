@@ -27,6 +27,7 @@ UNITS = {
     "nn.cu": [],
     "batch.cu": [],
     "cellgroup.cu": [],
+    "lu_tc.cu": [],
 }
 
 

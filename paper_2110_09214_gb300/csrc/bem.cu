@@ -9,19 +9,18 @@
 //                     dielectric rows; FP64 closed form for near cells,
 //                     FP32 quadrature (7/3/1 points by distance) for far ones
 //   equilibrate       scale every row by 1 / max |A_ij| (solution unchanged)
-//   LU                blocked right-looking, partial pivoting:
+//   LU                partial pivoting; panels of LU_NB columns factored by
 //                       panel_kernel   cooperative: one row chunk per CTA held
 //                                      in shared memory, bounded grid barriers
-//                       laswp_kernel   row swaps outside the panel
-//                       trsm_kernel    U12 = L11^-1 A12
-//                       cuBLAS GEMM    A22 -= L21 U12 (FP32 / TF32 / BF16 /
-//                                      BF16x9 per the requested precision;
-//                                      for BF16 the two panels are first
-//                                      rounded to BF16 by panels_bf16_kernel,
-//                                      products accumulated in FP32)
+//                       laswp_kernel   the panel's row swaps on whole rows
+//                     BF16 (OBEM_LU_BF16): recursive (rec_lu / rec_trsm), every
+//                       trailing update and off-diagonal TRSM block a
+//                       hand-written tcgen05 GEMM (lu_tc.cu: BF16 operands,
+//                       FP32 accumulation into the FP32 factors)
+//                     FP32 / TF32 / BF16x9: right-looking blocked, trsm_kernel
+//                       for U12 = L11^-1 A12 and cuBLAS for A22 -= L21 U12
 //   solve             y = L^-1 P b, x = U^-1 y (blocked, FP32 factors) inside
 //                     iterative refinement with FP64 residuals r = b - A x
-#include <cuda_bf16.h>
 #include <math.h>
 #include <vector>
 
@@ -390,6 +389,30 @@ __global__ void trsm_kernel(float *A, int n, int k, int kb)
         for (int r = 0; r < kb; ++r) A[(size_t)(k + r) * n + c] = X[r][threadIdx.x];
 }
 
+// X = L^-1 X for the unit lower triangular block L = A[r0:r0+m, r0:r0+m]
+// (m <= LU_NB) and X = A[r0:r0+m, c0:c0+nc]; a CTA of TRSM_COLS threads owns
+// TRSM_COLS columns, held in shared memory
+__global__ void trsm_range_kernel(float *A, int n, int r0, int m, int c0, int nc)
+{
+    __shared__ float L[LU_NB][LU_NB + 1];
+    __shared__ float X[LU_NB][TRSM_COLS];
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        int r = t / m, c = t % m;
+        L[r][c] = A[(size_t)(r0 + r) * n + r0 + c];
+    }
+    const int cl = blockIdx.x * TRSM_COLS + threadIdx.x;
+    const bool act = cl < nc;
+    const int c = c0 + cl;
+    for (int r = 0; r < m; ++r) X[r][threadIdx.x] = act ? A[(size_t)(r0 + r) * n + c] : 0.f;
+    __syncthreads();
+    for (int q = 0; q < m; ++q) {
+        const float xq = X[q][threadIdx.x];
+        for (int r = q + 1; r < m; ++r) X[r][threadIdx.x] = fmaf(-L[r][q], xq, X[r][threadIdx.x]);
+    }
+    if (act)
+        for (int r = 0; r < m; ++r) A[(size_t)(r0 + r) * n + c] = X[r][threadIdx.x];
+}
+
 // ------------------------------------------------------------------ solve kernels
 // b_i = rowscale_i * (V_group or free density) + drhs_i  (drhs unscaled input)
 __global__ void rhs_kernel(const int *kind, const int *group, const double *gv, const float *sigma_free,
@@ -507,41 +530,12 @@ __global__ void to_float_kernel(const double *x, float *a, float *b, int n)
     if (b) b[i] = v;
 }
 
-// Rounds the operands of one trailing update to BF16 (round to nearest even):
-// U12 = rows k..k+kb-1, columns k+kb..n-1 into Ub[j * ldu + i] (row j, column
-// k+kb+i), and L21 = rows k+kb..n-1, columns k..k+kb-1 into Lb[q * kb + p]
-// (row k+kb+q, column k+p).  One thread per element; the reads run along the
-// rows of A.
-__global__ void panels_bf16_kernel(const float *__restrict__ A, int n, int k, int kb, int M, int ldu,
-                                   __nv_bfloat16 *__restrict__ Ub, __nv_bfloat16 *__restrict__ Lb)
-{
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t nu = (size_t)kb * M;
-    if (t < nu) {
-        const int j = (int)(t / M), i = (int)(t % M);
-        Ub[(size_t)j * ldu + i] = __float2bfloat16_rn(A[(size_t)(k + j) * n + k + kb + i]);
-    } else if (t < 2 * nu) {
-        const size_t u = t - nu;
-        const int q = (int)(u / kb), p = (int)(u % kb);
-        Lb[u] = __float2bfloat16_rn(A[(size_t)(k + kb + q) * n + k + p]);
-    }
-}
-
-// Elements of the BF16 panel scratch for n cells: Ub (LU_NB rows of ldu >= M,
-// ldu a multiple of 8 so that every column starts on 16 bytes) then Lb.
-static size_t bf16_panel_elems(int n)
-{
-    const size_t ldu = ((size_t)n + 7) / 8 * 8;
-    return (size_t)LU_NB * ldu + (size_t)n * LU_NB;
-}
-
 // ------------------------------------------------------------------ host drivers
-// A22 -= L21 U12 for the panel at column k (width kb).  A is row-major; cuBLAS
-// sees it column-major, i.e. transposed, so the call computes
-// A22^T -= U12^T L21^T with U12 as its first operand.  bf16 is the scratch of
-// bf16_panel_elems(n) elements (used only for OBEM_LU_BF16).
-static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int kb,
-                       __nv_bfloat16 *bf16, cudaStream_t s)
+// A22 -= L21 U12 for the panel at column k (width kb) in cuBLAS (FP32, TF32
+// or BF16x9 arithmetic).  A is row-major; cuBLAS sees it column-major, i.e.
+// transposed, so the call computes A22^T -= U12^T L21^T with U12 as its first
+// operand.
+static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int kb, cudaStream_t s)
 {
     const int M = n - k - kb;
     if (M <= 0) return OBEM_OK;
@@ -549,20 +543,6 @@ static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int k
     float *A22 = A + (size_t)(k + kb) * n + (k + kb);
     float *L21 = A + (size_t)(k + kb) * n + k;
     float *U12 = A + (size_t)k * n + (k + kb);
-    if (precision == OBEM_LU_BF16) {
-        // BF16 operands, FP32 products and accumulation, FP32 A22
-        const int ldu = (M + 7) / 8 * 8;
-        __nv_bfloat16 *Ub = bf16, *Lb = bf16 + (size_t)kb * ldu;
-        const size_t tot = 2 * (size_t)kb * M;
-        panels_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(A, n, k, kb, M, ldu, Ub, Lb);
-        OBEM_LAUNCH(c);
-        cublasStatus_t st = cublasGemmEx(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, M, M, kb, &alpha, Ub,
-                                         CUDA_R_16BF, ldu, Lb, CUDA_R_16BF, kb, &beta, A22, CUDA_R_32F, n,
-                                         CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-        if (st != CUBLAS_STATUS_SUCCESS)
-            return obem_fail(c, OBEM_ERR_CUDA, "cublasGemmEx (BF16) failed (status %d)", (int)st);
-        return OBEM_OK;
-    }
     cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
     if (precision == OBEM_LU_TF32) ct = CUBLAS_COMPUTE_32F_FAST_TF32;
     else if (precision == OBEM_LU_BF16X9) ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
@@ -572,6 +552,125 @@ static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int k
     if (st != CUBLAS_STATUS_SUCCESS)
         return obem_fail(c, OBEM_ERR_CUDA, "cublasGemmEx failed (status %d)", (int)st);
     return OBEM_OK;
+}
+
+// Pivoting panel factorisation of A[k:n, k:k+kb] (cooperative panel_kernel)
+// followed by its row swaps on every other column.
+struct PanelScratch {
+    float *gval, *gpiv, *gdiag;
+    int *grow;
+    int nsm;
+};
+
+static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaStream_t s)
+{
+    const int n = c->np;
+    const int rows = n - k;
+    int G = (rows + 31) / 32;
+    if (G > P.nsm) G = P.nsm;
+    // above ~nsm x 787 rows (about 120k cells) one chunk per SM no longer
+    // fits a CTA's shared memory: m = 2, 3, 4 co-resident CTAs per SM,
+    // each chunk within 1/m of the SM's 224 KB (the occupancy check
+    // below rejects a size that still does not fit)
+    const size_t row_b = sizeof(float) * (size_t)(kb + 1);
+    if ((size_t)((rows + G - 1) / G) * row_b > 200 * 1024)
+        for (int m = 2; m <= 4; ++m) {
+            G = m * P.nsm;
+            if ((size_t)((rows + G - 1) / G) * row_b <= (size_t)224 * 1024 / m) break;
+        }
+    if (G > 1000) G = 1000;
+    int R = (rows + G - 1) / G;
+    G = (rows + R - 1) / R;
+    size_t smem = sizeof(float) * (size_t)R * (kb + 1);
+    if (smem > 200 * 1024)
+        return obem_fail(c, OBEM_ERR_ARG, "LU panel of %d rows does not fit shared memory", rows);
+    OBEM_CUDA(c, cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    OBEM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, 256, smem));
+    if (per_sm * P.nsm < G)
+        return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
+    PanelArgs pa;
+    pa.A = c->d_LU; pa.n = n; pa.k = k; pa.kb = kb; pa.rows_per_cta = R; pa.piv = c->d_piv;
+    pa.flag = c->d_flag; pa.gval = P.gval; pa.grow = P.grow; pa.gpiv = P.gpiv; pa.gdiag = P.gdiag;
+    void *args[] = {&pa};
+    OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
+    laswp_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_LU, n, k, kb, c->d_piv);
+    OBEM_LAUNCH(c);
+    return OBEM_OK;
+}
+
+// Split of a recursive block of w columns: a multiple of LU_NB near w / 2.
+static int rec_split(int w)
+{
+    const int h = (w / (2 * LU_NB)) * LU_NB;
+    return h > LU_NB ? h : LU_NB;
+}
+
+// X = L^-1 X with L = LU[r0:r0+m, r0:r0+m] (unit lower) and X = LU[r0:r0+m,
+// c0:c0+nc], recursively: X1 = L11^-1 X1, X2 -= L21 X1 (tensor-core GEMM),
+// X2 = L22^-1 X2.
+static int rec_trsm(obem_ctx *c, int r0, int m, int c0, int nc, cudaStream_t s)
+{
+    const int n = c->np;
+    float *A = c->d_LU;
+    if (nc <= 0 || m <= 0) return OBEM_OK;
+    if (m <= LU_NB) {
+        trsm_range_kernel<<<(nc + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, 0, s>>>(A, n, r0, m, c0, nc);
+        OBEM_LAUNCH(c);
+        return OBEM_OK;
+    }
+    const int m1 = rec_split(m);
+    int rc = rec_trsm(c, r0, m1, c0, nc, s);
+    if (rc == OBEM_OK)
+        rc = obem_tc_gemm_sub(c, A + (size_t)(r0 + m1) * n + c0, n, A + (size_t)(r0 + m1) * n + r0, n,
+                              A + (size_t)r0 * n + c0, n, m - m1, nc, m1, c->d_flag + 4, s);
+    if (rc == OBEM_OK) rc = rec_trsm(c, r0 + m1, m - m1, c0, nc, s);
+    return rc;
+}
+
+// Largest BF16 operands (elements, rows x 8-padded K) of the GEMMs that
+// rec_lu / rec_trsm issue, so that the scratch is reserved once.
+static void rec_trsm_sizes(int m, int nc, size_t &a, size_t &b)
+{
+    if (nc <= 0 || m <= LU_NB) return;
+    const int m1 = rec_split(m);
+    const size_t k8 = ((size_t)m1 + 7) / 8 * 8;
+    a = a > (size_t)(m - m1) * k8 ? a : (size_t)(m - m1) * k8;
+    b = b > (size_t)nc * k8 ? b : (size_t)nc * k8;
+    rec_trsm_sizes(m1, nc, a, b);
+    rec_trsm_sizes(m - m1, nc, a, b);
+}
+
+static void rec_lu_sizes(int n, int k0, int w, size_t &a, size_t &b)
+{
+    if (w <= LU_NB) return;
+    const int w1 = rec_split(w);
+    const size_t k8 = ((size_t)w1 + 7) / 8 * 8;
+    rec_lu_sizes(n, k0, w1, a, b);
+    rec_trsm_sizes(w1, w - w1, a, b);
+    a = a > (size_t)(n - k0 - w1) * k8 ? a : (size_t)(n - k0 - w1) * k8;
+    b = b > (size_t)(w - w1) * k8 ? b : (size_t)(w - w1) * k8;
+    rec_lu_sizes(n, k0 + w1, w - w1, a, b);
+}
+
+// Recursive LU with partial pivoting of the columns [k0, k0 + w) of rows
+// [k0, n) (Toledo's recursion): factor the left half, U12 = L11^-1 A12,
+// A22 -= L21 U12 on the tensor cores (BF16 operands, FP32 accumulation into
+// the FP32 matrix), factor the right half.  Panels of LU_NB columns are the
+// leaves; their row swaps are applied to whole rows at once.
+static int rec_lu(obem_ctx *c, const PanelScratch &P, int k0, int w, cudaStream_t s)
+{
+    const int n = c->np;
+    float *A = c->d_LU;
+    if (w <= LU_NB) return factor_panel(c, P, k0, w, s);
+    const int w1 = rec_split(w);
+    int rc = rec_lu(c, P, k0, w1, s);
+    if (rc == OBEM_OK) rc = rec_trsm(c, k0, w1, k0 + w1, w - w1, s);
+    if (rc == OBEM_OK)
+        rc = obem_tc_gemm_sub(c, A + (size_t)(k0 + w1) * n + (k0 + w1), n, A + (size_t)(k0 + w1) * n + k0, n,
+                              A + (size_t)k0 * n + (k0 + w1), n, n - k0 - w1, w - w1, w1, c->d_flag + 4, s);
+    if (rc == OBEM_OK) rc = rec_lu(c, P, k0 + w1, w - w1, s);
+    return rc;
 }
 
 int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
@@ -626,65 +725,45 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     cudaEventRecord(e0, s);
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    float *gval = c->d_work32;
-    int *grow = (int *)(c->d_work32 + 1024);
-    float *gpiv = c->d_work32 + 2048;
-    float *gdiag = c->d_work32 + 2048 + LU_NB;
-    __nv_bfloat16 *bf16 = NULL;
-    if (precision == OBEM_LU_BF16)
-        OBEM_CUDA(c, cudaMalloc((void **)&bf16, sizeof(__nv_bfloat16) * bf16_panel_elems(n)));
-    FreeOnExit bf16_guard{bf16};
-    for (int k = 0; k < n; k += LU_NB) {
-        const int kb = n - k < LU_NB ? n - k : LU_NB;
-        const int rows = n - k;
-        int G = (rows + 31) / 32;
-        if (G > nsm) G = nsm;
-        // above ~nsm x 787 rows (about 120k cells) one chunk per SM no longer
-        // fits a CTA's shared memory: m = 2, 3, 4 co-resident CTAs per SM,
-        // each chunk within 1/m of the SM's 224 KB (the occupancy check
-        // below rejects a size that still does not fit)
-        const size_t row_b = sizeof(float) * (size_t)(kb + 1);
-        if ((size_t)((rows + G - 1) / G) * row_b > 200 * 1024)
-            for (int m = 2; m <= 4; ++m) {
-                G = m * nsm;
-                if ((size_t)((rows + G - 1) / G) * row_b <= (size_t)224 * 1024 / m) break;
-            }
-        if (G > 1000) G = 1000;
-        int R = (rows + G - 1) / G;
-        G = (rows + R - 1) / R;
-        size_t smem = sizeof(float) * (size_t)R * (kb + 1);
-        if (smem > 200 * 1024)
-            return obem_fail(c, OBEM_ERR_ARG, "LU panel of %d rows does not fit shared memory", rows);
-        OBEM_CUDA(c, cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        OBEM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, 256, smem));
-        if (per_sm * nsm < G)
-            return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
-        PanelArgs pa;
-        pa.A = c->d_LU; pa.n = n; pa.k = k; pa.kb = kb; pa.rows_per_cta = R; pa.piv = c->d_piv;
-        pa.flag = c->d_flag; pa.gval = gval; pa.grow = grow; pa.gpiv = gpiv; pa.gdiag = gdiag;
-        void *args[] = {&pa};
-        OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
-        laswp_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_LU, n, k, kb, c->d_piv);
-        OBEM_LAUNCH(c);
-        if (k + kb < n) {
-            trsm_kernel<<<(n - k - kb + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, 0, s>>>(c->d_LU, n, k, kb);
-            OBEM_LAUNCH(c);
-            int rc = gemm_update(c, precision, c->d_LU, n, k, kb, bf16, s);
+    PanelScratch PS;
+    PS.gval = c->d_work32;
+    PS.grow = (int *)(c->d_work32 + 1024);
+    PS.gpiv = c->d_work32 + 2048;
+    PS.gdiag = c->d_work32 + 2048 + LU_NB;
+    PS.nsm = nsm;
+    if (precision == OBEM_LU_BF16) {
+        // recursive factorisation, trailing updates on the tensor cores
+        size_t ea = 0, eb = 0;
+        rec_lu_sizes(n, 0, n, ea, eb);
+        int rc = obem_tc_reserve(c, ea, eb);
+        if (rc == OBEM_OK) rc = rec_lu(c, PS, 0, n, s);
+        if (rc != OBEM_OK) return rc;
+    } else {
+        // right-looking blocked factorisation, trailing updates in cuBLAS
+        for (int k = 0; k < n; k += LU_NB) {
+            const int kb = n - k < LU_NB ? n - k : LU_NB;
+            int rc = factor_panel(c, PS, k, kb, s);
             if (rc != OBEM_OK) return rc;
+            if (k + kb < n) {
+                trsm_kernel<<<(n - k - kb + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, 0, s>>>(c->d_LU, n, k, kb);
+                OBEM_LAUNCH(c);
+                rc = gemm_update(c, precision, c->d_LU, n, k, kb, s);
+                if (rc != OBEM_OK) return rc;
+            }
         }
     }
     cudaEventRecord(e1, s);
-    int flag = 0;
-    OBEM_CUDA(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int flag[8] = {0};
+    OBEM_CUDA(c, cudaMemcpyAsync(flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, s));
     OBEM_CUDA(c, cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->factor_ms = ms;
-    if (flag == OBEM_ERR_SINGULAR) return obem_fail(c, OBEM_ERR_SINGULAR, "LU: zero pivot");
-    if (flag == OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: panel grid barrier timed out");
+    if (flag[0] == OBEM_ERR_SINGULAR) return obem_fail(c, OBEM_ERR_SINGULAR, "LU: zero pivot");
+    if (flag[0] == OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: panel grid barrier timed out");
+    if (flag[4] != 0) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: a tensor-core GEMM wait timed out");
     c->factored = 1;
     return OBEM_OK;
 }

@@ -32,6 +32,7 @@ static void free_mesh(obem_ctx *c)
     free_dev(c->d_nrm); free_dev(c->d_c_lo); free_dev(c->d_v64); free_dev(c->d_kind); free_dev(c->d_group);
     free_dev(c->d_geo64);
     obem_cell_groups_free(c);
+    obem_tc_free(c);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
     free_dev(c->d_tri9); free_dev(c->d_hstart); free_dev(c->d_htri); free_dev(c->d_area); free_dev(c->d_deposit);

@@ -167,6 +167,9 @@ struct obem_ctx {
     const float *grp_fit_sigma;     // sigma the charges in d_grp_q were fitted to (d_sigma only)
     unsigned long long grp_fit_ver; // and its version
     cublasHandle_t cublas;
+    // BF16 operand scratch of the tensor-core LU updates (lu_tc.cu)
+    void *tc_a, *tc_b;
+    size_t tc_a_bytes, tc_b_bytes;
     // step scratch (capacity-sized)
     float4 *s_E;
     unsigned long long *s_prop, *s_ionkey;
@@ -392,6 +395,13 @@ int obem_launch_surface_sigma(obem_ctx *ctx, float *sigma_free, cudaStream_t s);
 
 // bem.cu
 int obem_assemble_and_factor(obem_ctx *ctx, int precision, cudaStream_t s);
+
+// lu_tc.cu: C[M x N] -= A[M x K] B[K x N] (FP32 row-major blocks) with BF16
+// operands on the tensor cores, FP32 accumulation; err: device status word
+int obem_tc_gemm_sub(obem_ctx *c, float *C, long long ldc, const float *A, long long lda, const float *B,
+                     long long ldb, int M, int N, int K, int *err, cudaStream_t s);
+int obem_tc_reserve(obem_ctx *c, size_t a_elems, size_t b_elems);
+void obem_tc_free(obem_ctx *c);
 int obem_solve_system(obem_ctx *ctx, const double *gv, const float *sigma_free, const float *drhs,
                       float *sigma_out, obem_solve_report *rep, cudaStream_t s);
 int obem_solve_adjoint(obem_ctx *ctx, const float *g, double *dL_dgv, float *dL_db, obem_solve_report *rep,

@@ -100,6 +100,9 @@ def load():
     lib.obem_profile.argtypes = [P, I]
     lib.obem_alu_rates.argtypes = [P, P, P]
     lib.obem_selftest_wait_timeout.argtypes = [P, P]
+    L64 = C.c_int64
+    lib.obem_tc_gemm.argtypes = [P, P, L64, P, L64, P, L64, I, I, I, P]
+    lib.obem_tc_gemm.restype = C.c_int
     lib.obem_fieldmap_build.argtypes = [P, P, P, P, P, P]
     lib.obem_nbody_nn_eval.argtypes = [P, P, I, I, C.c_double, P, P]
     lib.obem_surface_charge.argtypes = [P, P, P, I, P]
@@ -343,6 +346,19 @@ def obem_selftest_wait_timeout(ctx, stream=None):
     include/obem.h): raises ObemError unless the wait ran out and reported
     OBEM_ERR_TIMEOUT."""
     _check(ctx, load().obem_selftest_wait_timeout(ctx, _stream(stream)))
+
+
+def obem_tc_gemm(ctx, C_, A, B, stream=None):
+    """C_ -= A @ B on the tensor cores with BF16 operands and FP32
+    accumulation (the BF16 LU's trailing update); C_, A, B: 2-D FP32 CUDA
+    tensors with unit column stride (row-major, any row stride)."""
+    M, K = A.shape
+    N = B.shape[1]
+    assert C_.shape == (M, N) and B.shape[0] == K
+    for t in (C_, A, B):
+        assert t.dtype.is_floating_point and t.element_size() == 4 and (t.shape[1] <= 1 or t.stride(1) == 1)
+    _check(ctx, load().obem_tc_gemm(ctx, _ptr(C_), C_.stride(0), _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                                    M, N, K, _stream(stream)))
 
 
 def obem_alu_rates(ctx, stream=None):
