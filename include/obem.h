@@ -334,6 +334,21 @@ int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t s
  * Allocates scratch and synchronises `stream`. */
 int obem_alu_rates(obem_ctx *ctx, double *out, obem_stream stream);
 
+/* The factorisation and refinement of obem_bem_assemble / obem_bem_solve on a
+ * caller-given dense system, for tests of the LU on arbitrary matrices (the
+ * assembled BEM matrices, row-equilibrated and diagonally large, seldom need
+ * row swaps) -- the paper's dense solve of Eq. (matrixBEM), Sec. 2.2, without
+ * the assembly.  obem_dense_factor: A device [n][n] FP32 row-major (copied),
+ * equilibrated and factorised with partial pivoting in the arithmetic
+ * `precision` (OBEM_LU_*).  obem_dense_solve: x = A^-1 b, b and x device FP64
+ * [n], iterative refinement with FP64 residuals; rep may be NULL.  Only on a
+ * context without a mesh (OBEM_ERR_STATE otherwise, and for a solve before
+ * the factorisation); OBEM_ERR_SINGULAR for a zero pivot,
+ * OBEM_ERR_NOT_CONVERGED if the refinement stalls.  Both allocate and
+ * synchronise `stream`. */
+int obem_dense_factor(obem_ctx *ctx, const float *A, int32_t n, int32_t precision, obem_stream stream);
+int obem_dense_solve(obem_ctx *ctx, const double *b, double *x, obem_solve_report *rep, obem_stream stream);
+
 /* The trailing update of the BF16 LU factorisation on the tensor cores, as a
  * plain call (a building block of obem_bem_assemble with OBEM_LU_BF16, for
  * tests and measurement; the paper's dense solve, Sec. 2.2, Eq. (matrixBEM)):

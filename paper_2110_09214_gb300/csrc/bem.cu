@@ -8,7 +8,8 @@
 //                     j): Q_ij = k_C phi_j(r_i) for electrode rows, W_ij for
 //                     dielectric rows; FP64 closed form for near cells,
 //                     FP32 quadrature (7/3/1 points by distance) for far ones
-//   equilibrate       scale every row by 1 / max |A_ij| (solution unchanged)
+//   equilibrate       scale every row by the power of two nearest below
+//                     1 / max |A_ij| (exact; solution unchanged)
 //   LU                partial pivoting; panels of LU_NB columns factored by
 //                       panel_kernel   cooperative: one row chunk per CTA held
 //                                      in shared memory, bounded grid barriers
@@ -142,7 +143,7 @@ __global__ void assemble_kernel(PanelsDev P, const int *kind, const double *em, 
     A[(size_t)i * n + j] = (float)a;
 }
 
-// one block per row: scale by 1 / max |a_ij|, record the scale and |row|_1
+// one block per row: scale by 2^-floor(log2 max |a_ij|), record the scale and |row|_1
 __global__ void equilibrate_kernel(float *A, int n, double *rowscale, double *rownorm)
 {
     __shared__ float smax[32];
@@ -160,7 +161,9 @@ __global__ void equilibrate_kernel(float *A, int n, double *rowscale, double *ro
     }
     __syncthreads();
     const float mx = smax[0];
-    const float sc = mx > 0.f ? 1.0f / mx : 1.0f;
+    // a power of two: the scaled row is exact, so the equilibrated system is
+    // D A itself and the refined solution keeps FP64 accuracy for A
+    const float sc = mx > 0.f ? ldexpf(1.0f, -ilogbf(mx)) : 1.0f;
     double s = 0.0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         float v = row[j] * sc;
@@ -244,102 +247,133 @@ extern "C" int obem_selftest_wait_timeout(obem_ctx *c, obem_stream stream)
     return OBEM_OK;
 }
 
+#define PAN_MAXG 1024           // largest panel grid
+#define PAN_SCRATCH_FLOATS (4 * PAN_MAXG + 2 * LU_NB + 2 * PAN_MAXG * LU_NB)
+
 struct PanelArgs {
     float *A;
     int n, k, kb, rows_per_cta;
     int *piv;
     int *flag;          // [0] status, [1] barrier count, [2] barrier generation
-    float *gval;        // [gridDim] candidate |pivot|
-    int *grow;          // [gridDim] candidate row
-    float *gpiv;        // [LU_NB] pivot row
-    float *gdiag;       // [LU_NB] row displaced by the pivot
+    // exchange buffers, two sets used by alternate columns (a set is rewritten
+    // only after the next barrier, when every CTA has finished reading it)
+    float *cval;        // [2][PAN_MAXG] each CTA's candidate |pivot|
+    int *crow;          // [2][PAN_MAXG] its row
+    float *crows;       // [2][PAN_MAXG][LU_NB] the candidate row's panel values
+    float *gdiag;       // [2][LU_NB] the row receiving the pivot, before the swap
 };
 
+// (value, row) of the better pivot candidate: larger |a|, ties to the lower row
+__device__ __forceinline__ bool pan_better(float v2, int r2, float v, int r)
+{
+    return v2 > v || (v2 == v && r2 < r);
+}
+
+// best (value, row, slot) over the CTA, result in every thread
+__device__ __forceinline__ void pan_reduce(float &v, int &r, int &q, float *sv, int *sr, int *sq)
+{
+    for (int o = 16; o; o >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
+        const int q2 = __shfl_xor_sync(0xffffffffu, q, o);
+        if (pan_better(v2, r2, v, r)) { v = v2; r = r2; q = q2; }
+    }
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { sv[w] = v; sr[w] = r; sq[w] = q; }
+    __syncthreads();
+    v = sv[0]; r = sr[0]; q = sq[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+        if (pan_better(sv[k], sr[k], v, r)) { v = sv[k]; r = sr[k]; q = sq[k]; }
+}
+
 // Panel factorisation of A[k:n, k:k+kb] with partial pivoting.  CTA b owns
-// rows k + b*R .. k + (b+1)*R - 1 of the panel in shared memory.
+// rows k + b*R .. k + (b+1)*R - 1 of the panel in shared memory.  One grid
+// barrier per column: before it every CTA publishes its best candidate (value,
+// row and the row's panel values) and the owner of row k + j publishes that
+// row; after it every CTA picks the same pivot from the published candidates
+// and swaps and eliminates its own rows.
 __global__ void __launch_bounds__(256)
 panel_kernel(PanelArgs a)
 {
     extern __shared__ float sp[];            // [R][kb + 1] (padded against bank conflicts)
-    __shared__ float sv[256];
-    __shared__ int si[256];
+    __shared__ float sv[8];
+    __shared__ int sr[8], sq[8];
     __shared__ float urow[LU_NB];
     const int R = a.rows_per_cta, kb = a.kb, n = a.n, k = a.k;
     const int ld = kb + 1;
-    const int r0 = k + blockIdx.x * R;
+    const int b = blockIdx.x, G = gridDim.x;
+    const int r0 = k + b * R;
     const int rows = max(0, min(R, n - r0));
     unsigned *cnt = (unsigned *)&a.flag[1];
     volatile unsigned *gen = (volatile unsigned *)&a.flag[2];
-    for (int t = threadIdx.x; t < rows * kb; t += blockDim.x) {
-        int r = t / kb, c = t % kb;
-        sp[r * ld + c] = a.A[(size_t)(r0 + r) * n + k + c];
+    {
+        // 8 loads in flight per thread before the shared-memory stores
+        const int tot = rows * kb;
+        for (int t0 = 0; t0 < tot; t0 += 8 * 256) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + u * 256 + threadIdx.x;
+                v[u] = t < tot ? a.A[(size_t)(r0 + t / kb) * n + k + t % kb] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + u * 256 + threadIdx.x;
+                if (t < tot) sp[(t / kb) * ld + t % kb] = v[u];
+            }
+        }
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
+        const int par = j & 1;
         const int pr = k + j;                     // row receiving the pivot
-        // local candidate: max |a| over own rows >= pr, ties to the lowest row
+        float *cval = a.cval + par * PAN_MAXG;
+        int *crow = a.crow + par * PAN_MAXG;
+        float *crows = a.crows + (size_t)par * PAN_MAXG * LU_NB;
+        float *gdiag = a.gdiag + par * LU_NB;
+        // local candidate: max |a| over own rows >= pr
         float bv = -1.f;
-        int bi = 0x7fffffff;
+        int bi = 0x7fffffff, bq = b;
         for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-            int gr = r0 + r;
+            const int gr = r0 + r;
             if (gr < pr) continue;
-            float v = fabsf(sp[r * ld + j]);
-            if (v > bv || (v == bv && gr < bi)) { bv = v; bi = gr; }
+            const float v = fabsf(sp[r * ld + j]);
+            if (pan_better(v, gr, bv, bi)) { bv = v; bi = gr; }
         }
-        sv[threadIdx.x] = bv;
-        si[threadIdx.x] = bi;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                float v2 = sv[threadIdx.x + o];
-                int i2 = si[threadIdx.x + o];
-                if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
-                    sv[threadIdx.x] = v2;
-                    si[threadIdx.x] = i2;
-                }
-            }
-            __syncthreads();
+        pan_reduce(bv, bi, bq, sv, sr, sq);
+        if (threadIdx.x == 0) { cval[b] = bv; crow[b] = bi; }
+        if (bi != 0x7fffffff)
+            for (int c = threadIdx.x; c < kb; c += blockDim.x) crows[(size_t)b * LU_NB + c] = sp[(bi - r0) * ld + c];
+        if (pr >= r0 && pr < r0 + rows)
+            for (int c = threadIdx.x; c < kb; c += blockDim.x) gdiag[c] = sp[(pr - r0) * ld + c];
+        if (!grid_barrier(a.flag, cnt, gen, G)) return;
+        // global pivot: the same reduction in every CTA
+        float v = -1.f;
+        int p = 0x7fffffff, q = 0;
+        for (int t = threadIdx.x; t < G; t += blockDim.x) {
+            const float v2 = __ldcg(cval + t);
+            const int r2 = __ldcg(crow + t);
+            if (pan_better(v2, r2, v, p)) { v = v2; p = r2; q = t; }
         }
-        if (threadIdx.x == 0) { a.gval[blockIdx.x] = sv[0]; a.grow[blockIdx.x] = si[0]; }
-        if (!grid_barrier(a.flag, cnt, gen, gridDim.x)) return;
-        // global pivot (every CTA computes the same answer)
-        if (threadIdx.x == 0) {
-            float v = -1.f;
-            int p = 0x7fffffff;
-            for (int b = 0; b < (int)gridDim.x; ++b) {
-                float v2 = ((volatile float *)a.gval)[b];
-                int i2 = ((volatile int *)a.grow)[b];
-                if (v2 > v || (v2 == v && i2 < p)) { v = v2; p = i2; }
-            }
-            si[0] = p;
-            sv[0] = v;
-        }
-        __syncthreads();
-        const int p = si[0];
-        if (!(sv[0] > 0.f)) {
+        pan_reduce(v, p, q, sv, sr, sq);
+        if (!(v > 0.f)) {
             if (threadIdx.x == 0) atomicCAS(a.flag, 0, OBEM_ERR_SINGULAR);
             return;
         }
-        const bool own_p = p >= r0 && p < r0 + rows;
-        const bool own_d = pr >= r0 && pr < r0 + rows;
-        if (own_p)
-            for (int c = threadIdx.x; c < kb; c += blockDim.x) a.gpiv[c] = sp[(p - r0) * ld + c];
-        if (own_d)
-            for (int c = threadIdx.x; c < kb; c += blockDim.x) a.gdiag[c] = sp[(pr - r0) * ld + c];
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.piv[pr] = p;
-        if (!grid_barrier(a.flag, cnt, gen, gridDim.x)) return;
-        for (int c = threadIdx.x; c < kb; c += blockDim.x) urow[c] = ((volatile float *)a.gpiv)[c];
+        for (int c = threadIdx.x; c < kb; c += blockDim.x) urow[c] = __ldcg(crows + (size_t)q * LU_NB + c);
+        if (b == 0 && threadIdx.x == 0) a.piv[pr] = p;
         __syncthreads();
-        if (own_d)
+        if (pr >= r0 && pr < r0 + rows)
             for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[(pr - r0) * ld + c] = urow[c];
-        if (own_p && p != pr)
-            for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[(p - r0) * ld + c] = ((volatile float *)a.gdiag)[c];
+        if (p != pr && p >= r0 && p < r0 + rows)
+            for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[(p - r0) * ld + c] = __ldcg(gdiag + c);
         __syncthreads();
         const float inv = 1.0f / urow[j];
         for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-            int gr = r0 + r;
+            const int gr = r0 + r;
             if (gr <= pr) continue;
-            float l = sp[r * ld + j] * inv;
+            const float l = sp[r * ld + j] * inv;
             sp[r * ld + j] = l;
             for (int c = j + 1; c < kb; ++c) sp[r * ld + c] = fmaf(-l, urow[c], sp[r * ld + c]);
         }
@@ -389,28 +423,57 @@ __global__ void trsm_kernel(float *A, int n, int k, int kb)
         for (int r = 0; r < kb; ++r) A[(size_t)(k + r) * n + c] = X[r][threadIdx.x];
 }
 
+// T[r][c] = M[(r0 + r) * n + c0 + c] for r, c < kb (kb <= LU_NB), loaded by
+// blockDim.x (a multiple of 64) threads with 16 loads in flight per thread
+// before the shared-memory stores (the loads of a few-CTA kernel are
+// latency-bound otherwise)
+__device__ __forceinline__ void load_block(float (*T)[LU_NB + 1], const float *M, int n, int r0, int c0, int kb,
+                                           bool transpose)
+{
+    const int c = threadIdx.x & 63, rstep = blockDim.x >> 6;
+    for (int rb = threadIdx.x >> 6; rb < kb; rb += 16 * rstep) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int r = rb + i * rstep;
+            v[i] = (r < kb && c < kb) ? M[(size_t)(r0 + r) * n + c0 + c] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int r = rb + i * rstep;
+            if (r < kb && c < kb) {
+                if (transpose) T[c][r] = v[i];
+                else T[r][c] = v[i];
+            }
+        }
+    }
+}
+
 // X = L^-1 X for the unit lower triangular block L = A[r0:r0+m, r0:r0+m]
-// (m <= LU_NB) and X = A[r0:r0+m, c0:c0+nc]; a CTA of TRSM_COLS threads owns
-// TRSM_COLS columns, held in shared memory
-__global__ void trsm_range_kernel(float *A, int n, int r0, int m, int c0, int nc)
+// (m <= LU_NB) and X = A[r0:r0+m, c0:c0+nc]: one warp per column of X, lane
+// l holding rows l and l + 32, L in shared memory; column q's value is
+// broadcast with a shuffle and eliminated from the rows below it.
+#define TRSW_WARPS 8
+__global__ void __launch_bounds__(TRSW_WARPS * 32)
+trsm_range_kernel(float *A, int n, int r0, int m, int c0, int nc)
 {
     __shared__ float L[LU_NB][LU_NB + 1];
-    __shared__ float X[LU_NB][TRSM_COLS];
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-        int r = t / m, c = t % m;
-        L[r][c] = A[(size_t)(r0 + r) * n + r0 + c];
-    }
-    const int cl = blockIdx.x * TRSM_COLS + threadIdx.x;
-    const bool act = cl < nc;
-    const int c = c0 + cl;
-    for (int r = 0; r < m; ++r) X[r][threadIdx.x] = act ? A[(size_t)(r0 + r) * n + c] : 0.f;
+    load_block(L, A, n, r0, r0, m, false);
     __syncthreads();
-    for (int q = 0; q < m; ++q) {
-        const float xq = X[q][threadIdx.x];
-        for (int r = q + 1; r < m; ++r) X[r][threadIdx.x] = fmaf(-L[r][q], xq, X[r][threadIdx.x]);
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.x * TRSW_WARPS + (threadIdx.x >> 5);
+    if (col >= nc) return;
+    float *x = A + (size_t)r0 * n + c0 + col;
+    const bool h0 = lane < m, h1 = lane + 32 < m;
+    float x0 = h0 ? x[(size_t)lane * n] : 0.f;
+    float x1 = h1 ? x[(size_t)(lane + 32) * n] : 0.f;
+    for (int q = 0; q < m - 1; ++q) {
+        const float xq = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31);
+        if (h0 && lane > q) x0 = fmaf(-L[lane][q], xq, x0);
+        if (h1 && lane + 32 > q) x1 = fmaf(-L[lane + 32][q], xq, x1);
     }
-    if (act)
-        for (int r = 0; r < m; ++r) A[(size_t)(r0 + r) * n + c] = X[r][threadIdx.x];
+    if (h0) x[(size_t)lane * n] = x0;
+    if (h1) x[(size_t)(lane + 32) * n] = x1;
 }
 
 // ------------------------------------------------------------------ solve kernels
@@ -458,46 +521,45 @@ __global__ void norms_kernel(const double *r, const double *x, const double *b, 
     if (threadIdx.x == 0) { out[0] = s[0][0]; out[1] = s[1][0]; out[2] = s[2][0]; }
 }
 
-// y = P r (in order of the factorisation's swaps), rounded to FP32 after scaling by 1/sc
-__global__ void permute_kernel(const double *r, float *y, const int *piv, int n, const double *norms)
+// y = P r / sc in FP32 (sc = max |r|): the factorisation's row swaps as one
+// gather, y[i] = r[perm[i]] / sc
+__global__ void permute_kernel(const double *r, float *y, const int *perm, int n, const double *norms)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double sc = norms[0] > 0 ? norms[0] : 1.0;
-    for (int i = 0; i < n; ++i) y[i] = (float)(r[i] / sc);
-    for (int i = 0; i < n; ++i) {
-        int p = piv[i];
-        if (p != i) { float t = y[i]; y[i] = y[p]; y[p] = t; }
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double sc = norms[0] > 0 ? norms[0] : 1.0;
+    y[i] = (float)(r[perm[i]] / sc);
 }
 
-// Forward (lower=1, unit diagonal) or backward (lower=0) substitution on the
-// diagonal block [k, k+kb) of the factors: one CTA of LU_NB threads, the block
-// in shared memory, one column eliminated per barrier.
-__global__ void trsv_block_kernel(const float *LU, float *y, int n, int k, int kb, int lower)
+// Forward (lower = 1, unit diagonal) or backward (lower = 0) substitution on
+// the diagonal block [k, k+kb) of the factors: one warp, lane l holding rows
+// l and l + 32, the block in shared memory; column q's solved value is
+// broadcast with a shuffle.
+__global__ void __launch_bounds__(256) trsv_block_kernel(const float *LU, float *y, int n, int k, int kb, int lower)
 {
     __shared__ float T[LU_NB][LU_NB + 1];
-    __shared__ float yb[LU_NB];
-    for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
-        int r = t / kb, c = t % kb;
-        T[r][c] = LU[(size_t)(k + r) * n + k + c];
-    }
-    const int r = threadIdx.x;
-    if (r < kb) yb[r] = y[k + r];
+    load_block(T, LU, n, k, k, kb, false);
     __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int l = threadIdx.x;
+    const bool h0 = l < kb, h1 = l + 32 < kb;
+    float y0 = h0 ? y[k + l] : 0.f, y1 = h1 ? y[k + l + 32] : 0.f;
     if (lower) {
         for (int q = 0; q < kb; ++q) {
-            if (r > q && r < kb) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
-            __syncthreads();
+            const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
+            if (h0 && l > q) y0 = fmaf(-T[l][q], yq, y0);
+            if (h1 && l + 32 > q) y1 = fmaf(-T[l + 32][q], yq, y1);
         }
     } else {
         for (int q = kb - 1; q >= 0; --q) {
-            if (r == q) yb[q] = yb[q] / T[q][q];
-            __syncthreads();
-            if (r < q) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
-            __syncthreads();
+            const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31) / T[q][q];
+            if (l == (q & 31)) { if (q < 32) y0 = yq; else y1 = yq; }
+            if (h0 && l < q) y0 = fmaf(-T[l][q], yq, y0);
+            if (h1 && l + 32 < q) y1 = fmaf(-T[l + 32][q], yq, y1);
         }
     }
-    if (r < kb) y[k + r] = yb[r];
+    if (h0) y[k + l] = y0;
+    if (h1) y[k + l + 32] = y1;
 }
 
 // y[rows] -= LU[rows, k:k+kb] y[k:k+kb], one warp per row; rows = [r0, r1)
@@ -557,14 +619,14 @@ static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int k
 // Pivoting panel factorisation of A[k:n, k:k+kb] (cooperative panel_kernel)
 // followed by its row swaps on every other column.
 struct PanelScratch {
-    float *gval, *gpiv, *gdiag;
-    int *grow;
+    float *cval, *crows, *gdiag;
+    int *crow;
     int nsm;
 };
 
 static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaStream_t s)
 {
-    const int n = c->np;
+    const int n = c->nsys;
     const int rows = n - k;
     int G = (rows + 31) / 32;
     if (G > P.nsm) G = P.nsm;
@@ -578,7 +640,7 @@ static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaS
             G = m * P.nsm;
             if ((size_t)((rows + G - 1) / G) * row_b <= (size_t)224 * 1024 / m) break;
         }
-    if (G > 1000) G = 1000;
+    if (G > PAN_MAXG) G = PAN_MAXG;
     int R = (rows + G - 1) / G;
     G = (rows + R - 1) / R;
     size_t smem = sizeof(float) * (size_t)R * (kb + 1);
@@ -591,7 +653,7 @@ static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaS
         return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
     PanelArgs pa;
     pa.A = c->d_LU; pa.n = n; pa.k = k; pa.kb = kb; pa.rows_per_cta = R; pa.piv = c->d_piv;
-    pa.flag = c->d_flag; pa.gval = P.gval; pa.grow = P.grow; pa.gpiv = P.gpiv; pa.gdiag = P.gdiag;
+    pa.flag = c->d_flag; pa.cval = P.cval; pa.crow = P.crow; pa.crows = P.crows; pa.gdiag = P.gdiag;
     void *args[] = {&pa};
     OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
     laswp_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_LU, n, k, kb, c->d_piv);
@@ -611,11 +673,11 @@ static int rec_split(int w)
 // X2 = L22^-1 X2.
 static int rec_trsm(obem_ctx *c, int r0, int m, int c0, int nc, cudaStream_t s)
 {
-    const int n = c->np;
+    const int n = c->nsys;
     float *A = c->d_LU;
     if (nc <= 0 || m <= 0) return OBEM_OK;
     if (m <= LU_NB) {
-        trsm_range_kernel<<<(nc + TRSM_COLS - 1) / TRSM_COLS, TRSM_COLS, 0, s>>>(A, n, r0, m, c0, nc);
+        trsm_range_kernel<<<(nc + TRSW_WARPS - 1) / TRSW_WARPS, TRSW_WARPS * 32, 0, s>>>(A, n, r0, m, c0, nc);
         OBEM_LAUNCH(c);
         return OBEM_OK;
     }
@@ -660,7 +722,7 @@ static void rec_lu_sizes(int n, int k0, int w, size_t &a, size_t &b)
 // leaves; their row swaps are applied to whole rows at once.
 static int rec_lu(obem_ctx *c, const PanelScratch &P, int k0, int w, cudaStream_t s)
 {
-    const int n = c->np;
+    const int n = c->nsys;
     float *A = c->d_LU;
     if (w <= LU_NB) return factor_panel(c, P, k0, w, s);
     const int w1 = rec_split(w);
@@ -673,27 +735,44 @@ static int rec_lu(obem_ctx *c, const PanelScratch &P, int k0, int w, cudaStream_
     return rc;
 }
 
+// Buffers of an n x n system (matrix, factors, pivots, scaling, refinement
+// and panel scratch), reallocated when n changes.
+static int alloc_system(obem_ctx *c, int n)
+{
+    if (c->d_A && c->nsys_alloc == n) return OBEM_OK;
+    void *bufs[] = {c->d_A, c->d_LU, c->d_piv, c->d_rowscale, c->d_work64, c->d_work32, c->d_flag, c->d_panel,
+                    c->d_perm};
+    for (void *q : bufs)
+        if (q) cudaFree(q);
+    c->d_A = c->d_LU = NULL;
+    c->d_piv = c->d_flag = c->d_perm = NULL;
+    c->d_rowscale = c->d_work64 = NULL;
+    c->d_work32 = c->d_panel = NULL;
+    c->nsys_alloc = 0;
+    const size_t nn = (size_t)n * n;
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_A, sizeof(float) * nn));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_LU, sizeof(float) * nn));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_piv, sizeof(int) * n));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_rowscale, sizeof(double) * n));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_work64, sizeof(double) * (4 * (size_t)n + 8)));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_work32, sizeof(float) * (2 * (size_t)n + 4096)));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_flag, sizeof(int) * 8));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_panel, sizeof(float) * PAN_SCRATCH_FLOATS));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_perm, sizeof(int) * n));
+    c->nsys_alloc = n;
+    return OBEM_OK;
+}
+
+static int factor_system(obem_ctx *c, int precision, cudaStream_t s);
+
 int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
 {
-    const int n = c->np;
-    const size_t nn = (size_t)n * n;
     c->factored = 0;
-    if (!c->d_A) {
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_A, sizeof(float) * nn));
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_LU, sizeof(float) * nn));
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_piv, sizeof(int) * n));
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_rowscale, sizeof(double) * n));
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_work64, sizeof(double) * (4 * (size_t)n + 8)));
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_work32, sizeof(float) * (2 * (size_t)n + 4096)));
-        OBEM_CUDA(c, cudaMalloc((void **)&c->d_flag, sizeof(int) * 8));
-    }
-    if (!c->cublas) {
-        if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS)
-            return obem_fail(c, OBEM_ERR_CUDA, "cublasCreate failed");
-    }
-    cublasSetStream(c->cublas, s);
-    double *d_rownorm = c->d_work64;     // reused as scratch here
-    // --- assembly + equilibration
+    c->nsys = c->np;
+    const int n = c->nsys;
+    int rc0 = alloc_system(c, n);
+    if (rc0 != OBEM_OK) return rc0;
+    // --- assembly
     PanelsDev P;
     P.c_a = c->d_c_a; P.g0_h = c->d_g0_h; P.g1 = c->d_g1; P.g2 = c->d_g2; P.nrm = c->d_nrm;
     P.c_lo = c->d_c_lo;
@@ -709,6 +788,33 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     dim3 ag(n, (n + 127) / 128);
     assemble_kernel<<<ag, 128, 0, s>>>(P, c->d_kind, d_em, d_ep, c->d_A, n);
     OBEM_LAUNCH(c);
+    return factor_system(c, precision, s);
+}
+
+// A caller-given dense system in place of an assembled one (see obem.h).
+int obem_factor_dense(obem_ctx *c, const float *A, int n, int precision, cudaStream_t s)
+{
+    c->factored = 0;
+    c->nsys = n;
+    int rc = alloc_system(c, n);
+    if (rc != OBEM_OK) return rc;
+    OBEM_CUDA(c, cudaMemcpyAsync(c->d_A, A, sizeof(float) * (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    return factor_system(c, precision, s);
+}
+
+// Row equilibration of d_A (rows scaled by 1 / max |a_ij|, ||A||_inf kept for
+// the backward error), LU factorisation into d_LU in the requested
+// arithmetic, and the row permutation of the pivots.
+static int factor_system(obem_ctx *c, int precision, cudaStream_t s)
+{
+    const int n = c->nsys;
+    const size_t nn = (size_t)n * n;
+    if (!c->cublas) {
+        if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS)
+            return obem_fail(c, OBEM_ERR_CUDA, "cublasCreate failed");
+    }
+    cublasSetStream(c->cublas, s);
+    double *d_rownorm = c->d_work64;     // reused as scratch here
     equilibrate_kernel<<<n, 256, 0, s>>>(c->d_A, n, c->d_rowscale, d_rownorm);
     OBEM_LAUNCH(c);
     std::vector<double> rn(n);
@@ -726,10 +832,10 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     PanelScratch PS;
-    PS.gval = c->d_work32;
-    PS.grow = (int *)(c->d_work32 + 1024);
-    PS.gpiv = c->d_work32 + 2048;
-    PS.gdiag = c->d_work32 + 2048 + LU_NB;
+    PS.cval = c->d_panel;
+    PS.crow = (int *)(c->d_panel + 2 * PAN_MAXG);
+    PS.gdiag = c->d_panel + 4 * PAN_MAXG;
+    PS.crows = c->d_panel + 4 * PAN_MAXG + 2 * LU_NB;
     PS.nsm = nsm;
     if (precision == OBEM_LU_BF16) {
         // recursive factorisation, trailing updates on the tensor cores
@@ -764,49 +870,51 @@ int obem_assemble_and_factor(obem_ctx *c, int precision, cudaStream_t s)
     if (flag[0] == OBEM_ERR_SINGULAR) return obem_fail(c, OBEM_ERR_SINGULAR, "LU: zero pivot");
     if (flag[0] == OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: panel grid barrier timed out");
     if (flag[4] != 0) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: a tensor-core GEMM wait timed out");
+    // the row swaps as one permutation: (P b)[i] = b[perm[i]]
+    {
+        std::vector<int> piv(n), perm(n);
+        OBEM_CUDA(c, cudaMemcpy(piv.data(), c->d_piv, sizeof(int) * n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        for (int i = 0; i < n; ++i)
+            if (piv[i] != i) { const int t = perm[i]; perm[i] = perm[piv[i]]; perm[piv[i]] = t; }
+        OBEM_CUDA(c, cudaMemcpy(c->d_perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    }
     c->factored = 1;
     return OBEM_OK;
 }
 
 static int lu_solve(obem_ctx *c, float *y, cudaStream_t s)
 {
-    const int n = c->np;
+    const int n = c->nsys;
     for (int k = 0; k < n; k += LU_NB) {
         const int kb = n - k < LU_NB ? n - k : LU_NB;
-        trsv_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 1);
+        trsv_block_kernel<<<1, 256, 0, s>>>(c->d_LU, y, n, k, kb, 1);
         if (k + kb < n)
             trsv_update_kernel<<<(n - k - kb + 7) / 8, 256, 0, s>>>(c->d_LU, y, n, k, kb, k + kb, n);
     }
     for (int k = ((n - 1) / LU_NB) * LU_NB; k >= 0; k -= LU_NB) {
         const int kb = n - k < LU_NB ? n - k : LU_NB;
-        trsv_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 0);
+        trsv_block_kernel<<<1, 256, 0, s>>>(c->d_LU, y, n, k, kb, 0);
         if (k > 0) trsv_update_kernel<<<(k + 7) / 8, 256, 0, s>>>(c->d_LU, y, n, k, kb, 0, k);
     }
     OBEM_LAUNCH(c);
     return OBEM_OK;
 }
 
-int obem_solve_system(obem_ctx *c, const double *gv, const float *sigma_free, const float *drhs,
-                      float *sigma_out, obem_solve_report *rep, cudaStream_t s)
+// Iterative refinement of A x = b with the stored factors: b (device, FP64,
+// rows already equilibrated) in c->d_work64[0, n), x in [n, 2n); FP64
+// residuals r = b - A x from the FP32 equilibrated matrix, corrections from
+// the factors.  Returns the iterations, status and backward error.
+static int refine(obem_ctx *c, int &it, int &status, double &be, cudaStream_t s)
 {
-    const int n = c->np;
-    cublasSetStream(c->cublas, s);
+    const int n = c->nsys;
     double *b = c->d_work64, *x = b + n, *r = x + n, *nrm = r + n;
     float *y = c->d_work32;
-    double *d_gv = NULL;
-    int ng = c->n_groups > 0 ? c->n_groups : 1;
-    OBEM_CUDA(c, cudaMalloc((void **)&d_gv, sizeof(double) * ng));
-    if (c->n_groups > 0)
-        OBEM_CUDA(c, cudaMemcpyAsync(d_gv, gv, sizeof(double) * c->n_groups, cudaMemcpyHostToDevice, s));
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-    rhs_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_kind, c->d_group, d_gv, sigma_free, drhs, c->d_rowscale, b, n);
-    OBEM_LAUNCH(c);
     OBEM_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-    double be = 1.0, be_prev = 2.0;
-    int it = 0, status = OBEM_ERR_NOT_CONVERGED;
+    double be_prev = 2.0;
+    be = 1.0;
+    it = 0;
+    status = OBEM_ERR_NOT_CONVERGED;
     const int max_it = 30;
     for (; it <= max_it; ++it) {
         residual_kernel<<<(n + 7) / 8, 256, 0, s>>>(c->d_A, x, b, r, n);
@@ -821,13 +929,48 @@ int obem_solve_system(obem_ctx *c, const double *gv, const float *sigma_free, co
         if (be < 1e-12 || (be < 1e-9 && be > 0.5 * be_prev)) { status = OBEM_OK; break; }
         be_prev = be;
         if (it == max_it) break;
-        permute_kernel<<<1, 32, 0, s>>>(r, y, c->d_piv, n, nrm);
+        permute_kernel<<<(n + 255) / 256, 256, 0, s>>>(r, y, c->d_perm, n, nrm);
         OBEM_LAUNCH(c);
         int rc = lu_solve(c, y, s);
-        if (rc != OBEM_OK) { cudaFree(d_gv); return rc; }
+        if (rc != OBEM_OK) return rc;
         axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, nrm, n);
         OBEM_LAUNCH(c);
     }
+    return OBEM_OK;
+}
+
+static void fill_report(obem_ctx *c, obem_solve_report *rep, int it, int status, double be, float ms)
+{
+    if (!rep) return;
+    rep->iterations = it;
+    rep->status = status;
+    rep->backward_error = be;
+    rep->factor_ms = c->factor_ms;
+    rep->solve_ms = ms;
+}
+
+int obem_solve_system(obem_ctx *c, const double *gv, const float *sigma_free, const float *drhs,
+                      float *sigma_out, obem_solve_report *rep, cudaStream_t s)
+{
+    const int n = c->nsys;
+    cublasSetStream(c->cublas, s);
+    double *b = c->d_work64, *x = b + n;
+    double *d_gv = NULL;
+    int ng = c->n_groups > 0 ? c->n_groups : 1;
+    OBEM_CUDA(c, cudaMalloc((void **)&d_gv, sizeof(double) * ng));
+    struct FreeOnExit { void *p; ~FreeOnExit() { if (p) cudaFree(p); } } gv_guard{d_gv};
+    if (c->n_groups > 0)
+        OBEM_CUDA(c, cudaMemcpyAsync(d_gv, gv, sizeof(double) * c->n_groups, cudaMemcpyHostToDevice, s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    rhs_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_kind, c->d_group, d_gv, sigma_free, drhs, c->d_rowscale, b, n);
+    OBEM_LAUNCH(c);
+    int it = 0, status = OBEM_ERR_NOT_CONVERGED;
+    double be = 1.0;
+    int rc = refine(c, it, status, be, s);
+    if (rc != OBEM_OK) return rc;
     to_float_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, sigma_out, c->d_sigma, n);
     OBEM_LAUNCH(c);
     cudaEventRecord(e1, s);
@@ -836,16 +979,45 @@ int obem_solve_system(obem_ctx *c, const double *gv, const float *sigma_free, co
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_gv);
     c->sigma_valid = 1;
     c->sigma_ver++;
-    if (rep) {
-        rep->iterations = it;
-        rep->status = status;
-        rep->backward_error = be;
-        rep->factor_ms = c->factor_ms;
-        rep->solve_ms = ms;
-    }
+    fill_report(c, rep, it, status, be, ms);
+    if (status != OBEM_OK)
+        return obem_fail(c, OBEM_ERR_NOT_CONVERGED, "refinement stopped at backward error %.3e after %d iterations", be, it);
+    return OBEM_OK;
+}
+
+// b_i = rowscale_i * bin_i
+__global__ void scale_rhs_kernel(const double *bin, const double *rowscale, double *b, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = bin[i] * rowscale[i];
+}
+
+// Solve of the dense system given to obem_dense_factor for one right-hand
+// side (device FP64 b, x), with the same refinement as the BEM solve.
+int obem_solve_dense_rhs(obem_ctx *c, const double *bin, double *xout, obem_solve_report *rep, cudaStream_t s)
+{
+    const int n = c->nsys;
+    double *b = c->d_work64, *x = b + n;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    scale_rhs_kernel<<<(n + 255) / 256, 256, 0, s>>>(bin, c->d_rowscale, b, n);
+    OBEM_LAUNCH(c);
+    int it = 0, status = OBEM_ERR_NOT_CONVERGED;
+    double be = 1.0;
+    int rc = refine(c, it, status, be, s);
+    if (rc != OBEM_OK) return rc;
+    OBEM_CUDA(c, cudaMemcpyAsync(xout, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    cudaEventRecord(e1, s);
+    OBEM_CUDA(c, cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    fill_report(c, rep, it, status, be, ms);
     if (status != OBEM_OK)
         return obem_fail(c, OBEM_ERR_NOT_CONVERGED, "refinement stopped at backward error %.3e after %d iterations", be, it);
     return OBEM_OK;
@@ -929,15 +1101,14 @@ __global__ void scale_to_float_kernel(const double *r, float *y, int n, const do
     y[i] = (float)(r[i] / sc);
 }
 
-// undo the factorisation's row swaps (applied in forward order by the
-// factorisation, so undone in reverse order)
-__global__ void unpermute_kernel(float *y, const int *piv, int n)
+// x += P^T y sc: the transposed row permutation as a scatter, x[perm[i]] +=
+// y[i] sc (sc = max |r|)
+__global__ void axpy_unpermute_kernel(double *x, const float *y, const int *perm, const double *norms, int n)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int i = n - 1; i >= 0; --i) {
-        int p = piv[i];
-        if (p != i) { float t = y[i]; y[i] = y[p]; y[p] = t; }
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double sc = norms[0] > 0 ? norms[0] : 1.0;
+    x[perm[i]] += (double)y[i] * sc;
 }
 
 // Diagonal block [k, k+kb) of a transposed triangular solve: upper_unit = 0
@@ -947,10 +1118,7 @@ __global__ void trsv_t_block_kernel(const float *LU, float *y, int n, int k, int
 {
     __shared__ float T[LU_NB][LU_NB + 1];
     __shared__ float yb[LU_NB];
-    for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) {
-        const int c = t / kb, r = t % kb;                    // coalesced along r
-        T[r][c] = LU[(size_t)(k + c) * n + k + r];
-    }
+    load_block(T, LU, n, k, k, kb, true);                    // T = the block transposed
     const int r = threadIdx.x;
     if (r < kb) yb[r] = y[k + r];
     __syncthreads();
@@ -986,7 +1154,7 @@ __global__ void trsv_t_update_kernel(const float *LU, float *y, int n, int k, in
 
 static int lu_solve_t(obem_ctx *c, float *y, cudaStream_t s)
 {
-    const int n = c->np;
+    const int n = c->nsys;
     for (int k = 0; k < n; k += LU_NB) {
         const int kb = n - k < LU_NB ? n - k : LU_NB;
         trsv_t_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 0);
@@ -1005,7 +1173,7 @@ static int lu_solve_t(obem_ctx *c, float *y, cudaStream_t s)
 int obem_solve_adjoint(obem_ctx *c, const float *g, double *dL_dgv, float *dL_db, obem_solve_report *rep,
                        cudaStream_t s)
 {
-    const int n = c->np;
+    const int n = c->nsys;
     double *b = c->d_work64, *x = b + n, *r = x + n, *nrm = r + n;
     float *y = c->d_work32;
     double *part = NULL, *col = NULL, *mu = NULL;
@@ -1046,8 +1214,7 @@ int obem_solve_adjoint(obem_ctx *c, const float *g, double *dL_dgv, float *dL_db
         ADJ_CUDA(cudaGetLastError());
         rc = lu_solve_t(c, y, s);
         if (rc != OBEM_OK) goto done;
-        unpermute_kernel<<<1, 32, 0, s>>>(y, c->d_piv, n);
-        axpy_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, nrm, n);
+        axpy_unpermute_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, c->d_perm, nrm, n);
         ADJ_CUDA(cudaGetLastError());
     }
     // mu = D nu: the row scale of the equilibrated system

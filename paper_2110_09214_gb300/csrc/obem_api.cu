@@ -35,6 +35,9 @@ static void free_mesh(obem_ctx *c)
     obem_tc_free(c);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
+    free_dev(c->d_panel); free_dev(c->d_perm);
+    c->d_panel = NULL;
+    c->d_perm = NULL;
     free_dev(c->d_tri9); free_dev(c->d_hstart); free_dev(c->d_htri); free_dev(c->d_area); free_dev(c->d_deposit);
     c->d_tri9 = NULL;
     c->d_hstart = c->d_htri = NULL;
@@ -52,6 +55,7 @@ static void free_mesh(obem_ctx *c)
     c->d_sigma = NULL;
     c->np = 0;
     c->factored = 0;
+    c->nsys = c->nsys_alloc = 0;
     c->sigma_valid = 0;
 }
 
@@ -584,6 +588,25 @@ extern "C" int obem_bem_solve(obem_ctx *c, const double *gv, const float *sigma_
     if (c->n_groups > 0 && !gv) return obem_fail(c, OBEM_ERR_ARG, "solve: group_voltage is NULL");
     if (!sigma_out) return obem_fail(c, OBEM_ERR_ARG, "solve: sigma_out is NULL");
     return obem_solve_system(c, gv, sigma_free, drhs, sigma_out, rep, (cudaStream_t)stream);
+}
+
+extern "C" int obem_dense_factor(obem_ctx *c, const float *A, int32_t n, int32_t precision, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (c->np > 0) return obem_fail(c, OBEM_ERR_STATE, "dense factor: the context holds a mesh");
+    if (!A || n < 1) return obem_fail(c, OBEM_ERR_ARG, "dense factor: no matrix");
+    if (precision < OBEM_LU_FP32 || precision > OBEM_LU_BF16X9)
+        return obem_fail(c, OBEM_ERR_ARG, "dense factor: unknown precision %d", precision);
+    return obem_factor_dense(c, A, n, precision, (cudaStream_t)stream);
+}
+
+extern "C" int obem_dense_solve(obem_ctx *c, const double *b, double *x, obem_solve_report *rep,
+                                obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (c->np > 0 || !c->factored) return obem_fail(c, OBEM_ERR_STATE, "dense solve: call obem_dense_factor first");
+    if (!b || !x) return obem_fail(c, OBEM_ERR_ARG, "dense solve: null b or x");
+    return obem_solve_dense_rhs(c, b, x, rep, (cudaStream_t)stream);
 }
 
 extern "C" int obem_bem_solve_adjoint(obem_ctx *c, const float *dL_dsigma, double *dL_dgroup_voltage,

@@ -141,13 +141,16 @@ struct obem_ctx {
     int *d_kind, *d_group;
     float bbox_lo[3], bbox_hi[3];   // of the cell vertices (target binning grid)
     // BEM
-    float *d_A;          // equilibrated matrix, row-major [np][np]
+    int nsys, nsys_alloc; // size of the system held (np after obem_bem_assemble) and of its buffers
+    float *d_A;          // equilibrated matrix, row-major [nsys][nsys]
     float *d_LU;         // LU factors (row-major, unit lower L below the diagonal)
     int *d_piv;          // row swaps of the factorisation
     double *d_rowscale;  // 1 / max |A_ij| per row
     double *d_work64;    // 4 * np doubles
     float *d_work32;     // 2 * np floats
     int *d_flag;         // device status of the LU (singular / timeout)
+    float *d_panel;      // exchange buffers of the pivoting panel kernel
+    int *d_perm;         // row permutation of the factorisation: (P b)[i] = b[d_perm[i]]
     int factored;
     double factor_ms;
     double a_norm_inf;
@@ -395,6 +398,8 @@ int obem_launch_surface_sigma(obem_ctx *ctx, float *sigma_free, cudaStream_t s);
 
 // bem.cu
 int obem_assemble_and_factor(obem_ctx *ctx, int precision, cudaStream_t s);
+int obem_factor_dense(obem_ctx *c, const float *A, int n, int precision, cudaStream_t s);
+int obem_solve_dense_rhs(obem_ctx *c, const double *b, double *x, obem_solve_report *rep, cudaStream_t s);
 
 // lu_tc.cu: C[M x N] -= A[M x K] B[K x N] (FP32 row-major blocks) with BF16
 // operands on the tensor cores, FP32 accumulation; err: device status word

@@ -103,6 +103,10 @@ def load():
     L64 = C.c_int64
     lib.obem_tc_gemm.argtypes = [P, P, L64, P, L64, P, L64, I, I, I, P]
     lib.obem_tc_gemm.restype = C.c_int
+    lib.obem_dense_factor.argtypes = [P, P, I, I, P]
+    lib.obem_dense_factor.restype = C.c_int
+    lib.obem_dense_solve.argtypes = [P, P, P, C.POINTER(obem_solve_report), P]
+    lib.obem_dense_solve.restype = C.c_int
     lib.obem_fieldmap_build.argtypes = [P, P, P, P, P, P]
     lib.obem_nbody_nn_eval.argtypes = [P, P, I, I, C.c_double, P, P]
     lib.obem_surface_charge.argtypes = [P, P, P, I, P]
@@ -346,6 +350,23 @@ def obem_selftest_wait_timeout(ctx, stream=None):
     include/obem.h): raises ObemError unless the wait ran out and reported
     OBEM_ERR_TIMEOUT."""
     _check(ctx, load().obem_selftest_wait_timeout(ctx, _stream(stream)))
+
+
+def obem_dense_factor(ctx, A, precision=OBEM_LU_FP32, stream=None):
+    """Factorise a dense FP32 CUDA matrix [n, n] (row-major, contiguous) in
+    place of an assembled BEM system (context without a mesh)."""
+    n = A.shape[0]
+    assert A.shape == (n, n) and A.is_contiguous() and A.element_size() == 4
+    _check(ctx, load().obem_dense_factor(ctx, _ptr(A), n, int(precision), _stream(stream)))
+
+
+def obem_dense_solve(ctx, b, x, stream=None):
+    """x = A^-1 b (FP64 CUDA vectors) with the factors of obem_dense_factor
+    and FP64-residual refinement; returns the solve report."""
+    rep = obem_solve_report()
+    _check(ctx, load().obem_dense_solve(ctx, _ptr(b), _ptr(x), C.byref(rep), _stream(stream)))
+    return {"iterations": rep.iterations, "status": rep.status, "backward_error": rep.backward_error,
+            "factor_ms": rep.factor_ms, "solve_ms": rep.solve_ms}
 
 
 def obem_tc_gemm(ctx, C_, A, B, stream=None):
