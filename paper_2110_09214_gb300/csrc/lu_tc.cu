@@ -5,7 +5,8 @@
 //   C[M x N] -= A[M x K] B[K x N]      C, A, B: FP32 row-major sub-blocks
 //
 // The operands are rounded to BF16 (round to nearest even) into K-major
-// scratch (A as is, B transposed), then one CTA per 128 x 256 tile of C runs
+// scratch (A as is, B transposed), then one CTA per 128 x 256 tile of C (tiles
+// ordered in groups of 8 row tiles for L2 reuse) runs
 // a TMA -> shared memory -> tcgen05.mma pipeline:
 //   warp 0, one lane   TMA producer: 64-wide K slices of A (128 rows) and B
 //                      (256 rows) into a 4-stage ring, 128B-swizzled
@@ -28,6 +29,7 @@ constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;               // 16 KB
 constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK * 2;               // 32 KB
 constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr int TC_GROUP_M = 8;                                    // row tiles per rasterisation group
 constexpr size_t TC_SMEM = 1024 + (size_t)TC_STAGES * TC_STAGE_BYTES + 256;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
 // instruction descriptor of tcgen05.mma.kind::f16: D FP32 (bits 4-5 = 1),
@@ -141,7 +143,20 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     int *s_fail = (int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM;
+    // tile of this CTA: groups of TC_GROUP_M row tiles are walked down the
+    // rows first, so the CTAs resident at one time cover a compact block of C
+    // and share their A and B slices in L2
+    int m_tile, n_tile;
+    {
+        const int num_m = (M + TC_BM - 1) / TC_BM, num_n = (N + TC_BN - 1) / TC_BN;
+        const int pid = blockIdx.x;
+        const int per_group = TC_GROUP_M * num_n;
+        const int first_m = (pid / per_group) * TC_GROUP_M;
+        const int gm = min(num_m - first_m, TC_GROUP_M);
+        m_tile = first_m + (pid % per_group) % gm;
+        n_tile = (pid % per_group) / gm;
+    }
+    const int n0 = n_tile * TC_BN, m0 = m_tile * TC_BM;
     const int nk = (K + TC_BK - 1) / TC_BK;
 
     if (threadIdx.x == 0) {
@@ -218,14 +233,18 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
             for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
             __syncwarp();
+            // the 32 rows' values of this lane's column: all loads in
+            // flight before any store (one HBM latency per chunk, not 32)
             const int col = n0 + c + lane;
+            const int nrow = min(32, M - rbase);
+            float *cp = C + (size_t)rbase * ldc + col;
             if (col < N) {
-                for (int i = 0; i < 32; ++i) {
-                    const int row = rbase + i;
-                    if (row >= M) break;
-                    float *p = C + (size_t)row * ldc + col;
-                    *p -= stage[i * 33 + lane];
-                }
+                float v[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = i < nrow ? __ldcg(cp + (size_t)i * ldc) : 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (i < nrow) __stcg(cp + (size_t)i * ldc, v[i] - stage[i * 33 + lane]);
             }
             __syncwarp();
         }
@@ -362,9 +381,9 @@ int obem_tc_gemm_sub(obem_ctx *c, float *C, long long ldc, const float *A, long 
         OBEM_CUDA(c, cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         attr = true;
     }
-    dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
-    if (grid.y > 65535) return obem_fail(c, OBEM_ERR_ARG, "tensor-core GEMM: %d rows exceed the grid", M);
-    tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, C, ldc, M, N, K, err);
+    const long long tiles = (long long)((N + TC_BN - 1) / TC_BN) * ((M + TC_BM - 1) / TC_BM);
+    if (tiles > 0x7fffffffll) return obem_fail(c, OBEM_ERR_ARG, "tensor-core GEMM: %d x %d exceeds the grid", M, N);
+    tc_gemm_kernel<<<(unsigned)tiles, TC_THREADS, TC_SMEM, s>>>(ma, mb, C, ldc, M, N, K, err);
     OBEM_LAUNCH(c);
     return OBEM_OK;
 }
