@@ -87,7 +87,7 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--charges", type=int, default=1_000_000)
     p.add_argument("--cells", type=int, default=60000)
-    p.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x9"])
+    p.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16", "bf16x9"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -396,8 +396,10 @@ def run_ours(a, ws, rank, local):
     if ws == 1 and not a.no_batch:
         bres = batch_timing(dev, a.batch_chambers)
     bemp = None
+    lu_gemm = None
     if ws == 1 and not a.no_bem_precisions:
         bemp = bem_precision_timing(mesh, dev)
+        lu_gemm = lu_gemm_roofline(dev, mesh.n)
     aval = None
     if ws == 1 and not a.no_avalanche:
         aval = avalanche_timing(dev)
@@ -468,6 +470,7 @@ def run_ours(a, ws, rank, local):
         "fieldmap": fmap,
         "batched_sweep": bres,
         "bem_precisions": bemp,
+        "roofline_lu_gemm": lu_gemm,
         "nbody_nn": nnres,
         "avalanche_snapshots": aval,
         "double_gem": dgem,
@@ -638,6 +641,57 @@ def batch_timing(dev, n_chambers=256, steps=3, swarm_steps=12, single=True):
     return out
 
 
+def measured_peaks():
+    """Denominators of the rooflines: the machine's measured copy bandwidth and
+    BF16 GEMM rate (MEASURED_PEAKS.json beside this file), else the profiling
+    fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def lu_gemm_roofline(dev, n_cells):
+    """The tensor-core kernel of the BF16 LU alone: the top-level trailing
+    update of the recursive factorisation of the headline system (M = N = K =
+    n/2), C -= A B through obem_tc_gemm (BF16 operands rounded from FP32,
+    FP32 accumulation), best of 3 launches timed with CUDA events on the
+    launching stream; 2 M N K flops against the measured BF16 burst rate."""
+    import torch
+    from paper_2110_09214_gb300 import obem
+    h = n_cells // 2
+    ctx = obem.obem_create(capacity=16, dt=1e-12)
+    try:
+        A = torch.randn(h, h, device=dev)
+        B = torch.randn(h, h, device=dev)
+        C = torch.randn(h, h, device=dev)
+        obem.obem_tc_gemm(ctx, C, A, B)
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            obem.obem_tc_gemm(ctx, C, A, B)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        del A, B, C
+        torch.cuda.empty_cache()
+    finally:
+        obem.obem_destroy(ctx)
+    pk = measured_peaks()
+    tf = 2.0 * h ** 3 / (best * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "tc_gemm_kernel (tcgen05 BF16 GEMM, FP32 accumulation)",
+            "shape": [h, h, h], "ms": best, "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": tf / pk["bf16_tflops"], "peak_source": pk["source"] + ", BF16 burst",
+            "note": "time includes the BF16 rounding of both operands (two conversion kernels)"}
+
+
 def bem_precision_timing(mesh, dev):
     """The dense BEM solve of the headline mesh (Eq. (matrixBEM), 59,968
     cells) with the LU's trailing updates in each arithmetic -- FP32 SIMT,
@@ -670,8 +724,21 @@ def bem_precision_timing(mesh, dev):
         finally:
             obem.obem_destroy(ctx)
     out["cells"] = int(mesh.n)
-    out["note"] = ("trailing updates through cuBLAS in the named arithmetic; pivoting panels, triangular solves "
-                   "and the FP64 residuals of the refinement are this library's kernels")
+    n = float(mesh.n)
+    pk = measured_peaks()
+    bf = out["bf16"]
+    tf = 2.0 / 3.0 * n ** 3 / (bf["factor_ms"] * 1e-3) / 1e12
+    out["bf16_factor_roofline"] = {"bound": "tensor", "flops": 2.0 / 3.0 * n ** 3, "achieved": tf,
+                                   "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                                   "frac": tf / pk["bf16_tflops_sustained"],
+                                   "peak_source": pk["source"] + ", BF16 sustained"}
+    out["bf16_vs_fp32_total_speedup"] = ((out["fp32"]["factor_ms"] + out["fp32"]["solve_ms"]) /
+                                         (bf["factor_ms"] + bf["solve_ms"]))
+    out["note"] = ("bf16: recursive LU, every trailing update and off-diagonal TRSM block on this library's "
+                   "tcgen05 GEMM (BF16 operands, FP32 accumulation); fp32 / tf32 / bf16x9: right-looking blocked "
+                   "LU with the trailing updates through cuBLAS in the named arithmetic; pivoting panels, "
+                   "triangular solves and the FP64 residuals of the refinement are this library's kernels in "
+                   "every case")
     return out
 
 
