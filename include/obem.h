@@ -194,7 +194,23 @@ int obem_bem_solve(obem_ctx *ctx, const double *group_voltage, const float *sigm
                    const float *drhs, float *sigma_out, obem_solve_report *rep,
                    obem_stream stream);
 
-/* Adjoint of obem_bem_solve, for gradients through the solve.  Given
+/* Influence of free charges on the cells (Sec. 3.2.2, Eqs. (potpart),
+ * (fldpart)): the right-hand-side correction of Eqs. (BEMpotpart),
+ * (BEMfldpart) for obem_bem_solve's drhs, so that the cell charges respond
+ * to the space charge (the paper's dynamic option):
+ *   electrode cell i:   drhs_i = -Vbar_i,  Vbar_i = k_C sum_p q_p phi_i(y_p) / A_i
+ *   dielectric cell i:  drhs_i = -(eps+ - eps-) eps0 Ebar_i . n_i,
+ *                       Ebar_i = -k_C sum_p q_p F_i(y_p) / A_i
+ * i.e. the charges' potential and field averaged over cell i (phi_i, F_i:
+ * potential and field of a unit density on cell i; A_i its area; n_i its
+ * normal).  sources: device [ns][4] (x, y, z, q), 16-byte aligned; drhs:
+ * device [n_panels].  The cell integrals use the quadrature tiers of the
+ * field evaluation and the FP64 closed form within one cell size of a charge.
+ * OBEM_ERR_STATE without a mesh.  The first call allocates per-cell scratch;
+ * later calls allocate nothing and do not synchronise. */
+int obem_influence_rhs(obem_ctx *ctx, const float *sources, int32_t ns, float *drhs, obem_stream stream);
+
+/* Adjoint of obem_bem_solve, for gradients through the solve./* Adjoint of obem_bem_solve, for gradients through the solve.  Given
  * dL_dsigma = dL/dsigma (device [n_panels]), solves A^T mu = dL/dsigma with
  * the stored factors (transposed triangular solves, iterative refinement
  * with FP64 residuals on the equilibrated matrix); mu = dL/db is the

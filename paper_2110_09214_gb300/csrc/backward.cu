@@ -344,6 +344,114 @@ __global__ void __launch_bounds__(BS_WARPS * 32) bw_sigma_kernel(BwLaunch B)
     }
 }
 
+// ---------------------------------------------------------------- influence of the charges on the cells
+// S_j = k_C sum_p q_p (phi_j(y_p), F_j(y_p)) for every cell j (Eqs. (potpart),
+// (fldpart) before the division by the cell area): the transpose cell
+// operator of dL/dsigma with the forward's tiers, four sums per cell.  Block:
+// BS_PANELS cells, warp w takes cells w, w + 8, ...; lanes stride over a tile
+// of BS_TILE charges in shared memory; one charge's quadrature points are
+// summed in FP32, charges in FP64; the FP64 closed form below one cell size.
+__global__ void __launch_bounds__(BS_WARPS * 32) infl_kernel(const float4 *src, int ns, PanelsDev P, double *S)
+{
+    __shared__ float4 s_x[BS_TILE];
+    constexpr int PER_WARP = BS_PANELS / BS_WARPS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc[PER_WARP][4];
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
+    for (int tb = 0; tb < ns; tb += BS_TILE) {
+        __syncthreads();
+        for (int l = threadIdx.x; l < BS_TILE; l += BS_WARPS * 32) {
+            const int t = tb + l;
+            s_x[l] = t < ns ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        const int n = min(BS_TILE, ns - tb);
+#pragma unroll
+        for (int i = 0; i < PER_WARP; ++i) {
+            const int j = blockIdx.x * BS_PANELS + warp + BS_WARPS * i;
+            if (j >= P.np) continue;
+            const float4 ca = P.c_a[j], cl = P.c_lo[j], g0 = P.g0_h[j], g1 = P.g1[j], g2 = P.g2[j];
+            const float3 G0 = make_float3(g0.x, g0.y, g0.z), G1 = make_float3(g1.x, g1.y, g1.z),
+                         G2 = make_float3(g2.x, g2.y, g2.z);
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            for (int l = lane; l < n; l += 32) {
+                const float4 x = s_x[l];
+                const float ex = (x.x - ca.x) - cl.x, ey = (x.y - ca.y) - cl.y, ez = (x.z - ca.z) - cl.z;
+                const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                const int nq = fld_tier(d2, g0.w);
+                if (nq > 0) {
+                    float vp = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+                    for (int k = 0; k < nq; ++k) {
+                        float3 off;
+                        float wf;
+                        tier_point(nq, k, G0, G1, G2, off, wf);
+                        const float dx = ex - off.x, dy = ey - off.y, dz = ez - off.z;
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        if (!(r2 > 0.f)) continue;
+                        const float inv = rsq(r2);
+                        const float w = ca.w * wf * inv;
+                        const float w3 = w * inv * inv;
+                        vp += w;
+                        vx = fmaf(w3, dx, vx); vy = fmaf(w3, dy, vy); vz = fmaf(w3, dz, vz);
+                    }
+                    a0 += (double)x.w * vp; a1 += (double)x.w * vx; a2 += (double)x.w * vy; a3 += (double)x.w * vz;
+                } else {
+                    double phi, fx, fy, fz;
+                    tri_closed_form(P.v64 + 9 * (size_t)j, (double)x.x, (double)x.y, (double)x.z, phi, fx, fy, fz);
+                    const double qk = (double)x.w * OBEM_KC;
+                    a0 += qk * phi; a1 += qk * fx; a2 += qk * fy; a3 += qk * fz;
+                }
+            }
+            acc[i][0] += a0; acc[i][1] += a1; acc[i][2] += a2; acc[i][3] += a3;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i) {
+        const int j = blockIdx.x * BS_PANELS + warp + BS_WARPS * i;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double v = acc[i][c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && j < P.np) S[4 * (size_t)j + c] = v;
+        }
+    }
+}
+
+// Right-hand-side correction of Eqs. (BEMpotpart), (BEMfldpart) from S:
+// electrode cells -Vbar_j = -S_phi / A_j; dielectric cells
+// -(eps+ - eps-) eps0 Ebar_j . n_j with Ebar_j = -S_F / A_j.
+__global__ void infl_rhs_kernel(const double *S, const double *geo, const int *kind, const double *epsd, int np,
+                                float *drhs)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const double *g = geo + (size_t)OBEM_GEO64 * j;
+    const double area = 0.5 * g[3];
+    const double *s = S + 4 * (size_t)j;
+    double v;
+    if (kind[j] == OBEM_CELL_ELECTRODE) v = -s[0] / area;
+    else v = epsd[j] * OBEM_EPS0 * (s[1] * g[0] + s[2] * g[1] + s[3] * g[2]) / area;
+    drhs[j] = (float)v;
+}
+
+int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const PanelsDev &P, double *S, const double *geo,
+                          const int *kind, const double *epsd, float *drhs, cudaStream_t s)
+{
+    if (P.np <= 0) return OBEM_OK;
+    if (ns > 0) {
+        infl_kernel<<<(P.np + BS_PANELS - 1) / BS_PANELS, BS_WARPS * 32, 0, s>>>(src, ns, P, S);
+        OBEM_LAUNCH(ctx);
+    } else {
+        OBEM_CUDA(ctx, cudaMemsetAsync(S, 0, sizeof(double) * 4 * (size_t)P.np, s));
+    }
+    infl_rhs_kernel<<<(P.np + 255) / 256, 256, 0, s>>>(S, geo, kind, epsd, P.np, drhs);
+    OBEM_LAUNCH(ctx);
+    return OBEM_OK;
+}
+
 int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s)
 {
     BwLaunch B;

@@ -35,7 +35,8 @@ static void free_mesh(obem_ctx *c)
     obem_tc_free(c);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
-    free_dev(c->d_panel); free_dev(c->d_perm);
+    free_dev(c->d_panel); free_dev(c->d_perm); free_dev(c->d_infl); free_dev(c->d_epsd);
+    c->d_infl = c->d_epsd = NULL;
     c->d_panel = NULL;
     c->d_perm = NULL;
     free_dev(c->d_tri9); free_dev(c->d_hstart); free_dev(c->d_htri); free_dev(c->d_area); free_dev(c->d_deposit);
@@ -691,6 +692,29 @@ extern "C" int obem_field_eval_backward(obem_ctx *c, const float *targets, int32
     A.dL_dtargets = dL_dtargets;
     A.dL_dsources = dL_dsources;
     return obem_launch_backward(c, A, s);
+}
+
+extern "C" int obem_influence_rhs(obem_ctx *c, const float *sources, int32_t ns, float *drhs, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (c->np < 1) return obem_fail(c, OBEM_ERR_STATE, "influence: no mesh loaded");
+    if (ns < 0 || (ns > 0 && !sources) || !drhs) return obem_fail(c, OBEM_ERR_ARG, "influence: bad arguments");
+    if ((uintptr_t)sources & 15) return obem_fail(c, OBEM_ERR_ARG, "influence: sources must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->d_infl) {
+        // first call: the per-cell sums and eps+ - eps- of the dielectric cells
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_infl, sizeof(double) * 4 * (size_t)c->np));
+        OBEM_CUDA(c, cudaMalloc((void **)&c->d_epsd, sizeof(double) * (size_t)c->np));
+        double *h = (double *)malloc(sizeof(double) * (size_t)c->np);
+        if (!h) return obem_fail(c, OBEM_ERR_ARG, "influence: host allocation failed");
+        for (int i = 0; i < c->np; ++i)
+            h[i] = c->h_kind[i] == OBEM_CELL_DIELECTRIC ? c->h_ep[i] - c->h_em[i] : 0.0;
+        cudaError_t e = cudaMemcpy(c->d_epsd, h, sizeof(double) * (size_t)c->np, cudaMemcpyHostToDevice);
+        free(h);
+        OBEM_CUDA(c, e);
+    }
+    return obem_launch_influence(c, (const float4 *)sources, ns, panels_of(c), c->d_infl, c->d_geo64, c->d_kind,
+                                 c->d_epsd, drhs, s);
 }
 
 extern "C" int obem_surface_charge(obem_ctx *c, float *sigma_free, int64_t *counts, int32_t reset,

@@ -155,6 +155,8 @@ struct obem_ctx {
     double factor_ms;
     double a_norm_inf;
     float *d_sigma;      // current sigma [np]
+    double *d_infl;      // [np][4] charge sums of the influence right-hand side (obem_influence_rhs)
+    double *d_epsd;      // [np] eps_plus - eps_minus of the dielectric cells (0 on electrode cells)
     int sigma_valid;
     unsigned long long sigma_ver;   // bumped whenever d_sigma is rewritten
     // far-cell groups (OBEM_STEP_CELL_GROUPS; ngrp == 0: not built)
@@ -390,6 +392,8 @@ struct BwArgs {
     float *dL_dsigma, *dL_dtargets, *dL_dsources;
 };
 int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s);
+int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const PanelsDev &P, double *S, const double *geo,
+                          const int *kind, const double *epsd, float *drhs, cudaStream_t s);
 
 // step.cu
 int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,

@@ -103,6 +103,8 @@ def load():
     L64 = C.c_int64
     lib.obem_tc_gemm.argtypes = [P, P, L64, P, L64, P, L64, I, I, I, P]
     lib.obem_tc_gemm.restype = C.c_int
+    lib.obem_influence_rhs.argtypes = [P, P, I, P, P]
+    lib.obem_influence_rhs.restype = C.c_int
     lib.obem_dense_factor.argtypes = [P, P, I, I, P]
     lib.obem_dense_factor.restype = C.c_int
     lib.obem_dense_solve.argtypes = [P, P, P, C.POINTER(obem_solve_report), P]
@@ -350,6 +352,14 @@ def obem_selftest_wait_timeout(ctx, stream=None):
     include/obem.h): raises ObemError unless the wait ran out and reported
     OBEM_ERR_TIMEOUT."""
     _check(ctx, load().obem_selftest_wait_timeout(ctx, _stream(stream)))
+
+
+def obem_influence_rhs(ctx, sources, drhs, stream=None):
+    """drhs (CUDA float [n_panels]) = the right-hand-side correction of the
+    charges sources (CUDA float [ns, 4]: x, y, z, q) on the cells, for
+    obem_bem_solve(..., drhs=drhs) (Eqs. (BEMpotpart), (BEMfldpart))."""
+    ns = sources.shape[0] if sources is not None else 0
+    _check(ctx, load().obem_influence_rhs(ctx, _ptr(sources), ns, _ptr(drhs), _stream(stream)))
 
 
 def obem_dense_factor(ctx, A, precision=OBEM_LU_FP32, stream=None):
