@@ -93,6 +93,7 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-fieldmap", action="store_true")
     p.add_argument("--no-nn", action="store_true")
+    p.add_argument("--no-dynamic", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-bem-precisions", action="store_true")
     p.add_argument("--no-avalanche", action="store_true")
@@ -380,6 +381,12 @@ def run_ours(a, ws, rank, local):
         for key, v in snap.items():
             getattr(st, key).copy_(v)
         e2e = run_e2e(ctx, st, a.steps, step_index, dev)
+    dyn = None
+    if ws == 1 and not a.no_dynamic:
+        restore()
+        n_now = int(st.download()[0].pos_q.shape[0])
+        dyn = dynamic_resolve_timing(ctx, mesh, st.pos_q[:n_now], dev)
+        obem.obem_bem_solve(ctx, mesh.group_voltage, sigma)         # back to the static sigma
     nnres = None
     if ws == 1 and not a.no_nn:
         for key, v in snap.items():
@@ -472,6 +479,7 @@ def run_ours(a, ws, rank, local):
         "bem_precisions": bemp,
         "roofline_lu_gemm": lu_gemm,
         "nbody_nn": nnres,
+        "dynamic_resolve": dyn,
         "avalanche_snapshots": aval,
         "double_gem": dgem,
     }
@@ -690,6 +698,33 @@ def lu_gemm_roofline(dev, n_cells):
             "shape": [h, h, h], "ms": best, "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
             "frac": tf / pk["bf16_tflops"], "peak_source": pk["source"] + ", BF16 burst",
             "note": "time includes the BF16 rounding of both operands (two conversion kernels)"}
+
+
+def dynamic_resolve_timing(ctx, mesh, pos_q, dev, reps=2):
+    """The paper's dynamic option (Sec. 3.2.2) at the headline size: the
+    influence of every charge on every cell (obem_influence_rhs, Eqs.
+    (potpart), (fldpart); the same cell-charge pairs as the field
+    evaluation) and the re-solve of the cell charges with it (obem_bem_solve
+    with drhs, refinement on the stored factors).  Best of reps, CUDA events."""
+    import torch
+    from paper_2110_09214_gb300 import obem
+    drhs = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+    sig = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        obem.obem_influence_rhs(ctx, pos_q, drhs)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    rep = obem.obem_bem_solve(ctx, mesh.group_voltage, sig, drhs=drhs)
+    pairs = float(mesh.n) * float(pos_q.shape[0])
+    return {"influence_ms": best, "cell_charge_pairs": pairs, "pairs_per_s": pairs / (best * 1e-3),
+            "resolve_ms": rep["solve_ms"], "resolve_ir_iterations": rep["iterations"],
+            "resolve_backward_error": rep["backward_error"]}
 
 
 def bem_precision_timing(mesh, dev):

@@ -1319,6 +1319,19 @@ __host__ __device__ inline int sym_h(const SymGeom &g, int I)
     return I < g.n / 2 ? g.hmax : g.hmax - 1;
 }
 
+// Partial-sum slots of a launch, one whole set of charges or one pass over a
+// range of diagonals: units (I, kch) for kch in [kch_lo, kch_lo + kch_n), the
+// target-side sums of unit (I, kch) in slot I * kch_n + (kch - kch_lo), the
+// source-side sums of item (I, d) in slot I * jd + (d - kch_lo * SY_CH).
+// kch_n == 0: every unit of each chamber (batch of chambers), jd = hmax + 1.
+// first / last: the fold starts from the initial field / writes the result;
+// otherwise it reads / writes the per-charge FP64 accumulator acc.
+struct SymPass {
+    int kch_lo, kch_n, jd, first, last;
+    double *acc;           // [capacity][4]
+};
+#define SY_PASS_CH 32      // units (of SY_CH diagonals) per pass: 512 diagonals
+
 size_t obem_sym_jpart_floats(int capacity)
 {
     const SymGeom g = sym_geom(capacity);
@@ -1328,6 +1341,18 @@ size_t obem_sym_ipart_floats(int capacity)
 {
     const SymGeom g = sym_geom(capacity);
     return (size_t)g.n * g.nch * 8 * SY_T;
+}
+// the same for one pass of SY_PASS_CH units per row (the single-context path)
+size_t obem_sym_pass_jpart_floats(int capacity)
+{
+    const SymGeom g = sym_geom(capacity);
+    const int jd = g.hmax + 1 < SY_PASS_CH * SY_CH ? g.hmax + 1 : SY_PASS_CH * SY_CH;
+    return (size_t)g.n * jd * 4 * SY_T;
+}
+size_t obem_sym_pass_ipart_floats(int capacity)
+{
+    const SymGeom g = sym_geom(capacity);
+    return (size_t)g.n * (g.nch < SY_PASS_CH ? g.nch : SY_PASS_CH) * 8 * SY_T;
 }
 
 // dynamic shared memory of nbsym_kernel: target-side S and C [NC][SY_NI][SY_THREADS]
@@ -1492,7 +1517,7 @@ template <bool B> struct SyBool { static constexpr bool value = B; };
 
 template <bool WANT_V, bool BATCH>
 __global__ void __launch_bounds__(SY_THREADS, SY_MINB)
-nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const float *tileq, SymBatch SB)
+nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const float *tileq, SymBatch SB, SymPass PS)
 {
     constexpr int NC = WANT_V ? 4 : 3;
     extern __shared__ __align__(16) unsigned char sy_smem[];
@@ -1515,8 +1540,11 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
         nt0 = L.nt_dev ? *L.nt_dev : L.nt;
         if (nt0 <= 0) return;
         G0 = sym_geom(nt0);
-        units = G0.n * G0.nch;
+        units = G0.n * max(0, min(PS.kch_n, G0.nch - PS.kch_lo));
     }
+    // this launch's units of a row and its slot strides (one set of charges)
+    const int kn0 = BATCH ? 1 : max(1, min(PS.kch_n, G0.nch - PS.kch_lo)), klo0 = BATCH ? 0 : PS.kch_lo,
+              jd0 = BATCH ? 1 : PS.jd;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // k_C x 2^80 (kCs q is k_C q scaled exactly); L.eps2 comes in the scaled
     // positions' units (x 2^80) from the launch
@@ -1552,7 +1580,11 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
         const int off = BATCH ? s_off : 0;
         const int lim = BATCH ? off + s_nt : nt0;        // end of the live slots
         const SymGeom G = BATCH ? sym_geom(s_nt) : G0;
-        const int I = unit / G.nch, kch = unit % G.nch;
+        // this launch's units of row I: all (batch) or the pass's range
+        const int kn = BATCH ? G.nch : kn0;
+        const int klo = BATCH ? 0 : klo0;
+        const int jd = BATCH ? G.hmax + 1 : jd0;
+        const int I = unit / kn, kch = klo + unit % kn;
         const int d0 = kch * SY_CH, d1 = min(d0 + SY_CH, sym_h(G, I) + 1);
         const int base = off + I * SY_T;
         // targets of tile I: 8 per thread (k * 128 + tid), four packs
@@ -1754,11 +1786,11 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
             if (uni) rounds(SyBool<true>{});
             else rounds(SyBool<false>{});
             // the item's source-side sums (S + C) to its own slot
-            float *jp = jpart + (BATCH ? s_joff : 0) + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
+            float *jp = jpart + (BATCH ? s_joff : 0) + ((size_t)I * jd + (d - klo * SY_CH)) * 4 * SY_T;
             for (int l = tid; l < NC * SY_T; l += SY_THREADS) jp[l] = s_jS[l] + s_jC[l];
         }
         // the unit's target-side sums (S and C) to its own slot
-        float *ip = ipart + (BATCH ? s_ioff : 0) + ((size_t)I * G.nch + kch) * 8 * SY_T;
+        float *ip = ipart + (BATCH ? s_ioff : 0) + ((size_t)I * kn + (kch - klo)) * 8 * SY_T;
 #pragma unroll
         for (int k = 0; k < SY_NI; ++k)
 #pragma unroll
@@ -1774,7 +1806,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
 // slot of the sorted copy; perm[t] the charge it holds.
 template <bool WANT_V>
 __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float *ipart, int add, const int32_t *perm,
-                                  SymBatch SB)
+                                  SymBatch SB, SymPass PS)
 {
     constexpr int NC = WANT_V ? 4 : 3;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1795,15 +1827,23 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
     const SymGeom G = sym_geom(nt);
     const int T = lt / SY_T, w = lt % SY_T;
     const int o = perm ? perm[t] : t;                  // sorted slot t is charge o
+    // this pass's units and diagonals (all of them for a batch)
+    const int kn = PS.kch_n ? min(PS.kch_n, G.nch - PS.kch_lo) : G.nch;
+    const int klo = PS.kch_n ? PS.kch_lo : 0;
+    const int jd = PS.kch_n ? PS.jd : G.hmax + 1;
+    const int dlo = max(1, klo * SY_CH), dhi = min(G.hmax, klo * SY_CH + jd - 1);
     double e[4] = {0.0, 0.0, 0.0, 0.0};
-    if (add) {
+    if (!PS.first) {
+        const double *a = PS.acc + 4 * (size_t)t;
+        e[0] = a[0]; e[1] = a[1]; e[2] = a[2]; e[3] = a[3];
+    } else if (add) {
         const float4 q = L.E_out[o];
         e[0] = q.x; e[1] = q.y; e[2] = q.z; e[3] = q.w;
     } else {
         e[0] = L.e_ext.x; e[1] = L.e_ext.y; e[2] = L.e_ext.z;
     }
-    for (int k = 0; k < G.nch; ++k) {
-        const float *ip = ipart + ioff + ((size_t)T * G.nch + k) * 8 * SY_T;
+    for (int k = 0; k < kn; ++k) {
+        const float *ip = ipart + ioff + ((size_t)T * kn + k) * 8 * SY_T;
 #pragma unroll
         for (int c = 0; c < NC; ++c) e[c] += (double)ip[(2 * c) * SY_T + w] + (double)ip[(2 * c + 1) * SY_T + w];
     }
@@ -1814,14 +1854,14 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
     float js[NC], jc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) { js[c] = 0.f; jc[c] = 0.f; }
-    for (int d0 = 1; d0 <= G.hmax; d0 += FU) {
+    for (int d0 = dlo; d0 <= dhi; d0 += FU) {
         float v[FU][NC];
 #pragma unroll
         for (int u = 0; u < FU; ++u) {
             const int d = d0 + u;
             const int I = T - d >= 0 ? T - d : T - d + G.n;
-            const bool ok = d <= G.hmax && d <= sym_h(G, I);
-            const float *jp = jpart + joff + ((size_t)I * (G.hmax + 1) + d) * 4 * SY_T;
+            const bool ok = d <= dhi && d <= sym_h(G, I);
+            const float *jp = jpart + joff + ((size_t)I * jd + (ok ? d - klo * SY_CH : 0)) * 4 * SY_T;
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[u][c] = ok ? jp[c * SY_T + w] : 0.f;
         }
@@ -1832,7 +1872,12 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) e[c] += (double)js[c] + (double)jc[c];
-    L.E_out[o] = make_float4((float)e[0], (float)e[1], (float)e[2], WANT_V ? (float)e[3] : 0.f);
+    if (PS.last) {
+        L.E_out[o] = make_float4((float)e[0], (float)e[1], (float)e[2], WANT_V ? (float)e[3] : 0.f);
+    } else {
+        double *a = PS.acc + 4 * (size_t)t;
+        a[0] = e[0]; a[1] = e[1]; a[2] = e[2]; a[3] = e[3];
+    }
 }
 
 // occupancy-limited persistent grid of the symmetric kernel
@@ -1840,7 +1885,7 @@ int obem_sym_grid(int device)
 {
     int sms = 0, best = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    void (*ks[])(FieldLaunch, float *, float *, int *, const float *, SymBatch) = {
+    void (*ks[])(FieldLaunch, float *, float *, int *, const float *, SymBatch, SymPass) = {
         nbsym_kernel<true, false>, nbsym_kernel<false, false>, nbsym_kernel<false, true>};
     const size_t sm[] = {sym_smem(4), sym_smem(3), sym_smem(3)};
     for (int q = 0; q < 3; ++q) {
@@ -1961,22 +2006,39 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             Ls.targets = ctx->sym_sorted;
             Ls.sources = ctx->sym_sorted;
             Ls.eps2 = L.eps2 * SY_QS;                    // the sorted copy's positions are x 2^40
-            OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
+            // the diagonals in passes of SY_PASS_CH units per row, each folded
+            // in order into a per-charge FP64 accumulator: partial sums O(N)
+            // (a fixed pass size keeps the summation order, and so the bits,
+            // independent of the memory available)
+            const SymGeom Gc = sym_geom(capacity_targets);
+            const int npass = (Gc.nch + SY_PASS_CH - 1) / SY_PASS_CH;
             const dim3 sg(ctx->sym_grid);
-            if (L.want_v)
-                nbsym_kernel<true, false><<<sg, SY_THREADS, sym_smem(4), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
-                                                                      ctx->sym_tileq, SB);
-            else
-                nbsym_kernel<false, false><<<sg, SY_THREADS, sym_smem(3), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter,
-                                                                       ctx->sym_tileq, SB);
-            OBEM_LAUNCH(ctx);
             const int fb = (capacity_targets + 255) / 256;
-            if (L.want_v)
-                nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm, SB);
-            else
-                nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm, SB);
-            OBEM_LAUNCH(ctx);
-            if (L.events) ctx->launches += 6;
+            for (int pz = 0; pz < npass; ++pz) {
+                SymPass PS;
+                PS.kch_lo = pz * SY_PASS_CH;
+                PS.kch_n = SY_PASS_CH;
+                PS.jd = Gc.hmax + 1 < SY_PASS_CH * SY_CH ? Gc.hmax + 1 : SY_PASS_CH * SY_CH;   // as allocated
+                PS.first = pz == 0;
+                PS.last = pz == npass - 1;
+                PS.acc = ctx->sym_acc;
+                OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
+                if (L.want_v)
+                    nbsym_kernel<true, false><<<sg, SY_THREADS, sym_smem(4), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart,
+                                                                          ctx->sym_counter, ctx->sym_tileq, SB, PS);
+                else
+                    nbsym_kernel<false, false><<<sg, SY_THREADS, sym_smem(3), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart,
+                                                                           ctx->sym_counter, ctx->sym_tileq, SB, PS);
+                OBEM_LAUNCH(ctx);
+                if (L.want_v)
+                    nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0,
+                                                                ctx->sym_perm, SB, PS);
+                else
+                    nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0,
+                                                                 ctx->sym_perm, SB, PS);
+                OBEM_LAUNCH(ctx);
+            }
+            if (L.events) ctx->launches += 4 + 2 * npass;
         } else if (L.want_v) {
             if (add) nbody_kernel<true, true><<<grid, FT_THREADS, 0, s>>>(L);
             else nbody_kernel<true, false><<<grid, FT_THREADS, 0, s>>>(L);
@@ -2092,9 +2154,10 @@ int obem_launch_field_batch(obem_ctx *ctx, const FieldBatch &F, const float4 *po
         Ls.eps2 = L.eps2 * SY_QS;                        // the sorted copy's positions are x 2^40
         OBEM_CUDA(ctx, cudaMemsetAsync(F.counter, 0, sizeof(int), s));
         nbsym_kernel<false, true><<<F.sym_grid, SY_THREADS, sym_smem(3), s>>>(Ls, F.jpart, F.ipart, F.counter, F.tileq,
-                                                                       F.sym);
+                                                                       F.sym, SymPass{0, 0, 0, 1, 1, NULL});
         OBEM_LAUNCH(ctx);
-        nbsym_fold_kernel<false><<<F.slots / 256, 256, 0, s>>>(L, F.jpart, F.ipart, F.cells ? 1 : 0, F.perm, F.sym);
+        nbsym_fold_kernel<false><<<F.slots / 256, 256, 0, s>>>(L, F.jpart, F.ipart, F.cells ? 1 : 0, F.perm, F.sym,
+                                                               SymPass{0, 0, 0, 1, 1, NULL});
         OBEM_LAUNCH(ctx);
     }
     if (!F.cells && !F.charges) {

@@ -129,26 +129,31 @@ extern "C" int obem_create(obem_ctx **out, const obem_config *cfg)
     ALLOC(c->nn_cursor, sizeof(int32_t) * (size_t)OBEM_NN_GMAX * OBEM_NN_GMAX * OBEM_NN_GMAX);
     ALLOC(c->nn_agg, sizeof(float4) * 2 * (size_t)OBEM_NN_GMAX * OBEM_NN_GMAX * OBEM_NN_GMAX);
 #undef ALLOC
-    // partial sums of the symmetric all-pairs kernel: they grow as capacity^2,
-    // so they are kept only within a quarter of the free memory (and 64 GB);
-    // with them the charge-sorted copy of the charges and its permutation
+    // partial sums of the symmetric all-pairs kernel for one pass of
+    // diagonals (they grow as capacity x 512 tiles) and the per-charge
+    // accumulator of the passes, kept within a quarter of the free memory
+    // (and 64 GB); with them the charge-sorted copy of the charges and its
+    // permutation
     {
-        const size_t jb = sizeof(float) * obem_sym_jpart_floats(cap), ib = sizeof(float) * obem_sym_ipart_floats(cap);
+        const size_t jb = sizeof(float) * obem_sym_pass_jpart_floats(cap) + sizeof(double) * 4 * (size_t)cap,
+                     ib = sizeof(float) * obem_sym_pass_ipart_floats(cap);
         const size_t nb = (size_t)obem_sym_part_blocks(cap) + 1, ntile = (size_t)obem_sym_tiles(cap);
         size_t fr = 0, tot = 0;
         c->sym_grid = obem_sym_grid(c->device);
         if (c->sym_grid > 0 && cudaMemGetInfo(&fr, &tot) == cudaSuccess && jb + ib <= fr / 4 &&
             jb + ib <= ((size_t)64 << 30)) {
-            if (cudaMalloc((void **)&c->sym_jpart, jb) != cudaSuccess ||
+            if (cudaMalloc((void **)&c->sym_jpart, jb - sizeof(double) * 4 * (size_t)cap) != cudaSuccess ||
+                cudaMalloc((void **)&c->sym_acc, sizeof(double) * 4 * (size_t)cap) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_ipart, ib) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_counter, sizeof(int)) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_sorted, sizeof(float4) * cap) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_perm, sizeof(int32_t) * cap) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_bcnt, sizeof(int32_t) * nb) != cudaSuccess ||
                 cudaMalloc((void **)&c->sym_tileq, sizeof(float) * ntile) != cudaSuccess) {
-                free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
+                free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter); free_dev(c->sym_acc);
                 free_dev(c->sym_sorted); free_dev(c->sym_perm); free_dev(c->sym_bcnt); free_dev(c->sym_tileq);
                 c->sym_jpart = c->sym_ipart = NULL;
+                c->sym_acc = NULL;
                 c->sym_counter = c->sym_perm = c->sym_bcnt = NULL;
                 c->sym_sorted = NULL;
                 c->sym_tileq = NULL;
@@ -173,7 +178,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
     free_dev(c->s_tk); free_dev(c->s_tv); free_dev(c->s_rh);
-    free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter);
+    free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter); free_dev(c->sym_acc);
     free_dev(c->sym_sorted); free_dev(c->sym_perm); free_dev(c->sym_bcnt); free_dev(c->sym_tileq);
     free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted); free_dev(c->ph_bsum);
     free_dev(c->fm.nodes);

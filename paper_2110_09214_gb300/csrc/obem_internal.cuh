@@ -195,7 +195,8 @@ struct obem_ctx {
     // symmetric all-pairs kernel (targets == sources): per-item source-side and
     // per-unit target-side partial sums, work counter, persistent grid; NULL
     // when they did not fit the memory budget (the one-sided kernel runs)
-    float *sym_jpart, *sym_ipart;
+    float *sym_jpart, *sym_ipart;   // one pass of diagonals (field.cu SymPass)
+    double *sym_acc;                 // [capacity][4] FP64 sums carried between passes
     // partner search: hash-bucket counts / starts / cursors, bucket of each
     // charge, cations sorted by bucket
     int32_t *ph_count, *ph_start, *ph_cursor, *ph_bucket, *ph_sorted, *ph_bsum;
@@ -364,6 +365,8 @@ int obem_cell_layout(const double *tri, const int32_t *kind, int np, float4 *ca,
                      float4 *g2, float4 *nr, float4 *cl);
 void obem_cell_geo64(const double *tri, int np, double *geo);
 size_t obem_sym_jpart_floats(int capacity);
+size_t obem_sym_pass_jpart_floats(int capacity);
+size_t obem_sym_pass_ipart_floats(int capacity);
 size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);
 int obem_sym_part_blocks(int capacity);

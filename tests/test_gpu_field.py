@@ -290,3 +290,35 @@ def test_full_size_gem_sampled(symmetric):
     den = np.maximum(np.linalg.norm(ref, axis=1), 1e-2 * rms_all)
     err = np.linalg.norm(got[idx, :3] - ref, axis=1) / den
     assert err.max() <= FIELD_TOL, (err.max(), int(np.argmax(err)))
+
+
+def test_four_million_charges_on_the_symmetric_kernel():
+    """4e6 charges: the symmetric all-pairs kernel runs its diagonals in
+    passes with O(N) partial sums (33 GB at this size instead of ~125 GB),
+    so a context of this capacity keeps it.  Its field is checked at 256
+    sampled charges against the oracle and against the one-sided kernel (a
+    context of small capacity), whose summation order differs: the two agree
+    within the tolerance but not bit for bit."""
+    n = 4_000_000
+    rng = np.random.default_rng(12)
+    src = _charges(rng, n, box=2e-3, pairs=2000)
+    free0 = torch.cuda.mem_get_info()[0]
+    big = _ctx(cap=n)
+    try:
+        assert free0 - torch.cuda.mem_get_info()[0] > 8e9        # the symmetric kernel's buffers
+        got = _gpu_field(big, src, src, self_exclude=True)
+    finally:
+        obem.obem_destroy(big)
+    small = _ctx(cap=16)
+    try:
+        one = _gpu_field(small, src, src, self_exclude=True)
+    finally:
+        obem.obem_destroy(small)
+    assert np.all(np.isfinite(got))
+    idx = np.sort(rng.choice(n, 256, replace=False))
+    pts = src[idx, :3].astype(np.float64)
+    ref, _ = oracle.nbody_field(pts, src.astype(np.float64), False)
+    assert guarded_rel_err(got[idx, :3], ref) <= FIELD_TOL
+    assert guarded_rel_err(one[idx, :3], ref) <= FIELD_TOL
+    assert guarded_rel_err(got[:, :3], one[:, :3]) <= 2 * FIELD_TOL
+    assert not np.array_equal(got, one)
