@@ -334,7 +334,54 @@ int obem_nbody_nn_eval(obem_ctx *ctx, const float *pos_q, int32_t n, int32_t gri
 int obem_step(obem_ctx *ctx, const obem_state *st, const float *E_in, uint32_t step,
               obem_step_stats *stats, obem_stream stream);
 
-/* Measured ALU rates of the context's GPU, for the roofline of the FP32-bound
+/* Sharded tracking step: the charges partitioned among shards (one GPU each,
+ * as the paper's multi-GPU runs of Sec. 2.4 and Sec. 3.2.4 divide the work), a
+ * shard evaluating the field at its own charges only.  A shard is its own
+ * context and obem_state (sorted by id; initially a contiguous id range).  The
+ * exchanges between shards are the caller's (collectives among ranks, or
+ * plain copies for shards on one GPU); "gathered" means the live charges of
+ * every shard concatenated in shard order, this shard's at [self_off,
+ * self_off + n).  One step, for every shard, in this order:
+ *   1. obem_shard_field: E_out (device [capacity][4]) = cell field (current
+ *      sigma) + softened Coulomb field of the ns gathered charges `sources`
+ *      (device [ns][4], x y z q) at the shard's charges, the charge itself
+ *      excluded, + e_ext -- the field obem_step would compute (Eqs. (BEM3),
+ *      (nbody)), summed in another order (one-sided kernel).
+ *   2. obem_shard_propose: every electron of the shard proposes the nearest
+ *      cation of `gathered` (an obem_state over the gathered arrays, its n the
+ *      gathered count) within R_c, ties to the lower id; ionkey (device int64
+ *      [gathered capacity]) receives, per gathered cation, the smallest
+ *      (d^2 bits << 32 | electron id) of this shard's proposals, INT64_MAX
+ *      when none.  The caller reduces ionkey over all shards with MIN.
+ *   3. obem_shard_count: with the reduced keys, the recombination outcome of
+ *      the shard's charges (an electron recombines when its cation chose it, a
+ *      cation when it chose anyone) and the flight / collision pass;
+ *      stats->spawned_pairs, required_capacity and status are final; nothing
+ *      is written to st.  The caller gathers every shard's spawned_pairs and
+ *      status.
+ *   4. obem_shard_commit: if every shard's status is OBEM_OK (commit != 0):
+ *      spawned charges get ids from id_base = global next_id + 2 x (spawned
+ *      pairs of the shards before this one), the state is written, and the
+ *      moments computed; st->next_id is left at id_base + 2 x this shard's
+ *      spawned pairs (the caller sets every shard's next_id to the global
+ *      next_id + 2 x all spawned pairs).  commit == 0: nothing is written
+ *      and a shard without an error of its own reports OBEM_ERR_STATE.
+ * The union of the shards' states then equals obem_step's result on the
+ * union of the charges given the same field: ids, order within each shard,
+ * every decision (Philox draws are keyed by id).  The context's capacity must
+ * cover the gathered count (its spatial-hash scratch holds every cation).
+ * The static map and the approximate N-body field are not sharded
+ * (OBEM_ERR_ARG).  None of the calls allocates or synchronises. */
+int obem_shard_field(obem_ctx *ctx, const obem_state *st, const float *sources, int32_t ns, int32_t self_off,
+                     float *E_out, obem_stream stream);
+int obem_shard_propose(obem_ctx *ctx, const obem_state *st, const obem_state *gathered, uint32_t step,
+                       int64_t *ionkey, obem_stream stream);
+int obem_shard_count(obem_ctx *ctx, const obem_state *st, const float *E, uint32_t step, const int64_t *ionkey,
+                     int32_t self_off, obem_step_stats *stats, obem_stream stream);
+int obem_shard_commit(obem_ctx *ctx, const obem_state *st, const float *E, uint32_t step, uint32_t id_base,
+                      int32_t commit, obem_step_stats *stats, obem_stream stream);
+
+/* Measured ALU rates of the context's GPU, for the roofline of the FP32-bound/* Measured ALU rates of the context's GPU, for the roofline of the FP32-bound
  * field kernels (not part of the method).  Runs dependent-chain kernels on
  * every SM for a few milliseconds each and writes out[7] (host):
  *   out[0] FP32 TFLOP/s of packed f32x2 FMA chains (2 flops per lane-op),

@@ -1169,7 +1169,8 @@ nbody_kernel(FieldLaunch L)
             s_src[l] = sp;
         }
         __syncthreads();
-        const bool diag = L.self_exclude && sb < base + FT_BLOCK_TARGETS && base < sb + FT_SRC_TILE;
+        const bool diag = L.self_exclude && sb < base + L.self_off + FT_BLOCK_TARGETS &&
+                          base + L.self_off < sb + FT_SRC_TILE;
         float part[FT_TPT][4];
         if (!diag) {
             u64 AX[FT_NP], AY[FT_NP], AZ[FT_NP], AV[FT_NP];
@@ -1216,7 +1217,7 @@ nbody_kernel(FieldLaunch L)
                 upk(s_src[jj].zz, sz, dum); upk(s_src[jj].qq, sq, dum);
 #pragma unroll
                 for (int k = 0; k < FT_TPT; ++k) {
-                    if (j == base + k * FT_THREADS + tid) continue;
+                    if (j == base + L.self_off + k * FT_THREADS + tid) continue;
                     float txk, tyk, tzk, t2;
                     if (k & 1) { upk(TX[k >> 1], t2, txk); upk(TY[k >> 1], t2, tyk); upk(TZ[k >> 1], t2, tzk); }
                     else { upk(TX[k >> 1], txk, t2); upk(TY[k >> 1], tyk, t2); upk(TZ[k >> 1], tzk, t2); }
@@ -1983,8 +1984,8 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             if (L.events) ctx->launches++;
         }
         // self_exclude: the targets are the sources (same charges, nt == ns)
-        const bool nn = L.nn_grid > 0 && L.self_exclude;
-        const bool sym = !nn && ctx->sym_jpart && L.self_exclude && capacity_targets <= ctx->sym_cap;
+        const bool nn = L.nn_grid > 0 && L.self_exclude && !L.shard;
+        const bool sym = !nn && ctx->sym_jpart && L.self_exclude && !L.shard && capacity_targets <= ctx->sym_cap;
         if (nn) {
             int rc = obem_launch_nbody_nn(ctx, L.sources, L.nt_dev, capacity_targets, L.nn_grid, L.eps2, L.E_out,
                                           L.e_ext, add ? 1 : 0, s);

@@ -699,6 +699,90 @@ extern "C" int obem_field_eval_backward(obem_ctx *c, const float *targets, int32
     return obem_launch_backward(c, A, s);
 }
 
+// ---------------------------------------------------------------- sharded step
+static int shard_state_ok(obem_ctx *c, const obem_state *st, const char *who)
+{
+    if (!st) return obem_fail(c, OBEM_ERR_ARG, "%s: null state", who);
+    if (!st->pos_q || !st->vel || !st->id || !st->birth || !st->species || !st->n || !st->next_id)
+        return obem_fail(c, OBEM_ERR_ARG, "%s: null state array", who);
+    if (st->capacity < 1 || st->capacity > c->cap)
+        return obem_fail(c, OBEM_ERR_ARG, "%s: state capacity %d outside 1..%d", who, st->capacity, c->cap);
+    if (((uintptr_t)st->pos_q | (uintptr_t)st->vel) & 15)
+        return obem_fail(c, OBEM_ERR_ARG, "%s: pos_q / vel must be 16-byte aligned", who);
+    return OBEM_OK;
+}
+
+extern "C" int obem_shard_field(obem_ctx *c, const obem_state *st, const float *sources, int32_t ns, int32_t self_off,
+                                float *E_out, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    int rc = shard_state_ok(c, st, "shard field");
+    if (rc != OBEM_OK) return rc;
+    if (!E_out || ns < 0 || (ns > 0 && !sources) || self_off < 0 || self_off > ns)
+        return obem_fail(c, OBEM_ERR_ARG, "shard field: bad sources, offset or output");
+    if (((uintptr_t)sources | (uintptr_t)E_out) & 15)
+        return obem_fail(c, OBEM_ERR_ARG, "shard field: sources / E_out must be 16-byte aligned");
+    if (c->cfg.flags & (OBEM_STEP_FIELD_MAP | OBEM_STEP_NBODY_NN))
+        return obem_fail(c, OBEM_ERR_ARG, "shard field: the static map and the approximate N-body field are not sharded");
+    const int want_cells = (c->cfg.flags & OBEM_STEP_CELL_FIELD) && c->sigma_valid;
+    const int want_nbody = (c->cfg.flags & OBEM_STEP_SPACE_CHARGE) && ns > 0;
+    FieldLaunch L;
+    memset(&L, 0, sizeof L);
+    L.targets = (const float4 *)st->pos_q;
+    L.nt_dev = st->n;
+    L.nt = st->capacity;
+    L.sources = want_nbody ? (const float4 *)sources : NULL;
+    L.ns = ns;
+    L.self_exclude = 1;
+    L.self_off = self_off;
+    L.shard = 1;
+    L.eps2 = (float)(c->cfg.softening * c->cfg.softening);
+    L.sigma = want_cells ? c->d_sigma : NULL;
+    L.panels = panels_of(c);
+    L.perm = want_cells ? c->s_perm : NULL;
+    L.blocks = want_cells ? c->s_blocks : NULL;
+    L.nblocks = want_cells ? c->s_nblocks : NULL;
+    L.E_out = (float4 *)E_out;
+    L.e_ext = make_float3((float)c->cfg.e_ext[0], (float)c->cfg.e_ext[1], (float)c->cfg.e_ext[2]);
+    return obem_launch_field(c, L, st->capacity, (cudaStream_t)stream);
+}
+
+extern "C" int obem_shard_propose(obem_ctx *c, const obem_state *st, const obem_state *gathered, uint32_t step,
+                                  int64_t *ionkey, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (!c->gas_loaded) return obem_fail(c, OBEM_ERR_STATE, "shard propose: call obem_gas_load first");
+    int rc = shard_state_ok(c, st, "shard propose");
+    if (rc == OBEM_OK) rc = shard_state_ok(c, gathered, "shard propose (gathered)");
+    if (rc != OBEM_OK) return rc;
+    if (!ionkey) return obem_fail(c, OBEM_ERR_ARG, "shard propose: null ionkey");
+    return obem_launch_shard_propose(c, st, gathered, step, (unsigned long long *)ionkey, (cudaStream_t)stream);
+}
+
+extern "C" int obem_shard_count(obem_ctx *c, const obem_state *st, const float *E, uint32_t step,
+                                const int64_t *ionkey, int32_t self_off, obem_step_stats *stats, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (!c->gas_loaded) return obem_fail(c, OBEM_ERR_STATE, "shard count: call obem_gas_load first");
+    int rc = shard_state_ok(c, st, "shard count");
+    if (rc != OBEM_OK) return rc;
+    if (!E || !ionkey || !stats || self_off < 0 || ((uintptr_t)E & 15))
+        return obem_fail(c, OBEM_ERR_ARG, "shard count: bad field, keys, stats or offset");
+    return obem_launch_shard_count(c, st, (const float4 *)E, step, (const unsigned long long *)ionkey, self_off, stats,
+                                   (cudaStream_t)stream);
+}
+
+extern "C" int obem_shard_commit(obem_ctx *c, const obem_state *st, const float *E, uint32_t step, uint32_t id_base,
+                                 int32_t commit, obem_step_stats *stats, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    int rc = shard_state_ok(c, st, "shard commit");
+    if (rc != OBEM_OK) return rc;
+    if (!E || !stats || ((uintptr_t)E & 15)) return obem_fail(c, OBEM_ERR_ARG, "shard commit: bad field or stats");
+    return obem_launch_shard_commit(c, st, (const float4 *)E, step, id_base, commit ? 1 : 0, stats,
+                                    (cudaStream_t)stream);
+}
+
 extern "C" int obem_influence_rhs(obem_ctx *c, const float *sources, int32_t ns, float *drhs, obem_stream stream)
 {
     if (!c) return OBEM_ERR_ARG;

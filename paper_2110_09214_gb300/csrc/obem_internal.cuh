@@ -262,6 +262,9 @@ struct FieldLaunch {
     const int32_t *ns_dev;
     int ns;
     int self_exclude;
+    int shard;               // the targets are a slice of the sources (a shard's own charges inside the
+                             // gathered charges of every shard): one-sided kernel only
+    int self_off;            // with self_exclude: target t is source t + self_off (0: targets are the sources)
     float eps2;              // Plummer softening squared (m^2)
     const float *sigma;      // NULL: no cell part
     PanelsDev panels;
@@ -402,6 +405,12 @@ int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const Panels
 int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,
                      obem_step_stats *stats, cudaStream_t s);
 int obem_launch_surface_sigma(obem_ctx *ctx, float *sigma_free, cudaStream_t s);
+int obem_launch_shard_propose(obem_ctx *c, const obem_state *st, const obem_state *G, uint32_t step,
+                              unsigned long long *ionkey, cudaStream_t s);
+int obem_launch_shard_count(obem_ctx *c, const obem_state *st, const float4 *E, uint32_t step,
+                            const unsigned long long *ionkey, int self_off, obem_step_stats *stats, cudaStream_t s);
+int obem_launch_shard_commit(obem_ctx *c, const obem_state *st, const float4 *E, uint32_t step, uint32_t id_base,
+                             int commit, obem_step_stats *stats, cudaStream_t s);
 
 // bem.cu
 int obem_assemble_and_factor(obem_ctx *ctx, int precision, cudaStream_t s);

@@ -882,6 +882,200 @@ __global__ void __launch_bounds__(1024) moments_fold_kernel(const obem_state st,
     moments_fold(part, (n + ST_THREADS - 1) / ST_THREADS, stats);
 }
 
+// ====================================================================
+// Sharded step (the charges partitioned among shards, Sec. 2.4 / 3.2.4 run on
+// several GPUs): a shard holds its own charges, sorted by id, and sees the
+// charges of every shard through gathered copies (G, in shard order; its own
+// at [self_off, self_off + n)).  Recombination keys are exchanged as int64 with
+// INT64_MAX for "none", so that a signed MIN reduction across shards is the
+// unsigned minimum of the keys (valid keys are below 2^63: a finite non-negative
+// binary32 d^2 in the high word).
+#define SH_NONE 0x7FFFFFFFFFFFFFFFull
+
+// each local electron's nearest cation of the gathered set within R_c: ties to
+// the lower cation id (as in the unsharded step, whose array order is id
+// order); prop[i] = d^2 bits << 32 | gathered index of that cation
+__global__ void sh_query_kernel(const obem_state st, const obem_state G, GasDev g, double inv_h,
+                                const int32_t *start, const int32_t *sorted, u64 *prop)
+{
+    const int n = cur_n(st);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u64 best = ~0ull, best_idx = 0;
+    if (st.species[i] == OBEM_ELECTRON) {
+        const float4 pe = reinterpret_cast<const float4 *>(st.pos_q)[i];
+        long long cx, cy, cz;
+        ph_cell(pe, inv_h, cx, cy, cz);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const uint32_t h = ph_hash(cx + dx, cy + dy, cz + dz);
+                    for (int k = start[h]; k < start[h + 1]; ++k) {
+                        const int c = sorted[k];
+                        const float4 pc = reinterpret_cast<const float4 *>(G.pos_q)[c];
+                        const float ex = pe.x - pc.x, ey = pe.y - pc.y, ez = pe.z - pc.z;
+                        const float d2 = ex * ex + ey * ey + ez * ez;
+                        if (!(d2 <= g.rc2)) continue;
+                        const u64 key = ((u64)__float_as_uint(d2) << 32) | (u64)G.id[c];
+                        if (key < best) { best = key; best_idx = (u64)(uint32_t)c; }
+                    }
+                }
+    }
+    prop[i] = best == ~0ull ? ~0ull : ((best & 0xFFFFFFFF00000000ull) | best_idx);
+}
+
+// the local electrons' proposals into the gathered cations' keys: (d^2, id)
+__global__ void sh_propose_kernel(const obem_state st, const u64 *prop, unsigned long long *ionkey)
+{
+    const int n = cur_n(st);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u64 pr = prop[i];
+    if (pr == ~0ull || st.species[i] != OBEM_ELECTRON) return;
+    atomicMin(&ionkey[(uint32_t)(pr & 0xFFFFFFFFu)], (pr & 0xFFFFFFFF00000000ull) | (u64)st.id[i]);
+}
+
+__global__ void sh_fill_kernel(unsigned long long *k, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        k[i] = SH_NONE;
+}
+
+// the reduced keys as the local arrays of the unsharded step: a local
+// electron that won its cation gets prop = ionkey = (d^2, own index) at its
+// own index; a local cation that accepted a proposal a key != ~0
+__global__ void sh_localize_kernel(const obem_state st, const unsigned long long *ionkey, int self_off, u64 *prop,
+                                   u64 *ionloc)
+{
+    const int n = cur_n(st);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint8_t sp = st.species[i];
+    u64 p = ~0ull, k = ~0ull;
+    if (sp == OBEM_ELECTRON) {
+        const u64 pr = prop[i];
+        if (pr != ~0ull &&
+            ionkey[(uint32_t)(pr & 0xFFFFFFFFu)] == ((pr & 0xFFFFFFFF00000000ull) | (u64)st.id[i])) {
+            p = (pr & 0xFFFFFFFF00000000ull) | (u64)(uint32_t)i;
+            k = p;
+        }
+    } else if (sp == OBEM_CATION) {
+        if (ionkey[self_off + i] != SH_NONE) k = 0ull;
+    }
+    prop[i] = p;
+    ionloc[i] = k;
+}
+
+static GasDev step_gas(obem_ctx *c)
+{
+    GasDev g = c->gas;
+    g.hit_on = (c->cfg.flags & OBEM_STEP_SURFACE_HITS) && c->np > 0 && c->d_tri9;
+    if (g.hit_on) {
+        g.tri9 = c->d_tri9;
+        g.hstart = c->d_hstart;
+        g.htri = c->d_htri;
+        for (int k = 0; k < 3; ++k) { g.hlo[k] = c->h_hlo[k]; g.hdim[k] = c->h_hdim[k]; }
+        g.hinv = c->h_hinv;
+    }
+    return g;
+}
+
+int obem_launch_shard_propose(obem_ctx *c, const obem_state *stp, const obem_state *Gp, uint32_t step,
+                              unsigned long long *ionkey, cudaStream_t s)
+{
+    const obem_state st = *stp, G = *Gp;
+    const int nblk = (st.capacity + ST_THREADS - 1) / ST_THREADS;
+    const int gblk = (G.capacity + ST_THREADS - 1) / ST_THREADS;
+    const GasDev g = step_gas(c);
+    sh_fill_kernel<<<(G.capacity + 255) / 256 < 4096 ? (G.capacity + 255) / 256 : 4096, 256, 0, s>>>(ionkey,
+                                                                                                  G.capacity);
+    OBEM_LAUNCH(c);
+    if (!g.recomb_on || !(g.rc2 > 0.f)) {
+        OBEM_CUDA(c, cudaMemsetAsync(c->s_prop, 0xFF, sizeof(u64) * (size_t)st.capacity, s));
+        return OBEM_OK;
+    }
+    // spatial hash of the gathered cations, queried by the local electrons
+    const double inv_h = 1.0 / (sqrt((double)g.rc2) * (1.0 + 1e-5));
+    OBEM_CUDA(c, cudaMemsetAsync(c->ph_count, 0, sizeof(int32_t) * PH_BUCKETS, s));
+    ph_count_kernel<<<gblk, ST_THREADS, 0, s>>>(G, step, inv_h, c->ph_bucket, c->ph_count);
+    ph_blocksum_kernel<<<PH_NBLK, PH_BLK, 0, s>>>(c->ph_count, c->ph_bsum);
+    ph_scan_sums_kernel<<<1, PH_BLK, 0, s>>>(c->ph_bsum);
+    ph_scan_apply_kernel<<<PH_NBLK, PH_BLK, 0, s>>>(c->ph_count, c->ph_bsum, c->ph_start, c->ph_cursor);
+    ph_scatter_kernel<<<gblk, ST_THREADS, 0, s>>>(G, c->ph_bucket, c->ph_cursor, c->ph_sorted);
+    sh_query_kernel<<<nblk, ST_THREADS, 0, s>>>(st, G, g, inv_h, c->ph_start, c->ph_sorted, c->s_prop);
+    sh_propose_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_prop, ionkey);
+    OBEM_LAUNCH(c);
+    return OBEM_OK;
+}
+
+int obem_launch_shard_count(obem_ctx *c, const obem_state *stp, const float4 *E, uint32_t step,
+                            const unsigned long long *ionkey, int self_off, obem_step_stats *stats, cudaStream_t s)
+{
+    const obem_state st = *stp;
+    const int cap = st.capacity;
+    const int nblk = (cap + ST_THREADS - 1) / ST_THREADS;
+    const GasDev g = step_gas(c);
+    init_kernel<<<1, 32, 0, s>>>(stats, c->s_ctl, st);
+    OBEM_LAUNCH(c);
+    if (g.recomb_on) {
+        sh_localize_kernel<<<nblk, ST_THREADS, 0, s>>>(st, ionkey, self_off, c->s_prop, c->s_ionkey);
+        OBEM_LAUNCH(c);
+    }
+    count_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, E, step, c->s_prop, c->s_ionkey, c->s_keep,
+                                             c->s_nsp, c->s_blk, stats, c->s_ctl, c->s_hit);
+    OBEM_LAUNCH(c);
+    scan_kernel<<<1, 1024, 0, s>>>(st, c->s_blk, stats, c->s_ctl, cap < c->cap ? cap : c->cap);
+    OBEM_LAUNCH(c);
+    return OBEM_OK;
+}
+
+// the shard does not commit (another shard's step failed): nothing is
+// written, and a shard that had no error of its own reports OBEM_ERR_STATE
+__global__ void sh_abort_kernel(StepCtl *ctl, obem_step_stats *stats)
+{
+    if (threadIdx.x != 0) return;
+    ctl->abort = 1;
+    if (stats->status == OBEM_OK) stats->status = OBEM_ERR_STATE;
+    stats->n_after = stats->n_before;
+}
+
+__global__ void sh_set_id_kernel(uint32_t *next_id, uint32_t v)
+{
+    if (threadIdx.x == 0) *next_id = v;
+}
+
+int obem_launch_shard_commit(obem_ctx *c, const obem_state *stp, const float4 *E, uint32_t step, uint32_t id_base,
+                             int commit, obem_step_stats *stats, cudaStream_t s)
+{
+    const obem_state st = *stp;
+    const int cap = st.capacity;
+    const int nblk = (cap + ST_THREADS - 1) / ST_THREADS;
+    const GasDev g = step_gas(c);
+    if (!commit) {
+        sh_abort_kernel<<<1, 32, 0, s>>>(c->s_ctl, stats);
+        OBEM_LAUNCH(c);
+        return OBEM_OK;
+    }
+    sh_set_id_kernel<<<1, 32, 0, s>>>(st.next_id, id_base);
+    write_kernel<<<nblk, ST_THREADS, 0, s>>>(st, g, E, step, c->s_prop, c->s_ionkey, c->s_keep,
+                                             c->s_nsp, c->s_blk, c->s_ctl, c->o_pos, c->o_vel,
+                                             c->o_id, c->o_birth, c->o_sp);
+    OBEM_LAUNCH(c);
+    commit_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_ctl, c->o_pos, c->o_vel, c->o_id, c->o_birth,
+                                              c->o_sp);
+    OBEM_LAUNCH(c);
+    if (g.hit_on) {
+        deposit_kernel<<<nblk, ST_THREADS, 0, s>>>(st, c->s_ctl, c->s_hit, (unsigned long long *)c->d_deposit);
+        OBEM_LAUNCH(c);
+    }
+    finish_kernel<<<1, 32, 0, s>>>(st, c->s_ctl);
+    OBEM_LAUNCH(c);
+    moments_kernel<<<nblk, ST_THREADS, 0, s>>>(st, stats, c->s_mpart);
+    moments_fold_kernel<<<1, 1024, 0, s>>>(st, c->s_mpart, stats);
+    OBEM_LAUNCH(c);
+    return OBEM_OK;
+}
+
 int obem_launch_step(obem_ctx *c, const obem_state *stp, const float4 *E, uint32_t step,
                      obem_step_stats *stats, cudaStream_t s)
 {

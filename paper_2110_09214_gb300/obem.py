@@ -103,6 +103,12 @@ def load():
     L64 = C.c_int64
     lib.obem_tc_gemm.argtypes = [P, P, L64, P, L64, P, L64, I, I, I, P]
     lib.obem_tc_gemm.restype = C.c_int
+    lib.obem_shard_field.argtypes = [P, C.POINTER(obem_state), P, I, I, P, P]
+    lib.obem_shard_propose.argtypes = [P, C.POINTER(obem_state), C.POINTER(obem_state), U, P, P]
+    lib.obem_shard_count.argtypes = [P, C.POINTER(obem_state), P, U, P, I, P, P]
+    lib.obem_shard_commit.argtypes = [P, C.POINTER(obem_state), P, U, U, I, P, P]
+    for f in ("obem_shard_field", "obem_shard_propose", "obem_shard_count", "obem_shard_commit"):
+        getattr(lib, f).restype = C.c_int
     lib.obem_influence_rhs.argtypes = [P, P, I, P, P]
     lib.obem_influence_rhs.restype = C.c_int
     lib.obem_dense_factor.argtypes = [P, P, I, I, P]
@@ -352,6 +358,29 @@ def obem_selftest_wait_timeout(ctx, stream=None):
     include/obem.h): raises ObemError unless the wait ran out and reported
     OBEM_ERR_TIMEOUT."""
     _check(ctx, load().obem_selftest_wait_timeout(ctx, _stream(stream)))
+
+
+def obem_shard_field(ctx, state, sources, ns, self_off, E_out, stream=None):
+    """Field at a shard's charges from the gathered charges (see obem.h)."""
+    _check(ctx, load().obem_shard_field(ctx, C.byref(state.c_struct()), _ptr(sources), int(ns), int(self_off),
+                                        _ptr(E_out), _stream(stream)))
+
+
+def obem_shard_propose(ctx, state, gathered, step, ionkey, stream=None):
+    """Recombination proposals of a shard's electrons into ionkey (int64 CUDA
+    tensor over the gathered charges; reduce with MIN over the shards)."""
+    _check(ctx, load().obem_shard_propose(ctx, C.byref(state.c_struct()), C.byref(gathered.c_struct()), int(step),
+                                          _ptr(ionkey), _stream(stream)))
+
+
+def obem_shard_count(ctx, state, E, step, ionkey, self_off, stats, stream=None):
+    _check(ctx, load().obem_shard_count(ctx, C.byref(state.c_struct()), _ptr(E), int(step), _ptr(ionkey),
+                                        int(self_off), _ptr(stats), _stream(stream)))
+
+
+def obem_shard_commit(ctx, state, E, step, id_base, commit, stats, stream=None):
+    _check(ctx, load().obem_shard_commit(ctx, C.byref(state.c_struct()), _ptr(E), int(step), int(id_base),
+                                         int(bool(commit)), _ptr(stats), _stream(stream)))
 
 
 def obem_influence_rhs(ctx, sources, drhs, stream=None):
