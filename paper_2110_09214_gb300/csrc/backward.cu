@@ -182,45 +182,40 @@ __device__ __forceinline__ void tier_point(int n, int k, float3 g0, float3 g1, f
 }
 
 // ---------------------------------------------------------------- dL/dx
+// One warp per target: the lanes take every 32nd charge and every 32nd cell
+// (a target's sums are split across 32 lanes, so a few thousand probe points
+// fill the GPU), each lane summing in FP64 partial sums of at most BW_CHUNK
+// FP32 charge terms or one cell's quadrature points; the lanes' sums are
+// added by a fixed butterfly of shuffles (deterministic).
 __global__ void __launch_bounds__(BW_THREADS) bw_targets_kernel(BwLaunch B)
 {
-    __shared__ float4 s_pt[BW_TILE];
-    const int t = blockIdx.x * BW_THREADS + threadIdx.x;
-    const bool live = t < B.nt;
-    const float4 x = live ? B.targets[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 g = live ? B.g[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int t = (blockIdx.x * BW_THREADS + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= B.nt) return;                              // warp-uniform
+    const float4 x = B.targets[t];
+    const float4 g = B.g[t];
     double acc[3] = {0.0, 0.0, 0.0};
     const float kC = (float)OBEM_KC;
     // point charges
-    for (int sb = 0; sb < B.ns; sb += BW_TILE) {
-        __syncthreads();
-        for (int l = threadIdx.x; l < BW_TILE; l += BW_THREADS) {
-            const int p = sb + l;
-            float4 s = p < B.ns ? B.sources[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-            s.w *= kC;
-            s_pt[l] = s;
+    for (int p0 = 0; p0 < B.ns; p0 += 32 * BW_CHUNK) {
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        const int p1 = min(B.ns, p0 + 32 * BW_CHUNK);
+        for (int p = p0 + lane; p < p1; p += 32) {
+            if (B.self_exclude && p == t) continue;
+            const float4 s = B.sources[p];
+            tgt_term(x.x - s.x, x.y - s.y, x.z - s.z, kC * s.w, g, ax, ay, az);
         }
-        __syncthreads();
-        const int n = min(BW_TILE, B.ns - sb);
-        for (int l0 = 0; l0 < n; l0 += BW_CHUNK) {
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            for (int l = l0; l < min(n, l0 + BW_CHUNK); ++l) {
-                if (B.self_exclude && sb + l == t) continue;
-                const float4 s = s_pt[l];
-                tgt_term(x.x - s.x, x.y - s.y, x.z - s.z, s.w, g, ax, ay, az);
-            }
-            acc[0] += ax; acc[1] += ay; acc[2] += az;
-        }
+        acc[0] += ax; acc[1] += ay; acc[2] += az;
     }
     // cells
     if (B.sigma) {
         const PanelsDev &P = B.panels;
-        for (int j = 0; j < P.np; ++j) {
+        for (int j = lane; j < P.np; j += 32) {
             const float4 ca = P.c_a[j], cl = P.c_lo[j], g0 = P.g0_h[j];
             // exact target - centroid: x - c_hi is exact for nearby targets
             const float ex = (x.x - ca.x) - cl.x, ey = (x.y - ca.y) - cl.y, ez = (x.z - ca.z) - cl.z;
             const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-            const int n = live ? jac_tier(d2, g0.w) : -1;
+            const int n = jac_tier(d2, g0.w);
             const float sg = B.sigma[j];
             if (n > 0) {
                 const float4 g1 = P.g1[j], g2 = P.g2[j];
@@ -235,7 +230,7 @@ __global__ void __launch_bounds__(BW_THREADS) bw_targets_kernel(BwLaunch B)
                     tgt_term(ex - off.x, ey - off.y, ez - off.z, wq * wf, g, ax, ay, az);
                 }
                 acc[0] += ax; acc[1] += ay; acc[2] += az;
-            } else if (n == 0) {
+            } else {
                 double J[9], F[3];
                 tri_closed_jac(P.v64 + 9 * (size_t)j, (double)x.x, (double)x.y, (double)x.z, J, F);
                 const double s = OBEM_KC * (double)sg;
@@ -244,7 +239,10 @@ __global__ void __launch_bounds__(BW_THREADS) bw_targets_kernel(BwLaunch B)
             }
         }
     }
-    if (live) B.dtargets[t] = make_float4((float)acc[0], (float)acc[1], (float)acc[2], 0.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0) B.dtargets[t] = make_float4((float)acc[0], (float)acc[1], (float)acc[2], 0.f);
 }
 
 // ---------------------------------------------------------------- dL/dy, dL/dq
@@ -468,7 +466,7 @@ int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s)
     B.dtargets = (float4 *)A.dL_dtargets;
     B.dsources = (float4 *)A.dL_dsources;
     if (B.dtargets && B.nt > 0) {
-        bw_targets_kernel<<<(B.nt + BW_THREADS - 1) / BW_THREADS, BW_THREADS, 0, s>>>(B);
+        bw_targets_kernel<<<(unsigned)(((long long)B.nt * 32 + BW_THREADS - 1) / BW_THREADS), BW_THREADS, 0, s>>>(B);
         OBEM_LAUNCH(ctx);
     }
     if (B.dsources && B.ns > 0) {
