@@ -94,6 +94,7 @@ def _args():
     p.add_argument("--no-fieldmap", action="store_true")
     p.add_argument("--no-nn", action="store_true")
     p.add_argument("--no-dynamic", action="store_true")
+    p.add_argument("--no-gradient", action="store_true")
     p.add_argument("--sharded", action="store_true",
                    help="split the headline charges among the ranks (target sharding with NCCL exchanges, "
                         "strong scaling) instead of one independent workload per rank")
@@ -104,8 +105,9 @@ def _args():
     p.add_argument("--double-gem", action="store_true",
                    help="also time the double-GEM gradient and charging-up workload (~120k cells)")
     p.add_argument("--double-gem-only", action="store_true")
-    p.add_argument("--cell-groups", action="store_true",
-                   help="far cells in fitted groups (OBEM_STEP_CELL_GROUPS) on the headline workload")
+    p.add_argument("--no-cell-groups", dest="cell_groups", action="store_false",
+                   help="far cells by the per-cell tiers only (default: distant groups of 32 cells as "
+                        "fitted equivalent charges, OBEM_STEP_CELL_GROUPS)")
     p.add_argument("--batch-chambers", type=int, default=256)
     p.add_argument("--batch-only", action="store_true")
     p.add_argument("--batch-skip-single", action="store_true",
@@ -315,6 +317,7 @@ def run_ours(a, ws, rank, local):
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()          # a profiler started with --profile-from-start off sees these steps only
     ev0.record()
     for k in range(a.steps):
         flush.zero_()
@@ -322,6 +325,7 @@ def run_ours(a, ws, rank, local):
         obem.obem_step(ctx, st, step_index, stats[k])
     ev1.record()
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -390,6 +394,11 @@ def run_ours(a, ws, rank, local):
         n_now = int(st.download()[0].pos_q.shape[0])
         dyn = dynamic_resolve_timing(ctx, mesh, st.pos_q[:n_now], dev)
         obem.obem_bem_solve(ctx, mesh.group_voltage, sigma)         # back to the static sigma
+    grad = None
+    if ws == 1 and not a.no_gradient:
+        restore()
+        n_now = int(st.download()[0].pos_q.shape[0])
+        grad = gradient_timing(ctx, mesh, geo, st.pos_q[:n_now], sigma, dev)
     nnres = None
     if ws == 1 and not a.no_nn:
         for key, v in snap.items():
@@ -483,6 +492,7 @@ def run_ours(a, ws, rank, local):
         "roofline_lu_gemm": lu_gemm,
         "nbody_nn": nnres,
         "dynamic_resolve": dyn,
+        "gradient": grad,
         "avalanche_snapshots": aval,
         "double_gem": dgem,
     }
@@ -783,6 +793,49 @@ def lu_gemm_roofline(dev, n_cells):
             "shape": [h, h, h], "ms": best, "achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
             "frac": tf / pk["bf16_tflops"], "peak_source": pk["source"] + ", BF16 burst",
             "note": "time includes the BF16 rounding of both operands (two conversion kernels)"}
+
+
+def gradient_timing(ctx, mesh, geo, pos_q, sigma, dev, n_probe=4096, reps=2):
+    """The differentiable field on the headline workload: L = mean |E|^2 on a
+    4096-point probe line along the central hole's axis (drift plane to
+    anode); forward (cells + all charges at the probe) and backward (dL/dsigma
+    for every cell, dL/d(position, charge) for every charge) through
+    obem_field_eval / obem_field_eval_backward.  Best of reps, CUDA events."""
+    import torch
+    from paper_2110_09214_gb300 import obem
+    c = geo.hole_centres()[0]
+    z = np.linspace(geo.z_anode, geo.z_drift, n_probe + 2)[1:-1]
+    tgt = torch.zeros((n_probe, 4), dtype=torch.float32, device=dev)
+    tgt[:, 0], tgt[:, 1] = float(c[0]), float(c[1])
+    tgt[:, 2] = torch.from_numpy(z.astype(np.float32)).to(dev)
+    E = torch.empty((n_probe, 4), dtype=torch.float32, device=dev)
+    dsig = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+    dsrc = torch.empty((pos_q.shape[0], 4), dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    fwd = timed(lambda: obem.obem_field_eval(ctx, tgt, E, sources=pos_q, sigma=sigma))
+    g = torch.zeros_like(E)
+    g[:, :3] = 2.0 * E[:, :3] / n_probe
+    bwd = timed(lambda: obem.obem_field_eval_backward(ctx, tgt, g, sources=pos_q, sigma=sigma, dL_dsigma=dsig,
+                                                      dL_dsources=dsrc))
+    pairs = float(n_probe) * (mesh.n + pos_q.shape[0])
+    return {"probe_points": n_probe, "forward_ms": fwd, "backward_ms": bwd,
+            "backward_pairs_per_s": pairs / (bwd * 1e-3),
+            "note": "backward: dL/dsigma of every cell and dL/d(position, charge) of every charge (the probe "
+                    "points' own gradient not requested)",
+            "finite": bool(torch.isfinite(dsig).all() and torch.isfinite(dsrc).all())}
 
 
 def dynamic_resolve_timing(ctx, mesh, pos_q, dev, reps=2):
