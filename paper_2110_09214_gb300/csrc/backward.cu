@@ -345,107 +345,526 @@ __global__ void __launch_bounds__(BS_WARPS * 32) bw_sigma_kernel(BwLaunch B)
 // ---------------------------------------------------------------- influence of the charges on the cells
 // S_j = k_C sum_p q_p (phi_j(y_p), F_j(y_p)) for every cell j (Eqs. (potpart),
 // (fldpart) before the division by the cell area): the transpose cell
-// operator of dL/dsigma with the forward's tiers, four sums per cell.  Block:
-// BS_PANELS cells, warp w takes cells w, w + 8, ...; lanes stride over a tile
-// of BS_TILE charges in shared memory; one charge's quadrature points are
-// summed in FP32, charges in FP64; the FP64 closed form below one cell size.
-__global__ void __launch_bounds__(BS_WARPS * 32) infl_kernel(const float4 *src, int ns, PanelsDev P, double *S)
+// operator of dL/dsigma with the forward's tiers, four sums per cell.
+//
+// The charges are put in spatial order (Morton bins of the cell box, blocks
+// of at most 512 inside a super-bin); every block gets its bounding box and
+// a copy of its charges relative to the box centre, stored by pairs in the
+// f32x2 layout and padded with empty slots to a multiple of IF_FLUSH.  The
+// cells are put in the same Morton order, so that a warp's 32 cells are
+// neighbours.
+//   infl_far_kernel   a thread block takes IF_CT cells, one per thread, and
+//                     runs over the charge blocks, each copied into shared
+//                     memory by TMA two blocks ahead.  For a block at least
+//                     3 h from a cell's centroid the cell gets the forward's
+//                     far tier (1, 3, 4, 6 or 7 points by that distance); the
+//                     points of all the cells form one list, taken one or two
+//                     points per thread per round against all the block's
+//                     charges (broadcast reads, two charges per f32x2
+//                     instruction), and a cell then adds up its points.  The
+//                     blocks are cut into IF_NCH chunks (grid y), each with
+//                     its own sums.
+//   infl_near_kernel  one warp per cell over its blocks closer than 3 h, one
+//                     charge per lane with the per-pair tier (points of every
+//                     tier precomputed in shared memory); pairs within h go to
+//                     a per-warp queue of the FP64 closed form, evaluated 32
+//                     at a time.
+// The far pass sums IF_FLUSH charges of a point in FP32 and adds these to a
+// compensated (two-sum) FP32 accumulator, and a cell adds its points' sums to
+// another; the near pass sums one block per lane in FP32, reduces the lanes
+// by a fixed butterfly and adds the block sums in FP64.  The chunk sums and
+// the near sum are added in a fixed order: the result does not depend on the
+// schedule.
+#define IF_NCH 8                // block chunks of the far pass
+#define IF_FLUSH 64             // charges per FP32 partial sum of the far pass
+#define IF_FAR_H2 TIER_7PT_H2   // far pass: blocks at least 3 h away
+#define IF_Q 64                 // closed-form queue per warp (< 32 left after a flush, + 32 appended)
+#define IF_NPT 151              // points of the tiers 1, 3, 7, 28, 112
+#define IN_WARPS 4
+
+// first pair of block b in the pair layout: never overlaps block b - 1's
+// padded pairs (ceil(n / IF_FLUSH) * IF_FLUSH / 2 <= n / 2 + 31.5)
+__device__ __forceinline__ int if_pair0(int2 bl, int b) { return (bl.x + 1) / 2 + 33 * b; }
+int obem_influence_pairs(int ns, int maxblocks) { return (ns + 1) / 2 + 33 * maxblocks + 32; }
+
+// the sorted copy of the charges (absolute: xs) and, relative to the block's
+// box centre o, in pairs: xr[2 m] = (x0, x1, y0, y1), xr[2 m + 1] = (z0, z1,
+// q0, q1), padding slots at o with no charge; every block's box: box[3 b] =
+// lo, box[3 b + 1] = hi, box[3 b + 2] = o
+__global__ void __launch_bounds__(256) infl_blocks_kernel(const float4 *src, const int32_t *perm, const int2 *blocks,
+                                                          const int32_t *nblocks, float4 *xs, float4 *xr, float4 *box)
 {
-    __shared__ float4 s_x[BS_TILE];
-    constexpr int PER_WARP = BS_PANELS / BS_WARPS;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double acc[PER_WARP][4];
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= *nblocks) return;
+    const int2 bl = blocks[b];
+    float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
+    for (int l = lane; l < bl.y; l += 32) {
+        const float4 p = src[perm[bl.x + l]];
+        xs[bl.x + l] = p;
+        mn[0] = fminf(mn[0], p.x); mn[1] = fminf(mn[1], p.y); mn[2] = fminf(mn[2], p.z);
+        mx[0] = fmaxf(mx[0], p.x); mx[1] = fmaxf(mx[1], p.y); mx[2] = fmaxf(mx[2], p.z);
+    }
 #pragma unroll
-    for (int i = 0; i < PER_WARP; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
-    for (int tb = 0; tb < ns; tb += BS_TILE) {
-        __syncthreads();
-        for (int l = threadIdx.x; l < BS_TILE; l += BS_WARPS * 32) {
-            const int t = tb + l;
-            s_x[l] = t < ns ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o; o >>= 1) {
+            mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
         }
-        __syncthreads();
-        const int n = min(BS_TILE, ns - tb);
+    const float ox = 0.5f * (mn[0] + mx[0]), oy = 0.5f * (mn[1] + mx[1]), oz = 0.5f * (mn[2] + mx[2]);
+    __syncwarp();
+    const int npair = (bl.y + IF_FLUSH - 1) / IF_FLUSH * (IF_FLUSH / 2);
+    const int p0 = if_pair0(bl, b);
+    for (int m = lane; m < npair; m += 32) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (2 * m < bl.y) a = xs[bl.x + 2 * m];
+        if (2 * m + 1 < bl.y) c = xs[bl.x + 2 * m + 1];
+        const bool ha = 2 * m < bl.y, hc = 2 * m + 1 < bl.y;
+        xr[2 * (size_t)(p0 + m)] = make_float4(ha ? a.x - ox : 0.f, hc ? c.x - ox : 0.f, ha ? a.y - oy : 0.f,
+                                               hc ? c.y - oy : 0.f);
+        xr[2 * (size_t)(p0 + m) + 1] = make_float4(ha ? a.z - oz : 0.f, hc ? c.z - oz : 0.f, a.w, c.w);
+    }
+    if (lane == 0) {
+        box[3 * b] = make_float4(mn[0], mn[1], mn[2], 0.f);
+        box[3 * b + 1] = make_float4(mx[0], mx[1], mx[2], 0.f);
+        box[3 * b + 2] = make_float4(ox, oy, oz, 0.f);
+    }
+}
+
+__device__ __forceinline__ float if_box_d2(float4 c, float4 lo, float4 hi)
+{
+    const float dx = fmaxf(fmaxf(lo.x - c.x, c.x - hi.x), 0.f);
+    const float dy = fmaxf(fmaxf(lo.y - c.y, c.y - hi.y), 0.f);
+    const float dz = fmaxf(fmaxf(lo.z - c.z, c.z - hi.z), 0.f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// ---- bulk copies of a block's charges into shared memory (TMA, 1D), with
+// bounded waits: a wait that runs out (IF_WAIT_NS) records OBEM_ERR_TIMEOUT
+#define IF_WAIT_NS 2000000000ull
+__device__ __forceinline__ uint32_t if_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long if_now()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void if_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(if_smem(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(if_smem(dst)), "l"((unsigned long long)src), "r"(bytes), "r"(if_smem(bar))
+                 : "memory");
+}
+// true once the phase of the given parity has completed, false after IF_WAIT_NS
+__device__ __forceinline__ bool if_bar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = if_smem(bar);
+    const unsigned long long t0 = if_now();
+    for (unsigned i = 0;; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((i & 255u) == 255u && if_now() - t0 > IF_WAIT_NS) return false;
+    }
+}
+
+// One round of the far pass: KP points per thread (slots e0 + IF_CT k + tid
+// of the point list) against every charge of the block (pairs in shared
+// memory); the charges are read once for the KP points.
+#define IF_CT 128               // threads (cells) per block of the far pass
+#define IF_BPAIRS 256           // padded pairs of a block of 512
+template <int KP>
+__device__ __forceinline__ void if_round(const ulonglong2 *xs2, int ng, float4 *sp, int e0)
+{
+    const int tid = threadIdx.x;
+    u64 cx[KP], cy[KP], cz[KP];
+    float pw[KP], ps[KP][4], pc[KP][4];
 #pragma unroll
-        for (int i = 0; i < PER_WARP; ++i) {
-            const int j = blockIdx.x * BS_PANELS + warp + BS_WARPS * i;
-            if (j >= P.np) continue;
-            const float4 ca = P.c_a[j], cl = P.c_lo[j], g0 = P.g0_h[j], g1 = P.g1[j], g2 = P.g2[j];
+    for (int k = 0; k < KP; ++k) {
+        const float4 pt = sp[e0 + IF_CT * k + tid];
+        cx[k] = pk(pt.x, pt.x); cy[k] = pk(pt.y, pt.y); cz[k] = pk(pt.z, pt.z);
+        pw[k] = pt.w;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ps[k][i] = pc[k][i] = 0.f;
+    }
+    for (int g = 0; g < ng; ++g) {
+        const ulonglong2 *xg = xs2 + g * IF_FLUSH;
+        u64 tp[KP], tx[KP], ty[KP], tz[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) tp[k] = tx[k] = ty[k] = tz[k] = 0ull;
+#pragma unroll 4
+        for (int m = 0; m < IF_FLUSH / 2; ++m) {
+            const ulonglong2 A = xg[2 * m], B = xg[2 * m + 1];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const u64 dx = sub2(A.x, cx[k]), dy = sub2(A.y, cy[k]), dz = sub2(B.x, cz[k]);
+                const u64 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                float r0, r1;
+                upk(r2, r0, r1);
+                const u64 inv = pk(rsq(r0), rsq(r1));
+                const u64 w = mul2(B.y, inv);
+                const u64 w3 = mul2(w, mul2(inv, inv));
+                tp[k] = add2(tp[k], w);
+                tx[k] = fma2(w3, dx, tx[k]); ty[k] = fma2(w3, dy, ty[k]); tz[k] = fma2(w3, dz, tz[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            float a0, a1;
+            upk(tp[k], a0, a1); two_sum_acc(ps[k][0], pc[k][0], a0 + a1);
+            upk(tx[k], a0, a1); two_sum_acc(ps[k][1], pc[k][1], a0 + a1);
+            upk(ty[k], a0, a1); two_sum_acc(ps[k][2], pc[k][2], a0 + a1);
+            upk(tz[k], a0, a1); two_sum_acc(ps[k][3], pc[k][3], a0 + a1);
+        }
+    }
+    // each thread overwrites the slots it read: the point's weighted sums
+#pragma unroll
+    for (int k = 0; k < KP; ++k)
+        sp[e0 + IF_CT * k + tid] = make_float4((ps[k][0] + pc[k][0]) * pw[k], (ps[k][1] + pc[k][1]) * pw[k],
+                                               (ps[k][2] + pc[k][2]) * pw[k], (ps[k][3] + pc[k][3]) * pw[k]);
+}
+
+// padded pairs and bytes of block b in the pair layout
+__device__ __forceinline__ uint32_t if_block_bytes(int2 bl)
+{
+    return (uint32_t)((bl.y + IF_FLUSH - 1) / IF_FLUSH * (IF_FLUSH / 2)) * 2u * (uint32_t)sizeof(float4);
+}
+
+// Block of IF_CT threads: cells t = IF_CT x + tid of the cell order (one per
+// thread); charge blocks [b0, b1) of chunk blockIdx.y, each copied into one
+// of two shared buffers (TMA) two blocks ahead.  For every charge block the
+// cells' far points form one list (a block-wide scan of the point counts),
+// processed in rounds of IF_CT or 2 IF_CT slots.  A far block is at least
+// 3 h from the centroid and every point within 2 h / 3 of it, so no pair
+// has zero distance (nor a padding slot: the box centre, no charge); padding
+// points sit at 1e18 m with weight 0.
+__global__ void __launch_bounds__(IF_CT) infl_far_kernel(const float4 *xr, const int2 *blocks, const int32_t *nblocks,
+                                                        const float4 *box, const int32_t *corder, PanelsDev P,
+                                                        double *Spart, int *err)
+{
+    __shared__ __align__(128) float4 s_x[2][2 * IF_BPAIRS];
+    __shared__ float4 s_p[IF_CT * 7];
+    __shared__ int s_w[IF_CT / 32];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t = blockIdx.x * IF_CT + tid;
+    const bool live = t < P.np;
+    const int j = live ? corder[t] : 0;
+    const float4 ca = P.c_a[j], cl = P.c_lo[j];
+    const float h2 = P.g0_h[j].w;
+    const int nb = *nblocks;
+    const int b0 = (int)((long long)nb * blockIdx.y / gridDim.y);
+    const int b1 = (int)((long long)nb * (blockIdx.y + 1) / gridDim.y);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(if_smem(&s_bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(if_smem(&s_bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int q = 0; q < 2 && b0 + q < b1; ++q) {
+            const int2 bl = blocks[b0 + q];
+            if_bulk_load(s_x[q], xr + 2 * (size_t)if_pair0(bl, b0 + q), if_block_bytes(bl), &s_bar[q]);
+        }
+    }
+    __syncthreads();
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int b = b0; b < b1; ++b) {
+        const int it = b - b0, buf = it & 1;
+        const float d2 = if_box_d2(ca, box[3 * b], box[3 * b + 1]);
+        int n = d2 >= TIER_1PT_H2 * h2 ? 1 : d2 >= TIER_3PT_H2 * h2 ? 3 : d2 >= TIER_4PT_H2 * h2 ? 4
+              : d2 >= TIER_6PT_H2 * h2 ? 6 : d2 >= IF_FAR_H2 * h2 ? 7 : 0;
+        if (!live) n = 0;
+        int inc = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        int before = 0, npts = 0;
+#pragma unroll
+        for (int w = 0; w < IF_CT / 32; ++w) {
+            const int v = s_w[w];
+            before += w < warp ? v : 0;
+            npts += v;
+        }
+        const int off = before + inc - n;
+        if (n) {
+            const float4 bo = box[3 * b + 2];
+            const float4 g0 = P.g0_h[j], g1 = P.g1[j], g2 = P.g2[j];
             const float3 G0 = make_float3(g0.x, g0.y, g0.z), G1 = make_float3(g1.x, g1.y, g1.z),
                          G2 = make_float3(g2.x, g2.y, g2.z);
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            for (int l = lane; l < n; l += 32) {
-                const float4 x = s_x[l];
-                const float ex = (x.x - ca.x) - cl.x, ey = (x.y - ca.y) - cl.y, ez = (x.z - ca.z) - cl.z;
-                const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                const int nq = fld_tier(d2, g0.w);
+            const float bx = ca.x - bo.x, by = ca.y - bo.y, bz = ca.z - bo.z;
+            for (int k = 0; k < n; ++k) {
+                float3 o;
+                float wf;
+                far_point(n, k, G0, G1, G2, o, wf);
+                s_p[off + k] = make_float4(bx + (cl.x + o.x), by + (cl.y + o.y), bz + (cl.z + o.z), ca.w * wf);
+            }
+        }
+        const int pend = (npts + IF_CT - 1) / IF_CT * IF_CT;
+        if (npts + tid < pend) s_p[npts + tid] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        const bool ok = if_bar_wait(&s_bar[buf], (uint32_t)(it >> 1) & 1u);
+        if (!__syncthreads_and(ok)) {
+            // the copy of this block never completed: report, wait (bounded)
+            // for the copy of the next one, and leave
+            if (tid == 0) {
+                atomicExch(err, OBEM_ERR_TIMEOUT);
+                if (b + 1 < b1) if_bar_wait(&s_bar[buf ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        if (npts > 0) {
+            const int2 bl = blocks[b];
+            const ulonglong2 *xs2 = (const ulonglong2 *)s_x[buf];
+            const int ng = (bl.y + IF_FLUSH - 1) / IF_FLUSH;
+            // a warp skips the parts of a round that hold padding only
+            for (int e0 = 0; e0 < npts;) {
+                const int wb = e0 + 32 * warp;
+                if (npts - e0 > IF_CT) {
+                    if (wb + IF_CT < npts) if_round<2>(xs2, ng, s_p, e0);
+                    else if_round<1>(xs2, ng, s_p, e0);
+                    e0 += 2 * IF_CT;
+                } else {
+                    if (wb < npts) if_round<1>(xs2, ng, s_p, e0);
+                    e0 += IF_CT;
+                }
+            }
+        }
+        __syncthreads();
+        if (n) {
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < n; ++k) {
+                const float4 e = s_p[off + k];
+                v[0] += e.x; v[1] += e.y; v[2] += e.z; v[3] += e.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) two_sum_acc(s[i], c[i], v[i]);
+        }
+        __syncthreads();
+        if (tid == 0 && b + 2 < b1) {
+            // every thread is done with this buffer: refill it two blocks ahead
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const int2 bl = blocks[b + 2];
+            if_bulk_load(s_x[buf], xr + 2 * (size_t)if_pair0(bl, b + 2), if_block_bytes(bl), &s_bar[buf]);
+        }
+    }
+    if (live) {
+        double *o = Spart + ((size_t)blockIdx.y * P.np + j) * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = (double)s[i] + (double)c[i];
+    }
+}
+
+// butterfly over the warp: lanes 8 g .. 8 g + 7 end with the warp's sum of v[g]
+__device__ __forceinline__ float if_reduce4(const float (&v)[4])
+{
+    const int lane = threadIdx.x & 31;
+    const bool up = lane & 16;
+    const float k0 = up ? v[2] : v[0], k1 = up ? v[3] : v[1];
+    const float b0 = k0 + __shfl_xor_sync(0xffffffffu, up ? v[0] : v[2], 16);
+    const float b1 = k1 + __shfl_xor_sync(0xffffffffu, up ? v[1] : v[3], 16);
+    const bool u8 = lane & 8;
+    float c = (u8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, u8 ? b0 : b1, 8);
+    c += __shfl_xor_sync(0xffffffffu, c, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+// the queued charges [0, n) of the closed-form queue, one per lane (FP64,
+// result rounded to FP32 into the lane's sums)
+__device__ __forceinline__ void if_closed(const PanelsDev &P, int j, const float4 *cq, int n, float (&v)[4])
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        const float4 x = cq[lane];
+        double phi, fx, fy, fz;
+        tri_closed_form(P.v64 + 9 * (size_t)j, (double)x.x, (double)x.y, (double)x.z, phi, fx, fy, fz);
+        const double qk = (double)x.w * OBEM_KC;
+        v[0] += (float)(qk * phi); v[1] += (float)(qk * fx);
+        v[2] += (float)(qk * fy); v[3] += (float)(qk * fz);
+    }
+    __syncwarp();
+}
+
+// first point of a tier in the near pass's point table
+__device__ __forceinline__ int if_tier_base(int nq)
+{
+    return nq == 1 ? 0 : nq == 3 ? 1 : nq == 7 ? 4 : nq == 28 ? 11 : 39;
+}
+
+__global__ void __launch_bounds__(IN_WARPS * 32) infl_near_kernel(const float4 *xs, const int2 *blocks,
+                                                                  const int32_t *nblocks, const float4 *box,
+                                                                  PanelsDev P, double *Snear)
+{
+    __shared__ float4 s_cq[IN_WARPS][IF_Q];
+    __shared__ float4 s_pt[IN_WARPS][IF_NPT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.x * IN_WARPS + warp;
+    if (j >= P.np) return;
+    const float4 ca = P.c_a[j], cl = P.c_lo[j], g0 = P.g0_h[j], g1 = P.g1[j], g2 = P.g2[j];
+    {
+        const float3 G0 = make_float3(g0.x, g0.y, g0.z), G1 = make_float3(g1.x, g1.y, g1.z),
+                     G2 = make_float3(g2.x, g2.y, g2.z);
+        for (int e = lane; e < IF_NPT; e += 32) {
+            const int nq = e < 1 ? 1 : e < 4 ? 3 : e < 11 ? 7 : e < 39 ? 28 : 112;
+            float3 off;
+            float wf;
+            tier_point(nq, e - if_tier_base(nq), G0, G1, G2, off, wf);
+            s_pt[warp][e] = make_float4(cl.x + off.x, cl.y + off.y, cl.z + off.z, ca.w * wf);
+        }
+        __syncwarp();
+    }
+    const float4 *pt = s_pt[warp];
+    float4 *cq = s_cq[warp];
+    const int nb = *nblocks;
+    double acc = 0.0;
+    for (int bb0 = 0; bb0 < nb; bb0 += 32) {
+        const int bb = bb0 + lane;
+        const bool near = bb < nb && if_box_d2(ca, box[3 * bb], box[3 * bb + 1]) < IF_FAR_H2 * g0.w;
+        unsigned bal = __ballot_sync(0xffffffffu, near);
+        while (bal) {
+            const int b = bb0 + __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int2 bl = blocks[b];
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            int qn = 0;
+            for (int l0 = 0; l0 < bl.y; l0 += 32) {
+                const int l = l0 + lane;
+                const float4 x = l < bl.y ? xs[bl.x + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float ex = x.x - ca.x, ey = x.y - ca.y, ez = x.z - ca.z;
+                const float fx = ex - cl.x, fy = ey - cl.y, fz = ez - cl.z;
+                const int nq = l < bl.y ? fld_tier(fmaf(fz, fz, fmaf(fy, fy, fx * fx)), g0.w) : -1;
                 if (nq > 0) {
-                    float vp = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+                    float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+                    const int k0 = if_tier_base(nq);
                     for (int k = 0; k < nq; ++k) {
-                        float3 off;
-                        float wf;
-                        tier_point(nq, k, G0, G1, G2, off, wf);
-                        const float dx = ex - off.x, dy = ey - off.y, dz = ez - off.z;
+                        const float4 o = pt[k0 + k];
+                        const float dx = ex - o.x, dy = ey - o.y, dz = ez - o.z;
                         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                         if (!(r2 > 0.f)) continue;
                         const float inv = rsq(r2);
-                        const float w = ca.w * wf * inv;
+                        const float w = o.w * inv;
                         const float w3 = w * inv * inv;
-                        vp += w;
-                        vx = fmaf(w3, dx, vx); vy = fmaf(w3, dy, vy); vz = fmaf(w3, dz, vz);
+                        sp += w;
+                        sx = fmaf(w3, dx, sx); sy = fmaf(w3, dy, sy); sz = fmaf(w3, dz, sz);
                     }
-                    a0 += (double)x.w * vp; a1 += (double)x.w * vx; a2 += (double)x.w * vy; a3 += (double)x.w * vz;
-                } else {
-                    double phi, fx, fy, fz;
-                    tri_closed_form(P.v64 + 9 * (size_t)j, (double)x.x, (double)x.y, (double)x.z, phi, fx, fy, fz);
-                    const double qk = (double)x.w * OBEM_KC;
-                    a0 += qk * phi; a1 += qk * fx; a2 += qk * fy; a3 += qk * fz;
+                    v[0] = fmaf(x.w, sp, v[0]); v[1] = fmaf(x.w, sx, v[1]);
+                    v[2] = fmaf(x.w, sy, v[2]); v[3] = fmaf(x.w, sz, v[3]);
+                }
+                const unsigned cb = __ballot_sync(0xffffffffu, nq == 0);
+                if (cb) {
+                    if (nq == 0) cq[qn + __popc(cb & ((1u << lane) - 1u))] = x;
+                    qn += __popc(cb);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        if_closed(P, j, cq, 32, v);
+                        const float4 tq = lane < qn - 32 ? cq[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        __syncwarp();
+                        if (lane < qn - 32) cq[lane] = tq;
+                        qn -= 32;
+                        __syncwarp();
+                    }
                 }
             }
-            acc[i][0] += a0; acc[i][1] += a1; acc[i][2] += a2; acc[i][3] += a3;
+            if (qn > 0) if_closed(P, j, cq, qn, v);
+            acc += (double)if_reduce4(v);
         }
     }
-#pragma unroll
-    for (int i = 0; i < PER_WARP; ++i) {
-        const int j = blockIdx.x * BS_PANELS + warp + BS_WARPS * i;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            double v = acc[i][c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && j < P.np) S[4 * (size_t)j + c] = v;
-        }
-    }
+    if ((lane & 7) == 0) Snear[4 * (size_t)j + (lane >> 3)] = acc;
 }
 
-// Right-hand-side correction of Eqs. (BEMpotpart), (BEMfldpart) from S:
-// electrode cells -Vbar_j = -S_phi / A_j; dielectric cells
-// -(eps+ - eps-) eps0 Ebar_j . n_j with Ebar_j = -S_F / A_j.
-__global__ void infl_rhs_kernel(const double *S, const double *geo, const int *kind, const double *epsd, int np,
-                                float *drhs)
+// Right-hand-side correction of Eqs. (BEMpotpart), (BEMfldpart) from S
+// (the far chunks' sums, then the near sum; S itself is kept): electrode
+// cells -Vbar_j = -S_phi / A_j; dielectric cells -(eps+ - eps-) eps0
+// Ebar_j . n_j with Ebar_j = -S_F / A_j.
+__global__ void infl_rhs_kernel(const double *Spart, int nparts, const double *Snear, double *S, const double *geo,
+                                const int *kind, const double *epsd, int np, float *drhs)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= np) return;
+    double t[4];
+    for (int i = 0; i < 4; ++i) {
+        double v = 0.0;
+        for (int c = 0; c < nparts; ++c) v += Spart[((size_t)c * np + j) * 4 + i];
+        if (Snear) v += Snear[4 * (size_t)j + i];
+        t[i] = v;
+        S[4 * (size_t)j + i] = v;
+    }
     const double *g = geo + (size_t)OBEM_GEO64 * j;
     const double area = 0.5 * g[3];
-    const double *s = S + 4 * (size_t)j;
     double v;
-    if (kind[j] == OBEM_CELL_ELECTRODE) v = -s[0] / area;
-    else v = epsd[j] * OBEM_EPS0 * (s[1] * g[0] + s[2] * g[1] + s[3] * g[2]) / area;
+    if (kind[j] == OBEM_CELL_ELECTRODE) v = -t[0] / area;
+    else v = epsd[j] * OBEM_EPS0 * (t[1] * g[0] + t[2] * g[1] + t[3] * g[2]) / area;
     drhs[j] = (float)v;
 }
 
+static size_t if_align(size_t b) { return (b + 255) & ~(size_t)255; }
+// scratch: point bins (charges, then the cells), the cell order, the sorted
+// charges (absolute and relative), the block boxes, the chunk sums and the
+// near sums
+size_t obem_influence_scratch_bytes(int ns, int np)
+{
+    if (ns <= 0 || np <= 0) return 0;
+    const size_t bins = obem_point_bins_bytes(ns > np ? ns : np);
+    const int mb = obem_point_bins_maxblocks(ns);
+    return bins + if_align(sizeof(int32_t) * (size_t)np) + if_align(sizeof(float4) * (size_t)ns) +
+           if_align(sizeof(float4) * 2 * (size_t)obem_influence_pairs(ns, mb)) + if_align(sizeof(float4) * 3 * (size_t)mb) +
+           if_align(sizeof(double) * 4 * (size_t)np * (IF_NCH + 1) + sizeof(int));
+}
+
 int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const PanelsDev &P, double *S, const double *geo,
-                          const int *kind, const double *epsd, float *drhs, cudaStream_t s)
+                          const int *kind, const double *epsd, float *drhs, void *scratch, cudaStream_t s)
 {
     if (P.np <= 0) return OBEM_OK;
     if (ns > 0) {
-        infl_kernel<<<(P.np + BS_PANELS - 1) / BS_PANELS, BS_WARPS * 32, 0, s>>>(src, ns, P, S);
+        char *p = (char *)scratch;
+        char *bins = p;
+        p += obem_point_bins_bytes(ns > P.np ? ns : P.np);
+        int32_t *corder = (int32_t *)p;
+        p += if_align(sizeof(int32_t) * (size_t)P.np);
+        float4 *xs = (float4 *)p;
+        p += if_align(sizeof(float4) * (size_t)ns);
+        float4 *xr = (float4 *)p;
+        p += if_align(sizeof(float4) * 2 * (size_t)obem_influence_pairs(ns, obem_point_bins_maxblocks(ns)));
+        float4 *box = (float4 *)p;
+        p += if_align(sizeof(float4) * 3 * (size_t)obem_point_bins_maxblocks(ns));
+        double *Spart = (double *)p;
+        double *Snear = Spart + 4 * (size_t)P.np * IF_NCH;
+        int *err = (int *)(Snear + 4 * (size_t)P.np);
+        int32_t *perm, *nblocks;
+        int2 *blocks;
+        // the cells in Morton order of their centroids
+        int rc = obem_point_bins(ctx, P.c_a, P.np, bins, &perm, &blocks, &nblocks, s);
+        if (rc != OBEM_OK) return rc;
+        OBEM_CUDA(ctx, cudaMemcpyAsync(corder, perm, sizeof(int32_t) * (size_t)P.np, cudaMemcpyDeviceToDevice, s));
+        // the charges in blocks
+        rc = obem_point_bins(ctx, src, ns, bins, &perm, &blocks, &nblocks, s);
+        if (rc != OBEM_OK) return rc;
+        const int mb = obem_point_bins_maxblocks(ns);
+        infl_blocks_kernel<<<(mb + 7) / 8, 256, 0, s>>>(src, perm, blocks, nblocks, xs, xr, box);
+        OBEM_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
+        infl_far_kernel<<<dim3((P.np + IF_CT - 1) / IF_CT, IF_NCH), IF_CT, 0, s>>>(xr, blocks, nblocks, box, corder,
+                                                                                 P, Spart, err);
+        infl_near_kernel<<<(P.np + IN_WARPS - 1) / IN_WARPS, IN_WARPS * 32, 0, s>>>(xs, blocks, nblocks, box, P,
+                                                                                   Snear);
         OBEM_LAUNCH(ctx);
+        infl_rhs_kernel<<<(P.np + 255) / 256, 256, 0, s>>>(Spart, IF_NCH, Snear, S, geo, kind, epsd, P.np, drhs);
+        OBEM_LAUNCH(ctx);
+        int h = 0;
+        OBEM_CUDA(ctx, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        OBEM_CUDA(ctx, cudaStreamSynchronize(s));
+        if (h != 0) return obem_fail(ctx, OBEM_ERR_TIMEOUT, "influence: a wait for a bulk copy timed out");
+        return OBEM_OK;
     } else {
         OBEM_CUDA(ctx, cudaMemsetAsync(S, 0, sizeof(double) * 4 * (size_t)P.np, s));
+        infl_rhs_kernel<<<(P.np + 255) / 256, 256, 0, s>>>(S, 1, NULL, S, geo, kind, epsd, P.np, drhs);
     }
-    infl_rhs_kernel<<<(P.np + 255) / 256, 256, 0, s>>>(S, geo, kind, epsd, P.np, drhs);
     OBEM_LAUNCH(ctx);
     return OBEM_OK;
 }

@@ -16,8 +16,8 @@
 // Cells.  Targets are ordered along a 64^3 Morton grid (stable radix sort) and
 // cut into blocks of <= 512; per block, cells near its box get the FP64
 // closed form (targets within h) and a 112- or 28-point rule, the others one
-// of the quadrature tiers listed at TIER_*_H2 below, emitted as point sources
-// into the same packed loop as the charges.
+// of the quadrature tiers of field_common.cuh (TIER_*_H2, far_point),
+// emitted as point sources into the same packed loop as the charges.
 #include "obem_internal.cuh"
 #include "field_common.cuh"
 
@@ -37,17 +37,7 @@
 #define FT_SRC_TILE 256
 #define FT_PAN_TILE 64
 
-// Far-cell tiers by the squared distance of the cell's centroid to the target
-// box in units of h^2 (h: longest edge).  Worst-case relative error of one
-// cell's field (targets in every direction, in-plane toward the vertices
-// included): centroid 3.6e-6 at 200 h; 3-point (degree 2) 3.0e-6 at 16 h;
-// 4-point (degree 3) 2.0e-6 at 10 h; 6-point (degree 4) 1.4e-6 at 4 h;
-// 7-point (degree 5) 1.7e-6 at 3 h; 28-point 2.6e-6 at 1.5 h.
-#define TIER_1PT_H2 40000.0f
-#define TIER_3PT_H2 256.0f
-#define TIER_4PT_H2 100.0f
-#define TIER_6PT_H2 16.0f
-#define TIER_7PT_H2 9.0f
+// Far-cell tiers (TIER_*_H2) and their rules (far_point): field_common.cuh.
 
 
 
@@ -256,6 +246,51 @@ static void binsort(const uint32_t *code_in, uint32_t *code, int32_t *perm, uint
         rs_scan_kernel<<<1, 1024, 0, s>>>(rh, RS_RADIX * nblk);
         rs_scatter_kernel<<<nblk, RS_BLOCK, 0, s>>>(kin[p], vin[p], kout[p], vout[p], nt, nt_dev, 6 * p, nblk, rh);
     }
+}
+
+// Spatial order of n points for a pass that runs over the cells outermost
+// (the influence of charges on the cells): the Morton bins of the cell box,
+// the stable radix sort and the blocks of at most CT_BLOCK_N points inside a
+// super-bin, as for the targets of the cell kernels, in scratch of
+// obem_point_bins_bytes(n) bytes.
+static size_t pb_align(size_t b) { return (b + 255) & ~(size_t)255; }
+int obem_point_bins_maxblocks(int n) { return n / CT_BLOCK_N + 2 + (n < OBEM_NSUPER ? n : OBEM_NSUPER); }
+size_t obem_point_bins_bytes(int n)
+{
+    const size_t e = pb_align(sizeof(int32_t) * (size_t)n);
+    return 4 * e + pb_align(sizeof(int32_t) * ((size_t)RS_RADIX * obem_binsort_blocks(n) + 1)) +
+           pb_align(sizeof(int32_t) * OBEM_NBINS) + pb_align(sizeof(int2) * obem_point_bins_maxblocks(n)) +
+           pb_align(sizeof(int32_t) * 8);
+}
+int obem_point_bins(obem_ctx *ctx, const float4 *pts, int n, void *scratch, int32_t **perm, int2 **blocks,
+                    int32_t **nblocks, cudaStream_t s)
+{
+    char *p = (char *)scratch;
+    const size_t e = pb_align(sizeof(int32_t) * (size_t)n);
+    uint32_t *code = (uint32_t *)p; p += e;
+    *perm = (int32_t *)p; p += e;
+    uint32_t *tk = (uint32_t *)p; p += e;
+    int32_t *tv = (int32_t *)p; p += e;
+    int32_t *rh = (int32_t *)p; p += pb_align(sizeof(int32_t) * ((size_t)RS_RADIX * obem_binsort_blocks(n) + 1));
+    int32_t *hist = (int32_t *)p; p += pb_align(sizeof(int32_t) * OBEM_NBINS);
+    *blocks = (int2 *)p; p += pb_align(sizeof(int2) * obem_point_bins_maxblocks(n));
+    *nblocks = (int32_t *)p;
+    FieldLaunch L;
+    memset(&L, 0, sizeof L);
+    L.targets = pts;
+    L.nt = n;
+    float3 lo = make_float3(ctx->bbox_lo[0], ctx->bbox_lo[1], ctx->bbox_lo[2]);
+    float3 sc;
+    sc.x = (float)OBEM_BINS_PER_AXIS / fmaxf(ctx->bbox_hi[0] - ctx->bbox_lo[0], 1e-30f);
+    sc.y = (float)OBEM_BINS_PER_AXIS / fmaxf(ctx->bbox_hi[1] - ctx->bbox_lo[1], 1e-30f);
+    sc.z = (float)OBEM_BINS_PER_AXIS / fmaxf(ctx->bbox_hi[2] - ctx->bbox_lo[2], 1e-30f);
+    OBEM_CUDA(ctx, cudaMemsetAsync(hist, 0, sizeof(int32_t) * OBEM_NBINS, s));
+    bin_count_kernel<<<(n + 255) / 256, 256, 0, s>>>(L, lo, sc, code, hist);
+    bin_scan_kernel<<<1, 1024, 0, s>>>(hist);
+    block_list_kernel<<<1, 1024, 0, s>>>(hist, n, NULL, *blocks, *nblocks);
+    binsort(code, code, *perm, tk, tv, rh, n, NULL, n, s);
+    OBEM_LAUNCH(ctx);
+    return OBEM_OK;
 }
 
 // ---------------------------------------------------------------- cell field kernels
@@ -777,32 +812,9 @@ cell_kernel(FieldLaunch L)
                     float w;
                     // points c + s g_k (g_k = v_k - c): the symmetric rules' points
                     // (a, b, b) are c + (a - b) g_k since g_0 + g_1 + g_2 = 0
-                    if (n == 1) { off = make_float3(0.f, 0.f, 0.f); w = q; }
-                    else if (n == 3) {
-                        // degree 2: barycentric (2/3, 1/6, 1/6), weights 1/3
-                        const float3 g = k == 0 ? G0 : (k == 1 ? G1 : G2);
-                        off = make_float3(0.5f * g.x, 0.5f * g.y, 0.5f * g.z);
-                        w = q * (1.0f / 3.0f);
-                    } else if (n == 4) {
-                        // degree 3: centroid (weight -27/48), (0.6, 0.2, 0.2) (weights 25/48)
-                        if (k == 0) { off = make_float3(0.f, 0.f, 0.f); w = q * (-27.0f / 48.0f); }
-                        else {
-                            const float3 g = k == 1 ? G0 : (k == 2 ? G1 : G2);
-                            off = make_float3(0.4f * g.x, 0.4f * g.y, 0.4f * g.z);
-                            w = q * (25.0f / 48.0f);
-                        }
-                    } else if (n == 6) {
-                        // degree 4 (Dunavant): (a, b, b) with a - b = -0.3378454727478950, weight
-                        // 0.223381589678011, and a - b = 0.7252713594706880, weight 0.109951743655322
-                        const float3 g = (k % 3) == 0 ? G0 : ((k % 3) == 1 ? G1 : G2);
-                        const float sgk = k < 3 ? -0.33784547274789500f : 0.72527135947068800f;
-                        off = make_float3(sgk * g.x, sgk * g.y, sgk * g.z);
-                        w = q * (k < 3 ? 0.223381589678011f : 0.109951743655322f);
-                    } else {
-                        float wf;
-                        rule_point(n == 7 ? 0 : 1, k, G0, G1, G2, off, wf);
-                        w = q * wf;
-                    }
+                    float wf;
+                    far_point(n, k, G0, G1, G2, off, wf);
+                    w = q * wf;
                     const float px = t.cq.x + off.x, py = t.cq.y + off.y, pz = t.cq.z + off.z;
                     SrcPk sp;
                     sp.xx = pk(px, px); sp.yy = pk(py, py); sp.zz = pk(pz, pz); sp.qq = pk(w, w);
@@ -1043,28 +1055,9 @@ cell_group_kernel(FieldLaunch L, CellGroups G)
                 for (int k = sub; k < n; k += 4) {
                     float3 off;
                     float w;
-                    if (n == 1) { off = make_float3(0.f, 0.f, 0.f); w = q; }
-                    else if (n == 3) {
-                        const float3 gk = k == 0 ? G0 : (k == 1 ? G1 : G2);
-                        off = make_float3(0.5f * gk.x, 0.5f * gk.y, 0.5f * gk.z);
-                        w = q * (1.0f / 3.0f);
-                    } else if (n == 4) {
-                        if (k == 0) { off = make_float3(0.f, 0.f, 0.f); w = q * (-27.0f / 48.0f); }
-                        else {
-                            const float3 gk = k == 1 ? G0 : (k == 2 ? G1 : G2);
-                            off = make_float3(0.4f * gk.x, 0.4f * gk.y, 0.4f * gk.z);
-                            w = q * (25.0f / 48.0f);
-                        }
-                    } else if (n == 6) {
-                        const float3 gk = (k % 3) == 0 ? G0 : ((k % 3) == 1 ? G1 : G2);
-                        const float sgk = k < 3 ? -0.33784547274789500f : 0.72527135947068800f;
-                        off = make_float3(sgk * gk.x, sgk * gk.y, sgk * gk.z);
-                        w = q * (k < 3 ? 0.223381589678011f : 0.109951743655322f);
-                    } else {
-                        float wf;
-                        rule_point(n == 7 ? 0 : 1, k, G0, G1, G2, off, wf);
-                        w = q * wf;
-                    }
+                    float wf;
+                    far_point(n, k, G0, G1, G2, off, wf);
+                    w = q * wf;
                     const float px = t.cq.x + off.x, py = t.cq.y + off.y, pz = t.cq.z + off.z;
                     SrcPk sp;
                     sp.xx = pk(px, px); sp.yy = pk(py, py); sp.zz = pk(pz, pz); sp.qq = pk(w, w);

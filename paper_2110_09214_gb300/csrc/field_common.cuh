@@ -213,3 +213,46 @@ __device__ __forceinline__ void rule_point(int level, int k, float3 g0, float3 g
     off = make_float3(fmaf(t, V.x - sc.x, sc.x), fmaf(t, V.y - sc.y, sc.y), fmaf(t, V.z - sc.z, sc.z));
     wf = scale * (m <= 3 ? D7_W1 : D7_W2);
 }
+
+// Far-cell tiers by the squared distance of the cell's centroid to a box of
+// points in units of h^2 (h: longest edge).  Worst-case relative error of one
+// cell's field (points in every direction, in-plane toward the vertices
+// included): centroid 3.6e-6 at 200 h; 3-point (degree 2) 3.0e-6 at 16 h;
+// 4-point (degree 3) 2.0e-6 at 10 h; 6-point (degree 4) 1.4e-6 at 4 h;
+// 7-point (degree 5) 1.7e-6 at 3 h; 28-point 2.6e-6 at 1.5 h.
+#define TIER_1PT_H2 40000.0f
+#define TIER_3PT_H2 256.0f
+#define TIER_4PT_H2 100.0f
+#define TIER_6PT_H2 16.0f
+#define TIER_7PT_H2 9.0f
+
+// point k of the n-point far tier (n = 1, 3, 4, 6, 7, 28): offset from the
+// centroid (the rules' points (a, b, b) are c + (a - b) g_k, as g_0 + g_1 +
+// g_2 = 0) and weight fraction
+__device__ __forceinline__ void far_point(int n, int k, float3 G0, float3 G1, float3 G2, float3 &off, float &wf)
+{
+    if (n == 1) { off = make_float3(0.f, 0.f, 0.f); wf = 1.0f; }
+    else if (n == 3) {
+        // degree 2: barycentric (2/3, 1/6, 1/6), weights 1/3
+        const float3 g = k == 0 ? G0 : (k == 1 ? G1 : G2);
+        off = make_float3(0.5f * g.x, 0.5f * g.y, 0.5f * g.z);
+        wf = 1.0f / 3.0f;
+    } else if (n == 4) {
+        // degree 3: centroid (weight -27/48), (0.6, 0.2, 0.2) (weights 25/48)
+        if (k == 0) { off = make_float3(0.f, 0.f, 0.f); wf = -27.0f / 48.0f; }
+        else {
+            const float3 g = k == 1 ? G0 : (k == 2 ? G1 : G2);
+            off = make_float3(0.4f * g.x, 0.4f * g.y, 0.4f * g.z);
+            wf = 25.0f / 48.0f;
+        }
+    } else if (n == 6) {
+        // degree 4 (Dunavant): (a, b, b) with a - b = -0.3378454727478950, weight
+        // 0.223381589678011, and a - b = 0.7252713594706880, weight 0.109951743655322
+        const float3 g = (k % 3) == 0 ? G0 : ((k % 3) == 1 ? G1 : G2);
+        const float sgk = k < 3 ? -0.33784547274789500f : 0.72527135947068800f;
+        off = make_float3(sgk * g.x, sgk * g.y, sgk * g.z);
+        wf = k < 3 ? 0.223381589678011f : 0.109951743655322f;
+    } else {
+        rule_point(n == 7 ? 0 : 1, k, G0, G1, G2, off, wf);
+    }
+}

@@ -178,6 +178,7 @@ extern "C" void obem_destroy(obem_ctx *c)
     free_dev(c->o_vel); free_dev(c->o_id); free_dev(c->o_birth); free_dev(c->o_sp);
     free_dev(c->s_code); free_dev(c->s_perm); free_dev(c->s_hist); free_dev(c->s_blocks); free_dev(c->s_nblocks);
     free_dev(c->s_tk); free_dev(c->s_tv); free_dev(c->s_rh);
+    free_dev(c->d_ib);
     free_dev(c->sym_jpart); free_dev(c->sym_ipart); free_dev(c->sym_counter); free_dev(c->sym_acc);
     free_dev(c->sym_sorted); free_dev(c->sym_perm); free_dev(c->sym_bcnt); free_dev(c->sym_tileq);
     free_dev(c->ph_count); free_dev(c->ph_start); free_dev(c->ph_cursor); free_dev(c->ph_bucket); free_dev(c->ph_sorted); free_dev(c->ph_bsum);
@@ -802,8 +803,16 @@ extern "C" int obem_influence_rhs(obem_ctx *c, const float *sources, int32_t ns,
         free(h);
         OBEM_CUDA(c, e);
     }
+    const size_t need = obem_influence_scratch_bytes(ns, c->np);
+    if (ns > 0 && need > c->ib_bytes) {
+        free_dev(c->d_ib);
+        c->d_ib = NULL;
+        c->ib_bytes = 0;
+        OBEM_CUDA(c, cudaMalloc(&c->d_ib, need));
+        c->ib_bytes = need;
+    }
     return obem_launch_influence(c, (const float4 *)sources, ns, panels_of(c), c->d_infl, c->d_geo64, c->d_kind,
-                                 c->d_epsd, drhs, s);
+                                 c->d_epsd, drhs, c->d_ib, s);
 }
 
 extern "C" int obem_surface_charge(obem_ctx *c, float *sigma_free, int64_t *counts, int32_t reset,

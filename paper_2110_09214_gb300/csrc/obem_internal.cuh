@@ -157,6 +157,8 @@ struct obem_ctx {
     float *d_sigma;      // current sigma [np]
     double *d_infl;      // [np][4] charge sums of the influence right-hand side (obem_influence_rhs)
     double *d_epsd;      // [np] eps_plus - eps_minus of the dielectric cells (0 on electrode cells)
+    void *d_ib;          // scratch of the influence pass (binned charges), ib_bytes
+    size_t ib_bytes;
     int sigma_valid;
     unsigned long long sigma_ver;   // bumped whenever d_sigma is rewritten
     // far-cell groups (OBEM_STEP_CELL_GROUPS; ngrp == 0: not built)
@@ -374,6 +376,10 @@ size_t obem_sym_ipart_floats(int capacity);
 int obem_sym_grid(int device);
 int obem_sym_part_blocks(int capacity);
 int obem_binsort_blocks(int capacity);
+int obem_point_bins_maxblocks(int n);
+size_t obem_point_bins_bytes(int n);
+int obem_point_bins(obem_ctx *ctx, const float4 *pts, int n, void *scratch, int32_t **perm, int2 **blocks,
+                    int32_t **nblocks, cudaStream_t s);
 int obem_sym_tiles(int capacity);
 
 // nn.cu
@@ -398,8 +404,9 @@ struct BwArgs {
     float *dL_dsigma, *dL_dtargets, *dL_dsources;
 };
 int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s);
+size_t obem_influence_scratch_bytes(int ns, int np);
 int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const PanelsDev &P, double *S, const double *geo,
-                          const int *kind, const double *epsd, float *drhs, cudaStream_t s);
+                          const int *kind, const double *epsd, float *drhs, void *scratch, cudaStream_t s);
 
 // step.cu
 int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,

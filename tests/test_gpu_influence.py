@@ -130,3 +130,47 @@ def test_dynamic_resolve_with_the_influence_matches_oracle():
     ind, ind_ref = got - got0, ref - oracle.solve(A, oracle.bem_rhs(mesh))
     ulp = np.spacing(np.abs(got0).astype(np.float32)).astype(np.float64)
     assert np.all(np.abs(ind - ind_ref) <= 1e-3 * np.abs(ind_ref).max() + 4 * ulp)
+
+
+def test_influence_at_full_size_sampled_cells():
+    """The headline workload (59,968 cells of a GEM patch, 1e6 signed charges
+    in clouds on the hole axes) through the binned kernel: every cell on the
+    GPU, the oracle at 16 cells with a charge closer than one cell size (the
+    per-pair tiers and the closed form) and 16 random cells, with the charges'
+    sum-of-magnitudes scale of each sampled cell."""
+    from types import SimpleNamespace
+    from scipy.spatial import cKDTree
+    mesh, _, ch, _, _ = inputs.config_gem(seed=2)
+    src = np.ascontiguousarray(ch.pos_q.astype(np.float32))
+    src[:, 3] = np.where(ch.species == 0, -E, E)
+    ctx = obem.obem_create(capacity=8, dt=1e-12)
+    try:
+        obem.obem_mesh_load(ctx, mesh)
+        got = _gpu_influence(ctx, mesh, src).cpu().numpy().astype(np.float64)
+        again = _gpu_influence(ctx, mesh, src).cpu().numpy().astype(np.float64)
+    finally:
+        obem.obem_destroy(ctx)
+    assert np.all(np.isfinite(got)) and np.array_equal(got, again)
+    tri = np.asarray(mesh.tri, np.float64)
+    cen = tri.mean(axis=1)
+    h = np.max(np.linalg.norm(tri - np.roll(tri, 1, axis=1), axis=2), axis=1)
+    d, _ = cKDTree(src[:, :3].astype(np.float64)).query(cen, k=1)
+    rng = np.random.default_rng(7)
+    close = np.flatnonzero(d < h)
+    assert len(close) >= 16
+    sel = np.unique(np.concatenate([rng.choice(close, 16, replace=False), rng.choice(mesh.n, 16, replace=False)]))
+    sub = SimpleNamespace(n=len(sel), tri=tri[sel], kind=mesh.kind[sel], eps_minus=mesh.eps_minus[sel],
+                          eps_plus=mesh.eps_plus[sel])
+    ref = oracle.influence_rhs(sub, src.astype(np.float64))
+    p = src[:, :3].astype(np.float64)
+    aq = np.abs(src[:, 3]).astype(np.float64)
+    scale = np.empty(len(sel))
+    for i, j in enumerate(sel):
+        r = np.linalg.norm(p - cen[j], axis=1)
+        if mesh.kind[j] == 0:
+            scale[i] = KC * (aq / r).sum()
+        else:
+            scale[i] = abs(mesh.eps_plus[j] - mesh.eps_minus[j]) * EPS0 * KC * (aq / r ** 2).sum()
+    g = got[sel]
+    err = np.abs(g - ref) / np.maximum(np.abs(ref), 0.1 * scale)
+    assert err.max() <= FIELD_TOL, (err.max(), sel[int(np.argmax(err))])
