@@ -698,11 +698,44 @@ __device__ __forceinline__ int if_tier_base(int nq)
     return nq == 1 ? 0 : nq == 3 ? 1 : nq == 7 ? 4 : nq == 28 ? 11 : 39;
 }
 
+// the queued charges [0, n) of a quadrature queue (every one with the
+// nq-point tier, points k0 .. k0 + nq - 1 of the table), one per lane
+__device__ __forceinline__ void if_quad_flush(const float4 *cq, int n, float4 ca, const float4 *pt, int k0, int nq,
+                                              float (&v)[4])
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        const float4 x = cq[lane];
+        const float ex = x.x - ca.x, ey = x.y - ca.y, ez = x.z - ca.z;
+        float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int k = 0; k < nq; ++k) {
+            const float4 o = pt[k0 + k];
+            const float dx = ex - o.x, dy = ey - o.y, dz = ez - o.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (!(r2 > 0.f)) continue;
+            const float inv = rsq(r2);
+            const float w = o.w * inv;
+            const float w3 = w * inv * inv;
+            sp += w;
+            sx = fmaf(w3, dx, sx); sy = fmaf(w3, dy, sy); sz = fmaf(w3, dz, sz);
+        }
+        v[0] = fmaf(x.w, sp, v[0]); v[1] = fmaf(x.w, sx, v[1]);
+        v[2] = fmaf(x.w, sy, v[2]); v[3] = fmaf(x.w, sz, v[3]);
+    }
+    __syncwarp();
+}
+
+// Warp per cell.  Per 32 charges of a near block, the pairs of the 1- to
+// 7-point tiers are done in place; the 28-point, 112-point and closed-form
+// pairs are appended to three per-warp queues, each evaluated 32 pairs at a
+// time, so that the lanes of a warp run the same point loop.  Queue order
+// is (charge slot, lane) and every lane adds its results in that order: the
+// sums are deterministic.
 __global__ void __launch_bounds__(IN_WARPS * 32) infl_near_kernel(const float4 *xs, const int2 *blocks,
                                                                   const int32_t *nblocks, const float4 *box,
                                                                   PanelsDev P, double *Snear)
 {
-    __shared__ float4 s_cq[IN_WARPS][IF_Q];
+    __shared__ float4 s_cq[IN_WARPS][3][IF_Q];
     __shared__ float4 s_pt[IN_WARPS][IF_NPT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = blockIdx.x * IN_WARPS + warp;
@@ -721,7 +754,6 @@ __global__ void __launch_bounds__(IN_WARPS * 32) infl_near_kernel(const float4 *
         __syncwarp();
     }
     const float4 *pt = s_pt[warp];
-    float4 *cq = s_cq[warp];
     const int nb = *nblocks;
     double acc = 0.0;
     for (int bb0 = 0; bb0 < nb; bb0 += 32) {
@@ -733,21 +765,20 @@ __global__ void __launch_bounds__(IN_WARPS * 32) infl_near_kernel(const float4 *
             bal &= bal - 1;
             const int2 bl = blocks[b];
             float v[4] = {0.f, 0.f, 0.f, 0.f};
-            int qn = 0;
+            int qn[3] = {0, 0, 0};
             for (int l0 = 0; l0 < bl.y; l0 += 32) {
                 const int l = l0 + lane;
                 const float4 x = l < bl.y ? xs[bl.x + l] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float ex = x.x - ca.x, ey = x.y - ca.y, ez = x.z - ca.z;
                 const float fx = ex - cl.x, fy = ey - cl.y, fz = ez - cl.z;
                 const int nq = l < bl.y ? fld_tier(fmaf(fz, fz, fmaf(fy, fy, fx * fx)), g0.w) : -1;
-                if (nq > 0) {
+                if (nq > 0 && nq <= 7) {
                     float sp = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
                     const int k0 = if_tier_base(nq);
                     for (int k = 0; k < nq; ++k) {
                         const float4 o = pt[k0 + k];
                         const float dx = ex - o.x, dy = ey - o.y, dz = ez - o.z;
                         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        if (!(r2 > 0.f)) continue;
                         const float inv = rsq(r2);
                         const float w = o.w * inv;
                         const float w3 = w * inv * inv;
@@ -757,22 +788,28 @@ __global__ void __launch_bounds__(IN_WARPS * 32) infl_near_kernel(const float4 *
                     v[0] = fmaf(x.w, sp, v[0]); v[1] = fmaf(x.w, sx, v[1]);
                     v[2] = fmaf(x.w, sy, v[2]); v[3] = fmaf(x.w, sz, v[3]);
                 }
-                const unsigned cb = __ballot_sync(0xffffffffu, nq == 0);
-                if (cb) {
-                    if (nq == 0) cq[qn + __popc(cb & ((1u << lane) - 1u))] = x;
-                    qn += __popc(cb);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const unsigned cb = __ballot_sync(0xffffffffu, nq == (c == 0 ? 28 : c == 1 ? 112 : 0));
+                    if (!cb) continue;
+                    float4 *cq = s_cq[warp][c];
+                    if ((cb >> lane) & 1u) cq[qn[c] + __popc(cb & ((1u << lane) - 1u))] = x;
+                    qn[c] += __popc(cb);
                     __syncwarp();
-                    if (qn >= 32) {
-                        if_closed(P, j, cq, 32, v);
-                        const float4 tq = lane < qn - 32 ? cq[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (qn[c] >= 32) {
+                        if (c == 2) if_closed(P, j, cq, 32, v);
+                        else if_quad_flush(cq, 32, ca, pt, c == 0 ? 11 : 39, c == 0 ? 28 : 112, v);
+                        const float4 tq = lane < qn[c] - 32 ? cq[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
                         __syncwarp();
-                        if (lane < qn - 32) cq[lane] = tq;
-                        qn -= 32;
+                        if (lane < qn[c] - 32) cq[lane] = tq;
+                        qn[c] -= 32;
                         __syncwarp();
                     }
                 }
             }
-            if (qn > 0) if_closed(P, j, cq, qn, v);
+            if (qn[0] > 0) if_quad_flush(s_cq[warp][0], qn[0], ca, pt, 11, 28, v);
+            if (qn[1] > 0) if_quad_flush(s_cq[warp][1], qn[1], ca, pt, 39, 112, v);
+            if (qn[2] > 0) if_closed(P, j, s_cq[warp][2], qn[2], v);
             acc += (double)if_reduce4(v);
         }
     }
