@@ -28,6 +28,7 @@
 #include "obem_internal.cuh"
 
 #define LU_NB 64
+#define TS_R 128               // rows of a block row of the one-launch triangular solves
 #define BARRIER_SPIN_LIMIT (1ll << 24)
 
 // ------------------------------------------------------------------ closed form (FP64)
@@ -491,19 +492,57 @@ __global__ void rhs_kernel(const int *kind, const int *group, const double *gv, 
 }
 
 // r = b - A x (FP64 accumulation over the FP32 matrix), one warp per row
-__global__ void residual_kernel(const float *A, const double *x, const double *b, double *r, int n)
+// x = xh + xl in two floats (xl: the rounding remainder of xh, so that
+// |x - xh - xl| <= 2^-48 |x|)
+__global__ void split_kernel(const double *x, float *xh, float *xl, int n)
 {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    const float *a = A + (size_t)row * n;
-    double s = 0.0;
-    for (int j = lane; j < n; j += 32) s += (double)a[j] * x[j];
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) r[row] = b[row] - s;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float h = (float)x[i];
+    xh[i] = h;
+    xl[i] = (float)(x[i] - (double)h);
 }
 
-// out = [max|r|, max|x|, max|b|]
+// r = b - A x in FP64 without FP64 products: a warp per row; each product
+// a xh is split exactly (FMA) into its float value p and error e, p goes to
+// a per-lane two-sum (s, c) and e + a xl to c; the lanes' s + c are added
+// in FP64.  The result differs from the FP64 dot product by a few units of
+// 2^-48 of sum |a x|.
+__device__ __forceinline__ void df_acc(float &s, float &c, float a, float h, float l)
+{
+    const float p = __fmul_rn(a, h);
+    const float e = __fmaf_rn(a, h, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(a, l, e)));
+    s = t;
+}
+__global__ void __launch_bounds__(256) residual_kernel(const float *A, const float *xh, const float *xl,
+                                                       const double *b, double *r, int n)
+{
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float *a = A + (size_t)row * n;
+    float s = 0.f, c = 0.f;
+    int j = lane;
+    for (; j + 32 * 7 < n; j += 32 * 8) {
+        float av[8], hv[8], lv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            av[u] = __ldcs(a + j + 32 * u);
+            hv[u] = xh[j + 32 * u];
+            lv[u] = xl[j + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) df_acc(s, c, av[u], hv[u], lv[u]);
+    }
+    for (; j < n; j += 32) df_acc(s, c, a[j], xh[j], xl[j]);
+    double v = (double)s + (double)c;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) r[row] = b[row] - v;
+}
 __global__ void norms_kernel(const double *r, const double *x, const double *b, int n, double *out)
 {
     __shared__ double s[3][256];
@@ -590,6 +629,163 @@ __global__ void to_float_kernel(const double *x, float *a, float *b, int n)
     float v = (float)x[i];
     a[i] = v;
     if (b) b[i] = v;
+}
+
+// ------------------------------------------------------------------ one-launch triangular solves
+// Forward (unit lower L) or backward (upper U) substitution with the factors
+// in one launch.  Block row i of TS_R rows is taken by the thread block that
+// draws ticket i (in dependency order: i = 0 is the first block row of L,
+// the last of U), so every block row it depends on belongs to a thread block
+// that started before it, whatever the scheduling.  Each warp owns 8 rows
+// and runs over the solved blocks of y in dependency order: the loads of its
+// rows of the factor do not wait, the loads of y wait for that block's flag
+// to show the launch's epoch.  The block row then solves its diagonal block
+// (one warp) and publishes its y values and flag.  A wait on a flag is
+// bounded (TS_WAIT_NS): one that runs out records OBEM_ERR_TIMEOUT and goes
+// on, so that the launch always ends.
+#define TS_WAIT_NS 2000000000ull
+#define TS_SMEM (sizeof(float) * (TS_R * (TS_R + 1) + TS_R))
+#define TS_INV_SMEM (sizeof(float) * 2 * TS_R * (TS_R + 1))
+
+__device__ __forceinline__ unsigned long long ts_now()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ts_ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ts_st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct TsArgs {
+    const float *LU;
+    const float *dinv;  // inverses of the diagonal blocks (inv_diag_kernel)
+    float *y;           // right-hand side in, solution out
+    int n, lower, epoch;
+    int *flags;         // [nbk] epoch of the last launch that solved the block row
+    int *ticket;        // zero before the launch
+    int *err;
+};
+
+// Inverses of the diagonal blocks (TS_R x TS_R) of the unit lower factor L
+// (blockIdx.y = 0) and of the upper factor U (blockIdx.y = 1): thread c
+// solves for column c of the inverse by substitution; rows and columns past
+// the matrix are zero.
+#define TS_LD (TS_R + 1)
+__global__ void __launch_bounds__(TS_R) inv_diag_kernel(const float *LU, int n, float *dinv)
+{
+    extern __shared__ float ts_sm[];
+    float *T = ts_sm, *X = ts_sm + TS_R * TS_LD;
+    const int blk = blockIdx.x, upper = blockIdx.y, c = threadIdx.x;
+    const int r0 = blk * TS_R, rows = min(TS_R, n - r0);
+    for (int e = c; e < TS_R * TS_R; e += TS_R) {
+        const int i = e / TS_R, k = e % TS_R;
+        T[i * TS_LD + k] = (i < rows && k < rows) ? LU[(size_t)(r0 + i) * n + r0 + k] : 0.f;
+    }
+    __syncthreads();
+    if (!upper) {
+        for (int i = 0; i < TS_R; ++i) {
+            float v = (i == c && i < rows) ? 1.f : 0.f;
+            for (int k = c; k < i; ++k) v = fmaf(-T[i * TS_LD + k], X[k * TS_LD + c], v);
+            X[i * TS_LD + c] = (i < rows && c < rows) ? v : 0.f;
+        }
+    } else {
+        for (int i = TS_R - 1; i >= 0; --i) {
+            float v = (i == c && i < rows) ? 1.f : 0.f;
+            for (int k = i + 1; k <= c; ++k) v = fmaf(-T[i * TS_LD + k], X[k * TS_LD + c], v);
+            X[i * TS_LD + c] = (i < rows && c < rows) ? v / T[i * TS_LD + i] : 0.f;
+        }
+    }
+    __syncthreads();
+    float *D = dinv + (size_t)(2 * blk + upper) * TS_R * TS_R;
+    for (int e = c; e < TS_R * TS_R; e += TS_R) D[e] = X[(e / TS_R) * TS_LD + e % TS_R];
+}
+
+__global__ void __launch_bounds__(256) trsv_chain_kernel(TsArgs a)
+{
+    extern __shared__ float ts_sm[];
+    float *D = ts_sm;                        // [TS_R][TS_LD] inverse of the diagonal block
+    float *s_b = ts_sm + TS_R * TS_LD;       // [TS_R] right-hand side minus the solved part
+    __shared__ int s_t;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    constexpr int RW = TS_R / 8;             // rows per warp
+    const int n = a.n, nbk = (n + TS_R - 1) / TS_R;
+    if (tid == 0) s_t = atomicAdd(a.ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    const int blk = a.lower ? t : nbk - 1 - t;
+    const int r0 = blk * TS_R, rows = min(TS_R, n - r0);
+    {
+        const float *g = a.dinv + (size_t)(2 * blk + (a.lower ? 0 : 1)) * TS_R * TS_R;
+        for (int e = tid; e < TS_R * TS_R; e += 256) D[(e / TS_R) * TS_LD + e % TS_R] = g[e];
+    }
+    float acc[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) acc[r] = 0.f;
+    int ready = 0;          // dependency steps this warp knows to be solved
+    for (int st = 0; st < t; ++st) {
+        const int j = a.lower ? st : nbk - 1 - st;
+        const int c0 = j * TS_R, cols = min(TS_R, n - c0);
+        if (st >= ready) {
+            // flags of steps st .. st + 31, until step st is solved
+            const unsigned long long t0 = ts_now();
+            for (unsigned it = 0;; ++it) {
+                const int q = st + lane;
+                const int f = q < t ? ts_ld_acquire(a.flags + (a.lower ? q : nbk - 1 - q)) : 0;
+                const unsigned ok = __ballot_sync(0xffffffffu, q < t && f == a.epoch);
+                if (ok & 1u) {
+                    ready = st + (~ok ? __ffs(~ok) - 1 : 32);
+                    break;
+                }
+                if ((it & 63u) == 63u && ts_now() - t0 > TS_WAIT_NS) {
+                    if (lane == 0) atomicExch(a.err, OBEM_ERR_TIMEOUT);
+                    ready = st + 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int h = 0; h < TS_R; h += 64) {
+            float l0[RW], l1[RW];
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int row = RW * w + r;
+                const float *arow = a.LU + (size_t)(r0 + row) * n + c0 + h;
+                l0[r] = (row < rows && h + lane < cols) ? arow[lane] : 0.f;
+                l1[r] = (row < rows && h + lane + 32 < cols) ? arow[lane + 32] : 0.f;
+            }
+            const float y0 = h + lane < cols ? __ldcg(a.y + c0 + h + lane) : 0.f;
+            const float y1 = h + lane + 32 < cols ? __ldcg(a.y + c0 + h + lane + 32) : 0.f;
+#pragma unroll
+            for (int r = 0; r < RW; ++r) acc[r] = fmaf(l0[r], y0, fmaf(l1[r], y1, acc[r]));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        float v = acc[r];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int row = RW * w + r;
+        if (lane == 0) s_b[row] = row < rows ? a.y[r0 + row] - v : 0.f;
+    }
+    __syncthreads();
+    if (tid < rows) {
+        const float *d = D + tid * TS_LD;
+        float v = 0.f;
+        for (int k = 0; k < rows; ++k) v = fmaf(d[k], s_b[k], v);
+        a.y[r0 + tid] = v;
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) ts_st_release(a.flags + blk, a.epoch);
 }
 
 // ------------------------------------------------------------------ host drivers
@@ -741,11 +937,12 @@ static int alloc_system(obem_ctx *c, int n)
 {
     if (c->d_A && c->nsys_alloc == n) return OBEM_OK;
     void *bufs[] = {c->d_A, c->d_LU, c->d_piv, c->d_rowscale, c->d_work64, c->d_work32, c->d_flag, c->d_panel,
-                    c->d_perm};
+                    c->d_perm, c->d_trsv, c->d_dinv};
     for (void *q : bufs)
         if (q) cudaFree(q);
     c->d_A = c->d_LU = NULL;
-    c->d_piv = c->d_flag = c->d_perm = NULL;
+    c->d_piv = c->d_flag = c->d_perm = c->d_trsv = NULL;
+    c->d_dinv = NULL;
     c->d_rowscale = c->d_work64 = NULL;
     c->d_work32 = c->d_panel = NULL;
     c->nsys_alloc = 0;
@@ -759,6 +956,10 @@ static int alloc_system(obem_ctx *c, int n)
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_flag, sizeof(int) * 8));
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_panel, sizeof(float) * PAN_SCRATCH_FLOATS));
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_perm, sizeof(int) * n));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_trsv, sizeof(int) * ((size_t)n / TS_R + 16)));
+    OBEM_CUDA(c, cudaMemset(c->d_trsv, 0, sizeof(int) * ((size_t)n / TS_R + 16)));
+    c->trsv_epoch = 0;
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_dinv, sizeof(float) * 2 * TS_R * TS_R * (size_t)((n + TS_R - 1) / TS_R)));
     c->nsys_alloc = n;
     return OBEM_OK;
 }
@@ -879,25 +1080,48 @@ static int factor_system(obem_ctx *c, int precision, cudaStream_t s)
             if (piv[i] != i) { const int t = perm[i]; perm[i] = perm[piv[i]]; perm[piv[i]] = t; }
         OBEM_CUDA(c, cudaMemcpy(c->d_perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     }
+    // inverses of the diagonal blocks for the one-launch substitutions
+    {
+        static bool attr = false;
+        if (!attr) {
+            OBEM_CUDA(c, cudaFuncSetAttribute(inv_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)TS_INV_SMEM));
+            OBEM_CUDA(c, cudaFuncSetAttribute(trsv_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)TS_SMEM));
+            attr = true;
+        }
+        inv_diag_kernel<<<dim3((n + TS_R - 1) / TS_R, 2), TS_R, TS_INV_SMEM, s>>>(c->d_LU, n, c->d_dinv);
+        OBEM_LAUNCH(c);
+    }
     c->factored = 1;
     return OBEM_OK;
 }
 
+// y <- U^-1 L^-1 y with the stored factors: two one-launch substitutions.
+// A flag wait that ran out is reported as OBEM_ERR_TIMEOUT after the launch.
 static int lu_solve(obem_ctx *c, float *y, cudaStream_t s)
 {
-    const int n = c->nsys;
-    for (int k = 0; k < n; k += LU_NB) {
-        const int kb = n - k < LU_NB ? n - k : LU_NB;
-        trsv_block_kernel<<<1, 256, 0, s>>>(c->d_LU, y, n, k, kb, 1);
-        if (k + kb < n)
-            trsv_update_kernel<<<(n - k - kb + 7) / 8, 256, 0, s>>>(c->d_LU, y, n, k, kb, k + kb, n);
+    const int n = c->nsys, nbk = (n + TS_R - 1) / TS_R;
+    int *ticket = c->d_trsv + nbk, *err = ticket + 2;
+    OBEM_CUDA(c, cudaMemsetAsync(ticket, 0, sizeof(int) * 3, s));
+    for (int lower = 1; lower >= 0; --lower) {
+        TsArgs a;
+        a.LU = c->d_LU;
+        a.dinv = c->d_dinv;
+        a.y = y;
+        a.n = n;
+        a.lower = lower;
+        a.epoch = ++c->trsv_epoch;
+        a.flags = c->d_trsv;
+        a.ticket = ticket + (lower ? 0 : 1);
+        a.err = err;
+        trsv_chain_kernel<<<nbk, 256, TS_SMEM, s>>>(a);
+        OBEM_LAUNCH(c);
     }
-    for (int k = ((n - 1) / LU_NB) * LU_NB; k >= 0; k -= LU_NB) {
-        const int kb = n - k < LU_NB ? n - k : LU_NB;
-        trsv_block_kernel<<<1, 256, 0, s>>>(c->d_LU, y, n, k, kb, 0);
-        if (k > 0) trsv_update_kernel<<<(k + 7) / 8, 256, 0, s>>>(c->d_LU, y, n, k, kb, 0, k);
-    }
-    OBEM_LAUNCH(c);
+    int h = 0;
+    OBEM_CUDA(c, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    OBEM_CUDA(c, cudaStreamSynchronize(s));
+    if (h != 0) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU solve: a wait for a solved block timed out");
     return OBEM_OK;
 }
 
@@ -917,7 +1141,8 @@ static int refine(obem_ctx *c, int &it, int &status, double &be, cudaStream_t s)
     status = OBEM_ERR_NOT_CONVERGED;
     const int max_it = 30;
     for (; it <= max_it; ++it) {
-        residual_kernel<<<(n + 7) / 8, 256, 0, s>>>(c->d_A, x, b, r, n);
+        split_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, y + n, n);
+        residual_kernel<<<(n + 7) / 8, 256, 0, s>>>(c->d_A, y, y + n, b, r, n);
         norms_kernel<<<1, 256, 0, s>>>(r, x, b, n, nrm);
         OBEM_LAUNCH(c);
         double h[3];

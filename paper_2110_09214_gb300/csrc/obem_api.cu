@@ -35,7 +35,9 @@ static void free_mesh(obem_ctx *c)
     obem_tc_free(c);
     free_dev(c->d_A); free_dev(c->d_LU); free_dev(c->d_piv); free_dev(c->d_rowscale);
     free_dev(c->d_work64); free_dev(c->d_work32); free_dev(c->d_flag); free_dev(c->d_sigma);
-    free_dev(c->d_panel); free_dev(c->d_perm); free_dev(c->d_infl); free_dev(c->d_epsd);
+    free_dev(c->d_panel); free_dev(c->d_perm); free_dev(c->d_infl); free_dev(c->d_epsd); free_dev(c->d_trsv); free_dev(c->d_dinv);
+    c->d_trsv = NULL;
+    c->d_dinv = NULL;
     c->d_infl = c->d_epsd = NULL;
     c->d_panel = NULL;
     c->d_perm = NULL;

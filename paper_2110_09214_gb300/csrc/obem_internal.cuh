@@ -150,6 +150,9 @@ struct obem_ctx {
     float *d_work32;     // 2 * np floats
     int *d_flag;         // device status of the LU (singular / timeout)
     float *d_panel;      // exchange buffers of the pivoting panel kernel
+    int *d_trsv;         // one-launch triangular solves: block flags, ticket counter, status
+    int trsv_epoch;      // flag value of the last triangular-solve launch
+    float *d_dinv;       // inverses of the diagonal blocks of L and U, [nbk][2][TS_R][TS_R]
     int *d_perm;         // row permutation of the factorisation: (P b)[i] = b[d_perm[i]]
     int factored;
     double factor_ms;
