@@ -570,49 +570,7 @@ __global__ void permute_kernel(const double *r, float *y, const int *perm, int n
     y[i] = (float)(r[perm[i]] / sc);
 }
 
-// Forward (lower = 1, unit diagonal) or backward (lower = 0) substitution on
-// the diagonal block [k, k+kb) of the factors: one warp, lane l holding rows
-// l and l + 32, the block in shared memory; column q's solved value is
-// broadcast with a shuffle.
-__global__ void __launch_bounds__(256) trsv_block_kernel(const float *LU, float *y, int n, int k, int kb, int lower)
-{
-    __shared__ float T[LU_NB][LU_NB + 1];
-    load_block(T, LU, n, k, k, kb, false);
-    __syncthreads();
-    if (threadIdx.x >= 32) return;
-    const int l = threadIdx.x;
-    const bool h0 = l < kb, h1 = l + 32 < kb;
-    float y0 = h0 ? y[k + l] : 0.f, y1 = h1 ? y[k + l + 32] : 0.f;
-    if (lower) {
-        for (int q = 0; q < kb; ++q) {
-            const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31);
-            if (h0 && l > q) y0 = fmaf(-T[l][q], yq, y0);
-            if (h1 && l + 32 > q) y1 = fmaf(-T[l + 32][q], yq, y1);
-        }
-    } else {
-        for (int q = kb - 1; q >= 0; --q) {
-            const float yq = __shfl_sync(0xffffffffu, q < 32 ? y0 : y1, q & 31) / T[q][q];
-            if (l == (q & 31)) { if (q < 32) y0 = yq; else y1 = yq; }
-            if (h0 && l < q) y0 = fmaf(-T[l][q], yq, y0);
-            if (h1 && l + 32 < q) y1 = fmaf(-T[l + 32][q], yq, y1);
-        }
-    }
-    if (h0) y[k + l] = y0;
-    if (h1) y[k + l + 32] = y1;
-}
 
-// y[rows] -= LU[rows, k:k+kb] y[k:k+kb], one warp per row; rows = [r0, r1)
-__global__ void trsv_update_kernel(const float *LU, float *y, int n, int k, int kb, int r0, int r1)
-{
-    int row = r0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    int lane = threadIdx.x & 31;
-    if (row >= r1) return;
-    const float *a = LU + (size_t)row * n + k;
-    float s = 0.f;
-    for (int q = lane; q < kb; q += 32) s = fmaf(a[q], y[k + q], s);
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[row] -= s;
-}
 
 __global__ void axpy_kernel(double *x, const float *d, const double *norms, int n)
 {
@@ -636,13 +594,14 @@ __global__ void to_float_kernel(const double *x, float *a, float *b, int n)
 // in one launch.  Block row i of TS_R rows is taken by the thread block that
 // draws ticket i (in dependency order: i = 0 is the first block row of L,
 // the last of U), so every block row it depends on belongs to a thread block
-// that started before it, whatever the scheduling.  Each warp owns 8 rows
-// and runs over the solved blocks of y in dependency order: the loads of its
-// rows of the factor do not wait, the loads of y wait for that block's flag
-// to show the launch's epoch.  The block row then solves its diagonal block
-// (one warp) and publishes its y values and flag.  A wait on a flag is
-// bounded (TS_WAIT_NS): one that runs out records OBEM_ERR_TIMEOUT and goes
-// on, so that the launch always ends.
+// that started before it, whatever the scheduling.  Each warp owns TS_R / 8
+// rows and runs over the solved blocks of y in dependency order; the loads
+// of y wait for that block's flag to show the launch's epoch.  The block row
+// then multiplies its right-hand side, less the solved part, by the inverse
+// of its diagonal block (computed once after the factorisation) and
+// publishes its y values and flag.  A wait on a flag is bounded
+// (TS_WAIT_NS): one that runs out records OBEM_ERR_TIMEOUT and goes on, so
+// that the launch always ends.
 #define TS_WAIT_NS 2000000000ull
 #define TS_SMEM (sizeof(float) * (TS_R * (TS_R + 1) + TS_R))
 #define TS_INV_SMEM (sizeof(float) * 2 * TS_R * (TS_R + 1))
@@ -782,6 +741,93 @@ __global__ void __launch_bounds__(256) trsv_chain_kernel(TsArgs a)
         float v = 0.f;
         for (int k = 0; k < rows; ++k) v = fmaf(d[k], s_b[k], v);
         a.y[r0 + tid] = v;
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) ts_st_release(a.flags + blk, a.epoch);
+}
+
+// The transposed substitutions of the adjoint solve, A^T x = b with
+// P A = L U: U^T (lower, forward; lower = 1) and L^T (unit upper, backward;
+// lower = 0) in one launch each, with the same tickets and flags.  Block row
+// i of U^T (L^T) is block column i of U (L): thread (c, half) sums column c
+// over every other row of each solved block j, whose y values warp 0 puts in
+// shared memory (double-buffered, one barrier per block); the diagonal block
+// uses the transposed inverse.
+#define TS_T_SMEM (sizeof(float) * (TS_R * (TS_R + 1) + 4 * TS_R))
+__global__ void __launch_bounds__(256) trsv_chain_t_kernel(TsArgs a)
+{
+    extern __shared__ float ts_sm[];
+    float *D = ts_sm;                        // [TS_R][TS_LD]
+    float *s_b = D + TS_R * TS_LD;           // [TS_R]
+    float *s_z = s_b + TS_R;                 // [2][TS_R]
+    float *s_h = s_z + 2 * TS_R;             // [TS_R]
+    __shared__ int s_t;
+    const int tid = threadIdx.x, lane = tid & 31, c = tid & (TS_R - 1), half = tid / TS_R;
+    const int n = a.n, nbk = (n + TS_R - 1) / TS_R;
+    if (tid == 0) s_t = atomicAdd(a.ticket, 1);
+    __syncthreads();
+    const int t = s_t;
+    const int blk = a.lower ? t : nbk - 1 - t;
+    const int i0 = blk * TS_R, ni = min(TS_R, n - i0);
+    {
+        const float *g = a.dinv + (size_t)(2 * blk + (a.lower ? 1 : 0)) * TS_R * TS_R;
+        for (int e = tid; e < TS_R * TS_R; e += 256) D[(e / TS_R) * TS_LD + e % TS_R] = g[e];
+    }
+    float acc = 0.f;
+    int ready = 0;
+    for (int st = 0; st < t; ++st) {
+        const int j = a.lower ? st : nbk - 1 - st;
+        const int j0 = j * TS_R, nj = min(TS_R, n - j0);
+        float *z = s_z + (st & 1) * TS_R;
+        if (tid < 32) {
+            if (st >= ready) {
+                const unsigned long long t0 = ts_now();
+                for (unsigned it = 0;; ++it) {
+                    const int q = st + lane;
+                    const int f = q < t ? ts_ld_acquire(a.flags + (a.lower ? q : nbk - 1 - q)) : 0;
+                    const unsigned ok = __ballot_sync(0xffffffffu, q < t && f == a.epoch);
+                    if (ok & 1u) {
+                        ready = st + (~ok ? __ffs(~ok) - 1 : 32);
+                        break;
+                    }
+                    if ((it & 63u) == 63u && ts_now() - t0 > TS_WAIT_NS) {
+                        if (lane == 0) atomicExch(a.err, OBEM_ERR_TIMEOUT);
+                        ready = st + 1;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int q = 0; q < TS_R / 32; ++q) {
+                const int r = lane + 32 * q;
+                z[r] = r < nj ? __ldcg(a.y + j0 + r) : 0.f;
+            }
+        }
+        __syncthreads();
+        if (c < ni) {
+            const float *col = a.LU + (size_t)j0 * n + i0 + c;
+            int r = half;
+            for (; r + 14 < nj; r += 16) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = col[(size_t)(r + 2 * u) * n];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc = fmaf(v[u], z[r + 2 * u], acc);
+            }
+            for (; r < nj; r += 2) acc = fmaf(col[(size_t)r * n], z[r], acc);
+        }
+    }
+    if (half == 1) s_h[c] = acc;
+    __syncthreads();
+    if (half == 0) s_b[c] = c < ni ? a.y[i0 + c] - (acc + s_h[c]) : 0.f;
+    __syncthreads();
+    if (tid < ni) {
+        float v = 0.f;
+        for (int k = 0; k < ni; ++k) v = fmaf(D[k * TS_LD + tid], s_b[k], v);
+        a.y[i0 + tid] = v;
         __threadfence();
     }
     __syncthreads();
@@ -1259,23 +1305,24 @@ int obem_solve_dense_rhs(obem_ctx *c, const double *bin, double *xout, obem_solv
 #define ADJ_SPLIT 16           // row ranges of the transposed residual
 
 // part[s][j] = sum over rows i of range s of At[i][j] x[i]; one thread per column
-__global__ void residual_t_part_kernel(const float *A, const double *x, double *part, int n)
+__global__ void residual_t_part_kernel(const float *A, const float *xh, const float *xl, double *part, int n)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = blockIdx.y;
     const int i0 = (int)((long long)n * s / ADJ_SPLIT), i1 = (int)((long long)n * (s + 1) / ADJ_SPLIT);
     if (j >= n) return;
-    double a0 = 0.0, a1 = 0.0;
+    float sm = 0.f, cm = 0.f;
     int i = i0;
-    for (; i + 1 < i1; i += 2) {
-        a0 += (double)A[(size_t)i * n + j] * x[i];
-        a1 += (double)A[(size_t)(i + 1) * n + j] * x[i + 1];
+    for (; i + 7 < i1; i += 8) {
+        float av[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) av[u] = __ldcs(A + (size_t)(i + u) * n + j);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) df_acc(sm, cm, av[u], xh[i + u], xl[i + u]);
     }
-    if (i < i1) a0 += (double)A[(size_t)i * n + j] * x[i];
-    part[(size_t)s * n + j] = a0 + a1;
+    for (; i < i1; ++i) df_acc(sm, cm, A[(size_t)i * n + j], xh[i], xl[i]);
+    part[(size_t)s * n + j] = (double)sm + (double)cm;
 }
-
-// r = b - sum_s part[s]  (ranges added in order)
 __global__ void residual_t_fold_kernel(const double *part, const double *b, double *r, int n)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1336,62 +1383,38 @@ __global__ void axpy_unpermute_kernel(double *x, const float *y, const int *perm
     x[perm[i]] += (double)y[i] * sc;
 }
 
-// Diagonal block [k, k+kb) of a transposed triangular solve: upper_unit = 0
-// solves with U^T (lower, U's diagonal, forward), upper_unit = 1 with L^T
-// (upper, unit diagonal, backward).  T holds the transposed block.
-__global__ void trsv_t_block_kernel(const float *LU, float *y, int n, int k, int kb, int upper_unit)
-{
-    __shared__ float T[LU_NB][LU_NB + 1];
-    __shared__ float yb[LU_NB];
-    load_block(T, LU, n, k, k, kb, true);                    // T = the block transposed
-    const int r = threadIdx.x;
-    if (r < kb) yb[r] = y[k + r];
-    __syncthreads();
-    if (!upper_unit) {
-        for (int q = 0; q < kb; ++q) {
-            if (r == q) yb[q] = yb[q] / T[q][q];
-            __syncthreads();
-            if (r > q && r < kb) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
-            __syncthreads();
-        }
-    } else {
-        for (int q = kb - 1; q >= 0; --q) {
-            if (r < q) yb[r] = fmaf(-T[r][q], yb[q], yb[r]);
-            __syncthreads();
-        }
-    }
-    if (r < kb) y[k + r] = yb[r];
-}
 
-// y[row] -= sum_q LU[k+q][row] y[k+q] for rows in [r0, r1); one thread per row
-// (the factors' rows k..k+kb are read along their length: coalesced)
-__global__ void trsv_t_update_kernel(const float *LU, float *y, int n, int k, int kb, int r0, int r1)
-{
-    __shared__ float yk[LU_NB];
-    if (threadIdx.x < kb) yk[threadIdx.x] = y[k + threadIdx.x];
-    __syncthreads();
-    const int row = r0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= r1) return;
-    float s = 0.f;
-    for (int q = 0; q < kb; ++q) s = fmaf(LU[(size_t)(k + q) * n + row], yk[q], s);
-    y[row] -= s;
-}
 
+// y <- L^-T U^-T y with the stored factors (the adjoint's substitutions)
 static int lu_solve_t(obem_ctx *c, float *y, cudaStream_t s)
 {
-    const int n = c->nsys;
-    for (int k = 0; k < n; k += LU_NB) {
-        const int kb = n - k < LU_NB ? n - k : LU_NB;
-        trsv_t_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 0);
-        if (k + kb < n)
-            trsv_t_update_kernel<<<(n - k - kb + 255) / 256, 256, 0, s>>>(c->d_LU, y, n, k, kb, k + kb, n);
+    const int n = c->nsys, nbk = (n + TS_R - 1) / TS_R;
+    int *ticket = c->d_trsv + nbk, *err = ticket + 2;
+    static bool attr = false;
+    if (!attr) {
+        OBEM_CUDA(c, cudaFuncSetAttribute(trsv_chain_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)TS_T_SMEM));
+        attr = true;
     }
-    for (int k = ((n - 1) / LU_NB) * LU_NB; k >= 0; k -= LU_NB) {
-        const int kb = n - k < LU_NB ? n - k : LU_NB;
-        trsv_t_block_kernel<<<1, LU_NB, 0, s>>>(c->d_LU, y, n, k, kb, 1);
-        if (k > 0) trsv_t_update_kernel<<<(k + 255) / 256, 256, 0, s>>>(c->d_LU, y, n, k, kb, 0, k);
+    OBEM_CUDA(c, cudaMemsetAsync(ticket, 0, sizeof(int) * 3, s));
+    for (int lower = 1; lower >= 0; --lower) {
+        TsArgs a;
+        a.LU = c->d_LU;
+        a.dinv = c->d_dinv;
+        a.y = y;
+        a.n = n;
+        a.lower = lower;
+        a.epoch = ++c->trsv_epoch;
+        a.flags = c->d_trsv;
+        a.ticket = ticket + (lower ? 0 : 1);
+        a.err = err;
+        trsv_chain_t_kernel<<<nbk, 256, TS_T_SMEM, s>>>(a);
+        OBEM_LAUNCH(c);
     }
-    OBEM_LAUNCH(c);
+    int h = 0;
+    OBEM_CUDA(c, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    OBEM_CUDA(c, cudaStreamSynchronize(s));
+    if (h != 0) return obem_fail(c, OBEM_ERR_TIMEOUT, "adjoint solve: a wait for a solved block timed out");
     return OBEM_OK;
 }
 
@@ -1424,7 +1447,8 @@ int obem_solve_adjoint(obem_ctx *c, const float *g, double *dL_dgv, float *dL_db
     ADJ_CUDA(cudaGetLastError());
     ADJ_CUDA(cudaMemcpyAsync(&a1, col + n, sizeof(double), cudaMemcpyDeviceToHost, s));
     for (; it <= 30; ++it) {
-        residual_t_part_kernel<<<dim3((n + 255) / 256, ADJ_SPLIT), 256, 0, s>>>(c->d_A, x, part, n);
+        split_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, y, y + n, n);
+        residual_t_part_kernel<<<dim3((n + 255) / 256, ADJ_SPLIT), 256, 0, s>>>(c->d_A, y, y + n, part, n);
         residual_t_fold_kernel<<<(n + 255) / 256, 256, 0, s>>>(part, b, r, n);
         norms_kernel<<<1, 256, 0, s>>>(r, x, b, n, nrm);
         ADJ_CUDA(cudaGetLastError());
