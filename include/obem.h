@@ -434,6 +434,20 @@ int obem_tc_gemm(obem_ctx *ctx, float *C, int64_t ldc, const float *A, int64_t l
  * OBEM_ERR_STATE otherwise.  Allocates a few bytes, synchronises `stream`. */
 int obem_selftest_wait_timeout(obem_ctx *ctx, obem_stream stream);
 
+/* Failure-detection self-tests of the library's other bounded device waits
+ * (no passage in the paper).  which = 0: the LU panel's grid barrier, as
+ * obem_selftest_wait_timeout.  which = 1: the flag wait of the one-launch
+ * triangular substitutions of obem_bem_solve: one thread block waits for a
+ * block row that no block solves (needs a factored system of at least 256
+ * cells).  which = 2: the bulk-copy wait of obem_influence_rhs's far pass:
+ * every copy's barrier expects 16 bytes more than the copy brings (needs a
+ * mesh; the cells' centroids serve as charges).  Each wait gives up after 2 s,
+ * records OBEM_ERR_TIMEOUT in a device status word and the kernel returns,
+ * leaving the context usable.  Returns OBEM_OK when that status was read
+ * back, OBEM_ERR_STATE when it was not or the preconditions fail,
+ * OBEM_ERR_ARG for another `which`.  Synchronises `stream`. */
+int obem_selftest_waits(obem_ctx *ctx, int32_t which, obem_stream stream);
+
 /* Stage timing of obem_step, for measurement (not part of the method).
  * obem_profile(ctx, 1) starts recording CUDA events on the step's stream
  * around its stages (up to 256 steps are kept; older ones are dropped) and

@@ -448,9 +448,13 @@ __device__ __forceinline__ unsigned long long if_now()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ void if_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+// (expect: bytes + extra; extra > 0 only in the self-test, where the phase
+// then never completes)
+__device__ __forceinline__ void if_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                             uint32_t extra)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(if_smem(bar)), "r"(bytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(if_smem(bar)), "r"(bytes + extra)
+                 : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(if_smem(dst)), "l"((unsigned long long)src), "r"(bytes), "r"(if_smem(bar))
                  : "memory");
@@ -545,7 +549,7 @@ __device__ __forceinline__ uint32_t if_block_bytes(int2 bl)
 // points sit at 1e18 m with weight 0.
 __global__ void __launch_bounds__(IF_CT) infl_far_kernel(const float4 *xr, const int2 *blocks, const int32_t *nblocks,
                                                         const float4 *box, const int32_t *corder, PanelsDev P,
-                                                        double *Spart, int *err)
+                                                        double *Spart, int *err, uint32_t tx_extra)
 {
     __shared__ __align__(128) float4 s_x[2][2 * IF_BPAIRS];
     __shared__ float4 s_p[IF_CT * 7];
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(IF_CT) infl_far_kernel(const float4 *xr, const
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int q = 0; q < 2 && b0 + q < b1; ++q) {
             const int2 bl = blocks[b0 + q];
-            if_bulk_load(s_x[q], xr + 2 * (size_t)if_pair0(bl, b0 + q), if_block_bytes(bl), &s_bar[q]);
+            if_bulk_load(s_x[q], xr + 2 * (size_t)if_pair0(bl, b0 + q), if_block_bytes(bl), &s_bar[q], tx_extra);
         }
     }
     __syncthreads();
@@ -650,7 +654,7 @@ __global__ void __launch_bounds__(IF_CT) infl_far_kernel(const float4 *xr, const
             // every thread is done with this buffer: refill it two blocks ahead
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             const int2 bl = blocks[b + 2];
-            if_bulk_load(s_x[buf], xr + 2 * (size_t)if_pair0(bl, b + 2), if_block_bytes(bl), &s_bar[buf]);
+            if_bulk_load(s_x[buf], xr + 2 * (size_t)if_pair0(bl, b + 2), if_block_bytes(bl), &s_bar[buf], tx_extra);
         }
     }
     if (live) {
@@ -856,7 +860,8 @@ size_t obem_influence_scratch_bytes(int ns, int np)
 }
 
 int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const PanelsDev &P, double *S, const double *geo,
-                          const int *kind, const double *epsd, float *drhs, void *scratch, cudaStream_t s)
+                          const int *kind, const double *epsd, float *drhs, void *scratch, int selftest,
+                          cudaStream_t s)
 {
     if (P.np <= 0) return OBEM_OK;
     if (ns > 0) {
@@ -887,7 +892,7 @@ int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const Panels
         infl_blocks_kernel<<<(mb + 7) / 8, 256, 0, s>>>(src, perm, blocks, nblocks, xs, xr, box);
         OBEM_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), s));
         infl_far_kernel<<<dim3((P.np + IF_CT - 1) / IF_CT, IF_NCH), IF_CT, 0, s>>>(xr, blocks, nblocks, box, corder,
-                                                                                 P, Spart, err);
+                                                                                 P, Spart, err, selftest ? 16u : 0u);
         infl_near_kernel<<<(P.np + IN_WARPS - 1) / IN_WARPS, IN_WARPS * 32, 0, s>>>(xs, blocks, nblocks, box, P,
                                                                                    Snear);
         OBEM_LAUNCH(ctx);

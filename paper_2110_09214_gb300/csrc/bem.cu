@@ -1171,6 +1171,38 @@ static int lu_solve(obem_ctx *c, float *y, cudaStream_t s)
     return OBEM_OK;
 }
 
+// Failure-detection self-test of the substitutions' flag wait: one thread
+// block draws ticket 1 (the counter starts at 1) and waits for block row 0,
+// which no block solves; the wait runs out after TS_WAIT_NS and records
+// OBEM_ERR_TIMEOUT.  Needs the factors of a system of at least 2 TS_R rows.
+int obem_selftest_solve_wait(obem_ctx *c, cudaStream_t s)
+{
+    if (!c->factored || c->nsys < 2 * TS_R)
+        return obem_fail(c, OBEM_ERR_STATE, "wait self-test: needs the factors of a system of >= %d rows", 2 * TS_R);
+    const int n = c->nsys, nbk = (n + TS_R - 1) / TS_R;
+    int *ticket = c->d_trsv + nbk, *err = ticket + 2;
+    const int one = 1;
+    OBEM_CUDA(c, cudaMemsetAsync(ticket, 0, sizeof(int) * 3, s));
+    OBEM_CUDA(c, cudaMemcpyAsync(ticket, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    TsArgs a;
+    a.LU = c->d_LU;
+    a.dinv = c->d_dinv;
+    a.y = c->d_work32;
+    a.n = n;
+    a.lower = 1;
+    a.epoch = ++c->trsv_epoch;
+    a.flags = c->d_trsv;
+    a.ticket = ticket;
+    a.err = err;
+    trsv_chain_kernel<<<1, 256, TS_SMEM, s>>>(a);
+    OBEM_LAUNCH(c);
+    int h = 0;
+    OBEM_CUDA(c, cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    OBEM_CUDA(c, cudaStreamSynchronize(s));
+    if (h != OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_STATE, "wait self-test: status %d, expected a timeout", h);
+    return OBEM_OK;
+}
+
 // Iterative refinement of A x = b with the stored factors: b (device, FP64,
 // rows already equilibrated) in c->d_work64[0, n), x in [n, 2n); FP64
 // residuals r = b - A x from the FP32 equilibrated matrix, corrections from

@@ -786,13 +786,8 @@ extern "C" int obem_shard_commit(obem_ctx *c, const obem_state *st, const float 
                                     (cudaStream_t)stream);
 }
 
-extern "C" int obem_influence_rhs(obem_ctx *c, const float *sources, int32_t ns, float *drhs, obem_stream stream)
+static int influence(obem_ctx *c, const float *sources, int32_t ns, float *drhs, int selftest, cudaStream_t s)
 {
-    if (!c) return OBEM_ERR_ARG;
-    if (c->np < 1) return obem_fail(c, OBEM_ERR_STATE, "influence: no mesh loaded");
-    if (ns < 0 || (ns > 0 && !sources) || !drhs) return obem_fail(c, OBEM_ERR_ARG, "influence: bad arguments");
-    if ((uintptr_t)sources & 15) return obem_fail(c, OBEM_ERR_ARG, "influence: sources must be 16-byte aligned");
-    cudaStream_t s = (cudaStream_t)stream;
     if (!c->d_infl) {
         // first call: the per-cell sums and eps+ - eps- of the dielectric cells
         OBEM_CUDA(c, cudaMalloc((void **)&c->d_infl, sizeof(double) * 4 * (size_t)c->np));
@@ -814,7 +809,38 @@ extern "C" int obem_influence_rhs(obem_ctx *c, const float *sources, int32_t ns,
         c->ib_bytes = need;
     }
     return obem_launch_influence(c, (const float4 *)sources, ns, panels_of(c), c->d_infl, c->d_geo64, c->d_kind,
-                                 c->d_epsd, drhs, c->d_ib, s);
+                                 c->d_epsd, drhs, c->d_ib, selftest, s);
+}
+
+extern "C" int obem_influence_rhs(obem_ctx *c, const float *sources, int32_t ns, float *drhs, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    if (c->np < 1) return obem_fail(c, OBEM_ERR_STATE, "influence: no mesh loaded");
+    if (ns < 0 || (ns > 0 && !sources) || !drhs) return obem_fail(c, OBEM_ERR_ARG, "influence: bad arguments");
+    if ((uintptr_t)sources & 15) return obem_fail(c, OBEM_ERR_ARG, "influence: sources must be 16-byte aligned");
+    return influence(c, sources, ns, drhs, 0, (cudaStream_t)stream);
+}
+
+extern "C" int obem_selftest_waits(obem_ctx *c, int32_t which, obem_stream stream)
+{
+    if (!c) return OBEM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (which == 0) return obem_selftest_wait_timeout(c, stream);
+    if (which == 1) return obem_selftest_solve_wait(c, s);
+    if (which != 2) return obem_fail(c, OBEM_ERR_ARG, "wait self-test: no wait %d", which);
+    if (c->np < 1) return obem_fail(c, OBEM_ERR_STATE, "wait self-test: no mesh loaded");
+    // the cells' centroids (weights as charges) as sources: the values do not
+    // matter, every bulk copy's barrier expects 16 bytes more than it gets
+    float *drhs = NULL;
+    OBEM_CUDA(c, cudaMalloc((void **)&drhs, sizeof(float) * (size_t)c->np));
+    const int rc = influence(c, (const float *)panels_of(c).c_a, c->np, drhs, 1, s);
+    cudaFree(drhs);
+    if (rc == OBEM_ERR_TIMEOUT) {
+        c->err[0] = 0;
+        return OBEM_OK;
+    }
+    if (rc != OBEM_OK) return rc;
+    return obem_fail(c, OBEM_ERR_STATE, "wait self-test: the influence pass reported no timeout");
 }
 
 extern "C" int obem_surface_charge(obem_ctx *c, float *sigma_free, int64_t *counts, int32_t reset,

@@ -409,7 +409,9 @@ struct BwArgs {
 int obem_launch_backward(obem_ctx *ctx, const BwArgs &A, cudaStream_t s);
 size_t obem_influence_scratch_bytes(int ns, int np);
 int obem_launch_influence(obem_ctx *ctx, const float4 *src, int ns, const PanelsDev &P, double *S, const double *geo,
-                          const int *kind, const double *epsd, float *drhs, void *scratch, cudaStream_t s);
+                          const int *kind, const double *epsd, float *drhs, void *scratch, int selftest,
+                          cudaStream_t s);
+int obem_selftest_solve_wait(obem_ctx *c, cudaStream_t s);
 
 // step.cu
 int obem_launch_step(obem_ctx *ctx, const obem_state *st, const float4 *E, uint32_t step,

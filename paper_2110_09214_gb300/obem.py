@@ -100,6 +100,7 @@ def load():
     lib.obem_profile.argtypes = [P, I]
     lib.obem_alu_rates.argtypes = [P, P, P]
     lib.obem_selftest_wait_timeout.argtypes = [P, P]
+    lib.obem_selftest_waits.argtypes = [P, C.c_int32, P]
     L64 = C.c_int64
     lib.obem_tc_gemm.argtypes = [P, P, L64, P, L64, P, L64, I, I, I, P]
     lib.obem_tc_gemm.restype = C.c_int
@@ -358,6 +359,13 @@ def obem_selftest_wait_timeout(ctx, stream=None):
     include/obem.h): raises ObemError unless the wait ran out and reported
     OBEM_ERR_TIMEOUT."""
     _check(ctx, load().obem_selftest_wait_timeout(ctx, _stream(stream)))
+
+
+def obem_selftest_waits(ctx, which, stream=None):
+    """Failure-detection self-test of bounded device wait `which` (0: LU panel
+    barrier, 1: substitution flags, 2: influence bulk copies); raises unless
+    the wait reported OBEM_ERR_TIMEOUT (see include/obem.h)."""
+    _check(ctx, load().obem_selftest_waits(ctx, int(which), _stream(stream)))
 
 
 def obem_shard_field(ctx, state, sources, ns, self_off, E_out, stream=None):

@@ -152,3 +152,35 @@ def test_bounded_wait_reports_timeout_and_leaves_the_context_usable():
     A = oracle.assemble(mesh)
     b = oracle.bem_rhs(mesh)
     _check(mesh, sig, A, b, oracle.solve(A, b))
+
+
+def test_solve_and_influence_waits_report_timeout_and_leave_the_context_usable():
+    """Failure detection of the two other bounded device waits: the flag wait
+    of the one-launch substitutions (a block row that no block solves) and the
+    bulk-copy wait of the influence pass (barriers expecting more bytes than
+    arrive).  Each runs out, is reported as OBEM_ERR_TIMEOUT and read back;
+    the same context then solves the system and evaluates the influence of a
+    distant charge correctly."""
+    mesh = inputs.parallel_plates(1e-2, 1e-3, 8, 0.0, 100.0)
+    assert mesh.n >= 256
+    ctx = obem.obem_create(capacity=8, dt=1e-12)
+    try:
+        obem.obem_mesh_load(ctx, mesh)
+        obem.obem_bem_assemble(ctx, obem.OBEM_LU_FP32)
+        obem.obem_selftest_waits(ctx, 1)
+        obem.obem_selftest_waits(ctx, 2)
+        out = torch.empty(mesh.n, dtype=torch.float32, device="cuda")
+        rep = obem.obem_bem_solve(ctx, mesh.group_voltage, out)
+        assert rep["status"] == 0
+        sig = out.cpu().numpy().astype(np.float64)
+        src = torch.tensor([[5e-3, 5e-3, 0.5, 1.602176634e-19]], dtype=torch.float32, device="cuda")
+        drhs = torch.empty(mesh.n, dtype=torch.float32, device="cuda")
+        obem.obem_influence_rhs(ctx, src, drhs)
+        d = drhs.cpu().numpy().astype(np.float64)
+    finally:
+        obem.obem_destroy(ctx)
+    A = oracle.assemble(mesh)
+    b = oracle.bem_rhs(mesh)
+    _check(mesh, sig, A, b, oracle.solve(A, b))
+    ref = oracle.influence_rhs(mesh, np.array([[5e-3, 5e-3, 0.5, 1.602176634e-19]]))
+    assert np.abs(d - ref).max() <= 1e-5 * np.abs(ref).max()
