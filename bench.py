@@ -105,6 +105,8 @@ def _args():
     p.add_argument("--double-gem", action="store_true",
                    help="also time the double-GEM gradient and charging-up workload (~120k cells)")
     p.add_argument("--double-gem-only", action="store_true")
+    p.add_argument("--lu-dense", type=int, default=0,
+                   help="only factorise and solve a synthetic dense system of this order (BF16 LU + refinement)")
     p.add_argument("--no-cell-groups", dest="cell_groups", action="store_false",
                    help="far cells by the per-cell tiers only (default: distant groups of 32 cells as "
                         "fitted equivalent charges, OBEM_STEP_CELL_GROUPS)")
@@ -865,6 +867,40 @@ def dynamic_resolve_timing(ctx, mesh, pos_q, dev, reps=2):
             "resolve_backward_error": rep["backward_error"]}
 
 
+def dense_lu_timing(n, dev, precision="bf16"):
+    """The factorisation and refined solve alone (obem_dense_factor /
+    obem_dense_solve) on a synthetic dense system of order n: uniform
+    entries in [-1/2, 1/2] plus sqrt(n) on the diagonal, rows permuted at
+    random so that partial pivoting swaps at almost every column (the BEM
+    matrix's size without its assembly)."""
+    import torch
+    from paper_2110_09214_gb300 import obem
+    prec = {"fp32": obem.OBEM_LU_FP32, "tf32": obem.OBEM_LU_TF32, "bf16": obem.OBEM_LU_BF16,
+            "bf16x9": obem.OBEM_LU_BF16X9}[precision]
+    g = torch.Generator(device=dev).manual_seed(1)
+    A = torch.rand((n, n), device=dev, generator=g) - 0.5
+    A += torch.diag(torch.full((n,), float(n) ** 0.5, device=dev))
+    A = A[torch.randperm(n, device=dev, generator=g)].contiguous()
+    ctx = obem.obem_create(capacity=16, dt=1e-12)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        obem.obem_dense_factor(ctx, A, prec)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        b = torch.rand(n, device=dev, dtype=torch.float64, generator=g)
+        x = torch.empty_like(b)
+        rep = obem.obem_dense_solve(ctx, b, x)
+    finally:
+        obem.obem_destroy(ctx)
+    pk = measured_peaks()
+    tf = 2.0 / 3.0 * float(n) ** 3 / (rep["factor_ms"] * 1e-3) / 1e12
+    return {"n": n, "precision": precision, "factor_wall_s": wall, **rep,
+            "factor_roofline": {"bound": "tensor", "achieved": tf, "peak": pk["bf16_tflops_sustained"],
+                                "unit": "TFLOP/s", "frac": tf / pk["bf16_tflops_sustained"],
+                                "peak_source": pk["source"] + ", BF16 sustained"}}
+
+
 def bem_precision_timing(mesh, dev):
     """The dense BEM solve of the headline mesh (Eq. (matrixBEM), 59,968
     cells) with the LU's trailing updates in each arithmetic -- FP32 SIMT,
@@ -1172,6 +1208,10 @@ def main():
     ws, rank, local = _dist()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.lu_dense > 0:
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps({"dense_lu": dense_lu_timing(a.lu_dense, "cuda:%d" % local, a.precision)}))
     elif a.double_gem_only:
         import torch
         torch.cuda.set_device(local)
