@@ -428,7 +428,7 @@ int obem_tc_gemm(obem_ctx *ctx, float *C, int64_t ldc, const float *A, int64_t l
 /* Failure-detection self-test of the bounded device wait that the LU panel
  * factorisation uses between its CTAs (no passage in the paper): two blocks
  * wait at that grid barrier for a third arrival that never comes; each gives
- * up after the barrier's poll limit (2^24 polls: a few seconds), records
+ * up after the barrier's limit (2 s on the global timer), records
  * OBEM_ERR_TIMEOUT in a device status word and returns, leaving the context
  * usable.  Returns OBEM_OK when the status read back is OBEM_ERR_TIMEOUT,
  * OBEM_ERR_STATE otherwise.  Allocates a few bytes, synchronises `stream`. */

@@ -29,7 +29,6 @@
 
 #define LU_NB 64
 #define TS_R 128               // rows of a block row of the one-launch triangular solves
-#define BARRIER_SPIN_LIMIT (1ll << 24)
 
 // ------------------------------------------------------------------ closed form (FP64)
 // Same expansion as the field kernels: unit-density potential phi and field F
@@ -184,48 +183,54 @@ __global__ void equilibrate_kernel(float *A, int n, double *rowscale, double *ro
 }
 
 // ------------------------------------------------------------------ grid barrier
-// Sense-free generation barrier among the CTAs of a cooperative launch.  The
-// wait is bounded: after BARRIER_SPIN_LIMIT polls the CTA records
-// OBEM_ERR_TIMEOUT in flag[0] and returns false.
-__device__ bool grid_barrier(int *flag, unsigned *count, volatile unsigned *gen, unsigned nblocks)
+// Barrier among the CTAs of a cooperative launch on a monotonic arrival
+// counter (zero at the launch): the k-th barrier of the launch is passed when
+// the counter reaches `target` = (k + 1) x the CTAs.  Thread 0 of each CTA
+// arrives with a release add and polls with acquire loads.  The wait is bounded:
+// after BARRIER_WAIT_NS on the global timer the CTA records OBEM_ERR_TIMEOUT
+// in flag[0] and returns false.
+#define BARRIER_WAIT_NS 2000000000ull
+__device__ __forceinline__ unsigned gb_ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long gb_now()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ bool grid_barrier(int *flag, unsigned *count, unsigned target)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        unsigned g = *gen;
-        __threadfence();
-        unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            *count = 0u;
-            __threadfence();
-            atomicAdd((unsigned *)gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g) {
-                if (++spins > BARRIER_SPIN_LIMIT) {
-                    atomicExch(flag, OBEM_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        // release: the CTA's writes before the barrier above are visible to
+        // any CTA that acquires the counter after this arrival
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        const unsigned long long t0 = gb_now();
+        for (unsigned it = 1; gb_ld_acquire(count) < target; ++it) {
+            if ((it & 63u) == 0u && gb_now() - t0 > BARRIER_WAIT_NS) {
+                atomicExch(flag, OBEM_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
-        if (*(volatile int *)flag != 0) ok = 0;
     }
+    // the acquire above orders, through this barrier, every thread's later reads
     __syncthreads();
     return ok != 0;
 }
 
 // Failure-detection self-test: the blocks wait at the barrier for one more
 // arrival than there are blocks, so every wait runs out after
-// BARRIER_SPIN_LIMIT polls and records OBEM_ERR_TIMEOUT in flag[0].
+// BARRIER_WAIT_NS and records OBEM_ERR_TIMEOUT in flag[0].
 __global__ void barrier_timeout_kernel(int *flag)
 {
-    unsigned *cnt = (unsigned *)&flag[1];
-    volatile unsigned *gen = (volatile unsigned *)&flag[2];
-    grid_barrier(flag, cnt, gen, gridDim.x + 1);
+    grid_barrier(flag, (unsigned *)&flag[1], gridDim.x + 1);
 }
 
 extern "C" int obem_selftest_wait_timeout(obem_ctx *c, obem_stream stream)
@@ -255,11 +260,10 @@ struct PanelArgs {
     float *A;
     int n, k, kb, rows_per_cta;
     int *piv;
-    int *flag;          // [0] status, [1] barrier count, [2] barrier generation
+    int *flag;          // [0] status, [1] barrier arrival counter (zero at the launch)
     // exchange buffers, two sets used by alternate columns (a set is rewritten
     // only after the next barrier, when every CTA has finished reading it)
-    float *cval;        // [2][PAN_MAXG] each CTA's candidate |pivot|
-    int *crow;          // [2][PAN_MAXG] its row
+    unsigned long long *crec;   // [2][PAN_MAXG] each CTA's candidate: |pivot| bits << 32 | ~row (0: none)
     float *crows;       // [2][PAN_MAXG][LU_NB] the candidate row's panel values
     float *gdiag;       // [2][LU_NB] the row receiving the pivot, before the swap
 };
@@ -307,7 +311,7 @@ panel_kernel(PanelArgs a)
     const int r0 = k + b * R;
     const int rows = max(0, min(R, n - r0));
     unsigned *cnt = (unsigned *)&a.flag[1];
-    volatile unsigned *gen = (volatile unsigned *)&a.flag[2];
+    __shared__ unsigned long long sk[8];
     {
         // 8 loads in flight per thread before the shared-memory stores
         const int tot = rows * kb;
@@ -329,11 +333,10 @@ panel_kernel(PanelArgs a)
     for (int j = 0; j < kb; ++j) {
         const int par = j & 1;
         const int pr = k + j;                     // row receiving the pivot
-        float *cval = a.cval + par * PAN_MAXG;
-        int *crow = a.crow + par * PAN_MAXG;
+        unsigned long long *crec = a.crec + par * PAN_MAXG;
         float *crows = a.crows + (size_t)par * PAN_MAXG * LU_NB;
         float *gdiag = a.gdiag + par * LU_NB;
-        // local candidate: max |a| over own rows >= pr
+        // local candidate: max |a| over own rows >= pr, ties to the lower row
         float bv = -1.f;
         int bi = 0x7fffffff, bq = b;
         for (int r = threadIdx.x; r < rows; r += blockDim.x) {
@@ -343,25 +346,41 @@ panel_kernel(PanelArgs a)
             if (pan_better(v, gr, bv, bi)) { bv = v; bi = gr; }
         }
         pan_reduce(bv, bi, bq, sv, sr, sq);
-        if (threadIdx.x == 0) { cval[b] = bv; crow[b] = bi; }
+        // record: the |value|'s bits (non-negative floats order as integers)
+        // above the complemented row, so that the largest key is the pivot
+        if (threadIdx.x == 0)
+            crec[b] = bi == 0x7fffffff ? 0ull
+                                       : ((unsigned long long)__float_as_uint(bv) << 32) | (unsigned)(~(unsigned)bi);
         if (bi != 0x7fffffff)
             for (int c = threadIdx.x; c < kb; c += blockDim.x) crows[(size_t)b * LU_NB + c] = sp[(bi - r0) * ld + c];
         if (pr >= r0 && pr < r0 + rows)
             for (int c = threadIdx.x; c < kb; c += blockDim.x) gdiag[c] = sp[(pr - r0) * ld + c];
-        if (!grid_barrier(a.flag, cnt, gen, G)) return;
-        // global pivot: the same reduction in every CTA
-        float v = -1.f;
-        int p = 0x7fffffff, q = 0;
+        if (!grid_barrier(a.flag, cnt, (unsigned)(j + 1) * (unsigned)G)) return;
+        // global pivot: the largest record, the same in every CTA
+        unsigned long long key = 0ull;
         for (int t = threadIdx.x; t < G; t += blockDim.x) {
-            const float v2 = __ldcg(cval + t);
-            const int r2 = __ldcg(crow + t);
-            if (pan_better(v2, r2, v, p)) { v = v2; p = r2; q = t; }
+            const unsigned long long k2 = __ldcg(crec + t);
+            key = k2 > key ? k2 : key;
         }
-        pan_reduce(v, p, q, sv, sr, sq);
-        if (!(v > 0.f)) {
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+            key = k2 > key ? k2 : key;
+        }
+        if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = key;
+        __syncthreads();
+        key = sk[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) key = sk[w] > key ? sk[w] : key;
+        const float v = __uint_as_float((unsigned)(key >> 32));
+        const int p = (int)(~(unsigned)(key & 0xffffffffu));
+        if (key == 0ull || !(v > 0.f)) {
+            // singular: every CTA stops here; the panel's remaining pivots
+            // are set to no swap
             if (threadIdx.x == 0) atomicCAS(a.flag, 0, OBEM_ERR_SINGULAR);
+            if (b == 0)
+                for (int jj = j + threadIdx.x; jj < kb; jj += blockDim.x) a.piv[k + jj] = k + jj;
             return;
         }
+        const int q = (p - k) / R;                // the CTA holding the pivot row
         for (int c = threadIdx.x; c < kb; c += blockDim.x) urow[c] = __ldcg(crows + (size_t)q * LU_NB + c);
         if (b == 0 && threadIdx.x == 0) a.piv[pr] = p;
         __syncthreads();
@@ -386,19 +405,64 @@ panel_kernel(PanelArgs a)
     }
 }
 
-// apply the panel's row swaps to the columns outside the panel
-__global__ void laswp_kernel(float *A, int n, int k, int kb, const int *piv)
+// The panel's kb row swaps (piv[k .. k + kb)) applied to the columns outside
+// the panel, unless the factorisation's status (flag[0]) records a failure.  The rows they touch -- the kb panel rows and the distinct pivot
+// rows below the panel, at most 2 kb -- are loaded once per column (all loads
+// in flight), permuted in shared memory by the swaps in order, and stored back
+// (swapping in global memory one pivot after the other made every swap wait
+// for the previous one's stores).
+#define LS_COLS 64
+__global__ void __launch_bounds__(LS_COLS) laswp_kernel(float *A, int n, int k, int kb, const int *piv,
+                                                         const int *flag)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n || (c >= k && c < k + kb)) return;
-    for (int j = 0; j < kb; ++j) {
-        int p = piv[k + j];
-        if (p != k + j) {
-            float t = A[(size_t)(k + j) * n + c];
-            A[(size_t)(k + j) * n + c] = A[(size_t)p * n + c];
-            A[(size_t)p * n + c] = t;
+    // a panel that stopped (zero pivot, barrier timeout) may have left
+    // pivots unwritten: no swaps then
+    if (*(volatile const int *)flag != 0) return;
+    __shared__ int s_piv[LU_NB], s_pos[LU_NB], s_row[2 * LU_NB];
+    __shared__ unsigned s_first[LU_NB / 32];
+    __shared__ float s_v[2 * LU_NB][LS_COLS + 1];
+    const int tid = threadIdx.x, lane = tid & 31;
+    // the position of every swap's pivot row among the touched rows: panel
+    // rows first, then the pivot rows below the panel by first appearance
+    const int p = tid < kb ? piv[k + tid] : -1;
+    s_piv[tid] = p;
+    __syncthreads();
+    int f = tid;
+    if (tid < kb && p >= k + kb)
+        for (int q = 0; q < tid; ++q)
+            if (s_piv[q] == p) { f = q; break; }
+    const bool first = tid < kb && p >= k + kb && f == tid;
+    const unsigned bal = __ballot_sync(0xffffffffu, first);
+    if (lane == 0) s_first[tid >> 5] = bal;
+    __syncthreads();
+    const unsigned long long mask = (unsigned long long)s_first[0] | ((unsigned long long)s_first[1] << 32);
+    if (tid < kb) {
+        s_pos[tid] = p < k + kb ? p - k : kb + __popcll(mask & ((1ull << f) - 1ull));
+        s_row[tid] = k + tid;
+    }
+    if (first) s_row[kb + __popcll(mask & ((1ull << tid) - 1ull))] = p;
+    const int m = kb + __popcll(mask);
+    __syncthreads();
+    const int c = blockIdx.x * LS_COLS + tid;
+    const bool live = c < n && !(c >= k && c < k + kb);
+    if (!live) return;
+    for (int q0 = 0; q0 < m; q0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = q0 + u < m ? A[(size_t)s_row[q0 + u] * n + c] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (q0 + u < m) s_v[q0 + u][tid] = v[u];
+    }
+    for (int q = 0; q < kb; ++q) {
+        const int r = s_pos[q];
+        if (r != q) {
+            const float t = s_v[q][tid];
+            s_v[q][tid] = s_v[r][tid];
+            s_v[r][tid] = t;
         }
     }
+    for (int q = 0; q < m; ++q) A[(size_t)s_row[q] * n + c] = s_v[q][tid];
 }
 
 // U12 = L11^-1 A12 with L11 unit lower triangular (kb x kb); a CTA of
@@ -861,8 +925,7 @@ static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int k
 // Pivoting panel factorisation of A[k:n, k:k+kb] (cooperative panel_kernel)
 // followed by its row swaps on every other column.
 struct PanelScratch {
-    float *cval, *crows, *gdiag;
-    int *crow;
+    float *cval, *crows, *gdiag;    // cval: the 2 x PAN_MAXG 64-bit candidate records
     int nsm;
 };
 
@@ -895,10 +958,11 @@ static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaS
         return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
     PanelArgs pa;
     pa.A = c->d_LU; pa.n = n; pa.k = k; pa.kb = kb; pa.rows_per_cta = R; pa.piv = c->d_piv;
-    pa.flag = c->d_flag; pa.cval = P.cval; pa.crow = P.crow; pa.crows = P.crows; pa.gdiag = P.gdiag;
+    pa.flag = c->d_flag; pa.crec = (unsigned long long *)P.cval; pa.crows = P.crows; pa.gdiag = P.gdiag;
     void *args[] = {&pa};
+    OBEM_CUDA(c, cudaMemsetAsync(c->d_flag + 1, 0, sizeof(int), s));      // the barrier's arrival counter
     OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
-    laswp_kernel<<<(n + 255) / 256, 256, 0, s>>>(c->d_LU, n, k, kb, c->d_piv);
+    laswp_kernel<<<(n + LS_COLS - 1) / LS_COLS, LS_COLS, 0, s>>>(c->d_LU, n, k, kb, c->d_piv, c->d_flag);
     OBEM_LAUNCH(c);
     return OBEM_OK;
 }
@@ -1080,7 +1144,6 @@ static int factor_system(obem_ctx *c, int precision, cudaStream_t s)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     PanelScratch PS;
     PS.cval = c->d_panel;
-    PS.crow = (int *)(c->d_panel + 2 * PAN_MAXG);
     PS.gdiag = c->d_panel + 4 * PAN_MAXG;
     PS.crows = c->d_panel + 4 * PAN_MAXG + 2 * LU_NB;
     PS.nsm = nsm;
