@@ -412,7 +412,8 @@ panel_kernel(PanelArgs a)
 // (swapping in global memory one pivot after the other made every swap wait
 // for the previous one's stores).
 #define LS_COLS 64
-__global__ void __launch_bounds__(LS_COLS) laswp_kernel(float *A, int n, int k, int kb, const int *piv,
+#define LS_RG 4                 // row groups per column
+__global__ void __launch_bounds__(LS_COLS * LS_RG) laswp_kernel(float *A, int n, int k, int kb, const int *piv,
                                                          const int *flag)
 {
     // a panel that stopped (zero pivot, barrier timeout) may have left
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(LS_COLS) laswp_kernel(float *A, int n, int k, 
     // the position of every swap's pivot row among the touched rows: panel
     // rows first, then the pivot rows below the panel by first appearance
     const int p = tid < kb ? piv[k + tid] : -1;
-    s_piv[tid] = p;
+    if (tid < LU_NB) s_piv[tid] = p;
     __syncthreads();
     int f = tid;
     if (tid < kb && p >= k + kb)
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(LS_COLS) laswp_kernel(float *A, int n, int k, 
             if (s_piv[q] == p) { f = q; break; }
     const bool first = tid < kb && p >= k + kb && f == tid;
     const unsigned bal = __ballot_sync(0xffffffffu, first);
-    if (lane == 0) s_first[tid >> 5] = bal;
+    if (lane == 0 && tid < LU_NB) s_first[tid >> 5] = bal;
     __syncthreads();
     const unsigned long long mask = (unsigned long long)s_first[0] | ((unsigned long long)s_first[1] << 32);
     if (tid < kb) {
@@ -443,26 +444,38 @@ __global__ void __launch_bounds__(LS_COLS) laswp_kernel(float *A, int n, int k, 
     if (first) s_row[kb + __popcll(mask & ((1ull << tid) - 1ull))] = p;
     const int m = kb + __popcll(mask);
     __syncthreads();
-    const int c = blockIdx.x * LS_COLS + tid;
+    // 64 columns x LS_RG row groups: every thread loads and stores rows
+    // rg, rg + LS_RG, ... of its column (more loads in flight per SM), the
+    // swaps run one thread per column
+    const int cl = tid & (LS_COLS - 1), rg = tid / LS_COLS;
+    const int c = blockIdx.x * LS_COLS + cl;
     const bool live = c < n && !(c >= k && c < k + kb);
-    if (!live) return;
-    for (int q0 = 0; q0 < m; q0 += 8) {
-        float v[8];
+    if (live) {
+        float v[2 * LU_NB / LS_RG];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = q0 + u < m ? A[(size_t)s_row[q0 + u] * n + c] : 0.f;
+        for (int u = 0; u < 2 * LU_NB / LS_RG; ++u) {
+            const int q = rg + LS_RG * u;
+            v[u] = q < m ? A[(size_t)s_row[q] * n + c] : 0.f;
+        }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (q0 + u < m) s_v[q0 + u][tid] = v[u];
-    }
-    for (int q = 0; q < kb; ++q) {
-        const int r = s_pos[q];
-        if (r != q) {
-            const float t = s_v[q][tid];
-            s_v[q][tid] = s_v[r][tid];
-            s_v[r][tid] = t;
+        for (int u = 0; u < 2 * LU_NB / LS_RG; ++u) {
+            const int q = rg + LS_RG * u;
+            if (q < m) s_v[q][cl] = v[u];
         }
     }
-    for (int q = 0; q < m; ++q) A[(size_t)s_row[q] * n + c] = s_v[q][tid];
+    __syncthreads();
+    if (live && rg == 0)
+        for (int q = 0; q < kb; ++q) {
+            const int r = s_pos[q];
+            if (r != q) {
+                const float t = s_v[q][cl];
+                s_v[q][cl] = s_v[r][cl];
+                s_v[r][cl] = t;
+            }
+        }
+    __syncthreads();
+    if (live)
+        for (int q = rg; q < m; q += LS_RG) A[(size_t)s_row[q] * n + c] = s_v[q][cl];
 }
 
 // U12 = L11^-1 A12 with L11 unit lower triangular (kb x kb); a CTA of
@@ -962,7 +975,7 @@ static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaS
     void *args[] = {&pa};
     OBEM_CUDA(c, cudaMemsetAsync(c->d_flag + 1, 0, sizeof(int), s));      // the barrier's arrival counter
     OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
-    laswp_kernel<<<(n + LS_COLS - 1) / LS_COLS, LS_COLS, 0, s>>>(c->d_LU, n, k, kb, c->d_piv, c->d_flag);
+    laswp_kernel<<<(n + LS_COLS - 1) / LS_COLS, LS_COLS * LS_RG, 0, s>>>(c->d_LU, n, k, kb, c->d_piv, c->d_flag);
     OBEM_LAUNCH(c);
     return OBEM_OK;
 }
