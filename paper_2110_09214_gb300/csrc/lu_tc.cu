@@ -181,6 +181,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    if (warp >= 2) {
+        // the epilogue reads and rewrites this CTA's tile of C: bring it into
+        // L2 while the main loop runs (8 lines of 128 bytes per row)
+        for (int e = threadIdx.x - 64; e < TC_BM * (TC_BN / 32); e += 64) {
+            const int r = m0 + e / (TC_BN / 32), cc = n0 + (e % (TC_BN / 32)) * 32;
+            if (r < M && cc < N)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"((unsigned long long)(C + (size_t)r * ldc + cc)));
+        }
+    }
     if (warp == 0 && lane == 0) {
         // producer
         int kb = 0;
@@ -226,22 +235,36 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (fine && !*(volatile int *)s_fail) {
         float *stage = (float *)sA + warp * 32 * 33;       // pipeline smem is idle now
         const int rbase = m0 + warp * 32;
+        const int nrow = min(32, M - rbase);
+        // the 32 rows' values of this lane's column, chunk by chunk of 32
+        // columns; the next chunk's loads are in flight while this one is
+        // written back
+        float vn[32];
+        {
+            const int col = n0 + lane;
+            const float *cp = C + (size_t)rbase * ldc + col;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) vn[i] = (i < nrow && col < N) ? __ldcg(cp + (size_t)i * ldc) : 0.f;
+        }
         for (int c = 0; c < TC_BN; c += 32) {
             if (n0 + c >= N) break;                         // warp-uniform
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = vn[i];
+            if (c + 32 < TC_BN && n0 + c + 32 < N) {
+                const int coln = n0 + c + 32 + lane;
+                const float *cpn = C + (size_t)rbase * ldc + coln;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) vn[i] = (i < nrow && coln < N) ? __ldcg(cpn + (size_t)i * ldc) : 0.f;
+            }
             uint32_t r[32];
             tc_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
 #pragma unroll
             for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
             __syncwarp();
-            // the 32 rows' values of this lane's column: all loads in
-            // flight before any store (one HBM latency per chunk, not 32)
             const int col = n0 + c + lane;
-            const int nrow = min(32, M - rbase);
             float *cp = C + (size_t)rbase * ldc + col;
             if (col < N) {
-                float v[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = i < nrow ? __ldcg(cp + (size_t)i * ldc) : 0.f;
 #pragma unroll
                 for (int i = 0; i < 32; ++i)
                     if (i < nrow) __stcg(cp + (size_t)i * ldc, v[i] - stage[i * 33 + lane]);
@@ -258,14 +281,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                      : "memory");
 }
 
-// out[i * ldo + k] = bf16(A[i * lda + k]), i < M, k < K
+// out[i * ldo + k] = bf16(A[i * lda + k]), i < M, k < K: blockDim.x threads
+// across a row (a multiple of 32, not above K's), blockDim.y rows per pass,
+// grid-stride in both
 __global__ void tc_cvt_rows_kernel(const float *__restrict__ A, long long lda, int M, int K,
                                    __nv_bfloat16 *__restrict__ out, int ldo)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    for (int i = blockIdx.y; i < M; i += gridDim.y)
-        out[(size_t)i * ldo + k] = __float2bfloat16_rn(A[(size_t)i * lda + k]);
+    for (int i = blockIdx.y * blockDim.y + threadIdx.y; i < M; i += gridDim.y * blockDim.y)
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x)
+            out[(size_t)i * ldo + k] = __float2bfloat16_rn(A[(size_t)i * lda + k]);
 }
 
 // out[j * ldo + k] = bf16(B[k * ldb + j]), j < N, k < K (transpose through
@@ -366,8 +390,11 @@ int obem_tc_gemm_sub(obem_ctx *c, float *C, long long ldc, const float *A, long 
     if (rc != OBEM_OK) return rc;
     __nv_bfloat16 *Ab = (__nv_bfloat16 *)c->tc_a, *Bb = (__nv_bfloat16 *)c->tc_b;
     {
-        dim3 g((K + 255) / 256, M < 65535 ? M : 65535);
-        tc_cvt_rows_kernel<<<g, 256, 0, s>>>(A, lda, M, K, Ab, ldk);
+        // skinny operands (K of 64 against tall M) get several rows per block
+        const int tx = K >= 256 ? 256 : (K + 31) / 32 * 32, ty = 256 / tx;
+        const int gx = K >= 256 ? ((K + 255) / 256 < 64 ? (K + 255) / 256 : 64) : 1;
+        const int gyn = (M + ty - 1) / ty, gy = gyn < 4096 ? gyn : 4096;
+        tc_cvt_rows_kernel<<<dim3(gx, gy), dim3(tx, ty), 0, s>>>(A, lda, M, K, Ab, ldk);
         dim3 gt((N + 31) / 32, (K + 31) / 32 < 65535 ? (K + 31) / 32 : 65535);
         tc_cvt_trans_kernel<<<gt, dim3(32, 8), 0, s>>>(B, ldb, K, N, Bb, ldk);
         OBEM_LAUNCH(c);
