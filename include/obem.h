@@ -206,11 +206,13 @@ int obem_bem_solve(obem_ctx *ctx, const double *group_voltage, const float *sigm
  * normal).  sources: device [ns][4] (x, y, z, q), 16-byte aligned; drhs:
  * device [n_panels].  The cell integrals use the quadrature tiers of the
  * field evaluation and the FP64 closed form within one cell size of a charge.
- * OBEM_ERR_STATE without a mesh.  The first call allocates per-cell scratch;
- * later calls allocate nothing and do not synchronise. */
+ * OBEM_ERR_STATE without a mesh; OBEM_ERR_TIMEOUT if a bounded wait for a
+ * bulk copy of the charges ran out (drhs is then undefined).  Allocates
+ * scratch on the first call and whenever ns exceeds every earlier call's;
+ * synchronises `stream` (to read the status of its waits). */
 int obem_influence_rhs(obem_ctx *ctx, const float *sources, int32_t ns, float *drhs, obem_stream stream);
 
-/* Adjoint of obem_bem_solve, for gradients through the solve./* Adjoint of obem_bem_solve, for gradients through the solve.  Given
+/* Adjoint of obem_bem_solve, for gradients through the solve.  Given
  * dL_dsigma = dL/dsigma (device [n_panels]), solves A^T mu = dL/dsigma with
  * the stored factors (transposed triangular solves, iterative refinement
  * with FP64 residuals on the equilibrated matrix); mu = dL/db is the
