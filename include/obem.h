@@ -498,7 +498,8 @@ int obem_stage_times(obem_ctx *ctx, double *ms /* [5] */, int64_t *counts /* [9]
  *   err       optional host buffer of err_len bytes for an error message
  * Sizes beyond the maxima return OBEM_ERR_ARG with a message in err; nothing
  * is launched then.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current.  Every call reuses
+ * address (cudaGetSymbolAddress) with that device current, and caches it; make
+ * that first call before any stream capture begins.  Every call reuses
  * the same array and leaves its contents behind: two calls whose work
  * overlaps on the GPU (on different streams, or from different host threads)
  * race on it and give wrong results; serialise them on one stream. */
