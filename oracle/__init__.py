@@ -15,9 +15,11 @@ Parity status of each function (see the test-suite for the pins):
   gas_constants and the step on tabulated cross sections (grid lookup,
   interpolation, thresholds, majorant, excitation and ionisation energetics):
   pinned by tests/test_oracle_gas_pins.py.
-  Swarm parameters of the synthetic argon-like gas: parity unpinned (no closed
-  form; only GPU-vs-oracle agreement within 3 sigma and the Maxwell-model
-  limits are checked).
+  No function here is unpinned.  The swarm parameters of the synthetic
+  argon-like gas are not a function of their own: they are the pinned fits
+  applied to the moments of many pinned steps.  That gas has no closed form
+  for them, so their GPU-vs-oracle agreement (16 seeds per side, 3 sigma) is
+  a consistency check, not a pin.
 """
 from __future__ import annotations
 
