@@ -429,15 +429,16 @@ int obem_tc_gemm(obem_ctx *ctx, float *C, int64_t ldc, const float *A, int64_t l
 
 /* Failure-detection self-test of the bounded device wait that the LU panel
  * factorisation uses between its CTAs (no passage in the paper): two blocks
- * wait at that grid barrier for a third arrival that never comes; each gives
- * up after the barrier's limit (2 s on the global timer), records
+ * wait, as the panel's CTAs wait for each other's pivot candidates of a
+ * column, for two candidate records that no block publishes; each gives
+ * up after the wait's limit (2 s on the global timer), records
  * OBEM_ERR_TIMEOUT in a device status word and returns, leaving the context
  * usable.  Returns OBEM_OK when the status read back is OBEM_ERR_TIMEOUT,
  * OBEM_ERR_STATE otherwise.  Allocates a few bytes, synchronises `stream`. */
 int obem_selftest_wait_timeout(obem_ctx *ctx, obem_stream stream);
 
 /* Failure-detection self-tests of the library's other bounded device waits
- * (no passage in the paper).  which = 0: the LU panel's grid barrier, as
+ * (no passage in the paper).  which = 0: the LU panel's candidate wait, as
  * obem_selftest_wait_timeout.  which = 1: the flag wait of the one-launch
  * triangular substitutions of obem_bem_solve: one thread block waits for a
  * block row that no block solves (needs a factored system of at least 256

@@ -12,7 +12,8 @@
 //                     1 / max |A_ij| (exact; solution unchanged)
 //   LU                partial pivoting; panels of LU_NB columns factored by
 //                       panel_kernel   cooperative: one row chunk per CTA held
-//                                      in shared memory, bounded grid barriers
+//                                      in shared memory, one bounded exchange
+//                                      of pivot candidates per column
 //                       laswp_kernel   the panel's row swaps on whole rows
 //                     BF16 (OBEM_LU_BF16): recursive (rec_lu / rec_trsm), every
 //                       trailing update and off-diagonal TRSM block a
@@ -182,55 +183,73 @@ __global__ void equilibrate_kernel(float *A, int n, double *rowscale, double *ro
     }
 }
 
-// ------------------------------------------------------------------ grid barrier
-// Barrier among the CTAs of a cooperative launch on a monotonic arrival
-// counter (zero at the launch): the k-th barrier of the launch is passed when
-// the counter reaches `target` = (k + 1) x the CTAs.  Thread 0 of each CTA
-// arrives with a release add and polls with acquire loads.  The wait is bounded:
-// after BARRIER_WAIT_NS on the global timer the CTA records OBEM_ERR_TIMEOUT
-// in flag[0] and returns false.
+// ------------------------------------------------------------------ panel exchange
+// The CTAs of the pivoting panel (a cooperative launch) meet once per column:
+// each CTA writes its pivot candidate (a 64-bit record and the candidate's
+// row), then arrives on a monotonic counter (zero at the launch) with a
+// release add; a CTA waits for column j until the counter reaches (j + 1) x
+// the CTAs (acquire loads) and then reads every record.  Records and rows go
+// to two buffer sets used by alternate columns: a CTA rewrites a set two
+// columns later, after every CTA has arrived for the column in between, i.e.
+// has finished reading it.  The wait is bounded: after BARRIER_WAIT_NS on
+// the global timer the CTA records OBEM_ERR_TIMEOUT in flag[0] and gives up.
 #define BARRIER_WAIT_NS 2000000000ull
-__device__ __forceinline__ unsigned gb_ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
+#define PAN_MAXG 1024           // largest panel grid
+// records [2][PAN_MAXG] (64-bit), gdiag [2][LU_NB], candidate rows [2][PAN_MAXG][LU_NB]
+#define PAN_REC_FLOATS (4 * PAN_MAXG)
+#define PAN_SCRATCH_FLOATS (PAN_REC_FLOATS + 2 * LU_NB + 2 * PAN_MAXG * LU_NB)
+
 __device__ __forceinline__ unsigned long long gb_now()
 {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ bool grid_barrier(int *flag, unsigned *count, unsigned target)
+
+// Called by warp 0 only: waits until *count >= target and returns the
+// largest of the G records (in every lane), 0 when the wait ran out (then
+// flag[0] = OBEM_ERR_TIMEOUT).  Lane 0 polls with acquire loads; the warp
+// barrier after it orders the other lanes' reads of the records.
+__device__ unsigned long long pan_wait_records(const unsigned long long *recs, int G, const unsigned *count,
+                                               unsigned target, int *flag)
 {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        // release: the CTA's writes before the barrier above are visible to
-        // any CTA that acquires the counter after this arrival
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    const int lane = threadIdx.x & 31;
+    int ok = 1;
+    if (lane == 0) {
         const unsigned long long t0 = gb_now();
-        for (unsigned it = 1; gb_ld_acquire(count) < target; ++it) {
+        for (unsigned it = 1;; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
             if ((it & 63u) == 0u && gb_now() - t0 > BARRIER_WAIT_NS) {
-                atomicExch(flag, OBEM_ERR_TIMEOUT);
                 ok = 0;
+                atomicExch(flag, OBEM_ERR_TIMEOUT);
                 break;
             }
         }
     }
-    // the acquire above orders, through this barrier, every thread's later reads
-    __syncthreads();
-    return ok != 0;
+    __syncwarp();
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    unsigned long long best = 0ull;
+    if (ok)
+        for (int t = lane; t < G; t += 32) {
+            const unsigned long long v = __ldcg(recs + t);
+            best = v > best ? v : best;
+        }
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v2 > best ? v2 : best;
+    }
+    return ok ? (best ? best : 1ull) : 0ull;
 }
 
-// Failure-detection self-test: the blocks wait at the barrier for one more
-// arrival than there are blocks, so every wait runs out after
-// BARRIER_WAIT_NS and records OBEM_ERR_TIMEOUT in flag[0].
+// Failure-detection self-test: the blocks arrive and wait for one block more
+// than was launched, so every wait runs out after BARRIER_WAIT_NS and records
+// OBEM_ERR_TIMEOUT in flag[0] (flag[1]: the counter, flag[2..]: records).
 __global__ void barrier_timeout_kernel(int *flag)
 {
-    grid_barrier(flag, (unsigned *)&flag[1], gridDim.x + 1);
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"((unsigned *)&flag[1]) : "memory");
+    pan_wait_records((const unsigned long long *)(flag + 2), 1, (const unsigned *)&flag[1], gridDim.x + 1, flag);
 }
 
 extern "C" int obem_selftest_wait_timeout(obem_ctx *c, obem_stream stream)
@@ -253,65 +272,110 @@ extern "C" int obem_selftest_wait_timeout(obem_ctx *c, obem_stream stream)
     return OBEM_OK;
 }
 
-#define PAN_MAXG 1024           // largest panel grid
-#define PAN_SCRATCH_FLOATS (4 * PAN_MAXG + 2 * LU_NB + 2 * PAN_MAXG * LU_NB)
-
 struct PanelArgs {
     float *A;
     int n, k, kb, rows_per_cta;
     int *piv;
-    int *flag;          // [0] status, [1] barrier arrival counter (zero at the launch)
-    // exchange buffers, two sets used by alternate columns (a set is rewritten
-    // only after the next barrier, when every CTA has finished reading it)
-    unsigned long long *crec;   // [2][PAN_MAXG] each CTA's candidate: |pivot| bits << 32 | ~row (0: none)
+    int *flag;          // [0] status, [1] arrival counter (zero at the launch)
+    unsigned long long *rec;    // [2][PAN_MAXG] CTA b's candidate: |pivot| bits << 32 | ~row, 1: none
     float *crows;       // [2][PAN_MAXG][LU_NB] the candidate row's panel values
     float *gdiag;       // [2][LU_NB] the row receiving the pivot, before the swap
 };
 
-// (value, row) of the better pivot candidate: larger |a|, ties to the lower row
-__device__ __forceinline__ bool pan_better(float v2, int r2, float v, int r)
+// best candidate over the CTA, in every thread: v = |a| (-1: none), r = its
+// row, larger |a| first, ties to the lower row.  One CTA barrier; the warps'
+// results go to the buffer set `par` (calls alternate the sets, so a set is
+// rewritten only after the barriers of the call in between).
+__device__ __forceinline__ void pan_reduce(float &v, int &r, unsigned (*sv)[8], unsigned (*sr)[8], int par)
 {
-    return v2 > v || (v2 == v && r2 < r);
+    // non-negative floats order as their bits; +1 leaves 0 for "none"
+    const unsigned kv = v < 0.f ? 0u : __float_as_uint(v) + 1u;
+    const unsigned m = __reduce_max_sync(0xffffffffu, kv);
+    const unsigned rm = __reduce_min_sync(0xffffffffu, kv == m ? (unsigned)r : 0xffffffffu);
+    if ((threadIdx.x & 31) == 0) {
+        sv[par][threadIdx.x >> 5] = m;
+        sr[par][threadIdx.x >> 5] = rm;
+    }
+    __syncthreads();
+    unsigned bm = sv[par][0], br = sr[par][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        const unsigned m2 = sv[par][w], r2 = sr[par][w];
+        if (m2 > bm || (m2 == bm && r2 < br)) { bm = m2; br = r2; }
+    }
+    v = bm == 0u ? -1.f : __uint_as_float(bm - 1u);
+    r = bm == 0u ? 0x7fffffff : (int)br;
 }
 
-// best (value, row, slot) over the CTA, result in every thread
-__device__ __forceinline__ void pan_reduce(float &v, int &r, int &q, float *sv, int *sr, int *sq)
+// Warp 0 publishes the CTA's candidate for column col: the candidate row bi
+// and, from its owner, the row that receives the pivot (both up to date),
+// then the record, then the arrival.  With j >= 0 the two rows' columns
+// j + 2 .. kb - 1 are first brought up to date with the multipliers of
+// column j (the rest of the CTA's rows are updated after the publication);
+// j = -1: no update.
+__device__ __forceinline__ void pan_publish(const PanelArgs &a, int col, int j, float bv, int bi, int r0, int rows,
+                                            float *sp, int ld, const float *urow)
 {
-    for (int o = 16; o; o >>= 1) {
-        const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        const int r2 = __shfl_xor_sync(0xffffffffu, r, o);
-        const int q2 = __shfl_xor_sync(0xffffffffu, q, o);
-        if (pan_better(v2, r2, v, r)) { v = v2; r = r2; q = q2; }
+    const int lane = threadIdx.x & 31, kb = a.kb, b = blockIdx.x;
+    const int par = col & 1;
+    const int pr = a.k + col;
+    float *crow = a.crows + ((size_t)par * PAN_MAXG + b) * LU_NB;
+    float *gd = a.gdiag + par * LU_NB;
+    const bool has = bi != 0x7fffffff;
+    const bool own = pr >= r0 && pr < r0 + rows;
+    for (int c = lane; c < kb; c += 32) {
+        if (has) {
+            float *row = sp + (size_t)(bi - r0) * ld;
+            float x = row[c];
+            if (j >= 0 && c >= j + 2) {
+                x = fmaf(-row[j], urow[c], x);
+                row[c] = x;
+            }
+            crow[c] = x;
+            if (bi == pr) gd[c] = x;
+        }
+        if (own && bi != pr) {
+            float *row = sp + (size_t)(pr - r0) * ld;
+            float x = row[c];
+            if (j >= 0 && c >= j + 2) {
+                x = fmaf(-row[j], urow[c], x);
+                row[c] = x;
+            }
+            gd[c] = x;
+        }
     }
-    const int w = threadIdx.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) { sv[w] = v; sr[w] = r; sq[w] = q; }
-    __syncthreads();
-    v = sv[0]; r = sr[0]; q = sq[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
-        if (pan_better(sv[k], sr[k], v, r)) { v = sv[k]; r = sr[k]; q = sq[k]; }
+    if (lane == 0)
+        a.rec[(size_t)par * PAN_MAXG + b] =
+            has ? ((unsigned long long)__float_as_uint(bv) << 32) | (unsigned)(~(unsigned)bi) : 1ull;
+    __syncwarp();
+    // release: the warp's writes above are visible to any CTA that acquires
+    // the counter after this arrival
+    if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"((unsigned *)&a.flag[1]) : "memory");
 }
 
 // Panel factorisation of A[k:n, k:k+kb] with partial pivoting.  CTA b owns
-// rows k + b*R .. k + (b+1)*R - 1 of the panel in shared memory.  One grid
-// barrier per column: before it every CTA publishes its best candidate (value,
-// row and the row's panel values) and the owner of row k + j publishes that
-// row; after it every CTA picks the same pivot from the published candidates
-// and swaps and eliminates its own rows.
+// rows k + b*R .. k + (b+1)*R - 1 of the panel in shared memory.  Per column
+// j: wait for every CTA's candidate of column j and take the largest (the
+// same pivot in every CTA), fetch the pivot row, swap, form the multipliers
+// and update column j + 1 of the own rows, find the CTA's candidate for
+// column j + 1 and publish it (warp 0, which then waits for the next
+// column); the other warps update the other columns of the own rows
+// meanwhile.
 __global__ void __launch_bounds__(256)
 panel_kernel(PanelArgs a)
 {
     extern __shared__ float sp[];            // [R][kb + 1] (padded against bank conflicts)
-    __shared__ float sv[8];
-    __shared__ int sr[8], sq[8];
+    __shared__ unsigned sv[2][8], sr[2][8];
+    __shared__ unsigned long long skey;
     __shared__ float urow[LU_NB];
     const int R = a.rows_per_cta, kb = a.kb, n = a.n, k = a.k;
     const int ld = kb + 1;
     const int b = blockIdx.x, G = gridDim.x;
     const int r0 = k + b * R;
     const int rows = max(0, min(R, n - r0));
-    unsigned *cnt = (unsigned *)&a.flag[1];
-    __shared__ unsigned long long sk[8];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // a factorisation that already failed (zero pivot, a wait that ran out)
+    // stops here instead of waiting again in every later panel
+    if (*(volatile const int *)a.flag != 0) return;
     {
         // 8 loads in flight per thread before the shared-memory stores
         const int tot = rows * kb;
@@ -319,87 +383,100 @@ panel_kernel(PanelArgs a)
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int t = t0 + u * 256 + threadIdx.x;
+                const int t = t0 + u * 256 + tid;
                 v[u] = t < tot ? a.A[(size_t)(r0 + t / kb) * n + k + t % kb] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int t = t0 + u * 256 + threadIdx.x;
+                const int t = t0 + u * 256 + tid;
                 if (t < tot) sp[(t / kb) * ld + t % kb] = v[u];
             }
         }
     }
     __syncthreads();
+    {
+        // candidate of column 0
+        float bv = -1.f;
+        int bi = 0x7fffffff;
+        for (int r = tid; r < rows; r += blockDim.x) {
+            const float v = fabsf(sp[r * ld]);
+            if (v > bv) { bv = v; bi = r0 + r; }
+        }
+        pan_reduce(bv, bi, sv, sr, 0);
+        if (warp == 0) pan_publish(a, 0, -1, bv, bi, r0, rows, sp, ld, urow);
+    }
     for (int j = 0; j < kb; ++j) {
         const int par = j & 1;
         const int pr = k + j;                     // row receiving the pivot
-        unsigned long long *crec = a.crec + par * PAN_MAXG;
-        float *crows = a.crows + (size_t)par * PAN_MAXG * LU_NB;
-        float *gdiag = a.gdiag + par * LU_NB;
-        // local candidate: max |a| over own rows >= pr, ties to the lower row
-        float bv = -1.f;
-        int bi = 0x7fffffff, bq = b;
-        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-            const int gr = r0 + r;
-            if (gr < pr) continue;
-            const float v = fabsf(sp[r * ld + j]);
-            if (pan_better(v, gr, bv, bi)) { bv = v; bi = gr; }
+        if (warp == 0) {
+            const unsigned long long kw =
+                pan_wait_records(a.rec + (size_t)par * PAN_MAXG, G, (const unsigned *)&a.flag[1],
+                                 (unsigned)(j + 1) * (unsigned)G, a.flag);
+            if (tid == 0) skey = kw;
         }
-        pan_reduce(bv, bi, bq, sv, sr, sq);
-        // record: the |value|'s bits (non-negative floats order as integers)
-        // above the complemented row, so that the largest key is the pivot
-        if (threadIdx.x == 0)
-            crec[b] = bi == 0x7fffffff ? 0ull
-                                       : ((unsigned long long)__float_as_uint(bv) << 32) | (unsigned)(~(unsigned)bi);
-        if (bi != 0x7fffffff)
-            for (int c = threadIdx.x; c < kb; c += blockDim.x) crows[(size_t)b * LU_NB + c] = sp[(bi - r0) * ld + c];
-        if (pr >= r0 && pr < r0 + rows)
-            for (int c = threadIdx.x; c < kb; c += blockDim.x) gdiag[c] = sp[(pr - r0) * ld + c];
-        if (!grid_barrier(a.flag, cnt, (unsigned)(j + 1) * (unsigned)G)) return;
-        // global pivot: the largest record, the same in every CTA
-        unsigned long long key = 0ull;
-        for (int t = threadIdx.x; t < G; t += blockDim.x) {
-            const unsigned long long k2 = __ldcg(crec + t);
-            key = k2 > key ? k2 : key;
-        }
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-            key = k2 > key ? k2 : key;
-        }
-        if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = key;
         __syncthreads();
-        key = sk[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) key = sk[w] > key ? sk[w] : key;
+        const unsigned long long key = skey;
+        if (key == 0ull) return;                  // the wait ran out
         const float v = __uint_as_float((unsigned)(key >> 32));
         const int p = (int)(~(unsigned)(key & 0xffffffffu));
-        if (key == 0ull || !(v > 0.f)) {
+        if (key == 1ull || !(v > 0.f)) {
             // singular: every CTA stops here; the panel's remaining pivots
             // are set to no swap
-            if (threadIdx.x == 0) atomicCAS(a.flag, 0, OBEM_ERR_SINGULAR);
+            if (tid == 0) atomicCAS(a.flag, 0, OBEM_ERR_SINGULAR);
             if (b == 0)
-                for (int jj = j + threadIdx.x; jj < kb; jj += blockDim.x) a.piv[k + jj] = k + jj;
+                for (int jj = j + tid; jj < kb; jj += blockDim.x) a.piv[k + jj] = k + jj;
             return;
         }
         const int q = (p - k) / R;                // the CTA holding the pivot row
-        for (int c = threadIdx.x; c < kb; c += blockDim.x) urow[c] = __ldcg(crows + (size_t)q * LU_NB + c);
-        if (b == 0 && threadIdx.x == 0) a.piv[pr] = p;
-        __syncthreads();
-        if (pr >= r0 && pr < r0 + rows)
-            for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[(pr - r0) * ld + c] = urow[c];
-        if (p != pr && p >= r0 && p < r0 + rows)
-            for (int c = threadIdx.x; c < kb; c += blockDim.x) sp[(p - r0) * ld + c] = __ldcg(gdiag + c);
+        if (tid < kb) {
+            const float u = __ldcg(a.crows + ((size_t)par * PAN_MAXG + q) * LU_NB + tid);
+            const float g = __ldcg(a.gdiag + par * LU_NB + tid);
+            urow[tid] = u;
+            if (pr >= r0 && pr < r0 + rows) sp[(pr - r0) * ld + tid] = u;
+            if (p != pr && p >= r0 && p < r0 + rows) sp[(p - r0) * ld + tid] = g;
+        }
+        if (b == 0 && tid == 0) a.piv[pr] = p;
         __syncthreads();
         const float inv = 1.0f / urow[j];
-        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        if (j + 1 == kb) {
+            for (int r = tid; r < rows; r += blockDim.x)
+                if (r0 + r > pr) sp[r * ld + j] *= inv;
+            break;
+        }
+        // multipliers of column j, column j + 1 of the own rows, candidate
+        const float u1 = urow[j + 1];
+        float bv = -1.f;
+        int bi = 0x7fffffff;
+        for (int r = tid; r < rows; r += blockDim.x) {
             const int gr = r0 + r;
             if (gr <= pr) continue;
             const float l = sp[r * ld + j] * inv;
             sp[r * ld + j] = l;
-            for (int c = j + 1; c < kb; ++c) sp[r * ld + c] = fmaf(-l, urow[c], sp[r * ld + c]);
+            const float x = fmaf(-l, u1, sp[r * ld + j + 1]);
+            sp[r * ld + j + 1] = x;
+            const float ax = fabsf(x);
+            if (ax > bv) { bv = ax; bi = gr; }
         }
-        __syncthreads();
+        pan_reduce(bv, bi, sv, sr, (j + 1) & 1);
+        if (warp == 0) {
+            pan_publish(a, j + 1, j, bv, bi, r0, rows, sp, ld, urow);
+        } else {
+            // the other rows' columns j + 2 .. kb - 1, while warp 0 waits
+            // for the next column (the barrier after that wait comes before
+            // any of them is read)
+            const int nx = pr + 1;
+            for (int r = tid - 32; r < rows; r += (int)blockDim.x - 32) {
+                const int gr = r0 + r;
+                if (gr <= pr || gr == bi || gr == nx) continue;
+                float *row = sp + (size_t)r * ld;
+                const float l = row[j];
+#pragma unroll 8
+                for (int c = j + 2; c < kb; ++c) row[c] = fmaf(-l, urow[c], row[c]);
+            }
+        }
     }
-    for (int t = threadIdx.x; t < rows * kb; t += blockDim.x) {
+    __syncthreads();
+    for (int t = tid; t < rows * kb; t += blockDim.x) {
         int r = t / kb, c = t % kb;
         a.A[(size_t)(r0 + r) * n + k + c] = sp[r * ld + c];
     }
@@ -414,8 +491,10 @@ panel_kernel(PanelArgs a)
 #define LS_COLS 64
 #define LS_RG 4                 // row groups per column
 __global__ void __launch_bounds__(LS_COLS * LS_RG) laswp_kernel(float *A, int n, int k, int kb, const int *piv,
-                                                         const int *flag)
+                                                         int *flag)
 {
+    // the panel's arrival counter, zeroed for the next panel
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag[1] = 0;
     // a panel that stopped (zero pivot, barrier timeout) may have left
     // pivots unwritten: no swaps then
     if (*(volatile const int *)flag != 0) return;
@@ -971,9 +1050,8 @@ static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaS
         return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
     PanelArgs pa;
     pa.A = c->d_LU; pa.n = n; pa.k = k; pa.kb = kb; pa.rows_per_cta = R; pa.piv = c->d_piv;
-    pa.flag = c->d_flag; pa.crec = (unsigned long long *)P.cval; pa.crows = P.crows; pa.gdiag = P.gdiag;
+    pa.flag = c->d_flag; pa.rec = (unsigned long long *)P.cval; pa.crows = P.crows; pa.gdiag = P.gdiag;
     void *args[] = {&pa};
-    OBEM_CUDA(c, cudaMemsetAsync(c->d_flag + 1, 0, sizeof(int), s));      // the barrier's arrival counter
     OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
     laswp_kernel<<<(n + LS_COLS - 1) / LS_COLS, LS_COLS * LS_RG, 0, s>>>(c->d_LU, n, k, kb, c->d_piv, c->d_flag);
     OBEM_LAUNCH(c);
@@ -1157,8 +1235,8 @@ static int factor_system(obem_ctx *c, int precision, cudaStream_t s)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     PanelScratch PS;
     PS.cval = c->d_panel;
-    PS.gdiag = c->d_panel + 4 * PAN_MAXG;
-    PS.crows = c->d_panel + 4 * PAN_MAXG + 2 * LU_NB;
+    PS.gdiag = c->d_panel + PAN_REC_FLOATS;
+    PS.crows = c->d_panel + PAN_REC_FLOATS + 2 * LU_NB;
     PS.nsm = nsm;
     if (precision == OBEM_LU_BF16) {
         // recursive factorisation, trailing updates on the tensor cores
@@ -1191,7 +1269,7 @@ static int factor_system(obem_ctx *c, int precision, cudaStream_t s)
     cudaEventDestroy(e1);
     c->factor_ms = ms;
     if (flag[0] == OBEM_ERR_SINGULAR) return obem_fail(c, OBEM_ERR_SINGULAR, "LU: zero pivot");
-    if (flag[0] == OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: panel grid barrier timed out");
+    if (flag[0] == OBEM_ERR_TIMEOUT) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: a panel's wait for the pivot candidates timed out");
     if (flag[4] != 0) return obem_fail(c, OBEM_ERR_TIMEOUT, "LU: a tensor-core GEMM wait timed out");
     // the row swaps as one permutation: (P b)[i] = b[perm[i]]
     {

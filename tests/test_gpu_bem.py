@@ -131,9 +131,10 @@ def test_solve_before_assemble_is_a_state_error():
 
 
 def test_bounded_wait_reports_timeout_and_leaves_the_context_usable():
-    """Failure detection without a fault: the grid barrier that the LU panel
-    factorisation uses between its CTAs is made to wait for one more block
-    than was launched.  Every wait gives up after its time limit, the kernel
+    """Failure detection without a fault: the wait that the LU panel
+    factorisation uses between its CTAs (for every CTA's pivot candidate of a
+    column) is made to wait for candidates that no block publishes.  Every
+    wait gives up after its time limit, the kernel
     records OBEM_ERR_TIMEOUT in its status word and returns (the call reports
     OBEM_OK when it reads that status back); the same context then assembles,
     factorises and solves a small system correctly."""
