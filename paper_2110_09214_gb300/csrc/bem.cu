@@ -607,30 +607,74 @@ __device__ __forceinline__ void load_block(float (*T)[LU_NB + 1], const float *M
 }
 
 // X = L^-1 X for the unit lower triangular block L = A[r0:r0+m, r0:r0+m]
-// (m <= LU_NB) and X = A[r0:r0+m, c0:c0+nc]: one warp per column of X, lane
-// l holding rows l and l + 32, L in shared memory; column q's value is
-// broadcast with a shuffle and eliminated from the rows below it.
-#define TRSW_WARPS 8
-__global__ void __launch_bounds__(TRSW_WARPS * 32)
-trsm_range_kernel(float *A, int n, int r0, int m, int c0, int nc)
+// (m <= M) and X = A[r0:r0+m, c0:c0+nc]: one thread per column of X, the
+// block's columns staged through shared memory (coalesced loads and stores)
+// and each column's M values held in registers; L transposed in shared
+// memory (zero outside its strict lower triangle; a column of L read as
+// broadcast float4).  For q = 0 .. M-2, x[r] -= L[r][q] x[q] for every
+// r > q, in FP32 (64 rows at a time in registers, each row's updates still
+// in the order of q).  M = 64 or 128: the leaves of the recursive TRSM (a 128-row
+// leaf replaces two 64-row leaves and the BF16 tensor-core update between
+// them).
+#define TRSM_LEAF 128
+#define TRSM_LEAF_THREADS 128
+template <int M>
+constexpr size_t trsm_leaf_smem() { return sizeof(float) * (size_t)M * (M + TRSM_LEAF_THREADS); }
+template <int M>
+__global__ void __launch_bounds__(TRSM_LEAF_THREADS)
+trsm_leaf_kernel(float *A, int n, int r0, int m, int c0, int nc)
 {
-    __shared__ float L[LU_NB][LU_NB + 1];
-    load_block(L, A, n, r0, r0, m, false);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int col = blockIdx.x * TRSW_WARPS + (threadIdx.x >> 5);
-    if (col >= nc) return;
-    float *x = A + (size_t)r0 * n + c0 + col;
-    const bool h0 = lane < m, h1 = lane + 32 < m;
-    float x0 = h0 ? x[(size_t)lane * n] : 0.f;
-    float x1 = h1 ? x[(size_t)(lane + 32) * n] : 0.f;
-    for (int q = 0; q < m - 1; ++q) {
-        const float xq = __shfl_sync(0xffffffffu, q < 32 ? x0 : x1, q & 31);
-        if (h0 && lane > q) x0 = fmaf(-L[lane][q], xq, x0);
-        if (h1 && lane + 32 > q) x1 = fmaf(-L[lane + 32][q], xq, x1);
+    extern __shared__ float4 tl_L4[];            // [M][M / 4]: row q = column q of L
+    float *Lt = (float *)tl_L4;
+    float *Xs = Lt + M * M;                      // [M][TRSM_LEAF_THREADS]
+    const int tid = threadIdx.x;
+    for (int t = tid; t < M * M; t += blockDim.x) {
+        const int r = t / M, q = t % M;           // coalesced over q
+        Lt[q * M + r] = (r < m && q < r) ? A[(size_t)(r0 + r) * n + r0 + q] : 0.f;
     }
-    if (h0) x[(size_t)lane * n] = x0;
-    if (h1) x[(size_t)(lane + 32) * n] = x1;
+    const int col = blockIdx.x * TRSM_LEAF_THREADS + tid;
+    const bool live = col < nc;
+    float *x = A + (size_t)r0 * n + c0 + col;
+#pragma unroll 8
+    for (int r = 0; r < M; ++r) Xs[r * TRSM_LEAF_THREADS + tid] = (live && r < m) ? x[(size_t)r * n] : 0.f;
+    __syncthreads();
+    // 64 rows at a time in registers: the rows of the earlier blocks (already
+    // solved, back in shared memory) first, then the block's own triangle
+#pragma unroll
+    for (int h = 0; h < M / 64; ++h) {
+        float v[64];
+#pragma unroll
+        for (int r = 0; r < 64; ++r) v[r] = Xs[(64 * h + r) * TRSM_LEAF_THREADS + tid];
+#pragma unroll 4
+        for (int q = 0; q < 64 * h; ++q) {
+            const float xq = Xs[q * TRSM_LEAF_THREADS + tid];
+#pragma unroll
+            for (int r4 = 0; r4 < 64; r4 += 4) {
+                const float4 l = tl_L4[q * (M / 4) + (64 * h + r4) / 4];
+                v[r4] = fmaf(-l.x, xq, v[r4]);
+                v[r4 + 1] = fmaf(-l.y, xq, v[r4 + 1]);
+                v[r4 + 2] = fmaf(-l.z, xq, v[r4 + 2]);
+                v[r4 + 3] = fmaf(-l.w, xq, v[r4 + 3]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 63; ++q) {
+            const float xq = v[q];
+#pragma unroll
+            for (int r4 = (q + 1) & ~3; r4 < 64; r4 += 4) {
+                const float4 l = tl_L4[(64 * h + q) * (M / 4) + (64 * h + r4) / 4];
+                if (r4 > q) v[r4] = fmaf(-l.x, xq, v[r4]);
+                if (r4 + 1 > q) v[r4 + 1] = fmaf(-l.y, xq, v[r4 + 1]);
+                if (r4 + 2 > q) v[r4 + 2] = fmaf(-l.z, xq, v[r4 + 2]);
+                if (r4 + 3 > q) v[r4 + 3] = fmaf(-l.w, xq, v[r4 + 3]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 64; ++r) Xs[(64 * h + r) * TRSM_LEAF_THREADS + tid] = v[r];
+    }
+    if (!live) return;
+#pragma unroll 8
+    for (int r = 0; r < m; ++r) x[(size_t)r * n] = Xs[r * TRSM_LEAF_THREADS + tid];
 }
 
 // ------------------------------------------------------------------ solve kernels
@@ -1073,8 +1117,20 @@ static int rec_trsm(obem_ctx *c, int r0, int m, int c0, int nc, cudaStream_t s)
     const int n = c->nsys;
     float *A = c->d_LU;
     if (nc <= 0 || m <= 0) return OBEM_OK;
-    if (m <= LU_NB) {
-        trsm_range_kernel<<<(nc + TRSW_WARPS - 1) / TRSW_WARPS, TRSW_WARPS * 32, 0, s>>>(A, n, r0, m, c0, nc);
+    if (m <= TRSM_LEAF) {
+        const int nb = (nc + TRSM_LEAF_THREADS - 1) / TRSM_LEAF_THREADS;
+        static bool attr = false;
+        if (!attr) {
+            OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)trsm_leaf_smem<64>()));
+            OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)trsm_leaf_smem<128>()));
+            attr = true;
+        }
+        if (m <= 64)
+            trsm_leaf_kernel<64><<<nb, TRSM_LEAF_THREADS, trsm_leaf_smem<64>(), s>>>(A, n, r0, m, c0, nc);
+        else
+            trsm_leaf_kernel<128><<<nb, TRSM_LEAF_THREADS, trsm_leaf_smem<128>(), s>>>(A, n, r0, m, c0, nc);
         OBEM_LAUNCH(c);
         return OBEM_OK;
     }
@@ -1091,7 +1147,7 @@ static int rec_trsm(obem_ctx *c, int r0, int m, int c0, int nc, cudaStream_t s)
 // rec_lu / rec_trsm issue, so that the scratch is reserved once.
 static void rec_trsm_sizes(int m, int nc, size_t &a, size_t &b)
 {
-    if (nc <= 0 || m <= LU_NB) return;
+    if (nc <= 0 || m <= TRSM_LEAF) return;
     const int m1 = rec_split(m);
     const size_t k8 = ((size_t)m1 + 7) / 8 * 8;
     a = a > (size_t)(m - m1) * k8 ? a : (size_t)(m - m1) * k8;
