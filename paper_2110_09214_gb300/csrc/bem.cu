@@ -618,6 +618,7 @@ __device__ __forceinline__ void load_block(float (*T)[LU_NB + 1], const float *M
 // them).
 #define TRSM_LEAF 128
 #define TRSM_LEAF_THREADS 128
+__device__ __forceinline__ unsigned tl_smem(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 template <int M>
 constexpr size_t trsm_leaf_smem() { return sizeof(float) * (size_t)M * (M + TRSM_LEAF_THREADS); }
 template <int M>
@@ -628,15 +629,29 @@ trsm_leaf_kernel(float *A, int n, int r0, int m, int c0, int nc)
     float *Lt = (float *)tl_L4;
     float *Xs = Lt + M * M;                      // [M][TRSM_LEAF_THREADS]
     const int tid = threadIdx.x;
-    for (int t = tid; t < M * M; t += blockDim.x) {
-        const int r = t / M, q = t % M;           // coalesced over q
-        Lt[q * M + r] = (r < m && q < r) ? A[(size_t)(r0 + r) * n + r0 + q] : 0.f;
-    }
     const int col = blockIdx.x * TRSM_LEAF_THREADS + tid;
     const bool live = col < nc;
     float *x = A + (size_t)r0 * n + c0 + col;
-#pragma unroll 8
-    for (int r = 0; r < M; ++r) Xs[r * TRSM_LEAF_THREADS + tid] = (live && r < m) ? x[(size_t)r * n] : 0.f;
+    // every load of the block in flight at once: 4-byte asynchronous copies
+    // into shared memory (a zero-size source writes a zero).  L: lanes take
+    // consecutive rows (conflict-free transposed stores); X: lanes take
+    // consecutive columns (coalesced).
+    for (int t = tid; t < M * M; t += blockDim.x) {
+        const int r = t % M, q = t / M;
+        const bool in = r < m && q < r;
+        const float *src = in ? A + (size_t)(r0 + r) * n + r0 + q : A;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tl_smem(&Lt[q * M + r])), "l"(src),
+                     "r"(in ? 4 : 0)
+                     : "memory");
+    }
+    for (int r = 0; r < M; ++r) {
+        const bool in = live && r < m;
+        const float *src = in ? x + (size_t)r * n : A;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tl_smem(&Xs[r * TRSM_LEAF_THREADS + tid])),
+                     "l"(src), "r"(in ? 4 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     // 64 rows at a time in registers: the rows of the earlier blocks (already
     // solved, back in shared memory) first, then the block's own triangle
