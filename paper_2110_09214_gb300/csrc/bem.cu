@@ -14,7 +14,8 @@
 //                       panel_kernel   cooperative: one row chunk per CTA held
 //                                      in shared memory, one bounded exchange
 //                                      of pivot candidates per column
-//                       laswp_kernel   the panel's row swaps on whole rows
+//                       laswp_*        the panel's row swaps on whole rows
+//                                      (plan, gather to scratch, scatter)
 //                     BF16 (OBEM_LU_BF16): recursive (rec_lu / rec_trsm), every
 //                       trailing update and off-diagonal TRSM block a
 //                       hand-written tcgen05 GEMM (lu_tc.cu: BF16 operands,
@@ -198,6 +199,7 @@ __global__ void equilibrate_kernel(float *A, int n, double *rowscale, double *ro
 // records [2][PAN_MAXG] (64-bit), gdiag [2][LU_NB], candidate rows [2][PAN_MAXG][LU_NB]
 #define PAN_REC_FLOATS (4 * PAN_MAXG)
 #define PAN_SCRATCH_FLOATS (PAN_REC_FLOATS + 2 * LU_NB + 2 * PAN_MAXG * LU_NB)
+#define PAN_PLAN_FLOATS 260     // the row swaps' plan (1 + 4 LU_NB ints, padded to 16 bytes)
 
 __device__ __forceinline__ unsigned long long gb_now()
 {
@@ -483,29 +485,33 @@ panel_kernel(PanelArgs a)
 }
 
 // The panel's kb row swaps (piv[k .. k + kb)) applied to the columns outside
-// the panel, unless the factorisation's status (flag[0]) records a failure.  The rows they touch -- the kb panel rows and the distinct pivot
-// rows below the panel, at most 2 kb -- are loaded once per column (all loads
-// in flight), permuted in shared memory by the swaps in order, and stored back
-// (swapping in global memory one pivot after the other made every swap wait
-// for the previous one's stores).
-#define LS_COLS 64
-#define LS_RG 4                 // row groups per column
-__global__ void __launch_bounds__(LS_COLS * LS_RG) laswp_kernel(float *A, int n, int k, int kb, const int *piv,
-                                                         int *flag)
+// the panel, unless the factorisation's status (flag[0]) records a failure,
+// in three launches: laswp_plan_kernel lists the rows the swaps touch (the kb
+// panel rows and the distinct pivot rows below the panel, at most 2 kb) and,
+// for each, the touched row whose content it receives (the swaps undone in
+// reverse order, independently per row); laswp_gather_kernel copies the
+// touched rows whole into a scratch block, laswp_scatter_kernel writes each
+// receiving row from it.  Whole-row copies stream at the HBM rate; a
+// single-pass permutation in shared memory (every block holding a column
+// slice of all touched rows) ran at a fifth of it.
+#define LS_PLAN_INTS (1 + 4 * LU_NB)        // m, rows[2 LU_NB], src[2 LU_NB]
+__global__ void __launch_bounds__(LU_NB) laswp_plan_kernel(int k, int kb, const int *piv, int *flag, int *plan)
 {
     // the panel's arrival counter, zeroed for the next panel
-    if (blockIdx.x == 0 && threadIdx.x == 0) flag[1] = 0;
-    // a panel that stopped (zero pivot, barrier timeout) may have left
+    if (threadIdx.x == 0) flag[1] = 0;
+    // a panel that stopped (zero pivot, a wait that ran out) may have left
     // pivots unwritten: no swaps then
-    if (*(volatile const int *)flag != 0) return;
+    if (*(volatile const int *)flag != 0) {
+        if (threadIdx.x == 0) plan[0] = 0;
+        return;
+    }
     __shared__ int s_piv[LU_NB], s_pos[LU_NB], s_row[2 * LU_NB];
     __shared__ unsigned s_first[LU_NB / 32];
-    __shared__ float s_v[2 * LU_NB][LS_COLS + 1];
     const int tid = threadIdx.x, lane = tid & 31;
     // the position of every swap's pivot row among the touched rows: panel
     // rows first, then the pivot rows below the panel by first appearance
     const int p = tid < kb ? piv[k + tid] : -1;
-    if (tid < LU_NB) s_piv[tid] = p;
+    s_piv[tid] = p;
     __syncthreads();
     int f = tid;
     if (tid < kb && p >= k + kb)
@@ -513,7 +519,7 @@ __global__ void __launch_bounds__(LS_COLS * LS_RG) laswp_kernel(float *A, int n,
             if (s_piv[q] == p) { f = q; break; }
     const bool first = tid < kb && p >= k + kb && f == tid;
     const unsigned bal = __ballot_sync(0xffffffffu, first);
-    if (lane == 0 && tid < LU_NB) s_first[tid >> 5] = bal;
+    if (lane == 0) s_first[tid >> 5] = bal;
     __syncthreads();
     const unsigned long long mask = (unsigned long long)s_first[0] | ((unsigned long long)s_first[1] << 32);
     if (tid < kb) {
@@ -523,38 +529,56 @@ __global__ void __launch_bounds__(LS_COLS * LS_RG) laswp_kernel(float *A, int n,
     if (first) s_row[kb + __popcll(mask & ((1ull << tid) - 1ull))] = p;
     const int m = kb + __popcll(mask);
     __syncthreads();
-    // 64 columns x LS_RG row groups: every thread loads and stores rows
-    // rg, rg + LS_RG, ... of its column (more loads in flight per SM), the
-    // swaps run one thread per column
-    const int cl = tid & (LS_COLS - 1), rg = tid / LS_COLS;
-    const int c = blockIdx.x * LS_COLS + cl;
-    const bool live = c < n && !(c >= k && c < k + kb);
-    if (live) {
-        float v[2 * LU_NB / LS_RG];
-#pragma unroll
-        for (int u = 0; u < 2 * LU_NB / LS_RG; ++u) {
-            const int q = rg + LS_RG * u;
-            v[u] = q < m ? A[(size_t)s_row[q] * n + c] : 0.f;
+    // the touched row whose content ends in touched row t: the swaps
+    // (position q <-> s_pos[q], q = 0 .. kb-1, in order) undone in reverse
+    for (int t = tid; t < m; t += blockDim.x) {
+        int j = t;
+        for (int q = kb - 1; q >= 0; --q) {
+            const int pq = s_pos[q];
+            j = j == q ? pq : (j == pq ? q : j);
         }
-#pragma unroll
-        for (int u = 0; u < 2 * LU_NB / LS_RG; ++u) {
-            const int q = rg + LS_RG * u;
-            if (q < m) s_v[q][cl] = v[u];
-        }
+        plan[1 + t] = s_row[t];
+        plan[1 + 2 * LU_NB + t] = j;
     }
-    __syncthreads();
-    if (live && rg == 0)
-        for (int q = 0; q < kb; ++q) {
-            const int r = s_pos[q];
-            if (r != q) {
-                const float t = s_v[q][cl];
-                s_v[q][cl] = s_v[r][cl];
-                s_v[r][cl] = t;
-            }
-        }
-    __syncthreads();
-    if (live)
-        for (int q = rg; q < m; q += LS_RG) A[(size_t)s_row[q] * n + c] = s_v[q][cl];
+    if (tid == 0) plan[0] = m;
+}
+
+// S[q][:] = A[rows[q]][:] for the touched rows q < m (grid y: q)
+__global__ void laswp_gather_kernel(const float *__restrict__ A, int n, const int *plan, float *__restrict__ S)
+{
+    const int q = blockIdx.y;
+    if (q >= plan[0]) return;
+    const float *a = A + (size_t)plan[1 + q] * n;
+    float *d = S + (size_t)q * n;
+    const int stride = gridDim.x * blockDim.x;
+    if ((n & 3) == 0) {
+        for (int c4 = blockIdx.x * blockDim.x + threadIdx.x; c4 < n / 4; c4 += stride)
+            ((float4 *)d)[c4] = __ldcs((const float4 *)a + c4);
+    } else {
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) d[c] = __ldcs(a + c);
+    }
+}
+
+// A[rows[t]][c] = S[src[t]][c] for the touched rows t < m that receive
+// another row, outside the panel's own columns [k, k + kb) (the panel kernel
+// already swapped those)
+__global__ void laswp_scatter_kernel(float *__restrict__ A, int n, int k, int kb, const int *plan,
+                                     const float *__restrict__ S)
+{
+    const int t = blockIdx.y;
+    if (t >= plan[0]) return;
+    const int sq = plan[1 + 2 * LU_NB + t];
+    if (sq == t) return;
+    float *d = A + (size_t)plan[1 + t] * n;
+    const float *a = S + (size_t)sq * n;
+    const int stride = gridDim.x * blockDim.x;
+    if ((n & 3) == 0 && (k & 3) == 0 && ((k + kb) & 3) == 0) {
+        for (int c4 = blockIdx.x * blockDim.x + threadIdx.x; c4 < n / 4; c4 += stride)
+            if (4 * c4 < k || 4 * c4 >= k + kb) ((float4 *)d)[c4] = __ldcs((const float4 *)a + c4);
+    } else {
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride)
+            if (c < k || c >= k + kb) d[c] = __ldcs(a + c);
+    }
 }
 
 // U12 = L11^-1 A12 with L11 unit lower triangular (kb x kb); a CTA of
@@ -1077,6 +1101,8 @@ static int gemm_update(obem_ctx *c, int precision, float *A, int n, int k, int k
 // followed by its row swaps on every other column.
 struct PanelScratch {
     float *cval, *crows, *gdiag;    // cval: the 2 x PAN_MAXG 64-bit candidate records
+    int *plan;                      // the row swaps' plan (LS_PLAN_INTS)
+    float *rows;                    // [2 LU_NB][n] the touched rows during the swaps
     int nsm;
 };
 
@@ -1112,7 +1138,10 @@ static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaS
     pa.flag = c->d_flag; pa.rec = (unsigned long long *)P.cval; pa.crows = P.crows; pa.gdiag = P.gdiag;
     void *args[] = {&pa};
     OBEM_CUDA(c, cudaLaunchCooperativeKernel((void *)panel_kernel, dim3(G), dim3(256), args, smem, s));
-    laswp_kernel<<<(n + LS_COLS - 1) / LS_COLS, LS_COLS * LS_RG, 0, s>>>(c->d_LU, n, k, kb, c->d_piv, c->d_flag);
+    laswp_plan_kernel<<<1, LU_NB, 0, s>>>(k, kb, c->d_piv, c->d_flag, P.plan);
+    const dim3 lg(n / 1024 + 1 < 64 ? n / 1024 + 1 : 64, 2 * LU_NB);
+    laswp_gather_kernel<<<lg, 256, 0, s>>>(c->d_LU, n, P.plan, P.rows);
+    laswp_scatter_kernel<<<lg, 256, 0, s>>>(c->d_LU, n, k, kb, P.plan, P.rows);
     OBEM_LAUNCH(c);
     return OBEM_OK;
 }
@@ -1226,7 +1255,8 @@ static int alloc_system(obem_ctx *c, int n)
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_work64, sizeof(double) * (4 * (size_t)n + 8)));
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_work32, sizeof(float) * (2 * (size_t)n + 4096)));
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_flag, sizeof(int) * 8));
-    OBEM_CUDA(c, cudaMalloc((void **)&c->d_panel, sizeof(float) * PAN_SCRATCH_FLOATS));
+    OBEM_CUDA(c, cudaMalloc((void **)&c->d_panel,
+                            sizeof(float) * (PAN_SCRATCH_FLOATS + PAN_PLAN_FLOATS + 2 * (size_t)LU_NB * n)));
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_perm, sizeof(int) * n));
     OBEM_CUDA(c, cudaMalloc((void **)&c->d_trsv, sizeof(int) * ((size_t)n / TS_R + 16)));
     OBEM_CUDA(c, cudaMemset(c->d_trsv, 0, sizeof(int) * ((size_t)n / TS_R + 16)));
@@ -1308,6 +1338,8 @@ static int factor_system(obem_ctx *c, int precision, cudaStream_t s)
     PS.cval = c->d_panel;
     PS.gdiag = c->d_panel + PAN_REC_FLOATS;
     PS.crows = c->d_panel + PAN_REC_FLOATS + 2 * LU_NB;
+    PS.plan = (int *)(c->d_panel + PAN_SCRATCH_FLOATS);
+    PS.rows = c->d_panel + PAN_SCRATCH_FLOATS + PAN_PLAN_FLOATS;
     PS.nsm = nsm;
     if (precision == OBEM_LU_BF16) {
         // recursive factorisation, trailing updates on the tensor cores
