@@ -716,6 +716,73 @@ trsm_leaf_kernel(float *A, int n, int r0, int m, int c0, int nc)
     for (int r = 0; r < m; ++r) x[(size_t)r * n] = Xs[r * TRSM_LEAF_THREADS + tid];
 }
 
+// The same leaf solve for narrow X (few blocks: the latency of one block
+// decides): one warp per 4 columns, lane l holding rows l, l + 32, ... of
+// them in registers, L row-major in shared memory (padded: the column reads
+// are conflict-free), x[q] broadcast by a shuffle at step q.  Same updates
+// in the same order as trsm_leaf_kernel (the results are identical).
+#define TL2_C 4
+#define TL2_W 8
+#define TL2_BC (TL2_C * TL2_W)
+template <int M>
+constexpr size_t trsm_leaf2_smem() { return sizeof(float) * ((size_t)M * (M + 1) + (size_t)M * (TL2_BC + 1)); }
+template <int M>
+__global__ void __launch_bounds__(TL2_W * 32)
+trsm_leaf2_kernel(float *A, int n, int r0, int m, int c0, int nc)
+{
+    constexpr int RL = M / 32;
+    extern __shared__ float tl2_s[];
+    float *Ls = tl2_s;                    // [M][M + 1]: L row-major, padded (column reads conflict-free)
+    float *Xs = tl2_s + M * (M + 1);      // [M][TL2_BC + 1]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cb = blockIdx.x * TL2_BC;
+    for (int t = tid; t < M * M; t += blockDim.x) {
+        const int r = t / M, q = t % M;           // coalesced over q
+        const bool in = r < m && q < r;
+        const float *src = in ? A + (size_t)(r0 + r) * n + r0 + q : A;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tl_smem(&Ls[r * (M + 1) + q])), "l"(src),
+                     "r"(in ? 4 : 0)
+                     : "memory");
+    }
+    for (int e = tid; e < M * TL2_BC; e += blockDim.x) {
+        const int r = e / TL2_BC, c = e % TL2_BC;
+        const bool in = r < m && cb + c < nc;
+        const float *src = in ? A + (size_t)(r0 + r) * n + c0 + cb + c : A;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tl_smem(&Xs[r * (TL2_BC + 1) + c])),
+                     "l"(src), "r"(in ? 4 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    float v[TL2_C][RL];
+#pragma unroll
+    for (int j = 0; j < TL2_C; ++j)
+#pragma unroll
+        for (int i = 0; i < RL; ++i) v[j][i] = Xs[(32 * i + lane) * (TL2_BC + 1) + warp * TL2_C + j];
+#pragma unroll
+    for (int q = 0; q < M - 1; ++q) {
+        float lq[RL];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) lq[i] = Ls[(32 * i + lane) * (M + 1) + q];
+#pragma unroll
+        for (int j = 0; j < TL2_C; ++j) {
+            const float xq = __shfl_sync(0xffffffffu, v[j][q / 32], q % 32);
+#pragma unroll
+            for (int i = 0; i < RL; ++i)
+                if (32 * i + 31 > q && 32 * i + lane > q) v[j][i] = fmaf(-lq[i], xq, v[j][i]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < TL2_C; ++j)
+#pragma unroll
+        for (int i = 0; i < RL; ++i) Xs[(32 * i + lane) * (TL2_BC + 1) + warp * TL2_C + j] = v[j][i];
+    __syncthreads();
+    for (int e = tid; e < M * TL2_BC; e += blockDim.x) {
+        const int r = e / TL2_BC, c = e % TL2_BC;
+        if (r < m && cb + c < nc) A[(size_t)(r0 + r) * n + c0 + cb + c] = Xs[r * (TL2_BC + 1) + c];
+    }
+}
+
 // ------------------------------------------------------------------ solve kernels
 // b_i = rowscale_i * (V_group or free density) + drhs_i  (drhs unscaled input)
 __global__ void rhs_kernel(const int *kind, const int *group, const double *gv, const float *sigma_free,
@@ -1169,12 +1236,24 @@ static int rec_trsm(obem_ctx *c, int r0, int m, int c0, int nc, cudaStream_t s)
                                               (int)trsm_leaf_smem<64>()));
             OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)trsm_leaf_smem<128>()));
+            OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf2_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)trsm_leaf2_smem<64>()));
+            OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf2_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)trsm_leaf2_smem<128>()));
             attr = true;
         }
-        if (m <= 64)
+        const int nb2 = (nc + TL2_BC - 1) / TL2_BC;
+        if (nc <= 8192) {
+            // narrow: the warp-per-columns form has the shorter block latency
+            if (m <= 64)
+                trsm_leaf2_kernel<64><<<nb2, TL2_W * 32, trsm_leaf2_smem<64>(), s>>>(A, n, r0, m, c0, nc);
+            else
+                trsm_leaf2_kernel<128><<<nb2, TL2_W * 32, trsm_leaf2_smem<128>(), s>>>(A, n, r0, m, c0, nc);
+        } else if (m <= 64) {
             trsm_leaf_kernel<64><<<nb, TRSM_LEAF_THREADS, trsm_leaf_smem<64>(), s>>>(A, n, r0, m, c0, nc);
-        else
+        } else {
             trsm_leaf_kernel<128><<<nb, TRSM_LEAF_THREADS, trsm_leaf_smem<128>(), s>>>(A, n, r0, m, c0, nc);
+        }
         OBEM_LAUNCH(c);
         return OBEM_OK;
     }
