@@ -513,10 +513,11 @@ __global__ void __launch_bounds__(LU_NB) laswp_plan_kernel(int k, int kb, const 
     const int p = tid < kb ? piv[k + tid] : -1;
     s_piv[tid] = p;
     __syncthreads();
+    // the first swap with the same pivot row (all 64 reads in flight)
     int f = tid;
-    if (tid < kb && p >= k + kb)
-        for (int q = 0; q < tid; ++q)
-            if (s_piv[q] == p) { f = q; break; }
+#pragma unroll
+    for (int q = LU_NB - 1; q >= 0; --q)
+        if (q < tid && s_piv[q] == p) f = q;
     const bool first = tid < kb && p >= k + kb && f == tid;
     const unsigned bal = __ballot_sync(0xffffffffu, first);
     if (lane == 0) s_first[tid >> 5] = bal;
@@ -533,8 +534,9 @@ __global__ void __launch_bounds__(LU_NB) laswp_plan_kernel(int k, int kb, const 
     // (position q <-> s_pos[q], q = 0 .. kb-1, in order) undone in reverse
     for (int t = tid; t < m; t += blockDim.x) {
         int j = t;
-        for (int q = kb - 1; q >= 0; --q) {
-            const int pq = s_pos[q];
+#pragma unroll
+        for (int q = LU_NB - 1; q >= 0; --q) {
+            const int pq = q < kb ? s_pos[q] : q;
             j = j == q ? pq : (j == pq ? q : j);
         }
         plan[1 + t] = s_row[t];
