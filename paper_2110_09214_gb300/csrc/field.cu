@@ -1284,6 +1284,10 @@ nbody_kernel(FieldLaunch L)
 #define SY_WARPS (SY_THREADS / 32)
 #define SY_NG (SY_T / 32)      // 32-source groups of a tile (rounds of an item)
 #define SY_CH 16
+#define SY_CH_SMALL 1
+#define SY_SMALL_TILES 32      // sets of at most 32 tiles (32768 charges) use single-item units
+#define SY_CH_MID 4
+#define SY_MID_TILES 256       // and of at most 256 tiles units of 4 items
 #define SY_FOLD 8              // rounds (of 32 sources) between compensated folds
 #define SY_DTILE 256           // staged sources of the d = 0 item
 // The kernel works on positions scaled by 2^40 and charges (k_C q) by 2^80:
@@ -1298,14 +1302,18 @@ nbody_kernel(FieldLaunch L)
 struct SymGeom {
     int n, hmax, nch;
 };
-__host__ __device__ inline SymGeom sym_geom(int nt)
+// CH: items per work unit (SY_CH; SY_CH_SMALL for a set of at most
+// SY_SMALL_TILES tiles, so that its few tile pairs still spread over the SMs)
+template <int CH>
+__host__ __device__ inline SymGeom sym_geom_ch(int nt)
 {
     SymGeom g;
     g.n = (nt + SY_T - 1) / SY_T;
     g.hmax = g.n / 2;
-    g.nch = (g.hmax + 1 + SY_CH - 1) / SY_CH;
+    g.nch = (g.hmax + 1 + CH - 1) / CH;
     return g;
 }
+__host__ __device__ inline SymGeom sym_geom(int nt) { return sym_geom_ch<SY_CH>(nt); }
 // off-diagonal items of row I
 __host__ __device__ inline int sym_h(const SymGeom &g, int I)
 {
@@ -1346,7 +1354,13 @@ size_t obem_sym_pass_jpart_floats(int capacity)
 size_t obem_sym_pass_ipart_floats(int capacity)
 {
     const SymGeom g = sym_geom(capacity);
-    return (size_t)g.n * (g.nch < SY_PASS_CH ? g.nch : SY_PASS_CH) * 8 * SY_T;
+    size_t f = (size_t)g.n * (g.nch < SY_PASS_CH ? g.nch : SY_PASS_CH) * 8 * SY_T;
+    if (g.n <= SY_MID_TILES) {
+        const SymGeom g1 = g.n <= SY_SMALL_TILES ? sym_geom_ch<SY_CH_SMALL>(capacity) : sym_geom_ch<SY_CH_MID>(capacity);
+        const size_t f1 = (size_t)g1.n * (g1.nch < SY_PASS_CH ? g1.nch : SY_PASS_CH) * 8 * SY_T;
+        f = f1 > f ? f1 : f;
+    }
+    return f;
 }
 
 // dynamic shared memory of nbsym_kernel: target-side S and C [NC][SY_NI][SY_THREADS]
@@ -1509,7 +1523,7 @@ __global__ void sym_units_kernel(SymBatch SB)
 
 template <bool B> struct SyBool { static constexpr bool value = B; };
 
-template <bool WANT_V, bool BATCH>
+template <bool WANT_V, bool BATCH, int CH = SY_CH>
 __global__ void __launch_bounds__(SY_THREADS, SY_MINB)
 nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const float *tileq, SymBatch SB, SymPass PS)
 {
@@ -1533,7 +1547,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
     } else {
         nt0 = L.nt_dev ? *L.nt_dev : L.nt;
         if (nt0 <= 0) return;
-        G0 = sym_geom(nt0);
+        G0 = sym_geom_ch<CH>(nt0);
         units = G0.n * max(0, min(PS.kch_n, G0.nch - PS.kch_lo));
     }
     // this launch's units of a row and its slot strides (one set of charges)
@@ -1573,13 +1587,13 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
         if (unit < 0) break;
         const int off = BATCH ? s_off : 0;
         const int lim = BATCH ? off + s_nt : nt0;        // end of the live slots
-        const SymGeom G = BATCH ? sym_geom(s_nt) : G0;
+        const SymGeom G = BATCH ? sym_geom_ch<CH>(s_nt) : G0;
         // this launch's units of row I: all (batch) or the pass's range
         const int kn = BATCH ? G.nch : kn0;
         const int klo = BATCH ? 0 : klo0;
         const int jd = BATCH ? G.hmax + 1 : jd0;
         const int I = unit / kn, kch = klo + unit % kn;
-        const int d0 = kch * SY_CH, d1 = min(d0 + SY_CH, sym_h(G, I) + 1);
+        const int d0 = kch * CH, d1 = min(d0 + CH, sym_h(G, I) + 1);
         const int base = off + I * SY_T;
         // targets of tile I: 8 per thread (k * 128 + tid), four packs
         u64 TX[SY_NP], TY[SY_NP], TZ[SY_NP], QI[SY_NP];
@@ -1780,7 +1794,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
             if (uni) rounds(SyBool<true>{});
             else rounds(SyBool<false>{});
             // the item's source-side sums (S + C) to its own slot
-            float *jp = jpart + (BATCH ? s_joff : 0) + ((size_t)I * jd + (d - klo * SY_CH)) * 4 * SY_T;
+            float *jp = jpart + (BATCH ? s_joff : 0) + ((size_t)I * jd + (d - klo * CH)) * 4 * SY_T;
             for (int l = tid; l < NC * SY_T; l += SY_THREADS) jp[l] = s_jS[l] + s_jC[l];
         }
         // the unit's target-side sums (S and C) to its own slot
@@ -1798,7 +1812,7 @@ nbsym_kernel(FieldLaunch L, float *jpart, float *ipart, int *counter, const floa
 // E_out[t] = init + target-side sums of t's row + minus the source-side sums of
 // every item whose second tile holds t, added in a fixed order (FP64).  t is a
 // slot of the sorted copy; perm[t] the charge it holds.
-template <bool WANT_V>
+template <bool WANT_V, int CH = SY_CH>
 __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float *ipart, int add, const int32_t *perm,
                                   SymBatch SB, SymPass PS)
 {
@@ -1818,14 +1832,14 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
     }
     const int lt = t - off;
     if (lt >= nt) return;
-    const SymGeom G = sym_geom(nt);
+    const SymGeom G = sym_geom_ch<CH>(nt);
     const int T = lt / SY_T, w = lt % SY_T;
     const int o = perm ? perm[t] : t;                  // sorted slot t is charge o
     // this pass's units and diagonals (all of them for a batch)
     const int kn = PS.kch_n ? min(PS.kch_n, G.nch - PS.kch_lo) : G.nch;
     const int klo = PS.kch_n ? PS.kch_lo : 0;
     const int jd = PS.kch_n ? PS.jd : G.hmax + 1;
-    const int dlo = max(1, klo * SY_CH), dhi = min(G.hmax, klo * SY_CH + jd - 1);
+    const int dlo = max(1, klo * CH), dhi = min(G.hmax, klo * CH + jd - 1);
     double e[4] = {0.0, 0.0, 0.0, 0.0};
     if (!PS.first) {
         const double *a = PS.acc + 4 * (size_t)t;
@@ -1855,7 +1869,7 @@ __global__ void nbsym_fold_kernel(FieldLaunch L, const float *jpart, const float
             const int d = d0 + u;
             const int I = T - d >= 0 ? T - d : T - d + G.n;
             const bool ok = d <= dhi && d <= sym_h(G, I);
-            const float *jp = jpart + joff + ((size_t)I * jd + (ok ? d - klo * SY_CH : 0)) * 4 * SY_T;
+            const float *jp = jpart + joff + ((size_t)I * jd + (ok ? d - klo * CH : 0)) * 4 * SY_T;
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[u][c] = ok ? jp[c * SY_T + w] : 0.f;
         }
@@ -1880,9 +1894,11 @@ int obem_sym_grid(int device)
     int sms = 0, best = 0, occ = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     void (*ks[])(FieldLaunch, float *, float *, int *, const float *, SymBatch, SymPass) = {
-        nbsym_kernel<true, false>, nbsym_kernel<false, false>, nbsym_kernel<false, true>};
-    const size_t sm[] = {sym_smem(4), sym_smem(3), sym_smem(3)};
-    for (int q = 0; q < 3; ++q) {
+        nbsym_kernel<true, false>, nbsym_kernel<false, false>, nbsym_kernel<false, true>,
+        nbsym_kernel<true, false, SY_CH_SMALL>, nbsym_kernel<false, false, SY_CH_SMALL>,
+        nbsym_kernel<true, false, SY_CH_MID>, nbsym_kernel<false, false, SY_CH_MID>};
+    const size_t sm[] = {sym_smem(4), sym_smem(3), sym_smem(3), sym_smem(4), sym_smem(3), sym_smem(4), sym_smem(3)};
+    for (int q = 0; q < 7; ++q) {
         if (cudaFuncSetAttribute(ks[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]) != cudaSuccess)
             return 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks[q], SY_THREADS, sm[q]) != cudaSuccess) return 0;
@@ -2004,32 +2020,46 @@ int obem_launch_field(obem_ctx *ctx, const FieldLaunch &L, int capacity_targets,
             // in order into a per-charge FP64 accumulator: partial sums O(N)
             // (a fixed pass size keeps the summation order, and so the bits,
             // independent of the memory available)
-            const SymGeom Gc = sym_geom(capacity_targets);
+            // contexts for at most SY_SMALL_TILES / SY_MID_TILES tiles take
+            // units of fewer items, so that a set's few tile pairs still
+            // spread over the SMs (separate instantiations: the large-set
+            // kernel is untouched); chosen by the capacity the partial-sum
+            // scratch was sized for (the live count is on the device)
+            const int ntile = sym_geom(ctx->sym_cap).n;
+            const int ch = ntile <= SY_SMALL_TILES ? SY_CH_SMALL : (ntile <= SY_MID_TILES ? SY_CH_MID : SY_CH);
+            const SymGeom Gc = ch == SY_CH_SMALL ? sym_geom_ch<SY_CH_SMALL>(capacity_targets)
+                               : ch == SY_CH_MID ? sym_geom_ch<SY_CH_MID>(capacity_targets) : sym_geom(capacity_targets);
             const int npass = (Gc.nch + SY_PASS_CH - 1) / SY_PASS_CH;
             const dim3 sg(ctx->sym_grid);
             const int fb = (capacity_targets + 255) / 256;
+            typedef void (*SymK)(FieldLaunch, float *, float *, int *, const float *, SymBatch, SymPass);
+            typedef void (*FoldK)(FieldLaunch, const float *, const float *, int, const int32_t *, SymBatch, SymPass);
+            const SymK kern = L.want_v ? (ch == SY_CH_SMALL ? nbsym_kernel<true, false, SY_CH_SMALL>
+                                          : ch == SY_CH_MID ? nbsym_kernel<true, false, SY_CH_MID>
+                                                            : nbsym_kernel<true, false>)
+                                       : (ch == SY_CH_SMALL ? nbsym_kernel<false, false, SY_CH_SMALL>
+                                          : ch == SY_CH_MID ? nbsym_kernel<false, false, SY_CH_MID>
+                                                            : nbsym_kernel<false, false>);
+            const FoldK fold = L.want_v ? (ch == SY_CH_SMALL ? nbsym_fold_kernel<true, SY_CH_SMALL>
+                                           : ch == SY_CH_MID ? nbsym_fold_kernel<true, SY_CH_MID>
+                                                             : nbsym_fold_kernel<true>)
+                                        : (ch == SY_CH_SMALL ? nbsym_fold_kernel<false, SY_CH_SMALL>
+                                           : ch == SY_CH_MID ? nbsym_fold_kernel<false, SY_CH_MID>
+                                                             : nbsym_fold_kernel<false>);
+            const size_t ksmem = sym_smem(L.want_v ? 4 : 3);
             for (int pz = 0; pz < npass; ++pz) {
                 SymPass PS;
                 PS.kch_lo = pz * SY_PASS_CH;
                 PS.kch_n = SY_PASS_CH;
-                PS.jd = Gc.hmax + 1 < SY_PASS_CH * SY_CH ? Gc.hmax + 1 : SY_PASS_CH * SY_CH;   // as allocated
+                PS.jd = Gc.hmax + 1 < SY_PASS_CH * ch ? Gc.hmax + 1 : SY_PASS_CH * ch;   // within the allocation
                 PS.first = pz == 0;
                 PS.last = pz == npass - 1;
                 PS.acc = ctx->sym_acc;
                 OBEM_CUDA(ctx, cudaMemsetAsync(ctx->sym_counter, 0, sizeof(int), s));
-                if (L.want_v)
-                    nbsym_kernel<true, false><<<sg, SY_THREADS, sym_smem(4), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart,
-                                                                          ctx->sym_counter, ctx->sym_tileq, SB, PS);
-                else
-                    nbsym_kernel<false, false><<<sg, SY_THREADS, sym_smem(3), s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart,
-                                                                           ctx->sym_counter, ctx->sym_tileq, SB, PS);
+                kern<<<sg, SY_THREADS, ksmem, s>>>(Ls, ctx->sym_jpart, ctx->sym_ipart, ctx->sym_counter, ctx->sym_tileq,
+                                                   SB, PS);
                 OBEM_LAUNCH(ctx);
-                if (L.want_v)
-                    nbsym_fold_kernel<true><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0,
-                                                                ctx->sym_perm, SB, PS);
-                else
-                    nbsym_fold_kernel<false><<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0,
-                                                                 ctx->sym_perm, SB, PS);
+                fold<<<fb, 256, 0, s>>>(L, ctx->sym_jpart, ctx->sym_ipart, add ? 1 : 0, ctx->sym_perm, SB, PS);
                 OBEM_LAUNCH(ctx);
             }
             if (L.events) ctx->launches += 4 + 2 * npass;
