@@ -98,3 +98,31 @@ def test_dense_calls_need_a_context_without_mesh():
         assert e.value.code == obem.OBEM_ERR_STATE
     finally:
         obem.obem_destroy(ctx)
+
+
+def test_bf16_factorisation_at_20480_against_a_known_solution():
+    """A system of order 20,480 (made on the GPU: P (2 I + G / sqrt(n)),
+    pivoting at every column) with a known solution x: b = A x in FP64.  At
+    this order the recursion's TRSM leaves meet right-hand sides wider than
+    8192 columns (the thread-per-column leaf) as well as narrow ones (the
+    warp-per-columns leaf), and the panels span up to 135 rows per CTA.  The
+    refined solution must reproduce x: its error is at most the condition
+    number (about 3) times the backward error."""
+    n = 20480
+    g = torch.Generator(device="cuda").manual_seed(7)
+    M = torch.randn((n, n), device="cuda", generator=g) / n ** 0.5
+    M.diagonal().add_(2.0)
+    A = M[torch.randperm(n, device="cuda", generator=g)].contiguous()
+    del M
+    x_true = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    b = A.double() @ x_true
+    ctx = obem.obem_create(capacity=8, dt=1e-12)
+    try:
+        obem.obem_dense_factor(ctx, A, obem.OBEM_LU_BF16)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        rep = obem.obem_dense_solve(ctx, b, x)
+    finally:
+        obem.obem_destroy(ctx)
+    assert rep["status"] == 0 and rep["backward_error"] < 1e-12
+    err = (x - x_true).abs().max().item() / x_true.abs().max().item()
+    assert err < 1e-11, err

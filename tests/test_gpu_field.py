@@ -325,3 +325,35 @@ def test_four_million_charges_on_the_symmetric_kernel():
     assert guarded_rel_err(one[idx, :3], ref) <= FIELD_TOL
     assert guarded_rel_err(got[:, :3], one[:, :3]) <= 2 * FIELD_TOL
     assert not np.array_equal(got, one)
+
+
+@pytest.mark.parametrize("n,cap", [(10_000, 17_024), (33_000, 33_000), (100_000, 161_024)])
+def test_symmetric_kernel_work_unit_sizes(n, cap):
+    """The symmetric all-pairs kernel takes units of one tile pair in
+    contexts of at most 32 tiles of capacity and of 4 tile pairs up to 256
+    tiles (units of 16 above).  Here the live count is below the capacity,
+    as in an avalanche that grows: the field (and potential) at 512 sampled
+    charges against the oracle, and at every charge against the one-sided
+    kernel (a context of small capacity; another summation order, so within
+    the tolerance but not bit for bit)."""
+    rng = np.random.default_rng(n)
+    src = _charges(rng, n, pairs=n // 50)
+    ctx = _ctx(cap=cap)
+    try:
+        got = _gpu_field(ctx, src, src, self_exclude=True)
+    finally:
+        obem.obem_destroy(ctx)
+    small = _ctx(cap=16)
+    try:
+        one = _gpu_field(small, src, src, self_exclude=True)
+    finally:
+        obem.obem_destroy(small)
+    assert np.all(np.isfinite(got))
+    idx = np.sort(rng.choice(n, 512, replace=False))
+    pts = src[idx, :3].astype(np.float64)
+    # a sampled charge's own source sits at distance 0, which the oracle skips
+    ref_E, ref_V = oracle.nbody_field(pts, src.astype(np.float64), False)
+    Vabs = oracle.nbody_field(pts, np.abs(src.astype(np.float64)), False)[1]
+    assert guarded_rel_err(got[idx, :3], ref_E) <= FIELD_TOL
+    assert potential_err(got[idx, 3], ref_V, Vabs) <= FIELD_TOL
+    assert guarded_rel_err(got[:, :3], one[:, :3]) <= 2 * FIELD_TOL
