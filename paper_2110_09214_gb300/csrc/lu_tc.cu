@@ -5,16 +5,22 @@
 //   C[M x N] -= A[M x K] B[K x N]      C, A, B: FP32 row-major sub-blocks
 //
 // The operands are rounded to BF16 (round to nearest even) into K-major
-// scratch (A as is, B transposed), then one CTA per 128 x 256 tile of C (tiles
+// scratch (A as is, B transposed), then one CTA per 256 x 256 tile of C (tiles
 // ordered in groups of 8 row tiles for L2 reuse) runs
 // a TMA -> shared memory -> tcgen05.mma pipeline:
-//   warp 0, one lane   TMA producer: 64-wide K slices of A (128 rows) and B
-//                      (256 rows) into a 4-stage ring, 128B-swizzled
-//   warp 1, one lane   MMA issuer: 4 x tcgen05.mma.kind::f16 (M 128, N 256,
-//                      K 16) per slice, FP32 accumulation in tensor memory
-//                      (256 columns x 128 lanes); tcgen05.commit frees a stage
-//   warps 0-3          epilogue: tcgen05.ld of their 32 lanes, through shared
-//                      memory, C -= D with coalesced row accesses
+//   warp 0, one lane   TMA producer: 64-wide K slices of A (256 rows) and B
+//                      (256 rows) into a 3-stage ring, 128B-swizzled
+//   warp 1, one lane   MMA issuer: per slice 4 K steps x 2 tcgen05.mma.kind::f16
+//                      (M 128, N 256, K 16), one per half of the tile's rows,
+//                      both on the stage's B; FP32 accumulation in tensor
+//                      memory (two accumulators of 256 columns x 128 lanes: all
+//                      512 columns); tcgen05.commit frees a stage
+//   warps 0-3          epilogue: tcgen05.ld of their 32 lanes of each
+//                      accumulator, through shared memory, C -= D with
+//                      coalesced row accesses
+// The 256-row tile halves the operand bytes each SM fetches per flop against
+// a 128-row one (the 128 x 256 tiles kept the tensor pipe about half busy,
+// fed from L2).
 // Every wait on an mbarrier is bounded; a wait that runs out records
 // OBEM_ERR_TIMEOUT in *err, the kernel lets its issued copies and MMAs finish
 // (bounded again), frees its tensor memory and returns.
@@ -24,11 +30,13 @@
 #include "obem_internal.cuh"
 
 namespace {
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 128;
-constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;               // 16 KB
+constexpr int TC_MM = 128;                                        // rows of one MMA and of one accumulator
+constexpr int TC_BM = 256, TC_BN = 256, TC_BK = 64, TC_STAGES = 3, TC_THREADS = 128;
+constexpr int TC_ACC = TC_BM / TC_MM;                             // accumulators per tile
+constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;               // 32 KB
 constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK * 2;               // 32 KB
 constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr uint32_t TC_TMEM_COLS = TC_ACC * TC_BN;                 // 512: all of the SM's tensor memory
 constexpr int TC_GROUP_M = 8;                                    // row tiles per rasterisation group
 constexpr size_t TC_SMEM = 1024 + (size_t)TC_STAGES * TC_STAGE_BYTES + 256;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
@@ -36,7 +44,7 @@ constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
 // A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                              ((uint32_t)(TC_BM >> 4) << 24);
+                              ((uint32_t)(TC_MM >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t tc_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -218,9 +226,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
             tc_fence_after();
             const uint32_t a0 = tc_smem(sA + s * TC_A_BYTES), b0 = tc_smem(sB + s * TC_B_BYTES);
+            // accumulator a: rows a*128 .. a*128+127 of the tile (their A rows
+            // start a*128 rows = 16 KB into the stage, a whole number of
+            // 1024-byte swizzle atoms) in tensor-memory columns a*256 ..;
+            // both share the stage's B.  A half of the tile past M is skipped.
 #pragma unroll
             for (int j = 0; j < TC_BK / 16; ++j)
-                tc_mma(tmem, tc_desc(a0 + 32 * j), tc_desc(b0 + 32 * j), (kb | j) != 0);
+#pragma unroll
+                for (int a = 0; a < TC_ACC; ++a)
+                    if (a == 0 || m0 + a * TC_MM < M)
+                        tc_mma(tmem + (uint32_t)(a * TC_BN), tc_desc(a0 + (uint32_t)(a * TC_MM * 128) + 32 * j),
+                               tc_desc(b0 + 32 * j), (kb | j) != 0);
             tc_commit(&empty[s]);
         }
         // arrives once every MMA issued above has completed (also on failure)
@@ -234,42 +250,45 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     if (fine && !*(volatile int *)s_fail) {
         float *stage = (float *)sA + warp * 32 * 33;       // pipeline smem is idle now
-        const int rbase = m0 + warp * 32;
-        const int nrow = min(32, M - rbase);
-        // the 32 rows' values of this lane's column, chunk by chunk of 32
-        // columns; the next chunk's loads are in flight while this one is
-        // written back
-        float vn[32];
-        {
-            const int col = n0 + lane;
-            const float *cp = C + (size_t)rbase * ldc + col;
+        for (int acc = 0; acc < TC_ACC; ++acc) {
+            const int rbase = m0 + acc * TC_MM + warp * 32;
+            if (rbase >= M) break;                          // warp-uniform
+            const int nrow = min(32, M - rbase);
+            // the 32 rows' values of this lane's column, chunk by chunk of 32
+            // columns; the next chunk's loads are in flight while this one is
+            // written back
+            float vn[32];
+            {
+                const int col = n0 + lane;
+                const float *cp = C + (size_t)rbase * ldc + col;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) vn[i] = (i < nrow && col < N) ? __ldcg(cp + (size_t)i * ldc) : 0.f;
-        }
-        for (int c = 0; c < TC_BN; c += 32) {
-            if (n0 + c >= N) break;                         // warp-uniform
-            float v[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = vn[i];
-            if (c + 32 < TC_BN && n0 + c + 32 < N) {
-                const int coln = n0 + c + 32 + lane;
-                const float *cpn = C + (size_t)rbase * ldc + coln;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) vn[i] = (i < nrow && coln < N) ? __ldcg(cpn + (size_t)i * ldc) : 0.f;
+                for (int i = 0; i < 32; ++i) vn[i] = (i < nrow && col < N) ? __ldcg(cp + (size_t)i * ldc) : 0.f;
             }
-            uint32_t r[32];
-            tc_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+            for (int c = 0; c < TC_BN; c += 32) {
+                if (n0 + c >= N) break;                     // warp-uniform
+                float v[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
-            __syncwarp();
-            const int col = n0 + c + lane;
-            float *cp = C + (size_t)rbase * ldc + col;
-            if (col < N) {
+                for (int i = 0; i < 32; ++i) v[i] = vn[i];
+                if (c + 32 < TC_BN && n0 + c + 32 < N) {
+                    const int coln = n0 + c + 32 + lane;
+                    const float *cpn = C + (size_t)rbase * ldc + coln;
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    if (i < nrow) __stcg(cp + (size_t)i * ldc, v[i] - stage[i * 33 + lane]);
+                    for (int i = 0; i < 32; ++i) vn[i] = (i < nrow && coln < N) ? __ldcg(cpn + (size_t)i * ldc) : 0.f;
+                }
+                uint32_t r[32];
+                tc_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * TC_BN + c), r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
+                __syncwarp();
+                const int col = n0 + c + lane;
+                float *cp = C + (size_t)rbase * ldc + col;
+                if (col < N) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < nrow) __stcg(cp + (size_t)i * ldc, v[i] - stage[i * 33 + lane]);
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
     } else if (threadIdx.x == 0) {
         atomicExch(err, OBEM_ERR_TIMEOUT);
