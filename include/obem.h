@@ -421,7 +421,7 @@ int obem_dense_solve(obem_ctx *ctx, const double *b, double *x, obem_solve_repor
  * C, A, B: device FP32 row-major arrays with leading dimensions ldc >= N,
  * lda >= K, ldb >= N (elements).  The operands are rounded to BF16 (round to
  * nearest even) and the products accumulated in FP32 by tcgen05.mma in
- * 128 x 256 tiles.  Uses the context's BF16 scratch (grown here: allocates)
+ * 256 x 256 tiles.  Uses the context's BF16 scratch (grown here: allocates)
  * and synchronises `stream`.  OBEM_ERR_ARG for bad sizes; OBEM_ERR_TIMEOUT if
  * a bounded wait of the pipeline ran out (C is then undefined). */
 int obem_tc_gemm(obem_ctx *ctx, float *C, int64_t ldc, const float *A, int64_t lda, const float *B, int64_t ldb,

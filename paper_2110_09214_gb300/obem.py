@@ -363,7 +363,7 @@ def obem_selftest_wait_timeout(ctx, stream=None):
 
 def obem_selftest_waits(ctx, which, stream=None):
     """Failure-detection self-test of bounded device wait `which` (0: LU panel
-    barrier, 1: substitution flags, 2: influence bulk copies); raises unless
+    candidate exchange, 1: substitution flags, 2: influence bulk copies); raises unless
     the wait reported OBEM_ERR_TIMEOUT (see include/obem.h)."""
     _check(ctx, load().obem_selftest_waits(ctx, int(which), _stream(stream)))
 
