@@ -1197,11 +1197,22 @@ static int factor_panel(obem_ctx *c, const PanelScratch &P, int k, int kb, cudaS
     size_t smem = sizeof(float) * (size_t)R * (kb + 1);
     if (smem > 200 * 1024)
         return obem_fail(c, OBEM_ERR_ARG, "LU panel of %d rows does not fit shared memory", rows);
-    OBEM_CUDA(c, cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    OBEM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, 256, smem));
-    if (per_sm * P.nsm < G)
-        return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
+    // host-side queries once, not per panel (they cost tens of microseconds
+    // each, and the factorisation issues a panel every few hundred): the
+    // attribute at the largest panel size; one CTA per SM always fits (at
+    // most 200 KB of shared memory, 48 registers x 256 threads), so the
+    // occupancy is checked only when there are more CTAs than SMs
+    static unsigned long long attr = 0;   // devices done (a bit each)
+    if (!(attr >> (c->device & 63) & 1ull)) {
+        OBEM_CUDA(c, cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr |= 1ull << (c->device & 63);
+    }
+    if (G > P.nsm) {
+        int per_sm = 0;
+        OBEM_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_kernel, 256, smem));
+        if (per_sm * P.nsm < G)
+            return obem_fail(c, OBEM_ERR_CUDA, "LU panel: %d CTAs cannot be co-resident", G);
+    }
     PanelArgs pa;
     pa.A = c->d_LU; pa.n = n; pa.k = k; pa.kb = kb; pa.rows_per_cta = R; pa.piv = c->d_piv;
     pa.flag = c->d_flag; pa.rec = (unsigned long long *)P.cval; pa.crows = P.crows; pa.gdiag = P.gdiag;
@@ -1232,8 +1243,8 @@ static int rec_trsm(obem_ctx *c, int r0, int m, int c0, int nc, cudaStream_t s)
     if (nc <= 0 || m <= 0) return OBEM_OK;
     if (m <= TRSM_LEAF) {
         const int nb = (nc + TRSM_LEAF_THREADS - 1) / TRSM_LEAF_THREADS;
-        static bool attr = false;
-        if (!attr) {
+        static unsigned long long attr = 0;   // devices done (a bit each)
+        if (!(attr >> (c->device & 63) & 1ull)) {
             OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)trsm_leaf_smem<64>()));
             OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1242,7 +1253,7 @@ static int rec_trsm(obem_ctx *c, int r0, int m, int c0, int nc, cudaStream_t s)
                                               (int)trsm_leaf2_smem<64>()));
             OBEM_CUDA(c, cudaFuncSetAttribute(trsm_leaf2_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)trsm_leaf2_smem<128>()));
-            attr = true;
+            attr |= 1ull << (c->device & 63);
         }
         const int nb2 = (nc + TL2_BC - 1) / TL2_BC;
         if (nc <= 8192) {
@@ -1466,13 +1477,13 @@ static int factor_system(obem_ctx *c, int precision, cudaStream_t s)
     }
     // inverses of the diagonal blocks for the one-launch substitutions
     {
-        static bool attr = false;
-        if (!attr) {
+        static unsigned long long attr = 0;   // devices done (a bit each)
+        if (!(attr >> (c->device & 63) & 1ull)) {
             OBEM_CUDA(c, cudaFuncSetAttribute(inv_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)TS_INV_SMEM));
             OBEM_CUDA(c, cudaFuncSetAttribute(trsv_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)TS_SMEM));
-            attr = true;
+            attr |= 1ull << (c->device & 63);
         }
         inv_diag_kernel<<<dim3((n + TS_R - 1) / TS_R, 2), TS_R, TS_INV_SMEM, s>>>(c->d_LU, n, c->d_dinv);
         OBEM_LAUNCH(c);
@@ -1760,11 +1771,11 @@ static int lu_solve_t(obem_ctx *c, float *y, cudaStream_t s)
 {
     const int n = c->nsys, nbk = (n + TS_R - 1) / TS_R;
     int *ticket = c->d_trsv + nbk, *err = ticket + 2;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0;   // devices done (a bit each)
+    if (!(attr >> (c->device & 63) & 1ull)) {
         OBEM_CUDA(c, cudaFuncSetAttribute(trsv_chain_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)TS_T_SMEM));
-        attr = true;
+        attr |= 1ull << (c->device & 63);
     }
     OBEM_CUDA(c, cudaMemsetAsync(ticket, 0, sizeof(int) * 3, s));
     for (int lower = 1; lower >= 0; --lower) {

@@ -422,10 +422,10 @@ int obem_tc_gemm_sub(obem_ctx *c, float *C, long long ldc, const float *A, long 
     rc = tc_map(c, &ma, Ab, M, K, ldk, TC_BM);
     if (rc == OBEM_OK) rc = tc_map(c, &mb, Bb, N, K, ldk, TC_BN);
     if (rc != OBEM_OK) return rc;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0;   // devices done (a bit each)
+    if (!(attr >> (c->device & 63) & 1ull)) {
         OBEM_CUDA(c, cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-        attr = true;
+        attr |= 1ull << (c->device & 63);
     }
     const long long tiles = (long long)((N + TC_BN - 1) / TC_BN) * ((M + TC_BM - 1) / TC_BM);
     if (tiles > 0x7fffffffll) return obem_fail(c, OBEM_ERR_ARG, "tensor-core GEMM: %d x %d exceeds the grid", M, N);
